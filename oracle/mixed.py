@@ -1,0 +1,73 @@
+"""The chosen mixed-precision form (oracle side).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The paper's preconditioner only has to be spectrally close to H (the event
+E_rho of Section 2.2 bounds ||C_S - I||), so the sketch and the sketched
+Gram matrix may be formed in low precision while the accuracy of the final
+iterate is restored by iterative refinement on the exact residual
+b - A^T A x - nu^2 Lambda x.  This module defines, in float64 arithmetic on
+exactly represented values, the pieces whose rounding decisions the GPU must
+reproduce bit for bit:
+
+* ``bf16_round``: float32 -> bfloat16 with round-to-nearest-even.
+* ``split_hi_lo``: A = hi + lo + tail with hi = bf16(A), lo = bf16(A - hi)
+  (A - hi is exact in float32), so hi + lo carries ~16 significant bits.
+* ``gaussian_sketch_bf16``: Y = bf16(G) (hi + lo), with G the Gaussian
+  entries of ``rng.gaussian_block`` rounded from float32.
+* ``refine``: the outer refinement loop around any inner solver.
+"""
+import numpy as np
+
+from . import rng as R
+from .solvers import hess_apply, h_norm_sq
+
+
+def bf16_round(x):
+    """Round float32 values to the nearest bfloat16 (ties to even); returns
+    float64 holding the exact bfloat16 values."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    u = (u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
+    return (u.astype(np.uint32)).view(np.float32).astype(np.float64)
+
+
+def split_hi_lo(A32):
+    """hi = bf16(A), lo = bf16(A - hi) for float32 A."""
+    A32 = np.asarray(A32, dtype=np.float32)
+    hi = bf16_round(A32)
+    rem = (A32.astype(np.float64) - hi).astype(np.float32)  # exact
+    lo = bf16_round(rem)
+    return hi, lo
+
+
+def gaussian_bf16(n_rows_data, m_rows, seed):
+    """bf16(float32(G)) with G from ``rng.gaussian_block`` (the GPU forms the
+    Box-Muller values in float32; values within one float32 ulp of a bfloat16
+    rounding midpoint may round the other way there, which the parity test's
+    tolerance absorbs)."""
+    G = R.gaussian_block(n_rows_data, m_rows, seed)
+    return bf16_round(G.astype(np.float32))
+
+
+def gaussian_sketch_bf16_unscaled(A32, m, seed):
+    """Y = bf16(G) (hi + lo): the mixed form's unscaled Gaussian sketch."""
+    hi, lo = split_hi_lo(A32)
+    Gb = gaussian_bf16(A32.shape[0], m, seed)
+    return Gb @ (hi + lo)
+
+
+def refine(A, b, nu, lam, inner, tol, max_outer=20):
+    """Iterative refinement: x <- x + inner(r) with r = b - H x formed from A in
+    float64, until ||r||_{H^{-1}} estimate via the inner solve is below tol
+    relative to ||x||_H.  ``inner(r)`` returns an approximate H^{-1} r.
+    Returns (x, outer iterations)."""
+    x = np.zeros_like(b, dtype=np.float64)
+    for it in range(1, max_outer + 1):
+        r = b - hess_apply(A, nu, lam, x)
+        dx = inner(r)
+        x = x + dx
+        if h_norm_sq(A, nu, lam, dx) <= (tol / 2.0) ** 2 * max(h_norm_sq(A, nu, lam, x), 1e-300):
+            return x, it
+    return x, max_outer

@@ -1,0 +1,206 @@
+"""Seeded generators of the five workloads the solver is measured on.
+
+All workloads follow the recipe of the paper's synthetic experiments
+(Section 6): A = U diag(sigma) V^T with U (n x d) and V (d x d) orthonormal and
+a prescribed decay of sigma.  U and V come from the QR factorisation of seeded
+N(0, 1) matrices, with the sign convention diag(R) > 0 so that the factor is
+unique.  ``make_problem`` does this in NumPy float64 (sizes the CPU handles in
+seconds); ``make_problem_torch`` does the same recipe on a torch device for the
+full benchmark sizes, orthonormalising by one CholeskyQR pass.
+
+Workloads (n rows, d columns):
+  C1  n=4096,  d=256,  sigma_j = 0.95^j,        nu=1e-2, Lambda=I,   b=A^T y
+  C2  n=2^17,  d=2048, sigma_j = 1/(1+j),       nu=1e-3, Lambda=1+9U, b=A^T y + 0.1 N(0,1)
+  C3  n=2^20,  d=4096, sigma_j = 0.98^j + 1e-6, nu=1e-4, Lambda=I,   b=A^T y   (A stored fp32)
+  C4  n=2^18,  d=1024, sigma_j = (1+j)^-1/2,    nu=1e-2, Lambda=1+U,  b=A^T N(0,1)^(n x 8)
+  C5  256 problems, n in [2^11, 2^16], d in [32, 1024] log-uniform with n >= 4d,
+      sigma_j = 0.9^j or 1/(1+j), nu log-uniform in [1e-4, 1e-1], Lambda=I.
+with y ~ N(0, 1)^n and j = 0, ..., d-1.
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+CONFIGS = {
+    "C1": dict(n=4096, d=256, decay="geom0.95", nu=1e-2, lam="identity", rhs="Aty", k=1,
+               dtype="f64", kind="gaussian", m_init=1, tol=1e-10),
+    "C2": dict(n=1 << 17, d=2048, decay="harmonic", nu=1e-3, lam="one_plus_9u", rhs="Aty_noise", k=1,
+               dtype="f64", kind="srht", m_init=16, m_max=4096, tol=1e-10),
+    "C3": dict(n=1 << 20, d=4096, decay="geom0.98_floor", nu=1e-4, lam="identity", rhs="Aty", k=1,
+               dtype="f32", kind="gaussian", m_init=1, tol=1e-8),
+    "C4": dict(n=1 << 18, d=1024, decay="sqrt_harmonic", nu=1e-2, lam="one_plus_u", rhs="Aty_multi", k=8,
+               dtype="f32", kind="gaussian", m_init=1, tol=1e-8),
+}
+
+
+def spectrum(decay, d):
+    """Singular values sigma_j, j = 0..d-1, for the named decay."""
+    j = np.arange(d, dtype=np.float64)
+    if decay == "geom0.95":
+        return 0.95 ** j
+    if decay == "geom0.9":
+        return 0.9 ** j
+    if decay == "geom0.995":
+        return 0.995 ** (j + 1)
+    if decay == "harmonic":
+        return 1.0 / (1.0 + j)
+    if decay == "geom0.98_floor":
+        return 0.98 ** j + 1e-6
+    if decay == "sqrt_harmonic":
+        return (1.0 + j) ** -0.5
+    raise ValueError(decay)
+
+
+@dataclass
+class Problem:
+    """One instance of problem (1).  A is n x d row-major; b is d x k."""
+    A: np.ndarray
+    b: np.ndarray
+    nu: float
+    lam: np.ndarray
+    sigma: np.ndarray = None
+    U: np.ndarray = None
+    V: np.ndarray = None
+    y: np.ndarray = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return self.A.shape[0]
+
+    @property
+    def d(self):
+        return self.A.shape[1]
+
+
+def _orthonormal(rng, rows, cols):
+    Z = rng.standard_normal((rows, cols))
+    Q, R = np.linalg.qr(Z)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s[None, :]
+
+
+def _lambda(kind, rng, d):
+    if kind == "identity":
+        return np.ones(d)
+    if kind == "one_plus_9u":
+        return 1.0 + 9.0 * rng.random(d)
+    if kind == "one_plus_u":
+        return 1.0 + rng.random(d)
+    raise ValueError(kind)
+
+
+def make_problem(config="C1", seed=0, n=None, d=None, nu=None, decay=None, lam=None,
+                 rhs=None, k=None, dtype=None):
+    """NumPy float64 generator (the stored matrix is rounded to float32 when the
+    workload stores A in float32; the float64 problem is then the exact upcast
+    of that float32 matrix, so both precisions solve the same problem)."""
+    cfg = dict(CONFIGS[config])
+    for key, val in dict(n=n, d=d, nu=nu, decay=decay, lam=lam, rhs=rhs, k=k, dtype=dtype).items():
+        if val is not None:
+            cfg[key] = val
+    n, d = int(cfg["n"]), int(cfg["d"])
+    rng = np.random.default_rng(seed)
+    U = _orthonormal(rng, n, d)
+    V = _orthonormal(rng, d, d)
+    sigma = spectrum(cfg["decay"], d)
+    A = (U * sigma[None, :]) @ V.T
+    if cfg["dtype"] == "f32":
+        A = A.astype(np.float32).astype(np.float64)
+    lam_v = _lambda(cfg["lam"], rng, d)
+    kk = int(cfg["k"])
+    if cfg["rhs"] == "Aty":
+        y = rng.standard_normal(n)
+        b = A.T @ y
+    elif cfg["rhs"] == "Aty_noise":
+        y = rng.standard_normal(n)
+        b = A.T @ y + 0.1 * rng.standard_normal(d)
+    elif cfg["rhs"] == "Aty_multi":
+        y = rng.standard_normal((n, kk))
+        b = A.T @ y
+    else:
+        raise ValueError(cfg["rhs"])
+    return Problem(A=np.ascontiguousarray(A), b=b, nu=float(cfg["nu"]), lam=lam_v, sigma=sigma,
+                   U=U, V=V, y=y, meta=dict(config=config, seed=seed, **cfg))
+
+
+def make_problem_torch(config="C2", seed=0, device="cuda", n=None, d=None):
+    """Same recipe as ``make_problem`` on a torch device, for full sizes.
+
+    Draws come from a seeded ``torch.Generator`` on the device (so the values
+    differ from the NumPy generator's); U is orthonormalised by CholeskyQR in
+    float64.  Returns a dict of device tensors: A64 (float64) and, for
+    float32-stored workloads, A32 with A64 its exact upcast; b (d x k); lam (d).
+    """
+    import torch
+
+    cfg = dict(CONFIGS[config])
+    if n is not None:
+        cfg["n"] = n
+    if d is not None:
+        cfg["d"] = d
+    n, d, kk = int(cfg["n"]), int(cfg["d"]), int(cfg["k"])
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+    sigma = torch.as_tensor(spectrum(cfg["decay"], d), device=device, dtype=f64)
+    # V: QR of a d x d Gaussian (small).
+    Zv = torch.randn(d, d, generator=g, device=device, dtype=f64)
+    V, Rv = torch.linalg.qr(Zv)
+    V = V * torch.sign(torch.diagonal(Rv))[None, :]
+    # U: CholeskyQR of an n x d Gaussian.  float32-stored workloads do the two
+    # n x d x d products in float32 (U then orthonormal to ~1e-5, which only
+    # perturbs the spectrum by that relative amount; the stored A defines the
+    # problem); float64 workloads do them in float64.
+    wdt = torch.float32 if cfg["dtype"] == "f32" else f64
+    Z = torch.randn(n, d, generator=g, device=device, dtype=wdt)
+    C = (Z.T @ Z).to(f64)
+    L = torch.linalg.cholesky(C)
+    # U = Z L^{-T}; then fold diag(sigma) V^T:  A = Z (L^{-T} diag(sigma) V^T)
+    M = torch.linalg.solve_triangular(L.T, torch.diag(sigma) @ V.T, upper=True).to(wdt)
+    A = torch.empty(n, d, device=device, dtype=wdt)
+    blk = 1 << 15
+    for r0 in range(0, n, blk):
+        A[r0:r0 + blk] = Z[r0:r0 + blk] @ M
+    del Z
+    if cfg["lam"] == "identity":
+        lam = torch.ones(d, device=device, dtype=f64)
+    elif cfg["lam"] == "one_plus_9u":
+        lam = 1.0 + 9.0 * torch.rand(d, generator=g, device=device, dtype=f64)
+    else:
+        lam = 1.0 + torch.rand(d, generator=g, device=device, dtype=f64)
+    out = dict(n=n, d=d, nu=float(cfg["nu"]), lam=lam, sigma=sigma, meta=dict(config=config, seed=seed, **cfg))
+    if cfg["dtype"] == "f32":
+        out["A32"] = A
+        A = A.to(f64)
+    out["A64"] = A
+    if cfg["rhs"] == "Aty":
+        y = torch.randn(n, 1, generator=g, device=device, dtype=f64)
+        b = A.T @ y
+    elif cfg["rhs"] == "Aty_noise":
+        y = torch.randn(n, 1, generator=g, device=device, dtype=f64)
+        b = A.T @ y + 0.1 * torch.randn(d, 1, generator=g, device=device, dtype=f64)
+    else:
+        y = torch.randn(n, kk, generator=g, device=device, dtype=f64)
+        b = A.T @ y
+    out["b"] = b
+    return out
+
+
+def batched_specs(count=256, seed=0):
+    """Shapes of the uneven batch C5: n and d log-uniform (n in [2^11, 2^16],
+    d in [32, 1024]) redrawn until n >= 4 d; decay 0.9^j or 1/(1+j) and nu
+    log-uniform in [1e-4, 1e-1], one draw per problem from the seed."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    while len(specs) < count:
+        n = int(round(math.exp(rng.uniform(math.log(2 ** 11), math.log(2 ** 16)))))
+        d = int(round(math.exp(rng.uniform(math.log(32), math.log(1024)))))
+        if n < 4 * d:
+            continue
+        decay = "geom0.9" if rng.random() < 0.5 else "harmonic"
+        nu = float(math.exp(rng.uniform(math.log(1e-4), math.log(1e-1))))
+        specs.append(dict(n=n, d=d, decay=decay, nu=nu, seed=int(rng.integers(0, 2 ** 31))))
+    return specs

@@ -1,0 +1,87 @@
+"""Pins of the oracle's gradient formulas (central finite differences) and of
+the mixed-precision rounding rules (torch's bfloat16 conversion, exactness of
+the hi/lo split)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import adjoint as ADJ
+from oracle import mixed as MX
+from oracle import solvers as S
+
+
+def _loss(A, B, nu, lam, C):
+    return float(np.sum(C * S.direct_solve(A, B, nu, lam)))
+
+
+def test_gradients_match_central_differences():
+    p = synthetic.make_problem("C4", 0, n=96, d=12)
+    A, B, nu, lam = p.A, p.b, p.nu, p.lam
+    rng = np.random.default_rng(7)
+    C = rng.standard_normal(B.shape)
+    _, g = ADJ.solve_and_grads(A, B, nu, lam, C)
+    h = 1e-3
+    # b: coordinate directions
+    for i in range(3):
+        E = np.zeros_like(B)
+        E[i, 1] = h
+        fd = (_loss(A, B + E, nu, lam, C) - _loss(A, B - E, nu, lam, C)) / (2 * h)
+        assert math.isclose(fd, g["b"][i, 1], rel_tol=1e-6, abs_tol=1e-9)
+    # A: random directions (scaled so the step is h in Frobenius norm)
+    for _ in range(4):
+        D = rng.standard_normal(A.shape)
+        D *= h / np.linalg.norm(D)
+        fd = (_loss(A + D, B, nu, lam, C) - _loss(A - D, B, nu, lam, C)) / 2
+        an = float(np.sum(g["A"] * D))
+        assert math.isclose(fd, an, rel_tol=1e-4, abs_tol=1e-9 * h)
+    # Lambda
+    for i in range(3):
+        E = np.zeros_like(lam)
+        E[i] = h
+        fd = (_loss(A, B, nu, lam + E, C) - _loss(A, B, nu, lam - E, C)) / (2 * h)
+        assert math.isclose(fd, g["lam"][i], rel_tol=1e-5, abs_tol=1e-9)
+    # nu, with a step relative to nu (a 1e-3 absolute step would be 10% of nu)
+    hn = 1e-3 * nu
+    fd = (_loss(A, B, nu + hn, lam, C) - _loss(A, B, nu - hn, lam, C)) / (2 * hn)
+    assert math.isclose(fd, g["nu"], rel_tol=1e-5)
+
+
+def test_bf16_round_matches_torch():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(100000).astype(np.float32),
+                        (rng.standard_normal(1000) * 1e-30).astype(np.float32),
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.01171875, 65504.0], dtype=np.float32)])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(MX.bf16_round(x), ref)
+
+
+def test_bf16_ties_to_even():
+    # 1 + 2^-8 is halfway between bf16 neighbours 1 and 1 + 2^-7: ties to even -> 1
+    assert MX.bf16_round(np.float32(1 + 2 ** -8)) == 1.0
+    # 1 + 3 * 2^-8 is halfway between 1 + 2^-7 and 1 + 2^-6: ties to even -> 1 + 2^-6
+    assert MX.bf16_round(np.float32(1 + 3 * 2 ** -8)) == 1 + 2 ** -6
+
+
+def test_split_hi_lo_accuracy():
+    A = np.random.default_rng(1).standard_normal((200, 30)).astype(np.float32)
+    hi, lo = MX.split_hi_lo(A)
+    assert np.array_equal(MX.bf16_round(hi.astype(np.float32)), hi)
+    assert np.array_equal(MX.bf16_round(lo.astype(np.float32)), lo)
+    err = np.abs(A.astype(np.float64) - hi - lo)
+    assert np.all(err <= np.abs(A) * 2.0 ** -16)
+
+
+def test_refine_reaches_tolerance_with_inexact_inner():
+    p = synthetic.make_problem("C1", 0, n=1024, d=64, nu=1e-4)
+    xs = S.direct_solve(p.A, p.b, p.nu, p.lam)
+    H32 = S.hessian(p.A, p.nu, p.lam).astype(np.float32)
+
+    def inner(r):  # a float32 direct solve: relative accuracy ~1e-3 at this kappa
+        return np.linalg.solve(H32, r.astype(np.float32)).astype(np.float64)
+
+    x, outer = MX.refine(p.A, p.b, p.nu, p.lam, inner, tol=1e-10)
+    assert outer > 1
+    assert S.rel_err_H(p.A, p.nu, p.lam, x, xs) <= 1e-10

@@ -1,0 +1,210 @@
+/*
+ * sks.h -- C ABI of the GB300 (sm_103a) adaptive sketching-based solvers for
+ *
+ *     x* = argmin_x  1/2 <x, H x> - b^T x,   H = A^T A + nu^2 Lambda      (eq. 1)
+ *
+ * of Lacotte & Pilanci, "Fast Convex Quadratic Optimization Solvers with
+ * Adaptive Sketching-based Preconditioners" (arXiv 2104.14101).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named "device" point to GPU global memory of the current device;
+ *   they are borrowed, never freed, and must stay valid until the work queued
+ *   on `stream` has finished.  Host pointers are read before the call returns.
+ * - A is n x d, row-major, leading dimension lda >= d (elements), stored as
+ *   float64 (SKS_F64) or float32 (SKS_F32).  The base address must be 16-byte
+ *   aligned and lda * sizeof(element) a multiple of 16 bytes (A is streamed by
+ *   the Tensor Memory Accelerator); otherwise SKS_ERR_INVALID_ARG.
+ * - Vectors of length d with k right-hand sides are d x k column-major
+ *   float64 arrays (column c starts at element c*d).
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy stream.
+ *   All GPU work is queued on it in order.
+ * - Scratch memory is caller-allocated device memory (`ws`, `ws_bytes`), sized
+ *   by the matching *_workspace_size query; the library allocates no device
+ *   memory.  Handles (sks_sketch, sks_precond) are small host objects that
+ *   refer to their own caller-allocated device storage.
+ * - Every entry point returns an sks_status and never aborts; on failure
+ *   sks_last_error() describes the cause (thread-local string).
+ */
+#ifndef SKS_H_
+#define SKS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SKS_OK = 0,
+  SKS_ERR_INVALID_ARG = 1,    /* bad size, pointer, alignment, nu <= 0, lambda_i < 1 */
+  SKS_ERR_NOT_PD = 2,         /* non-positive pivot in a Cholesky factorisation      */
+  SKS_ERR_NO_CONVERGENCE = 3, /* max_iter reached; x holds the last accepted iterate */
+  SKS_ERR_NUMERIC = 4,        /* NaN / Inf met in the iteration                      */
+  SKS_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out                  */
+  SKS_ERR_CUDA = 6,           /* a CUDA runtime call failed                          */
+  SKS_ERR_WORKSPACE = 7,      /* ws_bytes smaller than the size query returned       */
+  SKS_ERR_UNSUPPORTED = 8     /* valid request that this build does not implement    */
+} sks_status;
+
+/* Random embeddings of Section 2.1. */
+typedef enum {
+  SKS_SRHT = 0,     /* S = R H E: Walsh-Hadamard of the sign-flipped, zero-padded A, rows subsampled */
+  SKS_GAUSSIAN = 1, /* i.i.d. N(0, 1/m) entries, generated from Philox, never stored               */
+  SKS_SJLT = 2      /* s nonzeros +-1/sqrt(s) per column at distinct hashed rows                    */
+} sks_kind;
+
+typedef enum { SKS_F64 = 0, SKS_F32 = 1 } sks_dtype;
+
+/* Arithmetic of a solve. */
+typedef enum {
+  SKS_PLAIN_F64 = 0,    /* everything in float64 (A must be SKS_F64)                           */
+  SKS_MIXED_REFINED = 1 /* float32 A, BF16/float32 sketch and inner PCG, float64 refinement      */
+} sks_precision;
+
+/* Problem (1).  A, b, lambda_diag: device pointers. */
+typedef struct {
+  sks_dtype dtype;
+  int64_t n, d, lda, k;        /* k = number of right-hand sides (columns of b)    */
+  const void* A;               /* n x d row-major, leading dimension lda           */
+  const double* b;             /* d x k column-major float64                       */
+  double nu;                   /* nu > 0                                           */
+  const double* lambda_diag;   /* d entries, each >= 1 (Lambda >= I_d, eq. 1)      */
+} sks_problem;
+
+/* One improvement test of Algorithm 1 / 2 (optional host-side trace). */
+typedef struct {
+  int64_t t;         /* time index of the step                        */
+  int64_t m;         /* sketch size used by the step                  */
+  double ratio;      /* delta~+ / delta~_I                            */
+  double threshold;  /* c(rho) phi(rho)^(t+1-I)                       */
+  int32_t accepted;  /* 1: x+ accepted; 0: rejected, m doubled        */
+  int32_t outer;     /* refinement step (mixed form), 0 otherwise     */
+} sks_trace_event;
+
+/* Options of Algorithms 1 and 2 (defaults by sks_opts_default). */
+typedef struct {
+  double rho;          /* rate parameter rho in (0, 1); default 1/8 (Section 4.1)            */
+  int64_t m_init;      /* initial sketch size m_init >= 1                                    */
+  int64_t m_max;       /* cap on m; 0 = n_pad (SRHT) or n (Gaussian, SJLT)                   */
+  sks_kind kind;       /* embedding                                                          */
+  int sjlt_s;          /* nonzeros per column of the SJLT (>= 1)                             */
+  double tol;          /* target ||x - x*||_H / ||x*||_H                                     */
+  int64_t max_iter;    /* bound T on accepted iterations                                     */
+  sks_precision precision;
+  int reuse_residual;  /* 1: keep the recursive r_t at a restart (Algorithm 2 recomputes it) */
+  uint64_t seed;       /* Philox key of every random draw                                    */
+  int64_t max_outer;   /* refinement steps of SKS_MIXED_REFINED                              */
+  double inner_tol;    /* relative accuracy asked of each inner solve (mixed form)           */
+  sks_trace_event* trace; /* optional host array receiving every test; NULL = none            */
+  int64_t trace_cap;   /* capacity of `trace`                                                */
+} sks_opts;
+
+/* Per-solve statistics (host struct, filled before the solve returns). */
+typedef struct {
+  int64_t iters;          /* accepted iterations t                              */
+  int64_t rejections;     /* failed improvement tests (= sketch doublings)      */
+  int64_t final_m;        /* sketch size at exit                                */
+  int64_t a_passes;       /* full reads of A by the iteration (H p, residuals)  */
+  int64_t sketch_passes;  /* sketch formations / extensions                     */
+  int64_t factorizations; /* preconditioner builds                              */
+  int64_t outer_iters;    /* refinement steps (mixed form)                      */
+  double final_delta_tilde;
+  double est_rel_err;     /* sqrt(delta~_t / b^T x_t): the stop rule's estimate */
+  int64_t trace_len;      /* events written to opts.trace                       */
+  float ms_total, ms_sketch, ms_factor, ms_iter;
+  sks_status status;
+} sks_stats;
+
+typedef struct sks_sketch sks_sketch;
+typedef struct sks_precond sks_precond;
+
+/* Fill `o` with the defaults: rho = 1/8, m_init = 1, m_max = 0, SRHT, s = 1,
+ * tol = 1e-10, max_iter = 1000, plain float64, reuse_residual = 1, seed = 0,
+ * max_outer = 20, inner_tol = 1e-4, no trace. */
+void sks_opts_default(sks_opts* o);
+
+/* Version string of the library build. */
+const char* sks_version(void);
+
+/* Last error message of the calling thread ("" if none). */
+const char* sks_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Hessian pass (Section 4.1.2: the O(nd) per-iteration cost).
+ * y = A^T (A x) + nu^2 Lambda x for the k columns of x, in ONE read of A.
+ * x, y: device d x k column-major float64 (y may not alias x).  Arithmetic in
+ * the precision of A (float32 A: float32 products and row sums, float64
+ * cross-block accumulation), or with `extended` = 1 float64 arithmetic on any
+ * A (the refinement residual of the mixed form).
+ * ws: device scratch of sks_hess_apply_workspace_size(problem) bytes.
+ * ------------------------------------------------------------------------- */
+sks_status sks_hess_apply_workspace_size(const sks_problem* p, size_t* bytes);
+sks_status sks_hess_apply(const sks_problem* p, const double* x, double* y, int extended,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Sketch S A of Section 2.1 with nested growth.
+ * sks_sketch_create forms S_m A for m = m_init (SRHT: also the n_pad x d
+ * matrix H E A_pad, once); sks_sketch_grow(new_m) extends it to new_m >= m
+ * rows (SRHT: gathers more rows of H E A_pad; Gaussian: appends rows of G A;
+ * SJLT: re-hashes and re-forms S A in one pass).  The sketch is kept in the
+ * precision of A and "unscaled": S A = scale * Y with scale = 1/sqrt(m) (SRHT,
+ * Gaussian) or 1 (SJLT); sks_sketch_copy_out writes the scaled S A (m x d
+ * row-major float64).
+ * Random draws: Philox4x32-10 keyed by `seed`, bit-identical to the oracle.
+ * ws: device scratch of sks_sketch_workspace_size bytes, owned by the handle
+ * until sks_sketch_destroy.
+ * ------------------------------------------------------------------------- */
+sks_status sks_sketch_workspace_size(const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s,
+                                     size_t* bytes);
+sks_status sks_sketch_create(sks_sketch** out, const sks_problem* p, sks_kind kind, int64_t m_init,
+                             int64_t m_max, int sjlt_s, uint64_t seed, void* ws, size_t ws_bytes,
+                             void* stream);
+sks_status sks_sketch_grow(sks_sketch* s, int64_t new_m, void* stream);
+sks_status sks_sketch_rows(const sks_sketch* s, int64_t* m);
+sks_status sks_sketch_copy_out(const sks_sketch* s, double* SA, void* stream);
+void sks_sketch_destroy(sks_sketch* s);
+
+/* ---------------------------------------------------------------------------
+ * Sketched preconditioner H_S = (SA)^T SA + nu^2 Lambda (Section 4.1.1).
+ * m >= d: float64 Cholesky of the d x d matrix H_S; m < d: float64 Cholesky of
+ * W_S = SA Lambda^{-1} (SA)^T + nu^2 I_m and the Woodbury identity
+ *   v = (Lambda^{-1}/nu^2) (I - (SA)^T W_S^{-1} SA Lambda^{-1}) z.
+ * The triangular factor is inverted explicitly so that an apply is two
+ * matrix-vector products.  Returns SKS_ERR_NOT_PD on a non-positive pivot.
+ * sks_precond_apply: v = H_S^{-1} z for k columns (device float64 d x k).
+ * ------------------------------------------------------------------------- */
+sks_status sks_precond_workspace_size(const sks_problem* p, int64_t m_max, size_t* bytes);
+sks_status sks_precond_build(sks_precond** out, const sks_sketch* s, const sks_problem* p,
+                             void* ws, size_t ws_bytes, void* stream);
+sks_status sks_precond_apply(const sks_precond* P, const double* z, double* v, int64_t k, void* stream);
+void sks_precond_destroy(sks_precond* P);
+
+/* ---------------------------------------------------------------------------
+ * Adaptive solvers.
+ * sks_adaptive_pcg_solve: Algorithm 2 (adaptive PCG).
+ * sks_adaptive_ihs_solve: Algorithm 1 with the IHS step x - (1-rho) H_S^{-1} grad f(x)
+ *                         (Theorem 3.2).
+ * Both start from m = m_init, test delta~+/delta~_I > c(rho) phi(rho)^(t+1-I)
+ * after every step, and on failure double m (capped at m_max, where the step is
+ * accepted instead), extend the sketch, refactor H_S and restart at x_t.
+ * Stop rule (the paper prescribes none; Remark 4.2): after an accepted step,
+ * stop when the estimate delta~_t / (b^T x_t) of ||x_t - x*||_H^2/||x*||_H^2
+ * is <= (tol/2)^2 (IHS: 2 delta~_t).  k > 1 right-hand sides are solved one
+ * after the other.
+ * x: device float64 d x k, in: x_0, out: the solution.  stats: host, may be NULL.
+ * ws: device scratch of sks_solve_workspace_size bytes.
+ * Returns SKS_ERR_NO_CONVERGENCE if max_iter accepted steps did not reach tol.
+ * ------------------------------------------------------------------------- */
+sks_status sks_solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes);
+sks_status sks_adaptive_pcg_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                                  void* ws, size_t ws_bytes, void* stream);
+sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                                  void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKS_H_ */

@@ -1,0 +1,236 @@
+"""Python front of the sks library: torch tensors in, torch tensors out.
+
+Only argument marshalling lives here -- every step of the computation runs in
+the CUDA kernels of ``libsks.so``.  Device memory (inputs, outputs and the
+scratch workspaces the C ABI asks for) is allocated with torch; the current
+torch stream is passed to every call.
+"""
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+
+def _stream(device=None):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(None)
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def make_problem(A, b, nu, lam):
+    """Build the C problem struct from device tensors.
+
+    A: (n, d) float64 or float32, rows contiguous (stride(1) == 1).
+    b: (d,) or (d, k) float64 -- k right-hand sides.
+    lam: (d,) float64, entries >= 1.
+    Returns (problem_struct, b2d) where b2d is the column-major d x k copy kept alive.
+    """
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be 2-D with unit column stride")
+    if A.dtype not in (torch.float64, torch.float32):
+        raise ValueError("A must be float64 or float32")
+    n, d = A.shape
+    esz = A.element_size()
+    if n > 0 and ((A.stride(0) * esz) % 16 != 0 or A.data_ptr() % 16 != 0 or (n == 1 and (d * esz) % 16 != 0)):
+        # The C ABI streams A with 2-D tensor copies, which need 16-byte rows:
+        # pad the leading dimension (a marshalling copy, same values).
+        ld = (d * esz + 15) // 16 * 16 // esz
+        Ap = torch.zeros(n, ld, dtype=A.dtype, device=A.device)
+        Ap[:, :d] = A
+        A = Ap[:, :d]
+    b = b.to(device=A.device, dtype=torch.float64)
+    if b.dim() == 1:
+        b = b[:, None]
+    k = b.shape[1]
+    bcm = b.t().contiguous()  # k x d row-major == d x k column-major
+    lam = lam.to(device=A.device, dtype=torch.float64).contiguous()
+    p = L.Problem()
+    p.dtype = L.F64 if A.dtype == torch.float64 else L.F32
+    p.n, p.d, p.lda, p.k = n, d, (A.stride(0) if n > 0 else (d * esz + 15) // 16 * 16 // esz), k
+    p.A = A.data_ptr() if n > 0 else None
+    p.b = bcm.data_ptr()
+    p.nu = float(nu)
+    p.lambda_diag = lam.data_ptr()
+    return p, (A, bcm, lam)
+
+
+def hess_apply(A, x, nu, lam, extended=False):
+    """y = A^T (A x) + nu^2 Lambda x in one pass over A (x: (d,) or (d, k) float64)."""
+    lib = L.load()
+    x2 = x.to(torch.float64)
+    squeeze = x2.dim() == 1
+    if squeeze:
+        x2 = x2[:, None]
+    xcm = x2.t().contiguous()
+    p, keep = make_problem(A, x2, nu, lam)  # b slot unused by the pass
+    ycm = torch.empty_like(xcm)
+    nb = C.c_size_t()
+    L.check(lib.sks_hess_apply_workspace_size(C.byref(p), C.byref(nb)))
+    ws = _workspace(nb.value, A.device)
+    L.check(lib.sks_hess_apply(C.byref(p), _ptr(xcm), _ptr(ycm), int(bool(extended)), _ptr(ws), nb.value,
+                               _stream(A.device)))
+    y = ycm.t()
+    return y[:, 0] if squeeze else y.contiguous()
+
+
+class Sketch:
+    """Nested sketch S_m A (Section 2.1) held on the device."""
+
+    def __init__(self, A, nu, lam, kind="srht", m=1, m_max=0, sjlt_s=1, seed=0):
+        self._lib = L.load()
+        b = torch.zeros(A.shape[1], dtype=torch.float64, device=A.device)
+        self.problem, self._keep = make_problem(A, b, nu, lam)
+        nb = C.c_size_t()
+        L.check(self._lib.sks_sketch_workspace_size(C.byref(self.problem), L.KINDS[kind], int(m_max), int(sjlt_s),
+                                                    C.byref(nb)))
+        self.ws = _workspace(nb.value, A.device)
+        h = C.c_void_p()
+        L.check(self._lib.sks_sketch_create(C.byref(h), C.byref(self.problem), L.KINDS[kind], int(m), int(m_max),
+                                            int(sjlt_s), C.c_uint64(seed), _ptr(self.ws), nb.value,
+                                            _stream(A.device)))
+        self.handle = h
+        self.device = A.device
+        self.m_max = int(m_max)
+
+    @property
+    def m(self):
+        v = C.c_int64()
+        L.check(self._lib.sks_sketch_rows(self.handle, C.byref(v)))
+        return v.value
+
+    def grow(self, new_m):
+        L.check(self._lib.sks_sketch_grow(self.handle, int(new_m), _stream(self.device)))
+
+    def matrix(self):
+        """S A (m x d float64, scaled)."""
+        out = torch.empty(self.m, int(self.problem.d), dtype=torch.float64, device=self.device)
+        L.check(self._lib.sks_sketch_copy_out(self.handle, _ptr(out), _stream(self.device)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self._lib.sks_sketch_destroy(self.handle)
+            self.handle = None
+
+
+class Preconditioner:
+    """H_S = (SA)^T SA + nu^2 Lambda factored on the device (Section 4.1.1)."""
+
+    def __init__(self, sketch, m_max=None):
+        self._lib = L.load()
+        self.sketch = sketch
+        p = sketch.problem
+        mm = int(m_max) if m_max else max(sketch.m, 1)
+        nb = C.c_size_t()
+        L.check(self._lib.sks_precond_workspace_size(C.byref(p), mm, C.byref(nb)))
+        # the handle is sized by the sketch's own m_max; ask for the larger
+        nb2 = C.c_size_t()
+        L.check(self._lib.sks_precond_workspace_size(C.byref(p), max(mm, self._sketch_mmax()), C.byref(nb2)))
+        self.ws = _workspace(max(nb.value, nb2.value), sketch.device)
+        h = C.c_void_p()
+        L.check(self._lib.sks_precond_build(C.byref(h), sketch.handle, C.byref(p), _ptr(self.ws), self.ws.numel(),
+                                            _stream(sketch.device)))
+        self.handle = h
+
+    def _sketch_mmax(self):
+        p = self.sketch.problem
+        if self.sketch.m_max > 0:
+            return self.sketch.m_max
+        n = int(p.n)
+        npad = 1
+        while npad < max(n, 1):
+            npad <<= 1
+        return npad
+
+    def apply(self, z):
+        z2 = z.to(torch.float64)
+        squeeze = z2.dim() == 1
+        if squeeze:
+            z2 = z2[:, None]
+        zcm = z2.t().contiguous()
+        vcm = torch.empty_like(zcm)
+        L.check(self._lib.sks_precond_apply(self.handle, _ptr(zcm), _ptr(vcm), zcm.shape[0], _stream(self.sketch.device)))
+        v = vcm.t()
+        return v[:, 0] if squeeze else v.contiguous()
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self._lib.sks_precond_destroy(self.handle)
+            self.handle = None
+
+
+def options(kind="srht", rho=0.125, m_init=1, m_max=0, sjlt_s=1, tol=1e-10, max_iter=1000, precision="plain",
+            reuse_residual=True, seed=0, max_outer=20, inner_tol=1e-4):
+    lib = L.load()
+    o = L.Opts()
+    lib.sks_opts_default(C.byref(o))
+    o.kind = L.KINDS[kind]
+    o.rho, o.m_init, o.m_max, o.sjlt_s = float(rho), int(m_init), int(m_max), int(sjlt_s)
+    o.tol, o.max_iter = float(tol), int(max_iter)
+    o.precision = L.PLAIN_F64 if precision == "plain" else L.MIXED_REFINED
+    o.reuse_residual = int(bool(reuse_residual))
+    o.seed = int(seed)
+    o.max_outer, o.inner_tol = int(max_outer), float(inner_tol)
+    return o
+
+
+class Solver:
+    """Reusable adaptive solver: sizes and holds the workspace once, then
+    ``solve`` can be called repeatedly (the hot path of a benchmark)."""
+
+    def __init__(self, A, b, nu, lam, method="pcg", trace_cap=0, **opts):
+        self._lib = L.load()
+        self.method = method
+        self.problem, self._keep = make_problem(A, b, nu, lam)
+        self.opts = options(**opts)
+        self.trace_buf = (L.TraceEvent * trace_cap)() if trace_cap else None
+        if trace_cap:
+            self.opts.trace = C.cast(self.trace_buf, C.POINTER(L.TraceEvent))
+            self.opts.trace_cap = trace_cap
+        nb = C.c_size_t()
+        L.check(self._lib.sks_solve_workspace_size(C.byref(self.problem), C.byref(self.opts), C.byref(nb)))
+        self.ws = _workspace(nb.value, A.device)
+        self.device = A.device
+        self.d, self.k = int(self.problem.d), int(self.problem.k)
+
+    def solve(self, x0=None, check=True):
+        xcm = torch.zeros(self.k, self.d, dtype=torch.float64, device=self.device)
+        if x0 is not None:
+            x02 = x0.to(torch.float64)
+            xcm.copy_((x02[:, None] if x02.dim() == 1 else x02).t())
+        st = L.Stats()
+        fn = self._lib.sks_adaptive_pcg_solve if self.method == "pcg" else self._lib.sks_adaptive_ihs_solve
+        status = fn(C.byref(self.problem), C.byref(self.opts), _ptr(xcm), C.byref(st), _ptr(self.ws),
+                    self.ws.numel(), _stream(self.device))
+        if check and status not in (L.OK,):
+            L.check(status)
+        x = xcm.t()
+        x = x[:, 0] if self.k == 1 else x.contiguous()
+        stats = st.as_dict()
+        stats["status_name"] = L.STATUS_NAMES.get(status, status)
+        trace = []
+        if self.trace_buf is not None:
+            for i in range(st.trace_len):
+                e = self.trace_buf[i]
+                trace.append(dict(t=e.t, m=e.m, ratio=e.ratio, thr=e.threshold, accepted=bool(e.accepted),
+                                  outer=e.outer))
+        return x, stats, trace
+
+
+def adaptive_pcg(A, b, nu, lam, x0=None, trace_cap=0, **opts):
+    """Algorithm 2 on the GPU; returns (x, stats, trace)."""
+    return Solver(A, b, nu, lam, method="pcg", trace_cap=trace_cap, **opts).solve(x0)
+
+
+def adaptive_ihs(A, b, nu, lam, x0=None, trace_cap=0, **opts):
+    """Algorithm 1 with the IHS step (mu = 1 - rho) on the GPU; returns (x, stats, trace)."""
+    return Solver(A, b, nu, lam, method="ihs", trace_cap=trace_cap, **opts).solve(x0)

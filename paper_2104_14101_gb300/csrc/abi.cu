@@ -1,0 +1,48 @@
+// abi.cu -- the exported C entry points that are not tied to a handle type
+// (options, version, errors, the Hessian pass and the adaptive solvers).
+#include "internal.h"
+
+using namespace sks;
+
+extern "C" void sks_opts_default(sks_opts* o) {
+  if (!o) return;
+  o->rho = 0.125;
+  o->m_init = 1;
+  o->m_max = 0;
+  o->kind = SKS_SRHT;
+  o->sjlt_s = 1;
+  o->tol = 1e-10;
+  o->max_iter = 1000;
+  o->precision = SKS_PLAIN_F64;
+  o->reuse_residual = 1;
+  o->seed = 0;
+  o->max_outer = 20;
+  o->inner_tol = 1e-4;
+  o->trace = nullptr;
+  o->trace_cap = 0;
+}
+
+extern "C" const char* sks_version(void) { return "sks 0.1 (sm_103a)"; }
+
+extern "C" const char* sks_last_error(void) { return last_error_cstr(); }
+
+extern "C" sks_status sks_hess_apply_workspace_size(const sks_problem* p, size_t* bytes) { return hess_apply_ws(p, bytes); }
+
+extern "C" sks_status sks_hess_apply(const sks_problem* p, const double* x, double* y, int extended, void* ws,
+                                     size_t ws_bytes, void* stream) {
+  return hess_apply(p, x, y, extended, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" sks_status sks_solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes) {
+  return solve_workspace_size(p, o, bytes);
+}
+
+extern "C" sks_status sks_adaptive_pcg_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                                             void* ws, size_t ws_bytes, void* stream) {
+  return adaptive_solve(0, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                                             void* ws, size_t ws_bytes, void* stream) {
+  return adaptive_solve(1, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
+}

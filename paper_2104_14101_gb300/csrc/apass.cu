@@ -1,0 +1,365 @@
+// apass.cu -- K1: the Hessian pass  y = A^T (A x) + nu^2 Lambda x  in ONE read
+// of A (Section 4.1.2: the O(nd) gradient / H p cost that dominates every
+// iteration of the IHS and of PCG).
+//
+// Design (GB300): a persistent grid, one CTA per SM.  Warp 8 is a producer
+// that streams row tiles of A into a ring of shared-memory stages with 2-D
+// bulk tensor copies (TMA, mbarrier completion); warps 0-7 consume.  Every
+// consumer thread owns a fixed set of 16-byte column vectors of the row, so
+// the running sum  sum_i (a_i^T x) a_i  stays in its registers for the whole
+// pass.  Per row, the dot a_i^T x is reduced over the group of threads that
+// shares the row (a warp for narrow rows, the 256 consumers for wide rows).
+// Each CTA (or warp group) writes one partial d-vector; a second small kernel
+// sums the partials in float64 and adds nu^2 lambda .* x.
+// Rows and columns past the edge of A are zero-filled by the tensor copy, so
+// there is no tail handling in the inner loop.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace sks {
+
+namespace {
+
+template <typename TA>
+struct Vec;
+template <>
+struct Vec<double> {
+  using T = double2;
+  static constexpr int N = 2;
+  static SKS_DEV void load(const double* p, double* o) {
+    const double2 v = *(const double2*)p;
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+};
+template <>
+struct Vec<float> {
+  using T = float4;
+  static constexpr int N = 4;
+  static SKS_DEV void load(const float* p, float* o) {
+    const float4 v = *(const float4*)p;
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+};
+
+constexpr int kConsumers = 256;
+constexpr int kThreads = kConsumers + 32;
+constexpr int kRC = 2;  // rows reduced together
+
+struct ApassArgs {
+  int d, dp, boxw, nbox, rows, stages, q, ntiles;
+  const void* x;  // d x K column-major, vector type
+  void* partials; // [grid * NG][K][d]
+  DevStatus* st;
+};
+
+SKS_HD size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename TA, typename TX, int G, int K>
+SKS_HD size_t apass_smem_bytes(int rows, int dp, int stages) {
+  size_t b = align_up((size_t)stages * rows * dp * sizeof(TA), 128);
+  b += align_up((size_t)K * dp * sizeof(TX), 128);
+  b += align_up((size_t)2 * 8 * kRC * K * sizeof(TX), 128);
+  b += 2 * 8 * (size_t)stages;
+  return b;
+}
+
+template <typename TA, typename TX, int G, int QMAX, int K>
+__global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constant__ CUtensorMap tmap, ApassArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int VEC = Vec<TA>::N;
+  constexpr int NG = kConsumers / G;
+  const int tid = threadIdx.x;
+  const size_t stage_elems = (size_t)a.rows * a.dp;
+  TA* stage0 = (TA*)smem;
+  size_t off = align_up((size_t)a.stages * stage_elems * sizeof(TA), 128);
+  TX* xs = (TX*)(smem + off);
+  off += align_up((size_t)K * a.dp * sizeof(TX), 128);
+  TX* red = (TX*)(smem + off);
+  off += align_up((size_t)2 * 8 * kRC * K * sizeof(TX), 128);
+  uint64_t* full = (uint64_t*)(smem + off);
+  uint64_t* empty = full + a.stages;
+  __shared__ volatile int abort_flag;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumers / 32);
+    }
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  // x -> shared, zero padded to dp columns
+  const TX* xg = (const TX*)a.x;
+  for (int i = tid; i < K * a.dp; i += blockDim.x) {
+    const int c = i / a.dp, j = i - c * a.dp;
+    xs[i] = (j < a.d) ? xg[(size_t)c * a.d + j] : TX(0);
+  }
+  __syncthreads();
+
+  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(TA));
+
+  if (tid >= kConsumers) {
+    // ------------------------------------------------------------ producer
+    if (tid == kConsumers) {
+      int it = 0;
+      for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+        const int s = it % a.stages;
+        const uint32_t ph = (uint32_t)(it / a.stages) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, a.st, 12)) break;
+        mbar_arrive_expect_tx(&full[s], stage_bytes);
+        TA* dst = stage0 + (size_t)s * stage_elems;
+        for (int b = 0; b < a.nbox; ++b)
+          tma_load_2d(dst + (size_t)b * a.rows * a.boxw, &tmap, &full[s], b * a.boxw, tile * a.rows);
+      }
+      // drain: every issued copy has landed before the CTA may exit
+      const int first = it > a.stages ? it - a.stages : 0;
+      for (int k = first; k < it; ++k) mbar_wait(&full[k % a.stages], (uint32_t)(k / a.stages) & 1u, a.st, 13);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int g = tid / G, l = tid % G;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int nvec = a.dp / VEC;
+  const int rg = a.rows / NG;  // rows of a stage handled by this group
+  TX acc[QMAX][VEC][K];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q)
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[q][e][c] = TX(0);
+
+  int buf = 0;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+    const int s = it % a.stages;
+    const uint32_t ph = (uint32_t)(it / a.stages) & 1u;
+    const bool ok = mbar_wait_warp(&full[s], ph, a.st, 11);
+    if (G > 32) {
+      // keep the 256 consumers in lock step: a timed-out warp flags, all leave
+      if (!ok && lane == 0) abort_flag = 1;
+      named_bar_sync(2, kConsumers);
+      if (abort_flag) break;
+    } else if (!ok) {
+      break;
+    }
+    const TA* S = stage0 + (size_t)s * stage_elems;
+    for (int j0 = 0; j0 < rg; j0 += kRC) {
+      TA v[kRC][QMAX][VEC];
+      TX dot[kRC][K];
+#pragma unroll
+      for (int rc = 0; rc < kRC; ++rc) {
+        const int r = g + NG * (j0 + rc);
+        const bool rok = (j0 + rc) < rg;
+#pragma unroll
+        for (int c = 0; c < K; ++c) dot[rc][c] = TX(0);
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          const int vi = l + q * G;
+          if (rok && q < a.q && vi < nvec) {
+            const int col = vi * VEC;
+            const int b = col / a.boxw, jj = col - b * a.boxw;
+            Vec<TA>::load(S + (size_t)b * a.rows * a.boxw + (size_t)r * a.boxw + jj, v[rc][q]);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+#pragma unroll
+              for (int c = 0; c < K; ++c) dot[rc][c] += (TX)v[rc][q][e] * xs[c * a.dp + col + e];
+          } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) v[rc][q][e] = TA(0);
+          }
+        }
+      }
+      // reduce the dots over the group sharing the rows
+#pragma unroll
+      for (int rc = 0; rc < kRC; ++rc)
+#pragma unroll
+        for (int c = 0; c < K; ++c) dot[rc][c] = warp_sum(dot[rc][c]);
+      if (G > 32) {
+        TX* rb = red + buf * (8 * kRC * K);
+        if (lane == 0) {
+#pragma unroll
+          for (int rc = 0; rc < kRC; ++rc)
+#pragma unroll
+            for (int c = 0; c < K; ++c) rb[warp * kRC * K + rc * K + c] = dot[rc][c];
+        }
+        named_bar_sync(1, kConsumers);
+#pragma unroll
+        for (int rc = 0; rc < kRC; ++rc)
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            TX t = TX(0);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) t += rb[w * kRC * K + rc * K + c];
+            dot[rc][c] = t;
+          }
+        buf ^= 1;
+      }
+      // rank-one updates  acc += (a_r^T x) a_r
+#pragma unroll
+      for (int rc = 0; rc < kRC; ++rc)
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e)
+#pragma unroll
+            for (int c = 0; c < K; ++c) acc[q][e][c] += dot[rc][c] * (TX)v[rc][q][e];
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+
+  TX* out = (TX*)a.partials + (size_t)(blockIdx.x * NG + g) * K * a.d;
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+    const int vi = l + q * G;
+    if (q < a.q && vi < nvec) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const int col = vi * VEC + e;
+        if (col < a.d)
+#pragma unroll
+          for (int c = 0; c < K; ++c) out[(size_t)c * a.d + col] = acc[q][e][c];
+      }
+    }
+  }
+}
+
+// y[c][j] = sum_p partials[p][c][j] + nu2 * lambda[j] * x[c][j]   (float64 sum)
+// (y = sgn * H x + addc * addv when addv is given: residuals b - H x, gradients H x - b)
+template <typename TX>
+__global__ void apass_finalize(int nparts, int d, int k, const TX* __restrict__ partials, const TX* __restrict__ x,
+                               TX* __restrict__ y, double nu2, const double* __restrict__ lambda, double sgn,
+                               const TX* __restrict__ addv, double addc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (j >= d) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int p = 0;
+  for (; p + 3 < nparts; p += 4) {
+    s0 += (double)partials[((size_t)(p + 0) * k + c) * d + j];
+    s1 += (double)partials[((size_t)(p + 1) * k + c) * d + j];
+    s2 += (double)partials[((size_t)(p + 2) * k + c) * d + j];
+    s3 += (double)partials[((size_t)(p + 3) * k + c) * d + j];
+  }
+  for (; p < nparts; ++p) s0 += (double)partials[((size_t)p * k + c) * d + j];
+  const double xv = (double)x[(size_t)c * d + j];
+  double v = sgn * ((s0 + s1) + (s2 + s3) + nu2 * lambda[j] * xv);
+  if (addv) v += addc * (double)addv[(size_t)c * d + j];
+  y[(size_t)c * d + j] = (TX)v;
+}
+
+template <typename TA, typename TX, int G, int QMAX, int K>
+sks_status launch_t(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int64_t d, const void* x,
+                    void* y, double nu2, const double* lambda, void* partials, DevStatus* st, cudaStream_t stream,
+                    double sgn, const void* addv, double addc) {
+  auto kern = apass_kernel<TA, TX, G, QMAX, K>;
+  SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+  const int nparts = pl.grid * (kConsumers / G);
+  if (n > 0) {
+    ApassArgs a;
+    a.d = (int)d;
+    a.dp = pl.dp;
+    a.boxw = pl.boxw;
+    a.nbox = pl.nbox;
+    a.rows = pl.rows_per_stage;
+    a.stages = pl.stages;
+    a.q = pl.q;
+    a.ntiles = (int)((n + pl.rows_per_stage - 1) / pl.rows_per_stage);
+    a.x = x;
+    a.partials = partials;
+    a.st = st;
+    kern<<<pl.grid, kThreads, pl.smem, stream>>>(*tmap, a);
+    SKS_CUDA_TRY(cudaGetLastError());
+  }
+  dim3 fg((unsigned)((d + 127) / 128), (unsigned)K);
+  apass_finalize<TX><<<fg, 128, 0, stream>>>(n > 0 ? nparts : 0, (int)d, K, (const TX*)partials, (const TX*)x,
+                                               (TX*)y, nu2, lambda, sgn, (const TX*)addv, addc);
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
+int vec_of(bool a_f32) { return a_f32 ? 4 : 2; }
+
+}  // namespace
+
+sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32, ApassPlan* pl) {
+  if (d < 1 || d > 4096) return fail(SKS_ERR_UNSUPPORTED, "A-pass supports 1 <= d <= 4096");
+  if (!(k == 1 || k == 8)) return fail(SKS_ERR_UNSUPPORTED, "A-pass kernel instantiated for k in {1, 8}");
+  const int vec = vec_of(a_f32);
+  const size_t esz = a_f32 ? 4 : 8, xsz = vec_f32 ? 4 : 8;
+  const int boxw = (int)std::min<int64_t>(256, (d + vec - 1) / vec * vec);
+  const int nbox = (int)((d + boxw - 1) / boxw);
+  const int dp = nbox * boxw;
+  const int nvec = dp / vec;
+  // narrow rows: one warp per row; wide rows: all 256 consumers per row.
+  // Per-thread column vectors: 8 (float64 A, 2 per vector) or 4 (float32 A,
+  // 4 per vector), i.e. 16 register-resident accumulators per right-hand side.
+  const int qcap = a_f32 ? 4 : 8;
+  int group = (nvec <= 32 * qcap && k == 1) ? 32 : 256;
+  if (k == 8) group = 256;
+  const int qmax = (k == 8) ? 1 : qcap;
+  const int q = (nvec + group - 1) / group;
+  if (q > qmax) return fail(SKS_ERR_UNSUPPORTED, "A-pass: row too wide for this instantiation");
+  const int ng = kConsumers / group;
+  const size_t row_bytes = (size_t)dp * esz;
+  int rows = (int)std::max<size_t>(1, (32 * 1024) / row_bytes);
+  rows = std::max(rows, ng);
+  rows = std::min(rows, 256);
+  rows = rows / ng * ng;
+  const DeviceInfo& di = device_info();
+  const size_t budget = di.smem_optin ? di.smem_optin : 232448;
+  const size_t fixed = ((size_t)k * dp * xsz + 127) / 128 * 128 + ((size_t)2 * 8 * kRC * k * xsz + 127) / 128 * 128;
+  const size_t stage_bytes = ((size_t)rows * row_bytes);
+  int stages = (int)std::min<size_t>(8, (budget - fixed - 1024) / stage_bytes);
+  if (stages < 2) return fail(SKS_ERR_UNSUPPORTED, "A-pass: shared memory too small");
+  const int64_t ntiles = (n + rows - 1) / rows;
+  const int sms = di.sms > 0 ? di.sms : 152;
+  pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms));
+  pl->group = group;
+  pl->q = q;
+  pl->rows_per_stage = rows;
+  pl->stages = stages;
+  pl->boxw = boxw;
+  pl->nbox = nbox;
+  pl->dp = dp;
+  pl->smem = (size_t)stages * stage_bytes + fixed + 2 * 8 * stages + 256;
+  pl->partial_elems = (size_t)pl->grid * ng * k * d;
+  return SKS_OK;
+}
+
+size_t apass_workspace_bytes(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32) {
+  ApassPlan pl;
+  if (apass_plan(n, d, k, a_f32, vec_f32, &pl) != SKS_OK) return 0;
+  return pl.partial_elems * (vec_f32 ? 4 : 8) + 256;
+}
+
+sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int64_t d, int64_t k, bool a_f32,
+                        bool vec_f32, const void* x, void* y, double nu2, const double* lambda, void* partials,
+                        DevStatus* st, cudaStream_t stream, double sgn, const void* addv, double addc) {
+  if (!a_f32 && vec_f32) return fail(SKS_ERR_UNSUPPORTED, "float64 A with float32 vectors");
+  if (!a_f32) {
+    if (k == 8) return launch_t<double, double, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+    if (pl.group == 32) return launch_t<double, double, 32, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+    return launch_t<double, double, 256, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+  }
+  if (vec_f32) {
+    if (k == 8) return launch_t<float, float, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+    if (pl.group == 32) return launch_t<float, float, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+    return launch_t<float, float, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+  }
+  if (k == 8) return launch_t<float, double, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+  if (pl.group == 32) return launch_t<float, double, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+  return launch_t<float, double, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+}
+
+}  // namespace sks

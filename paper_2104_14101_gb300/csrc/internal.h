@@ -1,0 +1,94 @@
+// internal.h -- host-side declarations shared by the translation units of the
+// sks library (not part of the public C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "common.cuh"
+#include "sks.h"
+
+namespace sks {
+
+// ---------------------------------------------------------------- errors
+void set_last_error(const std::string& msg);
+sks_status fail(sks_status code, const std::string& msg);
+const char* last_error_cstr();
+
+#define SKS_CUDA_TRY(expr)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::sks::fail(SKS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+#define SKS_TRY(...)                         \
+  do {                                       \
+    sks_status s_ = (__VA_ARGS__);           \
+    if (s_ != SKS_OK) return s_;             \
+  } while (0)
+
+// ---------------------------------------------------------------- device info
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+const DeviceInfo& device_info();
+
+// ---------------------------------------------------------------- workspace carving
+// Bump allocator over a caller-provided device buffer (256-byte alignment).
+struct Carver {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  Carver(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <typename T>
+  T* take(size_t count) {
+    used = (used + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + used) : nullptr;
+    used += count * sizeof(T);
+    return p;
+  }
+  bool ok() const { return used <= cap; }
+};
+
+// ---------------------------------------------------------------- tensor maps
+// 2-D tiled tensor map over a row-major rows x cols matrix with leading
+// dimension ld (elements), box (box_cols x box_rows), no swizzle, zero fill.
+sks_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, size_t elem_bytes,
+                        uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_cols, uint32_t box_rows);
+
+// ---------------------------------------------------------------- A-pass (K1)
+// Geometry of one A-pass launch (host-computed).
+struct ApassPlan {
+  int grid = 0, group = 0, q = 0, rows_per_stage = 0, stages = 0, boxw = 0, nbox = 0, dp = 0;
+  size_t smem = 0;
+  size_t partial_elems = 0;  // grid * k * d
+};
+
+// y = A^T (A x) + nu^2 lambda .* x for k columns.
+//   a_f32: A stored float32; vec_f32: x / y float32 (else float64).
+//   extended: float64 arithmetic on float32 A (the refinement residual).
+// partials: device scratch (plan.partial_elems elements of the vector type).
+// With addv: y = sgn * H x + addc * addv (residuals and gradients in one launch).
+sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32, ApassPlan* plan);
+sks_status apass_launch(const ApassPlan& plan, const CUtensorMap* tmap, int64_t n, int64_t d, int64_t k,
+                        bool a_f32, bool vec_f32, const void* x, void* y, double nu2, const double* lambda,
+                        void* partials, DevStatus* st, cudaStream_t stream, double sgn = 1.0,
+                        const void* addv = nullptr, double addc = 0.0);
+size_t apass_workspace_bytes(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32);
+
+// ---------------------------------------------------------------- solver entry points (solver.cu)
+sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes);
+// method 0: adaptive PCG (Algorithm 2); 1: adaptive IHS (Algorithm 1)
+sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
+                          size_t ws_bytes, cudaStream_t stream);
+sks_status hess_apply_ws(const sks_problem* p, size_t* bytes);
+sks_status hess_apply(const sks_problem* p, const double* x, double* y, int extended, void* ws, size_t ws_bytes,
+                      cudaStream_t stream);
+
+}  // namespace sks

@@ -1,0 +1,66 @@
+// runtime.cu -- host-side plumbing: thread-local error text, device
+// properties, and the tensor-map encoder (driver entry point fetched through
+// the runtime, so the library does not link libcuda directly).
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+
+namespace sks {
+
+namespace {
+thread_local std::string g_last_error;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+}  // namespace
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+sks_status fail(sks_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+const DeviceInfo& device_info() {
+  static thread_local DeviceInfo info;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return info;
+  if (info.device != dev) {
+    info.device = dev;
+    cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    info.smem_optin = (size_t)optin;
+  }
+  return info;
+}
+
+sks_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, size_t elem_bytes, uint64_t rows,
+                        uint64_t cols, uint64_t ld, uint32_t box_cols, uint32_t box_rows) {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  static cudaError_t qerr = cudaSuccess;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    qerr = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (qerr == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = (EncodeTiledFn)p;
+  });
+  if (!fn) return fail(SKS_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  if (((uintptr_t)base & 15) != 0) return fail(SKS_ERR_INVALID_ARG, "A must be 16-byte aligned");
+  if ((ld * elem_bytes) % 16 != 0) return fail(SKS_ERR_INVALID_ARG, "lda * element size must be a multiple of 16 bytes");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * elem_bytes)};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SKS_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  return SKS_OK;
+}
+
+}  // namespace sks

@@ -1,0 +1,243 @@
+// sketch.cu -- the random embeddings of Section 2.1 on the GPU.
+//
+//  K2 SRHT: B = H_{+-1} E A_pad (n_pad x d), the fast Walsh-Hadamard transform
+//     along the rows of the sign-flipped, zero-padded A.  Butterflies pair
+//     whole rows (r, r + h), so every pass loads 2^L rows x 16 contiguous
+//     columns into shared memory and applies L levels there; ceil(log2(n_pad)
+//     / L) passes cover all levels.  Formed once per solve; a larger sketch
+//     only gathers more rows of B.
+//  K3 SRHT gather: Y[r] = B[pi(r)] for the new rows r, pi the keyed Feistel
+//     permutation (nested subsampling R).
+//  K4 Gaussian: Y[r] = sum_i G[r][i] a_i, G from Philox + Box-Muller, produced
+//     chunk by chunk and multiplied with the CUDA-core GEMM (float64 form).
+//  K5 SJLT: Y[h_k(i)] += sigma_k(i)/sqrt(s_eff) a_i, one warp per data row,
+//     float64 atomics.
+// All sketches are stored unscaled (S A = scale * Y).
+#include <algorithm>
+
+#include "sketch.h"
+#include "dense.h"
+
+namespace sks {
+
+namespace {
+
+constexpr int kFwhtCols = 16;
+
+// One FWHT pass over the row bits [a, a + L): the CTA owns rows
+// r = hi * 2^(a+L) + j * 2^a + lo (j < 2^L) and columns [c0, c0 + 16).
+// first pass: source is A (rows >= n are zero) times the signs E.
+template <typename T>
+__global__ void __launch_bounds__(256) fwht_pass_kernel(const T* __restrict__ A, long long lda, int64_t n,
+                                                       T* __restrict__ B, long long ldb, int d, int a, int L,
+                                                       int first, Key key) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = (T*)smem_raw;  // [2^L][kFwhtCols]
+  const int T_rows = 1 << L;
+  const int ncb = (d + kFwhtCols - 1) / kFwhtCols;
+  const int cb = blockIdx.x % ncb;
+  const long long grp = blockIdx.x / ncb;
+  const long long lo = grp & ((1ll << a) - 1);
+  const long long hi = grp >> a;
+  const int c0 = cb * kFwhtCols;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < T_rows * kFwhtCols; e += blockDim.x) {
+    const int j = e / kFwhtCols, c = e % kFwhtCols;
+    const long long r = (hi << (a + L)) + ((long long)j << a) + lo;
+    T v = T(0);
+    if (c0 + c < d) {
+      if (first) {
+        if (r < n) v = A[r * lda + c0 + c] * (T)srht_sign(key, (uint32_t)r);
+      } else {
+        v = B[r * ldb + c0 + c];
+      }
+    }
+    tile[e] = v;
+  }
+  __syncthreads();
+  for (int h = 1; h < T_rows; h <<= 1) {
+    for (int e = tid; e < (T_rows / 2) * kFwhtCols; e += blockDim.x) {
+      const int p = e / kFwhtCols, c = e % kFwhtCols;
+      const int j0 = (p / h) * 2 * h + (p % h);
+      const T u = tile[j0 * kFwhtCols + c], w = tile[(j0 + h) * kFwhtCols + c];
+      tile[j0 * kFwhtCols + c] = u + w;
+      tile[(j0 + h) * kFwhtCols + c] = u - w;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < T_rows * kFwhtCols; e += blockDim.x) {
+    const int j = e / kFwhtCols, c = e % kFwhtCols;
+    const long long r = (hi << (a + L)) + ((long long)j << a) + lo;
+    if (c0 + c < d) B[r * ldb + c0 + c] = tile[e];
+  }
+}
+
+// Y[r] = B[pi(r)] for r in [r0, r1); one CTA per row.
+template <typename TB, typename TY>
+__global__ void srht_gather_kernel(const TB* __restrict__ B, long long ldb, int d, int bits, Key key, int r0,
+                                   TY* __restrict__ Y, long long ldy, DevStatus* st) {
+  const int r = r0 + blockIdx.x;
+  __shared__ uint32_t src;
+  if (threadIdx.x == 0) {
+    src = feistel_perm(key, (uint32_t)r, bits);
+    if (src == 0xffffffffu) raise_status(st, SKS_ERR_NUMERIC, 31, r);
+  }
+  __syncthreads();
+  if (src == 0xffffffffu) return;
+  const TB* row = B + (long long)src * ldb;
+  TY* out = Y + (long long)r * ldy;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) out[c] = (TY)row[c];
+}
+
+// G[r][i] (r < m_add, i < icnt) = N(0,1) entry of global sketch row m_off + r
+// and data row i0 + i; one thread per (quad, data row).
+template <typename T>
+__global__ void gauss_gen_kernel(Key key, int m_off, int m_add, int64_t i0, int icnt, T* __restrict__ G,
+                                 long long ldg) {
+  const int q0 = m_off / 4;
+  const int q1 = (m_off + m_add - 1) / 4;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nq = (long long)(q1 - q0 + 1);
+  if (e >= nq * icnt) return;
+  const int i = (int)(e % icnt);
+  const int q = q0 + (int)(e / icnt);
+  T g[4];
+  if (sizeof(T) == 8) {
+    double gd[4];
+    gauss4_d(key, (uint32_t)(i0 + i), (uint32_t)q, gd);
+    for (int t = 0; t < 4; ++t) g[t] = (T)gd[t];
+  } else {
+    float gf[4];
+    gauss4_f(key, (uint32_t)(i0 + i), (uint32_t)q, gf);
+    for (int t = 0; t < 4; ++t) g[t] = (T)gf[t];
+  }
+  for (int t = 0; t < 4; ++t) {
+    const int rg = 4 * q + t;
+    if (rg >= m_off && rg < m_off + m_add) G[(long long)(rg - m_off) * ldg + i] = g[t];
+  }
+}
+
+// SJLT scatter: one warp per data row.
+template <typename TA, typename TY>
+__global__ void sjlt_scatter_kernel(const TA* __restrict__ A, long long lda, int64_t n, int d, uint32_t m, int s_eff,
+                                    Key key, TY* __restrict__ Y, long long ldy) {
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  uint32_t rows[kSjltMaxS];
+  float signs[kSjltMaxS];
+  sjlt_hash(key, (uint32_t)warp, m, s_eff, rows, signs);
+  const TY inv = (TY)(1.0 / sqrt((double)s_eff));
+  const TA* a = A + warp * lda;
+  for (int c = lane; c < d; c += 32) {
+    const TY v = (TY)a[c] * inv;
+    for (int k = 0; k < s_eff; ++k) atomicAdd(&Y[(long long)rows[k] * ldy + c], (TY)signs[k] * v);
+  }
+}
+
+}  // namespace
+
+int ilog2_ceil(int64_t n) {
+  int b = 0;
+  while ((1ll << b) < n) ++b;
+  return b;
+}
+
+template <typename T>
+sks_status srht_form(cudaStream_t stream, const T* A, long long lda, int64_t n, int d, T* B, long long ldb,
+                     uint64_t seed) {
+  const int bits = ilog2_ceil(n);
+  const int Lmax = 9;  // 512 rows x 16 columns per CTA
+  const int ncb = (d + kFwhtCols - 1) / kFwhtCols;
+  int a = 0;
+  bool first = true;
+  if (bits == 0) {
+    // n_pad = 1: B = E A
+    const int L = 0;
+    const size_t smem = (size_t)kFwhtCols * sizeof(T);
+    fwht_pass_kernel<T><<<ncb, 256, smem, stream>>>(A, lda, n, B, ldb, d, 0, L, 1, make_key(seed));
+    SKS_CUDA_TRY(cudaGetLastError());
+    return SKS_OK;
+  }
+  while (a < bits) {
+    const int L = std::min(Lmax, bits - a);
+    const long long groups = 1ll << (bits - L);
+    const long long blocks = groups * ncb;
+    const size_t smem = ((size_t)1 << L) * kFwhtCols * sizeof(T);
+    if (blocks > 0x7fffffffll) return fail(SKS_ERR_UNSUPPORTED, "FWHT grid too large");
+    SKS_CUDA_TRY(cudaFuncSetAttribute(fwht_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fwht_pass_kernel<T><<<(unsigned)blocks, 256, smem, stream>>>(A, lda, n, B, ldb, d, a, L, first ? 1 : 0,
+                                                                 make_key(seed));
+    SKS_CUDA_TRY(cudaGetLastError());
+    first = false;
+    a += L;
+  }
+  return SKS_OK;
+}
+template sks_status srht_form<double>(cudaStream_t, const double*, long long, int64_t, int, double*, long long,
+                                      uint64_t);
+template sks_status srht_form<float>(cudaStream_t, const float*, long long, int64_t, int, float*, long long, uint64_t);
+
+template <typename TB, typename TY>
+sks_status srht_gather(cudaStream_t stream, const TB* B, long long ldb, int d, int64_t n_pad, uint64_t seed, int r0,
+                       int r1, TY* Y, long long ldy, DevStatus* st) {
+  if (r1 <= r0) return SKS_OK;
+  const int bits = ilog2_ceil(n_pad);
+  srht_gather_kernel<TB, TY><<<r1 - r0, 128, 0, stream>>>(B, ldb, d, bits, make_key(seed), r0, Y, ldy, st);
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+template sks_status srht_gather<double, double>(cudaStream_t, const double*, long long, int, int64_t, uint64_t, int,
+                                                int, double*, long long, DevStatus*);
+template sks_status srht_gather<float, float>(cudaStream_t, const float*, long long, int, int64_t, uint64_t, int, int,
+                                              float*, long long, DevStatus*);
+
+template <typename T>
+sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64_t n, int d, uint64_t seed, int m_off,
+                           int m_add, T* Y, long long ldy, T* gbuf, size_t gbuf_elems, T* split_ws,
+                           size_t split_elems) {
+  if (m_add <= 0) return SKS_OK;
+  if (n == 0) {
+    SKS_CUDA_TRY(cudaMemset2DAsync(Y + (long long)m_off * ldy, ldy * sizeof(T), 0, d * sizeof(T), m_add, stream));
+    return SKS_OK;
+  }
+  int64_t chunk = (int64_t)(gbuf_elems / (size_t)m_add);
+  chunk = std::min<int64_t>(chunk, n);
+  if (chunk < 1) return fail(SKS_ERR_WORKSPACE, "Gaussian sketch buffer too small");
+  const Key key = make_key(seed);
+  for (int64_t i0 = 0; i0 < n; i0 += chunk) {
+    const int icnt = (int)std::min<int64_t>(chunk, n - i0);
+    const long long nq = (m_off + m_add - 1) / 4 - m_off / 4 + 1;
+    const long long threads = nq * icnt;
+    gauss_gen_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(key, m_off, m_add, i0, icnt, gbuf,
+                                                                                icnt);
+    SKS_CUDA_TRY(cudaGetLastError());
+    SKS_TRY(gemm<T>(stream, m_add, d, icnt, gbuf, icnt, false, A + i0 * lda, lda, false, Y + (long long)m_off * ldy,
+                    ldy, 1.0, i0 == 0 ? 0.0 : 1.0, false, 1, 0, 0, 0, split_ws, split_elems));
+  }
+  return SKS_OK;
+}
+template sks_status gaussian_extend<double>(cudaStream_t, const double*, long long, int64_t, int, uint64_t, int, int,
+                                            double*, long long, double*, size_t, double*, size_t);
+template sks_status gaussian_extend<float>(cudaStream_t, const float*, long long, int64_t, int, uint64_t, int, int,
+                                           float*, long long, float*, size_t, float*, size_t);
+
+template <typename TA, typename TY>
+sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n, int d, int m, int s, uint64_t seed,
+                     TY* Y, long long ldy) {
+  SKS_CUDA_TRY(cudaMemset2DAsync(Y, ldy * sizeof(TY), 0, d * sizeof(TY), m, stream));
+  if (n == 0) return SKS_OK;
+  const int s_eff = std::min(s, m);
+  if (s_eff > kSjltMaxS) return fail(SKS_ERR_UNSUPPORTED, "SJLT s > 16");
+  const long long threads = n * 32;
+  sjlt_scatter_kernel<TA, TY><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(A, lda, n, d, (uint32_t)m, s_eff,
+                                                                                    make_key(seed), Y, ldy);
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+template sks_status sjlt_form<double, double>(cudaStream_t, const double*, long long, int64_t, int, int, int, uint64_t,
+                                              double*, long long);
+template sks_status sjlt_form<float, float>(cudaStream_t, const float*, long long, int64_t, int, int, int, uint64_t,
+                                            float*, long long);
+
+}  // namespace sks

@@ -1,0 +1,878 @@
+// solver.cu -- sketches, preconditioners and the adaptive solvers behind the
+// C ABI (include/sks.h).
+//
+// Algorithm 2 (adaptive PCG) and Algorithm 1 with the IHS step (Theorem 3.2)
+// run as a host loop that only queues work: every iteration is one A-pass
+// (K1) plus three small kernels (the step, the preconditioner apply, the
+// improvement test).  The test's verdict lives in a device control block;
+// the host reads that 96-byte block once per iteration to decide whether to
+// grow the sketch (the rare, variable-size branch).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dense.h"
+#include "internal.h"
+#include "sketch.h"
+
+// ============================================================================ handles
+
+struct sks_sketch {
+  sks_problem p;
+  sks_kind kind;
+  int64_t m = 0, m_max = 0, n_pad = 1;
+  int s = 1, d = 0;
+  uint64_t seed = 0;
+  bool f32 = false;
+  void* B = nullptr;  // SRHT: n_pad x d
+  void* Y = nullptr;  // m_max x d, unscaled sketch
+  long long ldy = 0;
+  void* gbuf = nullptr;
+  size_t gbuf_elems = 0;
+  void* split = nullptr;
+  size_t split_elems = 0;
+  sks::DevStatus* st = nullptr;
+  double scale2() const { return kind == SKS_SJLT ? 1.0 : 1.0 / (double)m; }
+};
+
+struct sks_precond {
+  int d = 0;
+  int64_t m = 0;
+  bool woodbury = false;
+  double nu2 = 0, c2 = 0;
+  const double* lam = nullptr;
+  double* H = nullptr;   // d x d (or m x m) matrix being factored
+  double* X = nullptr;   // inverse triangular factor
+  double* Xt = nullptr;  // its transpose
+  double* Y64 = nullptr; // float64 sketch (copy when the sketch is float32)
+  long long ldy64 = 0;
+  double* Yt = nullptr;  // d x m transpose of Y64 (Woodbury)
+  double* Ys = nullptr;  // Y64 Lambda^{-1} (Woodbury build)
+  double* chol_ws = nullptr;
+  double* split = nullptr;
+  size_t split_elems = 0;
+  double* t1 = nullptr;  // m-vectors
+  double* t2 = nullptr;
+  sks::DevStatus* st = nullptr;
+};
+
+namespace sks {
+
+namespace {
+
+// ---------------------------------------------------------------- validation
+sks_status validate_problem(const sks_problem* p) {
+  if (!p) return fail(SKS_ERR_INVALID_ARG, "problem is NULL");
+  if (p->n < 0 || p->d < 1 || p->k < 1) return fail(SKS_ERR_INVALID_ARG, "need n >= 0, d >= 1, k >= 1");
+  if (p->lda < p->d) return fail(SKS_ERR_INVALID_ARG, "lda < d");
+  if (p->n > 0 && !p->A) return fail(SKS_ERR_INVALID_ARG, "A is NULL");
+  if (!p->b || !p->lambda_diag) return fail(SKS_ERR_INVALID_ARG, "b or lambda is NULL");
+  if (!(p->nu > 0.0) || !std::isfinite(p->nu)) return fail(SKS_ERR_INVALID_ARG, "nu must be > 0");
+  if (p->dtype != SKS_F64 && p->dtype != SKS_F32) return fail(SKS_ERR_INVALID_ARG, "bad dtype");
+  if (p->d > 4096) return fail(SKS_ERR_UNSUPPORTED, "d > 4096");
+  if (p->n > (int64_t)1 << 31) return fail(SKS_ERR_UNSUPPORTED, "n > 2^31");
+  const size_t esz = p->dtype == SKS_F32 ? 4 : 8;
+  if (p->n > 0 && (((uintptr_t)p->A & 15) || (p->lda * esz) % 16))
+    return fail(SKS_ERR_INVALID_ARG, "A must be 16-byte aligned with lda * element size a multiple of 16");
+  return SKS_OK;
+}
+
+__global__ void check_lambda_kernel(int d, const double* lam, DevStatus* st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d && !(lam[i] >= 1.0 && isfinite(lam[i]))) raise_status(st, SKS_ERR_INVALID_ARG, 1, i);
+}
+
+sks_status read_status(DevStatus* st, cudaStream_t stream, const char* what) {
+  DevStatus h;
+  SKS_CUDA_TRY(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+  if (h.code != 0) {
+    std::string msg = std::string(what) + ": device status " + std::to_string(h.code) + " (site " +
+                      std::to_string(h.where) + ", detail " + std::to_string(h.aux) + ")";
+    if (h.code == SKS_ERR_INVALID_ARG && h.where == 1) msg = "lambda_i must be >= 1 (index " + std::to_string(h.aux) + ")";
+    if (h.code == SKS_ERR_NOT_PD) msg = "non-positive pivot in Cholesky at column " + std::to_string(h.aux);
+    if (h.code == SKS_ERR_TIMEOUT) msg = std::string(what) + ": bounded device wait ran out (site " + std::to_string(h.where) + ")";
+    return fail((sks_status)h.code, msg);
+  }
+  return SKS_OK;
+}
+
+sks_status map_for(const sks_problem* p, CUtensorMap* map, const ApassPlan& pl) {
+  const bool f32 = p->dtype == SKS_F32;
+  return make_tmap_2d(map, p->A, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                      f32 ? 4 : 8, (uint64_t)p->n, (uint64_t)p->d, (uint64_t)p->lda, (uint32_t)pl.boxw,
+                      (uint32_t)pl.rows_per_stage);
+}
+
+__global__ void f64_to_f32_kernel(long long count, const double* a, float* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f32_to_f64_kernel(long long count, const float* a, double* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+__global__ void f32_to_f64_2d_kernel(int rows, int cols, const float* a, long long lda, double* b, long long ldb) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  b[(long long)r * ldb + c] = (double)a[(long long)r * lda + c];
+}
+__global__ void scale_cols_kernel(int rows, int cols, const double* a, long long lda, const double* lam, double* b,
+                                  long long ldb) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  b[(long long)r * ldb + c] = a[(long long)r * lda + c] / lam[c];
+}
+__global__ void scale_rows_out_kernel(int rows, int cols, const void* Y, int f32, long long ldy, double scale,
+                                      double* out) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  const double v = f32 ? (double)((const float*)Y)[(long long)r * ldy + c] : ((const double*)Y)[(long long)r * ldy + c];
+  out[e] = scale * v;
+}
+
+inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)std::max<long long>(1, std::min<long long>((n + t - 1) / t, 65535ll * 16)); }
+
+// ---------------------------------------------------------------- sketch
+struct SketchSizes {
+  size_t b_elems = 0, y_elems = 0, g_elems = 0, split_elems = 0;
+};
+
+SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max) {
+  SketchSizes z;
+  const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
+  if (kind == SKS_SRHT) z.b_elems = (size_t)n_pad * p->d;
+  z.y_elems = (size_t)m_max * p->d;
+  if (kind == SKS_GAUSSIAN) {
+    z.g_elems = (size_t)std::min<int64_t>((int64_t)m_max * std::max<int64_t>(p->n, 1), (int64_t)1 << 24);
+    z.g_elems = std::max<size_t>(z.g_elems, (size_t)m_max * 64);
+    z.split_elems = std::min<size_t>((size_t)8 * m_max * p->d, (size_t)1 << 24);
+  }
+  return z;
+}
+
+int64_t resolve_m_max(const sks_problem* p, sks_kind kind, int64_t m_max) {
+  const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
+  const int64_t cap = kind == SKS_SRHT ? n_pad : std::max<int64_t>(p->n, 1);
+  if (m_max <= 0) return cap;
+  return std::min(m_max, cap);
+}
+
+size_t sketch_ws_bytes(const sks_problem* p, sks_kind kind, int64_t m_max) {
+  const SketchSizes z = sketch_sizes(p, kind, m_max);
+  const size_t esz = p->dtype == SKS_F32 ? 4 : 8;
+  Carver c(nullptr, 0);
+  c.take<DevStatus>(1);
+  c.take<char>(z.b_elems * esz);
+  c.take<char>(z.y_elems * esz);
+  c.take<char>(z.g_elems * esz);
+  c.take<char>(z.split_elems * esz);
+  return c.used + 256;
+}
+
+sks_status sketch_init(sks_sketch* s, const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s, uint64_t seed,
+                       void* ws, size_t ws_bytes, DevStatus* shared_st) {
+  s->p = *p;
+  s->kind = kind;
+  s->m = 0;
+  s->m_max = m_max;
+  s->s = std::max(1, sjlt_s);
+  s->seed = seed;
+  s->d = (int)p->d;
+  s->f32 = p->dtype == SKS_F32;
+  s->n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
+  const SketchSizes z = sketch_sizes(p, kind, m_max);
+  const size_t esz = s->f32 ? 4 : 8;
+  Carver c(ws, ws_bytes);
+  DevStatus* own = c.take<DevStatus>(1);
+  s->st = shared_st ? shared_st : own;
+  s->B = c.take<char>(z.b_elems * esz);
+  s->Y = c.take<char>(z.y_elems * esz);
+  s->ldy = p->d;
+  s->gbuf = c.take<char>(z.g_elems * esz);
+  s->gbuf_elems = z.g_elems;
+  s->split = c.take<char>(z.split_elems * esz);
+  s->split_elems = z.split_elems;
+  if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "sketch workspace too small");
+  if (z.b_elems == 0) s->B = nullptr;
+  return SKS_OK;
+}
+
+template <typename T>
+sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
+  const sks_problem& p = s->p;
+  const T* A = (const T*)p.A;
+  T* Y = (T*)s->Y;
+  const int d = s->d;
+  if (s->kind == SKS_SRHT) {
+    if (s->m == 0) SKS_TRY(srht_form<T>(stream, A, p.lda, p.n, d, (T*)s->B, d, s->seed));
+    SKS_TRY(srht_gather<T, T>(stream, (const T*)s->B, d, d, s->n_pad, s->seed, (int)s->m, (int)new_m, Y, s->ldy, s->st));
+  } else if (s->kind == SKS_GAUSSIAN) {
+    SKS_TRY(gaussian_extend<T>(stream, A, p.lda, p.n, d, s->seed, (int)s->m, (int)(new_m - s->m), Y, s->ldy,
+                               (T*)s->gbuf, s->gbuf_elems, (T*)s->split, s->split_elems));
+  } else {
+    SKS_TRY(sjlt_form<T, T>(stream, A, p.lda, p.n, d, (int)new_m, s->s, s->seed, Y, s->ldy));
+  }
+  s->m = new_m;
+  return SKS_OK;
+}
+
+sks_status sketch_to(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
+  if (new_m < s->m) return fail(SKS_ERR_INVALID_ARG, "sketch can only grow");
+  if (new_m > s->m_max) return fail(SKS_ERR_INVALID_ARG, "sketch size above m_max");
+  if (new_m == s->m) return SKS_OK;
+  if (s->f32) return sketch_to_t<float>(s, new_m, stream);
+  return sketch_to_t<double>(s, new_m, stream);
+}
+
+// ---------------------------------------------------------------- preconditioner
+size_t precond_ws_bytes(const sks_problem* p, int64_t m_max) {
+  const size_t d = (size_t)p->d;
+  Carver c(nullptr, 0);
+  c.take<DevStatus>(1);
+  c.take<double>(d * d);  // H
+  c.take<double>(d * d);  // X
+  c.take<double>(d * d);  // Xt
+  c.take<double>(d * d);  // Yt  (Woodbury only when m < d)
+  c.take<double>(d * d);  // Ys
+  if (p->dtype == SKS_F32) c.take<double>((size_t)m_max * d);  // Y64
+  c.take<double>(cholesky_ws_elems((int)d));
+  c.take<double>(std::min<size_t>(4 * d * d, (size_t)1 << 24));
+  c.take<double>(2 * std::max<size_t>(d, (size_t)m_max));
+  return c.used + 256;
+}
+
+sks_status precond_init(sks_precond* P, const sks_problem* p, int64_t m_max, void* ws, size_t ws_bytes,
+                        DevStatus* shared_st) {
+  const size_t d = (size_t)p->d;
+  Carver c(ws, ws_bytes);
+  DevStatus* own = c.take<DevStatus>(1);
+  P->st = shared_st ? shared_st : own;
+  P->d = (int)d;
+  P->H = c.take<double>(d * d);
+  P->X = c.take<double>(d * d);
+  P->Xt = c.take<double>(d * d);
+  P->Yt = c.take<double>(d * d);
+  P->Ys = c.take<double>(d * d);
+  P->Y64 = p->dtype == SKS_F32 ? c.take<double>((size_t)m_max * d) : nullptr;
+  P->chol_ws = c.take<double>(cholesky_ws_elems((int)d));
+  P->split_elems = std::min<size_t>(4 * d * d, (size_t)1 << 24);
+  P->split = c.take<double>(P->split_elems);
+  P->t1 = c.take<double>(std::max<size_t>(d, (size_t)m_max));
+  P->t2 = c.take<double>(std::max<size_t>(d, (size_t)m_max));
+  if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "preconditioner workspace too small");
+  return SKS_OK;
+}
+
+// H_S = c2 Y^T Y + nu^2 Lambda (m >= d) or W_S = c2 Y Lambda^{-1} Y^T + nu^2 I (m < d).
+sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const double* lam, cudaStream_t stream) {
+  const int d = s->d;
+  const int m = (int)s->m;
+  P->m = m;
+  P->woodbury = m < d;
+  P->nu2 = nu * nu;
+  P->c2 = s->scale2();
+  P->lam = lam;
+  const double* Y64;
+  long long ldy;
+  if (s->f32) {
+    f32_to_f64_2d_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, (const float*)s->Y, s->ldy, P->Y64, d);
+    SKS_CUDA_TRY(cudaGetLastError());
+    Y64 = P->Y64;
+    ldy = d;
+  } else {
+    Y64 = (const double*)s->Y;
+    ldy = s->ldy;
+  }
+  P->ldy64 = ldy;
+  if (!P->woodbury) {
+    SKS_TRY(gemm<double>(stream, d, d, m, Y64, ldy, true, Y64, ldy, false, P->H, d, P->c2, 0.0, true, 1, 0, 0, 0,
+                         P->split, P->split_elems));
+    SKS_TRY(add_diagonal(stream, d, P->H, d, 0.0, lam, P->nu2));
+    SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st));
+    SKS_TRY(transpose<double>(stream, d, d, P->X, d, P->Xt, d));
+  } else {
+    scale_cols_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, Y64, ldy, lam, P->Ys, d);
+    SKS_CUDA_TRY(cudaGetLastError());
+    SKS_TRY(gemm<double>(stream, m, m, d, P->Ys, d, false, Y64, ldy, true, P->H, m, P->c2, 0.0, true, 1, 0, 0, 0,
+                         P->split, P->split_elems));
+    SKS_TRY(add_diagonal(stream, m, P->H, m, P->nu2, nullptr, 0.0));
+    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st));
+    SKS_TRY(transpose<double>(stream, m, m, P->X, m, P->Xt, m));
+    SKS_TRY(transpose<double>(stream, m, d, Y64, ldy, P->Yt, m));
+  }
+  // keep the float64 sketch pointer for the apply
+  P->Y64 = const_cast<double*>(Y64);
+  return SKS_OK;
+}
+
+// v = H_S^{-1} z (one column)
+sks_status precond_apply1(const sks_precond* P, const double* z, double* v, cudaStream_t stream) {
+  const int d = P->d;
+  if (!P->woodbury) {
+    SKS_TRY(gemv_rows<double>(stream, d, d, P->X, d, 1, z, nullptr, 1.0, P->t1, 0, nullptr, nullptr, 0.0));
+    SKS_TRY(gemv_rows<double>(stream, d, d, P->Xt, d, 2, P->t1, nullptr, 1.0, v, 0, nullptr, nullptr, 0.0));
+    return SKS_OK;
+  }
+  const int m = (int)P->m;
+  const double c = std::sqrt(P->c2);
+  SKS_TRY(gemv_rows<double>(stream, m, d, P->Y64, P->ldy64, 0, z, P->lam, c, P->t1, 0, nullptr, nullptr, 0.0));
+  SKS_TRY(gemv_rows<double>(stream, m, m, P->X, m, 1, P->t1, nullptr, 1.0, P->t2, 0, nullptr, nullptr, 0.0));
+  SKS_TRY(gemv_rows<double>(stream, m, m, P->Xt, m, 2, P->t2, nullptr, 1.0, P->t1, 0, nullptr, nullptr, 0.0));
+  SKS_TRY(gemv_rows<double>(stream, d, m, P->Yt, m, 0, P->t1, nullptr, c, v, 1, z, P->lam, P->nu2));
+  return SKS_OK;
+}
+
+// ---------------------------------------------------------------- iteration kernels
+struct Ctl {
+  double dt, dI, dp, alpha, ratio, thr, btx;
+  long long t, I;
+  int accept, stop, numeric, pad;
+};
+
+constexpr int kStepThreads = 1024;
+
+__device__ double block_dot(int d, const double* a, const double* b) {
+  __shared__ double scratch[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s += a[j] * b[j];
+  return block_sum(s, scratch);
+}
+
+// PCG, first half of a step: alpha = delta~_t / p^T H p, x+ = x + alpha p, r+ = r - alpha H p.
+__global__ void __launch_bounds__(kStepThreads) pcg_step1_kernel(int d, const double* x, const double* r,
+                                                                 const double* p, const double* Hp, double* xp,
+                                                                 double* rp, Ctl* ctl) {
+  const double pHp = block_dot(d, p, Hp);
+  const double alpha = ctl->dt / pHp;
+  const bool bad = !(pHp > 0.0) || !isfinite(alpha);
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    xp[j] = x[j] + alpha * p[j];
+    rp[j] = r[j] - alpha * Hp[j];
+  }
+  if (threadIdx.x == 0) {
+    ctl->alpha = alpha;
+    ctl->numeric = bad ? 1 : 0;
+  }
+}
+
+// PCG, second half: delta~+ = r+^T r~+, the improvement test of Algorithm 2,
+// and on acceptance p+ = r~+ + (delta~+/delta~_t) p and the state shift.
+__global__ void __launch_bounds__(kStepThreads) pcg_step2_kernel(int d, const double* b, double* x, double* r,
+                                                                 double* rt, double* p, const double* xp,
+                                                                 const double* rp, const double* rtp, Ctl* ctl,
+                                                                 double c, double phi, int can_double, double tol2) {
+  __shared__ int s_accept;
+  const double dp = block_dot(d, rp, rtp);
+  if (threadIdx.x == 0) {
+    const long long t = ctl->t, I = ctl->I;
+    const double thr = c * pow(phi, (double)(t + 1 - I));
+    const double ratio = dp / ctl->dI;
+    ctl->dp = dp;
+    ctl->ratio = ratio;
+    ctl->thr = thr;
+    if (!isfinite(dp)) ctl->numeric = 1;
+    const int reject = (ratio > thr) && can_double;
+    s_accept = !reject;
+    ctl->accept = s_accept;
+    if (reject) ctl->I = t;
+  }
+  __syncthreads();
+  if (!s_accept) return;
+  const double beta = dp / ctl->dt;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    p[j] = rtp[j] + beta * p[j];
+    x[j] = xp[j];
+    r[j] = rp[j];
+    rt[j] = rtp[j];
+  }
+  __syncthreads();
+  const double btx = block_dot(d, b, x);
+  if (threadIdx.x == 0) {
+    ctl->dt = dp;
+    ctl->t += 1;
+    ctl->btx = btx;
+    ctl->stop = (dp <= 0.0) || (dp <= tol2 * btx);
+  }
+}
+
+// PCG restart at x_t with the current preconditioner: p = r~, delta~_t = delta~_I = r^T r~.
+__global__ void __launch_bounds__(kStepThreads) pcg_restart_kernel(int d, const double* r, const double* rt,
+                                                                   double* p, Ctl* ctl) {
+  const double dt = block_dot(d, r, rt);
+  for (int j = threadIdx.x; j < d; j += blockDim.x) p[j] = rt[j];
+  if (threadIdx.x == 0) {
+    ctl->dt = dt;
+    ctl->dI = dt;
+    ctl->accept = 1;
+    ctl->stop = (dt <= 0.0);
+    if (!isfinite(dt)) ctl->numeric = 1;
+  }
+}
+
+// IHS proposal x+ = x - mu v
+__global__ void ihs_prop_kernel(int d, const double* x, const double* v, double mu, double* xp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) xp[j] = x[j] - mu * v[j];
+}
+
+// IHS test: delta~+ = 1/2 g+^T v+, reject iff delta~+/delta~_I > c rho^(t+1-I).
+__global__ void __launch_bounds__(kStepThreads) ihs_step2_kernel(int d, const double* b, double* x, double* g,
+                                                                 double* v, const double* xp, const double* gp,
+                                                                 const double* vp, Ctl* ctl, double c, double phi,
+                                                                 int can_double, double tol2) {
+  __shared__ int s_accept;
+  const double dp = 0.5 * block_dot(d, gp, vp);
+  if (threadIdx.x == 0) {
+    const long long t = ctl->t, I = ctl->I;
+    const double thr = c * pow(phi, (double)(t + 1 - I));
+    const double ratio = dp / ctl->dI;
+    ctl->dp = dp;
+    ctl->ratio = ratio;
+    ctl->thr = thr;
+    if (!isfinite(dp)) ctl->numeric = 1;
+    const int reject = (ratio > thr) && can_double;
+    s_accept = !reject;
+    ctl->accept = s_accept;
+    if (reject) ctl->I = t;
+  }
+  __syncthreads();
+  if (!s_accept) return;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    x[j] = xp[j];
+    g[j] = gp[j];
+    v[j] = vp[j];
+  }
+  __syncthreads();
+  const double btx = block_dot(d, b, x);
+  if (threadIdx.x == 0) {
+    ctl->dt = dp;
+    ctl->t += 1;
+    ctl->btx = btx;
+    ctl->stop = (dp <= 0.0) || (2.0 * dp <= tol2 * btx);
+  }
+}
+
+// IHS restart: delta~_t = delta~_I = 1/2 g^T v with v = H_S^{-1} g.
+__global__ void __launch_bounds__(kStepThreads) ihs_restart_kernel(int d, const double* g, const double* v, Ctl* ctl) {
+  const double dt = 0.5 * block_dot(d, g, v);
+  if (threadIdx.x == 0) {
+    ctl->dt = dt;
+    ctl->dI = dt;
+    ctl->accept = 1;
+    ctl->stop = (dt <= 0.0);
+    if (!isfinite(dt)) ctl->numeric = 1;
+  }
+}
+
+__global__ void ctl_init_kernel(Ctl* ctl) {
+  memset(ctl, 0, sizeof(Ctl));
+}
+
+// ---------------------------------------------------------------- solve workspace
+struct SolveWs {
+  DevStatus* st;
+  Ctl* ctl;
+  double *x, *r, *rt, *p, *Hp, *xp, *rp, *rtp;
+  void* partials;
+  void* sketch_ws;
+  size_t sketch_bytes;
+  void* precond_ws;
+  size_t precond_bytes;
+};
+
+sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_t ws_bytes, SolveWs* L,
+                        size_t* total) {
+  const size_t d = (size_t)p->d;
+  const int64_t m_max = resolve_m_max(p, o->kind, o->m_max);
+  Carver c(ws, ws_bytes);
+  SolveWs w;
+  w.st = c.take<DevStatus>(1);
+  w.ctl = c.take<Ctl>(1);
+  w.x = c.take<double>(d);
+  w.r = c.take<double>(d);
+  w.rt = c.take<double>(d);
+  w.p = c.take<double>(d);
+  w.Hp = c.take<double>(d);
+  w.xp = c.take<double>(d);
+  w.rp = c.take<double>(d);
+  w.rtp = c.take<double>(d);
+  const size_t pbytes = apass_workspace_bytes(std::max<int64_t>(p->n, 1), p->d, 1, p->dtype == SKS_F32, false);
+  w.partials = c.take<char>(pbytes);
+  w.sketch_bytes = sketch_ws_bytes(p, o->kind, m_max);
+  w.sketch_ws = c.take<char>(w.sketch_bytes);
+  w.precond_bytes = precond_ws_bytes(p, m_max);
+  w.precond_ws = c.take<char>(w.precond_bytes);
+  if (total) *total = c.used + 256;
+  if (L) *L = w;
+  if (ws && !c.ok()) return fail(SKS_ERR_WORKSPACE, "solve workspace too small");
+  return SKS_OK;
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  float acc = 0.f;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  void start() { cudaEventRecord(a, s); }
+  void stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    acc += ms;
+  }
+};
+
+enum Method { PCG, IHS };
+
+sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sks_opts* o, double* x_io,
+                                sks_stats* stats, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  SKS_TRY(validate_problem(prob));
+  if (!o) return fail(SKS_ERR_INVALID_ARG, "opts is NULL");
+  if (!x_io) return fail(SKS_ERR_INVALID_ARG, "x is NULL");
+  if (!(o->rho > 0.0 && o->rho < 1.0)) return fail(SKS_ERR_INVALID_ARG, "rho must be in (0, 1)");
+  if (o->m_init < 1) return fail(SKS_ERR_INVALID_ARG, "m_init must be >= 1");
+  if (!(o->tol > 0.0)) return fail(SKS_ERR_INVALID_ARG, "tol must be > 0");
+  if (prob->dtype != SKS_F64) return fail(SKS_ERR_INVALID_ARG, "the plain float64 form needs a float64 A");
+  const int d = (int)prob->d;
+  SolveWs W;
+  size_t need = 0;
+  SKS_TRY(solve_layout(prob, o, nullptr, 0, nullptr, &need));
+  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "solve workspace too small (need " + std::to_string(need) + " bytes)");
+  SKS_TRY(solve_layout(prob, o, ws, ws_bytes, &W, nullptr));
+  const int64_t m_max = resolve_m_max(prob, o->kind, o->m_max);
+  const double nu2 = prob->nu * prob->nu;
+  const double rho = o->rho;
+  double phi, c;
+  if (method == PCG) {
+    phi = (1.0 - std::sqrt(1.0 - rho)) / (1.0 + std::sqrt(1.0 - rho));
+    c = 4.0 * (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
+  } else {
+    phi = rho;
+    c = (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
+  }
+  const double tol2 = (o->tol / 2.0) * (o->tol / 2.0);
+  sks_stats S;
+  std::memset(&S, 0, sizeof(S));
+  Timer t_total(stream), t_sketch(stream), t_factor(stream);
+  t_total.start();
+
+  SKS_CUDA_TRY(cudaMemsetAsync(W.st, 0, sizeof(DevStatus), stream));
+  ctl_init_kernel<<<1, 1, 0, stream>>>(W.ctl);
+  check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, W.st);
+  SKS_TRY(read_status(W.st, stream, "input check"));
+
+  ApassPlan plan;
+  SKS_TRY(apass_plan(std::max<int64_t>(prob->n, 1), d, 1, false, false, &plan));
+  CUtensorMap tmap;
+  if (prob->n > 0) SKS_TRY(map_for(prob, &tmap, plan));
+
+  sks_sketch sk;
+  SKS_TRY(sketch_init(&sk, prob, o->kind, m_max, o->sjlt_s, o->seed, W.sketch_ws, W.sketch_bytes, W.st));
+  sks_precond P;
+  SKS_TRY(precond_init(&P, prob, m_max, W.precond_ws, W.precond_bytes, W.st));
+
+  int64_t m = std::min<int64_t>(o->m_init, m_max);
+  t_sketch.start();
+  SKS_TRY(sketch_to(&sk, m, stream));
+  t_sketch.stop();
+  S.sketch_passes = 1;
+  t_factor.start();
+  SKS_TRY(precond_factor(&P, &sk, prob->nu, prob->lambda_diag, stream));
+  t_factor.stop();
+  S.factorizations = 1;
+  SKS_TRY(read_status(W.st, stream, "first preconditioner"));
+
+  auto hess = [&](const double* in, double* out, double sgn, const double* addv, double addc) -> sks_status {
+    S.a_passes += 1;
+    return apass_launch(plan, &tmap, prob->n, d, 1, false, false, in, out, nu2, prob->lambda_diag, W.partials, W.st,
+                        stream, sgn, addv, addc);
+  };
+
+  sks_status result = SKS_OK;
+  for (int64_t col = 0; col < prob->k; ++col) {
+    const double* b = prob->b + col * d;
+    double* xcol = x_io + col * d;
+    SKS_CUDA_TRY(cudaMemcpyAsync(W.x, xcol, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    ctl_init_kernel<<<1, 1, 0, stream>>>(W.ctl);
+    // PCG: r = b - H x0, r~ = H_S^{-1} r.   IHS: g = H x0 - b (in r), v = H_S^{-1} g (in rt).
+    if (method == PCG) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
+    else SKS_TRY(hess(W.x, W.r, 1.0, b, -1.0));
+    SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
+    if (method == PCG) pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
+    else ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
+    SKS_CUDA_TRY(cudaGetLastError());
+    Ctl h;
+    SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
+    SKS_TRY(read_status(W.st, stream, "initial residual"));
+    if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite initial decrement"); break; }
+    bool converged = h.stop != 0;
+    int64_t guard = 0;
+    while (!converged && h.t < o->max_iter && guard++ < o->max_iter + 64) {
+      const int can_double = m < m_max ? 1 : 0;
+      if (method == PCG) {
+        SKS_TRY(hess(W.p, W.Hp, 1.0, nullptr, 0.0));
+        pcg_step1_kernel<<<1, kStepThreads, 0, stream>>>(d, W.x, W.r, W.p, W.Hp, W.xp, W.rp, W.ctl);
+        SKS_CUDA_TRY(cudaGetLastError());
+        SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
+        pcg_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.p, W.xp, W.rp, W.rtp, W.ctl, c, phi,
+                                                         can_double, tol2);
+      } else {
+        ihs_prop_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, W.x, W.rt, 1.0 - rho, W.xp);
+        SKS_TRY(hess(W.xp, W.rp, 1.0, b, -1.0));
+        SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
+        ihs_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.xp, W.rp, W.rtp, W.ctl, c, phi,
+                                                         can_double, tol2);
+      }
+      SKS_CUDA_TRY(cudaGetLastError());
+      const long long t_before = h.t;
+      SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
+      SKS_TRY(read_status(W.st, stream, "iteration"));
+      if (o->trace && S.trace_len < o->trace_cap) {
+        sks_trace_event& e = o->trace[S.trace_len++];
+        e.t = t_before;
+        e.m = m;
+        e.ratio = h.ratio;
+        e.threshold = h.thr;
+        e.accepted = h.accept;
+        e.outer = 0;
+      }
+      if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite value in the iteration"); break; }
+      if (!h.accept) {
+        S.rejections += 1;
+        m = std::min<int64_t>(2 * m, m_max);
+        t_sketch.start();
+        SKS_TRY(sketch_to(&sk, m, stream));
+        t_sketch.stop();
+        S.sketch_passes += 1;
+        t_factor.start();
+        SKS_TRY(precond_factor(&P, &sk, prob->nu, prob->lambda_diag, stream));
+        t_factor.stop();
+        S.factorizations += 1;
+        if (method == PCG) {
+          if (!o->reuse_residual) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
+          SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
+          pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
+        } else {
+          SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
+          ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
+        }
+        SKS_CUDA_TRY(cudaGetLastError());
+        SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
+        SKS_TRY(read_status(W.st, stream, "restart"));
+        if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite decrement at restart"); break; }
+        converged = h.stop != 0;
+        continue;
+      }
+      converged = h.stop != 0;
+    }
+    SKS_CUDA_TRY(cudaMemcpyAsync(xcol, W.x, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    S.iters += h.t;
+    S.final_delta_tilde = h.dt;
+    const double fac = method == PCG ? 1.0 : 2.0;
+    S.est_rel_err = h.btx > 0 ? std::sqrt(std::max(0.0, fac * h.dt / h.btx)) : 0.0;
+    if (result != SKS_OK) break;
+    if (!converged && result == SKS_OK) result = fail(SKS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+  }
+  t_total.stop();
+  S.final_m = m;
+  S.ms_total = t_total.acc;
+  S.ms_sketch = t_sketch.acc;
+  S.ms_factor = t_factor.acc;
+  S.ms_iter = std::max(0.f, S.ms_total - S.ms_sketch - S.ms_factor);
+  S.status = result;
+  if (stats) *stats = S;
+  return result;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- exported helpers (used by abi.cu)
+sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes) {
+  SKS_TRY(validate_problem(p));
+  if (!o || !bytes) return fail(SKS_ERR_INVALID_ARG, "NULL argument");
+  return solve_layout(p, o, nullptr, 0, nullptr, bytes);
+}
+
+sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
+                          size_t ws_bytes, cudaStream_t stream) {
+  if (o && o->precision != SKS_PLAIN_F64)
+    return fail(SKS_ERR_UNSUPPORTED, "mixed-precision form not available in this entry point yet");
+  return adaptive_solve_plain(method == 0 ? PCG : IHS, p, o, x, stats, ws, ws_bytes, stream);
+}
+
+sks_status hess_apply_ws(const sks_problem* p, size_t* bytes) {
+  SKS_TRY(validate_problem(p));
+  if (!bytes) return fail(SKS_ERR_INVALID_ARG, "NULL argument");
+  const bool f32 = p->dtype == SKS_F32;
+  Carver c(nullptr, 0);
+  c.take<DevStatus>(1);
+  c.take<char>(apass_workspace_bytes(std::max<int64_t>(p->n, 1), p->d, p->k == 8 ? 8 : 1, f32, f32));
+  c.take<char>(apass_workspace_bytes(std::max<int64_t>(p->n, 1), p->d, p->k == 8 ? 8 : 1, f32, false));
+  c.take<float>((size_t)p->d * p->k * 2);
+  *bytes = c.used + 256;
+  return SKS_OK;
+}
+
+sks_status hess_apply(const sks_problem* p, const double* x, double* y, int extended, void* ws, size_t ws_bytes,
+                      cudaStream_t stream) {
+  SKS_TRY(validate_problem(p));
+  if (!x || !y) return fail(SKS_ERR_INVALID_ARG, "x or y is NULL");
+  size_t need = 0;
+  SKS_TRY(hess_apply_ws(p, &need));
+  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "hess_apply workspace too small");
+  const bool f32 = p->dtype == SKS_F32;
+  const bool vec32 = f32 && !extended;
+  const int64_t kb = p->k == 8 ? 8 : 1;
+  Carver c(ws, ws_bytes);
+  DevStatus* st = c.take<DevStatus>(1);
+  void* part32 = c.take<char>(apass_workspace_bytes(std::max<int64_t>(p->n, 1), p->d, kb, f32, f32));
+  void* part64 = c.take<char>(apass_workspace_bytes(std::max<int64_t>(p->n, 1), p->d, kb, f32, false));
+  float* xf = c.take<float>((size_t)p->d * p->k);
+  float* yf = c.take<float>((size_t)p->d * p->k);
+  SKS_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), stream));
+  ApassPlan plan;
+  SKS_TRY(apass_plan(std::max<int64_t>(p->n, 1), p->d, kb, f32, vec32, &plan));
+  CUtensorMap tmap;
+  if (p->n > 0) SKS_TRY(map_for(p, &tmap, plan));
+  const double nu2 = p->nu * p->nu;
+  for (int64_t c0 = 0; c0 < p->k; c0 += kb) {
+    const double* xc = x + c0 * p->d;
+    double* yc = y + c0 * p->d;
+    if (vec32) {
+      const long long cnt = (long long)p->d * kb;
+      f64_to_f32_kernel<<<blocks_for(cnt), 256, 0, stream>>>(cnt, xc, xf);
+      SKS_TRY(apass_launch(plan, &tmap, p->n, p->d, kb, true, true, xf, yf, nu2, p->lambda_diag, part32, st, stream));
+      f32_to_f64_kernel<<<blocks_for(cnt), 256, 0, stream>>>(cnt, yf, yc);
+      SKS_CUDA_TRY(cudaGetLastError());
+    } else {
+      SKS_TRY(apass_launch(plan, &tmap, p->n, p->d, kb, f32, false, xc, yc, nu2, p->lambda_diag, part64, st, stream));
+    }
+  }
+  return read_status(st, stream, "hess_apply");
+}
+
+}  // namespace sks
+
+// ============================================================================ C ABI: sketch / precond
+
+using namespace sks;
+
+extern "C" sks_status sks_sketch_workspace_size(const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s,
+                                                size_t* bytes) {
+  SKS_TRY(validate_problem(p));
+  if (!bytes) return fail(SKS_ERR_INVALID_ARG, "bytes is NULL");
+  (void)sjlt_s;
+  *bytes = sketch_ws_bytes(p, kind, resolve_m_max(p, kind, m_max));
+  return SKS_OK;
+}
+
+extern "C" sks_status sks_sketch_create(sks_sketch** out, const sks_problem* p, sks_kind kind, int64_t m_init,
+                                        int64_t m_max, int sjlt_s, uint64_t seed, void* ws, size_t ws_bytes,
+                                        void* stream) {
+  if (!out) return fail(SKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  SKS_TRY(validate_problem(p));
+  if (kind != SKS_SRHT && kind != SKS_GAUSSIAN && kind != SKS_SJLT) return fail(SKS_ERR_INVALID_ARG, "bad kind");
+  if (sjlt_s < 1 || sjlt_s > kSjltMaxS) return fail(SKS_ERR_INVALID_ARG, "sjlt_s must be in [1, 16]");
+  const int64_t mm = resolve_m_max(p, kind, m_max);
+  if (m_init < 1 || m_init > mm) return fail(SKS_ERR_INVALID_ARG, "m_init must be in [1, m_max]");
+  if (!ws || ws_bytes < sketch_ws_bytes(p, kind, mm)) return fail(SKS_ERR_WORKSPACE, "sketch workspace too small");
+  sks_sketch* s = new (std::nothrow) sks_sketch();
+  if (!s) return fail(SKS_ERR_INVALID_ARG, "host allocation failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  sks_status r = sketch_init(s, p, kind, mm, sjlt_s, seed, ws, ws_bytes, nullptr);
+  if (r == SKS_OK) {
+    cudaMemsetAsync(s->st, 0, sizeof(DevStatus), st);
+    r = sketch_to(s, m_init, st);
+  }
+  if (r == SKS_OK) r = read_status(s->st, st, "sketch_create");
+  if (r != SKS_OK) {
+    delete s;
+    return r;
+  }
+  *out = s;
+  return SKS_OK;
+}
+
+extern "C" sks_status sks_sketch_grow(sks_sketch* s, int64_t new_m, void* stream) {
+  if (!s) return fail(SKS_ERR_INVALID_ARG, "sketch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  SKS_TRY(sketch_to(s, new_m, st));
+  return read_status(s->st, st, "sketch_grow");
+}
+
+extern "C" sks_status sks_sketch_rows(const sks_sketch* s, int64_t* m) {
+  if (!s || !m) return fail(SKS_ERR_INVALID_ARG, "NULL argument");
+  *m = s->m;
+  return SKS_OK;
+}
+
+extern "C" sks_status sks_sketch_copy_out(const sks_sketch* s, double* SA, void* stream) {
+  if (!s || !SA) return fail(SKS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long cnt = (long long)s->m * s->d;
+  if (cnt == 0) return SKS_OK;
+  scale_rows_out_kernel<<<blocks_for(cnt), 256, 0, st>>>((int)s->m, s->d, s->Y, s->f32 ? 1 : 0, s->ldy,
+                                                         std::sqrt(s->scale2()), SA);
+  SKS_CUDA_TRY(cudaGetLastError());
+  SKS_CUDA_TRY(cudaStreamSynchronize(st));
+  return SKS_OK;
+}
+
+extern "C" void sks_sketch_destroy(sks_sketch* s) { delete s; }
+
+extern "C" sks_status sks_precond_workspace_size(const sks_problem* p, int64_t m_max, size_t* bytes) {
+  SKS_TRY(validate_problem(p));
+  if (!bytes) return fail(SKS_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = precond_ws_bytes(p, std::max<int64_t>(m_max, 1));
+  return SKS_OK;
+}
+
+extern "C" sks_status sks_precond_build(sks_precond** out, const sks_sketch* s, const sks_problem* p, void* ws,
+                                        size_t ws_bytes, void* stream) {
+  if (!out || !s) return fail(SKS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  SKS_TRY(validate_problem(p));
+  if (p->d != s->d) return fail(SKS_ERR_INVALID_ARG, "sketch and problem disagree on d");
+  if (!ws || ws_bytes < precond_ws_bytes(p, s->m_max)) return fail(SKS_ERR_WORKSPACE, "preconditioner workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  sks_precond* P = new (std::nothrow) sks_precond();
+  if (!P) return fail(SKS_ERR_INVALID_ARG, "host allocation failed");
+  sks_status r = precond_init(P, p, s->m_max, ws, ws_bytes, nullptr);
+  if (r == SKS_OK) {
+    cudaMemsetAsync(P->st, 0, sizeof(DevStatus), st);
+    check_lambda_kernel<<<(int)((p->d + 255) / 256), 256, 0, st>>>((int)p->d, p->lambda_diag, P->st);
+    r = precond_factor(P, s, p->nu, p->lambda_diag, st);
+  }
+  if (r == SKS_OK) r = read_status(P->st, st, "precond_build");
+  if (r != SKS_OK) {
+    delete P;
+    return r;
+  }
+  *out = P;
+  return SKS_OK;
+}
+
+extern "C" sks_status sks_precond_apply(const sks_precond* P, const double* z, double* v, int64_t k, void* stream) {
+  if (!P || !z || !v || k < 1) return fail(SKS_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int64_t c = 0; c < k; ++c) SKS_TRY(precond_apply1(P, z + c * P->d, v + c * P->d, st));
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
+extern "C" void sks_precond_destroy(sks_precond* P) { delete P; }

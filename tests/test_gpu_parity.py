@@ -1,0 +1,223 @@
+"""GPU parity: every kernel of the hot path against the CPU oracle, through
+the C ABI (sizes that span several tiles and ragged tails; edge cases)."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import sketch as OS
+from oracle import solvers as O
+from tests.gpu_util import dev, host, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def api():
+    import paper_2104_14101_gb300 as sks
+    return sks
+
+
+# ----------------------------------------------------------------------------- A-pass (K1)
+
+HESS_SHAPES = [
+    (1, 1), (7, 3), (1000, 33), (4096, 256), (5000, 512), (3001, 1000), (2049, 2048), (1500, 4096), (0, 17),
+]
+
+
+@pytest.mark.parametrize("n,d", HESS_SHAPES)
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f32ext"])
+def test_hess_apply_matches_oracle(n, d, dtype):
+    rng = np.random.default_rng(n * 7 + d)
+    A = rng.standard_normal((n, d))
+    if dtype != "f64":
+        A = A.astype(np.float32).astype(np.float64)
+    x = rng.standard_normal(d)
+    lam = 1 + rng.random(d)
+    nu = 0.3
+    ref = O.hess_apply(A, nu, lam, x)
+    # error scale: |A|^T |A| |x| + nu^2 lam |x|
+    scale = np.abs(A).T @ (np.abs(A) @ np.abs(x)) + nu ** 2 * lam * np.abs(x) + 1e-300
+    tA = dev(A, torch.float32 if dtype != "f64" else torch.float64)
+    got = host(api().hess_apply(tA, dev(x), nu, dev(lam), extended=(dtype == "f32ext")))
+    tol = 1e-5 if dtype == "f32" else 1e-13
+    assert float(np.max(np.abs(got - ref) / scale)) < tol
+
+
+def test_hess_apply_padded_leading_dimension():
+    rng = np.random.default_rng(3)
+    n, d, ld = 777, 250, 256
+    buf = rng.standard_normal((n, ld))
+    A = buf[:, :d]
+    x, lam = rng.standard_normal(d), 1 + rng.random(d)
+    ref = O.hess_apply(A, 0.1, lam, x)
+    tA = dev(buf)[:, :d]
+    got = host(api().hess_apply(tA, dev(x), 0.1, dev(lam)))
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_hess_apply_eight_rhs():
+    rng = np.random.default_rng(4)
+    n, d = 3000, 1024
+    A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+    X = rng.standard_normal((d, 8))
+    lam = 1 + rng.random(d)
+    ref = O.hess_apply(A, 0.2, lam, X)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        got = host(api().hess_apply(dev(A, dt), dev(X), 0.2, dev(lam)))
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < tol
+
+
+# ----------------------------------------------------------------------------- sketches (K2-K5)
+
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+@pytest.mark.parametrize("n,d,m", [(1000, 40, 24), (4096, 256, 300), (513, 7, 1), (64, 3, 64)])
+def test_sketch_matches_oracle_fp64(kind, n, d, m):
+    rng = np.random.default_rng(n + d + m)
+    A = rng.standard_normal((n, d))
+    lam = np.ones(d)
+    sk = api().Sketch(dev(A), 0.1, dev(lam), kind=kind, m=m, sjlt_s=3, seed=12345)
+    got = host(sk.matrix())
+    ref = OS.sketch(kind, A, m, seed=12345, sjlt_s=3)
+    scale = np.sqrt(np.sum(A * A, axis=0))[None, :] * (math.sqrt(OS.next_pow2(n) / m) if kind == "srht" else 1.0)
+    assert got.shape == ref.shape
+    assert float(np.max(np.abs(got - ref) / (scale + 1e-300))) < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+def test_sketch_fp32_within_1e5(kind):
+    rng = np.random.default_rng(9)
+    n, d, m = 3000, 64, 96
+    A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+    sk = api().Sketch(dev(A, torch.float32), 0.1, dev(np.ones(d)), kind=kind, m=m, sjlt_s=4, seed=77)
+    got = host(sk.matrix())
+    ref = OS.sketch(kind, A, m, seed=77, sjlt_s=4)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+
+
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+def test_sketch_growth_is_nested(kind):
+    rng = np.random.default_rng(5)
+    n, d = 2000, 30
+    A = rng.standard_normal((n, d))
+    sk = api().Sketch(dev(A), 0.1, dev(np.ones(d)), kind=kind, m=5, sjlt_s=2, seed=3)
+    for m in (10, 20, 40, 80):
+        sk.grow(m)
+        ref = OS.sketch(kind, A, m, seed=3, sjlt_s=2)
+        got = host(sk.matrix())
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_srht_full_size_gives_exact_hessian():
+    # m = n_pad: S^T S = I, so (SA)^T SA = A^T A exactly (up to rounding).
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((128, 16))
+    sk = api().Sketch(dev(A), 0.1, dev(np.ones(16)), kind="srht", m=128, seed=8)
+    SA = host(sk.matrix())
+    assert np.allclose(SA.T @ SA, A.T @ A, rtol=1e-12, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------- preconditioner (a5, a6)
+
+@pytest.mark.parametrize("m,d", [(1, 40), (17, 40), (39, 40), (40, 40), (100, 40), (300, 256), (64, 300)])
+def test_preconditioner_apply_matches_oracle(m, d):
+    rng = np.random.default_rng(m * 13 + d)
+    n = 2000
+    A = rng.standard_normal((n, d)) * (0.9 ** np.arange(d))[None, :]
+    lam = 1 + 9 * rng.random(d)
+    nu = 1e-2
+    sk = api().Sketch(dev(A), nu, dev(lam), kind="gaussian", m=m, seed=4)
+    P = api().Preconditioner(sk)
+    Z = rng.standard_normal((d, 3))
+    got = host(P.apply(dev(Z)))
+    ref = O.Preconditioner(OS.sketch("gaussian", A, m, seed=4), nu, lam).apply(Z)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-9
+
+
+def test_precond_rejects_lambda_below_one():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((100, 8))
+    lam = np.ones(8)
+    lam[3] = 0.5
+    sk = api().Sketch(dev(A), 0.1, dev(lam), kind="gaussian", m=4, seed=1)
+    from paper_2104_14101_gb300._lib import SksError
+    with pytest.raises(SksError) as e:
+        api().Preconditioner(sk)
+    assert "lambda" in str(e.value)
+
+
+# ----------------------------------------------------------------------------- adaptive solvers (a7-a11)
+
+def _xstar(p):
+    return O.direct_solve(p.A, p.b, p.nu, p.lam)
+
+
+@pytest.mark.parametrize("method", ["pcg", "ihs"])
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "sjlt"])
+def test_adaptive_solve_reaches_tolerance(method, kind):
+    p = synthetic.make_problem("C1", 0, n=2048, d=96, nu=1e-3, decay="harmonic", lam="one_plus_9u")
+    xs = _xstar(p)
+    fn = api().adaptive_pcg if method == "pcg" else api().adaptive_ihs
+    x, st, _ = fn(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind=kind, m_init=1, tol=1e-10, sjlt_s=2, seed=11)
+    err = O.rel_err_H(p.A, p.nu, p.lam, host(x), xs)
+    assert err <= 1e-10, (err, st)
+    assert st["status_name"] == "OK"
+
+
+@pytest.mark.parametrize("method", ["pcg", "ihs"])
+@pytest.mark.parametrize("kind", ["gaussian", "srht"])
+def test_m_sequence_matches_oracle(method, kind):
+    # Plain float64: the GPU takes the same accept/reject decisions as the
+    # oracle (literal restart), except where the oracle's ratio sits within
+    # 1e-9 of the threshold.
+    p = synthetic.make_problem("C1", 1, n=1024, d=64, nu=1e-2)
+    fo = O.adaptive_pcg if method == "pcg" else O.adaptive_ihs
+    kw = dict(literal_restart=True) if method == "pcg" else {}
+    xo, so, to = fo(p.A, p.b, p.nu, p.lam, kind=kind, seed=5, m_init=1, tol=1e-10, **kw)
+    fg = api().adaptive_pcg if method == "pcg" else api().adaptive_ihs
+    xg, sg, tg = fg(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind=kind, m_init=1, tol=1e-10, seed=5,
+                    reuse_residual=False, trace_cap=4096)
+    for eo, eg in zip(to, tg):
+        if abs(eo["ratio"] / eo["thr"] - 1) < 1e-9:
+            break
+        assert (eo["t"], eo["m"], eo["accepted"]) == (eg["t"], eg["m"], eg["accepted"])
+        assert math.isclose(eo["ratio"], eg["ratio"], rel_tol=1e-6)
+    else:
+        assert len(to) == len(tg)
+        assert so["final_m"] == sg["final_m"] and so["iters"] == sg["iters"]
+
+
+def test_config1_full_size():
+    # C1 at its stated size: Gaussian, m_init = 1, tol 1e-10, float64.
+    p = synthetic.make_problem("C1", 0)
+    xs = p.V @ ((p.sigma / (p.sigma ** 2 + p.nu ** 2)) * (p.U.T @ p.y))
+    x, st, _ = api().adaptive_pcg(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind="gaussian", m_init=1, tol=1e-10, seed=0)
+    assert O.rel_err_H(p.A, p.nu, p.lam, host(x), xs) <= 1e-10
+    assert st["final_m"] <= 4096
+
+
+def test_zero_rhs_returns_zero():
+    p = synthetic.make_problem("C1", 0, n=512, d=32)
+    x, st, _ = api().adaptive_pcg(dev(p.A), dev(np.zeros(32)), p.nu, dev(p.lam), kind="srht")
+    assert float(torch.abs(x).max()) == 0.0 and st["iters"] == 0
+
+
+def test_max_iter_reports_no_convergence():
+    p = synthetic.make_problem("C1", 0, n=1024, d=64, nu=1e-4)
+    from paper_2104_14101_gb300._lib import SksError
+    with pytest.raises(SksError) as e:
+        api().adaptive_pcg(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind="srht", m_init=1, tol=1e-14, max_iter=2)
+    assert "NO_CONVERGENCE" in str(e.value)
+
+
+def test_multiple_rhs_solved_columnwise():
+    p = synthetic.make_problem("C4", 0, n=2048, d=64, k=3, dtype="f64")
+    xs = O.direct_solve(p.A, p.b, p.nu, p.lam)
+    x, st, _ = api().adaptive_pcg(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind="gaussian", tol=1e-10)
+    for c in range(3):
+        assert O.rel_err_H(p.A, p.nu, p.lam, host(x)[:, c], xs[:, c]) <= 1e-10

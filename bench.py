@@ -1,0 +1,351 @@
+"""Benchmark of the adaptive sketching-based solver on one GB300 (or N replicas).
+
+One step = one complete adaptive solve (sketch, preconditioner builds,
+iterations to the tolerance) of the workload, inputs resident in HBM.
+Prints ONE JSON line (rank 0).  See the design doc for the workload recipe and the
+roofline arithmetic.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload C2] [--method pcg|ihs] [--no-cpu-baseline]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms to 1e-8 rel. H-error, mixed+refined vs FP64 adaptive PCG; A-pass HBM GB/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# Workloads (sizes and solver settings; generator in synthetic/problems.py).
+WORKLOADS = {
+    "C2": dict(config="C2", method="pcg", kind="srht", m_init=16, m_max=4096, tol=1e-10, precision="plain",
+               desc="adaptive PCG, SRHT, float64: n=2^17, d=2048, sigma_j=1/(1+j), nu=1e-3, "
+                    "Lambda=1+9U, m 16->4096, tol 1e-10"),
+    "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
+               desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
+}
+
+# ncu DRAM traffic per A-pass launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by the source hash of the kernel file it was captured from; any change
+# to the kernel source invalidates the figure (traffic then reported as null).
+TRAFFIC = {}
+
+
+def kernel_hash():
+    with open(os.path.join(ROOT, "paper_2104_14101_gb300", "csrc", "apass.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device):
+    if world == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def oracle_solve(wl, A, b, nu, lam):
+    """The CPU oracle's adaptive solve, as it stands (test infrastructure)."""
+    from oracle import solvers as O
+    fn = O.adaptive_pcg if wl["method"] == "pcg" else O.adaptive_ihs
+    kw = dict(kind=wl["kind"], seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"])
+    return fn(A, b, nu, lam, **kw)
+
+
+def run_reference(args, wl, world, rank):
+    """--impl reference: the CPU oracle on the host cores, same workload."""
+    if rank != 0:
+        return None
+    import synthetic
+    gdev = "cuda" if torch.cuda.is_available() else "cpu"
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=gdev)
+    A = prob["A64"].cpu().numpy()
+    b = prob["b"][:, 0].cpu().numpy()
+    lam = prob["lam"].cpu().numpy()
+    nu = prob["nu"]
+    del prob
+    # warm-up steps: the same solver on the first n/32 rows (untimed)
+    nw = max(A.shape[0] // 32, 4 * A.shape[1])
+    for _ in range(args.warmup):
+        oracle_solve(wl, A[:nw], A[:nw].T @ np.ones(nw), nu, lam)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x, st, _ = oracle_solve(wl, A, b, nu, lam)
+        times.append((time.perf_counter() - t0) * 1e3)
+    ms = sum(times) / len(times)
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": wl["config"] + ": " + wl["desc"], "method": "adaptive_" + wl["method"]},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "one full oracle adaptive solve of the workload per step "
+                                   "(warm-up steps on the first n/32 rows)"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_stats": {k: st[k] for k in ("iters", "rejections", "final_m", "a_passes")},
+    }
+    return line
+
+
+def run_ours(args, wl, world, rank, local):
+    import paper_2104_14101_gb300 as sks
+    from paper_2104_14101_gb300 import _lib
+    import synthetic
+
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    lib = _lib.load()
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev)
+    A = prob["A64"]
+    b = prob["b"][:, 0].contiguous()
+    lam = prob["lam"]
+    nu = prob["nu"]
+    n, d = A.shape
+    solver = sks.Solver(A, b, nu, lam, method=wl["method"], kind=wl["kind"], m_init=wl["m_init"], m_max=wl["m_max"],
+                        tol=wl["tol"], seed=0)
+    for _ in range(args.warmup):
+        solver.solve()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = lib.sks_kernel_launch_count()
+    stats = []
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    x = None
+    for _ in range(args.steps):
+        x, st, _ = solver.solve()
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = lib.sks_kernel_launch_count() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+
+    # ---- roofline of the dominant kernel (the A-pass): live CUDA-event times
+    ap_ms = sum(s["ms_apass"] for s in stats)
+    ap_n = sum(s["apass_timed"] for s in stats)
+    ap_avg_ms = ap_ms / max(ap_n, 1)
+    elem = 8
+    bytes_per_pass = n * d * elem + 3 * d * 8
+    flops_per_pass = 4.0 * n * d
+    gbs = bytes_per_pass / (ap_avg_ms * 1e-3) / 1e9
+    peaks, peak_src = load_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    # float64 A-pass: 2 FMA per element at 2 float64 FMA/clk/SM (152 SMs)
+    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    achieved_tflops = flops_per_pass / (ap_avg_ms * 1e-3) / 1e12
+    th = TRAFFIC.get(kernel_hash())
+    roofline = {
+        "bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+        "frac": achieved_tflops / fp64_peak_tflops, "traffic": th,
+        "kernel": "apass_kernel<double,double>", "launches": ap_n, "avg_launch_ms": ap_avg_ms,
+        "hbm_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": gbs / peaks["hbm_gbs"],
+        "peak_source": "float64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2 flop) at the sampled median "
+                       "SM clock; HBM peak " + peak_src,
+    }
+
+    # ---- e2e: host buffers, copies inside the timed region
+    A_h = A.cpu().pin_memory()
+    b_h = b.cpu().pin_memory()
+    lam_h = lam.cpu().pin_memory()
+    x_h = torch.empty(d, dtype=torch.float64).pin_memory()
+    A_d = torch.empty_like(A)
+    b_d = torch.empty_like(b)
+    lam_d = torch.empty_like(lam)
+    A_d.copy_(A_h)
+    b_d.copy_(b_h)
+    lam_d.copy_(lam_h)
+    solver_e2e = sks.Solver(A_d, b_d, nu, lam_d, method=wl["method"], kind=wl["kind"], m_init=wl["m_init"],
+                            m_max=wl["m_max"], tol=wl["tol"], seed=0)
+    solver_e2e.solve()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    k_e2e = max(1, min(args.steps, 5))
+    barrier(world)
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for _ in range(k_e2e):
+        A_d.copy_(A_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        lam_d.copy_(lam_h, non_blocking=True)
+        xe, _, _ = solver_e2e.solve()
+        x_h.copy_(xe, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3) / k_e2e, world, dev)
+    h2d = A.numel() * A.element_size() + b.numel() * 8 + lam.numel() * 8
+    d2h = d * 8
+
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["config"] + ": " + wl["desc"], "method": "adaptive_" + wl["method"],
+                   "n": n, "d": d, "kind": wl["kind"], "precision": wl["precision"],
+                   "l2": "inputs larger than L2 (A = %.2f GiB)" % (A.numel() * 8 / 2 ** 30),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "solve_stats": {k: st0[k] for k in ("iters", "rejections", "final_m", "a_passes", "factorizations",
+                                            "ms_sketch", "ms_factor", "ms_iter", "est_rel_err")},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        A_np = A_h.numpy()
+        b_np = b_h.numpy()
+        lam_np = lam_h.numpy()
+        t0 = time.perf_counter()
+        xo, so, _ = oracle_solve(wl, A_np, b_np, nu, lam_np)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        from oracle import solvers as O
+        xs = O.direct_solve(A_np, b_np, nu, lam_np)
+        line["cpu_baseline"] = {"value": cpu_ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": "one full oracle adaptive solve of the same workload (all rows)",
+                                "oracle_rel_err_H": O.rel_err_H(A_np, nu, lam_np, xo, xs)}
+        line["rel_err_H_vs_oracle"] = O.rel_err_H(A_np, nu, lam_np, x.cpu().numpy(), xs)
+    return line if rank == 0 else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--method", choices=["pcg", "ihs"], default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    wl = dict(WORKLOADS[args.workload])
+    if args.method:
+        wl["method"] = args.method
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        line = run_reference(args, wl, world, rank)
+    else:
+        line = run_ours(args, wl, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -114,6 +114,8 @@ typedef struct {
   double est_rel_err;     /* sqrt(delta~_t / b^T x_t): the stop rule's estimate */
   int64_t trace_len;      /* events written to opts.trace                       */
   float ms_total, ms_sketch, ms_factor, ms_iter;
+  float ms_apass;         /* device time of the A-pass kernels (CUDA events)    */
+  int64_t apass_timed;    /* A-pass launches covered by ms_apass                */
   sks_status status;
 } sks_stats;
 
@@ -130,6 +132,10 @@ const char* sks_version(void);
 
 /* Last error message of the calling thread ("" if none). */
 const char* sks_last_error(void);
+
+/* Number of CUDA kernels the calling thread has launched through this
+ * library since it was loaded (monotone counter, for launch accounting). */
+uint64_t sks_kernel_launch_count(void);
 
 /* ---------------------------------------------------------------------------
  * Hessian pass (Section 4.1.2: the O(nd) per-iteration cost).

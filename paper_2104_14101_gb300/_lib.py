@@ -44,7 +44,8 @@ class Stats(C.Structure):
                 ("sketch_passes", C.c_int64), ("factorizations", C.c_int64), ("outer_iters", C.c_int64),
                 ("final_delta_tilde", C.c_double), ("est_rel_err", C.c_double), ("trace_len", C.c_int64),
                 ("ms_total", C.c_float), ("ms_sketch", C.c_float), ("ms_factor", C.c_float),
-                ("ms_iter", C.c_float), ("status", C.c_int)]
+                ("ms_iter", C.c_float), ("ms_apass", C.c_float), ("apass_timed", C.c_int64),
+                ("status", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -55,6 +56,7 @@ _SIGS = {
     "sks_opts_default": (None, [P(Opts)]),
     "sks_version": (C.c_char_p, []),
     "sks_last_error": (C.c_char_p, []),
+    "sks_kernel_launch_count": (C.c_uint64, []),
     "sks_hess_apply_workspace_size": (C.c_int, [P(Problem), P(C.c_size_t)]),
     "sks_hess_apply": (C.c_int, [P(Problem), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
     "sks_sketch_workspace_size": (C.c_int, [P(Problem), C.c_int, C.c_int64, C.c_int, P(C.c_size_t)]),

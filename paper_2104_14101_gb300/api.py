@@ -34,7 +34,7 @@ def make_problem(A, b, nu, lam):
     """
     if not A.is_cuda:
         raise ValueError("A must be a CUDA tensor")
-    if A.dim() != 2 or A.stride(1) != 1:
+    if A.dim() != 2 or (A.numel() > 0 and A.stride(1) != 1):
         raise ValueError("A must be 2-D with unit column stride")
     if A.dtype not in (torch.float64, torch.float32):
         raise ValueError("A must be float64 or float32")

@@ -26,6 +26,8 @@ extern "C" const char* sks_version(void) { return "sks 0.1 (sm_103a)"; }
 
 extern "C" const char* sks_last_error(void) { return last_error_cstr(); }
 
+extern "C" uint64_t sks_kernel_launch_count(void) { return launch_count(); }
+
 extern "C" sks_status sks_hess_apply_workspace_size(const sks_problem* p, size_t* bytes) { return hess_apply_ws(p, bytes); }
 
 extern "C" sks_status sks_hess_apply(const sks_problem* p, const double* x, double* y, int extended, void* ws,

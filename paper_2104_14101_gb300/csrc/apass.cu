@@ -261,7 +261,7 @@ __global__ void apass_finalize(int nparts, int d, int k, const TX* __restrict__ 
 template <typename TA, typename TX, int G, int QMAX, int K>
 sks_status launch_t(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int64_t d, const void* x,
                     void* y, double nu2, const double* lambda, void* partials, DevStatus* st, cudaStream_t stream,
-                    double sgn, const void* addv, double addc) {
+                    double sgn, const void* addv, double addc, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   auto kern = apass_kernel<TA, TX, G, QMAX, K>;
   SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
   const int nparts = pl.grid * (kConsumers / G);
@@ -278,12 +278,19 @@ sks_status launch_t(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int
     a.x = x;
     a.partials = partials;
     a.st = st;
+    if (ev_begin) SKS_CUDA_TRY(cudaEventRecord(ev_begin, stream));
     kern<<<pl.grid, kThreads, pl.smem, stream>>>(*tmap, a);
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
+    if (ev_end) SKS_CUDA_TRY(cudaEventRecord(ev_end, stream));
+  } else if (ev_begin && ev_end) {
+    SKS_CUDA_TRY(cudaEventRecord(ev_begin, stream));
+    SKS_CUDA_TRY(cudaEventRecord(ev_end, stream));
   }
   dim3 fg((unsigned)((d + 127) / 128), (unsigned)K);
   apass_finalize<TX><<<fg, 128, 0, stream>>>(n > 0 ? nparts : 0, (int)d, K, (const TX*)partials, (const TX*)x,
                                                (TX*)y, nu2, lambda, sgn, (const TX*)addv, addc);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }
@@ -307,7 +314,7 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   const int qcap = a_f32 ? 4 : 8;
   int group = (nvec <= 32 * qcap && k == 1) ? 32 : 256;
   if (k == 8) group = 256;
-  const int qmax = (k == 8) ? 1 : qcap;
+  const int qmax = (k == 8) ? (a_f32 ? 1 : 2) : qcap;
   const int q = (nvec + group - 1) / group;
   if (q > qmax) return fail(SKS_ERR_UNSUPPORTED, "A-pass: row too wide for this instantiation");
   const int ng = kConsumers / group;
@@ -345,21 +352,22 @@ size_t apass_workspace_bytes(int64_t n, int64_t d, int64_t k, bool a_f32, bool v
 
 sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int64_t d, int64_t k, bool a_f32,
                         bool vec_f32, const void* x, void* y, double nu2, const double* lambda, void* partials,
-                        DevStatus* st, cudaStream_t stream, double sgn, const void* addv, double addc) {
+                        DevStatus* st, cudaStream_t stream, double sgn, const void* addv, double addc,
+                        cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   if (!a_f32 && vec_f32) return fail(SKS_ERR_UNSUPPORTED, "float64 A with float32 vectors");
   if (!a_f32) {
-    if (k == 8) return launch_t<double, double, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
-    if (pl.group == 32) return launch_t<double, double, 32, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
-    return launch_t<double, double, 256, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+    if (k == 8) return launch_t<double, double, 256, 2, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+    if (pl.group == 32) return launch_t<double, double, 32, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+    return launch_t<double, double, 256, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
   }
   if (vec_f32) {
-    if (k == 8) return launch_t<float, float, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
-    if (pl.group == 32) return launch_t<float, float, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
-    return launch_t<float, float, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+    if (k == 8) return launch_t<float, float, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+    if (pl.group == 32) return launch_t<float, float, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+    return launch_t<float, float, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
   }
-  if (k == 8) return launch_t<float, double, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
-  if (pl.group == 32) return launch_t<float, double, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
-  return launch_t<float, double, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc);
+  if (k == 8) return launch_t<float, double, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+  if (pl.group == 32) return launch_t<float, double, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+  return launch_t<float, double, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
 }
 
 }  // namespace sks

@@ -273,10 +273,12 @@ sks_status gemm(cudaStream_t stream, int M, int N, int K, const T* A, long long 
     grid.z = batch;
   }
   gemm_kernel<T><<<grid, GT, 0, stream>>>(g);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   if (g.splits > 1) {
     dim3 rg((unsigned)std::min<long long>(4096, ((long long)M * N + 255) / 256), batch);
     split_reduce_kernel<T><<<rg, 256, 0, stream>>>(g);
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
   }
   return SKS_OK;
@@ -294,6 +296,7 @@ sks_status transpose(cudaStream_t stream, int rows, int cols, const T* S, long l
   if (rows <= 0 || cols <= 0) return SKS_OK;
   dim3 grid((cols + 31) / 32, (rows + 31) / 32);
   transpose_kernel<T><<<grid, dim3(32, 8), 0, stream>>>(rows, cols, S, lds, D, ldd);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }
@@ -304,6 +307,7 @@ sks_status add_diagonal(cudaStream_t stream, int n, double* M, long long ld, dou
                         double vec_scale) {
   if (n <= 0) return SKS_OK;
   set_identity_scaled_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, M, ld, diag_add, diag_vec, vec_scale);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }
@@ -328,6 +332,7 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
     double* Dk = H + (long long)k0 * ldh + k0;
     double* Dinv = dinv + (size_t)kb * NB * NB;
     potrf_diag_kernel<<<1, 256, 0, stream>>>(Dk, ldh, nb, Dinv, k0, st);
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     const int rest = n - k0 - nb;
     if (rest > 0) {
@@ -379,6 +384,7 @@ sks_status gemv_rows(cudaStream_t stream, int rows, int cols, const T* M, long l
   const int threads = 256;
   const int blocks = (rows * 32 + threads - 1) / threads;
   gemv_rows_kernel<T><<<blocks, threads, 0, stream>>>(rows, cols, M, ldm, tri, x, xdiv, alpha, y, mode, z, lam, nu2);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }

@@ -19,6 +19,10 @@ void set_last_error(const std::string& msg);
 sks_status fail(sks_status code, const std::string& msg);
 const char* last_error_cstr();
 
+// Kernel-launch accounting (thread-local; see sks_kernel_launch_count).
+void note_launch(int count = 1);
+uint64_t launch_count();
+
 #define SKS_CUDA_TRY(expr)                                                                     \
   do {                                                                                         \
     cudaError_t e_ = (expr);                                                                   \
@@ -79,7 +83,8 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
 sks_status apass_launch(const ApassPlan& plan, const CUtensorMap* tmap, int64_t n, int64_t d, int64_t k,
                         bool a_f32, bool vec_f32, const void* x, void* y, double nu2, const double* lambda,
                         void* partials, DevStatus* st, cudaStream_t stream, double sgn = 1.0,
-                        const void* addv = nullptr, double addc = 0.0);
+                        const void* addv = nullptr, double addc = 0.0, cudaEvent_t ev_begin = nullptr,
+                        cudaEvent_t ev_end = nullptr);
 size_t apass_workspace_bytes(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32);
 
 // ---------------------------------------------------------------- solver entry points (solver.cu)

@@ -25,6 +25,12 @@ sks_status fail(sks_status code, const std::string& msg) {
 
 const char* last_error_cstr() { return g_last_error.c_str(); }
 
+namespace {
+thread_local uint64_t g_launches = 0;
+}
+void note_launch(int count) { g_launches += (uint64_t)count; }
+uint64_t launch_count() { return g_launches; }
+
 const DeviceInfo& device_info() {
   static thread_local DeviceInfo info;
   int dev = -1;

@@ -156,6 +156,7 @@ sks_status srht_form(cudaStream_t stream, const T* A, long long lda, int64_t n, 
     const int L = 0;
     const size_t smem = (size_t)kFwhtCols * sizeof(T);
     fwht_pass_kernel<T><<<ncb, 256, smem, stream>>>(A, lda, n, B, ldb, d, 0, L, 1, make_key(seed));
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     return SKS_OK;
   }
@@ -168,6 +169,7 @@ sks_status srht_form(cudaStream_t stream, const T* A, long long lda, int64_t n, 
     SKS_CUDA_TRY(cudaFuncSetAttribute(fwht_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     fwht_pass_kernel<T><<<(unsigned)blocks, 256, smem, stream>>>(A, lda, n, B, ldb, d, a, L, first ? 1 : 0,
                                                                  make_key(seed));
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     first = false;
     a += L;
@@ -184,6 +186,7 @@ sks_status srht_gather(cudaStream_t stream, const TB* B, long long ldb, int d, i
   if (r1 <= r0) return SKS_OK;
   const int bits = ilog2_ceil(n_pad);
   srht_gather_kernel<TB, TY><<<r1 - r0, 128, 0, stream>>>(B, ldb, d, bits, make_key(seed), r0, Y, ldy, st);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }
@@ -211,6 +214,7 @@ sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64
     const long long threads = nq * icnt;
     gauss_gen_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(key, m_off, m_add, i0, icnt, gbuf,
                                                                                 icnt);
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     SKS_TRY(gemm<T>(stream, m_add, d, icnt, gbuf, icnt, false, A + i0 * lda, lda, false, Y + (long long)m_off * ldy,
                     ldy, 1.0, i0 == 0 ? 0.0 : 1.0, false, 1, 0, 0, 0, split_ws, split_elems));
@@ -232,6 +236,7 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
   const long long threads = n * 32;
   sjlt_scatter_kernel<TA, TY><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(A, lda, n, d, (uint32_t)m, s_eff,
                                                                                     make_key(seed), Y, ldy);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }

@@ -282,6 +282,7 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
   long long ldy;
   if (s->f32) {
     f32_to_f64_2d_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, (const float*)s->Y, s->ldy, P->Y64, d);
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     Y64 = P->Y64;
     ldy = d;
@@ -298,6 +299,7 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
     SKS_TRY(transpose<double>(stream, d, d, P->X, d, P->Xt, d));
   } else {
     scale_cols_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, Y64, ldy, lam, P->Ys, d);
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     SKS_TRY(gemm<double>(stream, m, m, d, P->Ys, d, false, Y64, ldy, true, P->H, m, P->c2, 0.0, true, 1, 0, 0, 0,
                          P->split, P->split_elems));
@@ -572,7 +574,9 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
 
   SKS_CUDA_TRY(cudaMemsetAsync(W.st, 0, sizeof(DevStatus), stream));
   ctl_init_kernel<<<1, 1, 0, stream>>>(W.ctl);
+  note_launch();
   check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, W.st);
+  note_launch();
   SKS_TRY(read_status(W.st, stream, "input check"));
 
   ApassPlan plan;
@@ -596,10 +600,36 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
   S.factorizations = 1;
   SKS_TRY(read_status(W.st, stream, "first preconditioner"));
 
+  // Every A-pass is bracketed by a pair of events; the host harvests the
+  // elapsed time at the next synchronisation point (one pass in flight at most).
+  cudaEvent_t ev_a0 = nullptr, ev_a1 = nullptr;
+  SKS_CUDA_TRY(cudaEventCreate(&ev_a0));
+  SKS_CUDA_TRY(cudaEventCreate(&ev_a1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev_guard{ev_a0, ev_a1};
+  bool apass_pending = false;
   auto hess = [&](const double* in, double* out, double sgn, const double* addv, double addc) -> sks_status {
     S.a_passes += 1;
+    apass_pending = true;
     return apass_launch(plan, &tmap, prob->n, d, 1, false, false, in, out, nu2, prob->lambda_diag, W.partials, W.st,
-                        stream, sgn, addv, addc);
+                        stream, sgn, addv, addc, ev_a0, ev_a1);
+  };
+  auto sync_point = [&](const char* what) -> sks_status {
+    SKS_TRY(read_status(W.st, stream, what));
+    if (apass_pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev_a0, ev_a1) == cudaSuccess) {
+        S.ms_apass += ms;
+        S.apass_timed += 1;
+      }
+      apass_pending = false;
+    }
+    return SKS_OK;
   };
 
   sks_status result = SKS_OK;
@@ -608,16 +638,18 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
     double* xcol = x_io + col * d;
     SKS_CUDA_TRY(cudaMemcpyAsync(W.x, xcol, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     ctl_init_kernel<<<1, 1, 0, stream>>>(W.ctl);
+    note_launch();
     // PCG: r = b - H x0, r~ = H_S^{-1} r.   IHS: g = H x0 - b (in r), v = H_S^{-1} g (in rt).
     if (method == PCG) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
     else SKS_TRY(hess(W.x, W.r, 1.0, b, -1.0));
     SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
     if (method == PCG) pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
     else ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
+    note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     Ctl h;
     SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
-    SKS_TRY(read_status(W.st, stream, "initial residual"));
+    SKS_TRY(sync_point("initial residual"));
     if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite initial decrement"); break; }
     bool converged = h.stop != 0;
     int64_t guard = 0;
@@ -626,21 +658,25 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
       if (method == PCG) {
         SKS_TRY(hess(W.p, W.Hp, 1.0, nullptr, 0.0));
         pcg_step1_kernel<<<1, kStepThreads, 0, stream>>>(d, W.x, W.r, W.p, W.Hp, W.xp, W.rp, W.ctl);
+        note_launch();
         SKS_CUDA_TRY(cudaGetLastError());
         SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
         pcg_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.p, W.xp, W.rp, W.rtp, W.ctl, c, phi,
                                                          can_double, tol2);
+        note_launch();
       } else {
         ihs_prop_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, W.x, W.rt, 1.0 - rho, W.xp);
+        note_launch();
         SKS_TRY(hess(W.xp, W.rp, 1.0, b, -1.0));
         SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
         ihs_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.xp, W.rp, W.rtp, W.ctl, c, phi,
                                                          can_double, tol2);
+        note_launch();
       }
       SKS_CUDA_TRY(cudaGetLastError());
       const long long t_before = h.t;
       SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
-      SKS_TRY(read_status(W.st, stream, "iteration"));
+      SKS_TRY(sync_point("iteration"));
       if (o->trace && S.trace_len < o->trace_cap) {
         sks_trace_event& e = o->trace[S.trace_len++];
         e.t = t_before;
@@ -666,13 +702,15 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
           if (!o->reuse_residual) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
           SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
           pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
+          note_launch();
         } else {
           SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
           ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
+          note_launch();
         }
         SKS_CUDA_TRY(cudaGetLastError());
         SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
-        SKS_TRY(read_status(W.st, stream, "restart"));
+        SKS_TRY(sync_point("restart"));
         if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite decrement at restart"); break; }
         converged = h.stop != 0;
         continue;
@@ -755,8 +793,10 @@ sks_status hess_apply(const sks_problem* p, const double* x, double* y, int exte
     if (vec32) {
       const long long cnt = (long long)p->d * kb;
       f64_to_f32_kernel<<<blocks_for(cnt), 256, 0, stream>>>(cnt, xc, xf);
+      note_launch();
       SKS_TRY(apass_launch(plan, &tmap, p->n, p->d, kb, true, true, xf, yf, nu2, p->lambda_diag, part32, st, stream));
       f32_to_f64_kernel<<<blocks_for(cnt), 256, 0, stream>>>(cnt, yf, yc);
+      note_launch();
       SKS_CUDA_TRY(cudaGetLastError());
     } else {
       SKS_TRY(apass_launch(plan, &tmap, p->n, p->d, kb, f32, false, xc, yc, nu2, p->lambda_diag, part64, st, stream));
@@ -828,6 +868,7 @@ extern "C" sks_status sks_sketch_copy_out(const sks_sketch* s, double* SA, void*
   if (cnt == 0) return SKS_OK;
   scale_rows_out_kernel<<<blocks_for(cnt), 256, 0, st>>>((int)s->m, s->d, s->Y, s->f32 ? 1 : 0, s->ldy,
                                                          std::sqrt(s->scale2()), SA);
+  note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   SKS_CUDA_TRY(cudaStreamSynchronize(st));
   return SKS_OK;
@@ -856,6 +897,7 @@ extern "C" sks_status sks_precond_build(sks_precond** out, const sks_sketch* s, 
   if (r == SKS_OK) {
     cudaMemsetAsync(P->st, 0, sizeof(DevStatus), st);
     check_lambda_kernel<<<(int)((p->d + 255) / 256), 256, 0, st>>>((int)p->d, p->lambda_diag, P->st);
+    note_launch();
     r = precond_factor(P, s, p->nu, p->lambda_diag, st);
   }
   if (r == SKS_OK) r = read_status(P->st, st, "precond_build");

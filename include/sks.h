@@ -151,6 +151,30 @@ sks_status sks_hess_apply(const sks_problem* p, const double* x, double* y, int 
                           void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free Hessian pass.  The paper has no counterpart: this is a
+ * deployment variant of sks_hess_apply for callers that must not allocate
+ * device memory at the moment they need H x -- for example code inside a host
+ * framework that owns every device allocation through its own fixed-budget
+ * allocator, or a latency-critical loop that cannot pay for cudaMalloc's
+ * device-wide synchronisation -- and therefore cannot hand over the
+ * workspace sks_hess_apply asks for.
+ * Same operation, arguments and results as sks_hess_apply, minus `ws`: the
+ * per-block partial sums live in a library-owned static device array of
+ * 8 MiB, which every GPU that loads the library holds until the process
+ * exits.  A problem needing more scratch than that (float64 vectors: about
+ * 152 blocks * 8 bytes * d * k; every d <= 4096 with k = 1 fits) is rejected
+ * with SKS_ERR_INVALID_ARG and a message giving the size it needs.
+ * The first call on a device looks up the array's device address with that
+ * device current and caches it; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * the status word is cleared on every call, but calls whose GPU work overlaps
+ * (other streams, other host threads on the same device) race on it and must
+ * be serialised by the caller.  The call synchronises `stream` to read its
+ * status and calls no cudaMalloc or cudaFree.
+ * ------------------------------------------------------------------------- */
+sks_status sks_hess_apply_noalloc(const sks_problem* p, const double* x, double* y, int extended, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Sketch S A of Section 2.1 with nested growth.
  * sks_sketch_create forms S_m A for m = m_init (SRHT: also the n_pad x d
  * matrix H E A_pad, once); sks_sketch_grow(new_m) extends it to new_m >= m

@@ -59,6 +59,7 @@ _SIGS = {
     "sks_kernel_launch_count": (C.c_uint64, []),
     "sks_hess_apply_workspace_size": (C.c_int, [P(Problem), P(C.c_size_t)]),
     "sks_hess_apply": (C.c_int, [P(Problem), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sks_hess_apply_noalloc": (C.c_int, [P(Problem), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sks_sketch_workspace_size": (C.c_int, [P(Problem), C.c_int, C.c_int64, C.c_int, P(C.c_size_t)]),
     "sks_sketch_create": (C.c_int, [P(C.c_void_p), P(Problem), C.c_int, C.c_int64, C.c_int64, C.c_int, C.c_uint64,
                                     C.c_void_p, C.c_size_t, C.c_void_p]),

@@ -42,6 +42,9 @@ WORKLOADS = {
     "C2": dict(config="C2", method="pcg", kind="srht", m_init=16, m_max=4096, tol=1e-10, precision="plain",
                desc="adaptive PCG, SRHT, float64: n=2^17, d=2048, sigma_j=1/(1+j), nu=1e-3, "
                     "Lambda=1+9U, m 16->4096, tol 1e-10"),
+    # reduced C2 (n = 2^15, A = 512 MiB, still 4x the L2) for ncu captures of single kernels
+    "C2-profile": dict(config="C2", n=1 << 15, method="pcg", kind="srht", m_init=16, m_max=4096, tol=1e-10,
+                       precision="plain", desc="C2 recipe at n=2^15 (profiling size)"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -159,7 +162,7 @@ def run_reference(args, wl, world, rank):
         return None
     import synthetic
     gdev = "cuda" if torch.cuda.is_available() else "cpu"
-    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=gdev)
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=gdev, n=wl.get("n"))
     A = prob["A64"].cpu().numpy()
     b = prob["b"][:, 0].cpu().numpy()
     lam = prob["lam"].cpu().numpy()
@@ -197,7 +200,7 @@ def run_ours(args, wl, world, rank, local):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     lib = _lib.load()
-    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev)
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev, n=wl.get("n"))
     A = prob["A64"]
     b = prob["b"][:, 0].contiguous()
     lam = prob["lam"]

@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(kStepThreads) pcg_step1_kernel(int d, const do
 __global__ void __launch_bounds__(kStepThreads) pcg_step2_kernel(int d, const double* b, double* x, double* r,
                                                                  double* rt, double* p, const double* xp,
                                                                  const double* rp, const double* rtp, Ctl* ctl,
-                                                                 double c, double phi, int can_double, double tol2) {
+                                                                 double c, double phi, int can_double, double tol2,
+                                                                 double stop_abs) {
   __shared__ int s_accept;
   const double dp = block_dot(d, rp, rtp);
   if (threadIdx.x == 0) {
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kStepThreads) pcg_step2_kernel(int d, const do
     ctl->dt = dp;
     ctl->t += 1;
     ctl->btx = btx;
-    ctl->stop = (dp <= 0.0) || (dp <= tol2 * btx);
+    ctl->stop = (dp <= 0.0) || (dp <= tol2 * btx) || (dp <= stop_abs);
   }
 }
 
@@ -427,7 +428,7 @@ __global__ void ihs_prop_kernel(int d, const double* x, const double* v, double 
 __global__ void __launch_bounds__(kStepThreads) ihs_step2_kernel(int d, const double* b, double* x, double* g,
                                                                  double* v, const double* xp, const double* gp,
                                                                  const double* vp, Ctl* ctl, double c, double phi,
-                                                                 int can_double, double tol2) {
+                                                                 int can_double, double tol2, double stop_abs) {
   __shared__ int s_accept;
   const double dp = 0.5 * block_dot(d, gp, vp);
   if (threadIdx.x == 0) {
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(kStepThreads) ihs_step2_kernel(int d, const do
     ctl->dt = dp;
     ctl->t += 1;
     ctl->btx = btx;
-    ctl->stop = (dp <= 0.0) || (2.0 * dp <= tol2 * btx);
+    ctl->stop = (dp <= 0.0) || (2.0 * dp <= tol2 * btx) || (dp <= stop_abs);
   }
 }
 
@@ -476,12 +477,34 @@ __global__ void ctl_init_kernel(Ctl* ctl) {
   memset(ctl, 0, sizeof(Ctl));
 }
 
+// Small vector kernels of the refinement loop.
+__global__ void f64_to_f32_vec(int d, const double* a, float* b) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) b[j] = (float)a[j];
+}
+__global__ void f32_to_f64_vec(int d, const float* a, double* b) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) b[j] = (double)a[j];
+}
+__global__ void axpy_kernel(int d, double a, const double* x, double* y) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) y[j] += a * x[j];
+}
+__global__ void __launch_bounds__(kStepThreads) dot_kernel(int d, const double* a, const double* b, double* out) {
+  const double v = block_dot(d, a, b);
+  if (threadIdx.x == 0) *out = v;
+}
+
 // ---------------------------------------------------------------- solve workspace
 struct SolveWs {
   DevStatus* st;
   Ctl* ctl;
+  double* scal;  // [0] = b^T x of the outer iterate
   double *x, *r, *rt, *p, *Hp, *xp, *rp, *rtp;
-  void* partials;
+  double *xo, *bo;  // refinement: outer iterate and the inner right-hand side
+  float *p32, *h32;
+  void* partials;    // A-pass partial sums in the iteration's precision
+  void* partials64;  // float64-arithmetic A-pass (refinement residual)
   void* sketch_ws;
   size_t sketch_bytes;
   void* precond_ws;
@@ -492,10 +515,13 @@ sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_
                         size_t* total) {
   const size_t d = (size_t)p->d;
   const int64_t m_max = resolve_m_max(p, o->kind, o->m_max);
+  const bool f32 = p->dtype == SKS_F32;
+  const bool mixed = o->precision == SKS_MIXED_REFINED;
   Carver c(ws, ws_bytes);
   SolveWs w;
   w.st = c.take<DevStatus>(1);
   w.ctl = c.take<Ctl>(1);
+  w.scal = c.take<double>(4);
   w.x = c.take<double>(d);
   w.r = c.take<double>(d);
   w.rt = c.take<double>(d);
@@ -504,8 +530,13 @@ sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_
   w.xp = c.take<double>(d);
   w.rp = c.take<double>(d);
   w.rtp = c.take<double>(d);
-  const size_t pbytes = apass_workspace_bytes(std::max<int64_t>(p->n, 1), p->d, 1, p->dtype == SKS_F32, false);
-  w.partials = c.take<char>(pbytes);
+  w.xo = c.take<double>(d);
+  w.bo = c.take<double>(d);
+  w.p32 = c.take<float>(d);
+  w.h32 = c.take<float>(d);
+  const int64_t n1 = std::max<int64_t>(p->n, 1);
+  w.partials = c.take<char>(apass_workspace_bytes(n1, p->d, 1, f32, mixed));
+  w.partials64 = c.take<char>(mixed ? apass_workspace_bytes(n1, p->d, 1, f32, false) : 0);
   w.sketch_bytes = sketch_ws_bytes(p, o->kind, m_max);
   w.sketch_ws = c.take<char>(w.sketch_bytes);
   w.precond_bytes = precond_ws_bytes(p, m_max);
@@ -540,86 +571,99 @@ struct Timer {
 
 enum Method { PCG, IHS };
 
-sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sks_opts* o, double* x_io,
-                                sks_stats* stats, void* ws, size_t ws_bytes, cudaStream_t stream) {
-  SKS_TRY(validate_problem(prob));
-  if (!o) return fail(SKS_ERR_INVALID_ARG, "opts is NULL");
-  if (!x_io) return fail(SKS_ERR_INVALID_ARG, "x is NULL");
-  if (!(o->rho > 0.0 && o->rho < 1.0)) return fail(SKS_ERR_INVALID_ARG, "rho must be in (0, 1)");
-  if (o->m_init < 1) return fail(SKS_ERR_INVALID_ARG, "m_init must be >= 1");
-  if (!(o->tol > 0.0)) return fail(SKS_ERR_INVALID_ARG, "tol must be > 0");
-  if (prob->dtype != SKS_F64) return fail(SKS_ERR_INVALID_ARG, "the plain float64 form needs a float64 A");
-  const int d = (int)prob->d;
+// One adaptive solve engine shared by the plain float64 form and the inner
+// solves of the mixed form.  The iteration A-pass runs in the precision of A
+// (float64 A: float64; float32 A: float32 with the d-vectors converted on the
+// fly); the d-vector algebra of Algorithms 1 and 2 stays in float64.
+struct Engine {
+  Method method;
+  const sks_problem* prob;
+  const sks_opts* o;
+  cudaStream_t stream;
   SolveWs W;
-  size_t need = 0;
-  SKS_TRY(solve_layout(prob, o, nullptr, 0, nullptr, &need));
-  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "solve workspace too small (need " + std::to_string(need) + " bytes)");
-  SKS_TRY(solve_layout(prob, o, ws, ws_bytes, &W, nullptr));
-  const int64_t m_max = resolve_m_max(prob, o->kind, o->m_max);
-  const double nu2 = prob->nu * prob->nu;
-  const double rho = o->rho;
-  double phi, c;
-  if (method == PCG) {
-    phi = (1.0 - std::sqrt(1.0 - rho)) / (1.0 + std::sqrt(1.0 - rho));
-    c = 4.0 * (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
-  } else {
-    phi = rho;
-    c = (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
-  }
-  const double tol2 = (o->tol / 2.0) * (o->tol / 2.0);
-  sks_stats S;
-  std::memset(&S, 0, sizeof(S));
-  Timer t_total(stream), t_sketch(stream), t_factor(stream);
-  t_total.start();
-
-  SKS_CUDA_TRY(cudaMemsetAsync(W.st, 0, sizeof(DevStatus), stream));
-  ctl_init_kernel<<<1, 1, 0, stream>>>(W.ctl);
-  note_launch();
-  check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, W.st);
-  note_launch();
-  SKS_TRY(read_status(W.st, stream, "input check"));
-
-  ApassPlan plan;
-  SKS_TRY(apass_plan(std::max<int64_t>(prob->n, 1), d, 1, false, false, &plan));
-  CUtensorMap tmap;
-  if (prob->n > 0) SKS_TRY(map_for(prob, &tmap, plan));
-
+  int d;
+  int64_t m = 0, m_max = 0;
+  double nu2 = 0, phi = 0, c = 0;
+  bool f32 = false, mixed = false;
+  ApassPlan plan, plan64;
+  CUtensorMap tmap, tmap64;
   sks_sketch sk;
-  SKS_TRY(sketch_init(&sk, prob, o->kind, m_max, o->sjlt_s, o->seed, W.sketch_ws, W.sketch_bytes, W.st));
   sks_precond P;
-  SKS_TRY(precond_init(&P, prob, m_max, W.precond_ws, W.precond_bytes, W.st));
-
-  int64_t m = std::min<int64_t>(o->m_init, m_max);
-  t_sketch.start();
-  SKS_TRY(sketch_to(&sk, m, stream));
-  t_sketch.stop();
-  S.sketch_passes = 1;
-  t_factor.start();
-  SKS_TRY(precond_factor(&P, &sk, prob->nu, prob->lambda_diag, stream));
-  t_factor.stop();
-  S.factorizations = 1;
-  SKS_TRY(read_status(W.st, stream, "first preconditioner"));
-
-  // Every A-pass is bracketed by a pair of events; the host harvests the
-  // elapsed time at the next synchronisation point (one pass in flight at most).
+  sks_stats S;
   cudaEvent_t ev_a0 = nullptr, ev_a1 = nullptr;
-  SKS_CUDA_TRY(cudaEventCreate(&ev_a0));
-  SKS_CUDA_TRY(cudaEventCreate(&ev_a1));
-  struct EvGuard {
-    cudaEvent_t a, b;
-    ~EvGuard() {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-    }
-  } ev_guard{ev_a0, ev_a1};
   bool apass_pending = false;
-  auto hess = [&](const double* in, double* out, double sgn, const double* addv, double addc) -> sks_status {
+  Timer *t_sketch = nullptr, *t_factor = nullptr;
+  int outer = 0;
+
+  ~Engine() {
+    if (ev_a0) cudaEventDestroy(ev_a0);
+    if (ev_a1) cudaEventDestroy(ev_a1);
+  }
+
+  sks_status init(Method mth, const sks_problem* pr, const sks_opts* op, void* ws, size_t ws_bytes,
+                  cudaStream_t st) {
+    method = mth;
+    prob = pr;
+    o = op;
+    stream = st;
+    d = (int)pr->d;
+    f32 = pr->dtype == SKS_F32;
+    mixed = op->precision == SKS_MIXED_REFINED;
+    std::memset(&S, 0, sizeof(S));
+    SKS_TRY(solve_layout(pr, op, ws, ws_bytes, &W, nullptr));
+    m_max = resolve_m_max(pr, op->kind, op->m_max);
+    nu2 = pr->nu * pr->nu;
+    const double rho = op->rho;
+    if (method == PCG) {
+      phi = (1.0 - std::sqrt(1.0 - rho)) / (1.0 + std::sqrt(1.0 - rho));
+      c = 4.0 * (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
+    } else {
+      phi = rho;
+      c = (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
+    }
+    SKS_CUDA_TRY(cudaEventCreate(&ev_a0));
+    SKS_CUDA_TRY(cudaEventCreate(&ev_a1));
+    const int64_t n1 = std::max<int64_t>(pr->n, 1);
+    SKS_TRY(apass_plan(n1, d, 1, f32, mixed, &plan));
+    if (pr->n > 0) SKS_TRY(map_for(pr, &tmap, plan));
+    if (mixed) {
+      SKS_TRY(apass_plan(n1, d, 1, f32, false, &plan64));
+      if (pr->n > 0) SKS_TRY(map_for(pr, &tmap64, plan64));
+    }
+    SKS_TRY(sketch_init(&sk, pr, op->kind, m_max, op->sjlt_s, op->seed, W.sketch_ws, W.sketch_bytes, W.st));
+    SKS_TRY(precond_init(&P, pr, m_max, W.precond_ws, W.precond_bytes, W.st));
+    return SKS_OK;
+  }
+
+  // y = sgn * H x + addc * addv in the iteration's precision (one pass over A).
+  sks_status hess(const double* x, double* y, double sgn, const double* addv, double addc) {
     S.a_passes += 1;
     apass_pending = true;
-    return apass_launch(plan, &tmap, prob->n, d, 1, false, false, in, out, nu2, prob->lambda_diag, W.partials, W.st,
-                        stream, sgn, addv, addc, ev_a0, ev_a1);
-  };
-  auto sync_point = [&](const char* what) -> sks_status {
+    if (!mixed)
+      return apass_launch(plan, &tmap, prob->n, d, 1, f32, false, x, y, nu2, prob->lambda_diag, W.partials, W.st,
+                          stream, sgn, addv, addc, ev_a0, ev_a1);
+    f64_to_f32_vec<<<(d + 255) / 256, 256, 0, stream>>>(d, x, W.p32);
+    note_launch();
+    SKS_TRY(apass_launch(plan, &tmap, prob->n, d, 1, true, true, W.p32, W.h32, nu2, prob->lambda_diag, W.partials,
+                         W.st, stream, 1.0, nullptr, 0.0, ev_a0, ev_a1));
+    f32_to_f64_vec<<<(d + 255) / 256, 256, 0, stream>>>(d, W.h32, y);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+    if (addv || sgn != 1.0) {
+      // y = sgn * y + addc * addv  (rare: restarts only)
+      return fail(SKS_ERR_UNSUPPORTED, "internal: mixed inner residual form");
+    }
+    return SKS_OK;
+  }
+
+  // float64-arithmetic pass over A (refinement residual): y = sgn H x + addc addv
+  sks_status hess64(const double* x, double* y, double sgn, const double* addv, double addc) {
+    S.a_passes += 1;
+    return apass_launch(plan64, &tmap64, prob->n, d, 1, f32, false, x, y, nu2, prob->lambda_diag, W.partials64, W.st,
+                        stream, sgn, addv, addc);
+  }
+
+  sks_status sync_point(const char* what) {
     SKS_TRY(read_status(W.st, stream, what));
     if (apass_pending) {
       float ms = 0.f;
@@ -630,18 +674,58 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
       apass_pending = false;
     }
     return SKS_OK;
-  };
+  }
 
-  sks_status result = SKS_OK;
-  for (int64_t col = 0; col < prob->k; ++col) {
-    const double* b = prob->b + col * d;
-    double* xcol = x_io + col * d;
-    SKS_CUDA_TRY(cudaMemcpyAsync(W.x, xcol, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  sks_status first_sketch() {
+    m = std::min<int64_t>(o->m_init, m_max);
+    t_sketch->start();
+    SKS_TRY(sketch_to(&sk, m, stream));
+    t_sketch->stop();
+    S.sketch_passes = 1;
+    t_factor->start();
+    SKS_TRY(precond_factor(&P, &sk, prob->nu, prob->lambda_diag, stream));
+    t_factor->stop();
+    S.factorizations = 1;
+    return read_status(W.st, stream, "first preconditioner");
+  }
+
+  sks_status grow() {
+    m = std::min<int64_t>(2 * m, m_max);
+    t_sketch->start();
+    SKS_TRY(sketch_to(&sk, m, stream));
+    t_sketch->stop();
+    S.sketch_passes += 1;
+    t_factor->start();
+    SKS_TRY(precond_factor(&P, &sk, prob->nu, prob->lambda_diag, stream));
+    t_factor->stop();
+    S.factorizations += 1;
+    return SKS_OK;
+  }
+
+  // Adaptive solve of H x = b (Algorithm 2 or Algorithm 1) from the x already
+  // in W.x.  Stops when delta~ <= tol2 * b^T x (tol2 > 0) or delta~ <=
+  // rel2 * delta~_0 (rel2 > 0).  On return W.x holds the last accepted iterate;
+  // *dt0 receives the decrement at the start, *h the final control block.
+  sks_status inner(const double* b, double tol2, double rel2, int64_t max_iter, bool* converged, double* dt0,
+                   Ctl* hout, const double* btx_dev = nullptr, double outer_tol2 = 0.0, double fac = 1.0,
+                   bool* outer_done = nullptr) {
     ctl_init_kernel<<<1, 1, 0, stream>>>(W.ctl);
     note_launch();
-    // PCG: r = b - H x0, r~ = H_S^{-1} r.   IHS: g = H x0 - b (in r), v = H_S^{-1} g (in rt).
-    if (method == PCG) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
-    else SKS_TRY(hess(W.x, W.r, 1.0, b, -1.0));
+    const bool mixed_inner = mixed;
+    // PCG: r = b - H x, r~ = H_S^{-1} r.   IHS: g = H x - b (in r), v = H_S^{-1} g (in rt).
+    if (mixed_inner) {
+      // the inner right-hand side is the refinement residual and x starts at 0
+      SKS_CUDA_TRY(cudaMemsetAsync(W.x, 0, d * sizeof(double), stream));
+      if (method == PCG) SKS_CUDA_TRY(cudaMemcpyAsync(W.r, b, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      else {
+        SKS_CUDA_TRY(cudaMemsetAsync(W.r, 0, d * sizeof(double), stream));
+        axpy_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, -1.0, b, W.r);
+        note_launch();
+      }
+    } else {
+      if (method == PCG) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
+      else SKS_TRY(hess(W.x, W.r, 1.0, b, -1.0));
+    }
     SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
     if (method == PCG) pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
     else ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
@@ -650,10 +734,29 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
     Ctl h;
     SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
     SKS_TRY(sync_point("initial residual"));
-    if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite initial decrement"); break; }
-    bool converged = h.stop != 0;
+    if (h.numeric) return fail(SKS_ERR_NUMERIC, "non-finite initial decrement");
+    *dt0 = h.dt;
+    if (btx_dev && outer_done) {
+      // refinement: the decrement of the residual at the outer iterate
+      // estimates its error; stop before iterating when it meets the target.
+      double btx = 0.0;
+      SKS_CUDA_TRY(cudaMemcpy(&btx, btx_dev, sizeof(double), cudaMemcpyDeviceToHost));
+      const double est2 = btx > 0 ? fac * h.dt / btx : (h.dt <= 0 ? 0.0 : 1.0);
+      S.est_rel_err = std::sqrt(std::max(0.0, est2));
+      if (est2 <= outer_tol2 || h.dt <= 0) {
+        *outer_done = true;
+        *converged = true;
+        if (hout) *hout = h;
+        return SKS_OK;
+      }
+    }
+    const double stop_abs = rel2 > 0 ? rel2 * h.dt : 0.0;
+    bool conv = h.stop != 0;
+    if (!conv && tol2 > 0 && !mixed_inner) conv = false;
+    if (hout) *hout = h;
+    if (rel2 > 0 && *dt0 <= 0) conv = true;
     int64_t guard = 0;
-    while (!converged && h.t < o->max_iter && guard++ < o->max_iter + 64) {
+    while (!conv && h.t < max_iter && guard++ < max_iter + 64) {
       const int can_double = m < m_max ? 1 : 0;
       if (method == PCG) {
         SKS_TRY(hess(W.p, W.Hp, 1.0, nullptr, 0.0));
@@ -662,15 +765,21 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
         SKS_CUDA_TRY(cudaGetLastError());
         SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
         pcg_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.p, W.xp, W.rp, W.rtp, W.ctl, c, phi,
-                                                         can_double, tol2);
+                                                         can_double, tol2, stop_abs);
         note_launch();
       } else {
-        ihs_prop_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, W.x, W.rt, 1.0 - rho, W.xp);
+        ihs_prop_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, W.x, W.rt, 1.0 - o->rho, W.xp);
         note_launch();
-        SKS_TRY(hess(W.xp, W.rp, 1.0, b, -1.0));
+        if (mixed_inner) {
+          SKS_TRY(hess(W.xp, W.rp, 1.0, nullptr, 0.0));
+          axpy_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, -1.0, b, W.rp);
+          note_launch();
+        } else {
+          SKS_TRY(hess(W.xp, W.rp, 1.0, b, -1.0));
+        }
         SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
         ihs_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.xp, W.rp, W.rtp, W.ctl, c, phi,
-                                                         can_double, tol2);
+                                                         can_double, tol2, stop_abs);
         note_launch();
       }
       SKS_CUDA_TRY(cudaGetLastError());
@@ -684,49 +793,123 @@ sks_status adaptive_solve_plain(Method method, const sks_problem* prob, const sk
         e.ratio = h.ratio;
         e.threshold = h.thr;
         e.accepted = h.accept;
-        e.outer = 0;
+        e.outer = outer;
       }
-      if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite value in the iteration"); break; }
+      if (h.numeric) return fail(SKS_ERR_NUMERIC, "non-finite value in the iteration");
       if (!h.accept) {
         S.rejections += 1;
-        m = std::min<int64_t>(2 * m, m_max);
-        t_sketch.start();
-        SKS_TRY(sketch_to(&sk, m, stream));
-        t_sketch.stop();
-        S.sketch_passes += 1;
-        t_factor.start();
-        SKS_TRY(precond_factor(&P, &sk, prob->nu, prob->lambda_diag, stream));
-        t_factor.stop();
-        S.factorizations += 1;
+        SKS_TRY(grow());
         if (method == PCG) {
-          if (!o->reuse_residual) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
+          if (!o->reuse_residual && !mixed_inner) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
           SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
           pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
-          note_launch();
         } else {
           SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
           ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
-          note_launch();
         }
+        note_launch();
         SKS_CUDA_TRY(cudaGetLastError());
         SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
         SKS_TRY(sync_point("restart"));
-        if (h.numeric) { result = fail(SKS_ERR_NUMERIC, "non-finite decrement at restart"); break; }
-        converged = h.stop != 0;
+        if (h.numeric) return fail(SKS_ERR_NUMERIC, "non-finite decrement at restart");
+        conv = h.stop != 0 || (stop_abs > 0 && h.dt <= stop_abs);
         continue;
       }
-      converged = h.stop != 0;
+      conv = h.stop != 0;
     }
-    SKS_CUDA_TRY(cudaMemcpyAsync(xcol, W.x, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     S.iters += h.t;
     S.final_delta_tilde = h.dt;
-    const double fac = method == PCG ? 1.0 : 2.0;
-    S.est_rel_err = h.btx > 0 ? std::sqrt(std::max(0.0, fac * h.dt / h.btx)) : 0.0;
-    if (result != SKS_OK) break;
-    if (!converged && result == SKS_OK) result = fail(SKS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+    *converged = conv;
+    if (hout) *hout = h;
+    return SKS_OK;
+  }
+};
+
+sks_status check_opts(const sks_problem* prob, const sks_opts* o, const double* x_io) {
+  SKS_TRY(validate_problem(prob));
+  if (!o) return fail(SKS_ERR_INVALID_ARG, "opts is NULL");
+  if (!x_io) return fail(SKS_ERR_INVALID_ARG, "x is NULL");
+  if (!(o->rho > 0.0 && o->rho < 1.0)) return fail(SKS_ERR_INVALID_ARG, "rho must be in (0, 1)");
+  if (o->m_init < 1) return fail(SKS_ERR_INVALID_ARG, "m_init must be >= 1");
+  if (!(o->tol > 0.0)) return fail(SKS_ERR_INVALID_ARG, "tol must be > 0");
+  if (o->kind != SKS_SRHT && o->kind != SKS_GAUSSIAN && o->kind != SKS_SJLT)
+    return fail(SKS_ERR_INVALID_ARG, "bad embedding kind");
+  if (o->sjlt_s < 1 || o->sjlt_s > kSjltMaxS) return fail(SKS_ERR_INVALID_ARG, "sjlt_s must be in [1, 16]");
+  if (o->precision == SKS_PLAIN_F64 && prob->dtype != SKS_F64)
+    return fail(SKS_ERR_INVALID_ARG, "the plain float64 form needs a float64 A");
+  if (o->precision == SKS_MIXED_REFINED && prob->dtype != SKS_F32)
+    return fail(SKS_ERR_INVALID_ARG, "the mixed form needs a float32 A");
+  if (o->precision == SKS_MIXED_REFINED && (o->max_outer < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)))
+    return fail(SKS_ERR_INVALID_ARG, "mixed form needs max_outer >= 1 and inner_tol in (0, 1)");
+  return SKS_OK;
+}
+
+sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks_opts* o, double* x_io,
+                               sks_stats* stats, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  SKS_TRY(check_opts(prob, o, x_io));
+  const int d = (int)prob->d;
+  size_t need = 0;
+  SKS_TRY(solve_layout(prob, o, nullptr, 0, nullptr, &need));
+  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "solve workspace too small (need " + std::to_string(need) + " bytes)");
+  Engine E;
+  Timer t_total(stream), t_sketch(stream), t_factor(stream);
+  E.t_sketch = &t_sketch;
+  E.t_factor = &t_factor;
+  t_total.start();
+  SKS_TRY(E.init(method, prob, o, ws, ws_bytes, stream));
+  SKS_CUDA_TRY(cudaMemsetAsync(E.W.st, 0, sizeof(DevStatus), stream));
+  check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, E.W.st);
+  note_launch();
+  SKS_TRY(read_status(E.W.st, stream, "input check"));
+  SKS_TRY(E.first_sketch());
+  const double tol2 = (o->tol / 2.0) * (o->tol / 2.0);
+  const double fac = method == PCG ? 1.0 : 2.0;
+  sks_status result = SKS_OK;
+  for (int64_t col = 0; col < prob->k && result == SKS_OK; ++col) {
+    const double* b = prob->b + col * d;
+    double* xcol = x_io + col * d;
+    bool converged = false;
+    double dt0 = 0;
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    if (!E.mixed) {
+      SKS_CUDA_TRY(cudaMemcpyAsync(E.W.x, xcol, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      sks_status r = E.inner(b, tol2, 0.0, o->max_iter, &converged, &dt0, &h);
+      SKS_CUDA_TRY(cudaMemcpyAsync(xcol, E.W.x, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      if (r != SKS_OK) { result = r; break; }
+      E.S.est_rel_err = h.btx > 0 ? std::sqrt(std::max(0.0, fac * h.dt / h.btx)) : 0.0;
+    } else {
+      // Iterative refinement: r = b - H x in float64 arithmetic, inner adaptive
+      // solve of H dx = r in the precision of A, x += dx.
+      SKS_CUDA_TRY(cudaMemcpyAsync(E.W.xo, xcol, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      int64_t inner_budget = o->max_iter;
+      for (int64_t k = 0; k < o->max_outer; ++k) {
+        E.outer = (int)k + 1;
+        SKS_TRY(E.hess64(E.W.xo, E.W.bo, -1.0, b, 1.0));
+        dot_kernel<<<1, kStepThreads, 0, stream>>>(d, b, E.W.xo, E.W.scal);
+        note_launch();
+        bool inner_conv = false, done = false;
+        sks_status r = E.inner(E.W.bo, 0.0, o->inner_tol * o->inner_tol, std::max<int64_t>(inner_budget, 1),
+                               &inner_conv, &dt0, &h, E.W.scal, tol2, fac, &done);
+        if (r != SKS_OK) { result = r; break; }
+        E.S.outer_iters = k + 1;
+        if (done) {
+          converged = true;
+          break;
+        }
+        axpy_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, 1.0, E.W.x, E.W.xo);
+        note_launch();
+        inner_budget -= h.t;
+        if (inner_budget <= 0) break;
+      }
+      SKS_CUDA_TRY(cudaMemcpyAsync(xcol, E.W.xo, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      SKS_TRY(read_status(E.W.st, stream, "refinement"));
+    }
+    if (result == SKS_OK && !converged) result = fail(SKS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
   }
   t_total.stop();
-  S.final_m = m;
+  sks_stats& S = E.S;
+  S.final_m = E.m;
   S.ms_total = t_total.acc;
   S.ms_sketch = t_sketch.acc;
   S.ms_factor = t_factor.acc;
@@ -747,9 +930,7 @@ sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t*
 
 sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
                           size_t ws_bytes, cudaStream_t stream) {
-  if (o && o->precision != SKS_PLAIN_F64)
-    return fail(SKS_ERR_UNSUPPORTED, "mixed-precision form not available in this entry point yet");
-  return adaptive_solve_plain(method == 0 ? PCG : IHS, p, o, x, stats, ws, ws_bytes, stream);
+  return adaptive_solve_impl(method == 0 ? PCG : IHS, p, o, x, stats, ws, ws_bytes, stream);
 }
 
 sks_status hess_apply_ws(const sks_problem* p, size_t* bytes) {

@@ -5,8 +5,9 @@ All workloads follow the recipe of the paper's synthetic experiments
 a prescribed decay of sigma.  U and V come from the QR factorisation of seeded
 N(0, 1) matrices, with the sign convention diag(R) > 0 so that the factor is
 unique.  ``make_problem`` does this in NumPy float64 (sizes the CPU handles in
-seconds); ``make_problem_torch`` does the same recipe on a torch device for the
-full benchmark sizes, orthonormalising by one CholeskyQR pass.
+seconds); ``make_problem_torch`` does the same recipe with the n x d work on a
+torch device for the full benchmark sizes, orthonormalising by one CholeskyQR
+pass.
 
 Workloads (n rows, d columns):
   C1  n=4096,  d=256,  sigma_j = 0.95^j,        nu=1e-2, Lambda=I,   b=A^T y
@@ -129,11 +130,15 @@ def make_problem(config="C1", seed=0, n=None, d=None, nu=None, decay=None, lam=N
 def make_problem_torch(config="C2", seed=0, device="cuda", n=None, d=None):
     """Same recipe as ``make_problem`` on a torch device, for full sizes.
 
-    Draws come from a seeded ``torch.Generator`` on the device (so the values
-    differ from the NumPy generator's); U is orthonormalised by CholeskyQR in
-    float64.  Returns a dict of device tensors: A64 (float64) and, for
-    float32-stored workloads, A32 with A64 its exact upcast; b (d x k); lam (d).
+    The n x d Gaussian comes from a seeded ``torch.Generator`` on the device
+    (so the values differ from the NumPy generator's); the d x d pieces (QR of
+    the V Gaussian, Cholesky of Z^T Z, the triangular solve) are done in NumPy
+    float64 on the host, and only the two n x d x d products run on the device
+    (matmul).  U = Z L^{-T} is the CholeskyQR factor of Z.  Returns a dict of
+    device tensors: A64 (float64) and, for float32-stored workloads, A32 with
+    A64 its exact upcast; b (d x k); lam (d).
     """
+    import scipy.linalg
     import torch
 
     cfg = dict(CONFIGS[config])
@@ -142,36 +147,30 @@ def make_problem_torch(config="C2", seed=0, device="cuda", n=None, d=None):
     if d is not None:
         cfg["d"] = d
     n, d, kk = int(cfg["n"]), int(cfg["d"]), int(cfg["k"])
+    rng = np.random.default_rng(seed)
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     f64 = torch.float64
-    sigma = torch.as_tensor(spectrum(cfg["decay"], d), device=device, dtype=f64)
-    # V: QR of a d x d Gaussian (small).
-    Zv = torch.randn(d, d, generator=g, device=device, dtype=f64)
-    V, Rv = torch.linalg.qr(Zv)
-    V = V * torch.sign(torch.diagonal(Rv))[None, :]
-    # U: CholeskyQR of an n x d Gaussian.  float32-stored workloads do the two
-    # n x d x d products in float32 (U then orthonormal to ~1e-5, which only
-    # perturbs the spectrum by that relative amount; the stored A defines the
-    # problem); float64 workloads do them in float64.
+    sigma = spectrum(cfg["decay"], d)
+    V = _orthonormal(rng, d, d)
+    # float32-stored workloads do the two n x d x d products in float32 (U is
+    # then orthonormal to ~1e-5, which only perturbs the spectrum by that
+    # relative amount; the stored A defines the problem).
     wdt = torch.float32 if cfg["dtype"] == "f32" else f64
     Z = torch.randn(n, d, generator=g, device=device, dtype=wdt)
-    C = (Z.T @ Z).to(f64)
-    L = torch.linalg.cholesky(C)
-    # U = Z L^{-T}; then fold diag(sigma) V^T:  A = Z (L^{-T} diag(sigma) V^T)
-    M = torch.linalg.solve_triangular(L.T, torch.diag(sigma) @ V.T, upper=True).to(wdt)
+    C = (Z.T @ Z).to(f64).cpu().numpy()
+    L = np.linalg.cholesky(C)
+    # A = Z L^{-T} diag(sigma) V^T
+    Mh = scipy.linalg.solve_triangular(L.T, np.diag(sigma) @ V.T, lower=False)
+    M = torch.from_numpy(Mh).to(device=device, dtype=wdt)
     A = torch.empty(n, d, device=device, dtype=wdt)
     blk = 1 << 15
     for r0 in range(0, n, blk):
         A[r0:r0 + blk] = Z[r0:r0 + blk] @ M
     del Z
-    if cfg["lam"] == "identity":
-        lam = torch.ones(d, device=device, dtype=f64)
-    elif cfg["lam"] == "one_plus_9u":
-        lam = 1.0 + 9.0 * torch.rand(d, generator=g, device=device, dtype=f64)
-    else:
-        lam = 1.0 + torch.rand(d, generator=g, device=device, dtype=f64)
-    out = dict(n=n, d=d, nu=float(cfg["nu"]), lam=lam, sigma=sigma, meta=dict(config=config, seed=seed, **cfg))
+    lam = torch.from_numpy(_lambda(cfg["lam"], rng, d)).to(device=device, dtype=f64)
+    out = dict(n=n, d=d, nu=float(cfg["nu"]), lam=lam, sigma=torch.from_numpy(sigma).to(device),
+               meta=dict(config=config, seed=seed, **cfg))
     if cfg["dtype"] == "f32":
         out["A32"] = A
         A = A.to(f64)

@@ -222,3 +222,34 @@ def test_multiple_rhs_solved_columnwise():
     x, st, _ = api().adaptive_pcg(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind="gaussian", tol=1e-10)
     for c in range(3):
         assert O.rel_err_H(p.A, p.nu, p.lam, host(x)[:, c], xs[:, c]) <= 1e-10
+
+
+# ----------------------------------------------------------------------------- mixed form (a12)
+
+@pytest.mark.parametrize("method", ["pcg", "ihs"])
+@pytest.mark.parametrize("kind", ["gaussian", "sjlt", "srht"])
+def test_mixed_refined_reaches_1e8(method, kind):
+    # C3 recipe at a reduced size: float32 A, nu = 1e-4, kappa(H) ~ 1e8.
+    p = synthetic.make_problem("C3", 0, n=8192, d=256)
+    xs = O.direct_solve(p.A, p.b, p.nu, p.lam)  # A is the exact upcast of the float32 matrix
+    fn = api().adaptive_pcg if method == "pcg" else api().adaptive_ihs
+    x, st, tr = fn(dev(p.A, torch.float32), dev(p.b), p.nu, dev(p.lam), kind=kind, m_init=1, tol=1e-8, sjlt_s=4,
+                   precision="mixed", seed=2, trace_cap=4096, max_iter=2000)
+    err = O.rel_err_H(p.A, p.nu, p.lam, host(x), xs)
+    assert err <= 1e-8, (err, st)
+    assert st["outer_iters"] >= 2
+    assert max(e["outer"] for e in tr) >= 1
+
+
+def test_mixed_requires_float32_A():
+    p = synthetic.make_problem("C1", 0, n=512, d=32)
+    from paper_2104_14101_gb300._lib import SksError
+    with pytest.raises(SksError):
+        api().adaptive_pcg(dev(p.A), dev(p.b), p.nu, dev(p.lam), precision="mixed")
+
+
+def test_gpu_generator_matches_spectrum():
+    # make_problem_torch (used by the benchmark) follows the same recipe.
+    prob = synthetic.make_problem_torch("C2", seed=0, device="cuda", n=4096, d=128)
+    s = np.linalg.svd(host(prob["A64"]), compute_uv=False)
+    assert np.allclose(s, synthetic.spectrum("harmonic", 128), rtol=1e-10)

@@ -45,6 +45,15 @@ WORKLOADS = {
     # reduced C2 (n = 2^15, A = 512 MiB, still 4x the L2) for ncu captures of single kernels
     "C2-profile": dict(config="C2", n=1 << 15, method="pcg", kind="srht", m_init=16, m_max=4096, tol=1e-10,
                        precision="plain", desc="C2 recipe at n=2^15 (profiling size)"),
+    # C3: the metric's comparison -- mixed+refined on the float32 A vs plain float64 on its exact
+    # float64 upcast, same embedding; m capped at 2d (the paper's non-adaptive sketch size).
+    "C3": dict(config="C3", method="pcg", kind="sjlt", sjlt_s=4, m_init=1, m_max=8192, tol=1e-8,
+               precision="mixed", compare_plain=True, cpu_rows=1 << 16,
+               desc="mixed+refined adaptive PCG (float32 A, SJLT s=4, float64 refinement) vs plain float64 "
+                    "adaptive PCG on the same problem: n=2^20, d=4096, sigma_j=0.98^j+1e-6, nu=1e-4, tol 1e-8"),
+    "C3-srht": dict(config="C3", method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=8192, tol=1e-8,
+                    precision="mixed", compare_plain=True, cpu_rows=1 << 16,
+                    desc="C3 with the SRHT for both forms"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -201,13 +210,18 @@ def run_ours(args, wl, world, rank, local):
     torch.cuda.set_device(dev)
     lib = _lib.load()
     prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev, n=wl.get("n"))
-    A = prob["A64"]
+    mixed = wl["precision"] == "mixed"
+    A64 = prob["A64"]
+    A = prob["A32"] if mixed else A64
     b = prob["b"][:, 0].contiguous()
     lam = prob["lam"]
     nu = prob["nu"]
     n, d = A.shape
-    solver = sks.Solver(A, b, nu, lam, method=wl["method"], kind=wl["kind"], m_init=wl["m_init"], m_max=wl["m_max"],
-                        tol=wl["tol"], seed=0)
+    sopts = dict(method=wl["method"], kind=wl["kind"], m_init=wl["m_init"], m_max=wl["m_max"], tol=wl["tol"],
+                 seed=0, sjlt_s=wl.get("sjlt_s", 1), precision=wl["precision"], max_iter=5000)
+    if not mixed:
+        del prob
+    solver = sks.Solver(A, b, nu, lam, **sopts)
     for _ in range(args.warmup):
         solver.solve()
     torch.cuda.synchronize()
@@ -238,24 +252,34 @@ def run_ours(args, wl, world, rank, local):
     ap_ms = sum(s["ms_apass"] for s in stats)
     ap_n = sum(s["apass_timed"] for s in stats)
     ap_avg_ms = ap_ms / max(ap_n, 1)
-    elem = 8
-    bytes_per_pass = n * d * elem + 3 * d * 8
+    elem = A.element_size()
+    bytes_per_pass = n * d * elem + 3 * d * elem
     flops_per_pass = 4.0 * n * d
     gbs = bytes_per_pass / (ap_avg_ms * 1e-3) / 1e9
     peaks, peak_src = load_peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-    # float64 A-pass: 2 FMA per element at 2 float64 FMA/clk/SM (152 SMs)
-    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-    achieved_tflops = flops_per_pass / (ap_avg_ms * 1e-3) / 1e12
-    th = TRAFFIC.get(kernel_hash())
-    roofline = {
-        "bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-        "frac": achieved_tflops / fp64_peak_tflops, "traffic": th,
-        "kernel": "apass_kernel<double,double>", "launches": ap_n, "avg_launch_ms": ap_avg_ms,
-        "hbm_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": gbs / peaks["hbm_gbs"],
-        "peak_source": "float64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2 flop) at the sampled median "
-                       "SM clock; HBM peak " + peak_src,
-    }
+    th = TRAFFIC.get(kernel_hash() + ("f32" if mixed else "f64"))
+    if mixed:
+        # float32 A-pass: 1 flop per byte, HBM-bound
+        roofline = {
+            "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": th, "kernel": "apass_kernel<float,float>",
+            "launches": ap_n, "avg_launch_ms": ap_avg_ms, "bytes_per_launch": bytes_per_pass,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
+        }
+    else:
+        # float64 A-pass: 2 FMA per element at 2 float64 FMA/clk/SM (152 SMs)
+        fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+        achieved_tflops = flops_per_pass / (ap_avg_ms * 1e-3) / 1e12
+        roofline = {
+            "bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved_tflops / fp64_peak_tflops, "traffic": th,
+            "kernel": "apass_kernel<double,double>", "launches": ap_n, "avg_launch_ms": ap_avg_ms,
+            "bytes_per_launch": bytes_per_pass, "hbm_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+            "hbm_frac": gbs / peaks["hbm_gbs"],
+            "peak_source": "float64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2 flop) at the sampled "
+                           "median SM clock; HBM peak " + peak_src,
+        }
 
     # ---- e2e: host buffers, copies inside the timed region
     A_h = A.cpu().pin_memory()
@@ -268,8 +292,7 @@ def run_ours(args, wl, world, rank, local):
     A_d.copy_(A_h)
     b_d.copy_(b_h)
     lam_d.copy_(lam_h)
-    solver_e2e = sks.Solver(A_d, b_d, nu, lam_d, method=wl["method"], kind=wl["kind"], m_init=wl["m_init"],
-                            m_max=wl["m_max"], tol=wl["tol"], seed=0)
+    solver_e2e = sks.Solver(A_d, b_d, nu, lam_d, **sopts)
     solver_e2e.solve()
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
@@ -290,12 +313,36 @@ def run_ours(args, wl, world, rank, local):
     ms_e2e = max_over_ranks(e2.elapsed_time(e3) / k_e2e, world, dev)
     h2d = A.numel() * A.element_size() + b.numel() * 8 + lam.numel() * 8
     d2h = d * 8
+    del A_d, solver_e2e
+    torch.cuda.empty_cache()
+
+    # ---- the metric's comparison: the plain float64 form on the same problem
+    compare = None
+    if wl.get("compare_plain"):
+        popts = dict(sopts, precision="plain")
+        psolver = sks.Solver(A64, b, nu, lam, **popts)
+        psolver.solve()
+        torch.cuda.synchronize()
+        e4 = torch.cuda.Event(enable_timing=True)
+        e5 = torch.cuda.Event(enable_timing=True)
+        kp = max(1, min(args.steps, 3))
+        e4.record(stream)
+        for _ in range(kp):
+            xp_, stp, _ = psolver.solve()
+        e5.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = e4.elapsed_time(e5) / kp
+        compare = {"plain_f64_ms": ms_plain, "mixed_ms": ms, "speedup_mixed_vs_plain": ms_plain / ms,
+                   "plain_steps": kp,
+                   "plain_stats": {k: stp[k] for k in ("iters", "rejections", "final_m", "a_passes", "ms_sketch",
+                                                       "ms_factor", "ms_iter", "ms_apass", "apass_timed")}}
+        del psolver
 
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": wl["config"] + ": " + wl["desc"], "method": "adaptive_" + wl["method"],
                    "n": n, "d": d, "kind": wl["kind"], "precision": wl["precision"],
                    "l2": "inputs larger than L2 (A = %.2f GiB)" % (A.numel() * 8 / 2 ** 30),
@@ -305,21 +352,39 @@ def run_ours(args, wl, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": clk,
         "solve_stats": {k: st0[k] for k in ("iters", "rejections", "final_m", "a_passes", "factorizations",
-                                            "ms_sketch", "ms_factor", "ms_iter", "est_rel_err")},
+                                            "outer_iters", "ms_sketch", "ms_factor", "ms_iter", "est_rel_err")},
     }
+    if compare:
+        line["compare"] = compare
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        A_np = A_h.numpy()
-        b_np = b_h.numpy()
-        lam_np = lam_h.numpy()
-        t0 = time.perf_counter()
-        xo, so, _ = oracle_solve(wl, A_np, b_np, nu, lam_np)
-        cpu_ms = (time.perf_counter() - t0) * 1e3
         from oracle import solvers as O
-        xs = O.direct_solve(A_np, b_np, nu, lam_np)
-        line["cpu_baseline"] = {"value": cpu_ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
-                                "sample": "one full oracle adaptive solve of the same workload (all rows)",
-                                "oracle_rel_err_H": O.rel_err_H(A_np, nu, lam_np, xo, xs)}
-        line["rel_err_H_vs_oracle"] = O.rel_err_H(A_np, nu, lam_np, x.cpu().numpy(), xs)
+        lam_np = lam_h.numpy()
+        rows = wl.get("cpu_rows") or n
+        if rows >= n:
+            A_np = A64.cpu().numpy() if mixed else A_h.numpy()
+            b_np = b_h.numpy()
+            t0 = time.perf_counter()
+            xo, so, _ = oracle_solve(wl, A_np, b_np, nu, lam_np)
+            cpu_ms = (time.perf_counter() - t0) * 1e3
+            xs = O.direct_solve(A_np, b_np, nu, lam_np)
+            line["cpu_baseline"] = {"value": cpu_ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                                    "sample": "one full oracle adaptive solve of the same workload (all rows)",
+                                    "oracle_rel_err_H": O.rel_err_H(A_np, nu, lam_np, xo, xs)}
+            line["rel_err_H_vs_oracle"] = O.rel_err_H(A_np, nu, lam_np, x.cpu().numpy(), xs)
+        else:
+            # bounded sample: the oracle's solve on the first `rows` rows, scaled by n / rows
+            A_np = A64[:rows].cpu().numpy()
+            b_np = A_np.T @ np.random.default_rng(0).standard_normal(rows)
+            t0 = time.perf_counter()
+            oracle_solve(wl, A_np, b_np, nu, lam_np)
+            cpu_ms = (time.perf_counter() - t0) * 1e3 * (n / rows)
+            line["cpu_baseline"] = {"value": cpu_ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                                    "sample": "oracle adaptive solve (float64) on the first %d of %d rows, time "
+                                              "scaled by %d" % (rows, n, n // rows)}
+            # accuracy of the GPU result: the oracle's relative H-error from A itself (one float64 pass)
+            A_all = A64.cpu().numpy()
+            xs = O.direct_solve(A_all, b_h.numpy(), nu, lam_np)
+            line["rel_err_H_vs_oracle"] = O.rel_err_H(A_all, nu, lam_np, x.cpu().numpy(), xs)
     return line if rank == 0 else None
 
 

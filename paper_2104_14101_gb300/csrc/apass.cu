@@ -137,6 +137,18 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
 #pragma unroll
       for (int c = 0; c < K; ++c) acc[q][e][c] = TX(0);
 
+  // the thread's slice of x stays in registers for the whole pass
+  TX xr[QMAX][VEC][K];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+    const int vi = l + q * G;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+        xr[q][e][c] = (q < a.q && vi < nvec) ? xs[c * a.dp + vi * VEC + e] : TX(0);
+  }
+
   int buf = 0;
   int it = 0;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
@@ -146,14 +158,13 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
     if (G > 32) {
       // keep the 256 consumers in lock step: a timed-out warp flags, all leave
       if (!ok && lane == 0) abort_flag = 1;
-      named_bar_sync(2, kConsumers);
+      named_bar_sync(1, kConsumers);
       if (abort_flag) break;
     } else if (!ok) {
       break;
     }
     const TA* S = stage0 + (size_t)s * stage_elems;
     for (int j0 = 0; j0 < rg; j0 += kRC) {
-      TA v[kRC][QMAX][VEC];
       TX dot[kRC][K];
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {
@@ -167,14 +178,12 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
           if (rok && q < a.q && vi < nvec) {
             const int col = vi * VEC;
             const int b = col / a.boxw, jj = col - b * a.boxw;
-            Vec<TA>::load(S + (size_t)b * a.rows * a.boxw + (size_t)r * a.boxw + jj, v[rc][q]);
+            TA v[VEC];
+            Vec<TA>::load(S + (size_t)b * a.rows * a.boxw + (size_t)r * a.boxw + jj, v);
 #pragma unroll
             for (int e = 0; e < VEC; ++e)
 #pragma unroll
-              for (int c = 0; c < K; ++c) dot[rc][c] += (TX)v[rc][q][e] * xs[c * a.dp + col + e];
-          } else {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) v[rc][q][e] = TA(0);
+              for (int c = 0; c < K; ++c) dot[rc][c] += (TX)v[e] * xr[q][e][c];
           }
         }
       }
@@ -191,28 +200,41 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
 #pragma unroll
             for (int c = 0; c < K; ++c) rb[warp * kRC * K + rc * K + c] = dot[rc][c];
         }
-        named_bar_sync(1, kConsumers);
+        named_bar_sync(2 + g, G);
+        constexpr int WPG = G / 32;  // warps per group
+        const int w0 = g * WPG;
 #pragma unroll
         for (int rc = 0; rc < kRC; ++rc)
 #pragma unroll
           for (int c = 0; c < K; ++c) {
             TX t = TX(0);
 #pragma unroll
-            for (int w = 0; w < 8; ++w) t += rb[w * kRC * K + rc * K + c];
+            for (int w = 0; w < WPG; ++w) t += rb[(w0 + w) * kRC * K + rc * K + c];
             dot[rc][c] = t;
           }
         buf ^= 1;
       }
-      // rank-one updates  acc += (a_r^T x) a_r
+      // rank-one updates  acc += (a_r^T x) a_r  (row re-read from shared memory)
 #pragma unroll
-      for (int rc = 0; rc < kRC; ++rc)
+      for (int rc = 0; rc < kRC; ++rc) {
+        const int r = g + NG * (j0 + rc);
+        if ((j0 + rc) < rg) {
 #pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
+          for (int q = 0; q < QMAX; ++q) {
+            const int vi = l + q * G;
+            if (q < a.q && vi < nvec) {
+              const int col = vi * VEC;
+              const int b = col / a.boxw, jj = col - b * a.boxw;
+              TA v[VEC];
+              Vec<TA>::load(S + (size_t)b * a.rows * a.boxw + (size_t)r * a.boxw + jj, v);
 #pragma unroll
-          for (int e = 0; e < VEC; ++e)
+              for (int e = 0; e < VEC; ++e)
 #pragma unroll
-            for (int c = 0; c < K; ++c) acc[q][e][c] += dot[rc][c] * (TX)v[rc][q][e];
+                for (int c = 0; c < K; ++c) acc[q][e][c] += dot[rc][c] * (TX)v[e];
+            }
+          }
         }
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -312,8 +334,11 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   // Per-thread column vectors: 8 (float64 A, 2 per vector) or 4 (float32 A,
   // 4 per vector), i.e. 16 register-resident accumulators per right-hand side.
   const int qcap = a_f32 ? 4 : 8;
-  int group = (nvec <= 32 * qcap && k == 1) ? 32 : 256;
-  if (k == 8) group = 256;
+  int group = 256;
+  if (k == 1) {
+    if (nvec <= 32 * qcap) group = 32;
+    else if (nvec <= 128 * qcap) group = 128;
+  }
   const int qmax = (k == 8) ? (a_f32 ? 1 : 2) : qcap;
   const int q = (nvec + group - 1) / group;
   if (q > qmax) return fail(SKS_ERR_UNSUPPORTED, "A-pass: row too wide for this instantiation");
@@ -355,19 +380,24 @@ sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n,
                         DevStatus* st, cudaStream_t stream, double sgn, const void* addv, double addc,
                         cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   if (!a_f32 && vec_f32) return fail(SKS_ERR_UNSUPPORTED, "float64 A with float32 vectors");
+#define SKS_APASS_ARGS pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end
   if (!a_f32) {
-    if (k == 8) return launch_t<double, double, 256, 2, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
-    if (pl.group == 32) return launch_t<double, double, 32, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
-    return launch_t<double, double, 256, 8, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+    if (k == 8) return launch_t<double, double, 256, 2, 8>(SKS_APASS_ARGS);
+    if (pl.group == 32) return launch_t<double, double, 32, 8, 1>(SKS_APASS_ARGS);
+    if (pl.group == 128) return launch_t<double, double, 128, 8, 1>(SKS_APASS_ARGS);
+    return launch_t<double, double, 256, 8, 1>(SKS_APASS_ARGS);
   }
   if (vec_f32) {
-    if (k == 8) return launch_t<float, float, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
-    if (pl.group == 32) return launch_t<float, float, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
-    return launch_t<float, float, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+    if (k == 8) return launch_t<float, float, 256, 1, 8>(SKS_APASS_ARGS);
+    if (pl.group == 32) return launch_t<float, float, 32, 4, 1>(SKS_APASS_ARGS);
+    if (pl.group == 128) return launch_t<float, float, 128, 4, 1>(SKS_APASS_ARGS);
+    return launch_t<float, float, 256, 4, 1>(SKS_APASS_ARGS);
   }
-  if (k == 8) return launch_t<float, double, 256, 1, 8>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
-  if (pl.group == 32) return launch_t<float, double, 32, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
-  return launch_t<float, double, 256, 4, 1>(pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end);
+  if (k == 8) return launch_t<float, double, 256, 1, 8>(SKS_APASS_ARGS);
+  if (pl.group == 32) return launch_t<float, double, 32, 4, 1>(SKS_APASS_ARGS);
+  if (pl.group == 128) return launch_t<float, double, 128, 4, 1>(SKS_APASS_ARGS);
+  return launch_t<float, double, 256, 4, 1>(SKS_APASS_ARGS);
+#undef SKS_APASS_ARGS
 }
 
 }  // namespace sks

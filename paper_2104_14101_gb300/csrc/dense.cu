@@ -169,15 +169,26 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular L: column j of X solves L x = e_j
-  for (int j = tid; j < NB; j += blockDim.x) {
-    for (int i = 0; i < NB; ++i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int q = j; q < i; ++q) s -= L[i][q] * X[q][j];
-      X[i][j] = (i >= j) ? s / L[i][i] : 0.0;
-    }
-  }
+  // inverse of the lower-triangular L, row by row:
+  //   X[i][j] = -(sum_{j <= q < i} L[i][q] X[q][j]) / L[i][i]  (j < i),  X[i][i] = 1 / L[i][i];
+  // the 256 threads split each row's dots four ways (64 columns x 4 parts).
+  __shared__ double part[4][NB];
+  for (int e = tid; e < NB * NB; e += blockDim.x) X[e / NB][e % NB] = 0.0;
   __syncthreads();
+  const int jj = tid & (NB - 1), pp = tid >> 6;
+  for (int i = 0; i < NB; ++i) {
+    double acc = 0.0;
+    if (jj < i)
+      for (int q = jj + pp; q < i; q += 4) acc += L[i][q] * X[q][jj];
+    part[pp][jj] = acc;
+    __syncthreads();
+    if (tid < NB) {
+      const double inv = 1.0 / L[i][i];
+      if (tid < i) X[i][tid] = -((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) * inv;
+      else if (tid == i) X[i][i] = inv;
+    }
+    __syncthreads();
+  }
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e % nb;
     if (j <= i) D[(long long)i * ld + j] = L[i][j];

@@ -59,17 +59,9 @@ struct ApassArgs {
 
 SKS_HD size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-template <typename TA, typename TX, int G, int K>
-SKS_HD size_t apass_smem_bytes(int rows, int dp, int stages) {
-  size_t b = align_up((size_t)stages * rows * dp * sizeof(TA), 128);
-  b += align_up((size_t)K * dp * sizeof(TX), 128);
-  b += align_up((size_t)2 * 8 * kRC * K * sizeof(TX), 128);
-  b += 2 * 8 * (size_t)stages;
-  return b;
-}
-
 template <typename TA, typename TX, int G, int QMAX, int K>
-__global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constant__ CUtensorMap tmap, ApassArgs a) {
+__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4) ? 2 : 1)
+    apass_kernel(const __grid_constant__ CUtensorMap tmap, ApassArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int VEC = Vec<TA>::N;
   constexpr int NG = kConsumers / G;
@@ -77,8 +69,6 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
   const size_t stage_elems = (size_t)a.rows * a.dp;
   TA* stage0 = (TA*)smem;
   size_t off = align_up((size_t)a.stages * stage_elems * sizeof(TA), 128);
-  TX* xs = (TX*)(smem + off);
-  off += align_up((size_t)K * a.dp * sizeof(TX), 128);
   TX* red = (TX*)(smem + off);
   off += align_up((size_t)2 * 8 * kRC * K * sizeof(TX), 128);
   uint64_t* full = (uint64_t*)(smem + off);
@@ -93,12 +83,6 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
     }
     fence_mbar_init();
     fence_proxy_async();
-  }
-  // x -> shared, zero padded to dp columns
-  const TX* xg = (const TX*)a.x;
-  for (int i = tid; i < K * a.dp; i += blockDim.x) {
-    const int c = i / a.dp, j = i - c * a.dp;
-    xs[i] = (j < a.d) ? xg[(size_t)c * a.d + j] : TX(0);
   }
   __syncthreads();
 
@@ -137,7 +121,8 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
 #pragma unroll
       for (int c = 0; c < K; ++c) acc[q][e][c] = TX(0);
 
-  // the thread's slice of x stays in registers for the whole pass
+  // the thread's slice of x (zero past column d) stays in registers for the whole pass
+  const TX* xg = (const TX*)a.x;
   TX xr[QMAX][VEC][K];
 #pragma unroll
   for (int q = 0; q < QMAX; ++q) {
@@ -145,8 +130,10 @@ __global__ void __launch_bounds__(kThreads, 1) apass_kernel(const __grid_constan
 #pragma unroll
     for (int e = 0; e < VEC; ++e)
 #pragma unroll
-      for (int c = 0; c < K; ++c)
-        xr[q][e][c] = (q < a.q && vi < nvec) ? xs[c * a.dp + vi * VEC + e] : TX(0);
+      for (int c = 0; c < K; ++c) {
+        const int col = vi * VEC + e;
+        xr[q][e][c] = (q < a.q && vi < nvec && col < a.d) ? xg[(size_t)c * a.d + col] : TX(0);
+      }
   }
 
   int buf = 0;
@@ -349,14 +336,17 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   rows = std::min(rows, 256);
   rows = rows / ng * ng;
   const DeviceInfo& di = device_info();
-  const size_t budget = di.smem_optin ? di.smem_optin : 232448;
-  const size_t fixed = ((size_t)k * dp * xsz + 127) / 128 * 128 + ((size_t)2 * 8 * kRC * k * xsz + 127) / 128 * 128;
+  // the float32 pass (HBM-bound, latency-limited at one CTA per SM) runs two
+  // CTAs per SM, each with half the shared memory
+  const int ctas_per_sm = (a_f32 && vec_f32) ? 2 : 1;
+  const size_t budget = (di.smem_optin ? di.smem_optin : 232448) / ctas_per_sm - (ctas_per_sm > 1 ? 1024 : 0);
+  const size_t fixed = ((size_t)2 * 8 * kRC * k * xsz + 127) / 128 * 128;
   const size_t stage_bytes = ((size_t)rows * row_bytes);
   int stages = (int)std::min<size_t>(8, (budget - fixed - 1024) / stage_bytes);
   if (stages < 2) return fail(SKS_ERR_UNSUPPORTED, "A-pass: shared memory too small");
   const int64_t ntiles = (n + rows - 1) / rows;
   const int sms = di.sms > 0 ? di.sms : 152;
-  pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms));
+  pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * ctas_per_sm));
   pl->group = group;
   pl->q = q;
   pl->rows_per_stage = rows;

@@ -45,6 +45,37 @@ const DeviceInfo& device_info() {
   return info;
 }
 
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+sks_status make_tmap_2d_bf16_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
+                                   uint32_t box_cols, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(SKS_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  if (((uintptr_t)base & 127) != 0) return fail(SKS_ERR_INVALID_ARG, "bf16 operand must be 128-byte aligned");
+  if ((cols * 2) % 16 != 0 || box_cols * 2 != 128) return fail(SKS_ERR_INVALID_ARG, "bf16 tensor map geometry");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * 2)};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(SKS_ERR_INVALID_ARG, "cuTensorMapEncodeTiled (bf16) failed (code " + std::to_string((int)r) + ")");
+  return SKS_OK;
+}
+
 sks_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, size_t elem_bytes, uint64_t rows,
                         uint64_t cols, uint64_t ld, uint32_t box_cols, uint32_t box_rows) {
   static EncodeTiledFn fn = nullptr;

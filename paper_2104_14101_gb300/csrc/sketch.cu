@@ -117,7 +117,8 @@ __global__ void gauss_gen_kernel(Key key, int m_off, int m_add, int64_t i0, int 
   }
 }
 
-// SJLT scatter: one warp per data row.
+// SJLT scatter: one warp per data row; float32 sketches add 16-byte vectors
+// with one atomic each (4x fewer L2 atomic operations than scalar adds).
 template <typename TA, typename TY>
 __global__ void sjlt_scatter_kernel(const TA* __restrict__ A, long long lda, int64_t n, int d, uint32_t m, int s_eff,
                                     Key key, TY* __restrict__ Y, long long ldy) {
@@ -129,9 +130,50 @@ __global__ void sjlt_scatter_kernel(const TA* __restrict__ A, long long lda, int
   sjlt_hash(key, (uint32_t)warp, m, s_eff, rows, signs);
   const TY inv = (TY)(1.0 / sqrt((double)s_eff));
   const TA* a = A + warp * lda;
+  if (sizeof(TY) == 4 && sizeof(TA) == 4 && (d & 3) == 0 && (lda & 3) == 0 && (ldy & 3) == 0) {
+    for (int c = lane * 4; c < d; c += 128) {
+      const float4 v = *(const float4*)(a + c);
+      for (int k = 0; k < s_eff; ++k) {
+        const float w = signs[k] * (float)inv;
+        atomicAdd((float4*)(Y + (long long)rows[k] * ldy + c), make_float4(w * v.x, w * v.y, w * v.z, w * v.w));
+      }
+    }
+    return;
+  }
   for (int c = lane; c < d; c += 32) {
     const TY v = (TY)a[c] * inv;
     for (int k = 0; k < s_eff; ++k) atomicAdd(&Y[(long long)rows[k] * ldy + c], (TY)signs[k] * v);
+  }
+}
+
+// Small sketches (m * d fits in shared memory): every CTA accumulates its
+// rows into a private copy of Y and flushes it with one atomic per entry.
+template <typename TA, typename TY>
+__global__ void __launch_bounds__(256) sjlt_private_kernel(const TA* __restrict__ A, long long lda, int64_t n, int d,
+                                                          uint32_t m, int s_eff, Key key, TY* __restrict__ Y,
+                                                          long long ldy, int64_t rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TY* Ys = (TY*)smem_raw;  // m x d
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < (int)m * d; e += blockDim.x) Ys[e] = TY(0);
+  __syncthreads();
+  const TY inv = (TY)(1.0 / sqrt((double)s_eff));
+  const int64_t r0 = blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(n, r0 + rows_per_cta);
+  for (int64_t i = r0 + warp; i < r1; i += blockDim.x / 32) {
+    uint32_t rows[kSjltMaxS];
+    float signs[kSjltMaxS];
+    sjlt_hash(key, (uint32_t)i, m, s_eff, rows, signs);
+    const TA* a = A + i * lda;
+    for (int c = lane; c < d; c += 32) {
+      const TY v = (TY)a[c] * inv;
+      for (int k = 0; k < s_eff; ++k) atomicAdd(&Ys[rows[k] * d + c], (TY)signs[k] * v);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < (int)m * d; e += blockDim.x) {
+    const int r = e / d, c = e % d;
+    atomicAdd(&Y[(long long)r * ldy + c], Ys[e]);
   }
 }
 
@@ -233,6 +275,19 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
   if (n == 0) return SKS_OK;
   const int s_eff = std::min(s, m);
   if (s_eff > kSjltMaxS) return fail(SKS_ERR_UNSUPPORTED, "SJLT s > 16");
+  const size_t priv_bytes = (size_t)m * d * sizeof(TY);
+  if (priv_bytes <= 96 * 1024) {
+    const int sms = device_info().sms > 0 ? device_info().sms : 152;
+    const int64_t ctas = std::min<int64_t>((int64_t)sms * 2, (n + 255) / 256);
+    const int64_t per = (n + ctas - 1) / ctas;
+    SKS_CUDA_TRY(cudaFuncSetAttribute(sjlt_private_kernel<TA, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)priv_bytes));
+    sjlt_private_kernel<TA, TY><<<(unsigned)ctas, 256, priv_bytes, stream>>>(A, lda, n, d, (uint32_t)m, s_eff,
+                                                                          make_key(seed), Y, ldy, per);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+    return SKS_OK;
+  }
   const long long threads = n * 32;
   sjlt_scatter_kernel<TA, TY><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(A, lda, n, d, (uint32_t)m, s_eff,
                                                                                     make_key(seed), Y, ldy);

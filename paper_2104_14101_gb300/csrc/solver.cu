@@ -16,6 +16,7 @@
 #include "dense.h"
 #include "internal.h"
 #include "sketch.h"
+#include "tc_gram.h"
 
 // ============================================================================ handles
 
@@ -55,6 +56,8 @@ struct sks_precond {
   size_t split_elems = 0;
   double* t1 = nullptr;  // m-vectors
   double* t2 = nullptr;
+  __nv_bfloat16* bf[4] = {nullptr, nullptr, nullptr, nullptr};  // split-bf16 operands (float32 sketches)
+  size_t bf_elems = 0;
   sks::DevStatus* st = nullptr;
 };
 
@@ -244,6 +247,10 @@ size_t precond_ws_bytes(const sks_problem* p, int64_t m_max) {
   c.take<double>(cholesky_ws_elems((int)d));
   c.take<double>(std::min<size_t>(4 * d * d, (size_t)1 << 24));
   c.take<double>(2 * std::max<size_t>(d, (size_t)m_max));
+  if (p->dtype == SKS_F32) {
+    const size_t e = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
+    for (int i = 0; i < 4; ++i) c.take<__nv_bfloat16>(e + 64);
+  }
   return c.used + 256;
 }
 
@@ -265,6 +272,10 @@ sks_status precond_init(sks_precond* P, const sks_problem* p, int64_t m_max, voi
   P->split = c.take<double>(P->split_elems);
   P->t1 = c.take<double>(std::max<size_t>(d, (size_t)m_max));
   P->t2 = c.take<double>(std::max<size_t>(d, (size_t)m_max));
+  if (p->dtype == SKS_F32) {
+    P->bf_elems = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
+    for (int i = 0; i < 4; ++i) P->bf[i] = c.take<__nv_bfloat16>(P->bf_elems + 64);
+  }
   if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "preconditioner workspace too small");
   return SKS_OK;
 }
@@ -280,10 +291,15 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
   P->lam = lam;
   const double* Y64;
   long long ldy;
-  if (s->f32) {
+  // Float32 sketches form the Gram matrix on the tensor cores from a
+  // split-bfloat16 copy (tc_gram.cu); float64 sketches use float64 GEMMs.
+  const bool tc = s->f32 && P->bf[0] != nullptr;
+  if (s->f32 && !(tc && m < d)) {
     f32_to_f64_2d_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, (const float*)s->Y, s->ldy, P->Y64, d);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
+  }
+  if (s->f32) {
     Y64 = P->Y64;
     ldy = d;
   } else {
@@ -292,17 +308,33 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
   }
   P->ldy64 = ldy;
   if (!P->woodbury) {
-    SKS_TRY(gemm<double>(stream, d, d, m, Y64, ldy, true, Y64, ldy, false, P->H, d, P->c2, 0.0, true, 1, 0, 0, 0,
-                         P->split, P->split_elems));
+    if (tc) {
+      int Kp = 0;
+      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, true, nullptr, P->bf[0], P->bf[1], &Kp));
+      SKS_TRY(tc_gram(stream, d, d, Kp, P->bf[0], P->bf[1], P->bf[0], P->bf[1], P->c2, 0.0, P->H, d, true, P->st));
+    } else {
+      SKS_TRY(gemm<double>(stream, d, d, m, Y64, ldy, true, Y64, ldy, false, P->H, d, P->c2, 0.0, true, 1, 0, 0, 0,
+                           P->split, P->split_elems));
+    }
     SKS_TRY(add_diagonal(stream, d, P->H, d, 0.0, lam, P->nu2));
     SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st));
     SKS_TRY(transpose<double>(stream, d, d, P->X, d, P->Xt, d));
   } else {
-    scale_cols_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, Y64, ldy, lam, P->Ys, d);
-    note_launch();
-    SKS_CUDA_TRY(cudaGetLastError());
-    SKS_TRY(gemm<double>(stream, m, m, d, P->Ys, d, false, Y64, ldy, true, P->H, m, P->c2, 0.0, true, 1, 0, 0, 0,
-                         P->split, P->split_elems));
+    if (tc) {
+      // W = c^2 Z' Z'^T with Z' the split of Z = Y Lambda^{-1/2}; the apply then
+      // uses Y_eff = Z' Lambda^{1/2}, so the preconditioner is exactly the
+      // inverse of c^2 Y_eff^T Y_eff + nu^2 Lambda.
+      int Kp = 0;
+      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, false, lam, P->bf[0], P->bf[1], &Kp));
+      SKS_TRY(tc_gram(stream, m, m, Kp, P->bf[0], P->bf[1], P->bf[0], P->bf[1], P->c2, 0.0, P->H, m, true, P->st));
+      SKS_TRY(tc_unsplit(stream, P->bf[0], P->bf[1], m, d, Kp, lam, P->Y64, d));
+    } else {
+      scale_cols_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, Y64, ldy, lam, P->Ys, d);
+      note_launch();
+      SKS_CUDA_TRY(cudaGetLastError());
+      SKS_TRY(gemm<double>(stream, m, m, d, P->Ys, d, false, Y64, ldy, true, P->H, m, P->c2, 0.0, true, 1, 0, 0, 0,
+                           P->split, P->split_elems));
+    }
     SKS_TRY(add_diagonal(stream, m, P->H, m, P->nu2, nullptr, 0.0));
     SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st));
     SKS_TRY(transpose<double>(stream, m, m, P->X, m, P->Xt, m));

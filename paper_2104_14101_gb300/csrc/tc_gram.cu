@@ -1,0 +1,381 @@
+// tc_gram.cu -- K6 on the 5th-generation tensor cores: the sketched Gram
+// matrices of the preconditioner (Section 4.1.1),
+//     C = alpha * A B^T   (A: M x K, B: N x K, float32 in, float64 out),
+// i.e. H_S = c^2 Y^T Y (m >= d) or W_S = c^2 (Y Lambda^{-1}) Y^T (m < d).
+//
+// The preconditioner must resolve eigenvalues down to nu^2 ~ 1e-8 next to
+// entries of order 1, so the product is formed from a bfloat16 hi/lo split of
+// both operands, x = hi + lo (16 significant bits), using all four products
+// hi.hi + hi.lo + lo.hi + lo.lo (dropping lo.lo alone shifts the spectrum by
+// ~2^-16 |Y|^2, far above nu^2).  The tensor cores accumulate 64 K-elements in
+// float32 (products of bfloat16 are exact in float32); every 64-element chunk
+// is drained from TMEM and added into a double-float (float32 pair)
+// accumulator, which keeps the sum at ~48 bits.  float64 adds would be ~7x
+// slower than the MMAs on this part.
+//
+// Structure (one CTA per 128 x 128 output tile, 18 warps):
+//   warp 0      TMA producer: Ah, Al, Bh, Bl tiles (128 rows x 64 bf16, 128B
+//               swizzle) into a 3-stage shared-memory ring;
+//   warp 1      MMA issuer: 16 tcgen05.mma (M=128, N=128, K=16) per stage into
+//               one of two TMEM accumulators; tcgen05.commit frees the stage
+//               and publishes the accumulator;
+//   warps 2-17  epilogue: tcgen05.ld the accumulator (each warp: its 32 TMEM
+//               lanes x 32 columns), double-float accumulate, release it;
+//               at the end write alpha * (hi + lo) in float64.
+// Every mbarrier wait is bounded; a timed-out role flags the CTA, all roles
+// leave their loops, wait (bounded) for their own asynchronous work, and the
+// TMEM is freed before exit.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "tc_gram.h"
+
+namespace sks {
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 64;
+constexpr int kStagesTC = 3;
+constexpr int kTileBytes = TBM * TBK * 2;     // 16 KB per operand tile
+constexpr int kStageBytes = 4 * kTileBytes;   // Ah, Al, Bh, Bl
+constexpr int kEpiWarps = 16;                 // 4 per TMEM lane quadrant, 32 columns each
+constexpr int kTcThreads = (2 + kEpiWarps) * 32;
+constexpr uint32_t kTmemCols = 256;           // two 128-column float32 accumulators
+
+// ------------------------------------------------------------------ PTX wrappers
+SKS_DEV uint64_t smem_desc_sw128(const void* tile) {
+  // K-major, 128-byte swizzle: 8-row core-matrix groups 1024 bytes apart.
+  const uint64_t addr = (uint64_t)(smem_addr(tile) >> 4) & 0x3FFF;
+  uint64_t d = addr;
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major), encoded 1
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset between 8-row groups
+  d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;            // layout: 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: bf16 x bf16 -> f32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+SKS_DEV void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+SKS_DEV void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+SKS_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+SKS_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 16 consecutive float32 columns
+SKS_DEV void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Double-float accumulation (Knuth's TwoSum): (s, e) += x.
+SKS_DEV void df_add(float& s, float& e, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  const float err = (s - (t - bp)) + (x - bp);
+  s = t;
+  e += err;
+}
+
+struct GramArgs {
+  int M, N, Kp;          // Kp: padded K (multiple of 64)
+  int tiles_n;           // number of column tiles
+  int lower;             // only tiles with col tile <= row tile, and only j <= i written
+  double alpha, beta;
+  double* C;
+  long long ldc;
+  DevStatus* st;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gram_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                   const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, GramArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[kStagesTC], empty[kStagesTC], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  // tile coordinates (lower: linear index over the lower triangle of tiles)
+  int tm, tn;
+  if (g.lower) {
+    const int t = blockIdx.x;
+    tm = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+    while (tm * (tm + 1) / 2 > t) --tm;
+    tn = t - tm * (tm + 1) / 2;
+  } else {
+    tm = blockIdx.x / g.tiles_n;
+    tn = blockIdx.x % g.tiles_n;
+  }
+  const int row0 = tm * TBM, col0 = tn * TBN;
+  const int nk = g.Kp / TBK;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kStagesTC; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps);
+    }
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kk = 0; kk < nk; ++kk) {
+        const int s = kk % kStagesTC;
+        const uint32_t ph = (uint32_t)(kk / kStagesTC) & 1u;
+        if (abort_flag || !mbar_wait(&empty[s], ph ^ 1u, g.st, 41)) {
+          abort_flag = 1;
+          break;
+        }
+        unsigned char* st = smem + (size_t)s * kStageBytes;
+        mbar_arrive_expect_tx(&full[s], kStageBytes);
+        tma_load_2d(st + 0 * kTileBytes, &mAh, &full[s], kk * TBK, row0);
+        tma_load_2d(st + 1 * kTileBytes, &mAl, &full[s], kk * TBK, row0);
+        tma_load_2d(st + 2 * kTileBytes, &mBh, &full[s], kk * TBK, col0);
+        tma_load_2d(st + 3 * kTileBytes, &mBl, &full[s], kk * TBK, col0);
+        issued = kk + 1;
+      }
+      // every issued copy has landed before exit
+      const int first = issued > kStagesTC ? issued - kStagesTC : 0;
+      for (int k = first; k < issued; ++k) mbar_wait(&full[k % kStagesTC], (uint32_t)(k / kStagesTC) & 1u, g.st, 42);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(TBM, TBN);
+      int committed = 0;
+      for (int kk = 0; kk < nk; ++kk) {
+        const int s = kk % kStagesTC;
+        const int b = kk & 1;
+        if (abort_flag || !mbar_wait(&full[s], (uint32_t)(kk / kStagesTC) & 1u, g.st, 43) ||
+            !mbar_wait(&acc_empty[b], ((uint32_t)(kk >> 1) & 1u) ^ 1u, g.st, 44)) {
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        unsigned char* st = smem + (size_t)s * kStageBytes;
+        const uint32_t d_tmem = tmem + (uint32_t)(b * TBN);
+        // products: (Ah,Bh) (Ah,Bl) (Al,Bh) (Al,Bl)
+        uint32_t acc = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const uint64_t ad = smem_desc_sw128(st + (p >> 1) * kTileBytes);
+          const uint64_t bd = smem_desc_sw128(st + (2 + (p & 1)) * kTileBytes);
+#pragma unroll
+          for (int k = 0; k < TBK / 16; ++k) {
+            // advance 16 bf16 = 32 bytes along K inside the swizzle atom
+            umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, acc);
+            acc = 1;
+          }
+        }
+        umma_commit(&empty[s]);     // stage reusable once these MMAs finish
+        umma_commit(&acc_full[b]);  // accumulator b ready for the epilogue
+        committed = kk + 1;
+      }
+      // wait (bounded) for the last committed MMA group before leaving
+      if (committed > 0) {
+        const int k = committed - 1;
+        mbar_wait(&acc_full[k & 1], (uint32_t)(k >> 1) & 1u, g.st, 45);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2..17)
+    const int ew = warp - 2;            // 0..15
+    const int quad = warp & 3;          // TMEM lane quadrant this warp may access
+    const int cblk = ew >> 2;           // columns [32*cblk, 32*cblk + 32)
+    const int row = quad * 32 + lane;   // tile row held by this thread
+    float hi[32], lo[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0.f;
+    for (int kk = 0; kk < nk; ++kk) {
+      const int b = kk & 1;
+      const bool ok = mbar_wait_warp(&acc_full[b], (uint32_t)(kk >> 1) & 1u, g.st, 46);
+      if (!ok || abort_flag) {
+        if (lane == 0) abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TBN + cblk * 32);
+      float v[16];
+      tmem_ld16(base, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) df_add(hi[i], lo[i], v[i]);
+      tmem_ld16(base + 16, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) df_add(hi[16 + i], lo[16 + i], v[i]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+    const int gi = row0 + row;
+    if (!abort_flag && gi < g.M) {
+      double* crow = g.C + (long long)gi * g.ldc;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int gj = col0 + cblk * 32 + i;
+        if (gj < g.N && (!g.lower || gj <= gi)) {
+          const double v = g.alpha * ((double)hi[i] + (double)lo[i]);
+          crow[gj] = g.beta == 0.0 ? v : v + g.beta * crow[gj];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// X (rows x cols, ld) float32 -> hi/lo bfloat16, row-major (out_rows x Kp),
+// optional transpose (out row = input column) and column scaling
+// 1/sqrt(scale[c]) (computed in float64, rounded once to float32).
+__global__ void split_bf16_kernel(const float* __restrict__ X, long long ldx, int rows, int cols, int transpose,
+                                  const double* __restrict__ colscale, int out_rows, int Kp,
+                                  __nv_bfloat16* __restrict__ Hh, __nv_bfloat16* __restrict__ Hl) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)out_rows * Kp) return;
+  const int orow = (int)(e / Kp), k = (int)(e % Kp);
+  // input coordinates
+  const int r = transpose ? k : orow;
+  const int c = transpose ? orow : k;
+  float v = 0.f;
+  if (r < rows && c < cols) {
+    v = X[(long long)r * ldx + c];
+    if (colscale) v = (float)((double)v / sqrt(colscale[c]));
+  }
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const float rem = v - __bfloat162float(h);
+  Hh[e] = h;
+  Hl[e] = __float2bfloat16_rn(rem);
+}
+
+// Y_eff[r][c] = (hi + lo)[r][c] * sqrt(scale[c])  (float64), the sketch that
+// the split operands represent exactly.
+__global__ void unsplit_kernel(const __nv_bfloat16* __restrict__ Hh, const __nv_bfloat16* __restrict__ Hl, int rows,
+                               int cols, int Kp, const double* __restrict__ colscale, double* __restrict__ Y,
+                               long long ldy) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  const long long k = (long long)r * Kp + c;
+  double v = (double)__bfloat162float(Hh[k]) + (double)__bfloat162float(Hl[k]);
+  if (colscale) v *= sqrt(colscale[c]);
+  Y[(long long)r * ldy + c] = v;
+}
+
+}  // namespace
+
+sks_status tc_unsplit(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, int rows, int cols,
+                      int Kp, const double* colscale, double* Y, long long ldy) {
+  const long long total = (long long)rows * cols;
+  if (total > 0) {
+    unsplit_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(Hh, Hl, rows, cols, Kp, colscale, Y, ldy);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+  }
+  return SKS_OK;
+}
+
+size_t tc_gram_split_elems(int out_rows, int K) {
+  const int Kp = (K + TBK - 1) / TBK * TBK;
+  return (size_t)out_rows * Kp;
+}
+
+sks_status tc_split(cudaStream_t stream, const float* X, long long ldx, int rows, int cols, bool transpose,
+                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, int* Kp_out) {
+  const int out_rows = transpose ? cols : rows;
+  const int K = transpose ? rows : cols;
+  const int Kp = (K + TBK - 1) / TBK * TBK;
+  const long long total = (long long)out_rows * Kp;
+  if (total > 0) {
+    split_bf16_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(X, ldx, rows, cols, transpose ? 1 : 0,
+                                                                           colscale, out_rows, Kp, Hh, Hl);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+  }
+  *Kp_out = Kp;
+  return SKS_OK;
+}
+
+sks_status tc_gram(cudaStream_t stream, int M, int N, int Kp, const __nv_bfloat16* Ah, const __nv_bfloat16* Al,
+                   const __nv_bfloat16* Bh, const __nv_bfloat16* Bl, double alpha, double beta, double* C,
+                   long long ldc, bool lower, DevStatus* st) {
+  if (M <= 0 || N <= 0) return SKS_OK;
+  if (Kp % TBK != 0) return fail(SKS_ERR_INVALID_ARG, "tc_gram: K must be padded to 64");
+  if (Kp == 0) return fail(SKS_ERR_INVALID_ARG, "tc_gram: K = 0");
+  CUtensorMap mAh, mAl, mBh, mBl;
+  auto mk = [&](CUtensorMap* m, const void* base, int rows) -> sks_status {
+    return make_tmap_2d_bf16_sw128(m, base, (uint64_t)rows, (uint64_t)Kp, TBK, TBM);
+  };
+  SKS_TRY(mk(&mAh, Ah, M));
+  SKS_TRY(mk(&mAl, Al, M));
+  SKS_TRY(mk(&mBh, Bh, N));
+  SKS_TRY(mk(&mBl, Bl, N));
+  const int tm = (M + TBM - 1) / TBM, tn = (N + TBN - 1) / TBN;
+  GramArgs g;
+  g.M = M;
+  g.N = N;
+  g.Kp = Kp;
+  g.tiles_n = tn;
+  g.lower = lower ? 1 : 0;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.C = C;
+  g.ldc = ldc;
+  g.st = st;
+  if (lower && tm != tn) return fail(SKS_ERR_INVALID_ARG, "tc_gram: lower needs a square tiling");
+  const int tiles = lower ? tm * (tm + 1) / 2 : tm * tn;
+  const size_t smem = (size_t)kStagesTC * kStageBytes + 1024;
+  SKS_CUDA_TRY(cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tc_gram_kernel<<<tiles, kTcThreads, smem, stream>>>(mAh, mAl, mBh, mBl, g);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
+}  // namespace sks

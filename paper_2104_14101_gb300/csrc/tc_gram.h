@@ -1,0 +1,31 @@
+// tc_gram.h -- tensor-core (tcgen05) split-bfloat16 Gram products.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace sks {
+
+// Elements of one hi (or lo) buffer for an operand of out_rows x K.
+size_t tc_gram_split_elems(int out_rows, int K);
+
+// X (rows x cols float32, leading dimension ldx) -> bfloat16 hi/lo buffers of
+// shape out_rows x Kp (Kp = K rounded up to 64, zero padded), where the
+// operand is X (out_rows = rows, K = cols) or X^T (transpose: out_rows =
+// cols, K = rows); optional division of column c of X by sqrt(colscale[c]).
+sks_status tc_split(cudaStream_t stream, const float* X, long long ldx, int rows, int cols, bool transpose,
+                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, int* Kp_out);
+
+// Y (rows x cols float64) = (Hh + Hl) * diag(sqrt(colscale)): the matrix the
+// split operands represent exactly (colscale may be NULL).
+sks_status tc_unsplit(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, int rows, int cols,
+                      int Kp, const double* colscale, double* Y, long long ldy);
+
+// C = alpha * (Ah + Al)(Bh + Bl)^T + beta * C (float64 C, M x N); operands
+// M x Kp and N x Kp bfloat16 row-major; lower: only C's lower triangle (M == N).
+sks_status tc_gram(cudaStream_t stream, int M, int N, int Kp, const __nv_bfloat16* Ah, const __nv_bfloat16* Al,
+                   const __nv_bfloat16* Bh, const __nv_bfloat16* Bl, double alpha, double beta, double* C,
+                   long long ldc, bool lower, DevStatus* st);
+
+}  // namespace sks

@@ -15,6 +15,9 @@ reproduce bit for bit:
   (A - hi is exact in float32), so hi + lo carries ~16 significant bits.
 * ``gaussian_sketch_bf16``: Y = bf16(G) (hi + lo), with G the Gaussian
   entries of ``rng.gaussian_block`` rounded from float32.
+* ``split_rowscaled``: the operand split of the tensor-core Gram matrix:
+  every row is cut against its own maximum exponent into two slices of
+  integers (8 + 8 bits), so that all slice products are exactly summable.
 * ``refine``: the outer refinement loop around any inner solver.
 """
 import numpy as np
@@ -40,6 +43,25 @@ def split_hi_lo(A32):
     rem = (A32.astype(np.float64) - hi).astype(np.float32)  # exact
     lo = bf16_round(rem)
     return hi, lo
+
+
+def split_rowscaled(X32):
+    """Row-scaled two-slice split of a float32 matrix (float32 arithmetic).
+
+    For each row with maximum |x| = f 2^e (f in [0.5, 1), so |x| < 2^e):
+        hi = rint(x 2^(8-e)) 2^(e-8),  lo = rint((x - hi) 2^(16-e)) 2^(e-16)
+    (rint = round half to even).  hi holds integers of magnitude <= 256 and lo
+    integers <= 128 in their units, both exact in bfloat16, and
+    |x - hi - lo| <= 2^(e-17).  Returns float64 arrays (hi, lo)."""
+    X = np.asarray(X32, dtype=np.float32)
+    mx = np.max(np.abs(X), axis=1)
+    _, ex = np.frexp(mx)
+    ex = ex.astype(np.int32)[:, None]
+    hi = np.ldexp(np.rint(np.ldexp(X, 8 - ex)), ex - 8).astype(np.float32)
+    hi[mx == 0] = 0
+    lo = np.ldexp(np.rint(np.ldexp((X - hi).astype(np.float32), 16 - ex)), ex - 16).astype(np.float32)
+    lo[mx == 0] = 0
+    return hi.astype(np.float64), lo.astype(np.float64)
 
 
 def gaussian_bf16(n_rows_data, m_rows, seed):

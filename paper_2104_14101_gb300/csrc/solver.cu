@@ -58,6 +58,7 @@ struct sks_precond {
   double* t2 = nullptr;
   __nv_bfloat16* bf[4] = {nullptr, nullptr, nullptr, nullptr};  // split-bf16 operands (float32 sketches)
   size_t bf_elems = 0;
+  unsigned* rmax = nullptr;  // per-row maximum scratch of the split
   sks::DevStatus* st = nullptr;
 };
 
@@ -250,6 +251,7 @@ size_t precond_ws_bytes(const sks_problem* p, int64_t m_max) {
   if (p->dtype == SKS_F32) {
     const size_t e = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
     for (int i = 0; i < 4; ++i) c.take<__nv_bfloat16>(e + 64);
+    c.take<unsigned>(std::max<size_t>(d, (size_t)m_max));
   }
   return c.used + 256;
 }
@@ -275,6 +277,7 @@ sks_status precond_init(sks_precond* P, const sks_problem* p, int64_t m_max, voi
   if (p->dtype == SKS_F32) {
     P->bf_elems = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
     for (int i = 0; i < 4; ++i) P->bf[i] = c.take<__nv_bfloat16>(P->bf_elems + 64);
+    P->rmax = c.take<unsigned>(std::max<size_t>(d, (size_t)m_max));
   }
   if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "preconditioner workspace too small");
   return SKS_OK;
@@ -310,7 +313,7 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
   if (!P->woodbury) {
     if (tc) {
       int Kp = 0;
-      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, true, nullptr, P->bf[0], P->bf[1], &Kp));
+      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, true, nullptr, P->bf[0], P->bf[1], P->rmax, &Kp));
       SKS_TRY(tc_gram(stream, d, d, Kp, P->bf[0], P->bf[1], P->bf[0], P->bf[1], P->c2, 0.0, P->H, d, true, P->st));
     } else {
       SKS_TRY(gemm<double>(stream, d, d, m, Y64, ldy, true, Y64, ldy, false, P->H, d, P->c2, 0.0, true, 1, 0, 0, 0,
@@ -325,7 +328,7 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
       // uses Y_eff = Z' Lambda^{1/2}, so the preconditioner is exactly the
       // inverse of c^2 Y_eff^T Y_eff + nu^2 Lambda.
       int Kp = 0;
-      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, false, lam, P->bf[0], P->bf[1], &Kp));
+      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, false, lam, P->bf[0], P->bf[1], P->rmax, &Kp));
       SKS_TRY(tc_gram(stream, m, m, Kp, P->bf[0], P->bf[1], P->bf[0], P->bf[1], P->c2, 0.0, P->H, m, true, P->st));
       SKS_TRY(tc_unsplit(stream, P->bf[0], P->bf[1], m, d, Kp, lam, P->Y64, d));
     } else {

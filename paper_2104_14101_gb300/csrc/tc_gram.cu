@@ -1,26 +1,34 @@
 // tc_gram.cu -- K6 on the 5th-generation tensor cores: the sketched Gram
 // matrices of the preconditioner (Section 4.1.1),
 //     C = alpha * A B^T   (A: M x K, B: N x K, float32 in, float64 out),
-// i.e. H_S = c^2 Y^T Y (m >= d) or W_S = c^2 (Y Lambda^{-1}) Y^T (m < d).
+// i.e. H_S = c^2 Y^T Y (m >= d) or W_S = c^2 Z Z^T, Z = Y Lambda^{-1/2} (m < d).
 //
 // The preconditioner must resolve eigenvalues down to nu^2 ~ 1e-8 next to
-// entries of order 1, so the product is formed from a bfloat16 hi/lo split of
-// both operands, x = hi + lo (16 significant bits), using all four products
-// hi.hi + hi.lo + lo.hi + lo.lo (dropping lo.lo alone shifts the spectrum by
-// ~2^-16 |Y|^2, far above nu^2).  The tensor cores accumulate 64 K-elements in
-// float32 (products of bfloat16 are exact in float32); every 64-element chunk
-// is drained from TMEM and added into a double-float (float32 pair)
-// accumulator, which keeps the sum at ~48 bits.  float64 adds would be ~7x
-// slower than the MMAs on this part.
+// entries of order 1, and when m ~ d the sketched Gram is nearly singular, so
+// float32 rounding of the accumulation (~1e-7) is not acceptable.  The product
+// is therefore made EXACT for a 16-bit representation of the operands
+// (Ozaki-style splitting): every operand row x is split against its own
+// maximum exponent e (|x| < 2^e) into two bfloat16 slices holding integers
+//     hi = rint(x 2^(8-e)) 2^(e-8)         (|hi| <= 256 units of 2^(e-8))
+//     lo = rint((x - hi) 2^(16-e)) 2^(e-16) (|lo| <= 128 units of 2^(e-16)),
+// so x = hi + lo + O(2^(e-17)).  For an output entry (i, j) every hi.hi product
+// is an integer multiple of 2^(e_i+f_j-16) below 2^16 of those units, hi.lo and
+// lo.hi products multiples of 2^(e_i+f_j-24) below 2^15, lo.lo multiples of
+// 2^(e_i+f_j-32) below 2^14: sums of up to 256 K-elements of each class are
+// exact in float32.  The three classes accumulate in three TMEM accumulators
+// that are drained every 256 K-elements into a double-float (float32 pair)
+// sum (~48 bits; float64 adds would be far slower on this part).  The result
+// is the exact Gram of the rounded operands, so H_S' = c^2 Y'^T Y' + nu^2
+// Lambda is positive definite by construction.
 //
 // Structure (one CTA per 128 x 128 output tile, 18 warps):
 //   warp 0      TMA producer: Ah, Al, Bh, Bl tiles (128 rows x 64 bf16, 128B
 //               swizzle) into a 3-stage shared-memory ring;
 //   warp 1      MMA issuer: 16 tcgen05.mma (M=128, N=128, K=16) per stage into
-//               one of two TMEM accumulators; tcgen05.commit frees the stage
-//               and publishes the accumulator;
-//   warps 2-17  epilogue: tcgen05.ld the accumulator (each warp: its 32 TMEM
-//               lanes x 32 columns), double-float accumulate, release it;
+//               the three accumulators; tcgen05.commit frees the stage, and
+//               after each group of 4 stages publishes the accumulators;
+//   warps 2-17  epilogue: tcgen05.ld the accumulators (each warp: its 32 TMEM
+//               lanes x 32 columns), double-float accumulate, release them;
 //               at the end write alpha * (hi + lo) in float64.
 // Every mbarrier wait is bounded; a timed-out role flags the CTA, all roles
 // leave their loops, wait (bounded) for their own asynchronous work, and the
@@ -41,7 +49,8 @@ constexpr int kTileBytes = TBM * TBK * 2;     // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTileBytes;   // Ah, Al, Bh, Bl
 constexpr int kEpiWarps = 16;                 // 4 per TMEM lane quadrant, 32 columns each
 constexpr int kTcThreads = (2 + kEpiWarps) * 32;
-constexpr uint32_t kTmemCols = 256;           // two 128-column float32 accumulators
+constexpr uint32_t kTmemCols = 512;           // three 128-column float32 accumulators (hh, hl+lh, ll)
+constexpr int kGroup = 4;                     // stages per exact accumulation group (4 x 64 = 256 K)
 
 // ------------------------------------------------------------------ PTX wrappers
 SKS_DEV uint64_t smem_desc_sw128(const void* tile) {
@@ -186,40 +195,48 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(TBM, TBN);
-      int committed = 0;
-      for (int kk = 0; kk < nk; ++kk) {
-        const int s = kk % kStagesTC;
-        const int b = kk & 1;
-        if (abort_flag || !mbar_wait(&full[s], (uint32_t)(kk / kStagesTC) & 1u, g.st, 43) ||
-            !mbar_wait(&acc_empty[b], ((uint32_t)(kk >> 1) & 1u) ^ 1u, g.st, 44)) {
+      const int ngroups = (nk + kGroup - 1) / kGroup;
+      int committed = -1;
+      for (int grp = 0; grp < ngroups && !abort_flag; ++grp) {
+        // the epilogue has drained the previous group
+        if (!mbar_wait(&acc_empty[0], ((uint32_t)grp & 1u) ^ 1u, g.st, 44)) {
           abort_flag = 1;
           break;
         }
         tc_fence_after();
-        unsigned char* st = smem + (size_t)s * kStageBytes;
-        const uint32_t d_tmem = tmem + (uint32_t)(b * TBN);
-        // products: (Ah,Bh) (Ah,Bl) (Al,Bh) (Al,Bl)
-        uint32_t acc = 0;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const uint64_t ad = smem_desc_sw128(st + (p >> 1) * kTileBytes);
-          const uint64_t bd = smem_desc_sw128(st + (2 + (p & 1)) * kTileBytes);
-#pragma unroll
-          for (int k = 0; k < TBK / 16; ++k) {
-            // advance 16 bf16 = 32 bytes along K inside the swizzle atom
-            umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, acc);
-            acc = 1;
+        const int k_end = min(nk, (grp + 1) * kGroup);
+        for (int kk = grp * kGroup; kk < k_end; ++kk) {
+          const int s = kk % kStagesTC;
+          if (abort_flag || !mbar_wait(&full[s], (uint32_t)(kk / kStagesTC) & 1u, g.st, 43)) {
+            abort_flag = 1;
+            break;
           }
+          tc_fence_after();
+          unsigned char* st = smem + (size_t)s * kStageBytes;
+          const bool first = (kk == grp * kGroup);
+          // products: (Ah,Bh) -> acc 0; (Ah,Bl), (Al,Bh) -> acc 1; (Al,Bl) -> acc 2
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int accn = (p == 0) ? 0 : (p == 3 ? 2 : 1);
+            const uint64_t ad = smem_desc_sw128(st + (p >> 1) * kTileBytes);
+            const uint64_t bd = smem_desc_sw128(st + (2 + (p & 1)) * kTileBytes);
+            const uint32_t d_tmem = tmem + (uint32_t)(accn * TBN);
+#pragma unroll
+            for (int k = 0; k < TBK / 16; ++k) {
+              // advance 16 bf16 = 32 bytes along K inside the swizzle atom;
+              // the first MMA of a group into an accumulator overwrites it
+              const uint32_t acc = (first && k == 0 && p != 2) ? 0u : 1u;
+              umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, acc);
+            }
+          }
+          umma_commit(&empty[s]);  // stage reusable once these MMAs finish
         }
-        umma_commit(&empty[s]);     // stage reusable once these MMAs finish
-        umma_commit(&acc_full[b]);  // accumulator b ready for the epilogue
-        committed = kk + 1;
+        if (abort_flag) break;
+        umma_commit(&acc_full[0]);  // group complete: accumulators ready
+        committed = grp;
       }
       // wait (bounded) for the last committed MMA group before leaving
-      if (committed > 0) {
-        const int k = committed - 1;
-        mbar_wait(&acc_full[k & 1], (uint32_t)(k >> 1) & 1u, g.st, 45);
-      }
+      if (committed >= 0) mbar_wait(&acc_full[0], (uint32_t)committed & 1u, g.st, 45);
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 2..17)
@@ -227,28 +244,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int quad = warp & 3;          // TMEM lane quadrant this warp may access
     const int cblk = ew >> 2;           // columns [32*cblk, 32*cblk + 32)
     const int row = quad * 32 + lane;   // tile row held by this thread
+    const int ngroups = (nk + kGroup - 1) / kGroup;
     float hi[32], lo[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0.f;
-    for (int kk = 0; kk < nk; ++kk) {
-      const int b = kk & 1;
-      const bool ok = mbar_wait_warp(&acc_full[b], (uint32_t)(kk >> 1) & 1u, g.st, 46);
+    for (int grp = 0; grp < ngroups; ++grp) {
+      const bool ok = mbar_wait_warp(&acc_full[0], (uint32_t)grp & 1u, g.st, 46);
       if (!ok || abort_flag) {
         if (lane == 0) abort_flag = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TBN + cblk * 32);
-      float v[16];
-      tmem_ld16(base, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) df_add(hi[i], lo[i], v[i]);
-      tmem_ld16(base + 16, v);
+      for (int accn = 0; accn < 3; ++accn) {
+        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(accn * TBN + cblk * 32);
+        float v[16];
+        tmem_ld16(base, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) df_add(hi[16 + i], lo[16 + i], v[i]);
+        for (int i = 0; i < 16; ++i) df_add(hi[i], lo[i], v[i]);
+        tmem_ld16(base + 16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) df_add(hi[16 + i], lo[16 + i], v[i]);
+      }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      if (lane == 0) mbar_arrive(&acc_empty[0]);
     }
     const int gi = row0 + row;
     if (!abort_flag && gi < g.M) {
@@ -271,27 +291,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-// X (rows x cols, ld) float32 -> hi/lo bfloat16, row-major (out_rows x Kp),
-// optional transpose (out row = input column) and column scaling
-// 1/sqrt(scale[c]) (computed in float64, rounded once to float32).
-__global__ void split_bf16_kernel(const float* __restrict__ X, long long ldx, int rows, int cols, int transpose,
-                                  const double* __restrict__ colscale, int out_rows, int Kp,
-                                  __nv_bfloat16* __restrict__ Hh, __nv_bfloat16* __restrict__ Hl) {
+// Operand element (orow, k) of X (transpose: X[k][orow], else X[orow][k]),
+// divided by sqrt(colscale[c]) in float64 and rounded once to float32.
+__device__ __forceinline__ float operand_elem(const float* __restrict__ X, long long ldx, int rows, int cols,
+                                             int transpose, const double* __restrict__ colscale, int orow, int k) {
+  const int r = transpose ? k : orow;
+  const int c = transpose ? orow : k;
+  if (r >= rows || c >= cols) return 0.f;
+  float v = X[(long long)r * ldx + c];
+  if (colscale) v = (float)((double)v / sqrt(colscale[c]));
+  return v;
+}
+
+// Maximum |element| of every operand row (as float bits; non-negative floats
+// order like their bit patterns).  Grid-stride over the input in its own
+// layout, so reads are coalesced for both orientations.
+__global__ void rowmax_kernel(const float* __restrict__ X, long long ldx, int rows, int cols, int transpose,
+                              const double* __restrict__ colscale, unsigned* __restrict__ rmax) {
+  const long long total = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e % cols);
+    const int orow = transpose ? c : r, k = transpose ? r : c;
+    const float v = fabsf(operand_elem(X, ldx, rows, cols, transpose, colscale, orow, k));
+    atomicMax(&rmax[orow], __float_as_uint(v));
+  }
+}
+
+// hi/lo slices against the row's maximum exponent (see the file comment).
+__global__ void split_scaled_kernel(const float* __restrict__ X, long long ldx, int rows, int cols, int transpose,
+                                    const double* __restrict__ colscale, const unsigned* __restrict__ rmax,
+                                    int out_rows, int Kp, __nv_bfloat16* __restrict__ Hh,
+                                    __nv_bfloat16* __restrict__ Hl) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)out_rows * Kp) return;
   const int orow = (int)(e / Kp), k = (int)(e % Kp);
-  // input coordinates
-  const int r = transpose ? k : orow;
-  const int c = transpose ? orow : k;
-  float v = 0.f;
-  if (r < rows && c < cols) {
-    v = X[(long long)r * ldx + c];
-    if (colscale) v = (float)((double)v / sqrt(colscale[c]));
+  const float v = operand_elem(X, ldx, rows, cols, transpose, colscale, orow, k);
+  const float mx = __uint_as_float(rmax[orow]);
+  float h = 0.f, l = 0.f;
+  if (mx > 0.f) {
+    int ex;
+    frexpf(mx, &ex);  // mx < 2^ex
+    h = ldexpf(rintf(ldexpf(v, 8 - ex)), ex - 8);
+    l = ldexpf(rintf(ldexpf(v - h, 16 - ex)), ex - 16);
   }
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  const float rem = v - __bfloat162float(h);
-  Hh[e] = h;
-  Hl[e] = __float2bfloat16_rn(rem);
+  Hh[e] = __float2bfloat16_rn(h);  // exact: integers below 2^9 times a power of two
+  Hl[e] = __float2bfloat16_rn(l);
 }
 
 // Y_eff[r][c] = (hi + lo)[r][c] * sqrt(scale[c])  (float64), the sketch that
@@ -327,14 +372,19 @@ size_t tc_gram_split_elems(int out_rows, int K) {
 }
 
 sks_status tc_split(cudaStream_t stream, const float* X, long long ldx, int rows, int cols, bool transpose,
-                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, int* Kp_out) {
+                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, unsigned* rmax, int* Kp_out) {
   const int out_rows = transpose ? cols : rows;
   const int K = transpose ? rows : cols;
   const int Kp = (K + TBK - 1) / TBK * TBK;
   const long long total = (long long)out_rows * Kp;
   if (total > 0) {
-    split_bf16_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(X, ldx, rows, cols, transpose ? 1 : 0,
-                                                                           colscale, out_rows, Kp, Hh, Hl);
+    SKS_CUDA_TRY(cudaMemsetAsync(rmax, 0, (size_t)out_rows * sizeof(unsigned), stream));
+    const long long in_total = (long long)rows * cols;
+    const unsigned g1 = (unsigned)std::max<long long>(1, std::min<long long>((in_total + 255) / 256, 4096));
+    rowmax_kernel<<<g1, 256, 0, stream>>>(X, ldx, rows, cols, transpose ? 1 : 0, colscale, rmax);
+    note_launch();
+    split_scaled_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(
+        X, ldx, rows, cols, transpose ? 1 : 0, colscale, rmax, out_rows, Kp, Hh, Hl);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
   }

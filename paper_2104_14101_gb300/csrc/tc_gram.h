@@ -10,12 +10,14 @@ namespace sks {
 // Elements of one hi (or lo) buffer for an operand of out_rows x K.
 size_t tc_gram_split_elems(int out_rows, int K);
 
-// X (rows x cols float32, leading dimension ldx) -> bfloat16 hi/lo buffers of
+// X (rows x cols float32, leading dimension ldx) -> bfloat16 hi/lo slices of
 // shape out_rows x Kp (Kp = K rounded up to 64, zero padded), where the
 // operand is X (out_rows = rows, K = cols) or X^T (transpose: out_rows =
 // cols, K = rows); optional division of column c of X by sqrt(colscale[c]).
+// Each operand row is split against its own maximum exponent so that the
+// tensor-core products are exact (tc_gram.cu).  rmax: out_rows scratch words.
 sks_status tc_split(cudaStream_t stream, const float* X, long long ldx, int rows, int cols, bool transpose,
-                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, int* Kp_out);
+                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, unsigned* rmax, int* Kp_out);
 
 // Y (rows x cols float64) = (Hh + Hl) * diag(sqrt(colscale)): the matrix the
 // split operands represent exactly (colscale may be NULL).

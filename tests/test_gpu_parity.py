@@ -260,28 +260,30 @@ def test_gpu_generator_matches_spectrum():
 @pytest.mark.parametrize("m,d", [(300, 256), (100, 300), (700, 520), (1, 64), (129, 200), (64, 64)])
 def test_tensor_core_preconditioner_matches_split_oracle(m, d):
     # float32 sketches build H_S (m >= d) or W_S (m < d) on the tensor cores
-    # from a bfloat16 hi/lo split.  The oracle rebuilds the same split
-    # operands bit for bit (Z = Y Lambda^{-1/2} rounded to float32 for the
-    # Woodbury form), so the only difference left is accumulation rounding.
+    # from a row-scaled two-slice bfloat16 split whose products sum exactly.
+    # The oracle rebuilds the same slices bit for bit (the Gram operand is
+    # Y^T, split per column of Y; the Woodbury operand is Z = Y Lambda^{-1/2}
+    # rounded to float32, split per row), so the preconditioners agree to the
+    # double-float accumulation accuracy.
     from oracle import mixed as MX
     rng = np.random.default_rng(m * 7 + d)
     n = 3000
     A = (rng.standard_normal((n, d)) * (0.9 ** np.arange(d))[None, :]).astype(np.float32).astype(np.float64)
     lam = 1 + 9 * rng.random(d)
-    nu = 0.3
+    nu = 1e-3
     sk = api().Sketch(dev(A, torch.float32), nu, dev(lam), kind="gaussian", m=m, seed=6)
     c = 1.0 / math.sqrt(m)
     Y32 = (host(sk.matrix()) / c).astype(np.float32)
     if m < d:
         Z32 = (Y32.astype(np.float64) / np.sqrt(lam)[None, :]).astype(np.float32)
-        zh, zl = MX.split_hi_lo(Z32)
+        zh, zl = MX.split_rowscaled(Z32)
         Yeff = (zh + zl) * np.sqrt(lam)[None, :]
     else:
-        yh, yl = MX.split_hi_lo(Y32)
-        Yeff = yh + yl
+        th, tl = MX.split_rowscaled(Y32.T)
+        Yeff = (th + tl).T
     ref_P = O.Preconditioner(c * Yeff, nu, lam)
     P = api().Preconditioner(sk)
     Z = rng.standard_normal((d, 2))
     got = host(P.apply(dev(Z)))
     ref = ref_P.apply(Z)
-    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-5
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-8

@@ -85,3 +85,28 @@ def test_refine_reaches_tolerance_with_inexact_inner():
     x, outer = MX.refine(p.A, p.b, p.nu, p.lam, inner, tol=1e-10)
     assert outer > 1
     assert S.rel_err_H(p.A, p.nu, p.lam, x, xs) <= 1e-10
+
+
+def test_split_rowscaled_exactness():
+    # The slices are bfloat16-exact integers in their row units, the remainder
+    # is below 2^(e-17), and every class of slice products sums exactly in
+    # float32 over 256 terms (the property the tensor-core Gram relies on).
+    rng = np.random.default_rng(3)
+    X = (rng.standard_normal((40, 300)) * np.exp(rng.uniform(-20, 20, size=(40, 1)))).astype(np.float32)
+    X[5] = 0
+    hi, lo = MX.split_rowscaled(X)
+    assert np.array_equal(MX.bf16_round(hi.astype(np.float32)), hi)
+    assert np.array_equal(MX.bf16_round(lo.astype(np.float32)), lo)
+    mx = np.max(np.abs(X), axis=1)
+    _, e = np.frexp(mx)
+    e = e[:, None]
+    assert np.all(np.abs(np.ldexp(hi, 8 - e)) <= 256) and np.all(np.abs(np.ldexp(lo, 16 - e)) <= 128)
+    assert np.all(np.abs(X.astype(np.float64) - hi - lo) <= np.ldexp(1.0, e - 17))
+    assert np.all(hi[5] == 0) and np.all(lo[5] == 0)
+    # exact float32 sums of 256 products of each class
+    for a, b in ((hi, hi), (hi, lo), (lo, lo)):
+        p32 = (a[0, :256].astype(np.float32) * b[1, :256].astype(np.float32))
+        s32 = np.float32(0)
+        for v in p32:
+            s32 = np.float32(s32 + v)
+        assert float(s32) == float(np.sum(a[0, :256] * b[1, :256]))

@@ -234,6 +234,24 @@ sks_status sks_adaptive_pcg_solve(const sks_problem* p, const sks_opts* o, doubl
 sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
                                   void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Adjoint of the solve (gradients of x*(A, b, nu, Lambda), implicit
+ * differentiation of H x = b, eq. 1).  For an upstream gradient g = dL/dx
+ * (d x k, device float64) the adjoint solve gives u = H^{-1} g and
+ *   db = u,   dA = -A (u x^T + x u^T)   (summed over the k columns),
+ *   dnu = -2 nu sum_k u_k^T Lambda x_k,   dlambda_i = -nu^2 sum_k u_ik x_ik.
+ * Must be called with the workspace of a preceding sks_adaptive_pcg_solve (or
+ * _ihs_) of the same problem and options: the adjoint solve reuses the sketch
+ * and factored preconditioner left there (adaptive PCG continues from its
+ * final m), and SKS_ERR_INVALID_ARG is returned if the workspace holds none.
+ * x: the forward solution (d x k).  db (required, d x k float64), dA (optional,
+ * n x d in the precision of A, leading dimension ldda), dnu (optional, host
+ * double), dlambda (optional, device d float64).  k <= 8 when dA is asked for.
+ * ------------------------------------------------------------------------- */
+sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g, double* db,
+                       void* dA, int64_t ldda, double* dnu, double* dlambda, sks_stats* stats,
+                       void* ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,10 +8,12 @@ from . import _lib  # noqa: F401
 from .api import (  # noqa: F401
     Preconditioner,
     Sketch,
+    SketchSolve,
     Solver,
     adaptive_ihs,
     adaptive_pcg,
     hess_apply,
     make_problem,
     options,
+    sketch_solve,
 )

@@ -76,6 +76,8 @@ _SIGS = {
                                          C.c_void_p]),
     "sks_adaptive_ihs_solve": (C.c_int, [P(Problem), P(Opts), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t,
                                          C.c_void_p]),
+    "sks_adjoint": (C.c_int, [P(Problem), P(Opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                              P(C.c_double), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t, C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

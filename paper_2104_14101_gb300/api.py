@@ -226,6 +226,56 @@ class Solver:
         return x, stats, trace
 
 
+    def adjoint(self, x, g, want_A=True):
+        """Gradients for upstream g = dL/dx at the solution x of the last
+        ``solve`` (same workspace, same preconditioner): returns
+        (dA, db, dnu, dlam) with dA in A's precision (None if not wanted)."""
+        A = self._keep[0]
+        gcm = (g.to(torch.float64)[:, None] if g.dim() == 1 else g.to(torch.float64)).t().contiguous()
+        xcm = (x.to(torch.float64)[:, None] if x.dim() == 1 else x.to(torch.float64)).t().contiguous()
+        dbcm = torch.empty_like(gcm)
+        dA = torch.empty(A.shape, dtype=A.dtype, device=self.device) if want_A else None
+        dlam = torch.empty(self.d, dtype=torch.float64, device=self.device)
+        dnu = C.c_double(0.0)
+        st = L.Stats()
+        L.check(self._lib.sks_adjoint(C.byref(self.problem), C.byref(self.opts), _ptr(xcm), _ptr(gcm), _ptr(dbcm),
+                                      _ptr(dA), int(dA.stride(0)) if dA is not None else 0, C.byref(dnu),
+                                      _ptr(dlam), C.byref(st), _ptr(self.ws), self.ws.numel(),
+                                      _stream(self.device)))
+        db = dbcm.t()
+        db = db[:, 0] if self.k == 1 else db.contiguous()
+        return dA, db, dnu.value, dlam
+
+
+class SketchSolve(torch.autograd.Function):
+    """x = argmin 1/2 <x, H x> - b^T x with H = A^T A + nu^2 diag(lam), solved by
+    the adaptive sketching solver; backward is the adjoint solve with the same
+    preconditioner plus the fused dA pass (``sks_adjoint``)."""
+
+    @staticmethod
+    def forward(ctx, A, b, nu, lam, opts):
+        nu_val = float(nu)
+        solver = Solver(A.detach(), b.detach(), nu_val, lam.detach(), **(opts or {}))
+        x, stats, _ = solver.solve()
+        ctx.solver = solver
+        ctx.nu_is_tensor = torch.is_tensor(nu)
+        ctx.save_for_backward(x)
+        ctx.stats = stats
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        dA, db, dnu, dlam = ctx.solver.adjoint(x, gx.contiguous(), want_A=ctx.needs_input_grad[0])
+        gnu = torch.tensor(dnu, dtype=torch.float64, device=x.device) if ctx.nu_is_tensor else None
+        return dA, db, gnu, dlam, None
+
+
+def sketch_solve(A, b, nu, lam, **opts):
+    """Differentiable adaptive solve (see ``SketchSolve``)."""
+    return SketchSolve.apply(A, b, nu, lam, opts)
+
+
 def adaptive_pcg(A, b, nu, lam, x0=None, trace_cap=0, **opts):
     """Algorithm 2 on the GPU; returns (x, stats, trace)."""
     return Solver(A, b, nu, lam, method="pcg", trace_cap=trace_cap, **opts).solve(x0)

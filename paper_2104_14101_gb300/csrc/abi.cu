@@ -48,3 +48,9 @@ extern "C" sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opt
                                              void* ws, size_t ws_bytes, void* stream) {
   return adaptive_solve(1, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
 }
+
+extern "C" sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g,
+                                  double* db, void* dA, int64_t ldda, double* dnu, double* dlambda, sks_stats* stats,
+                                  void* ws, size_t ws_bytes, void* stream) {
+  return adjoint(p, o, x, g, db, dA, ldda, dnu, dlambda, stats, ws, ws_bytes, (cudaStream_t)stream);
+}

@@ -323,6 +323,31 @@ sks_status add_diagonal(cudaStream_t stream, int n, double* M, long long ld, dou
   return SKS_OK;
 }
 
+__global__ void lower_to_f32_kernel(int n, const double* __restrict__ H, long long ldh, float* __restrict__ L,
+                                    long long ldl) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  L[(long long)i * ldl + j] = (j <= i) ? (float)H[(long long)i * ldh + j] : 0.f;
+}
+
+__global__ void f32_to_f64_mat_kernel(int n, const float* __restrict__ S, long long lds, double* __restrict__ D,
+                                      long long ldd) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  D[(long long)i * ldd + j] = (double)S[(long long)i * lds + j];
+}
+
+__global__ void dinv_to_f32_kernel(int n, int nblk, const double* __restrict__ dinv, float* __restrict__ X,
+                                   long long ldx) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)nblk * 64 * 64) return;
+  const int kb = (int)(e / (64 * 64)), r = (int)((e / 64) % 64), c = (int)(e % 64);
+  const int i = kb * 64 + r, j = kb * 64 + c;
+  if (i < n && j < n) X[(long long)i * ldx + j] = (float)dinv[e];
+}
+
 size_t cholesky_ws_elems(int n) {
   // diagonal-block inverses + split-K partials of the trailing updates
   const int nblk = (n + NB - 1) / NB;
@@ -332,7 +357,7 @@ size_t cholesky_ws_elems(int n) {
 // In-place blocked right-looking Cholesky H = L L^T (lower; upper set to 0),
 // then X = L^{-1} by recursive block inversion.  ws: cholesky_ws_elems(n).
 sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long ldh, double* X, long long ldx,
-                                double* ws, DevStatus* st) {
+                                double* ws, DevStatus* st, float* ws32) {
   if (n <= 0) return SKS_OK;
   const int nblk = (n + NB - 1) / NB;
   double* dinv = ws;                              // nblk * NB * NB
@@ -369,23 +394,57 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
                                    NB * sizeof(double), nb * sizeof(double), nb, cudaMemcpyDeviceToDevice, stream));
   }
   // inv([A 0; B C]) = [A^-1 0; -C^-1 B A^-1  C^-1]
+  if (ws32 == nullptr) {
+    for (int b = NB; b < n; b *= 2) {
+      for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
+        const int n1 = b, n2 = std::min(b, n - r0 - b);
+        const double* Binv_A = X + (long long)r0 * ldx + r0;          // A^{-1}: n1 x n1
+        const double* Lb = H + (long long)(r0 + b) * ldh + r0;        // B: n2 x n1
+        const double* Cinv = X + (long long)(r0 + b) * ldx + (r0 + b);  // C^{-1}: n2 x n2
+        double* out = X + (long long)(r0 + b) * ldx + r0;             // n2 x n1
+        double* tmp = split;                                          // n2 x n1
+        const size_t rest_elems = split_elems - (size_t)n2 * n1;
+        SKS_TRY(gemm<double>(stream, n2, n1, n1, Lb, ldh, false, Binv_A, ldx, false, tmp, n1, 1.0, 0.0, false, 1, 0,
+                             0, 0, split + (size_t)n2 * n1, rest_elems));
+        SKS_TRY(gemm<double>(stream, n2, n1, n2, Cinv, ldx, false, tmp, n1, false, out, ldx, -1.0, 0.0, false, 1, 0,
+                             0, 0, split + (size_t)n2 * n1, rest_elems));
+      }
+    }
+    return SKS_OK;
+  }
+  // float32 merge (the preconditioner only needs the inverse factor to be a
+  // close nonsingular approximation; the operator X^T X stays SPD)
+  float* L32 = ws32;
+  float* X32 = ws32 + (size_t)n * n;
+  float* tmp32 = ws32 + (size_t)2 * n * n;
+  const size_t rest32 = (size_t)n * n;  // split-K partials beyond the n x n/2 tmp block
+  const long long nn = (long long)n * n;
+  lower_to_f32_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(n, H, ldh, L32, n);
+  note_launch();
+  SKS_CUDA_TRY(cudaMemsetAsync(X32, 0, (size_t)n * n * sizeof(float), stream));
+  dinv_to_f32_kernel<<<(unsigned)(((long long)nblk * 64 * 64 + 255) / 256), 256, 0, stream>>>(n, nblk, dinv, X32, n);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
   for (int b = NB; b < n; b *= 2) {
     for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
       const int n1 = b, n2 = std::min(b, n - r0 - b);
-      const double* Binv_A = X + (long long)r0 * ldx + r0;          // A^{-1}: n1 x n1
-      const double* Lb = H + (long long)(r0 + b) * ldh + r0;        // B: n2 x n1
-      const double* Cinv = X + (long long)(r0 + b) * ldx + (r0 + b);  // C^{-1}: n2 x n2
-      double* out = X + (long long)(r0 + b) * ldx + r0;             // n2 x n1
-      double* tmp = split;                                          // n2 x n1
-      const size_t rest_elems = split_elems - (size_t)n2 * n1;
-      SKS_TRY(gemm<double>(stream, n2, n1, n1, Lb, ldh, false, Binv_A, ldx, false, tmp, n1, 1.0, 0.0, false, 1, 0, 0,
-                           0, split + (size_t)n2 * n1, rest_elems));
-      SKS_TRY(gemm<double>(stream, n2, n1, n2, Cinv, ldx, false, tmp, n1, false, out, ldx, -1.0, 0.0, false, 1, 0, 0,
-                           0, split + (size_t)n2 * n1, rest_elems));
+      const float* Ainv = X32 + (long long)r0 * n + r0;
+      const float* Lb = L32 + (long long)(r0 + b) * n + r0;
+      const float* Cinv = X32 + (long long)(r0 + b) * n + (r0 + b);
+      float* out = X32 + (long long)(r0 + b) * n + r0;
+      SKS_TRY(gemm<float>(stream, n2, n1, n1, Lb, n, false, Ainv, n, false, tmp32, n1, 1.0, 0.0, false, 1, 0, 0, 0,
+                          tmp32 + (size_t)n2 * n1, rest32));
+      SKS_TRY(gemm<float>(stream, n2, n1, n2, Cinv, n, false, tmp32, n1, false, out, n, -1.0, 0.0, false, 1, 0, 0, 0,
+                          tmp32 + (size_t)n2 * n1, rest32));
     }
   }
+  f32_to_f64_mat_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(n, X32, n, X, ldx);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }
+
+size_t cholesky_ws32_elems(int n) { return (size_t)4 * n * n + 64; }
 
 template <typename T>
 sks_status gemv_rows(cudaStream_t stream, int rows, int cols, const T* M, long long ldm, int tri, const double* x,

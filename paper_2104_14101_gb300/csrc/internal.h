@@ -95,6 +95,12 @@ sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t*
 // method 0: adaptive PCG (Algorithm 2); 1: adaptive IHS (Algorithm 1)
 sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
                           size_t ws_bytes, cudaStream_t stream);
+sks_status adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g, double* db, void* dA,
+                   long long ldda, double* dnu, double* dlambda, sks_stats* stats, void* ws, size_t ws_bytes,
+                   cudaStream_t stream);
+// adjoint.cu: gradients from x and u = H^{-1} g (device pointers, d x k column-major)
+sks_status adjoint_grads(cudaStream_t stream, const sks_problem* p, const double* x, const double* u, void* dA,
+                         long long ldda, double* dnu_dev, double* dlambda);
 sks_status hess_apply_ws(const sks_problem* p, size_t* bytes);
 sks_status hess_apply(const sks_problem* p, const double* x, double* y, int extended, void* ws, size_t ws_bytes,
                       cudaStream_t stream);

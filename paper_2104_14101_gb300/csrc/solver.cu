@@ -59,6 +59,7 @@ struct sks_precond {
   __nv_bfloat16* bf[4] = {nullptr, nullptr, nullptr, nullptr};  // split-bf16 operands (float32 sketches)
   size_t bf_elems = 0;
   unsigned* rmax = nullptr;  // per-row maximum scratch of the split
+  float* inv32 = nullptr;    // float32 inverse-factor scratch (float32 problems)
   sks::DevStatus* st = nullptr;
 };
 
@@ -252,12 +253,13 @@ size_t precond_ws_bytes(const sks_problem* p, int64_t m_max) {
     const size_t e = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
     for (int i = 0; i < 4; ++i) c.take<__nv_bfloat16>(e + 64);
     c.take<unsigned>(std::max<size_t>(d, (size_t)m_max));
+    c.take<float>(cholesky_ws32_elems((int)d));
   }
   return c.used + 256;
 }
 
 sks_status precond_init(sks_precond* P, const sks_problem* p, int64_t m_max, void* ws, size_t ws_bytes,
-                        DevStatus* shared_st) {
+                        DevStatus* shared_st, bool f32_inverse = false) {
   const size_t d = (size_t)p->d;
   Carver c(ws, ws_bytes);
   DevStatus* own = c.take<DevStatus>(1);
@@ -278,6 +280,8 @@ sks_status precond_init(sks_precond* P, const sks_problem* p, int64_t m_max, voi
     P->bf_elems = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
     for (int i = 0; i < 4; ++i) P->bf[i] = c.take<__nv_bfloat16>(P->bf_elems + 64);
     P->rmax = c.take<unsigned>(std::max<size_t>(d, (size_t)m_max));
+    float* w32 = c.take<float>(cholesky_ws32_elems((int)d));
+    P->inv32 = f32_inverse ? w32 : nullptr;
   }
   if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "preconditioner workspace too small");
   return SKS_OK;
@@ -320,7 +324,7 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
                            P->split, P->split_elems));
     }
     SKS_TRY(add_diagonal(stream, d, P->H, d, 0.0, lam, P->nu2));
-    SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st));
+    SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st, P->inv32));
     SKS_TRY(transpose<double>(stream, d, d, P->X, d, P->Xt, d));
   } else {
     if (tc) {
@@ -339,7 +343,7 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
                            P->split, P->split_elems));
     }
     SKS_TRY(add_diagonal(stream, m, P->H, m, P->nu2, nullptr, 0.0));
-    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st));
+    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st, P->inv32));
     SKS_TRY(transpose<double>(stream, m, m, P->X, m, P->Xt, m));
     SKS_TRY(transpose<double>(stream, m, d, Y64, ldy, P->Yt, m));
   }
@@ -531,7 +535,18 @@ __global__ void __launch_bounds__(kStepThreads) dot_kernel(int d, const double* 
 }
 
 // ---------------------------------------------------------------- solve workspace
+// Record left at the head of a solve workspace so that a later call on the
+// same workspace (the adjoint solve) can reuse the sketch and preconditioner.
+struct SolveState {
+  uint64_t magic;
+  int64_t n, d, m;
+  int dtype, precision, kind, sjlt_s;
+  uint64_t seed;
+};
+constexpr uint64_t kStateMagic = 0x736b73737461746full;
+
 struct SolveWs {
+  SolveState* state;
   DevStatus* st;
   Ctl* ctl;
   double* scal;  // [0] = b^T x of the outer iterate
@@ -554,6 +569,7 @@ sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_
   const bool mixed = o->precision == SKS_MIXED_REFINED;
   Carver c(ws, ws_bytes);
   SolveWs w;
+  w.state = c.take<SolveState>(1);
   w.st = c.take<DevStatus>(1);
   w.ctl = c.take<Ctl>(1);
   w.scal = c.take<double>(4);
@@ -666,8 +682,27 @@ struct Engine {
       if (pr->n > 0) SKS_TRY(map_for(pr, &tmap64, plan64));
     }
     SKS_TRY(sketch_init(&sk, pr, op->kind, m_max, op->sjlt_s, op->seed, W.sketch_ws, W.sketch_bytes, W.st));
-    SKS_TRY(precond_init(&P, pr, m_max, W.precond_ws, W.precond_bytes, W.st));
+    // the mixed form forms the inverse Cholesky factor in float32
+    SKS_TRY(precond_init(&P, pr, m_max, W.precond_ws, W.precond_bytes, W.st, mixed));
     return SKS_OK;
+  }
+
+  // Re-attach the sketch (m rows) and the factored preconditioner that a
+  // previous solve left in this workspace.
+  void restore(int64_t m_prev) {
+    m = m_prev;
+    sk.m = m_prev;
+    P.m = m_prev;
+    P.woodbury = m_prev < d;
+    P.nu2 = nu2;
+    P.c2 = sk.scale2();
+    P.lam = prob->lambda_diag;
+    if (sk.f32) {
+      P.ldy64 = d;
+    } else {
+      P.Y64 = (double*)sk.Y;
+      P.ldy64 = sk.ldy;
+    }
   }
 
   // y = sgn * H x + addc * addv in the iteration's precision (one pass over A).
@@ -879,30 +914,19 @@ sks_status check_opts(const sks_problem* prob, const sks_opts* o, const double* 
   return SKS_OK;
 }
 
-sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks_opts* o, double* x_io,
-                               sks_stats* stats, void* ws, size_t ws_bytes, cudaStream_t stream) {
-  SKS_TRY(check_opts(prob, o, x_io));
-  const int d = (int)prob->d;
-  size_t need = 0;
-  SKS_TRY(solve_layout(prob, o, nullptr, 0, nullptr, &need));
-  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "solve workspace too small (need " + std::to_string(need) + " bytes)");
-  Engine E;
-  Timer t_total(stream), t_sketch(stream), t_factor(stream);
-  E.t_sketch = &t_sketch;
-  E.t_factor = &t_factor;
-  t_total.start();
-  SKS_TRY(E.init(method, prob, o, ws, ws_bytes, stream));
-  SKS_CUDA_TRY(cudaMemsetAsync(E.W.st, 0, sizeof(DevStatus), stream));
-  check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, E.W.st);
-  note_launch();
-  SKS_TRY(read_status(E.W.st, stream, "input check"));
-  SKS_TRY(E.first_sketch());
+// Solve H X = B column by column with the engine's current sketch and
+// preconditioner (X holds x_0 on entry).
+sks_status solve_columns(Engine& E, const double* B, double* X_io) {
+  const sks_problem* prob = E.prob;
+  const sks_opts* o = E.o;
+  cudaStream_t stream = E.stream;
+  const int d = E.d;
   const double tol2 = (o->tol / 2.0) * (o->tol / 2.0);
-  const double fac = method == PCG ? 1.0 : 2.0;
+  const double fac = E.method == PCG ? 1.0 : 2.0;
   sks_status result = SKS_OK;
   for (int64_t col = 0; col < prob->k && result == SKS_OK; ++col) {
-    const double* b = prob->b + col * d;
-    double* xcol = x_io + col * d;
+    const double* b = B + col * d;
+    double* xcol = X_io + col * d;
     bool converged = false;
     double dt0 = 0;
     Ctl h;
@@ -911,7 +935,7 @@ sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks
       SKS_CUDA_TRY(cudaMemcpyAsync(E.W.x, xcol, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
       sks_status r = E.inner(b, tol2, 0.0, o->max_iter, &converged, &dt0, &h);
       SKS_CUDA_TRY(cudaMemcpyAsync(xcol, E.W.x, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-      if (r != SKS_OK) { result = r; break; }
+      if (r != SKS_OK) return r;
       E.S.est_rel_err = h.btx > 0 ? std::sqrt(std::max(0.0, fac * h.dt / h.btx)) : 0.0;
     } else {
       // Iterative refinement: r = b - H x in float64 arithmetic, inner adaptive
@@ -926,8 +950,8 @@ sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks
         bool inner_conv = false, done = false;
         sks_status r = E.inner(E.W.bo, 0.0, o->inner_tol * o->inner_tol, std::max<int64_t>(inner_budget, 1),
                                &inner_conv, &dt0, &h, E.W.scal, tol2, fac, &done);
-        if (r != SKS_OK) { result = r; break; }
-        E.S.outer_iters = k + 1;
+        if (r != SKS_OK) return r;
+        E.S.outer_iters += 1;
         if (done) {
           converged = true;
           break;
@@ -940,7 +964,94 @@ sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks
       SKS_CUDA_TRY(cudaMemcpyAsync(xcol, E.W.xo, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
       SKS_TRY(read_status(E.W.st, stream, "refinement"));
     }
-    if (result == SKS_OK && !converged) result = fail(SKS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+    if (!converged) result = fail(SKS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+  }
+  return result;
+}
+
+sks_status write_state(Engine& E) {
+  SolveState h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kStateMagic;
+  h.n = E.prob->n;
+  h.d = E.prob->d;
+  h.m = E.m;
+  h.dtype = (int)E.prob->dtype;
+  h.precision = (int)E.o->precision;
+  h.kind = (int)E.o->kind;
+  h.sjlt_s = E.o->sjlt_s;
+  h.seed = E.o->seed;
+  SKS_CUDA_TRY(cudaMemcpyAsync(E.W.state, &h, sizeof(h), cudaMemcpyHostToDevice, E.stream));
+  SKS_CUDA_TRY(cudaStreamSynchronize(E.stream));
+  return SKS_OK;
+}
+
+sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks_opts* o, double* x_io,
+                               sks_stats* stats, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  SKS_TRY(check_opts(prob, o, x_io));
+  const int d = (int)prob->d;
+  size_t need = 0;
+  SKS_TRY(solve_layout(prob, o, nullptr, 0, nullptr, &need));
+  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "solve workspace too small (need " + std::to_string(need) + " bytes)");
+  Engine E;
+  Timer t_total(stream), t_sketch(stream), t_factor(stream);
+  E.t_sketch = &t_sketch;
+  E.t_factor = &t_factor;
+  t_total.start();
+  SKS_TRY(E.init(method, prob, o, ws, ws_bytes, stream));
+  SKS_CUDA_TRY(cudaMemsetAsync(E.W.state, 0, sizeof(SolveState), stream));
+  SKS_CUDA_TRY(cudaMemsetAsync(E.W.st, 0, sizeof(DevStatus), stream));
+  check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, E.W.st);
+  note_launch();
+  SKS_TRY(read_status(E.W.st, stream, "input check"));
+  SKS_TRY(E.first_sketch());
+  const sks_status result = solve_columns(E, prob->b, x_io);
+  if (result == SKS_OK || result == SKS_ERR_NO_CONVERGENCE) SKS_TRY(write_state(E));
+  t_total.stop();
+  sks_stats& S = E.S;
+  S.final_m = E.m;
+  S.ms_total = t_total.acc;
+  S.ms_sketch = t_sketch.acc;
+  S.ms_factor = t_factor.acc;
+  S.ms_iter = std::max(0.f, S.ms_total - S.ms_sketch - S.ms_factor);
+  S.status = result;
+  if (stats) *stats = S;
+  if (result != SKS_OK) set_last_error(last_error_cstr());
+  return result;
+}
+
+sks_status adjoint_impl(const sks_problem* prob, const sks_opts* o, const double* x, const double* g, double* db,
+                        void* dA, long long ldda, double* dnu, double* dlambda, sks_stats* stats, void* ws,
+                        size_t ws_bytes, cudaStream_t stream) {
+  SKS_TRY(check_opts(prob, o, x));
+  if (!g || !db) return fail(SKS_ERR_INVALID_ARG, "g and db are required");
+  if (dA && ldda < prob->d) return fail(SKS_ERR_INVALID_ARG, "ldda < d");
+  size_t need = 0;
+  SKS_TRY(solve_layout(prob, o, nullptr, 0, nullptr, &need));
+  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "adjoint: workspace too small");
+  Engine E;
+  Timer t_total(stream), t_sketch(stream), t_factor(stream);
+  E.t_sketch = &t_sketch;
+  E.t_factor = &t_factor;
+  t_total.start();
+  SKS_TRY(E.init(PCG, prob, o, ws, ws_bytes, stream));
+  SolveState h;
+  SKS_CUDA_TRY(cudaMemcpyAsync(&h, E.W.state, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+  if (h.magic != kStateMagic || h.n != prob->n || h.d != prob->d || h.dtype != (int)prob->dtype ||
+      h.precision != (int)o->precision || h.kind != (int)o->kind || h.seed != o->seed || h.m < 1)
+    return fail(SKS_ERR_INVALID_ARG,
+                "adjoint: the workspace does not hold the preconditioner of a solve of this problem");
+  E.restore(h.m);
+  SKS_CUDA_TRY(cudaMemsetAsync(E.W.st, 0, sizeof(DevStatus), stream));
+  // u = H^{-1} g with the same preconditioner (solved into db: dL/db = u)
+  SKS_CUDA_TRY(cudaMemsetAsync(db, 0, (size_t)prob->d * prob->k * sizeof(double), stream));
+  const sks_status result = solve_columns(E, g, db);
+  if (result == SKS_OK || result == SKS_ERR_NO_CONVERGENCE) {
+    SKS_TRY(write_state(E));
+    SKS_TRY(adjoint_grads(stream, prob, x, db, dA, ldda, dnu ? E.W.scal + 1 : nullptr, dlambda));
+    if (dnu) SKS_CUDA_TRY(cudaMemcpyAsync(dnu, E.W.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SKS_TRY(read_status(E.W.st, stream, "adjoint"));
   }
   t_total.stop();
   sks_stats& S = E.S;
@@ -966,6 +1077,12 @@ sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t*
 sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
                           size_t ws_bytes, cudaStream_t stream) {
   return adaptive_solve_impl(method == 0 ? PCG : IHS, p, o, x, stats, ws, ws_bytes, stream);
+}
+
+sks_status adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g, double* db, void* dA,
+                   long long ldda, double* dnu, double* dlambda, sks_stats* stats, void* ws, size_t ws_bytes,
+                   cudaStream_t stream) {
+  return adjoint_impl(p, o, x, g, db, dA, ldda, dnu, dlambda, stats, ws, ws_bytes, stream);
 }
 
 sks_status hess_apply_ws(const sks_problem* p, size_t* bytes) {

@@ -287,3 +287,71 @@ def test_tensor_core_preconditioner_matches_split_oracle(m, d):
     got = host(P.apply(dev(Z)))
     ref = ref_P.apply(Z)
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-8
+
+
+# ----------------------------------------------------------------------------- adjoint (a13)
+
+@pytest.mark.parametrize("precision", ["plain", "mixed"])
+def test_adjoint_matches_oracle_gradient(precision):
+    # C4 recipe at n=4096, d=256, 8 right-hand sides; loss L = sum_k c_k^T x_k.
+    from oracle import adjoint as OA
+    p = synthetic.make_problem("C4", 0, n=4096, d=256)
+    rng = np.random.default_rng(1)
+    Cw = rng.standard_normal(p.b.shape)
+    Xo, go = OA.solve_and_grads(p.A, p.b, p.nu, p.lam, Cw)
+    dt = torch.float64 if precision == "plain" else torch.float32
+    tA = dev(p.A, dt).requires_grad_(True)
+    tb = dev(p.b).requires_grad_(True)
+    tlam = dev(p.lam).requires_grad_(True)
+    tnu = torch.tensor(p.nu, dtype=torch.float64, device="cuda", requires_grad=True)
+    tol = 1e-10 if precision == "plain" else 1e-8
+    x = api().sketch_solve(tA, tb, tnu, tlam, kind="gaussian", m_init=1, tol=tol, precision=precision, seed=3)
+    loss = (x * dev(Cw)).sum()
+    loss.backward()
+    gtol = 1e-7 if precision == "plain" else 1e-5
+    assert np.max(np.abs(host(tb.grad) - go["b"])) / np.max(np.abs(go["b"])) < gtol
+    assert np.max(np.abs(host(tA.grad).astype(np.float64) - go["A"])) / np.max(np.abs(go["A"])) < gtol
+    assert np.max(np.abs(host(tlam.grad) - go["lam"])) / np.max(np.abs(go["lam"])) < gtol
+    assert abs(float(tnu.grad) - go["nu"]) / abs(go["nu"]) < gtol
+
+
+def test_adjoint_central_differences():
+    # Directional central differences (h = 1e-3; for nu a step of 1e-3 * nu)
+    # of L = c^T x(A, b, nu, Lambda) with the plain float64 solver.
+    p = synthetic.make_problem("C4", 0, n=4096, d=256, k=1)
+    rng = np.random.default_rng(2)
+    cw = rng.standard_normal(256)
+    opts = dict(kind="gaussian", m_init=1, tol=1e-12, seed=3)
+
+    def L(A, b, nu, lam):
+        x, _, _ = api().adaptive_pcg(dev(A), dev(b), nu, dev(lam), **opts)
+        return float(np.dot(cw, host(x)))
+
+    tA = dev(p.A).requires_grad_(True)
+    tb = dev(p.b[:, 0]).requires_grad_(True)
+    tlam = dev(p.lam).requires_grad_(True)
+    tnu = torch.tensor(p.nu, dtype=torch.float64, device="cuda", requires_grad=True)
+    x = api().sketch_solve(tA, tb, tnu, tlam, **opts)
+    (x * dev(cw)).sum().backward()
+    h = 1e-3
+    D = rng.standard_normal(p.A.shape)
+    D *= h / np.linalg.norm(D)
+    fd = (L(p.A + D, p.b[:, 0], p.nu, p.lam) - L(p.A - D, p.b[:, 0], p.nu, p.lam)) / 2
+    assert math.isclose(fd, float(np.sum(host(tA.grad) * D)), rel_tol=1e-4)
+    e = np.zeros(256)
+    e[7] = h
+    fd = (L(p.A, p.b[:, 0] + e, p.nu, p.lam) - L(p.A, p.b[:, 0] - e, p.nu, p.lam)) / (2 * h)
+    assert math.isclose(fd, float(host(tb.grad)[7]), rel_tol=1e-5)
+    fd = (L(p.A, p.b[:, 0], p.nu, p.lam + e) - L(p.A, p.b[:, 0], p.nu, p.lam - e)) / (2 * h)
+    assert math.isclose(fd, float(host(tlam.grad)[7]), rel_tol=1e-4)
+    hn = 1e-3 * p.nu
+    fd = (L(p.A, p.b[:, 0], p.nu + hn, p.lam) - L(p.A, p.b[:, 0], p.nu - hn, p.lam)) / (2 * hn)
+    assert math.isclose(fd, float(tnu.grad), rel_tol=1e-4)
+
+
+def test_adjoint_requires_a_solved_workspace():
+    p = synthetic.make_problem("C1", 0, n=512, d=32)
+    solver = api().Solver(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind="srht")
+    from paper_2104_14101_gb300._lib import SksError
+    with pytest.raises(SksError):
+        solver.adjoint(dev(np.zeros(32)), dev(np.ones(32)))

@@ -142,8 +142,9 @@ uint64_t sks_kernel_launch_count(void);
  * y = A^T (A x) + nu^2 Lambda x for the k columns of x, in ONE read of A.
  * x, y: device d x k column-major float64 (y may not alias x).  Arithmetic in
  * the precision of A (float32 A: float32 products and row sums, float64
- * cross-block accumulation), or with `extended` = 1 float64 arithmetic on any
- * A (the refinement residual of the mixed form).
+ * cross-block accumulation), or with `extended` = 1 on a float32 A:
+ * double-float arithmetic (float32 pairs, unit roundoff ~2^-44; float64 x
+ * split into two floats), the refinement residual of the mixed form.
  * ws: device scratch of sks_hess_apply_workspace_size(problem) bytes.
  * ------------------------------------------------------------------------- */
 sks_status sks_hess_apply_workspace_size(const sks_problem* p, size_t* bytes);

@@ -46,6 +46,72 @@ struct Vec<float> {
   }
 };
 
+// ------------------------------------------------------------ accumulator arithmetic
+// float / double: plain arithmetic.  df32: double-float (an unevaluated sum of
+// two floats, ~44-48 significant bits) built from float32 operations --
+// TwoProd via fmaf and Knuth's TwoSum -- for the refinement residual, whose
+// float64 version is bound by the float64 FMA rate on this part.
+struct df32 {
+  float h, l;
+};
+
+template <typename TX>
+struct Acc {
+  using T = TX;
+  using In = TX;   // type of x in global memory
+  using Out = TX;  // type of the partial sums
+  static SKS_DEV T zero() { return T(0); }
+  static SKS_DEV T from_in(In x) { return x; }
+  template <typename TA>
+  static SKS_DEV void mac(T& acc, TA a, const T& x) { acc += (T)a * x; }
+  static SKS_DEV void add(T& a, const T& b) { a += b; }
+  static SKS_DEV T wsum(T v) { return warp_sum(v); }
+  static SKS_DEV Out out(const T& v) { return v; }
+};
+
+SKS_DEV void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+template <>
+struct Acc<df32> {
+  using T = df32;
+  using In = double;
+  using Out = double;
+  static SKS_DEV T zero() { return df32{0.f, 0.f}; }
+  static SKS_DEV T from_in(double x) {
+    const float h = (float)x;
+    return df32{h, (float)(x - (double)h)};
+  }
+  // acc += a * x  (a float, x double-float)
+  static SKS_DEV void mac(T& acc, float a, const T& x) {
+    const float ph = a * x.h;
+    const float pl = fmaf(a, x.l, fmaf(a, x.h, -ph));
+    float s, e;
+    two_sum(acc.h, ph, s, e);
+    acc.h = s;
+    acc.l += e + pl;
+  }
+  static SKS_DEV void add(T& a, const T& b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e += a.l + b.l;
+    a.h = s + e;
+    a.l = e - (a.h - s);
+  }
+  static SKS_DEV T wsum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const df32 w{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+      add(v, w);
+    }
+    return v;
+  }
+  static SKS_DEV Out out(const T& v) { return (double)v.h + (double)v.l; }
+};
+
 constexpr int kConsumers = 256;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kRC = 2;  // rows reduced together
@@ -69,6 +135,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
   const size_t stage_elems = (size_t)a.rows * a.dp;
   TA* stage0 = (TA*)smem;
   size_t off = align_up((size_t)a.stages * stage_elems * sizeof(TA), 128);
+  using AT = Acc<TX>;
   TX* red = (TX*)(smem + off);
   off += align_up((size_t)2 * 8 * kRC * K * sizeof(TX), 128);
   uint64_t* full = (uint64_t*)(smem + off);
@@ -119,10 +186,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
     for (int e = 0; e < VEC; ++e)
 #pragma unroll
-      for (int c = 0; c < K; ++c) acc[q][e][c] = TX(0);
+      for (int c = 0; c < K; ++c) acc[q][e][c] = AT::zero();
 
   // the thread's slice of x (zero past column d) stays in registers for the whole pass
-  const TX* xg = (const TX*)a.x;
+  const typename AT::In* xg = (const typename AT::In*)a.x;
   TX xr[QMAX][VEC][K];
 #pragma unroll
   for (int q = 0; q < QMAX; ++q) {
@@ -132,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         const int col = vi * VEC + e;
-        xr[q][e][c] = (q < a.q && vi < nvec && col < a.d) ? xg[(size_t)c * a.d + col] : TX(0);
+        xr[q][e][c] = (q < a.q && vi < nvec && col < a.d) ? AT::from_in(xg[(size_t)c * a.d + col]) : AT::zero();
       }
   }
 
@@ -158,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
         const int r = g + NG * (j0 + rc);
         const bool rok = (j0 + rc) < rg;
 #pragma unroll
-        for (int c = 0; c < K; ++c) dot[rc][c] = TX(0);
+        for (int c = 0; c < K; ++c) dot[rc][c] = AT::zero();
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
           const int vi = l + q * G;
@@ -170,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
             for (int e = 0; e < VEC; ++e)
 #pragma unroll
-              for (int c = 0; c < K; ++c) dot[rc][c] += (TX)v[e] * xr[q][e][c];
+              for (int c = 0; c < K; ++c) AT::mac(dot[rc][c], v[e], xr[q][e][c]);
           }
         }
       }
@@ -178,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc)
 #pragma unroll
-        for (int c = 0; c < K; ++c) dot[rc][c] = warp_sum(dot[rc][c]);
+        for (int c = 0; c < K; ++c) dot[rc][c] = AT::wsum(dot[rc][c]);
       if (G > 32) {
         TX* rb = red + buf * (8 * kRC * K);
         if (lane == 0) {
@@ -194,9 +261,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
         for (int rc = 0; rc < kRC; ++rc)
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            TX t = TX(0);
+            TX t = AT::zero();
 #pragma unroll
-            for (int w = 0; w < WPG; ++w) t += rb[(w0 + w) * kRC * K + rc * K + c];
+            for (int w = 0; w < WPG; ++w) AT::add(t, rb[(w0 + w) * kRC * K + rc * K + c]);
             dot[rc][c] = t;
           }
         buf ^= 1;
@@ -217,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
               for (int e = 0; e < VEC; ++e)
 #pragma unroll
-                for (int c = 0; c < K; ++c) acc[q][e][c] += dot[rc][c] * (TX)v[e];
+                for (int c = 0; c < K; ++c) AT::mac(acc[q][e][c], v[e], dot[rc][c]);
             }
           }
         }
@@ -227,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
     if (lane == 0) mbar_arrive(&empty[s]);
   }
 
-  TX* out = (TX*)a.partials + (size_t)(blockIdx.x * NG + g) * K * a.d;
+  typename AT::Out* out = (typename AT::Out*)a.partials + (size_t)(blockIdx.x * NG + g) * K * a.d;
 #pragma unroll
   for (int q = 0; q < QMAX; ++q) {
     const int vi = l + q * G;
@@ -237,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
         const int col = vi * VEC + e;
         if (col < a.d)
 #pragma unroll
-          for (int c = 0; c < K; ++c) out[(size_t)c * a.d + col] = acc[q][e][c];
+          for (int c = 0; c < K; ++c) out[(size_t)c * a.d + col] = AT::out(acc[q][e][c]);
       }
     }
   }
@@ -297,8 +364,9 @@ sks_status launch_t(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int
     SKS_CUDA_TRY(cudaEventRecord(ev_end, stream));
   }
   dim3 fg((unsigned)((d + 127) / 128), (unsigned)K);
-  apass_finalize<TX><<<fg, 128, 0, stream>>>(n > 0 ? nparts : 0, (int)d, K, (const TX*)partials, (const TX*)x,
-                                               (TX*)y, nu2, lambda, sgn, (const TX*)addv, addc);
+  using TO = typename Acc<TX>::Out;
+  apass_finalize<TO><<<fg, 128, 0, stream>>>(n > 0 ? nparts : 0, (int)d, K, (const TO*)partials, (const TO*)x,
+                                               (TO*)y, nu2, lambda, sgn, (const TO*)addv, addc);
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
@@ -383,10 +451,11 @@ sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n,
     if (pl.group == 128) return launch_t<float, float, 128, 4, 1>(SKS_APASS_ARGS);
     return launch_t<float, float, 256, 4, 1>(SKS_APASS_ARGS);
   }
-  if (k == 8) return launch_t<float, double, 256, 1, 8>(SKS_APASS_ARGS);
-  if (pl.group == 32) return launch_t<float, double, 32, 4, 1>(SKS_APASS_ARGS);
-  if (pl.group == 128) return launch_t<float, double, 128, 4, 1>(SKS_APASS_ARGS);
-  return launch_t<float, double, 256, 4, 1>(SKS_APASS_ARGS);
+  // float32 A, float64 vectors: double-float arithmetic (~2^-44 relative)
+  if (k == 8) return launch_t<float, df32, 256, 1, 8>(SKS_APASS_ARGS);
+  if (pl.group == 32) return launch_t<float, df32, 32, 4, 1>(SKS_APASS_ARGS);
+  if (pl.group == 128) return launch_t<float, df32, 128, 4, 1>(SKS_APASS_ARGS);
+  return launch_t<float, df32, 256, 4, 1>(SKS_APASS_ARGS);
 #undef SKS_APASS_ARGS
 }
 

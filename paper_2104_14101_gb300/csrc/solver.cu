@@ -324,6 +324,8 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
                            P->split, P->split_elems));
     }
     SKS_TRY(add_diagonal(stream, d, P->H, d, 0.0, lam, P->nu2));
+    // Cholesky form: the apply is X^T X, positive definite for any nonsingular
+    // X, so the inverse factor may be formed in float32 (mixed form).
     SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st, P->inv32));
     SKS_TRY(transpose<double>(stream, d, d, P->X, d, P->Xt, d));
   } else {
@@ -343,7 +345,9 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
                            P->split, P->split_elems));
     }
     SKS_TRY(add_diagonal(stream, m, P->H, m, P->nu2, nullptr, 0.0));
-    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st, P->inv32));
+    // Woodbury form: the apply subtracts two terms of size ~1/nu^2, so W^{-1}
+    // must be accurate: float64 inverse.
+    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st, nullptr));
     SKS_TRY(transpose<double>(stream, m, m, P->X, m, P->Xt, m));
     SKS_TRY(transpose<double>(stream, m, d, Y64, ldy, P->Yt, m));
   }

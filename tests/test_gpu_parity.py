@@ -241,6 +241,19 @@ def test_mixed_refined_reaches_1e8(method, kind):
     assert max(e["outer"] for e in tr) >= 1
 
 
+@pytest.mark.parametrize("kind", ["gaussian", "sjlt"])
+def test_mixed_refined_ill_conditioned_woodbury(kind):
+    # d = 1024 with sigma down to ~1e-6 and nu = 1e-4: the Woodbury phases
+    # (m < d) factor W_S with eigenvalues near nu^2, where the apply's
+    # cancellation demands an accurate W^{-1}.
+    p = synthetic.make_problem("C3", 1, n=16384, d=1024)
+    xs = O.direct_solve(p.A, p.b, p.nu, p.lam)
+    x, st, _ = api().adaptive_pcg(dev(p.A, torch.float32), dev(p.b), p.nu, dev(p.lam), kind=kind, m_init=1,
+                                  tol=1e-8, sjlt_s=4, precision="mixed", seed=4, max_iter=3000)
+    assert O.rel_err_H(p.A, p.nu, p.lam, host(x), xs) <= 1e-8, st
+    assert st["iters"] > 0
+
+
 def test_mixed_requires_float32_A():
     p = synthetic.make_problem("C1", 0, n=512, d=32)
     from paper_2104_14101_gb300._lib import SksError

@@ -132,7 +132,7 @@ __global__ void sjlt_scatter_kernel(const TA* __restrict__ A, long long lda, int
   const TA* a = A + warp * lda;
   if (sizeof(TY) == 4 && sizeof(TA) == 4 && (d & 3) == 0 && (lda & 3) == 0 && (ldy & 3) == 0) {
     for (int c = lane * 4; c < d; c += 128) {
-      const float4 v = *(const float4*)(a + c);
+      const float4 v = __ldcs((const float4*)(a + c));  // streamed once: evict first, keep Y in L2
       for (int k = 0; k < s_eff; ++k) {
         const float w = signs[k] * (float)inv;
         atomicAdd((float4*)(Y + (long long)rows[k] * ldy + c), make_float4(w * v.x, w * v.y, w * v.z, w * v.w));
@@ -141,7 +141,7 @@ __global__ void sjlt_scatter_kernel(const TA* __restrict__ A, long long lda, int
     return;
   }
   for (int c = lane; c < d; c += 32) {
-    const TY v = (TY)a[c] * inv;
+    const TY v = (TY)__ldcs(a + c) * inv;
     for (int k = 0; k < s_eff; ++k) atomicAdd(&Y[(long long)rows[k] * ldy + c], (TY)signs[k] * v);
   }
 }

@@ -118,6 +118,10 @@ constexpr int kRC = 2;  // rows reduced together
 
 struct ApassArgs {
   int d, dp, boxw, nbox, rows, stages, q, ntiles;
+  int bulk;            // 1: whole rows by 1-D bulk copies (row-major [rows][d] stages)
+  int64_t n;           // rows of A (bulk mode: rows past n are skipped)
+  const char* A;       // bulk mode source
+  long long lda_bytes;
   const void* x;  // d x K column-major, vector type
   void* partials; // [grid * NG][K][d]
   DevStatus* st;
@@ -163,10 +167,19 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
         const int s = it % a.stages;
         const uint32_t ph = (uint32_t)(it / a.stages) & 1u;
         if (!mbar_wait(&empty[s], ph ^ 1u, a.st, 12)) break;
-        mbar_arrive_expect_tx(&full[s], stage_bytes);
         TA* dst = stage0 + (size_t)s * stage_elems;
-        for (int b = 0; b < a.nbox; ++b)
-          tma_load_2d(dst + (size_t)b * a.rows * a.boxw, &tmap, &full[s], b * a.boxw, tile * a.rows);
+        if (a.bulk) {
+          const int64_t r0 = (int64_t)tile * a.rows;
+          const int valid = (int)min((int64_t)a.rows, a.n - r0);
+          const uint32_t row_bytes = (uint32_t)(a.d * sizeof(TA));
+          mbar_arrive_expect_tx(&full[s], (uint32_t)valid * row_bytes);
+          for (int r = 0; r < valid; ++r)
+            bulk_load(dst + (size_t)r * a.d, a.A + (r0 + r) * a.lda_bytes, row_bytes, &full[s]);
+        } else {
+          mbar_arrive_expect_tx(&full[s], stage_bytes);
+          for (int b = 0; b < a.nbox; ++b)
+            tma_load_2d(dst + (size_t)b * a.rows * a.boxw, &tmap, &full[s], b * a.boxw, tile * a.rows);
+        }
       }
       // drain: every issued copy has landed before the CTA may exit
       const int first = it > a.stages ? it - a.stages : 0;
@@ -223,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {
         const int r = g + NG * (j0 + rc);
-        const bool rok = (j0 + rc) < rg;
+        const bool rok = (j0 + rc) < rg && (!a.bulk || (int64_t)tile * a.rows + r < a.n);
 #pragma unroll
         for (int c = 0; c < K; ++c) dot[rc][c] = AT::zero();
 #pragma unroll
@@ -272,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {
         const int r = g + NG * (j0 + rc);
-        if ((j0 + rc) < rg) {
+        if ((j0 + rc) < rg && (!a.bulk || (int64_t)tile * a.rows + r < a.n)) {
 #pragma unroll
           for (int q = 0; q < QMAX; ++q) {
             const int vi = l + q * G;
@@ -354,6 +367,10 @@ sks_status launch_t(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int
     a.x = x;
     a.partials = partials;
     a.st = st;
+    a.bulk = pl.bulk;
+    a.n = n;
+    a.A = (const char*)pl.A;
+    a.lda_bytes = pl.lda_bytes;
     if (ev_begin) SKS_CUDA_TRY(cudaEventRecord(ev_begin, stream));
     kern<<<pl.grid, kThreads, pl.smem, stream>>>(*tmap, a);
     note_launch();
@@ -425,6 +442,18 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   pl->smem = (size_t)stages * stage_bytes + fixed + 2 * 8 * stages + 256;
   pl->partial_elems = (size_t)pl->grid * ng * k * d;
   return SKS_OK;
+}
+
+void apass_use_bulk(ApassPlan* pl, const void* A, int64_t d, int64_t lda, bool a_f32) {
+  const size_t esz = a_f32 ? 4 : 8;
+  if ((d * esz) % 16 != 0 || (lda * esz) % 16 != 0 || ((uintptr_t)A & 15) != 0) return;
+  // stage layout [rows][d]: same byte budget, no padding (d <= dp)
+  pl->bulk = 1;
+  pl->boxw = (int)d;
+  pl->nbox = 1;
+  pl->dp = (int)d;
+  pl->A = A;
+  pl->lda_bytes = (long long)(lda * esz);
 }
 
 size_t apass_workspace_bytes(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32) {

@@ -73,6 +73,9 @@ sks_status make_tmap_2d_bf16_sw128(CUtensorMap* map, const void* base, uint64_t 
 // Geometry of one A-pass launch (host-computed).
 struct ApassPlan {
   int grid = 0, group = 0, q = 0, rows_per_stage = 0, stages = 0, boxw = 0, nbox = 0, dp = 0;
+  int bulk = 0;                 // whole-row 1-D bulk copies (set by apass_use_bulk)
+  const void* A = nullptr;
+  long long lda_bytes = 0;
   size_t smem = 0;
   size_t partial_elems = 0;  // grid * k * d
 };
@@ -89,6 +92,9 @@ sks_status apass_launch(const ApassPlan& plan, const CUtensorMap* tmap, int64_t 
                         const void* addv = nullptr, double addc = 0.0, cudaEvent_t ev_begin = nullptr,
                         cudaEvent_t ev_end = nullptr);
 size_t apass_workspace_bytes(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32);
+// Switch a plan to whole-row bulk copies when every row of A is a 16-byte
+// multiple (stages then hold rows back to back, no column padding).
+void apass_use_bulk(ApassPlan* plan, const void* A, int64_t d, int64_t lda, bool a_f32);
 
 // ---------------------------------------------------------------- solver entry points (solver.cu)
 sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes);

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(256) fwht_pass_kernel(const T* __restrict__ A,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = (T*)smem_raw;  // [2^L][kFwhtCols]
   const int T_rows = 1 << L;
+  T* sign = tile + (size_t)T_rows * kFwhtCols;  // [2^L], first pass only
   const int ncb = (d + kFwhtCols - 1) / kFwhtCols;
   const int cb = blockIdx.x % ncb;
   const long long grp = blockIdx.x / ncb;
@@ -41,13 +42,21 @@ __global__ void __launch_bounds__(256) fwht_pass_kernel(const T* __restrict__ A,
   const long long hi = grp >> a;
   const int c0 = cb * kFwhtCols;
   const int tid = threadIdx.x;
+  if (first) {
+    // one Philox evaluation per row of the tile, not per element
+    for (int j = tid; j < T_rows; j += blockDim.x) {
+      const long long r = (hi << (a + L)) + ((long long)j << a) + lo;
+      sign[j] = (r < n) ? (T)srht_sign(key, (uint32_t)r) : T(0);
+    }
+    __syncthreads();
+  }
   for (int e = tid; e < T_rows * kFwhtCols; e += blockDim.x) {
     const int j = e / kFwhtCols, c = e % kFwhtCols;
     const long long r = (hi << (a + L)) + ((long long)j << a) + lo;
     T v = T(0);
     if (c0 + c < d) {
       if (first) {
-        if (r < n) v = A[r * lda + c0 + c] * (T)srht_sign(key, (uint32_t)r);
+        if (r < n) v = A[r * lda + c0 + c] * sign[j];
       } else {
         v = B[r * ldb + c0 + c];
       }
@@ -196,7 +205,7 @@ sks_status srht_form(cudaStream_t stream, const T* A, long long lda, int64_t n, 
   if (bits == 0) {
     // n_pad = 1: B = E A
     const int L = 0;
-    const size_t smem = (size_t)kFwhtCols * sizeof(T);
+    const size_t smem = (size_t)(kFwhtCols + 1) * sizeof(T);
     fwht_pass_kernel<T><<<ncb, 256, smem, stream>>>(A, lda, n, B, ldb, d, 0, L, 1, make_key(seed));
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
@@ -206,7 +215,7 @@ sks_status srht_form(cudaStream_t stream, const T* A, long long lda, int64_t n, 
     const int L = std::min(Lmax, bits - a);
     const long long groups = 1ll << (bits - L);
     const long long blocks = groups * ncb;
-    const size_t smem = ((size_t)1 << L) * kFwhtCols * sizeof(T);
+    const size_t smem = ((size_t)1 << L) * (kFwhtCols + 1) * sizeof(T);
     if (blocks > 0x7fffffffll) return fail(SKS_ERR_UNSUPPORTED, "FWHT grid too large");
     SKS_CUDA_TRY(cudaFuncSetAttribute(fwht_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     fwht_pass_kernel<T><<<(unsigned)blocks, 256, smem, stream>>>(A, lda, n, B, ldb, d, a, L, first ? 1 : 0,

@@ -681,9 +681,11 @@ struct Engine {
     const int64_t n1 = std::max<int64_t>(pr->n, 1);
     SKS_TRY(apass_plan(n1, d, 1, f32, mixed, &plan));
     if (pr->n > 0) SKS_TRY(map_for(pr, &tmap, plan));
+    apass_use_bulk(&plan, pr->A, d, pr->lda, f32);
     if (mixed) {
       SKS_TRY(apass_plan(n1, d, 1, f32, false, &plan64));
       if (pr->n > 0) SKS_TRY(map_for(pr, &tmap64, plan64));
+      apass_use_bulk(&plan64, pr->A, d, pr->lda, f32);
     }
     SKS_TRY(sketch_init(&sk, pr, op->kind, m_max, op->sjlt_s, op->seed, W.sketch_ws, W.sketch_bytes, W.st));
     // the mixed form forms the inverse Cholesky factor in float32
@@ -1123,6 +1125,7 @@ sks_status hess_apply(const sks_problem* p, const double* x, double* y, int exte
   SKS_TRY(apass_plan(std::max<int64_t>(p->n, 1), p->d, kb, f32, vec32, &plan));
   CUtensorMap tmap;
   if (p->n > 0) SKS_TRY(map_for(p, &tmap, plan));
+  apass_use_bulk(&plan, p->A, p->d, p->lda, f32);
   const double nu2 = p->nu * p->nu;
   for (int64_t c0 = 0; c0 < p->k; c0 += kb) {
     const double* xc = x + c0 * p->d;

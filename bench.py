@@ -57,6 +57,8 @@ WORKLOADS = {
     # reduced C3 (n = 2^17, A = 2 GiB float32) for ncu captures of the float32 kernels
     "C3-profile": dict(config="C3", n=1 << 17, method="pcg", kind="sjlt", sjlt_s=4, m_init=1, m_max=8192, tol=1e-8,
                        precision="mixed", desc="C3 recipe at n=2^17 (profiling size)"),
+    "C3-srht-profile": dict(config="C3", n=1 << 17, method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=8192,
+                            tol=1e-8, precision="mixed", desc="C3 recipe with the SRHT at n=2^17 (profiling size)"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }

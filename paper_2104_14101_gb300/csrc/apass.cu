@@ -144,10 +144,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
   off += align_up((size_t)2 * 8 * kRC * K * sizeof(TX), 128);
   uint64_t* full = (uint64_t*)(smem + off);
   uint64_t* empty = full + a.stages;
-  __shared__ volatile int abort_flag;
-
   if (tid == 0) {
-    abort_flag = 0;
     for (int s = 0; s < a.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumers / 32);
@@ -216,49 +213,70 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
       }
   }
 
+  // shared-memory offset of each of the thread's column vectors within a stage
+  // row (the row stride is boxw in both stage layouts), hoisted out of the loops
+  int soff[QMAX];
+  bool qv[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+    const int vi = l + q * G;
+    qv[q] = q < a.q && vi < nvec;
+    const int col = vi * VEC;
+    const int b = col / a.boxw;
+    soff[q] = b * a.rows * a.boxw + (col - b * a.boxw);
+  }
+  const int rstride = a.boxw;
+
   int buf = 0;
   int it = 0;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
     const int s = it % a.stages;
     const uint32_t ph = (uint32_t)(it / a.stages) & 1u;
     const bool ok = mbar_wait_warp(&full[s], ph, a.st, 11);
-    if (G > 32) {
-      // keep the 256 consumers in lock step: a timed-out warp flags, all leave
-      if (!ok && lane == 0) abort_flag = 1;
-      named_bar_sync(1, kConsumers);
-      if (abort_flag) break;
-    } else if (!ok) {
-      break;
-    }
+    // narrow rows: the warp is the group and leaves on its own.  Wide rows: a
+    // timed-out warp reads the (stale) stage like the others and the group
+    // leaves together at the reduction barrier below.
+    if (G <= 32 && !ok) break;
+    const int valid = a.bulk ? (int)min((int64_t)a.rows, a.n - (int64_t)tile * a.rows) : a.rows;
     const TA* S = stage0 + (size_t)s * stage_elems;
+    bool stop = false;
     for (int j0 = 0; j0 < rg; j0 += kRC) {
-      TX dot[kRC][K];
+      // partial dots: one chain per column vector for a single right-hand
+      // side (kRC * QMAX independent chains), one per (row, column) otherwise
+      constexpr int QD = K == 1 ? QMAX : 1;
+      TX dq[kRC][QD][K];
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {
         const int r = g + NG * (j0 + rc);
-        const bool rok = (j0 + rc) < rg && (!a.bulk || (int64_t)tile * a.rows + r < a.n);
+        const bool rok = (j0 + rc) < rg && r < valid;
+        const TA* row = S + r * rstride;
 #pragma unroll
-        for (int c = 0; c < K; ++c) dot[rc][c] = AT::zero();
+        for (int q = 0; q < QD; ++q)
+#pragma unroll
+          for (int c = 0; c < K; ++c) dq[rc][q][c] = AT::zero();
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
-          const int vi = l + q * G;
-          if (rok && q < a.q && vi < nvec) {
-            const int col = vi * VEC;
-            const int b = col / a.boxw, jj = col - b * a.boxw;
+          if (rok && qv[q]) {
             TA v[VEC];
-            Vec<TA>::load(S + (size_t)b * a.rows * a.boxw + (size_t)r * a.boxw + jj, v);
+            Vec<TA>::load(row + soff[q], v);
 #pragma unroll
             for (int e = 0; e < VEC; ++e)
 #pragma unroll
-              for (int c = 0; c < K; ++c) AT::mac(dot[rc][c], v[e], xr[q][e][c]);
+              for (int c = 0; c < K; ++c) AT::mac(dq[rc][QD > 1 ? q : 0][c], v[e], xr[q][e][c]);
           }
         }
       }
-      // reduce the dots over the group sharing the rows
+      TX dot[kRC][K];
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc)
 #pragma unroll
-        for (int c = 0; c < K; ++c) dot[rc][c] = AT::wsum(dot[rc][c]);
+        for (int c = 0; c < K; ++c) {
+#pragma unroll
+          for (int w = 1; w < QD; w <<= 1)
+#pragma unroll
+            for (int q = 0; q + w < QD; q += 2 * w) AT::add(dq[rc][q][c], dq[rc][q + w][c]);
+          dot[rc][c] = AT::wsum(dq[rc][0][c]);
+        }
       if (G > 32) {
         TX* rb = red + buf * (8 * kRC * K);
         if (lane == 0) {
@@ -267,7 +285,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
             for (int c = 0; c < K; ++c) rb[warp * kRC * K + rc * K + c] = dot[rc][c];
         }
-        named_bar_sync(2 + g, G);
+        if (named_bar_or(2 + g, G, !ok)) {
+          stop = true;
+          break;
+        }
         constexpr int WPG = G / 32;  // warps per group
         const int w0 = g * WPG;
 #pragma unroll
@@ -285,15 +306,13 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {
         const int r = g + NG * (j0 + rc);
-        if ((j0 + rc) < rg && (!a.bulk || (int64_t)tile * a.rows + r < a.n)) {
+        if ((j0 + rc) < rg && r < valid) {
+          const TA* row = S + r * rstride;
 #pragma unroll
           for (int q = 0; q < QMAX; ++q) {
-            const int vi = l + q * G;
-            if (q < a.q && vi < nvec) {
-              const int col = vi * VEC;
-              const int b = col / a.boxw, jj = col - b * a.boxw;
+            if (qv[q]) {
               TA v[VEC];
-              Vec<TA>::load(S + (size_t)b * a.rows * a.boxw + (size_t)r * a.boxw + jj, v);
+              Vec<TA>::load(row + soff[q], v);
 #pragma unroll
               for (int e = 0; e < VEC; ++e)
 #pragma unroll
@@ -303,6 +322,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
         }
       }
     }
+    if (stop) break;
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }

@@ -2,10 +2,11 @@
 //
 //  K2 SRHT: B = H_{+-1} E A_pad (n_pad x d), the fast Walsh-Hadamard transform
 //     along the rows of the sign-flipped, zero-padded A.  Butterflies pair
-//     whole rows (r, r + h), so every pass loads 2^L rows x 16 contiguous
-//     columns into shared memory and applies L levels there; ceil(log2(n_pad)
-//     / L) passes cover all levels.  Formed once per solve; a larger sketch
-//     only gathers more rows of B.
+//     whole rows (r, r + h), so every pass holds 2^L rows x 32 contiguous
+//     columns (lane = column) in registers and applies L <= 9 levels there,
+//     with one shared-memory exchange; ceil(log2(n_pad) / 9) passes (8 for
+//     float64) cover all levels.  Formed once per solve; a larger sketch only
+//     gathers more rows of B.
 //  K3 SRHT gather: Y[r] = B[pi(r)] for the new rows r, pi the keyed Feistel
 //     permutation (nested subsampling R).
 //  K4 Gaussian: Y[r] = sum_i G[r][i] a_i, G from Philox + Box-Muller, produced
@@ -22,63 +23,107 @@ namespace sks {
 
 namespace {
 
-constexpr int kFwhtCols = 16;
+constexpr int kFwhtCols = 32;  // one warp lane per column: 128-byte (float) row segments
 
-// One FWHT pass over the row bits [a, a + L): the CTA owns rows
-// r = hi * 2^(a+L) + j * 2^a + lo (j < 2^L) and columns [c0, c0 + 16).
-// first pass: source is A (rows >= n are zero) times the signs E.
-template <typename T>
-__global__ void __launch_bounds__(256) fwht_pass_kernel(const T* __restrict__ A, long long lda, int64_t n,
-                                                       T* __restrict__ B, long long ldb, int d, int a, int L,
-                                                       int first, Key key) {
+// One FWHT pass over the row bits [a, a + L), L = LOGR + logw: the CTA
+// (2^logw warps) owns the 2^L rows r(j) = hi * 2^(a+L) + j * 2^a + lo and the
+// columns [c0, c0 + 32); lane c holds column c0 + c.
+//   phase 1: warp w holds local rows j = w * 2^LOGR + i (i < 2^LOGR) in
+//            registers and applies the levels on local bits [0, LOGR);
+//   phase 2: after one exchange through shared memory, warp w holds rows
+//            j = i * 2^logw + w and applies the levels on bits [LOGR, L)
+//            (bits [LOGR - logw, LOGR) of i; logw <= LOGR).
+// Levels of the transform commute, so their order is free.  The first pass
+// reads A (rows >= n are zero) times the signs E.
+template <typename T, int LOGR>
+__global__ void __launch_bounds__(256, 2) fwht_pass_kernel(const T* __restrict__ A, long long lda, int64_t n,
+                                                       T* __restrict__ B, long long ldb, int d, int a, int logw,
+                                                       int first, Key key, int ncb) {
+  constexpr int R = 1 << LOGR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tile = (T*)smem_raw;  // [2^L][kFwhtCols]
-  const int T_rows = 1 << L;
-  T* sign = tile + (size_t)T_rows * kFwhtCols;  // [2^L], first pass only
-  const int ncb = (d + kFwhtCols - 1) / kFwhtCols;
+  const int L = LOGR + logw;
+  T* tile = (T*)smem_raw;                                   // [2^L][32] (logw > 0)
+  T* sign = tile + (logw > 0 ? ((size_t)kFwhtCols << L) : 0);  // [2^L], first pass only
   const int cb = blockIdx.x % ncb;
   const long long grp = blockIdx.x / ncb;
   const long long lo = grp & ((1ll << a) - 1);
   const long long hi = grp >> a;
-  const int c0 = cb * kFwhtCols;
-  const int tid = threadIdx.x;
+  const long long base = (hi << (a + L)) + lo;
+  const int w = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const int col = cb * kFwhtCols + c;
+  const bool cok = col < d;
   if (first) {
     // one Philox evaluation per row of the tile, not per element
-    for (int j = tid; j < T_rows; j += blockDim.x) {
-      const long long r = (hi << (a + L)) + ((long long)j << a) + lo;
+    for (int j = threadIdx.x; j < (1 << L); j += blockDim.x) {
+      const long long r = base + ((long long)j << a);
       sign[j] = (r < n) ? (T)srht_sign(key, (uint32_t)r) : T(0);
     }
     __syncthreads();
   }
-  for (int e = tid; e < T_rows * kFwhtCols; e += blockDim.x) {
-    const int j = e / kFwhtCols, c = e % kFwhtCols;
-    const long long r = (hi << (a + L)) + ((long long)j << a) + lo;
-    T v = T(0);
-    if (c0 + c < d) {
-      if (first) {
-        if (r < n) v = A[r * lda + c0 + c] * sign[j];
-      } else {
-        v = B[r * ldb + c0 + c];
+  T v[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = w * R + i;
+    const long long r = base + ((long long)j << a);
+    T x = T(0);
+    if (first) {
+      if (cok && r < n) x = A[r * lda + col] * sign[j];
+    } else if (cok) {
+      x = B[r * ldb + col];
+    }
+    v[i] = x;
+  }
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      if (!(i & h)) {
+        const T u = v[i], z = v[i + h];
+        v[i] = u + z;
+        v[i + h] = u - z;
       }
-    }
-    tile[e] = v;
-  }
-  __syncthreads();
-  for (int h = 1; h < T_rows; h <<= 1) {
-    for (int e = tid; e < (T_rows / 2) * kFwhtCols; e += blockDim.x) {
-      const int p = e / kFwhtCols, c = e % kFwhtCols;
-      const int j0 = (p / h) * 2 * h + (p % h);
-      const T u = tile[j0 * kFwhtCols + c], w = tile[(j0 + h) * kFwhtCols + c];
-      tile[j0 * kFwhtCols + c] = u + w;
-      tile[(j0 + h) * kFwhtCols + c] = u - w;
-    }
+  if (logw > 0) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) tile[(size_t)(w * R + i) * kFwhtCols + c] = v[i];
     __syncthreads();
+    const int W = 1 << logw;
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = tile[(size_t)(i * W + w) * kFwhtCols + c];
+#pragma unroll
+    for (int b = 0; b < LOGR; ++b) {
+      if (b < LOGR - logw) continue;
+      const int h = 1 << b;
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+        if (!(i & h)) {
+          const T u = v[i], z = v[i + h];
+          v[i] = u + z;
+          v[i + h] = u - z;
+        }
+    }
+    if (cok)
+#pragma unroll
+      for (int i = 0; i < R; ++i) B[(base + ((long long)(i * W + w) << a)) * ldb + col] = v[i];
+  } else if (cok) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) B[(base + ((long long)i << a)) * ldb + col] = v[i];
   }
-  for (int e = tid; e < T_rows * kFwhtCols; e += blockDim.x) {
-    const int j = e / kFwhtCols, c = e % kFwhtCols;
-    const long long r = (hi << (a + L)) + ((long long)j << a) + lo;
-    if (c0 + c < d) B[r * ldb + c0 + c] = tile[e];
-  }
+}
+
+template <typename T, int LOGR>
+sks_status fwht_launch(cudaStream_t stream, const T* A, long long lda, int64_t n, T* B, long long ldb, int d, int a,
+                       int logw, int bits, int first, Key key) {
+  const int L = LOGR + logw;
+  const int ncb = (d + kFwhtCols - 1) / kFwhtCols;
+  const long long blocks = (1ll << (bits - L)) * ncb;
+  if (blocks > 0x7fffffffll) return fail(SKS_ERR_UNSUPPORTED, "FWHT grid too large");
+  const size_t smem = (logw > 0 ? ((size_t)kFwhtCols << L) * sizeof(T) : 0) + (first ? ((size_t)1 << L) * sizeof(T) : 0);
+  SKS_CUDA_TRY(cudaFuncSetAttribute(fwht_pass_kernel<T, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  fwht_pass_kernel<T, LOGR><<<(unsigned)blocks, 32 << logw, smem, stream>>>(A, lda, n, B, ldb, d, a, logw, first,
+                                                                           key, ncb);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
 }
 
 // Y[r] = B[pi(r)] for r in [r0, r1); one CTA per row.
@@ -198,31 +243,29 @@ template <typename T>
 sks_status srht_form(cudaStream_t stream, const T* A, long long lda, int64_t n, int d, T* B, long long ldb,
                      uint64_t seed) {
   const int bits = ilog2_ceil(n);
-  const int Lmax = 9;  // 512 rows x 16 columns per CTA
-  const int ncb = (d + kFwhtCols - 1) / kFwhtCols;
+  // levels per pass: up to 2^6 (float) / 2^5 (float64) rows per thread in
+  // registers times up to 8 warps; passes balanced in size
+  constexpr int kLogRMax = sizeof(T) == 4 ? 6 : 5;
+  constexpr int kLMax = kLogRMax + 3;
+  const int passes = bits == 0 ? 1 : (bits + kLMax - 1) / kLMax;
+  const Key key = make_key(seed);
   int a = 0;
-  bool first = true;
-  if (bits == 0) {
-    // n_pad = 1: B = E A
-    const int L = 0;
-    const size_t smem = (size_t)(kFwhtCols + 1) * sizeof(T);
-    fwht_pass_kernel<T><<<ncb, 256, smem, stream>>>(A, lda, n, B, ldb, d, 0, L, 1, make_key(seed));
-    note_launch();
-    SKS_CUDA_TRY(cudaGetLastError());
-    return SKS_OK;
-  }
-  while (a < bits) {
-    const int L = std::min(Lmax, bits - a);
-    const long long groups = 1ll << (bits - L);
-    const long long blocks = groups * ncb;
-    const size_t smem = ((size_t)1 << L) * (kFwhtCols + 1) * sizeof(T);
-    if (blocks > 0x7fffffffll) return fail(SKS_ERR_UNSUPPORTED, "FWHT grid too large");
-    SKS_CUDA_TRY(cudaFuncSetAttribute(fwht_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fwht_pass_kernel<T><<<(unsigned)blocks, 256, smem, stream>>>(A, lda, n, B, ldb, d, a, L, first ? 1 : 0,
-                                                                 make_key(seed));
-    note_launch();
-    SKS_CUDA_TRY(cudaGetLastError());
-    first = false;
+  for (int p = 0; p < passes; ++p) {
+    const int L = bits / passes + (p < bits % passes ? 1 : 0);
+    const int logw = std::min(3, L / 2);
+    const int logr = L - logw;
+    const int first = p == 0 ? 1 : 0;
+    sks_status st;
+    switch (logr) {
+      case 0: st = fwht_launch<T, 0>(stream, A, lda, n, B, ldb, d, a, logw, bits, first, key); break;
+      case 1: st = fwht_launch<T, 1>(stream, A, lda, n, B, ldb, d, a, logw, bits, first, key); break;
+      case 2: st = fwht_launch<T, 2>(stream, A, lda, n, B, ldb, d, a, logw, bits, first, key); break;
+      case 3: st = fwht_launch<T, 3>(stream, A, lda, n, B, ldb, d, a, logw, bits, first, key); break;
+      case 4: st = fwht_launch<T, 4>(stream, A, lda, n, B, ldb, d, a, logw, bits, first, key); break;
+      case 5: st = fwht_launch<T, 5>(stream, A, lda, n, B, ldb, d, a, logw, bits, first, key); break;
+      default: st = fwht_launch<T, (sizeof(T) == 4 ? 6 : 5)>(stream, A, lda, n, B, ldb, d, a, logw, bits, first, key);
+    }
+    if (st != SKS_OK) return st;
     a += L;
   }
   return SKS_OK;

@@ -113,6 +113,20 @@ def test_sketch_growth_is_nested(kind):
         assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-12), (torch.float32, 1e-7)])
+def test_srht_multi_pass_transform(dt, tol):
+    # n_pad = 2^19: the transform runs in three passes of 7, 6 and 6 levels;
+    # d = 37 leaves a ragged column block of 5.
+    rng = np.random.default_rng(19)
+    n, d, m = 300001, 37, 200
+    A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+    sk = api().Sketch(dev(A, dt), 0.1, dev(np.ones(d)), kind="srht", m=m, seed=21)
+    got = host(sk.matrix())
+    ref = OS.sketch("srht", A, m, seed=21)
+    scale = np.sqrt(np.sum(A * A, axis=0))[None, :] * math.sqrt(OS.next_pow2(n) / m)
+    assert float(np.max(np.abs(got - ref) / scale)) < tol
+
+
 def test_srht_full_size_gives_exact_hessian():
     # m = n_pad: S^T S = I, so (SA)^T SA = A^T A exactly (up to rounding).
     rng = np.random.default_rng(1)

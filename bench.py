@@ -48,11 +48,11 @@ WORKLOADS = {
     # C3: the metric's comparison -- mixed+refined on the float32 A vs plain float64 on its exact
     # float64 upcast, same embedding; m capped at 2d (the paper's non-adaptive sketch size).
     "C3": dict(config="C3", method="pcg", kind="sjlt", sjlt_s=4, m_init=1, m_max=8192, tol=1e-8,
-               precision="mixed", compare_plain=True, cpu_rows=1 << 16,
+               precision="mixed", compare_plain=True, cpu_rows=1 << 14, ref_rows=1 << 13,
                desc="mixed+refined adaptive PCG (float32 A, SJLT s=4, float64 refinement) vs plain float64 "
                     "adaptive PCG on the same problem: n=2^20, d=4096, sigma_j=0.98^j+1e-6, nu=1e-4, tol 1e-8"),
     "C3-srht": dict(config="C3", method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=8192, tol=1e-8,
-                    precision="mixed", compare_plain=True, cpu_rows=1 << 16,
+                    precision="mixed", compare_plain=True, cpu_rows=1 << 14, ref_rows=1 << 13,
                     desc="C3 with the SRHT for both forms"),
     # reduced C3 (n = 2^17, A = 2 GiB float32) for ncu captures of the float32 kernels
     "C3-profile": dict(config="C3", n=1 << 17, method="pcg", kind="sjlt", sjlt_s=4, m_init=1, m_max=8192, tol=1e-8,
@@ -66,7 +66,14 @@ WORKLOADS = {
 # ncu DRAM traffic per A-pass launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by the source hash of the kernel file it was captured from; any change
 # to the kernel source invalidates the figure (traffic then reported as null).
-TRAFFIC = {}
+# float32 A-pass (inner PCG): captured at n=2^17, d=4096 (C3-srht-profile, three launches, mean
+# 2.147645 GB read + 5.61 MB written); the n=2^20 workloads run the same kernel with the same grid,
+# so the read bytes scale by 8 with the rows and the partial-sum writes stay.
+TRAFFIC = {
+    ("d586c9bbca7c43f5", "C3-srht-profile"): 2147645000 + 5613000,
+    ("d586c9bbca7c43f5", "C3"): 8 * 2147645000 + 5613000,
+    ("d586c9bbca7c43f5", "C3-srht"): 8 * 2147645000 + 5613000,
+}
 
 
 def kernel_hash():
@@ -166,12 +173,36 @@ def oracle_solve(wl, A, b, nu, lam):
     """The CPU oracle's adaptive solve, as it stands (test infrastructure)."""
     from oracle import solvers as O
     fn = O.adaptive_pcg if wl["method"] == "pcg" else O.adaptive_ihs
-    kw = dict(kind=wl["kind"], seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"])
+    kw = dict(kind=wl["kind"], seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"],
+              sjlt_s=wl.get("sjlt_s", 1))
     return fn(A, b, nu, lam, **kw)
 
 
+def oracle_sample(wl, A64, rows, nu, lam):
+    """One timed oracle solve on the first `rows` rows of A (b = A_s^T y, y ~ N(0,1)); returns ms."""
+    A_np = A64[:rows].cpu().numpy() if torch.is_tensor(A64) else A64[:rows]
+    b_np = A_np.T @ np.random.default_rng(0).standard_normal(rows)
+    t0 = time.perf_counter()
+    oracle_solve(wl, A_np, b_np, nu, lam)
+    return (time.perf_counter() - t0) * 1e3
+
+
+def extrapolate(t_small, r_small, t_large, r_large, n):
+    """Two-point model t(n) = f + g n: the sketch and A-pass work grows with the
+    rows, the Gram and factorisation work does not.  Falls back to scaling by
+    n / rows if the fitted slope is not positive."""
+    g = (t_large - t_small) / (r_large - r_small)
+    if g <= 0:
+        return t_large * n / r_large, None
+    return t_large + g * (n - r_large), g
+
+
 def run_reference(args, wl, world, rank):
-    """--impl reference: the CPU oracle on the host cores, same workload."""
+    """--impl reference: the CPU oracle on the host cores, same workload.
+
+    Workloads that carry `ref_rows` time each step on a bounded row sample and
+    extrapolate to all n rows with the two-point model of `extrapolate` (the
+    slope comes from one untimed warm-up solve on twice the rows)."""
     if rank != 0:
         return None
     import synthetic
@@ -182,27 +213,46 @@ def run_reference(args, wl, world, rank):
     lam = prob["lam"].cpu().numpy()
     nu = prob["nu"]
     del prob
-    # warm-up steps: the same solver on the first n/32 rows (untimed)
-    nw = max(A.shape[0] // 32, 4 * A.shape[1])
-    for _ in range(args.warmup):
-        oracle_solve(wl, A[:nw], A[:nw].T @ np.ones(nw), nu, lam)
-    times = []
+    n, d = A.shape
+    rows = min(wl.get("ref_rows") or n, n)
+    t_large = None
+    for i in range(args.warmup):
+        if i == 0 and rows < n:
+            t_large = oracle_sample(wl, A, min(2 * rows, n), nu, lam)
+        else:  # untimed warm-up on a small slice
+            nw, dw = 4 * min(d, 256), min(d, 256)
+            oracle_solve(wl, A[:nw, :dw], A[:nw, :dw].T @ np.ones(nw), nu, lam[:dw])
+    if rows < n and t_large is None:
+        t_large = oracle_sample(wl, A, min(2 * rows, n), nu, lam)
+    times, raw = [], []
+    st = None
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        x, st, _ = oracle_solve(wl, A, b, nu, lam)
-        times.append((time.perf_counter() - t0) * 1e3)
+        if rows >= n:
+            t0 = time.perf_counter()
+            x, st, _ = oracle_solve(wl, A, b, nu, lam)
+            times.append((time.perf_counter() - t0) * 1e3)
+        else:
+            t = oracle_sample(wl, A, rows, nu, lam)
+            raw.append(t)
+            times.append(extrapolate(t, rows, t_large, min(2 * rows, n), n)[0])
     ms = sum(times) / len(times)
+    if rows >= n:
+        sample = "one full oracle adaptive solve of the workload per step"
+    else:
+        sample = ("per step: oracle adaptive solve (float64) on the first %d of %d rows (%.0f ms), extrapolated "
+                  "to n with t(n) = f + g n fitted to that and one solve on %d rows (%.0f ms)"
+                  % (rows, n, sum(raw) / len(raw), min(2 * rows, n), t_large))
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": wl["config"] + ": " + wl["desc"], "method": "adaptive_" + wl["method"]},
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": "one full oracle adaptive solve of the workload per step "
-                                   "(warm-up steps on the first n/32 rows)"},
+        "config": {"workload": wl["config"] + ": " + wl["desc"], "method": "adaptive_" + wl["method"],
+                   "n": n, "d": d, "kind": wl["kind"], "precision": "plain (oracle, float64)"},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "oracle_stats": {k: st[k] for k in ("iters", "rejections", "final_m", "a_passes")},
     }
+    if st is not None:
+        line["oracle_stats"] = {k: st[k] for k in ("iters", "rejections", "final_m", "a_passes")}
     return line
 
 
@@ -263,7 +313,7 @@ def run_ours(args, wl, world, rank, local):
     gbs = bytes_per_pass / (ap_avg_ms * 1e-3) / 1e9
     peaks, peak_src = load_peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-    th = TRAFFIC.get(kernel_hash() + ("f32" if mixed else "f64"))
+    th = TRAFFIC.get((kernel_hash(), args.workload)) if mixed else None
     if mixed:
         # float32 A-pass: 1 flop per byte, HBM-bound
         roofline = {
@@ -377,15 +427,14 @@ def run_ours(args, wl, world, rank, local):
                                     "oracle_rel_err_H": O.rel_err_H(A_np, nu, lam_np, xo, xs)}
             line["rel_err_H_vs_oracle"] = O.rel_err_H(A_np, nu, lam_np, x.cpu().numpy(), xs)
         else:
-            # bounded sample: the oracle's solve on the first `rows` rows, scaled by n / rows
-            A_np = A64[:rows].cpu().numpy()
-            b_np = A_np.T @ np.random.default_rng(0).standard_normal(rows)
-            t0 = time.perf_counter()
-            oracle_solve(wl, A_np, b_np, nu, lam_np)
-            cpu_ms = (time.perf_counter() - t0) * 1e3 * (n / rows)
+            # bounded sample: oracle solves on the first rows / 2 and rows rows, extrapolated to n
+            t_small = oracle_sample(wl, A64, rows // 2, nu, lam_np)
+            t_large = oracle_sample(wl, A64, rows, nu, lam_np)
+            cpu_ms, g = extrapolate(t_small, rows // 2, t_large, rows, n)
             line["cpu_baseline"] = {"value": cpu_ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
-                                    "sample": "oracle adaptive solve (float64) on the first %d of %d rows, time "
-                                              "scaled by %d" % (rows, n, n // rows)}
+                                    "sample": "oracle adaptive solves (float64) on the first %d and %d of %d rows "
+                                              "(%.0f ms, %.0f ms), extrapolated to n with t(n) = f + g n"
+                                              % (rows // 2, rows, n, t_small, t_large)}
             # accuracy of the GPU result: the oracle's relative H-error from A itself (one float64 pass)
             A_all = A64.cpu().numpy()
             xs = O.direct_solve(A_all, b_h.numpy(), nu, lam_np)
@@ -399,7 +448,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="C3", choices=sorted(WORKLOADS))
     ap.add_argument("--method", choices=["pcg", "ihs"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

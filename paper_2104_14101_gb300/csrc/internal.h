@@ -97,6 +97,12 @@ size_t apass_workspace_bytes(int64_t n, int64_t d, int64_t k, bool a_f32, bool v
 void apass_use_bulk(ApassPlan* plan, const void* A, int64_t d, int64_t lda, bool a_f32);
 
 // ---------------------------------------------------------------- solver entry points (solver.cu)
+// Host-side checks of a problem description (sizes, pointers, alignment).
+sks_status validate_problem(const sks_problem* p);
+// Reads the device status word (one stream synchronisation) and turns a
+// device-side error into an sks_status with a message naming `what`.
+sks_status read_status(DevStatus* st, cudaStream_t stream, const char* what);
+
 sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes);
 // method 0: adaptive PCG (Algorithm 2); 1: adaptive IHS (Algorithm 1)
 sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,

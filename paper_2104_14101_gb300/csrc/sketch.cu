@@ -11,10 +11,12 @@
 //     permutation (nested subsampling R).
 //  K4 Gaussian: Y[r] = sum_i G[r][i] a_i, G from Philox + Box-Muller, produced
 //     chunk by chunk and multiplied with the CUDA-core GEMM (float64 form).
-//  K5 SJLT: Y[h_k(i)] += sigma_k(i)/sqrt(s_eff) a_i, one warp per data row,
-//     float64 atomics.
+//  K5 SJLT: Y[h_k(i)] += sigma_k(i)/sqrt(s_eff) a_i, one warp per (data row,
+//     512-column block), column blocks in sequence so the live part of Y
+//     stays in L2; small sketches accumulate in shared memory first.
 // All sketches are stored unscaled (S A = scale * Y).
 #include <algorithm>
+#include <type_traits>
 
 #include "sketch.h"
 #include "dense.h"
@@ -171,64 +173,133 @@ __global__ void gauss_gen_kernel(Key key, int m_off, int m_add, int64_t i0, int 
   }
 }
 
-// SJLT scatter: one warp per data row; float32 sketches add 16-byte vectors
-// with one atomic each (4x fewer L2 atomic operations than scalar adds).
+// SJLT scatter, tiled by column blocks: warp = one data row x one block of
+// kSjltCols columns, and the grid walks all rows of one column block before
+// the next, so the live part of Y (m x kSjltCols) stays in L2 while the
+// atomics land.  float32 sketches add 16-byte vectors with one atomic each.
+constexpr int kSjltCols = 512;
 template <typename TA, typename TY>
-__global__ void sjlt_scatter_kernel(const TA* __restrict__ A, long long lda, int64_t n, int d, uint32_t m, int s_eff,
-                                    Key key, TY* __restrict__ Y, long long ldy) {
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(256) sjlt_scatter_kernel(const TA* __restrict__ A, long long lda, int64_t n, int d,
+                                                          uint32_t m, int s_eff, Key key, TY* __restrict__ Y,
+                                                          long long ldy, long long row_blocks) {
+  const long long cb = blockIdx.x / row_blocks;
+  const long long i = (blockIdx.x - cb * row_blocks) * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
+  if (i >= n) return;
   uint32_t rows[kSjltMaxS];
   float signs[kSjltMaxS];
-  sjlt_hash(key, (uint32_t)warp, m, s_eff, rows, signs);
+  sjlt_hash(key, (uint32_t)i, m, s_eff, rows, signs);
   const TY inv = (TY)(1.0 / sqrt((double)s_eff));
-  const TA* a = A + warp * lda;
+  const TA* a = A + i * lda;
+  const int c0 = (int)cb * kSjltCols;
+  const int c1 = min(d, c0 + kSjltCols);
   if (sizeof(TY) == 4 && sizeof(TA) == 4 && (d & 3) == 0 && (lda & 3) == 0 && (ldy & 3) == 0) {
-    for (int c = lane * 4; c < d; c += 128) {
+#pragma unroll 4
+    for (int c = c0 + lane * 4; c < c1; c += 128) {
       const float4 v = __ldcs((const float4*)(a + c));  // streamed once: evict first, keep Y in L2
-      for (int k = 0; k < s_eff; ++k) {
+#pragma unroll
+      for (int k = 0; k < kSjltMaxS; ++k) {
+        if (k >= s_eff) break;
         const float w = signs[k] * (float)inv;
         atomicAdd((float4*)(Y + (long long)rows[k] * ldy + c), make_float4(w * v.x, w * v.y, w * v.z, w * v.w));
       }
     }
     return;
   }
-  for (int c = lane; c < d; c += 32) {
+  for (int c = c0 + lane; c < c1; c += 32) {
     const TY v = (TY)__ldcs(a + c) * inv;
-    for (int k = 0; k < s_eff; ++k) atomicAdd(&Y[(long long)rows[k] * ldy + c], (TY)signs[k] * v);
+#pragma unroll
+    for (int k = 0; k < kSjltMaxS; ++k) {
+      if (k >= s_eff) break;
+      atomicAdd(&Y[(long long)rows[k] * ldy + c], (TY)signs[k] * v);
+    }
   }
 }
 
-// Small sketches (m * d fits in shared memory): every CTA accumulates its
-// rows into a private copy of Y and flushes it with one atomic per entry.
-template <typename TA, typename TY>
-__global__ void __launch_bounds__(256) sjlt_private_kernel(const TA* __restrict__ A, long long lda, int64_t n, int d,
-                                                          uint32_t m, int s_eff, Key key, TY* __restrict__ Y,
-                                                          long long ldy, int64_t rows_per_cta) {
+// Small sketches (m rows of a column block fit in shared memory): the CTA
+// owns a block of 256 * VEC columns and a contiguous chunk of data rows;
+// thread t owns columns [t * VEC, t * VEC + VEC) of every one of the m partial
+// rows, so it accumulates without atomics.  The hashes of 256 rows at a time
+// are formed once into shared memory; the partial rows are flushed with one
+// (vector) atomic per entry at the end.
+template <typename T>
+struct SjVec;
+template <>
+struct SjVec<float> {
+  static constexpr int N = 4;
+  using V = float4;
+  static SKS_DEV V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static SKS_DEV void axpy(V& y, float w, const V& x) {
+    y.x += w * x.x;
+    y.y += w * x.y;
+    y.z += w * x.z;
+    y.w += w * x.w;
+  }
+  static SKS_DEV void flush(float* dst, const V& v) { atomicAdd((float4*)dst, v); }
+};
+template <>
+struct SjVec<double> {
+  static constexpr int N = 2;
+  using V = double2;
+  static SKS_DEV V zero() { return make_double2(0.0, 0.0); }
+  static SKS_DEV void axpy(V& y, double w, const V& x) {
+    y.x += w * x.x;
+    y.y += w * x.y;
+  }
+  static SKS_DEV void flush(double* dst, const V& v) {
+    atomicAdd(dst, v.x);
+    atomicAdd(dst + 1, v.y);
+  }
+};
+
+constexpr int kSjBlockThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kSjBlockThreads) sjlt_block_kernel(const T* __restrict__ A, long long lda, int64_t n,
+                                                                    int d, uint32_t m, int s_eff, Key key,
+                                                                    T* __restrict__ Y, long long ldy, int ncb,
+                                                                    int64_t rows_per_cta) {
+  using SV = SjVec<T>;
+  using V = typename SV::V;
+  constexpr int VEC = SV::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TY* Ys = (TY*)smem_raw;  // m x d
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < (int)m * d; e += blockDim.x) Ys[e] = TY(0);
-  __syncthreads();
-  const TY inv = (TY)(1.0 / sqrt((double)s_eff));
-  const int64_t r0 = blockIdx.x * rows_per_cta;
+  V* Ys = (V*)smem_raw;                                                   // [m][256]
+  uint32_t* hrow = (uint32_t*)(Ys + (size_t)m * kSjBlockThreads);          // [256][s_eff]
+  float* hsgn = (float*)(hrow + (size_t)kSjBlockThreads * s_eff);          // [256][s_eff]
+  const int tid = threadIdx.x;
+  const int cb = blockIdx.x % ncb;
+  const int64_t r0 = (int64_t)(blockIdx.x / ncb) * rows_per_cta;
   const int64_t r1 = min(n, r0 + rows_per_cta);
-  for (int64_t i = r0 + warp; i < r1; i += blockDim.x / 32) {
-    uint32_t rows[kSjltMaxS];
-    float signs[kSjltMaxS];
-    sjlt_hash(key, (uint32_t)i, m, s_eff, rows, signs);
-    const TA* a = A + i * lda;
-    for (int c = lane; c < d; c += 32) {
-      const TY v = (TY)a[c] * inv;
-      for (int k = 0; k < s_eff; ++k) atomicAdd(&Ys[rows[k] * d + c], (TY)signs[k] * v);
+  const int c = cb * kSjBlockThreads * VEC + tid * VEC;
+  const bool cok = c < d;
+  for (uint32_t h = 0; h < m; ++h) Ys[(size_t)h * kSjBlockThreads + tid] = SV::zero();
+  const T inv = (T)(1.0 / sqrt((double)s_eff));
+  for (int64_t base = r0; base < r1; base += kSjBlockThreads) {
+    __syncthreads();  // previous batch's hashes fully consumed
+    if (base + tid < r1) {
+      uint32_t rows[kSjltMaxS];
+      float signs[kSjltMaxS];
+      sjlt_hash(key, (uint32_t)(base + tid), m, s_eff, rows, signs);
+      for (int k = 0; k < s_eff; ++k) {
+        hrow[tid * s_eff + k] = rows[k];
+        hsgn[tid * s_eff + k] = signs[k];
+      }
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)kSjBlockThreads, r1 - base);
+    if (!cok) continue;
+    const T* a = A + base * lda + c;
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) {
+      const V v = *(const V*)(a + (int64_t)j * lda);
+      for (int k = 0; k < s_eff; ++k) {
+        V& y = Ys[(size_t)hrow[j * s_eff + k] * kSjBlockThreads + tid];
+        SV::axpy(y, (T)hsgn[j * s_eff + k] * inv, v);
+      }
     }
   }
-  __syncthreads();
-  for (int e = tid; e < (int)m * d; e += blockDim.x) {
-    const int r = e / d, c = e % d;
-    atomicAdd(&Y[(long long)r * ldy + c], Ys[e]);
-  }
+  if (!cok) return;
+  for (uint32_t h = 0; h < m; ++h) SV::flush(Y + (long long)h * ldy + c, Ys[(size_t)h * kSjBlockThreads + tid]);
 }
 
 }  // namespace
@@ -327,22 +398,29 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
   if (n == 0) return SKS_OK;
   const int s_eff = std::min(s, m);
   if (s_eff > kSjltMaxS) return fail(SKS_ERR_UNSUPPORTED, "SJLT s > 16");
-  const size_t priv_bytes = (size_t)m * d * sizeof(TY);
-  if (priv_bytes <= 96 * 1024) {
+  // small m: column-block kernel (rows of A read as 16-byte vectors, partial
+  // rows in shared memory, no atomics but the final flush)
+  constexpr int VEC = 16 / sizeof(TY);
+  const size_t blk_bytes = (size_t)m * kSjBlockThreads * 16 + (size_t)kSjBlockThreads * s_eff * 8;
+  if (std::is_same<TA, TY>::value && blk_bytes <= 64 * 1024 && d % VEC == 0 && lda % VEC == 0 && ldy % VEC == 0 &&
+      ((uintptr_t)A & 15) == 0 && ((uintptr_t)Y & 15) == 0) {
     const int sms = device_info().sms > 0 ? device_info().sms : 152;
-    const int64_t ctas = std::min<int64_t>((int64_t)sms * 2, (n + 255) / 256);
-    const int64_t per = (n + ctas - 1) / ctas;
-    SKS_CUDA_TRY(cudaFuncSetAttribute(sjlt_private_kernel<TA, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)priv_bytes));
-    sjlt_private_kernel<TA, TY><<<(unsigned)ctas, 256, priv_bytes, stream>>>(A, lda, n, d, (uint32_t)m, s_eff,
-                                                                          make_key(seed), Y, ldy, per);
+    const int ncb = (d + kSjBlockThreads * VEC - 1) / (kSjBlockThreads * VEC);
+    const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ((int64_t)sms * 8 + ncb - 1) / ncb));
+    const int64_t per = (n + chunks - 1) / chunks;
+    auto kern = sjlt_block_kernel<TY>;
+    SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_bytes));
+    kern<<<(unsigned)(chunks * ncb), kSjBlockThreads, blk_bytes, stream>>>((const TY*)A, lda, n, d, (uint32_t)m, s_eff,
+                                                                          make_key(seed), Y, ldy, ncb, per);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     return SKS_OK;
   }
-  const long long threads = n * 32;
-  sjlt_scatter_kernel<TA, TY><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(A, lda, n, d, (uint32_t)m, s_eff,
-                                                                                    make_key(seed), Y, ldy);
+  const long long row_blocks = (n + 7) / 8;
+  const long long blocks = row_blocks * ((d + kSjltCols - 1) / kSjltCols);
+  if (blocks > 0x7fffffffll) return fail(SKS_ERR_UNSUPPORTED, "SJLT grid too large");
+  sjlt_scatter_kernel<TA, TY><<<(unsigned)blocks, 256, 0, stream>>>(A, lda, n, d, (uint32_t)m, s_eff, make_key(seed),
+                                                                   Y, ldy, row_blocks);
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;

@@ -65,9 +65,6 @@ struct sks_precond {
 
 namespace sks {
 
-namespace {
-
-// ---------------------------------------------------------------- validation
 sks_status validate_problem(const sks_problem* p) {
   if (!p) return fail(SKS_ERR_INVALID_ARG, "problem is NULL");
   if (p->n < 0 || p->d < 1 || p->k < 1) return fail(SKS_ERR_INVALID_ARG, "need n >= 0, d >= 1, k >= 1");
@@ -84,11 +81,6 @@ sks_status validate_problem(const sks_problem* p) {
   return SKS_OK;
 }
 
-__global__ void check_lambda_kernel(int d, const double* lam, DevStatus* st) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < d && !(lam[i] >= 1.0 && isfinite(lam[i]))) raise_status(st, SKS_ERR_INVALID_ARG, 1, i);
-}
-
 sks_status read_status(DevStatus* st, cudaStream_t stream, const char* what) {
   DevStatus h;
   SKS_CUDA_TRY(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, stream));
@@ -103,6 +95,15 @@ sks_status read_status(DevStatus* st, cudaStream_t stream, const char* what) {
   }
   return SKS_OK;
 }
+
+namespace {
+
+// ---------------------------------------------------------------- validation
+__global__ void check_lambda_kernel(int d, const double* lam, DevStatus* st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d && !(lam[i] >= 1.0 && isfinite(lam[i]))) raise_status(st, SKS_ERR_INVALID_ARG, 1, i);
+}
+
 
 sks_status map_for(const sks_problem* p, CUtensorMap* map, const ApassPlan& pl) {
   const bool f32 = p->dtype == SKS_F32;

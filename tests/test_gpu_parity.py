@@ -127,6 +127,20 @@ def test_srht_multi_pass_transform(dt, tol):
     assert float(np.max(np.abs(got - ref) / scale)) < tol
 
 
+@pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
+@pytest.mark.parametrize("n,d,m", [(5000, 1000, 1), (3001, 2052, 3), (4096, 64, 8), (777, 36, 13)])
+def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
+    # small m: the column-block kernel (partial rows in shared memory); d = 2052
+    # spans three column blocks of 1024 float32 columns, the last one ragged.
+    rng = np.random.default_rng(n + d + m)
+    A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+    sk = api().Sketch(dev(A, dt), 0.1, dev(np.ones(d)), kind="sjlt", m=m, sjlt_s=4, seed=99)
+    got = host(sk.matrix())
+    ref = OS.sketch("sjlt", A, m, seed=99, sjlt_s=4)
+    scale = np.sqrt(np.sum(A * A, axis=0))[None, :]
+    assert float(np.max(np.abs(got - ref) / scale)) < tol
+
+
 def test_srht_full_size_gives_exact_hessian():
     # m = n_pad: S^T S = I, so (SA)^T SA = A^T A exactly (up to rounding).
     rng = np.random.default_rng(1)

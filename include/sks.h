@@ -253,6 +253,45 @@ sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const double* x,
                        void* dA, int64_t ldda, double* dnu, double* dlambda, sks_stats* stats,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched solve: `count` independent problems of eq. 1, each by the adaptive
+ * PCG of Algorithm 2 with the same options (float64 plain form, SRHT
+ * embedding, one right-hand side per problem, d <= 1024, n >= 1).  Every
+ * decision of Algorithm 2 is taken on the device, per problem, so one round of
+ * batched kernels advances every unfinished problem by one step or one
+ * re-sketch; the round is captured once as a CUDA graph and replayed until all
+ * problems have stopped.  Each problem's iterates, m sequence and stop are
+ * those of sks_adaptive_pcg_solve with the same options (up to the rounding
+ * order of the sums); the same seed serves every problem.
+ * probs:  host array of `count` problem descriptions (device A, b, lambda).
+ * x:      host array of `count` device pointers, d_i float64 each; in: x_0,
+ *         out: the solution (the last accepted iterate for a problem that
+ *         stopped with an error).
+ * stats:  host array of `count`, may be NULL; stats[i].status is the problem's
+ *         own status.
+ * info:   host, may be NULL; batch timings and the chosen A-pass unit height.
+ * rows_per_unit: rows of A per A-pass work unit; 0 = chosen by timing the
+ *         candidates 32..512 on this batch (autotuning), else in [32, 65536].
+ * ws:     device scratch of sks_batch_workspace_size bytes (holds H E A_pad of
+ *         every problem, the factors and the per-problem state).
+ * The call synchronises `stream` a few times (once per burst of replays).
+ * Returns SKS_OK when every problem met tol, else the status of the first
+ * failing problem (the others are still solved and reported in stats).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t rounds;            /* graph replays until every problem stopped            */
+  int64_t kernels_per_round; /* kernel nodes in the captured round                   */
+  int64_t rows_per_unit;     /* A-pass unit height used                              */
+  float ms_setup;            /* input checks, H E A_pad of every problem, states     */
+  float ms_autotune;         /* timing of the candidate unit heights                 */
+  float ms_solve;            /* graph replays                                        */
+} sks_batch_info;
+
+sks_status sks_batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes);
+sks_status sks_solve_batched(const sks_problem* probs, int count, const sks_opts* o, double* const* x,
+                             sks_stats* stats, sks_batch_info* info, int rows_per_unit, void* ws, size_t ws_bytes,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

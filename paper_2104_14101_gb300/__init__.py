@@ -6,6 +6,7 @@ all in hand-written CUDA behind the C ABI of include/sks.h.
 """
 from . import _lib  # noqa: F401
 from .api import (  # noqa: F401
+    BatchSolver,
     Preconditioner,
     Sketch,
     SketchSolve,
@@ -16,4 +17,5 @@ from .api import (  # noqa: F401
     make_problem,
     options,
     sketch_solve,
+    solve_batched,
 )

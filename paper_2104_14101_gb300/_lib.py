@@ -51,6 +51,14 @@ class Stats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("rounds", C.c_int64), ("kernels_per_round", C.c_int64), ("rows_per_unit", C.c_int64),
+                ("ms_setup", C.c_float), ("ms_autotune", C.c_float), ("ms_solve", C.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 P = C.POINTER
 _SIGS = {
     "sks_opts_default": (None, [P(Opts)]),
@@ -78,6 +86,9 @@ _SIGS = {
                                          C.c_void_p]),
     "sks_adjoint": (C.c_int, [P(Problem), P(Opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                               P(C.c_double), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sks_batch_workspace_size": (C.c_int, [P(Problem), C.c_int, P(Opts), P(C.c_size_t)]),
+    "sks_solve_batched": (C.c_int, [P(Problem), C.c_int, P(Opts), P(C.c_void_p), P(Stats), P(BatchInfo), C.c_int,
+                                    C.c_void_p, C.c_size_t, C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

@@ -284,3 +284,51 @@ def adaptive_pcg(A, b, nu, lam, x0=None, trace_cap=0, **opts):
 def adaptive_ihs(A, b, nu, lam, x0=None, trace_cap=0, **opts):
     """Algorithm 1 with the IHS step (mu = 1 - rho) on the GPU; returns (x, stats, trace)."""
     return Solver(A, b, nu, lam, method="ihs", trace_cap=trace_cap, **opts).solve(x0)
+
+
+class BatchSolver:
+    """Many independent problems (each one (A, b, nu, lam)) solved together by
+    ``sks_solve_batched``: adaptive PCG per problem, every decision on the
+    device, one captured CUDA graph replayed until all have stopped.  The
+    workspace is sized and held once; ``solve`` may be called repeatedly."""
+
+    def __init__(self, problems, rows_per_unit=0, **opts):
+        self._lib = L.load()
+        if len(problems) < 1:
+            raise ValueError("need at least one problem")
+        self.items = [make_problem(A, b, nu, lam) for (A, b, nu, lam) in problems]
+        self.count = len(self.items)
+        self.arr = (L.Problem * self.count)(*[p for p, _ in self.items])
+        self.opts = options(**opts)
+        nb = C.c_size_t()
+        L.check(self._lib.sks_batch_workspace_size(self.arr, self.count, C.byref(self.opts), C.byref(nb)))
+        self.device = problems[0][0].device
+        self.ws = _workspace(nb.value, self.device)
+        self.rows_per_unit = int(rows_per_unit)
+        self.ds = [int(p.d) for p, _ in self.items]
+
+    def solve(self, x0s=None, check=True):
+        xs = [torch.zeros(d, dtype=torch.float64, device=self.device) for d in self.ds]
+        if x0s is not None:
+            for x, x0 in zip(xs, x0s):
+                x.copy_(x0.to(torch.float64))
+        ptrs = (C.c_void_p * self.count)(*[x.data_ptr() for x in xs])
+        st = (L.Stats * self.count)()
+        info = L.BatchInfo()
+        status = self._lib.sks_solve_batched(self.arr, self.count, C.byref(self.opts), ptrs, st, C.byref(info),
+                                             self.rows_per_unit, _ptr(self.ws), self.ws.numel(),
+                                             _stream(self.device))
+        if check and status != L.OK:
+            L.check(status)
+        stats = []
+        for s in st:
+            dct = s.as_dict()
+            dct["status_name"] = L.STATUS_NAMES.get(s.status, s.status)
+            stats.append(dct)
+        return xs, stats, info.as_dict()
+
+
+def solve_batched(problems, x0s=None, rows_per_unit=0, **opts):
+    """Adaptive PCG on a batch of problems [(A, b, nu, lam), ...]; returns
+    (xs, per-problem stats, batch info)."""
+    return BatchSolver(problems, rows_per_unit=rows_per_unit, **opts).solve(x0s)

@@ -54,3 +54,13 @@ extern "C" sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const
                                   void* ws, size_t ws_bytes, void* stream) {
   return adjoint(p, o, x, g, db, dA, ldda, dnu, dlambda, stats, ws, ws_bytes, (cudaStream_t)stream);
 }
+
+extern "C" sks_status sks_batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes) {
+  return batch_workspace_size(probs, count, o, bytes);
+}
+
+extern "C" sks_status sks_solve_batched(const sks_problem* probs, int count, const sks_opts* o, double* const* x,
+                                        sks_stats* stats, sks_batch_info* info, int rows_per_unit, void* ws,
+                                        size_t ws_bytes, void* stream) {
+  return solve_batched(probs, count, o, x, stats, info, rows_per_unit, ws, ws_bytes, (cudaStream_t)stream);
+}

@@ -1,0 +1,1105 @@
+// batched.cu -- many independent problems (1) solved together by the adaptive
+// PCG of Algorithm 2 (float64, SRHT embedding of Section 2.1).
+//
+// Every decision of Algorithm 2 (accept / reject, doubling of m, stop) is
+// taken on the device, per problem, so one ROUND -- a fixed sequence of
+// batched kernels -- advances every unfinished problem by one event: an
+// iteration, or a re-sketch with a new factorisation and a restart.  The
+// round is captured once as a CUDA graph and replayed until every problem has
+// finished; the host reads one counter every few replays.
+//
+// Per problem p the state machine is
+//   INIT  : r = b - H x0                         (one A-pass)      -> GROW
+//   GROW  : m <- m_init or min(2m, m_max); rows of the nested SRHT; form and
+//           factor the sketched Hessian (d x d Cholesky form when m >= d,
+//           m x m Woodbury form otherwise, Section 4.2); r~ = H_S^{-1} r;
+//           p = r~, delta~_t = delta~_I = r^T r~                 -> ITER
+//   ITER  : one PCG step with the improvement test of Algorithm 2; on
+//           rejection I = t                                        -> GROW
+//           on acceptance, stop when delta~ <= (tol/2)^2 b^T x   -> DONE
+// A round runs, in order: m update, permutation rows, Gram / Woodbury
+// matrix, blocked Cholesky (three kernels per 64-column panel), the A-pass of
+// every INIT / ITER problem, its reduction, the first half of the step, the
+// preconditioner apply, the second half of the step and the counter.
+//
+// Work distribution: each batched kernel walks a static list of units (row
+// tiles of A, 64 x 64 tiles of a factor, column chunks, problems) over all
+// problems with a persistent grid; a unit whose problem is not in the phase
+// the kernel serves is skipped.  The A-pass unit height (rows of A per unit)
+// is chosen by timing candidate heights on the actual batch (autotuning).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "sketch.h"
+
+namespace sks {
+namespace {
+
+enum : int { PH_INIT = 0, PH_GROW = 1, PH_ITER = 2, PH_DONE = 3, PH_FAIL = 4 };
+// d-vector slots of a problem
+enum : int { V_R = 0, V_RT, V_P, V_HV, V_XP, V_RP, V_RTP, V_U, V_W, V_DINV, kNumVec };
+
+constexpr int kTile = 64;           // dense tiles and Cholesky panels
+constexpr int kTP = kTile + 2;      // padded shared-memory row
+constexpr int kMaxD = 1024;         // A-pass: 32 lanes x 32 columns
+constexpr int kApWarps = 8;
+constexpr int kApThreads = 32 * kApWarps;
+
+struct BDesc {
+  const double* A;
+  long long lda;
+  int64_t n;
+  int d, bits;       // n_pad = 2^bits
+  const double* b;
+  const double* lam;
+  double nu2;
+  double* x;         // caller's x (x0 on entry)
+  const double* B;   // H E A_pad, n_pad x d, ld d
+  uint32_t* perm;    // sketch row r is B[perm[r]]
+  double* M;         // d x d, ld d: lower = factor L, strict upper = L^T
+  double* vec;       // kNumVec d-vectors
+  double* part;      // A-pass partial sums, one d-vector per unit
+  int64_t m_max, m_init;
+};
+
+struct BState {
+  int phase, form;   // form 0: Cholesky (N = d), 1: Woodbury (N = m)
+  int status, pad;
+  int64_t m, m_old, t, I;
+  double dt, dI, btx;
+  int64_t rejections, a_passes, factorizations;
+};
+
+struct BCtl {
+  int P;
+  int rows_per_unit;
+  int64_t max_iter;
+  double c, phi, tol2;
+  Key key;
+  const int* pre_tri;  // prefix over problems of T(T+1)/2, T = ceil(d / 64)
+  const int* pre_T;    // prefix of T
+  const int* pre_ap;   // prefix of ceil(n / rows_per_unit)
+  const int* pre_red;  // prefix of ceil(d / 256)
+  int* active;         // problems not finished after the round
+};
+
+// largest p with pre[p] <= u  (pre[0] = 0 <= u < pre[P])
+SKS_DEV int find_problem(const int* __restrict__ pre, int P, int u) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(pre + mid) <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+SKS_DEV void tri_index(int l, int* ti, int* tj) {
+  int i = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= l) ++i;
+  while (i * (i + 1) / 2 > l) --i;
+  *ti = i;
+  *tj = l - i * (i + 1) / 2;
+}
+
+SKS_DEV double block_dot(int d, const double* a, const double* b, double* scratch) {
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s += a[j] * b[j];
+  return block_sum(s, scratch);
+}
+
+SKS_DEV int factor_size(const BState& s, const BDesc& q) { return s.form == 0 ? q.d : (int)s.m; }
+
+// ------------------------------------------------------------------ round kernels
+
+__global__ void b_begin_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.P) return;
+  BState& s = S[p];
+  if (s.phase != PH_GROW) return;
+  const BDesc& q = D[p];
+  s.m_old = s.m;
+  s.m = s.m == 0 ? min(q.m_init, q.m_max) : min(2 * s.m, q.m_max);
+  s.form = s.m >= q.d ? 0 : 1;
+  s.factorizations += 1;
+}
+
+// perm[r] = pi(r) for the new sketch rows r in [m_old, m)
+__global__ void b_perm_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
+  for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    for (int64_t r = s.m_old + threadIdx.x; r < s.m; r += blockDim.x) {
+      const uint32_t v = feistel_perm(c.key, (uint32_t)r, q.bits);
+      q.perm[r] = v == 0xffffffffu ? 0u : v;
+      if (v == 0xffffffffu) {
+        S[p].status = SKS_ERR_NUMERIC;
+        S[p].phase = PH_FAIL;
+      }
+    }
+  }
+}
+
+// acc[i][j] += sum_k As[k][ty*4+i] Bs[k][tx*4+j] for one 16-deep chunk
+SKS_DEV void mma_chunk(const double (*As)[kTP], const double (*Bs)[kTP], double acc[4][4], int tx, int ty) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const double2 a01 = *(const double2*)&As[k][ty * 4];
+    const double2 a23 = *(const double2*)&As[k][ty * 4 + 2];
+    const double2 b01 = *(const double2*)&Bs[k][tx * 4];
+    const double2 b23 = *(const double2*)&Bs[k][tx * 4 + 2];
+    const double a[4] = {a01.x, a01.y, a23.x, a23.y};
+    const double b[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
+// Sketched-Hessian matrix of every GROW problem, lower 64 x 64 tiles:
+//   form 0: M = (1/m) Y^T Y + nu^2 Lambda          (Y = rows perm[0..m) of B)
+//   form 1: M = I + (1/(m nu^2)) Y Lambda^{-1} Y^T
+__global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
+                                                     int total) {
+  __shared__ __align__(16) double As[16][kTP];
+  __shared__ __align__(16) double Bs[16][kTP];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_tri, c.P, u);
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    int ti, tj;
+    tri_index(u - c.pre_tri[p], &ti, &tj);
+    const int N = factor_size(s, q);
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    if (i0 >= N) continue;
+    const int d = q.d;
+    const int m = (int)s.m;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    if (s.form == 0) {
+      for (int k0 = 0; k0 < m; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+          const int kk = e >> 6, ii = e & 63;
+          const int r = k0 + kk;
+          double a = 0.0, b = 0.0;
+          if (r < m) {
+            const double* y = q.B + (int64_t)q.perm[r] * d;
+            if (i0 + ii < N) a = y[i0 + ii];
+            if (j0 + ii < N) b = y[j0 + ii];
+          }
+          As[kk][ii] = a;
+          Bs[kk][ii] = b;
+        }
+        __syncthreads();
+        mma_chunk(As, Bs, acc, tx, ty);
+        __syncthreads();
+      }
+    } else {
+      for (int k0 = 0; k0 < d; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+          const int ii = e >> 4, kk = e & 15;
+          const int col = k0 + kk;
+          double a = 0.0, b = 0.0;
+          if (col < d) {
+            if (i0 + ii < N) a = q.B[(int64_t)q.perm[i0 + ii] * d + col] / q.lam[col];
+            if (j0 + ii < N) b = q.B[(int64_t)q.perm[j0 + ii] * d + col];
+          }
+          As[kk][ii] = a;
+          Bs[kk][ii] = b;
+        }
+        __syncthreads();
+        mma_chunk(As, Bs, acc, tx, ty);
+        __syncthreads();
+      }
+    }
+    const double scale = s.form == 0 ? 1.0 / (double)m : 1.0 / ((double)m * q.nu2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
+        if (gi < N && gj < N) {
+          double v = acc[i][j] * scale;
+          if (gi == gj) v += s.form == 0 ? q.nu2 * q.lam[gi] : 1.0;
+          q.M[(int64_t)gi * d + gj] = v;
+        }
+      }
+  }
+}
+
+// Panel k, diagonal block: L_kk = chol(M_kk) in shared memory; writes L_kk
+// (lower), L_kk^T (strict upper) and 1 / diag(L_kk).
+__global__ void __launch_bounds__(256) b_potrf_kernel(BCtl c, const BDesc* __restrict__ D, BState* S, int k) {
+  __shared__ double L[kTile][kTile + 1];
+  __shared__ int bad;
+  for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    const int N = factor_size(s, q);
+    const int k0 = k * kTile;
+    if (k0 >= N) continue;
+    const int nb = min(kTile, N - k0);
+    const int d = q.d;
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int i = e >> 6, j = e & 63;
+      L[i][j] = (i < nb && j <= i) ? q.M[(int64_t)(k0 + i) * d + k0 + j] : 0.0;
+    }
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      if (threadIdx.x == 0) {
+        const double v = L[j][j];
+        if (!(v > 0.0) || !isfinite(v)) {
+          bad = j + 1;
+          L[j][j] = 1.0;
+        } else {
+          L[j][j] = sqrt(v);
+        }
+      }
+      __syncthreads();
+      if (bad) break;
+      const double rjj = 1.0 / L[j][j];
+      for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) L[i][j] *= rjj;
+      __syncthreads();
+      const int w = nb - j - 1;
+      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int ii = e / w, ll = e - ii * w;
+        if (ll <= ii) L[j + 1 + ii][j + 1 + ll] -= L[j + 1 + ii][j] * L[j + 1 + ll][j];
+      }
+      __syncthreads();
+    }
+    if (bad) {
+      if (threadIdx.x == 0) {
+        S[p].status = SKS_ERR_NOT_PD;
+        S[p].phase = PH_FAIL;
+      }
+      __syncthreads();
+      continue;
+    }
+    double* dinv = q.vec + (size_t)V_DINV * d;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      const int i = e / nb, j = e - i * nb;
+      if (j <= i) {
+        const double v = L[i][j];
+        q.M[(int64_t)(k0 + i) * d + k0 + j] = v;
+        if (j < i) q.M[(int64_t)(k0 + j) * d + k0 + i] = v;
+        else dinv[k0 + i] = 1.0 / v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Panel k, blocks below the diagonal: L_ik = M_ik L_kk^{-T} (one thread per
+// row, forward substitution), written to the lower part and transposed to the
+// upper part.
+__global__ void __launch_bounds__(64) b_trsm_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
+                                                    int total) {
+  extern __shared__ double tr_smem[];
+  double (*L)[kTile + 1] = (double (*)[kTile + 1])tr_smem;                    // [64][65]
+  double (*X)[kTile + 1] = (double (*)[kTile + 1])(tr_smem + kTile * (kTile + 1));  // [64][65]
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_T, c.P, u);
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    const int N = factor_size(s, q);
+    const int i = u - c.pre_T[p];
+    const int k0 = k * kTile, i0 = i * kTile;
+    if (i <= k || i0 >= N) continue;
+    const int nb = min(kTile, N - k0), rb = min(kTile, N - i0);
+    const int d = q.d;
+    const double* dinv = q.vec + (size_t)V_DINV * d;
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int a = e >> 6, b = e & 63;
+      L[a][b] = (a < nb && b < a) ? q.M[(int64_t)(k0 + a) * d + k0 + b] : 0.0;
+      X[a][b] = (a < rb && b < nb) ? q.M[(int64_t)(i0 + a) * d + k0 + b] : 0.0;
+    }
+    __syncthreads();
+    const int r = threadIdx.x;
+    if (r < rb) {
+      for (int j = 0; j < nb; ++j) {
+        double v = X[r][j];
+        for (int l = 0; l < j; ++l) v -= X[r][l] * L[j][l];
+        X[r][j] = v * dinv[k0 + j];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rb * nb; e += blockDim.x) {
+      const int a = e / nb, b = e - a * nb;
+      q.M[(int64_t)(i0 + a) * d + k0 + b] = X[a][b];
+    }
+    for (int e = threadIdx.x; e < rb * nb; e += blockDim.x) {
+      const int b = e / rb, a = e - b * rb;
+      q.M[(int64_t)(k0 + b) * d + i0 + a] = X[a][b];
+    }
+    __syncthreads();
+  }
+}
+
+// Panel k, trailing update of the lower tiles (ti >= tj > k):
+// M_ij -= L_ik L_jk^T.
+__global__ void __launch_bounds__(256) b_update_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
+                                                       int total) {
+  __shared__ __align__(16) double As[16][kTP];
+  __shared__ __align__(16) double Bs[16][kTP];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_tri, c.P, u);
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    int ti, tj;
+    tri_index(u - c.pre_tri[p], &ti, &tj);
+    const int N = factor_size(s, q);
+    const int k0 = k * kTile, i0 = ti * kTile, j0 = tj * kTile;
+    if (tj <= k || i0 >= N) continue;
+    const int nb = min(kTile, N - k0);
+    const int d = q.d;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int c0 = 0; c0 < nb; c0 += 16) {
+      for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+        const int ii = e >> 4, kk = e & 15;
+        const int col = k0 + c0 + kk;
+        double a = 0.0, b = 0.0;
+        if (c0 + kk < nb) {
+          if (i0 + ii < N) a = q.M[(int64_t)(i0 + ii) * d + col];
+          if (j0 + ii < N) b = q.M[(int64_t)(j0 + ii) * d + col];
+        }
+        As[kk][ii] = a;
+        Bs[kk][ii] = b;
+      }
+      __syncthreads();
+      mma_chunk(As, Bs, acc, tx, ty);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
+        if (gi < N && gj < N) q.M[(int64_t)gi * d + gj] -= acc[i][j];
+      }
+  }
+}
+
+// One A-pass unit: rows [r0, r1) of A against v (in shared memory); warp w
+// takes rows r0 + w, r0 + w + 8, ...; lane l owns columns l + 32 j (j < QC).
+template <int QC>
+SKS_DEV void apass_unit(const double* __restrict__ A, long long lda, int d, int64_t r0, int64_t r1,
+                        const double* vs, double* red, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc[QC];
+#pragma unroll
+  for (int j = 0; j < QC; ++j) acc[j] = 0.0;
+  for (int64_t r = r0 + warp; r < r1; r += kApWarps) {
+    const double* a = A + r * lda;
+    double av[QC];
+    double dot = 0.0;
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const int col = lane + 32 * j;
+      av[j] = col < d ? __ldg(a + col) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const int col = lane + 32 * j;
+      if (col < d) dot = fma(av[j], vs[col], dot);
+    }
+    dot = warp_sum(dot);
+#pragma unroll
+    for (int j = 0; j < QC; ++j) acc[j] = fma(dot, av[j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < QC; ++j) {
+    const int col = lane + 32 * j;
+    if (col < d) red[warp * d + col] = acc[j];
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < d; col += blockDim.x) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kApWarps; ++w) t += red[w * d + col];
+    out[col] = t;
+  }
+  __syncthreads();
+}
+
+// A-pass of every INIT (v = x) and ITER (v = p) problem: one partial
+// d-vector per unit of rows_per_unit rows.
+__global__ void __launch_bounds__(kApThreads, 1) b_apass_kernel(BCtl c, const BDesc* __restrict__ D,
+                                                                const BState* S, int total) {
+  extern __shared__ __align__(16) double ap_smem[];
+  double* vs = ap_smem;            // [d]
+  double* red = ap_smem + kMaxD;   // [8][d]
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_ap, c.P, u);
+    const int phase = S[p].phase;
+    if (phase != PH_INIT && phase != PH_ITER) continue;
+    const BDesc& q = D[p];
+    const int d = q.d;
+    const double* v = phase == PH_INIT ? q.x : q.vec + (size_t)V_P * d;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) vs[j] = v[j];
+    __syncthreads();
+    const int t = u - c.pre_ap[p];
+    const int64_t r0 = (int64_t)t * c.rows_per_unit;
+    const int64_t r1 = min(q.n, r0 + c.rows_per_unit);
+    double* out = q.part + (size_t)t * d;
+    if (d <= 32) apass_unit<1>(q.A, q.lda, d, r0, r1, vs, red, out);
+    else if (d <= 64) apass_unit<2>(q.A, q.lda, d, r0, r1, vs, red, out);
+    else if (d <= 128) apass_unit<4>(q.A, q.lda, d, r0, r1, vs, red, out);
+    else if (d <= 256) apass_unit<8>(q.A, q.lda, d, r0, r1, vs, red, out);
+    else if (d <= 512) apass_unit<16>(q.A, q.lda, d, r0, r1, vs, red, out);
+    else apass_unit<32>(q.A, q.lda, d, r0, r1, vs, red, out);
+  }
+}
+
+// Hv = sum of the unit partials + nu^2 Lambda v, in chunks of 256 columns.
+__global__ void __launch_bounds__(256) b_reduce_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
+                                                       int total) {
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_red, c.P, u);
+    const int phase = S[p].phase;
+    if (phase != PH_INIT && phase != PH_ITER) continue;
+    const BDesc& q = D[p];
+    const int d = q.d;
+    const int col = (u - c.pre_red[p]) * 256 + threadIdx.x;
+    if (col >= d) continue;
+    const int units = (int)((q.n + c.rows_per_unit - 1) / c.rows_per_unit);
+    const double* v = phase == PH_INIT ? q.x : q.vec + (size_t)V_P * d;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int t = 0;
+    for (; t + 3 < units; t += 4) {
+      s0 += q.part[(size_t)t * d + col];
+      s1 += q.part[(size_t)(t + 1) * d + col];
+      s2 += q.part[(size_t)(t + 2) * d + col];
+      s3 += q.part[(size_t)(t + 3) * d + col];
+    }
+    for (; t < units; ++t) s0 += q.part[(size_t)t * d + col];
+    q.vec[(size_t)V_HV * d + col] = ((s0 + s1) + (s2 + s3)) + q.nu2 * q.lam[col] * v[col];
+  }
+}
+
+// INIT: r = b - H x.   ITER: alpha = delta~_t / p^T H p, x+ = x + alpha p, r+ = r - alpha H p.
+__global__ void __launch_bounds__(256) b_step1_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
+  __shared__ double scratch[32];
+  for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    const int phase = S[p].phase;
+    if (phase != PH_INIT && phase != PH_ITER) continue;
+    const BDesc& q = D[p];
+    const int d = q.d;
+    double* r = q.vec + (size_t)V_R * d;
+    const double* Hv = q.vec + (size_t)V_HV * d;
+    if (phase == PH_INIT) {
+      for (int j = threadIdx.x; j < d; j += blockDim.x) r[j] = q.b[j] - Hv[j];
+    } else {
+      const double* pv = q.vec + (size_t)V_P * d;
+      const double pHp = block_dot(d, pv, Hv, scratch);
+      const double alpha = S[p].dt / pHp;
+      const bool bad = !(pHp > 0.0) || !isfinite(alpha);
+      double* xp = q.vec + (size_t)V_XP * d;
+      double* rp = q.vec + (size_t)V_RP * d;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        xp[j] = q.x[j] + alpha * pv[j];
+        rp[j] = r[j] - alpha * Hv[j];
+      }
+      if (bad && threadIdx.x == 0) {
+        S[p].status = SKS_ERR_NUMERIC;
+        S[p].phase = PH_FAIL;
+      }
+    }
+    if (threadIdx.x == 0) S[p].a_passes += 1;
+    __syncthreads();
+  }
+}
+
+// y = L^{-1} z (lower, forward) or U^{-1} z (upper = L^T, backward) for the
+// N x N factor in M (ld), in place on the shared vector y.  Blocks of 64: the
+// off-diagonal part as one warp per row, the diagonal block by warp 0.
+SKS_DEV void tri_solve(const double* __restrict__ M, int ld, int N, const double* __restrict__ dinv, double* y,
+                       bool upper) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nblk = (N + kTile - 1) / kTile;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = upper ? nblk - 1 - bi : bi;
+    const int b0 = blk * kTile, nb = min(kTile, N - b0);
+    // y[b0 + i] -= sum over the solved part
+    const int j0 = upper ? b0 + nb : 0, j1 = upper ? N : b0;
+    if (j1 > j0) {
+      for (int i = warp; i < nb; i += nw) {
+        const double* row = M + (int64_t)(b0 + i) * ld;
+        double s = 0.0;
+        for (int j = j0 + lane; j < j1; j += 32) s = fma(row[j], y[j], s);
+        s = warp_sum(s);
+        if (lane == 0) y[b0 + i] -= s;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int jj = 0; jj < nb; ++jj) {
+        const int j = upper ? nb - 1 - jj : jj;
+        const double yj = y[b0 + j] * dinv[b0 + j];
+        __syncwarp();
+        if (lane == 0) y[b0 + j] = yj;
+        if (upper) {
+          for (int i = lane; i < j; i += 32) y[b0 + i] -= M[(int64_t)(b0 + i) * ld + b0 + j] * yj;
+        } else {
+          for (int i = j + 1 + lane; i < nb; i += 32) y[b0 + i] -= M[(int64_t)(b0 + i) * ld + b0 + j] * yj;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// GROW: r~ = H_S^{-1} r.   ITER: r~+ = H_S^{-1} r+.
+//   form 0: H_S = L L^T (two triangular solves)
+//   form 1: H_S^{-1} z = u - (nu^2 Lambda)^{-1} Y_s^T K^{-1} Y_s u,  u = (nu^2 Lambda)^{-1} z,
+//           Y_s = Y / sqrt(m), K = I + Y_s (nu^2 Lambda)^{-1} Y_s^T = L L^T
+__global__ void __launch_bounds__(256) b_apply_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S) {
+  __shared__ double y[kMaxD];
+  for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    const BState s = S[p];
+    if (s.phase != PH_GROW && s.phase != PH_ITER) continue;
+    const BDesc& q = D[p];
+    const int d = q.d;
+    const double* z = q.vec + (size_t)(s.phase == PH_GROW ? V_R : V_RP) * d;
+    double* out = q.vec + (size_t)(s.phase == PH_GROW ? V_RT : V_RTP) * d;
+    const double* dinv = q.vec + (size_t)V_DINV * d;
+    if (s.form == 0) {
+      for (int j = threadIdx.x; j < d; j += blockDim.x) y[j] = z[j];
+      __syncthreads();
+      tri_solve(q.M, d, d, dinv, y, false);
+      tri_solve(q.M, d, d, dinv, y, true);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) out[j] = y[j];
+    } else {
+      const int m = (int)s.m;
+      const double ism = 1.0 / sqrt((double)m);
+      double* u = q.vec + (size_t)V_U * d;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) u[j] = z[j] / (q.nu2 * q.lam[j]);
+      __syncthreads();
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int r = warp; r < m; r += nw) {
+        const double* row = q.B + (int64_t)q.perm[r] * d;
+        double t = 0.0;
+        for (int j = lane; j < d; j += 32) t = fma(row[j], u[j], t);
+        t = warp_sum(t);
+        if (lane == 0) y[r] = t * ism;
+      }
+      __syncthreads();
+      tri_solve(q.M, d, m, dinv, y, false);
+      tri_solve(q.M, d, m, dinv, y, true);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double t = 0.0;
+        for (int r = 0; r < m; ++r) t = fma(q.B[(int64_t)q.perm[r] * d + j], y[r], t);
+        out[j] = u[j] - t * ism / (q.nu2 * q.lam[j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// GROW: restart p = r~, delta~_t = delta~_I = r^T r~.
+// ITER: delta~+ = r+^T r~+, the improvement test of Algorithm 2, the update.
+// INIT: on to the first sketch.
+__global__ void __launch_bounds__(256) b_step2_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
+  __shared__ double scratch[32];
+  __shared__ int s_accept, s_phase;
+  for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    // thread 0 changes the phase below: every thread reads it first
+    __syncthreads();
+    if (threadIdx.x == 0) s_phase = S[p].phase;
+    __syncthreads();
+    const int phase = s_phase;
+    if (phase == PH_INIT) {
+      if (threadIdx.x == 0) S[p].phase = PH_GROW;
+      continue;
+    }
+    if (phase != PH_GROW && phase != PH_ITER) continue;
+    const BDesc& q = D[p];
+    const int d = q.d;
+    double* r = q.vec + (size_t)V_R * d;
+    double* rt = q.vec + (size_t)V_RT * d;
+    double* pv = q.vec + (size_t)V_P * d;
+    if (phase == PH_GROW) {
+      const double dt = block_dot(d, r, rt, scratch);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) pv[j] = rt[j];
+      if (threadIdx.x == 0) {
+        BState& s = S[p];
+        s.dt = dt;
+        s.dI = dt;
+        if (!isfinite(dt)) {
+          s.status = SKS_ERR_NUMERIC;
+          s.phase = PH_FAIL;
+        } else {
+          s.phase = dt <= 0.0 ? PH_DONE : PH_ITER;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    const double* rp = q.vec + (size_t)V_RP * d;
+    const double* rtp = q.vec + (size_t)V_RTP * d;
+    const double* xp = q.vec + (size_t)V_XP * d;
+    const double dp = block_dot(d, rp, rtp, scratch);
+    if (threadIdx.x == 0) {
+      BState& s = S[p];
+      const double thr = c.c * pow(c.phi, (double)(s.t + 1 - s.I));
+      const double ratio = dp / s.dI;
+      const int reject = (ratio > thr) && (s.m < q.m_max);
+      s_accept = 1;
+      if (!isfinite(dp)) {
+        s.status = SKS_ERR_NUMERIC;
+        s.phase = PH_FAIL;
+        s_accept = 0;
+      } else if (reject) {
+        s.I = s.t;
+        s.rejections += 1;
+        s.phase = PH_GROW;
+        s_accept = 0;
+      }
+    }
+    __syncthreads();
+    if (!s_accept) continue;
+    const double beta = dp / S[p].dt;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      pv[j] = rtp[j] + beta * pv[j];
+      q.x[j] = xp[j];
+      r[j] = rp[j];
+      rt[j] = rtp[j];
+    }
+    __syncthreads();
+    const double btx = block_dot(d, q.b, q.x, scratch);
+    if (threadIdx.x == 0) {
+      BState& s = S[p];
+      s.dt = dp;
+      s.t += 1;
+      s.btx = btx;
+      if (dp <= 0.0 || dp <= c.tol2 * btx) {
+        s.phase = PH_DONE;
+      } else if (s.t >= c.max_iter) {
+        s.status = SKS_ERR_NO_CONVERGENCE;
+        s.phase = PH_FAIL;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void b_count_kernel(BCtl c, const BState* S) {
+  __shared__ int scratch[32];
+  int a = 0;
+  for (int p = threadIdx.x; p < c.P; p += blockDim.x) a += S[p].phase < PH_DONE ? 1 : 0;
+  a = block_sum(a, scratch);
+  if (threadIdx.x == 0) *c.active = a;
+}
+
+// ------------------------------------------------------------------ setup kernels
+
+__global__ void b_check_kernel(const BDesc* __restrict__ D, int P, DevStatus* st) {
+  for (int p = blockIdx.x; p < P; p += gridDim.x) {
+    const BDesc& q = D[p];
+    for (int j = threadIdx.x; j < q.d; j += blockDim.x)
+      if (!(q.lam[j] >= 1.0 && isfinite(q.lam[j]))) raise_status(st, SKS_ERR_INVALID_ARG, 1, ((long long)p << 32) | j);
+  }
+}
+
+__global__ void b_init_kernel(BState* S, int P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  BState s = {};
+  s.phase = PH_INIT;
+  s.status = SKS_OK;
+  S[p] = s;
+}
+
+// ------------------------------------------------------------------ host side
+
+struct Layout {
+  BDesc* D = nullptr;
+  BState* S = nullptr;
+  int *pre_tri = nullptr, *pre_T = nullptr, *pre_ap = nullptr, *pre_red = nullptr, *active = nullptr;
+  DevStatus* st = nullptr;
+  std::vector<BDesc> host;
+  size_t used = 0;
+};
+
+constexpr int kMinRowsPerUnit = 32;
+
+int64_t m_max_of(const sks_problem& p, const sks_opts* o) {
+  const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p.n, 1));
+  return o->m_max <= 0 ? n_pad : std::min<int64_t>(o->m_max, n_pad);
+}
+
+sks_status check_batch(const sks_problem* probs, int count, const sks_opts* o) {
+  if (!probs || count < 1) return fail(SKS_ERR_INVALID_ARG, "batch: need count >= 1 problems");
+  if (!o) return fail(SKS_ERR_INVALID_ARG, "opts is NULL");
+  if (!(o->rho > 0.0 && o->rho < 1.0)) return fail(SKS_ERR_INVALID_ARG, "rho must be in (0, 1)");
+  if (o->m_init < 1) return fail(SKS_ERR_INVALID_ARG, "m_init must be >= 1");
+  if (!(o->tol > 0.0)) return fail(SKS_ERR_INVALID_ARG, "tol must be > 0");
+  if (o->kind != SKS_SRHT) return fail(SKS_ERR_UNSUPPORTED, "batch: only the SRHT embedding is implemented");
+  if (o->precision != SKS_PLAIN_F64) return fail(SKS_ERR_UNSUPPORTED, "batch: only the plain float64 form");
+  for (int i = 0; i < count; ++i) {
+    const sks_problem& p = probs[i];
+    const sks_status v = validate_problem(&p);
+    if (v != SKS_OK) return fail(v, "batch problem " + std::to_string(i) + ": " + last_error_cstr());
+    if (p.dtype != SKS_F64) return fail(SKS_ERR_INVALID_ARG, "batch problem " + std::to_string(i) + ": needs float64 A");
+    if (p.k != 1) return fail(SKS_ERR_UNSUPPORTED, "batch problem " + std::to_string(i) + ": one right-hand side");
+    if (p.n < 1) return fail(SKS_ERR_UNSUPPORTED, "batch problem " + std::to_string(i) + ": n >= 1");
+    if (p.d > kMaxD) return fail(SKS_ERR_UNSUPPORTED, "batch problem " + std::to_string(i) + ": d <= 1024");
+  }
+  return SKS_OK;
+}
+
+// Carves the workspace (ws == nullptr: sizes only).
+sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void* ws, size_t ws_bytes, Layout* L) {
+  Carver c(ws, ws_bytes);
+  L->D = c.take<BDesc>(P);
+  L->S = c.take<BState>(P);
+  L->pre_tri = c.take<int>(P + 1);
+  L->pre_T = c.take<int>(P + 1);
+  L->pre_ap = c.take<int>(P + 1);
+  L->pre_red = c.take<int>(P + 1);
+  L->active = c.take<int>(1);
+  L->st = c.take<DevStatus>(1);
+  L->host.assign(P, BDesc{});
+  for (int i = 0; i < P; ++i) {
+    const sks_problem& p = probs[i];
+    BDesc& q = L->host[i];
+    q.A = (const double*)p.A;
+    q.lda = p.lda;
+    q.n = p.n;
+    q.d = (int)p.d;
+    q.bits = ilog2_ceil(std::max<int64_t>(p.n, 1));
+    q.b = (const double*)p.b;
+    q.lam = p.lambda_diag;
+    q.nu2 = p.nu * p.nu;
+    q.m_max = m_max_of(p, o);
+    q.m_init = o->m_init;
+    const int64_t n_pad = (int64_t)1 << q.bits;
+    q.B = c.take<double>((size_t)n_pad * q.d);
+    q.perm = c.take<uint32_t>((size_t)q.m_max);
+    q.M = c.take<double>((size_t)q.d * q.d);
+    q.vec = c.take<double>((size_t)kNumVec * q.d);
+    q.part = c.take<double>((size_t)((p.n + kMinRowsPerUnit - 1) / kMinRowsPerUnit) * q.d);
+  }
+  L->used = c.used + 256;
+  if (ws && !c.ok()) return fail(SKS_ERR_WORKSPACE, "batch: workspace too small");
+  return SKS_OK;
+}
+
+std::vector<int> prefix(const std::vector<BDesc>& h, int (*units)(const BDesc&, int), int arg) {
+  std::vector<int> pre(h.size() + 1, 0);
+  for (size_t i = 0; i < h.size(); ++i) pre[i + 1] = pre[i] + units(h[i], arg);
+  return pre;
+}
+int units_T(const BDesc& q, int) { return (q.d + kTile - 1) / kTile; }
+int units_tri(const BDesc& q, int) {
+  const int T = units_T(q, 0);
+  return T * (T + 1) / 2;
+}
+int units_ap(const BDesc& q, int rows) { return (int)((q.n + rows - 1) / rows); }
+int units_red(const BDesc& q, int) { return (q.d + 255) / 256; }
+
+constexpr size_t kTrsmSmem = 2 * kTile * (kTile + 1) * sizeof(double);
+
+struct Round {
+  BCtl ctl;
+  const BDesc* D;
+  BState* S;
+  int P, kmax, tot_tri, tot_T, tot_ap, tot_red;
+  int g_tile, g_trsm, g_ap, g_prob;
+  size_t ap_smem;
+};
+
+// Enqueues one round on `stream`; returns the number of kernels.
+int enqueue_round(const Round& R, cudaStream_t stream) {
+  int n = 0;
+  const int pb = (R.P + 127) / 128;
+  b_begin_kernel<<<pb, 128, 0, stream>>>(R.ctl, R.D, R.S);
+  ++n;
+  b_perm_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
+  ++n;
+  b_gram_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri);
+  ++n;
+  for (int k = 0; k < R.kmax; ++k) {
+    b_potrf_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S, k);
+    ++n;
+    if (k + 1 < R.kmax) {
+      b_trsm_kernel<<<R.g_trsm, 64, kTrsmSmem, stream>>>(R.ctl, R.D, R.S, k, R.tot_T);
+      b_update_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, k, R.tot_tri);
+      n += 2;
+    }
+  }
+  b_apass_kernel<<<R.g_ap, kApThreads, R.ap_smem, stream>>>(R.ctl, R.D, R.S, R.tot_ap);
+  b_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_red);
+  b_step1_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
+  b_apply_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
+  b_step2_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
+  b_count_kernel<<<1, 256, 0, stream>>>(R.ctl, R.S);
+  n += 6;
+  return n;
+}
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  sks_status init() {
+    SKS_CUDA_TRY(cudaEventCreate(&a));
+    SKS_CUDA_TRY(cudaEventCreate(&b));
+    return SKS_OK;
+  }
+  sks_status ms(float* out) {
+    SKS_CUDA_TRY(cudaEventSynchronize(b));
+    SKS_CUDA_TRY(cudaEventElapsedTime(out, a, b));
+    return SKS_OK;
+  }
+};
+
+struct GraphGuard {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+  cudaStream_t cs = nullptr;
+  ~GraphGuard() {
+    if (e) cudaGraphExecDestroy(e);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+sks_status upload_prefix(int* dst, const std::vector<int>& pre, cudaStream_t stream) {
+  SKS_CUDA_TRY(cudaMemcpyAsync(dst, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  return SKS_OK;
+}
+
+}  // namespace
+
+sks_status batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes) {
+  if (!bytes) return fail(SKS_ERR_INVALID_ARG, "bytes is NULL");
+  SKS_TRY(check_batch(probs, count, o));
+  Layout L;
+  SKS_TRY(batch_layout(probs, count, o, nullptr, 0, &L));
+  *bytes = L.used;
+  return SKS_OK;
+}
+
+sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, double* const* xs, sks_stats* stats,
+                         sks_batch_info* info, int rows_per_unit, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  SKS_TRY(check_batch(probs, P, o));
+  if (!xs) return fail(SKS_ERR_INVALID_ARG, "x array is NULL");
+  for (int i = 0; i < P; ++i)
+    if (!xs[i]) return fail(SKS_ERR_INVALID_ARG, "x of batch problem " + std::to_string(i) + " is NULL");
+  if (rows_per_unit != 0 && (rows_per_unit < kMinRowsPerUnit || rows_per_unit > 65536))
+    return fail(SKS_ERR_INVALID_ARG, "rows_per_unit must be 0 (autotune) or in [32, 65536]");
+  if (!ws) return fail(SKS_ERR_INVALID_ARG, "workspace is NULL");
+  Layout L;
+  SKS_TRY(batch_layout(probs, P, o, ws, ws_bytes, &L));
+  for (int i = 0; i < P; ++i) L.host[i].x = xs[i];
+  const DeviceInfo& di = device_info();
+  const int sms = di.sms > 0 ? di.sms : 152;
+
+  EventPair ev_setup, ev_tune, ev_solve;
+  SKS_TRY(ev_setup.init());
+  SKS_TRY(ev_tune.init());
+  SKS_TRY(ev_solve.init());
+
+  // ---- setup: descriptors, checks, SRHT transforms H E A, states
+  SKS_CUDA_TRY(cudaEventRecord(ev_setup.a, stream));
+  SKS_CUDA_TRY(cudaMemsetAsync(L.st, 0, sizeof(DevStatus), stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(L.D, L.host.data(), P * sizeof(BDesc), cudaMemcpyHostToDevice, stream));
+  const std::vector<int> pre_tri = prefix(L.host, units_tri, 0), pre_T = prefix(L.host, units_T, 0),
+                         pre_red = prefix(L.host, units_red, 0);
+  SKS_TRY(upload_prefix(L.pre_tri, pre_tri, stream));
+  SKS_TRY(upload_prefix(L.pre_T, pre_T, stream));
+  SKS_TRY(upload_prefix(L.pre_red, pre_red, stream));
+  b_check_kernel<<<std::min(P, 4 * sms), 256, 0, stream>>>(L.D, P, L.st);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  SKS_TRY(read_status(L.st, stream, "batch input check"));
+  for (int i = 0; i < P; ++i) {
+    const BDesc& q = L.host[i];
+    SKS_TRY(srht_form<double>(stream, q.A, q.lda, q.n, q.d, (double*)q.B, q.d, o->seed));
+  }
+  b_init_kernel<<<(P + 127) / 128, 128, 0, stream>>>(L.S, P);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  SKS_CUDA_TRY(cudaEventRecord(ev_setup.b, stream));
+
+  // ---- round description
+  Round R;
+  std::memset(&R, 0, sizeof(R));
+  R.P = P;
+  R.D = L.D;
+  R.S = L.S;
+  BCtl& c = R.ctl;
+  c.P = P;
+  c.max_iter = o->max_iter > 0 ? o->max_iter : 1000000;
+  const double rho = o->rho;
+  c.phi = (1.0 - std::sqrt(1.0 - rho)) / (1.0 + std::sqrt(1.0 - rho));
+  c.c = 4.0 * (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
+  c.tol2 = (o->tol / 2.0) * (o->tol / 2.0);
+  c.key = make_key(o->seed);
+  c.pre_tri = L.pre_tri;
+  c.pre_T = L.pre_T;
+  c.pre_ap = L.pre_ap;
+  c.pre_red = L.pre_red;
+  c.active = L.active;
+  int dmax = 0;
+  int64_t mmax_all = 1;
+  for (const BDesc& q : L.host) {
+    dmax = std::max(dmax, q.d);
+    mmax_all = std::max(mmax_all, q.m_max);
+  }
+  R.kmax = (dmax + kTile - 1) / kTile;
+  R.tot_tri = pre_tri[P];
+  R.tot_T = pre_T[P];
+  R.tot_red = pre_red[P];
+  R.g_prob = std::min(P, 8 * sms);
+  R.g_tile = std::max(1, std::min(R.tot_tri, 4 * sms));
+  R.g_trsm = std::max(1, std::min(R.tot_T, 8 * sms));
+  R.ap_smem = (size_t)(1 + kApWarps) * kMaxD * sizeof(double);
+  SKS_CUDA_TRY(cudaFuncSetAttribute(b_apass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R.ap_smem));
+  SKS_CUDA_TRY(cudaFuncSetAttribute(b_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsmSmem));
+  int ap_occ = 1;
+  SKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ap_occ, b_apass_kernel, kApThreads, R.ap_smem));
+  const int ap_grid_max = sms * std::max(1, ap_occ);
+
+  // ---- autotune the A-pass unit height on this batch (all problems in INIT)
+  SKS_CUDA_TRY(cudaEventRecord(ev_tune.a, stream));
+  int chosen = rows_per_unit;
+  std::vector<int> pre_ap;
+  if (chosen == 0) {
+    const int cands[] = {32, 64, 128, 256, 512};
+    float best = 1e30f;
+    EventPair e;
+    SKS_TRY(e.init());
+    for (int rows : cands) {
+      const std::vector<int> pa = prefix(L.host, units_ap, rows);
+      SKS_TRY(upload_prefix(L.pre_ap, pa, stream));
+      BCtl ct = c;
+      ct.rows_per_unit = rows;
+      const int g = std::max(1, std::min(pa[P], ap_grid_max));
+      b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);  // warm
+      SKS_CUDA_TRY(cudaEventRecord(e.a, stream));
+      for (int rep = 0; rep < 3; ++rep) b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);
+      SKS_CUDA_TRY(cudaEventRecord(e.b, stream));
+      note_launch(4);
+      SKS_CUDA_TRY(cudaGetLastError());
+      float ms = 0.f;
+      SKS_TRY(e.ms(&ms));
+      if (ms < best) {
+        best = ms;
+        chosen = rows;
+      }
+    }
+  }
+  pre_ap = prefix(L.host, units_ap, chosen);
+  SKS_TRY(upload_prefix(L.pre_ap, pre_ap, stream));
+  c.rows_per_unit = chosen;
+  R.tot_ap = pre_ap[P];
+  R.g_ap = std::max(1, std::min(R.tot_ap, ap_grid_max));
+  SKS_CUDA_TRY(cudaEventRecord(ev_tune.b, stream));
+
+  // ---- capture one round as a graph, replay until every problem is done
+  GraphGuard G;
+  SKS_CUDA_TRY(cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking));
+  SKS_CUDA_TRY(cudaStreamBeginCapture(G.cs, cudaStreamCaptureModeThreadLocal));
+  const int per_round = enqueue_round(R, G.cs);
+  const cudaError_t cap = cudaStreamEndCapture(G.cs, &G.g);
+  SKS_CUDA_TRY(cap);
+  SKS_CUDA_TRY(cudaGetLastError());
+  SKS_CUDA_TRY(cudaGraphInstantiate(&G.e, G.g, 0));
+
+  const int64_t max_rounds = 4 + 2 * (ilog2_ceil(mmax_all) + 2) + c.max_iter;
+  int64_t rounds = 0;
+  int* h_active = nullptr;
+  SKS_CUDA_TRY(cudaMallocHost(&h_active, sizeof(int)));
+  struct HostFree {
+    int* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{h_active};
+  SKS_CUDA_TRY(cudaEventRecord(ev_solve.a, stream));
+  int burst = 4;
+  while (rounds < max_rounds) {
+    const int nb = (int)std::min<int64_t>(burst, max_rounds - rounds);
+    for (int g = 0; g < nb; ++g) SKS_CUDA_TRY(cudaGraphLaunch(G.e, stream));
+    note_launch(per_round * nb);
+    rounds += nb;
+    SKS_CUDA_TRY(cudaMemcpyAsync(h_active, L.active, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (*h_active == 0) break;
+    burst = std::min(16, burst * 2);
+  }
+  SKS_CUDA_TRY(cudaEventRecord(ev_solve.b, stream));
+
+  // ---- per-problem results
+  std::vector<BState> hs(P);
+  SKS_CUDA_TRY(cudaMemcpyAsync(hs.data(), L.S, P * sizeof(BState), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+  float ms_setup = 0.f, ms_tune = 0.f, ms_solve = 0.f;
+  SKS_TRY(ev_setup.ms(&ms_setup));
+  SKS_TRY(ev_tune.ms(&ms_tune));
+  SKS_TRY(ev_solve.ms(&ms_solve));
+  sks_status result = SKS_OK;
+  int first_bad = -1;
+  for (int i = 0; i < P; ++i) {
+    BState& s = hs[i];
+    if (s.phase < PH_DONE) s.status = SKS_ERR_NO_CONVERGENCE;  // ran out of rounds
+    if (s.status != SKS_OK && first_bad < 0) {
+      first_bad = i;
+      result = (sks_status)s.status;
+    }
+    if (stats) {
+      sks_stats& t = stats[i];
+      std::memset(&t, 0, sizeof(t));
+      t.iters = s.t;
+      t.rejections = s.rejections;
+      t.final_m = s.m;
+      t.a_passes = s.a_passes;
+      t.sketch_passes = 1;
+      t.factorizations = s.factorizations;
+      t.final_delta_tilde = s.dt;
+      t.est_rel_err = s.btx > 0 ? std::sqrt(std::max(0.0, s.dt / s.btx)) : 0.0;
+      t.outer_iters = 1;
+      t.ms_total = ms_setup + ms_tune + ms_solve;
+      t.status = (sks_status)s.status;
+    }
+  }
+  if (info) {
+    info->rounds = rounds;
+    info->kernels_per_round = per_round;
+    info->rows_per_unit = chosen;
+    info->ms_setup = ms_setup;
+    info->ms_autotune = ms_tune;
+    info->ms_solve = ms_solve;
+  }
+  if (result != SKS_OK) {
+    const char* what = result == SKS_ERR_NO_CONVERGENCE ? "did not converge"
+                       : result == SKS_ERR_NOT_PD       ? "non-positive pivot in its factorisation"
+                                                        : "non-finite value";
+    return fail(result, "batch problem " + std::to_string(first_bad) + " " + what +
+                            " (per-problem statuses are in stats[i].status)");
+  }
+  return SKS_OK;
+}
+
+}  // namespace sks

@@ -70,3 +70,33 @@ def test_opts_default_and_validation_without_gpu(lib_path):
     p.lda = 4
     assert lib.sks_solve_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(nb)) == _lib.OK
     assert nb.value > 0
+
+
+def test_batched_validation_without_gpu(lib_path):
+    # The batched entry point rejects what it does not implement before any
+    # device work: no problems, float32 A, another embedding, d > 1024.
+    from paper_2104_14101_gb300 import _lib
+    lib = _lib.load(lib_path)
+    o = _lib.Opts()
+    lib.sks_opts_default(ctypes.byref(o))
+    arr = (_lib.Problem * 2)()
+    for p in arr:
+        p.dtype, p.n, p.d, p.lda, p.k, p.nu = _lib.F64, 64, 8, 8, 1, 1e-2
+        p.A, p.b, p.lambda_diag = 16, 16, 16  # never dereferenced
+    nb = ctypes.c_size_t()
+    assert lib.sks_batch_workspace_size(arr, 0, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_INVALID_ARG
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.OK
+    # H E A_pad (64 x 8), factor (8 x 8), perm and vectors of both problems at least
+    assert nb.value > 2 * 8 * (64 * 8 + 8 * 8 + 10 * 8)
+    arr[1].dtype = _lib.F32
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_INVALID_ARG
+    assert b"problem 1" in lib.sks_last_error()
+    arr[1].dtype = _lib.F64
+    arr[0].d, arr[0].lda = 1032, 1032
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_UNSUPPORTED
+    arr[0].d, arr[0].lda = 8, 8
+    o.kind = _lib.KINDS["gaussian"]
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_UNSUPPORTED
+    o.kind = _lib.KINDS["srht"]
+    arr[1].k = 2
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_UNSUPPORTED

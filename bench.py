@@ -59,6 +59,12 @@ WORKLOADS = {
                        precision="mixed", desc="C3 recipe at n=2^17 (profiling size)"),
     "C3-srht-profile": dict(config="C3", n=1 << 17, method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=8192,
                             tol=1e-8, precision="mixed", desc="C3 recipe with the SRHT at n=2^17 (profiling size)"),
+    # C5: 256 uneven problems solved together (float64, SRHT, tol 1e-8) vs the same problems one at a time
+    "C5": dict(config="C5", batched=True, count=256, method="pcg", kind="srht", m_init=1, m_max=0, tol=1e-8,
+               precision="plain", ref_problems=6,
+               desc="256 independent problems, n log-uniform in [2^11, 2^16], d log-uniform in [32, 1024], "
+                    "n >= 4d, sigma_j = 0.9^j or 1/(1+j), nu log-uniform in [1e-4, 1e-1], Lambda = I, SRHT, "
+                    "adaptive PCG to 1e-8, batched (one captured round replayed) vs one solve at a time"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -195,6 +201,43 @@ def extrapolate(t_small, r_small, t_large, r_large, n):
     if g <= 0:
         return t_large * n / r_large, None
     return t_large + g * (n - r_large), g
+
+
+def run_reference_batched(args, wl, world, rank):
+    """--impl reference for the batch: the oracle's adaptive PCG on the first
+    `ref_problems` problems per step, scaled to the whole batch by sum(n d)."""
+    if rank != 0:
+        return None
+    import synthetic
+    from oracle import solvers as O
+    gdev = "cuda" if torch.cuda.is_available() else "cpu"
+    specs, probs = synthetic.make_batch_torch(wl["count"], seed=0, device=gdev)
+    host = [(A.cpu().numpy(), b.cpu().numpy(), nu, lam.cpu().numpy()) for A, b, nu, lam in probs]
+    del probs
+    k = min(wl["ref_problems"], len(host))
+    nd_all = sum(A.shape[0] * A.shape[1] for A, _, _, _ in host)
+    nd_s = sum(A.shape[0] * A.shape[1] for A, _, _, _ in host[:k])
+    kw = dict(kind=wl["kind"], seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"])
+    for _ in range(args.warmup):  # untimed warm-up on the smallest problem
+        A, b, nu, lam = min(host, key=lambda t: t[0].size)
+        O.adaptive_pcg(A, b, nu, lam, **kw)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for A, b, nu, lam in host[:k]:
+            O.adaptive_pcg(A, b, nu, lam, **kw)
+        times.append((time.perf_counter() - t0) * 1e3 * nd_all / nd_s)
+    ms = sum(times) / len(times)
+    sample = ("per step: oracle adaptive PCG (float64) on the first %d of %d problems (sum n d = %d of %d), time "
+              "scaled by sum(n d)" % (k, len(host), nd_s, nd_all))
+    return {
+        "metric": BATCH_METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "C5: " + wl["desc"], "problems": len(host), "sum_nd": nd_all},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
 
 
 def run_reference(args, wl, world, rank):
@@ -442,6 +485,126 @@ def run_ours(args, wl, world, rank, local):
     return line if rank == 0 else None
 
 
+BATCH_METRIC = "ms to solve a batch of uneven problems to 1e-8 rel. H-error (batched vs one at a time)"
+
+
+def run_batched(args, wl, world, rank, local):
+    """The uneven batch C5: one sks_solve_batched call per step."""
+    import paper_2104_14101_gb300 as sks
+    from paper_2104_14101_gb300 import _lib
+    import synthetic
+    from oracle import solvers as O
+
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    lib = _lib.load()
+    specs, probs = synthetic.make_batch_torch(wl["count"], seed=0, device=dev)
+    opts = dict(kind=wl["kind"], m_init=wl["m_init"], m_max=wl["m_max"], tol=wl["tol"], seed=0, max_iter=1000)
+    bs = sks.BatchSolver(probs, **opts)
+    for _ in range(args.warmup):
+        bs.solve()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = lib.sks_kernel_launch_count()
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        xs, stats, info = bs.solve()
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = lib.sks_kernel_launch_count() - launches0
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    n_tot = sum(int(A.shape[0]) * int(A.shape[1]) for A, _, _, _ in probs)
+
+    # roofline of the batched A-pass (float64, ALU-bound): device-clock duration of its launches
+    ap_ms = sum(i["ms_apass"] for i in infos)
+    ap_flops = sum(i["apass_flops"] for i in infos)
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = ap_flops / (ap_ms * 1e-3) / 1e12 if ap_ms > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+                "kernel": "b_apass_kernel (batched float64 A-pass)", "ms_apass_per_step": ap_ms / args.steps,
+                "flops_per_step": ap_flops / args.steps,
+                "peak_source": "float64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2 flop) at the sampled "
+                               "median SM clock"}
+
+    # end to end through the public call: inputs from pinned host memory every step, solutions read back
+    host_in = [(A.cpu().pin_memory(), b.cpu().pin_memory(), lam.cpu().pin_memory()) for A, b, _, lam in probs]
+    h2d = sum(a.numel() * 8 + b.numel() * 8 + l.numel() * 8 for a, b, l in host_in)
+    d2h = sum(int(A.shape[1]) * 8 for A, _, _, _ in probs)
+    kp = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(kp):
+        for (A, b, _, lam), (ah, bh, lh) in zip(probs, host_in):
+            A.copy_(ah, non_blocking=True)
+            b.copy_(bh, non_blocking=True)
+            lam.copy_(lh, non_blocking=True)
+        xs_e, _, _ = sks.solve_batched(probs, **opts)
+        _ = [x.cpu() for x in xs_e]
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3) / kp
+
+    # the same problems one at a time through the single-problem solver
+    singles = [sks.Solver(A, b, nu, lam, method="pcg", **opts) for A, b, nu, lam in probs]
+    for sv in singles:
+        sv.solve()
+    torch.cuda.synchronize()
+    e4 = torch.cuda.Event(enable_timing=True)
+    e5 = torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    single_stats = [sv.solve()[1] for sv in singles]
+    e5.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e4.elapsed_time(e5)
+    del singles
+
+    # accuracy against the oracle's direct solve: the first problems and the largest d
+    idx = list(range(min(6, len(probs))))
+    idx.append(max(range(len(probs)), key=lambda i: int(probs[i][0].shape[1])))
+    errs = []
+    for i in idx:
+        A, b, nu, lam = probs[i]
+        An, bn, ln = A.cpu().numpy(), b.cpu().numpy(), lam.cpu().numpy()
+        xs_ref = O.direct_solve(An, bn, nu, ln)
+        errs.append(O.rel_err_H(An, nu, ln, xs[i].cpu().numpy(), xs_ref))
+    info = infos[-1]
+    line = {
+        "metric": BATCH_METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "C5: " + wl["desc"], "problems": len(probs), "sum_nd": n_tot,
+                   "max_d": max(int(A.shape[1]) for A, _, _, _ in probs),
+                   "l2": "inputs larger than L2 (A = %.2f GiB)" % (n_tot * 8 / 2 ** 30),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "batch_info": info,
+        "batch_stats": {"iters_max": max(s["iters"] for s in stats), "final_m_max": max(s["final_m"] for s in stats),
+                        "all_ok": all(s["status"] == 0 for s in stats)},
+        "compare": {"one_at_a_time_ms": ms_single, "batched_ms": ms, "speedup_batched": ms_single / ms,
+                    "same_iterations": sum(1 for a, b in zip(stats, single_stats)
+                                           if (a["iters"], a["final_m"]) == (b["iters"], b["final_m"]))},
+        "rel_err_H_vs_oracle_sample": {"problems": idx, "max": max(errs)},
+    }
+    return line if rank == 0 else None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -459,7 +622,9 @@ def main():
         wl["method"] = args.method
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
-        line = run_reference(args, wl, world, rank)
+        line = (run_reference_batched if wl.get("batched") else run_reference)(args, wl, world, rank)
+    elif wl.get("batched"):
+        line = run_batched(args, wl, world, rank, local)
     else:
         line = run_ours(args, wl, world, rank, local)
     if rank == 0 and line is not None:

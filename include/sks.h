@@ -285,6 +285,9 @@ typedef struct {
   float ms_setup;            /* input checks, H E A_pad of every problem, states     */
   float ms_autotune;         /* timing of the candidate unit heights                 */
   float ms_solve;            /* graph replays                                        */
+  float ms_apass;            /* summed duration of the rounds' A-pass kernels (device
+                                clock: first CTA start to last CTA end per round)   */
+  double apass_flops;        /* 4 n d per A-pass of every problem, summed            */
 } sks_batch_info;
 
 sks_status sks_batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes);

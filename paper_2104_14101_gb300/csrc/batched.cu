@@ -84,6 +84,11 @@ struct BCtl {
   const int* pre_ap;   // prefix of ceil(n / rows_per_unit)
   const int* pre_red;  // prefix of ceil(d / 256)
   int* active;         // problems not finished after the round
+  // A-pass accounting: [0] earliest CTA start and [1] latest CTA end of the
+  // round's A-pass kernel (%globaltimer ns), [2] summed durations over rounds;
+  // flops: 4 n d per A-pass unit row block, summed over rounds
+  unsigned long long* tap;
+  double* apass_flops;
 };
 
 // largest p with pre[p] <= u  (pre[0] = 0 <= u < pre[P])
@@ -447,6 +452,8 @@ __global__ void __launch_bounds__(kApThreads, 1) b_apass_kernel(BCtl c, const BD
   extern __shared__ __align__(16) double ap_smem[];
   double* vs = ap_smem;            // [d]
   double* red = ap_smem + kMaxD;   // [8][d]
+  if (threadIdx.x == 0 && c.tap) atomicMin(&c.tap[0], (unsigned long long)global_ns());
+  double flops = 0.0;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = find_problem(c.pre_ap, c.P, u);
     const int phase = S[p].phase;
@@ -466,6 +473,11 @@ __global__ void __launch_bounds__(kApThreads, 1) b_apass_kernel(BCtl c, const BD
     else if (d <= 256) apass_unit<8>(q.A, q.lda, d, r0, r1, vs, red, out);
     else if (d <= 512) apass_unit<16>(q.A, q.lda, d, r0, r1, vs, red, out);
     else apass_unit<32>(q.A, q.lda, d, r0, r1, vs, red, out);
+    flops += 4.0 * (double)(r1 - r0) * d;
+  }
+  if (threadIdx.x == 0 && c.tap) {
+    atomicMax(&c.tap[1], (unsigned long long)global_ns());
+    if (flops > 0) atomicAdd(c.apass_flops, flops);
   }
 }
 
@@ -707,7 +719,14 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
   int a = 0;
   for (int p = threadIdx.x; p < c.P; p += blockDim.x) a += S[p].phase < PH_DONE ? 1 : 0;
   a = block_sum(a, scratch);
-  if (threadIdx.x == 0) *c.active = a;
+  if (threadIdx.x == 0) {
+    *c.active = a;
+    if (c.tap) {
+      if (c.tap[1] > c.tap[0]) c.tap[2] += c.tap[1] - c.tap[0];
+      c.tap[0] = ~0ull;
+      c.tap[1] = 0ull;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ setup kernels
@@ -735,6 +754,8 @@ struct Layout {
   BDesc* D = nullptr;
   BState* S = nullptr;
   int *pre_tri = nullptr, *pre_T = nullptr, *pre_ap = nullptr, *pre_red = nullptr, *active = nullptr;
+  unsigned long long* tap = nullptr;
+  double* apass_flops = nullptr;
   DevStatus* st = nullptr;
   std::vector<BDesc> host;
   size_t used = 0;
@@ -777,6 +798,8 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
   L->pre_ap = c.take<int>(P + 1);
   L->pre_red = c.take<int>(P + 1);
   L->active = c.take<int>(1);
+  L->tap = c.take<unsigned long long>(3);
+  L->apass_flops = c.take<double>(1);
   L->st = c.take<DevStatus>(1);
   L->host.assign(P, BDesc{});
   for (int i = 0; i < P; ++i) {
@@ -963,6 +986,8 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
   c.pre_ap = L.pre_ap;
   c.pre_red = L.pre_red;
   c.active = L.active;
+  c.tap = L.tap;
+  c.apass_flops = L.apass_flops;
   int dmax = 0;
   int64_t mmax_all = 1;
   for (const BDesc& q : L.host) {
@@ -997,6 +1022,7 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
       SKS_TRY(upload_prefix(L.pre_ap, pa, stream));
       BCtl ct = c;
       ct.rows_per_unit = rows;
+      ct.tap = nullptr;
       const int g = std::max(1, std::min(pa[P], ap_grid_max));
       b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);  // warm
       SKS_CUDA_TRY(cudaEventRecord(e.a, stream));
@@ -1037,6 +1063,12 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
     int* p;
     ~HostFree() { cudaFreeHost(p); }
   } hf{h_active};
+  {
+    const unsigned long long t0[3] = {~0ull, 0ull, 0ull};
+    SKS_CUDA_TRY(cudaMemcpyAsync(L.tap, t0, sizeof(t0), cudaMemcpyHostToDevice, stream));
+    SKS_CUDA_TRY(cudaMemsetAsync(L.apass_flops, 0, sizeof(double), stream));
+    SKS_CUDA_TRY(cudaStreamSynchronize(stream));  // t0 is a host temporary
+  }
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.a, stream));
   int burst = 4;
   while (rounds < max_rounds) {
@@ -1053,7 +1085,11 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
 
   // ---- per-problem results
   std::vector<BState> hs(P);
+  unsigned long long h_tap[3] = {0, 0, 0};
+  double h_flops = 0.0;
   SKS_CUDA_TRY(cudaMemcpyAsync(hs.data(), L.S, P * sizeof(BState), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(h_tap, L.tap, sizeof(h_tap), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(&h_flops, L.apass_flops, sizeof(double), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaStreamSynchronize(stream));
   float ms_setup = 0.f, ms_tune = 0.f, ms_solve = 0.f;
   SKS_TRY(ev_setup.ms(&ms_setup));
@@ -1091,6 +1127,8 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
     info->ms_setup = ms_setup;
     info->ms_autotune = ms_tune;
     info->ms_solve = ms_solve;
+    info->ms_apass = (float)((double)h_tap[2] * 1e-6);
+    info->apass_flops = h_flops;
   }
   if (result != SKS_OK) {
     const char* what = result == SKS_ERR_NO_CONVERGENCE ? "did not converge"

@@ -13,4 +13,5 @@ from .problems import (  # noqa: F401
     make_problem_torch,
     spectrum,
     batched_specs,
+    make_batch_torch,
 )

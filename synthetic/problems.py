@@ -32,6 +32,9 @@ CONFIGS = {
                dtype="f32", kind="gaussian", m_init=1, tol=1e-8),
     "C4": dict(n=1 << 18, d=1024, decay="sqrt_harmonic", nu=1e-2, lam="one_plus_u", rhs="Aty_multi", k=8,
                dtype="f32", kind="gaussian", m_init=1, tol=1e-8),
+    # one member of the uneven batch; n, d, decay and nu come from batched_specs
+    "C5": dict(n=4096, d=128, decay="geom0.9", nu=1e-2, lam="identity", rhs="Aty", k=1,
+               dtype="f64", kind="srht", m_init=1, tol=1e-8),
 }
 
 
@@ -127,7 +130,7 @@ def make_problem(config="C1", seed=0, n=None, d=None, nu=None, decay=None, lam=N
                    U=U, V=V, y=y, meta=dict(config=config, seed=seed, **cfg))
 
 
-def make_problem_torch(config="C2", seed=0, device="cuda", n=None, d=None):
+def make_problem_torch(config="C2", seed=0, device="cuda", n=None, d=None, nu=None, decay=None):
     """Same recipe as ``make_problem`` on a torch device, for full sizes.
 
     The n x d Gaussian comes from a seeded ``torch.Generator`` on the device
@@ -142,10 +145,9 @@ def make_problem_torch(config="C2", seed=0, device="cuda", n=None, d=None):
     import torch
 
     cfg = dict(CONFIGS[config])
-    if n is not None:
-        cfg["n"] = n
-    if d is not None:
-        cfg["d"] = d
+    for key, val in dict(n=n, d=d, nu=nu, decay=decay).items():
+        if val is not None:
+            cfg[key] = val
     n, d, kk = int(cfg["n"]), int(cfg["d"]), int(cfg["k"])
     rng = np.random.default_rng(seed)
     g = torch.Generator(device=device)
@@ -203,3 +205,16 @@ def batched_specs(count=256, seed=0):
         nu = float(math.exp(rng.uniform(math.log(1e-4), math.log(1e-1))))
         specs.append(dict(n=n, d=d, decay=decay, nu=nu, seed=int(rng.integers(0, 2 ** 31))))
     return specs
+
+
+def make_batch_torch(count=256, seed=0, device="cuda"):
+    """The uneven batch C5 on a torch device: one ``make_problem_torch("C5")``
+    per entry of ``batched_specs(count, seed)``.  Returns (specs, problems)
+    with problems a list of (A64, b, nu, lam) device tensors."""
+    specs = batched_specs(count, seed)
+    out = []
+    for sp in specs:
+        p = make_problem_torch("C5", seed=sp["seed"], device=device, n=sp["n"], d=sp["d"], nu=sp["nu"],
+                               decay=sp["decay"])
+        out.append((p["A64"], p["b"][:, 0].contiguous(), p["nu"], p["lam"]))
+    return specs, out

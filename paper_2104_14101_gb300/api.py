@@ -290,7 +290,9 @@ class BatchSolver:
     """Many independent problems (each one (A, b, nu, lam)) solved together by
     ``sks_solve_batched``: adaptive PCG per problem, every decision on the
     device, one captured CUDA graph replayed until all have stopped.  The
-    workspace is sized and held once; ``solve`` may be called repeatedly."""
+    workspace is sized and held once; ``solve`` may be called repeatedly.
+    With rows_per_unit=0 the first solve times the candidate A-pass unit
+    heights on this batch and later solves reuse the winner."""
 
     def __init__(self, problems, rows_per_unit=0, **opts):
         self._lib = L.load()
@@ -320,6 +322,8 @@ class BatchSolver:
                                              _stream(self.device))
         if check and status != L.OK:
             L.check(status)
+        if self.rows_per_unit == 0 and info.rows_per_unit > 0:
+            self.rows_per_unit = int(info.rows_per_unit)  # tuned once per batch, reused by later solves
         stats = []
         for s in st:
             dct = s.as_dict()

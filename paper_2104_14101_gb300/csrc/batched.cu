@@ -62,6 +62,8 @@ struct BDesc {
   double* M;         // d x d, ld d: lower = factor L, strict upper = L^T
   double* vec;       // kNumVec d-vectors
   double* part;      // A-pass partial sums, one d-vector per unit
+  double* gpart;     // Gram slice partials: [kGramSplit][ntri][64 x 64]
+  int ntri;          // lower 64 x 64 tiles of a d x d matrix
   int64_t m_max, m_init;
 };
 
@@ -166,21 +168,37 @@ SKS_DEV void mma_chunk(const double (*As)[kTP], const double (*Bs)[kTP], double 
   }
 }
 
+// Split of the Gram's sum over the m sketch rows (Cholesky form): slices of
+// at least kGramSliceMin rows, at most kGramSplit slices, summed in a fixed
+// order by b_gram_reduce_kernel (deterministic).
+constexpr int kGramSplit = 8;
+constexpr int kGramSliceMin = 512;
+
+SKS_DEV int gram_slices(const BState& s) {
+  return s.form == 0 ? min(kGramSplit, max(1, (int)((s.m + kGramSliceMin - 1) / kGramSliceMin))) : 1;
+}
+
 // Sketched-Hessian matrix of every GROW problem, lower 64 x 64 tiles:
 //   form 0: M = (1/m) Y^T Y + nu^2 Lambda          (Y = rows perm[0..m) of B)
 //   form 1: M = I + (1/(m nu^2)) Y Lambda^{-1} Y^T
+// Units are (tile, slice); with one slice the tile is written to M, else the
+// raw slice sum goes to the problem's partial tiles.
 __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
                                                      int total) {
   __shared__ __align__(16) double As[16][kTP];
   __shared__ __align__(16) double Bs[16][kTP];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
-    const int p = find_problem(c.pre_tri, c.P, u);
+    const int tu = u / kGramSplit, ks = u - tu * kGramSplit;
+    const int p = find_problem(c.pre_tri, c.P, tu);
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
+    const int nks = gram_slices(s);
+    if (ks >= nks) continue;
     const BDesc& q = D[p];
+    const int l = tu - c.pre_tri[p];
     int ti, tj;
-    tri_index(u - c.pre_tri[p], &ti, &tj);
+    tri_index(l, &ti, &tj);
     const int N = factor_size(s, q);
     const int i0 = ti * kTile, j0 = tj * kTile;
     if (i0 >= N) continue;
@@ -192,12 +210,14 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
     if (s.form == 0) {
-      for (int k0 = 0; k0 < m; k0 += 16) {
+      const int per = ((m + nks - 1) / nks + 15) / 16 * 16;
+      const int kb = ks * per, ke = min(m, kb + per);
+      for (int k0 = kb; k0 < ke; k0 += 16) {
         for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
           const int kk = e >> 6, ii = e & 63;
           const int r = k0 + kk;
           double a = 0.0, b = 0.0;
-          if (r < m) {
+          if (r < ke) {
             const double* y = q.B + (int64_t)q.perm[r] * d;
             if (i0 + ii < N) a = y[i0 + ii];
             if (j0 + ii < N) b = y[j0 + ii];
@@ -227,6 +247,14 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
         __syncthreads();
       }
     }
+    if (nks > 1) {
+      double* tile = q.gpart + ((size_t)ks * (size_t)q.ntri + l) * (kTile * kTile);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tile[(ty * 4 + i) * kTile + tx * 4 + j] = acc[i][j];
+      continue;
+    }
     const double scale = s.form == 0 ? 1.0 / (double)m : 1.0 / ((double)m * q.nu2);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -239,6 +267,36 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
           q.M[(int64_t)gi * d + gj] = v;
         }
       }
+  }
+}
+
+// Sum of the slice partials (slice order fixed), scale and diagonal, into M.
+__global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
+                                                            int total) {
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_tri, c.P, u);
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const int nks = gram_slices(s);
+    if (nks <= 1) continue;
+    const BDesc& q = D[p];
+    const int l = u - c.pre_tri[p];
+    int ti, tj;
+    tri_index(l, &ti, &tj);
+    const int N = factor_size(s, q);
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    if (i0 >= N) continue;
+    const int d = q.d;
+    const double scale = 1.0 / (double)s.m;
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int gi = i0 + (e >> 6), gj = j0 + (e & 63);
+      if (gi >= N || gj >= N) continue;
+      double t = 0.0;
+      for (int ks = 0; ks < nks; ++ks) t += q.gpart[((size_t)ks * (size_t)q.ntri + l) * (kTile * kTile) + e];
+      double v = t * scale;
+      if (gi == gj) v += q.nu2 * q.lam[gi];
+      q.M[(int64_t)gi * d + gj] = v;
+    }
   }
 }
 
@@ -584,7 +642,7 @@ SKS_DEV void tri_solve(const double* __restrict__ M, int ld, int N, const double
 //   form 0: H_S = L L^T (two triangular solves)
 //   form 1: H_S^{-1} z = u - (nu^2 Lambda)^{-1} Y_s^T K^{-1} Y_s u,  u = (nu^2 Lambda)^{-1} z,
 //           Y_s = Y / sqrt(m), K = I + Y_s (nu^2 Lambda)^{-1} Y_s^T = L L^T
-__global__ void __launch_bounds__(256) b_apply_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S) {
+__global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S) {
   __shared__ double y[kMaxD];
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     const BState s = S[p];
@@ -821,6 +879,10 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
     q.M = c.take<double>((size_t)q.d * q.d);
     q.vec = c.take<double>((size_t)kNumVec * q.d);
     q.part = c.take<double>((size_t)((p.n + kMinRowsPerUnit - 1) / kMinRowsPerUnit) * q.d);
+    const int T = (q.d + kTile - 1) / kTile;
+    q.ntri = T * (T + 1) / 2;
+    // slices only exist when m can reach 2 kGramSliceMin rows
+    q.gpart = q.m_max > kGramSliceMin ? c.take<double>((size_t)kGramSplit * q.ntri * kTile * kTile) : nullptr;
   }
   L->used = c.used + 256;
   if (ws && !c.ok()) return fail(SKS_ERR_WORKSPACE, "batch: workspace too small");
@@ -847,7 +909,7 @@ struct Round {
   const BDesc* D;
   BState* S;
   int P, kmax, tot_tri, tot_T, tot_ap, tot_red;
-  int g_tile, g_trsm, g_ap, g_prob;
+  int g_tile, g_gram, g_trsm, g_ap, g_prob;
   size_t ap_smem;
 };
 
@@ -859,8 +921,9 @@ int enqueue_round(const Round& R, cudaStream_t stream) {
   ++n;
   b_perm_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
   ++n;
-  b_gram_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri);
-  ++n;
+  b_gram_kernel<<<R.g_gram, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri * kGramSplit);
+  b_gram_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri);
+  n += 2;
   for (int k = 0; k < R.kmax; ++k) {
     b_potrf_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S, k);
     ++n;
@@ -873,7 +936,7 @@ int enqueue_round(const Round& R, cudaStream_t stream) {
   b_apass_kernel<<<R.g_ap, kApThreads, R.ap_smem, stream>>>(R.ctl, R.D, R.S, R.tot_ap);
   b_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_red);
   b_step1_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
-  b_apply_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
+  b_apply_kernel<<<R.g_prob, 512, 0, stream>>>(R.ctl, R.D, R.S);
   b_step2_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
   b_count_kernel<<<1, 256, 0, stream>>>(R.ctl, R.S);
   n += 6;
@@ -1000,6 +1063,7 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
   R.tot_red = pre_red[P];
   R.g_prob = std::min(P, 8 * sms);
   R.g_tile = std::max(1, std::min(R.tot_tri, 4 * sms));
+  R.g_gram = std::max(1, std::min(R.tot_tri * kGramSplit, 4 * sms));
   R.g_trsm = std::max(1, std::min(R.tot_T, 8 * sms));
   R.ap_smem = (size_t)(1 + kApWarps) * kMaxD * sizeof(double);
   SKS_CUDA_TRY(cudaFuncSetAttribute(b_apass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R.ap_smem));

@@ -63,6 +63,7 @@ struct BDesc {
   double* vec;       // kNumVec d-vectors
   double* part;      // A-pass partial sums, one d-vector per unit
   double* gpart;     // Gram slice partials: [kGramSplit][ntri][64 x 64]
+  double* G;         // d x d, ld d: unscaled Y^T Y of the rows summed so far
   int ntri;          // lower 64 x 64 tiles of a d x d matrix
   int64_t m_max, m_init;
 };
@@ -71,6 +72,8 @@ struct BState {
   int phase, form;   // form 0: Cholesky (N = d), 1: Woodbury (N = m)
   int status, pad;
   int64_t m, m_old, t, I;
+  int64_t gram_rows;  // sketch rows already summed into G (Cholesky form)
+  int64_t k_begin;    // first sketch row this round's Gram adds
   double dt, dI, btx;
   int64_t rejections, a_passes, factorizations;
 };
@@ -131,6 +134,9 @@ __global__ void b_begin_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
   s.m_old = s.m;
   s.m = s.m == 0 ? min(q.m_init, q.m_max) : min(2 * s.m, q.m_max);
   s.form = s.m >= q.d ? 0 : 1;
+  // nested sketches: the Cholesky form keeps G = Y^T Y and adds the new rows
+  s.k_begin = s.form == 0 ? s.gram_rows : 0;
+  if (s.form == 0) s.gram_rows = s.m;
   s.factorizations += 1;
 }
 
@@ -172,14 +178,16 @@ SKS_DEV void mma_chunk(const double (*As)[kTP], const double (*Bs)[kTP], double 
 // at least kGramSliceMin rows, at most kGramSplit slices, summed in a fixed
 // order by b_gram_reduce_kernel (deterministic).
 constexpr int kGramSplit = 8;
-constexpr int kGramSliceMin = 512;
+constexpr int kGramSliceMin = 1024;
 
 SKS_DEV int gram_slices(const BState& s) {
-  return s.form == 0 ? min(kGramSplit, max(1, (int)((s.m + kGramSliceMin - 1) / kGramSliceMin))) : 1;
+  const int64_t rows = s.m - s.k_begin;
+  return s.form == 0 ? min(kGramSplit, max(1, (int)((rows + kGramSliceMin - 1) / kGramSliceMin))) : 1;
 }
 
 // Sketched-Hessian matrix of every GROW problem, lower 64 x 64 tiles:
-//   form 0: M = (1/m) Y^T Y + nu^2 Lambda          (Y = rows perm[0..m) of B)
+//   form 0: M = (1/m) G + nu^2 Lambda, G = Y^T Y (Y = rows perm[0..m) of B)
+//           kept across doublings: G += Y_new^T Y_new for the rows added
 //   form 1: M = I + (1/(m nu^2)) Y Lambda^{-1} Y^T
 // Units are (tile, slice); with one slice the tile is written to M, else the
 // raw slice sum goes to the problem's partial tiles.
@@ -210,8 +218,9 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
     if (s.form == 0) {
-      const int per = ((m + nks - 1) / nks + 15) / 16 * 16;
-      const int kb = ks * per, ke = min(m, kb + per);
+      const int k_begin = (int)s.k_begin;
+      const int per = ((m - k_begin + nks - 1) / nks + 15) / 16 * 16;
+      const int kb = k_begin + ks * per, ke = min(m, kb + per);
       for (int k0 = kb; k0 < ke; k0 += 16) {
         for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
           const int kk = e >> 6, ii = e & 63;
@@ -262,7 +271,13 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
       for (int j = 0; j < 4; ++j) {
         const int gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
         if (gi < N && gj < N) {
-          double v = acc[i][j] * scale;
+          double g = acc[i][j];
+          if (s.form == 0) {
+            double* gp = q.G + (int64_t)gi * d + gj;
+            if (s.k_begin > 0) g += *gp;
+            *gp = g;
+          }
+          double v = g * scale;
           if (gi == gj) v += s.form == 0 ? q.nu2 * q.lam[gi] : 1.0;
           q.M[(int64_t)gi * d + gj] = v;
         }
@@ -293,6 +308,9 @@ __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc*
       if (gi >= N || gj >= N) continue;
       double t = 0.0;
       for (int ks = 0; ks < nks; ++ks) t += q.gpart[((size_t)ks * (size_t)q.ntri + l) * (kTile * kTile) + e];
+      double* gp = q.G + (int64_t)gi * d + gj;
+      if (s.k_begin > 0) t = *gp + t;
+      *gp = t;
       double v = t * scale;
       if (gi == gj) v += q.nu2 * q.lam[gi];
       q.M[(int64_t)gi * d + gj] = v;
@@ -883,6 +901,7 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
     q.ntri = T * (T + 1) / 2;
     // slices only exist when m can reach 2 kGramSliceMin rows
     q.gpart = q.m_max > kGramSliceMin ? c.take<double>((size_t)kGramSplit * q.ntri * kTile * kTile) : nullptr;
+    q.G = c.take<double>((size_t)q.d * q.d);
   }
   L->used = c.used + 256;
   if (ws && !c.ok()) return fail(SKS_ERR_WORKSPACE, "batch: workspace too small");

@@ -288,6 +288,8 @@ typedef struct {
   float ms_apass;            /* summed duration of the rounds' A-pass kernels (device
                                 clock: first CTA start to last CTA end per round)   */
   double apass_flops;        /* 4 n d per A-pass of every problem, summed            */
+  float ms_gram;             /* the same for the sketched-Hessian (Gram) kernels     */
+  double gram_flops;         /* 2 x 64 x 64 per sketch row of every Gram tile        */
 } sks_batch_info;
 
 sks_status sks_batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes);

@@ -54,7 +54,8 @@ class Stats(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("rounds", C.c_int64), ("kernels_per_round", C.c_int64), ("rows_per_unit", C.c_int64),
                 ("ms_setup", C.c_float), ("ms_autotune", C.c_float), ("ms_solve", C.c_float),
-                ("ms_apass", C.c_float), ("apass_flops", C.c_double)]
+                ("ms_apass", C.c_float), ("apass_flops", C.c_double), ("ms_gram", C.c_float),
+                ("gram_flops", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -94,6 +94,8 @@ struct BCtl {
   // flops: 4 n d per A-pass unit row block, summed over rounds
   unsigned long long* tap;
   double* apass_flops;
+  unsigned long long* tgram;  // the same for the Gram kernel (first start, last end, sum)
+  double* gram_flops;         // 2 x 64 x 64 per sketch row (or column) of every Gram unit
 };
 
 // largest p with pre[p] <= u  (pre[0] = 0 <= u < pre[P])
@@ -174,15 +176,17 @@ SKS_DEV void mma_chunk(const double (*As)[kTP], const double (*Bs)[kTP], double 
   }
 }
 
-// Split of the Gram's sum over the m sketch rows (Cholesky form): slices of
-// at least kGramSliceMin rows, at most kGramSplit slices, summed in a fixed
-// order by b_gram_reduce_kernel (deterministic).
+// Split of the Gram's sum (over the new sketch rows in the Cholesky form, over
+// the d columns in the Woodbury form) into at most kGramSplit slices, summed in
+// a fixed order by b_gram_reduce_kernel (deterministic).
 constexpr int kGramSplit = 8;
-constexpr int kGramSliceMin = 1024;
+constexpr int kGramSliceRows = 256;  // Cholesky form: new sketch rows per slice (at least)
+constexpr int kGramSliceCols = 128;  // Woodbury form: columns of Y per slice (at least)
 
-SKS_DEV int gram_slices(const BState& s) {
-  const int64_t rows = s.m - s.k_begin;
-  return s.form == 0 ? min(kGramSplit, max(1, (int)((rows + kGramSliceMin - 1) / kGramSliceMin))) : 1;
+SKS_DEV int gram_slices(const BState& s, int d) {
+  const int64_t k = s.form == 0 ? s.m - s.k_begin : d;
+  const int per = s.form == 0 ? kGramSliceRows : kGramSliceCols;
+  return min(kGramSplit, max(1, (int)((k + per - 1) / per)));
 }
 
 // Sketched-Hessian matrix of every GROW problem, lower 64 x 64 tiles:
@@ -196,14 +200,16 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
   __shared__ __align__(16) double As[16][kTP];
   __shared__ __align__(16) double Bs[16][kTP];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (threadIdx.x == 0 && c.tgram) atomicMin(&c.tgram[0], (unsigned long long)global_ns());
+  double flops = 0.0;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int tu = u / kGramSplit, ks = u - tu * kGramSplit;
     const int p = find_problem(c.pre_tri, c.P, tu);
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
-    const int nks = gram_slices(s);
-    if (ks >= nks) continue;
     const BDesc& q = D[p];
+    const int nks = gram_slices(s, q.d);
+    if (ks >= nks) continue;
     const int l = tu - c.pre_tri[p];
     int ti, tj;
     tri_index(l, &ti, &tj);
@@ -221,6 +227,7 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
       const int k_begin = (int)s.k_begin;
       const int per = ((m - k_begin + nks - 1) / nks + 15) / 16 * 16;
       const int kb = k_begin + ks * per, ke = min(m, kb + per);
+      flops += 2.0 * kTile * kTile * (double)max(0, ke - kb);
       for (int k0 = kb; k0 < ke; k0 += 16) {
         for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
           const int kk = e >> 6, ii = e & 63;
@@ -239,12 +246,15 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
         __syncthreads();
       }
     } else {
-      for (int k0 = 0; k0 < d; k0 += 16) {
+      const int per = ((d + nks - 1) / nks + 15) / 16 * 16;
+      const int cb = ks * per, ce = min(d, cb + per);
+      flops += 2.0 * kTile * kTile * (double)max(0, ce - cb);
+      for (int k0 = cb; k0 < ce; k0 += 16) {
         for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
           const int ii = e >> 4, kk = e & 15;
           const int col = k0 + kk;
           double a = 0.0, b = 0.0;
-          if (col < d) {
+          if (col < ce) {
             if (i0 + ii < N) a = q.B[(int64_t)q.perm[i0 + ii] * d + col] / q.lam[col];
             if (j0 + ii < N) b = q.B[(int64_t)q.perm[j0 + ii] * d + col];
           }
@@ -283,6 +293,10 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
         }
       }
   }
+  if (threadIdx.x == 0 && c.tgram) {
+    atomicMax(&c.tgram[1], (unsigned long long)global_ns());
+    if (flops > 0) atomicAdd(c.gram_flops, flops);
+  }
 }
 
 // Sum of the slice partials (slice order fixed), scale and diagonal, into M.
@@ -292,9 +306,9 @@ __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc*
     const int p = find_problem(c.pre_tri, c.P, u);
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
-    const int nks = gram_slices(s);
-    if (nks <= 1) continue;
     const BDesc& q = D[p];
+    const int nks = gram_slices(s, q.d);
+    if (nks <= 1) continue;
     const int l = u - c.pre_tri[p];
     int ti, tj;
     tri_index(l, &ti, &tj);
@@ -302,17 +316,19 @@ __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc*
     const int i0 = ti * kTile, j0 = tj * kTile;
     if (i0 >= N) continue;
     const int d = q.d;
-    const double scale = 1.0 / (double)s.m;
+    const double scale = s.form == 0 ? 1.0 / (double)s.m : 1.0 / ((double)s.m * q.nu2);
     for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
       const int gi = i0 + (e >> 6), gj = j0 + (e & 63);
       if (gi >= N || gj >= N) continue;
       double t = 0.0;
       for (int ks = 0; ks < nks; ++ks) t += q.gpart[((size_t)ks * (size_t)q.ntri + l) * (kTile * kTile) + e];
-      double* gp = q.G + (int64_t)gi * d + gj;
-      if (s.k_begin > 0) t = *gp + t;
-      *gp = t;
+      if (s.form == 0) {
+        double* gp = q.G + (int64_t)gi * d + gj;
+        if (s.k_begin > 0) t = *gp + t;
+        *gp = t;
+      }
       double v = t * scale;
-      if (gi == gj) v += q.nu2 * q.lam[gi];
+      if (gi == gj) v += s.form == 0 ? q.nu2 * q.lam[gi] : 1.0;
       q.M[(int64_t)gi * d + gj] = v;
     }
   }
@@ -802,6 +818,11 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
       c.tap[0] = ~0ull;
       c.tap[1] = 0ull;
     }
+    if (c.tgram) {
+      if (c.tgram[1] > c.tgram[0]) c.tgram[2] += c.tgram[1] - c.tgram[0];
+      c.tgram[0] = ~0ull;
+      c.tgram[1] = 0ull;
+    }
   }
 }
 
@@ -832,6 +853,8 @@ struct Layout {
   int *pre_tri = nullptr, *pre_T = nullptr, *pre_ap = nullptr, *pre_red = nullptr, *active = nullptr;
   unsigned long long* tap = nullptr;
   double* apass_flops = nullptr;
+  unsigned long long* tgram = nullptr;
+  double* gram_flops = nullptr;
   DevStatus* st = nullptr;
   std::vector<BDesc> host;
   size_t used = 0;
@@ -876,6 +899,8 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
   L->active = c.take<int>(1);
   L->tap = c.take<unsigned long long>(3);
   L->apass_flops = c.take<double>(1);
+  L->tgram = c.take<unsigned long long>(3);
+  L->gram_flops = c.take<double>(1);
   L->st = c.take<DevStatus>(1);
   L->host.assign(P, BDesc{});
   for (int i = 0; i < P; ++i) {
@@ -900,7 +925,7 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
     const int T = (q.d + kTile - 1) / kTile;
     q.ntri = T * (T + 1) / 2;
     // slices only exist when m can reach 2 kGramSliceMin rows
-    q.gpart = q.m_max > kGramSliceMin ? c.take<double>((size_t)kGramSplit * q.ntri * kTile * kTile) : nullptr;
+    q.gpart = c.take<double>((size_t)kGramSplit * q.ntri * kTile * kTile);
     q.G = c.take<double>((size_t)q.d * q.d);
   }
   L->used = c.used + 256;
@@ -1070,6 +1095,8 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
   c.active = L.active;
   c.tap = L.tap;
   c.apass_flops = L.apass_flops;
+  c.tgram = L.tgram;
+  c.gram_flops = L.gram_flops;
   int dmax = 0;
   int64_t mmax_all = 1;
   for (const BDesc& q : L.host) {
@@ -1106,6 +1133,7 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
       BCtl ct = c;
       ct.rows_per_unit = rows;
       ct.tap = nullptr;
+      ct.tgram = nullptr;
       const int g = std::max(1, std::min(pa[P], ap_grid_max));
       b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);  // warm
       SKS_CUDA_TRY(cudaEventRecord(e.a, stream));
@@ -1150,6 +1178,8 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
     const unsigned long long t0[3] = {~0ull, 0ull, 0ull};
     SKS_CUDA_TRY(cudaMemcpyAsync(L.tap, t0, sizeof(t0), cudaMemcpyHostToDevice, stream));
     SKS_CUDA_TRY(cudaMemsetAsync(L.apass_flops, 0, sizeof(double), stream));
+    SKS_CUDA_TRY(cudaMemcpyAsync(L.tgram, t0, sizeof(t0), cudaMemcpyHostToDevice, stream));
+    SKS_CUDA_TRY(cudaMemsetAsync(L.gram_flops, 0, sizeof(double), stream));
     SKS_CUDA_TRY(cudaStreamSynchronize(stream));  // t0 is a host temporary
   }
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.a, stream));
@@ -1168,11 +1198,13 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
 
   // ---- per-problem results
   std::vector<BState> hs(P);
-  unsigned long long h_tap[3] = {0, 0, 0};
-  double h_flops = 0.0;
+  unsigned long long h_tap[3] = {0, 0, 0}, h_tgram[3] = {0, 0, 0};
+  double h_flops = 0.0, h_gflops = 0.0;
   SKS_CUDA_TRY(cudaMemcpyAsync(hs.data(), L.S, P * sizeof(BState), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(h_tap, L.tap, sizeof(h_tap), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(&h_flops, L.apass_flops, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(h_tgram, L.tgram, sizeof(h_tgram), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(&h_gflops, L.gram_flops, sizeof(double), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaStreamSynchronize(stream));
   float ms_setup = 0.f, ms_tune = 0.f, ms_solve = 0.f;
   SKS_TRY(ev_setup.ms(&ms_setup));
@@ -1212,6 +1244,8 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
     info->ms_solve = ms_solve;
     info->ms_apass = (float)((double)h_tap[2] * 1e-6);
     info->apass_flops = h_flops;
+    info->ms_gram = (float)((double)h_tgram[2] * 1e-6);
+    info->gram_flops = h_gflops;
   }
   if (result != SKS_OK) {
     const char* what = result == SKS_ERR_NO_CONVERGENCE ? "did not converge"

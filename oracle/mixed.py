@@ -18,6 +18,9 @@ reproduce bit for bit:
 * ``split_rowscaled``: the operand split of the tensor-core Gram matrix:
   every row is cut against its own maximum exponent into two slices of
   integers (8 + 8 bits), so that all slice products are exactly summable.
+* ``gaussian_sketch_tc_unscaled``: the float32 Gaussian sketch of the
+  tensor-core path, Y = bf16(G) (hi + lo) with (hi, lo) the row-scaled split
+  of A^T (each column of A against its own maximum exponent).
 * ``refine``: the outer refinement loop around any inner solver.
 """
 import numpy as np
@@ -78,6 +81,31 @@ def gaussian_sketch_bf16_unscaled(A32, m, seed):
     hi, lo = split_hi_lo(A32)
     Gb = gaussian_bf16(A32.shape[0], m, seed)
     return Gb @ (hi + lo)
+
+
+def gaussian_sketch_tc_unscaled(A32, m, seed, row0=0):
+    """Rows [row0, m) of Y = bf16(G) (hi + lo)^T (unscaled; S A = Y / sqrt(m)),
+    with (hi, lo) = split_rowscaled(A32^T) and G from ``rng.gaussian_block``
+    rounded to float32, then to bfloat16."""
+    hiT, loT = split_rowscaled(np.asarray(A32, dtype=np.float32).T)
+    Gb = gaussian_bf16(A32.shape[0], m, seed)[row0:]
+    return Gb @ (hiT + loT).T
+
+
+def bf16_midpoint_slack(g32, ulps=4):
+    """For float32 values g32: the size of one bfloat16 step at each entry
+    where a perturbation of up to `ulps` float32 ulps can change the
+    bfloat16 rounding (a rounding midpoint lies within reach), else 0.  Two
+    implementations of the same float32 formula that agree to `ulps` ulps
+    round to bfloat16 identically everywhere the slack is 0."""
+    g = np.asarray(g32, dtype=np.float32)
+    step = np.spacing(np.abs(g)).astype(np.float32) * np.float32(ulps)
+    lo = bf16_round((g - step).astype(np.float32))
+    hi = bf16_round((g + step).astype(np.float32))
+    here = bf16_round(g)
+    amb = (lo != here) | (hi != here)
+    ulp_bf16 = np.abs(here) * 2.0 ** -7 + 1e-45
+    return np.where(amb, np.maximum(np.abs(hi - lo), ulp_bf16), 0.0)
 
 
 def refine(A, b, nu, lam, inner, tol, max_outer=20):

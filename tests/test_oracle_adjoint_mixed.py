@@ -110,3 +110,36 @@ def test_split_rowscaled_exactness():
         for v in p32:
             s32 = np.float32(s32 + v)
         assert float(s32) == float(np.sum(a[0, :256] * b[1, :256]))
+
+
+def test_gaussian_sketch_tc_definition():
+    # (a) columns of A made of small integers are represented exactly by the
+    # hi slice, so the sketch is exactly bf16(G) A; (b) in general it is within
+    # the split's bound sum_i |g_ri| 2^(e_c - 17) of bf16(G) A; (c) rows are
+    # nested (rows [row0, m) of the m-row sketch are the tail of it).
+    rng = np.random.default_rng(11)
+    A = rng.integers(-50, 50, size=(300, 7)).astype(np.float32)
+    Gb = MX.gaussian_bf16(300, 12, 5)
+    assert np.array_equal(MX.gaussian_sketch_tc_unscaled(A, 12, 5), Gb @ A.astype(np.float64))
+    A = (rng.standard_normal((500, 9)) * np.exp(rng.uniform(-5, 5, size=(1, 9)))).astype(np.float32)
+    Y = MX.gaussian_sketch_tc_unscaled(A, 16, 7)
+    Gb = MX.gaussian_bf16(500, 16, 7)
+    _, e = np.frexp(np.max(np.abs(A), axis=0))
+    bound = np.abs(Gb).sum(axis=1)[:, None] * np.ldexp(1.0, e - 17)[None, :]
+    assert np.all(np.abs(Y - Gb @ A.astype(np.float64)) <= bound)
+    assert np.array_equal(MX.gaussian_sketch_tc_unscaled(A, 16, 7, row0=9), Y[9:])
+
+
+def test_bf16_midpoint_slack():
+    # values far from a bfloat16 midpoint have slack 0 and round identically
+    # under a small perturbation; values on a midpoint get one bfloat16 step
+    g = np.array([1.0, 1.0 + 2 ** -8, 1.5, -3.0 - 2 ** -7], dtype=np.float32)
+    sl = MX.bf16_midpoint_slack(g, ulps=2)
+    assert sl[0] == 0 and sl[2] == 0
+    assert sl[1] >= 2 ** -7 and sl[3] >= 2 ** -6  # at least one bfloat16 step
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal(20000).astype(np.float32)
+    sl = MX.bf16_midpoint_slack(x, ulps=2)
+    y = (x + np.spacing(np.abs(x)) * rng.integers(-2, 3, size=x.shape)).astype(np.float32)
+    same = MX.bf16_round(x) == MX.bf16_round(y)
+    assert np.all(same | (sl > 0))

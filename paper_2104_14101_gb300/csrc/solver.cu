@@ -34,6 +34,13 @@ struct sks_sketch {
   size_t gbuf_elems = 0;
   void* split = nullptr;
   size_t split_elems = 0;
+  // float32 Gaussian sketch on the tensor cores: split A^T, column maxima, slice partials
+  void* tch = nullptr;
+  void* tcl = nullptr;
+  unsigned* cmax = nullptr;
+  float* tcpart = nullptr;
+  size_t tcpart_elems = 0;
+  bool tc_ready = false;
   sks::DevStatus* st = nullptr;
   double scale2() const { return kind == SKS_SJLT ? 1.0 : 1.0 / (double)m; }
 };
@@ -147,6 +154,7 @@ inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)std::max
 // ---------------------------------------------------------------- sketch
 struct SketchSizes {
   size_t b_elems = 0, y_elems = 0, g_elems = 0, split_elems = 0;
+  size_t tc_elems = 0, tcpart_elems = 0, cmax_elems = 0;  // float32 Gaussian (tensor cores)
 };
 
 SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max) {
@@ -154,7 +162,11 @@ SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max) {
   const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
   if (kind == SKS_SRHT) z.b_elems = (size_t)n_pad * p->d;
   z.y_elems = (size_t)m_max * p->d;
-  if (kind == SKS_GAUSSIAN) {
+  if (kind == SKS_GAUSSIAN && p->dtype == SKS_F32) {
+    z.tc_elems = (size_t)p->d * (size_t)tc_gauss_kp(p->n);
+    z.cmax_elems = (size_t)p->d;
+    z.tcpart_elems = tc_gauss_part_elems(p->n, (int)p->d, (int)std::min<int64_t>(m_max, 1 << 30));
+  } else if (kind == SKS_GAUSSIAN) {
     z.g_elems = (size_t)std::min<int64_t>((int64_t)m_max * std::max<int64_t>(p->n, 1), (int64_t)1 << 24);
     z.g_elems = std::max<size_t>(z.g_elems, (size_t)m_max * 64);
     z.split_elems = std::min<size_t>((size_t)8 * m_max * p->d, (size_t)1 << 24);
@@ -176,6 +188,10 @@ size_t sketch_ws_bytes(const sks_problem* p, sks_kind kind, int64_t m_max) {
   c.take<DevStatus>(1);
   c.take<char>(z.b_elems * esz);
   c.take<char>(z.y_elems * esz);
+  c.take<__nv_bfloat16>(z.tc_elems);
+  c.take<__nv_bfloat16>(z.tc_elems);
+  c.take<unsigned>(z.cmax_elems);
+  c.take<float>(z.tcpart_elems);
   c.take<char>(z.g_elems * esz);
   c.take<char>(z.split_elems * esz);
   return c.used + 256;
@@ -204,6 +220,12 @@ sks_status sketch_init(sks_sketch* s, const sks_problem* p, sks_kind kind, int64
   s->gbuf_elems = z.g_elems;
   s->split = c.take<char>(z.split_elems * esz);
   s->split_elems = z.split_elems;
+  s->tch = c.take<__nv_bfloat16>(z.tc_elems);
+  s->tcl = c.take<__nv_bfloat16>(z.tc_elems);
+  s->cmax = c.take<unsigned>(z.cmax_elems);
+  s->tcpart = c.take<float>(z.tcpart_elems);
+  s->tcpart_elems = z.tcpart_elems;
+  s->tc_ready = false;
   if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "sketch workspace too small");
   if (z.b_elems == 0) s->B = nullptr;
   return SKS_OK;
@@ -218,6 +240,15 @@ sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
   if (s->kind == SKS_SRHT) {
     if (s->m == 0) SKS_TRY(srht_form<T>(stream, A, p.lda, p.n, d, (T*)s->B, d, s->seed));
     SKS_TRY(srht_gather<T, T>(stream, (const T*)s->B, d, d, s->n_pad, s->seed, (int)s->m, (int)new_m, Y, s->ldy, s->st));
+  } else if (s->kind == SKS_GAUSSIAN && s->f32) {
+    // bf16(G) times the split A^T on the tensor cores; the split is made once per sketch
+    if (!s->tc_ready) {
+      SKS_TRY(tc_split_t(stream, (const float*)A, p.lda, p.n, d, (__nv_bfloat16*)s->tch, (__nv_bfloat16*)s->tcl,
+                         s->cmax));
+      s->tc_ready = true;
+    }
+    SKS_TRY(tc_gauss_sketch(stream, (const __nv_bfloat16*)s->tch, (const __nv_bfloat16*)s->tcl, p.n, d, s->seed,
+                            (int)s->m, (int)(new_m - s->m), s->tcpart, s->tcpart_elems, (float*)Y, s->ldy, s->st));
   } else if (s->kind == SKS_GAUSSIAN) {
     SKS_TRY(gaussian_extend<T>(stream, A, p.lda, p.n, d, s->seed, (int)s->m, (int)(new_m - s->m), Y, s->ldy,
                                (T*)s->gbuf, s->gbuf_elems, (T*)s->split, s->split_elems));

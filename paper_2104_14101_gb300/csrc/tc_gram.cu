@@ -353,6 +353,258 @@ __global__ void unsplit_kernel(const __nv_bfloat16* __restrict__ Hh, const __nv_
   Y[(long long)r * ldy + c] = v;
 }
 
+// ------------------------------------------------------------------ Gaussian sketch on tensor cores
+//
+// K4 for float32 A: Y[r] = sum_i bf16(G[r][i]) (hi + lo)[.][i], i.e. the
+// product of the Philox/Box-Muller matrix G (rounded to bfloat16) with the
+// row-scaled two-slice split of A^T (each column of A against its own maximum
+// exponent, prepared once by tc_split_t).  One CTA per (128 sketch rows) x
+// (256 columns) x (K slice of data rows) tile, 18 warps:
+//   warp 0      TMA producer: the hi and lo tiles of A^T (256 x 64 bf16, 128B
+//               swizzle) into a 2-stage ring;
+//   warp 1      MMA issuer: 8 tcgen05.mma (M=128, N=256, K=16) per stage, both
+//               slices into one float32 TMEM accumulator;
+//   warps 2-17  generators: the 128 x 64 G tile of the stage from Philox in
+//               registers, rounded to bfloat16 and written in the swizzled
+//               K-major layout the MMA reads (G never goes to global memory);
+//               after the last stage they drain the accumulator to the
+//               slice's float32 partial.
+// Slices of at most 16384 data rows keep the float32 accumulation error near
+// 2^-24 sqrt(16384); the partials are summed in a fixed order in float64.
+constexpr int GBM = 128, GBN = 256, GBK = 64;
+constexpr int kGStages = 2;
+constexpr int kGTileG = GBM * GBK * 2;                 // 16 KB
+constexpr int kGTileA = GBN * GBK * 2;                 // 32 KB
+constexpr int kGStageBytes = kGTileG + 2 * kGTileA;    // 80 KB
+constexpr int kGGenWarps = 16;
+constexpr int kGThreads = (2 + kGGenWarps) * 32;
+constexpr uint32_t kGTmemCols = 256;
+constexpr int kGaussSlice = 16384;    // data rows per K slice
+constexpr int kGaussRowChunk = 4096;  // new sketch rows per launch (bounds the partials)
+
+struct GaussArgs {
+  int d, m_add, row_base;  // sketch rows [row_base, row_base + m_add)
+  long long n;             // data rows
+  int Kp, kc;              // padded K; data rows per slice (multiple of 64)
+  int tiles_m, tiles_n, ksplits;
+  Key key;
+  float* part;             // [ksplits][m_add][d]
+  DevStatus* st;
+};
+
+__global__ void __launch_bounds__(kGThreads, 1)
+    tc_gauss_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl, GaussArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t tfull[kGStages], gfull[kGStages], empty[kGStages], acc_full;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  const int ks = blockIdx.x % g.ksplits;
+  const int t2 = blockIdx.x / g.ksplits;
+  const int tn = t2 % g.tiles_n, tm = t2 / g.tiles_n;
+  const int rloc0 = tm * GBM;  // first tile row within the m_add new rows
+  const int col0 = tn * GBN;
+  const int kbeg = ks * g.kc;
+  const int kend = min(g.Kp, kbeg + g.kc);
+  const int nk = (kend - kbeg) / GBK;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kGStages; ++s) {
+      mbar_init(&tfull[s], 1);
+      mbar_init(&gfull[s], kGGenWarps);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(kGTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kk = 0; kk < nk; ++kk) {
+        const int s = kk % kGStages;
+        const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
+        if (abort_flag || !mbar_wait(&empty[s], ph ^ 1u, g.st, 51)) {
+          abort_flag = 1;
+          break;
+        }
+        unsigned char* st = smem + (size_t)s * kGStageBytes;
+        mbar_arrive_expect_tx(&tfull[s], 2 * kGTileA);
+        tma_load_2d(st + kGTileG, &mAh, &tfull[s], kbeg + kk * GBK, col0);
+        tma_load_2d(st + kGTileG + kGTileA, &mAl, &tfull[s], kbeg + kk * GBK, col0);
+        issued = kk + 1;
+      }
+      const int first = issued > kGStages ? issued - kGStages : 0;
+      for (int k = first; k < issued; ++k) mbar_wait(&tfull[k % kGStages], (uint32_t)(k / kGStages) & 1u, g.st, 52);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(GBM, GBN);
+      bool done_all = true;
+      for (int kk = 0; kk < nk; ++kk) {
+        const int s = kk % kGStages;
+        const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
+        if (abort_flag || !mbar_wait(&tfull[s], ph, g.st, 53) || !mbar_wait(&gfull[s], ph, g.st, 54)) {
+          abort_flag = 1;
+          done_all = false;
+          break;
+        }
+        tc_fence_after();
+        unsigned char* st = smem + (size_t)s * kGStageBytes;
+        const uint64_t gd = smem_desc_sw128(st);
+        const uint64_t hd = smem_desc_sw128(st + kGTileG);
+        const uint64_t ld = smem_desc_sw128(st + kGTileG + kGTileA);
+#pragma unroll
+        for (int k = 0; k < GBK / 16; ++k) {
+          umma_bf16(tmem, gd + (uint64_t)(k * 2), hd + (uint64_t)(k * 2), idesc, (kk == 0 && k == 0) ? 0u : 1u);
+          umma_bf16(tmem, gd + (uint64_t)(k * 2), ld + (uint64_t)(k * 2), idesc, 1u);
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(&acc_full);  // also after an abort: every issued MMA is tracked
+      if (!done_all) mbar_wait(&acc_full, 0u, g.st, 55);
+    }
+  } else {
+    // ------------------------------------------------------------ G generators, then epilogue
+    const int gtid = threadIdx.x - 64;  // 0..511
+    const int row_base = g.row_base + rloc0;  // global sketch row of tile row 0
+    const int row_end = g.row_base + g.m_add;  // first global row past the new rows
+    const int q0 = row_base >> 2;
+    const int nq = ((row_base + GBM - 1) >> 2) - q0 + 1;
+    bool ok = true;
+    for (int kk = 0; kk < nk && ok; ++kk) {
+      const int s = kk % kGStages;
+      const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
+      const bool got = mbar_wait_warp(&empty[s], ph ^ 1u, g.st, 56);
+      if (!got || __shfl_sync(0xffffffffu, (int)abort_flag, 0)) {
+        if (lane == 0) abort_flag = 1;
+        ok = false;
+        break;
+      }
+      unsigned char* gt = smem + (size_t)s * kGStageBytes;
+      const long long i0 = (long long)kbeg + (long long)kk * GBK;
+      for (int it = gtid; it < nq * GBK; it += kGGenWarps * 32) {
+        const int qi = it >> 6, kc = it & (GBK - 1);
+        const int Q = q0 + qi;
+        const long long i = i0 + kc;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (i < g.n) gauss4_f(g.key, (uint32_t)i, (uint32_t)Q, v);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int R = 4 * Q + t;
+          const int rl = R - row_base;
+          if (rl < 0 || rl >= GBM) continue;
+          const float x = (R < row_end) ? v[t] : 0.f;
+          const uint32_t off = (uint32_t)rl * 128u + ((((uint32_t)kc >> 3) ^ ((uint32_t)rl & 7u)) << 4) +
+                               (((uint32_t)kc & 7u) << 1);
+          *(__nv_bfloat16*)(gt + off) = __float2bfloat16_rn(x);
+        }
+      }
+      fence_proxy_async();  // generic-proxy writes visible to the tensor core
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&gfull[s]);
+    }
+    // epilogue: 16 warps = 4 TMEM lane quadrants x 4 blocks of 64 columns
+    const bool acc_ok = mbar_wait_warp(&acc_full, 0u, g.st, 57);
+    tc_fence_after();
+    const int aborted = __shfl_sync(0xffffffffu, (int)abort_flag, 0);
+    if (acc_ok && ok && !aborted) {
+      const int quad = warp & 3, cb = (warp - 2) >> 2;
+      const int row = quad * 32 + lane;
+      const int r = rloc0 + row;  // row within the m_add new rows
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 64 + h * 16), v);
+        const int c0 = col0 + cb * 64 + h * 16;
+        if (r < g.m_add) {
+          float* dst = g.part + ((size_t)ks * g.m_add + r) * g.d;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < g.d) dst[c0 + j] = v[j];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGTmemCols) : "memory");
+  }
+}
+
+// Y[row0 + r][c] = sum over slices of part[ks][r][c] (fixed order, float64)
+__global__ void gauss_reduce_kernel(const float* __restrict__ part, int ksplits, int m_add, int d,
+                                    float* __restrict__ Y, long long ldy, int row0) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)m_add * d) return;
+  const int r = (int)(e / d), c = (int)(e % d);
+  double t = 0.0;
+  for (int ks = 0; ks < ksplits; ++ks) t += (double)part[((size_t)ks * m_add + r) * d + c];
+  Y[(long long)(row0 + r) * ldy + c] = (float)t;
+}
+
+// Maximum |A[i][c]| of every column of A (n x d), float bits.
+__global__ void colmax_kernel(const float* __restrict__ A, long long lda, long long n, int d, long long rows_per,
+                              unsigned* __restrict__ cmax) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  const long long r0 = (long long)blockIdx.y * rows_per;
+  const long long r1 = min(n, r0 + rows_per);
+  float m = 0.f;
+  for (long long i = r0; i < r1; ++i) m = fmaxf(m, fabsf(A[i * lda + c]));
+  atomicMax(&cmax[c], __float_as_uint(m));
+}
+
+// Row-scaled split of A^T through 32 x 32 shared-memory tiles: out[c][i] for
+// i < Kp (zero past n), hi/lo against the maximum exponent of column c.
+__global__ void split_t_kernel(const float* __restrict__ A, long long lda, long long n, int d, int Kp,
+                               const unsigned* __restrict__ cmax, __nv_bfloat16* __restrict__ Hh,
+                               __nv_bfloat16* __restrict__ Hl) {
+  __shared__ float t[32][33];
+  const long long i0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const long long i = i0 + j;
+    const int c = c0 + threadIdx.x;
+    t[j][threadIdx.x] = (i < n && c < d) ? A[i * lda + c] : 0.f;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = c0 + j;
+    const long long i = i0 + threadIdx.x;
+    if (c >= d || i >= Kp) continue;
+    const float v = t[threadIdx.x][j];
+    const float mx = __uint_as_float(cmax[c]);
+    float h = 0.f, l = 0.f;
+    if (mx > 0.f) {
+      int ex;
+      frexpf(mx, &ex);
+      h = ldexpf(rintf(ldexpf(v, 8 - ex)), ex - 8);
+      l = ldexpf(rintf(ldexpf(v - h, 16 - ex)), ex - 16);
+    }
+    Hh[(size_t)c * Kp + i] = __float2bfloat16_rn(h);
+    Hl[(size_t)c * Kp + i] = __float2bfloat16_rn(l);
+  }
+}
+
 }  // namespace
 
 sks_status tc_unsplit(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, int rows, int cols,
@@ -425,6 +677,77 @@ sks_status tc_gram(cudaStream_t stream, int M, int N, int Kp, const __nv_bfloat1
   tc_gram_kernel<<<tiles, kTcThreads, smem, stream>>>(mAh, mAl, mBh, mBl, g);
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
+}  // namespace sks
+
+namespace sks {
+
+int tc_gauss_kp(long long n) { return (int)((std::max<long long>(n, 1) + GBK - 1) / GBK * GBK); }
+
+size_t tc_gauss_part_elems(long long n, int d, int max_rows) {
+  const int Kp = tc_gauss_kp(n);
+  const int kc = kGaussSlice;
+  const int ksplits = (Kp + kc - 1) / kc;
+  return (size_t)ksplits * (size_t)std::max(1, std::min(max_rows, kGaussRowChunk)) * (size_t)d;
+}
+
+sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long long n, int d, __nv_bfloat16* Hh,
+                      __nv_bfloat16* Hl, unsigned* cmax) {
+  const int Kp = tc_gauss_kp(n);
+  SKS_CUDA_TRY(cudaMemsetAsync(cmax, 0, (size_t)d * sizeof(unsigned), stream));
+  if (n > 0) {
+    const long long chunks = std::min<long long>((n + 1023) / 1024, 1024);
+    const long long per = (n + chunks - 1) / chunks;
+    colmax_kernel<<<dim3((unsigned)((d + 127) / 128), (unsigned)chunks), 128, 0, stream>>>(A, lda, n, d, per, cmax);
+    note_launch();
+  }
+  split_t_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)((d + 31) / 32)), dim3(32, 8), 0, stream>>>(A, lda, n, d, Kp,
+                                                                                                   cmax, Hh, Hl);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
+sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, long long n, int d,
+                           uint64_t seed, int m_off, int m_add, float* part, size_t part_elems, float* Y,
+                           long long ldy, DevStatus* st) {
+  if (m_add <= 0) return SKS_OK;
+  const int Kp = tc_gauss_kp(n);
+  CUtensorMap mh, ml;
+  SKS_TRY(make_tmap_2d_bf16_sw128(&mh, Hh, (uint64_t)d, (uint64_t)Kp, GBK, GBN));
+  SKS_TRY(make_tmap_2d_bf16_sw128(&ml, Hl, (uint64_t)d, (uint64_t)Kp, GBK, GBN));
+  const size_t smem = (size_t)kGStages * kGStageBytes + 1024;
+  SKS_CUDA_TRY(cudaFuncSetAttribute(tc_gauss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int kc = kGaussSlice;
+  const int ksplits = (Kp + kc - 1) / kc;
+  for (int r0 = 0; r0 < m_add; r0 += kGaussRowChunk) {
+    const int rows = std::min(kGaussRowChunk, m_add - r0);
+    if ((size_t)ksplits * rows * d > part_elems) return fail(SKS_ERR_WORKSPACE, "Gaussian sketch partials too small");
+    GaussArgs g;
+    g.d = d;
+    g.m_add = rows;
+    g.row_base = m_off + r0;
+    g.n = n;
+    g.Kp = Kp;
+    g.kc = kc;
+    g.tiles_m = (rows + GBM - 1) / GBM;
+    g.tiles_n = (d + GBN - 1) / GBN;
+    g.ksplits = ksplits;
+    g.key = make_key(seed);
+    g.part = part;
+    g.st = st;
+    const long long blocks = (long long)g.tiles_m * g.tiles_n * ksplits;
+    if (blocks > 0x7fffffffll) return fail(SKS_ERR_UNSUPPORTED, "Gaussian sketch grid too large");
+    tc_gauss_kernel<<<(unsigned)blocks, kGThreads, smem, stream>>>(mh, ml, g);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+    const long long tot = (long long)rows * d;
+    gauss_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, ksplits, rows, d, Y, ldy, m_off + r0);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+  }
   return SKS_OK;
 }
 

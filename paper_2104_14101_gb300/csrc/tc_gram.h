@@ -30,4 +30,20 @@ sks_status tc_gram(cudaStream_t stream, int M, int N, int Kp, const __nv_bfloat1
                    const __nv_bfloat16* Bh, const __nv_bfloat16* Bl, double alpha, double beta, double* C,
                    long long ldc, bool lower, DevStatus* st);
 
+// ---- Gaussian sketch of a float32 A on the tensor cores (K4)
+// Padded K (data rows rounded up to 64) of the split A^T.
+int tc_gauss_kp(long long n);
+// float32 elements of the slice partials for up to max_rows new rows per call.
+size_t tc_gauss_part_elems(long long n, int d, int max_rows);
+// Hh/Hl (d x Kp bfloat16): the row-scaled split of A^T, every column of A
+// against its own maximum exponent; cmax: d scratch words.
+sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long long n, int d, __nv_bfloat16* Hh,
+                      __nv_bfloat16* Hl, unsigned* cmax);
+// Y[m_off .. m_off + m_add) = bf16(G) (Hh + Hl)^T, G[r][i] the Philox /
+// Box-Muller entry of sketch row r and data row i (float32, rounded to
+// bfloat16), generated inside the kernel; unscaled (S A = Y / sqrt(m)).
+sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, long long n, int d,
+                           uint64_t seed, int m_off, int m_add, float* part, size_t part_elems, float* Y,
+                           long long ldy, DevStatus* st);
+
 }  // namespace sks

@@ -367,10 +367,14 @@ __global__ void unsplit_kernel(const __nv_bfloat16* __restrict__ Hh, const __nv_
 //   warps 2-17  generators: the 128 x 64 G tile of the stage from Philox in
 //               registers, rounded to bfloat16 and written in the swizzled
 //               K-major layout the MMA reads (G never goes to global memory);
-//               after the last stage they drain the accumulator to the
-//               slice's float32 partial.
-// Slices of at most 16384 data rows keep the float32 accumulation error near
-// 2^-24 sqrt(16384); the partials are summed in a fixed order in float64.
+//               they also drain the accumulator.
+// The tensor core's float32 accumulation does not round to nearest, so its
+// error grows with the number of MMAs summed into one accumulator: every
+// group of 4 stages (256 data rows, 32 MMAs) goes to one of two TMEM
+// accumulators (ping-pong) and is drained into float32 registers (round to
+// nearest) while the next group runs.  Each K slice of <= 16384 data rows
+// writes a float32 partial; the partials are summed in a fixed order in
+// float64.
 constexpr int GBM = 128, GBN = 256, GBK = 64;
 constexpr int kGStages = 2;
 constexpr int kGTileG = GBM * GBK * 2;                 // 16 KB
@@ -378,7 +382,8 @@ constexpr int kGTileA = GBN * GBK * 2;                 // 32 KB
 constexpr int kGStageBytes = kGTileG + 2 * kGTileA;    // 80 KB
 constexpr int kGGenWarps = 16;
 constexpr int kGThreads = (2 + kGGenWarps) * 32;
-constexpr uint32_t kGTmemCols = 256;
+constexpr uint32_t kGTmemCols = 512;  // two 256-column float32 accumulators
+constexpr int kGDrain = 4;             // stages per accumulator group
 constexpr int kGaussSlice = 16384;    // data rows per K slice
 constexpr int kGaussRowChunk = 4096;  // new sketch rows per launch (bounds the partials)
 
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     tc_gauss_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl, GaussArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t tfull[kGStages], gfull[kGStages], empty[kGStages], acc_full;
+  __shared__ uint64_t tfull[kGStages], gfull[kGStages], empty[kGStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
@@ -417,7 +422,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
       mbar_init(&gfull[s], kGGenWarps);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kGGenWarps);
+    }
     fence_mbar_init();
     fence_proxy_async();
   }
@@ -456,38 +464,77 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(GBM, GBN);
-      bool done_all = true;
-      for (int kk = 0; kk < nk; ++kk) {
-        const int s = kk % kGStages;
-        const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
-        if (abort_flag || !mbar_wait(&tfull[s], ph, g.st, 53) || !mbar_wait(&gfull[s], ph, g.st, 54)) {
+      const int ngroups = (nk + kGDrain - 1) / kGDrain;
+      int committed = -1;
+      for (int grp = 0; grp < ngroups && !abort_flag; ++grp) {
+        const int buf = grp & 1;
+        // the generators have drained this buffer's previous group
+        if (!mbar_wait(&acc_empty[buf], ((uint32_t)(grp >> 1) & 1u) ^ 1u, g.st, 58)) {
           abort_flag = 1;
-          done_all = false;
           break;
         }
         tc_fence_after();
-        unsigned char* st = smem + (size_t)s * kGStageBytes;
-        const uint64_t gd = smem_desc_sw128(st);
-        const uint64_t hd = smem_desc_sw128(st + kGTileG);
-        const uint64_t ld = smem_desc_sw128(st + kGTileG + kGTileA);
+        const uint32_t acc_t = tmem + (uint32_t)(buf * GBN);
+        const int k_end = min(nk, (grp + 1) * kGDrain);
+        for (int kk = grp * kGDrain; kk < k_end; ++kk) {
+          const int s = kk % kGStages;
+          const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
+          if (abort_flag || !mbar_wait(&tfull[s], ph, g.st, 53) || !mbar_wait(&gfull[s], ph, g.st, 54)) {
+            abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          unsigned char* st = smem + (size_t)s * kGStageBytes;
+          const uint64_t gd = smem_desc_sw128(st);
+          const uint64_t hd = smem_desc_sw128(st + kGTileG);
+          const uint64_t ld = smem_desc_sw128(st + kGTileG + kGTileA);
+          const bool first = kk == grp * kGDrain;
 #pragma unroll
-        for (int k = 0; k < GBK / 16; ++k) {
-          umma_bf16(tmem, gd + (uint64_t)(k * 2), hd + (uint64_t)(k * 2), idesc, (kk == 0 && k == 0) ? 0u : 1u);
-          umma_bf16(tmem, gd + (uint64_t)(k * 2), ld + (uint64_t)(k * 2), idesc, 1u);
+          for (int k = 0; k < GBK / 16; ++k) {
+            umma_bf16(acc_t, gd + (uint64_t)(k * 2), hd + (uint64_t)(k * 2), idesc, (first && k == 0) ? 0u : 1u);
+            umma_bf16(acc_t, gd + (uint64_t)(k * 2), ld + (uint64_t)(k * 2), idesc, 1u);
+          }
+          umma_commit(&empty[s]);
         }
-        umma_commit(&empty[s]);
+        if (abort_flag) break;
+        umma_commit(&acc_full[buf]);
+        committed = grp;
       }
-      umma_commit(&acc_full);  // also after an abort: every issued MMA is tracked
-      if (!done_all) mbar_wait(&acc_full, 0u, g.st, 55);
+      // every issued MMA has finished before the TMEM is freed
+      if (committed >= 0) mbar_wait(&acc_full[committed & 1], (uint32_t)(committed >> 1) & 1u, g.st, 55);
     }
   } else {
-    // ------------------------------------------------------------ G generators, then epilogue
+    // ------------------------------------------------------------ G generators and accumulator drains
     const int gtid = threadIdx.x - 64;  // 0..511
     const int row_base = g.row_base + rloc0;  // global sketch row of tile row 0
     const int row_end = g.row_base + g.m_add;  // first global row past the new rows
     const int q0 = row_base >> 2;
     const int nq = ((row_base + GBM - 1) >> 2) - q0 + 1;
+    const int quad = warp & 3, cb = (warp - 2) >> 2;  // TMEM lane quadrant, 64-column block
+    const int ngroups = (nk + kGDrain - 1) / kGDrain;
+    float accr[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) accr[j] = 0.f;
+    int drained = 0;
     bool ok = true;
+    // adds group `drained` (buffer drained & 1) into the registers and frees the buffer
+    auto drain = [&]() -> bool {
+      const int buf = drained & 1;
+      if (!mbar_wait_warp(&acc_full[buf], (uint32_t)(drained >> 1) & 1u, g.st, 57)) return false;
+      tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * GBN + cb * 64 + h * 16), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) accr[h * 16 + j] += v[j];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      ++drained;
+      return true;
+    };
     for (int kk = 0; kk < nk && ok; ++kk) {
       const int s = kk % kGStages;
       const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
@@ -519,26 +566,29 @@ __global__ void __launch_bounds__(kGThreads, 1)
       fence_proxy_async();  // generic-proxy writes visible to the tensor core
       __syncwarp();
       if (lane == 0) mbar_arrive(&gfull[s]);
-    }
-    // epilogue: 16 warps = 4 TMEM lane quadrants x 4 blocks of 64 columns
-    const bool acc_ok = mbar_wait_warp(&acc_full, 0u, g.st, 57);
-    tc_fence_after();
-    const int aborted = __shfl_sync(0xffffffffu, (int)abort_flag, 0);
-    if (acc_ok && ok && !aborted) {
-      const int quad = warp & 3, cb = (warp - 2) >> 2;
-      const int row = quad * 32 + lane;
-      const int r = rloc0 + row;  // row within the m_add new rows
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 64 + h * 16), v);
-        const int c0 = col0 + cb * 64 + h * 16;
-        if (r < g.m_add) {
-          float* dst = g.part + ((size_t)ks * g.m_add + r) * g.d;
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < g.d) dst[c0 + j] = v[j];
+      // once the first stage of a group is queued, drain the previous group
+      if (kk % kGDrain == 0 && kk > 0 && drained < kk / kGDrain) {
+        if (!drain()) {
+          if (lane == 0) abort_flag = 1;
+          ok = false;
         }
+      }
+    }
+    while (ok && drained < ngroups && !__shfl_sync(0xffffffffu, (int)abort_flag, 0)) {
+      if (!drain()) {
+        if (lane == 0) abort_flag = 1;
+        ok = false;
+      }
+    }
+    const int aborted = __shfl_sync(0xffffffffu, (int)abort_flag, 0);
+    if (ok && !aborted) {
+      const int r = rloc0 + quad * 32 + lane;  // row within the m_add new rows
+      if (r < g.m_add) {
+        float* dst = g.part + ((size_t)ks * g.m_add + r) * g.d;
+        const int c0 = col0 + cb * 64;
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+          if (c0 + j < g.d) dst[c0 + j] = accr[j];
       }
     }
   }

@@ -54,6 +54,13 @@ WORKLOADS = {
     "C3-srht": dict(config="C3", method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=8192, tol=1e-8,
                     precision="mixed", compare_plain=True, cpu_rows=1 << 14, ref_rows=1 << 13,
                     desc="C3 with the SRHT for both forms"),
+    # C3 with the Gaussian embedding: bf16 G generated inside the tcgen05 kernel; no float64 comparison
+    # (a float64 Gaussian sketch at m = 8192 is ~70 TFLOP on the float64 pipe)
+    "C3-gauss": dict(config="C3", method="pcg", kind="gaussian", sjlt_s=1, m_init=1, m_max=8192, tol=1e-8,
+                     precision="mixed", cpu_rows=1 << 14, ref_rows=1 << 13,
+                     desc="C3 with the Gaussian embedding (bfloat16 G on tensor cores), mixed form only"),
+    "C3-gauss-profile": dict(config="C3", n=1 << 17, method="pcg", kind="gaussian", sjlt_s=1, m_init=1, m_max=8192,
+                             tol=1e-8, precision="mixed", desc="C3 recipe with the Gaussian embedding at n=2^17"),
     # reduced C3 (n = 2^17, A = 2 GiB float32) for ncu captures of the float32 kernels
     "C3-profile": dict(config="C3", n=1 << 17, method="pcg", kind="sjlt", sjlt_s=4, m_init=1, m_max=8192, tol=1e-8,
                        precision="mixed", desc="C3 recipe at n=2^17 (profiling size)"),

@@ -546,21 +546,25 @@ __global__ void __launch_bounds__(kGThreads, 1)
       }
       unsigned char* gt = smem + (size_t)s * kGStageBytes;
       const long long i0 = (long long)kbeg + (long long)kk * GBK;
-      for (int it = gtid; it < nq * GBK; it += kGGenWarps * 32) {
-        const int qi = it >> 6, kc = it & (GBK - 1);
+      // item = (quad of sketch rows, pair of adjacent data rows): a warp covers
+      // the 64 data rows of one quad and stores whole 128-byte tile rows
+      for (int it = gtid; it < nq * (GBK / 2); it += kGGenWarps * 32) {
+        const int qi = it >> 5, kc = (it & 31) * 2;
         const int Q = q0 + qi;
         const long long i = i0 + kc;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (i < g.n) gauss4_f(g.key, (uint32_t)i, (uint32_t)Q, v);
+        float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
+        if (i < g.n) gauss4_f(g.key, (uint32_t)i, (uint32_t)Q, v0);
+        if (i + 1 < g.n) gauss4_f(g.key, (uint32_t)(i + 1), (uint32_t)Q, v1);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int R = 4 * Q + t;
           const int rl = R - row_base;
           if (rl < 0 || rl >= GBM) continue;
-          const float x = (R < row_end) ? v[t] : 0.f;
+          const bool live = R < row_end;
+          const __nv_bfloat162 x = __floats2bfloat162_rn(live ? v0[t] : 0.f, live ? v1[t] : 0.f);
           const uint32_t off = (uint32_t)rl * 128u + ((((uint32_t)kc >> 3) ^ ((uint32_t)rl & 7u)) << 4) +
                                (((uint32_t)kc & 7u) << 1);
-          *(__nv_bfloat16*)(gt + off) = __float2bfloat16_rn(x);
+          *(__nv_bfloat162*)(gt + off) = x;
         }
       }
       fence_proxy_async();  // generic-proxy writes visible to the tensor core

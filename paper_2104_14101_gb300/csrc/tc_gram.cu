@@ -353,6 +353,78 @@ __global__ void unsplit_kernel(const __nv_bfloat16* __restrict__ Hh, const __nv_
   Y[(long long)r * ldy + c] = v;
 }
 
+// ------------------------------------------------------------------ cluster (distributed shared memory) helpers
+SKS_DEV uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// address of the same shared-memory location in CTA `rank` of the cluster
+SKS_DEV uint32_t mapa_shared(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+SKS_DEV void st_cluster_b32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+SKS_DEV void fence_proxy_async_cluster() { asm volatile("fence.proxy.async.shared::cluster;" ::: "memory"); }
+SKS_DEV void mbar_arrive_remote(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+SKS_DEV bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait with cluster-scope acquire (barriers that other CTAs arrive on)
+SKS_DEV bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, DevStatus* st, int where) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      raise_status(st, SKS_ERR_TIMEOUT, where, 0);
+      return false;
+    }
+  }
+}
+SKS_DEV bool mbar_wait_cluster_warp(uint64_t* bar, uint32_t parity, DevStatus* st, int where) {
+  const int lane = threadIdx.x & 31;
+  uint64_t t0 = 0;
+  while (true) {
+    const bool ok = mbar_try_wait_cluster(bar, parity);
+    if (__all_sync(0xffffffffu, ok)) return true;
+    int to = 0;
+    if (lane == 0) {
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitLimitNs) to = 1;
+    }
+    to = __shfl_sync(0xffffffffu, to, 0);
+    if (to) {
+      if (lane == 0) raise_status(st, SKS_ERR_TIMEOUT, where, 0);
+      return false;
+    }
+  }
+}
+// tcgen05.commit arriving on the same barrier in every CTA of `mask`
+SKS_DEV void umma_commit_multicast(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_addr(bar)),
+      "h"(mask)
+      : "memory");
+}
+SKS_DEV void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ Gaussian sketch on tensor cores
 //
 // K4 for float32 A: Y[r] = sum_i bf16(G[r][i]) (hi + lo)[.][i], i.e. the
@@ -364,10 +436,14 @@ __global__ void unsplit_kernel(const __nv_bfloat16* __restrict__ Hh, const __nv_
 //               swizzle) into a 2-stage ring;
 //   warp 1      MMA issuer: 8 tcgen05.mma (M=128, N=256, K=16) per stage, both
 //               slices into one float32 TMEM accumulator;
-//   warps 2-17  generators: the 128 x 64 G tile of the stage from Philox in
-//               registers, rounded to bfloat16 and written in the swizzled
-//               K-major layout the MMA reads (G never goes to global memory);
-//               they also drain the accumulator.
+//   warps 2-17  generators: 32 rows of the 128 x 64 G tile of the stage
+//               from Philox in registers, rounded to bfloat16 and written in
+//               the swizzled K-major layout the MMA reads into the shared
+//               memory of all 4 CTAs of the cluster (the 4 column tiles that
+//               share the G tile; G never goes to global memory); they also
+//               drain the accumulator.
+// Stage reuse is cluster-wide: every CTA's MMA commit arrives (multicast) on
+// the stage barrier of all 4 CTAs.
 // The tensor core's float32 accumulation does not round to nearest, so its
 // error grows with the number of MMAs summed into one accumulator: every
 // group of 4 stages (256 data rows, 32 MMAs) goes to one of two TMEM
@@ -383,6 +459,7 @@ constexpr int kGStageBytes = kGTileG + 2 * kGTileA;    // 80 KB
 constexpr int kGGenWarps = 16;
 constexpr int kGThreads = (2 + kGGenWarps) * 32;
 constexpr uint32_t kGTmemCols = 512;  // two 256-column float32 accumulators
+constexpr int kGCluster = 4;           // CTAs along the columns sharing every G tile
 constexpr int kGDrain = 4;             // stages per accumulator group
 constexpr int kGaussSlice = 16384;    // data rows per K slice
 constexpr int kGaussRowChunk = 4096;  // new sketch rows per launch (bounds the partials)
@@ -391,13 +468,13 @@ struct GaussArgs {
   int d, m_add, row_base;  // sketch rows [row_base, row_base + m_add)
   long long n;             // data rows
   int Kp, kc;              // padded K; data rows per slice (multiple of 64)
-  int tiles_m, tiles_n, ksplits;
+  int tiles_m, tiles_n, ksplits;  // tiles_n: a multiple of the cluster size
   Key key;
   float* part;             // [ksplits][m_add][d]
   DevStatus* st;
 };
 
-__global__ void __launch_bounds__(kGThreads, 1)
+__global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1)
     tc_gauss_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl, GaussArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -405,9 +482,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
-  const int ks = blockIdx.x % g.ksplits;
-  const int t2 = blockIdx.x / g.ksplits;
-  const int tn = t2 % g.tiles_n, tm = t2 / g.tiles_n;
+  // column tile fastest: the CTAs of a cluster share (row tile, K slice)
+  const int tn = blockIdx.x % g.tiles_n;
+  const int t2 = blockIdx.x / g.tiles_n;
+  const int tm = t2 % g.tiles_m, ks = t2 / g.tiles_m;
+  const uint32_t crank = cluster_rank();
   const int rloc0 = tm * GBM;  // first tile row within the m_add new rows
   const int col0 = tn * GBN;
   const int kbeg = ks * g.kc;
@@ -419,8 +498,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     abort_flag = 0;
     for (int s = 0; s < kGStages; ++s) {
       mbar_init(&tfull[s], 1);
-      mbar_init(&gfull[s], kGGenWarps);
-      mbar_init(&empty[s], 1);
+      mbar_init(&gfull[s], kGGenWarps * kGCluster);  // every generator warp of the cluster
+      mbar_init(&empty[s], kGCluster);                // the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -437,6 +516,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // every CTA's barriers exist before remote arrivals
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
@@ -447,7 +527,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       for (int kk = 0; kk < nk; ++kk) {
         const int s = kk % kGStages;
         const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
-        if (abort_flag || !mbar_wait(&empty[s], ph ^ 1u, g.st, 51)) {
+        if (abort_flag || !mbar_wait_cluster(&empty[s], ph ^ 1u, g.st, 51)) {
           abort_flag = 1;
           break;
         }
@@ -479,7 +559,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         for (int kk = grp * kGDrain; kk < k_end; ++kk) {
           const int s = kk % kGStages;
           const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
-          if (abort_flag || !mbar_wait(&tfull[s], ph, g.st, 53) || !mbar_wait(&gfull[s], ph, g.st, 54)) {
+          if (abort_flag || !mbar_wait(&tfull[s], ph, g.st, 53) || !mbar_wait_cluster(&gfull[s], ph, g.st, 54)) {
             abort_flag = 1;
             break;
           }
@@ -494,7 +574,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             umma_bf16(acc_t, gd + (uint64_t)(k * 2), hd + (uint64_t)(k * 2), idesc, (first && k == 0) ? 0u : 1u);
             umma_bf16(acc_t, gd + (uint64_t)(k * 2), ld + (uint64_t)(k * 2), idesc, 1u);
           }
-          umma_commit(&empty[s]);
+          umma_commit_multicast(&empty[s], (uint16_t)((1u << kGCluster) - 1u));  // stage free in every CTA
         }
         if (abort_flag) break;
         umma_commit(&acc_full[buf]);
@@ -508,8 +588,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int gtid = threadIdx.x - 64;  // 0..511
     const int row_base = g.row_base + rloc0;  // global sketch row of tile row 0
     const int row_end = g.row_base + g.m_add;  // first global row past the new rows
-    const int q0 = row_base >> 2;
-    const int nq = ((row_base + GBM - 1) >> 2) - q0 + 1;
+    // this CTA generates tile rows [32 crank, 32 crank + 32) for the whole cluster
+    constexpr int kRowsPer = GBM / kGCluster;
+    const int rl_lo = (int)crank * kRowsPer;
+    const int q0 = (row_base + rl_lo) >> 2;
+    const int nq = ((row_base + rl_lo + kRowsPer - 1) >> 2) - q0 + 1;
+    uint32_t peer_smem[kGCluster], peer_gfull[kGStages][kGCluster];
+#pragma unroll
+    for (int j = 0; j < kGCluster; ++j) {
+      peer_smem[j] = mapa_shared(smem_addr(smem), (uint32_t)j);
+#pragma unroll
+      for (int s2 = 0; s2 < kGStages; ++s2) peer_gfull[s2][j] = mapa_shared(smem_addr(&gfull[s2]), (uint32_t)j);
+    }
     const int quad = warp & 3, cb = (warp - 2) >> 2;  // TMEM lane quadrant, 64-column block
     const int ngroups = (nk + kGDrain - 1) / kGDrain;
     float accr[64];
@@ -538,16 +628,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
     for (int kk = 0; kk < nk && ok; ++kk) {
       const int s = kk % kGStages;
       const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
-      const bool got = mbar_wait_warp(&empty[s], ph ^ 1u, g.st, 56);
+      // the stage is free in every CTA of the cluster (their MMAs have read it)
+      const bool got = mbar_wait_cluster_warp(&empty[s], ph ^ 1u, g.st, 56);
       if (!got || __shfl_sync(0xffffffffu, (int)abort_flag, 0)) {
         if (lane == 0) abort_flag = 1;
         ok = false;
         break;
       }
-      unsigned char* gt = smem + (size_t)s * kGStageBytes;
+      const uint32_t stage_off = (uint32_t)s * (uint32_t)kGStageBytes;
       const long long i0 = (long long)kbeg + (long long)kk * GBK;
       // item = (quad of sketch rows, pair of adjacent data rows): a warp covers
-      // the 64 data rows of one quad and stores whole 128-byte tile rows
+      // the 64 data rows of one quad and stores whole 128-byte tile rows into
+      // the G tile of every CTA of the cluster
       for (int it = gtid; it < nq * (GBK / 2); it += kGGenWarps * 32) {
         const int qi = it >> 5, kc = (it & 31) * 2;
         const int Q = q0 + qi;
@@ -559,17 +651,22 @@ __global__ void __launch_bounds__(kGThreads, 1)
         for (int t = 0; t < 4; ++t) {
           const int R = 4 * Q + t;
           const int rl = R - row_base;
-          if (rl < 0 || rl >= GBM) continue;
+          if (rl < rl_lo || rl >= rl_lo + kRowsPer) continue;
           const bool live = R < row_end;
           const __nv_bfloat162 x = __floats2bfloat162_rn(live ? v0[t] : 0.f, live ? v1[t] : 0.f);
           const uint32_t off = (uint32_t)rl * 128u + ((((uint32_t)kc >> 3) ^ ((uint32_t)rl & 7u)) << 4) +
                                (((uint32_t)kc & 7u) << 1);
-          *(__nv_bfloat162*)(gt + off) = x;
+          const uint32_t word = *(const uint32_t*)&x;
+#pragma unroll
+          for (int j = 0; j < kGCluster; ++j) st_cluster_b32(peer_smem[j] + stage_off + off, word);
         }
       }
-      fence_proxy_async();  // generic-proxy writes visible to the tensor core
+      fence_proxy_async_cluster();  // generic-proxy writes visible to the tensor cores of the cluster
       __syncwarp();
-      if (lane == 0) mbar_arrive(&gfull[s]);
+      if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < kGCluster; ++j) mbar_arrive_remote(peer_gfull[s][j]);
+      }
       // once the first stage of a group is queued, drain the previous group
       if (kk % kGDrain == 0 && kk > 0 && drained < kk / kGDrain) {
         if (!drain()) {
@@ -598,6 +695,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // no CTA leaves while its peers may still write or arrive into it
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGTmemCols) : "memory");
@@ -787,7 +885,7 @@ sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const _
     g.Kp = Kp;
     g.kc = kc;
     g.tiles_m = (rows + GBM - 1) / GBM;
-    g.tiles_n = (d + GBN - 1) / GBN;
+    g.tiles_n = ((d + GBN - 1) / GBN + kGCluster - 1) / kGCluster * kGCluster;  // whole clusters
     g.ksplits = ksplits;
     g.key = make_key(seed);
     g.part = part;

@@ -421,6 +421,14 @@ SKS_DEV void umma_commit_multicast(uint64_t* bar, uint16_t mask) {
       "h"(mask)
       : "memory");
 }
+// 1-D bulk copy of `bytes` from this CTA's shared memory to a peer's, completing
+// as transaction bytes on the peer's mbarrier (addresses from mapa_shared)
+SKS_DEV void bulk_copy_to_peer(uint32_t dst, const void* src, uint32_t bytes, uint32_t peer_bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "r"(smem_addr(src)), "r"(bytes), "r"(peer_bar)
+      : "memory");
+}
 SKS_DEV void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -438,10 +446,12 @@ SKS_DEV void cluster_sync_all() {
 //               slices into one float32 TMEM accumulator;
 //   warps 2-17  generators: 32 rows of the 128 x 64 G tile of the stage
 //               from Philox in registers, rounded to bfloat16 and written in
-//               the swizzled K-major layout the MMA reads into the shared
-//               memory of all 4 CTAs of the cluster (the 4 column tiles that
-//               share the G tile; G never goes to global memory); they also
-//               drain the accumulator.
+//               the swizzled K-major layout the MMA reads; one thread then
+//               sends these rows (one contiguous 4 KB block) to the other 3
+//               CTAs of the cluster -- the 4 column tiles that share the G
+//               tile -- by bulk copies that complete on their stage barriers
+//               (G never goes to global memory); they also drain the
+//               accumulator.
 // Stage reuse is cluster-wide: every CTA's MMA commit arrives (multicast) on
 // the stage barrier of all 4 CTAs.
 // The tensor core's float32 accumulation does not round to nearest, so its
@@ -498,7 +508,8 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
     abort_flag = 0;
     for (int s = 0; s < kGStages; ++s) {
       mbar_init(&tfull[s], 1);
-      mbar_init(&gfull[s], kGGenWarps * kGCluster);  // every generator warp of the cluster
+      // the local generator warps, plus the peers' rows as transaction bytes
+      mbar_init(&gfull[s], kGGenWarps);
       mbar_init(&empty[s], kGCluster);                // the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
@@ -593,13 +604,8 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
     const int rl_lo = (int)crank * kRowsPer;
     const int q0 = (row_base + rl_lo) >> 2;
     const int nq = ((row_base + rl_lo + kRowsPer - 1) >> 2) - q0 + 1;
-    uint32_t peer_smem[kGCluster], peer_gfull[kGStages][kGCluster];
-#pragma unroll
-    for (int j = 0; j < kGCluster; ++j) {
-      peer_smem[j] = mapa_shared(smem_addr(smem), (uint32_t)j);
-#pragma unroll
-      for (int s2 = 0; s2 < kGStages; ++s2) peer_gfull[s2][j] = mapa_shared(smem_addr(&gfull[s2]), (uint32_t)j);
-    }
+    constexpr uint32_t kRowBytes = kRowsPer * 128;  // this CTA's rows: one contiguous 4 KB block
+    constexpr uint32_t kPeerBytes = (kGCluster - 1) * kRowBytes;
     const int quad = warp & 3, cb = (warp - 2) >> 2;  // TMEM lane quadrant, 64-column block
     const int ngroups = (nk + kGDrain - 1) / kGDrain;
     float accr[64];
@@ -625,21 +631,22 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
       ++drained;
       return true;
     };
-    for (int kk = 0; kk < nk && ok; ++kk) {
+    for (int kk = 0; kk < nk; ++kk) {
       const int s = kk % kGStages;
       const uint32_t ph = (uint32_t)(kk / kGStages) & 1u;
       // the stage is free in every CTA of the cluster (their MMAs have read it)
-      const bool got = mbar_wait_cluster_warp(&empty[s], ph ^ 1u, g.st, 56);
-      if (!got || __shfl_sync(0xffffffffu, (int)abort_flag, 0)) {
+      const bool got = ok && mbar_wait_cluster_warp(&empty[s], ph ^ 1u, g.st, 56);
+      // every generator warp takes the same decision (the named barriers below
+      // need all 16): leave together on any timeout or abort
+      if (named_bar_or(2, kGGenWarps * 32, !got || abort_flag != 0)) {
         if (lane == 0) abort_flag = 1;
         ok = false;
         break;
       }
-      const uint32_t stage_off = (uint32_t)s * (uint32_t)kGStageBytes;
+      unsigned char* gt = smem + (size_t)s * kGStageBytes;
       const long long i0 = (long long)kbeg + (long long)kk * GBK;
       // item = (quad of sketch rows, pair of adjacent data rows): a warp covers
-      // the 64 data rows of one quad and stores whole 128-byte tile rows into
-      // the G tile of every CTA of the cluster
+      // the 64 data rows of one quad and stores whole 128-byte tile rows
       for (int it = gtid; it < nq * (GBK / 2); it += kGGenWarps * 32) {
         const int qi = it >> 5, kc = (it & 31) * 2;
         const int Q = q0 + qi;
@@ -653,19 +660,25 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
           const int rl = R - row_base;
           if (rl < rl_lo || rl >= rl_lo + kRowsPer) continue;
           const bool live = R < row_end;
-          const __nv_bfloat162 x = __floats2bfloat162_rn(live ? v0[t] : 0.f, live ? v1[t] : 0.f);
           const uint32_t off = (uint32_t)rl * 128u + ((((uint32_t)kc >> 3) ^ ((uint32_t)rl & 7u)) << 4) +
                                (((uint32_t)kc & 7u) << 1);
-          const uint32_t word = *(const uint32_t*)&x;
-#pragma unroll
-          for (int j = 0; j < kGCluster; ++j) st_cluster_b32(peer_smem[j] + stage_off + off, word);
+          *(__nv_bfloat162*)(gt + off) = __floats2bfloat162_rn(live ? v0[t] : 0.f, live ? v1[t] : 0.f);
         }
       }
-      fence_proxy_async_cluster();  // generic-proxy writes visible to the tensor cores of the cluster
-      __syncwarp();
-      if (lane == 0) {
+      fence_proxy_async();  // generic-proxy writes visible to the async proxy (MMA, bulk copies)
+      named_bar_sync(1, kGGenWarps * 32);  // this CTA's 32 rows are complete
+      if (gtid == 0) {
+        // the peers' rows arrive as transaction bytes on the local stage barrier
+        mbar_arrive_expect_tx(&gfull[s], kPeerBytes);
+        const unsigned char* mine = gt + (size_t)rl_lo * 128;
 #pragma unroll
-        for (int j = 0; j < kGCluster; ++j) mbar_arrive_remote(peer_gfull[s][j]);
+        for (int j = 1; j < kGCluster; ++j) {
+          const uint32_t peer = (crank + (uint32_t)j) % kGCluster;
+          bulk_copy_to_peer(mapa_shared(smem_addr(mine), peer), mine, kRowBytes,
+                            mapa_shared(smem_addr(&gfull[s]), peer));
+        }
+      } else if (lane == 0) {
+        mbar_arrive(&gfull[s]);
       }
       // once the first stage of a group is queued, drain the previous group
       if (kk % kGDrain == 0 && kk > 0 && drained < kk / kGDrain) {

@@ -159,13 +159,17 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
       }
     }
     __syncthreads();
-    const double piv = L[k][k];
-    for (int i = k + 1 + tid; i < nb; i += blockDim.x) L[i][k] /= piv;
+    const double rpiv = 1.0 / L[k][k];
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) L[i][k] *= rpiv;
     __syncthreads();
-    // trailing update of the lower triangle
-    for (int e = tid; e < (nb - k - 1) * (nb - k - 1); e += blockDim.x) {
-      const int i = k + 1 + e / (nb - k - 1), j = k + 1 + e % (nb - k - 1);
-      if (j <= i) L[i][j] -= L[i][k] * L[j][k];
+    // trailing update of the lower triangle: thread (ty, tx) of a 16 x 16
+    // layout takes rows k+1+ty+16a and columns k+1+tx+16b (no index division)
+    {
+      const int ty = tid >> 4, tx = tid & 15;
+      for (int i = k + 1 + ty; i < nb; i += 16) {
+        const double lik = L[i][k];
+        for (int j = k + 1 + tx; j <= i; j += 16) L[i][j] -= lik * L[j][k];
+      }
     }
     __syncthreads();
   }
@@ -176,6 +180,9 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
   for (int e = tid; e < NB * NB; e += blockDim.x) X[e / NB][e % NB] = 0.0;
   __syncthreads();
   const int jj = tid & (NB - 1), pp = tid >> 6;
+  __shared__ double rdiag[NB];
+  if (tid < NB) rdiag[tid] = 1.0 / L[tid][tid];
+  __syncthreads();
   for (int i = 0; i < NB; ++i) {
     double acc = 0.0;
     if (jj < i)
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
     part[pp][jj] = acc;
     __syncthreads();
     if (tid < NB) {
-      const double inv = 1.0 / L[i][i];
+      const double inv = rdiag[i];
       if (tid < i) X[i][tid] = -((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) * inv;
       else if (tid == i) X[i][i] = inv;
     }

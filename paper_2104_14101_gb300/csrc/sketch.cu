@@ -222,11 +222,10 @@ __global__ void __launch_bounds__(256) sjlt_scatter_kernel(const TA* __restrict_
 // rows, so it accumulates without atomics.  The hashes of 256 rows at a time
 // are formed once into shared memory; the partial rows are flushed with one
 // (vector) atomic per entry at the end.
-template <typename T>
+template <typename T, int VEC>
 struct SjVec;
 template <>
-struct SjVec<float> {
-  static constexpr int N = 4;
+struct SjVec<float, 4> {
   using V = float4;
   static SKS_DEV V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static SKS_DEV void axpy(V& y, float w, const V& x) {
@@ -238,8 +237,24 @@ struct SjVec<float> {
   static SKS_DEV void flush(float* dst, const V& v) { atomicAdd((float4*)dst, v); }
 };
 template <>
-struct SjVec<double> {
-  static constexpr int N = 2;
+struct SjVec<float, 2> {
+  using V = float2;
+  static SKS_DEV V zero() { return make_float2(0.f, 0.f); }
+  static SKS_DEV void axpy(V& y, float w, const V& x) {
+    y.x += w * x.x;
+    y.y += w * x.y;
+  }
+  static SKS_DEV void flush(float* dst, const V& v) { atomicAdd((float2*)dst, v); }
+};
+template <>
+struct SjVec<float, 1> {
+  using V = float;
+  static SKS_DEV V zero() { return 0.f; }
+  static SKS_DEV void axpy(V& y, float w, const V& x) { y += w * x; }
+  static SKS_DEV void flush(float* dst, const V& v) { atomicAdd(dst, v); }
+};
+template <>
+struct SjVec<double, 2> {
   using V = double2;
   static SKS_DEV V zero() { return make_double2(0.0, 0.0); }
   static SKS_DEV void axpy(V& y, double w, const V& x) {
@@ -251,17 +266,29 @@ struct SjVec<double> {
     atomicAdd(dst + 1, v.y);
   }
 };
+template <>
+struct SjVec<double, 1> {
+  using V = double;
+  static SKS_DEV V zero() { return 0.0; }
+  static SKS_DEV void axpy(V& y, double w, const V& x) { y += w * x; }
+  static SKS_DEV void flush(double* dst, const V& v) { atomicAdd(dst, v); }
+};
 
 constexpr int kSjBlockThreads = 256;
 
-template <typename T>
+// Small and medium sketches: the CTA owns a block of 256 * VEC columns and a
+// contiguous chunk of data rows; thread t owns columns [t * VEC, t * VEC + VEC)
+// of every one of the m partial rows (shared memory), so it accumulates
+// without atomics.  The hashes of 256 rows at a time are formed once into
+// shared memory; the partial rows are flushed with one (vector) atomic per
+// entry at the end.  VEC shrinks as m grows so that m partial rows fit.
+template <typename T, int VEC>
 __global__ void __launch_bounds__(kSjBlockThreads) sjlt_block_kernel(const T* __restrict__ A, long long lda, int64_t n,
                                                                     int d, uint32_t m, int s_eff, Key key,
                                                                     T* __restrict__ Y, long long ldy, int ncb,
                                                                     int64_t rows_per_cta) {
-  using SV = SjVec<T>;
+  using SV = SjVec<T, VEC>;
   using V = typename SV::V;
-  constexpr int VEC = SV::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* Ys = (V*)smem_raw;                                                   // [m][256]
   uint32_t* hrow = (uint32_t*)(Ys + (size_t)m * kSjBlockThreads);          // [256][s_eff]
@@ -289,7 +316,7 @@ __global__ void __launch_bounds__(kSjBlockThreads) sjlt_block_kernel(const T* __
     const int cnt = (int)min((int64_t)kSjBlockThreads, r1 - base);
     if (!cok) continue;
     const T* a = A + base * lda + c;
-#pragma unroll 4
+#pragma unroll 8
     for (int j = 0; j < cnt; ++j) {
       const V v = *(const V*)(a + (int64_t)j * lda);
       for (int k = 0; k < s_eff; ++k) {
@@ -300,6 +327,24 @@ __global__ void __launch_bounds__(kSjBlockThreads) sjlt_block_kernel(const T* __
   }
   if (!cok) return;
   for (uint32_t h = 0; h < m; ++h) SV::flush(Y + (long long)h * ldy + c, Ys[(size_t)h * kSjBlockThreads + tid]);
+}
+
+template <typename T, int VEC>
+sks_status sjlt_block_launch(cudaStream_t stream, const T* A, long long lda, int64_t n, int d, int m, int s_eff,
+                             uint64_t seed, T* Y, long long ldy, size_t smem) {
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int ncb = (d + kSjBlockThreads * VEC - 1) / (kSjBlockThreads * VEC);
+  const int per_sm = smem <= 100 * 1024 ? 2 : 1;
+  const int64_t chunks =
+      std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ((int64_t)sms * 4 * per_sm + ncb - 1) / ncb));
+  const int64_t per = (n + chunks - 1) / chunks;
+  auto kern = sjlt_block_kernel<T, VEC>;
+  SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)(chunks * ncb), kSjBlockThreads, smem, stream>>>(A, lda, n, d, (uint32_t)m, s_eff, make_key(seed),
+                                                                    Y, ldy, ncb, per);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
 }
 
 }  // namespace
@@ -398,23 +443,23 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
   if (n == 0) return SKS_OK;
   const int s_eff = std::min(s, m);
   if (s_eff > kSjltMaxS) return fail(SKS_ERR_UNSUPPORTED, "SJLT s > 16");
-  // small m: column-block kernel (rows of A read as 16-byte vectors, partial
-  // rows in shared memory, no atomics but the final flush)
-  constexpr int VEC = 16 / sizeof(TY);
-  const size_t blk_bytes = (size_t)m * kSjBlockThreads * 16 + (size_t)kSjBlockThreads * s_eff * 8;
-  if (std::is_same<TA, TY>::value && blk_bytes <= 64 * 1024 && d % VEC == 0 && lda % VEC == 0 && ldy % VEC == 0 &&
-      ((uintptr_t)A & 15) == 0 && ((uintptr_t)Y & 15) == 0) {
-    const int sms = device_info().sms > 0 ? device_info().sms : 152;
-    const int ncb = (d + kSjBlockThreads * VEC - 1) / (kSjBlockThreads * VEC);
-    const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ((int64_t)sms * 8 + ncb - 1) / ncb));
-    const int64_t per = (n + chunks - 1) / chunks;
-    auto kern = sjlt_block_kernel<TY>;
-    SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_bytes));
-    kern<<<(unsigned)(chunks * ncb), kSjBlockThreads, blk_bytes, stream>>>((const TY*)A, lda, n, d, (uint32_t)m, s_eff,
-                                                                          make_key(seed), Y, ldy, ncb, per);
-    note_launch();
-    SKS_CUDA_TRY(cudaGetLastError());
-    return SKS_OK;
+  // small and medium m: column-block kernel (partial rows in shared memory);
+  // the widest column vector whose m partial rows fit in 200 KB
+  if constexpr (std::is_same<TA, TY>::value) {
+    const size_t hash_bytes = (size_t)kSjBlockThreads * s_eff * 8;
+    const bool al16 = ((uintptr_t)A & 15) == 0 && ((uintptr_t)Y & 15) == 0;
+    const TY* At = (const TY*)A;
+    constexpr size_t kMax = 200 * 1024;
+    auto fits = [&](int vec) {
+      return (size_t)m * kSjBlockThreads * vec * sizeof(TY) + hash_bytes <= kMax && d % vec == 0 &&
+             lda % vec == 0 && ldy % vec == 0 && (vec == 1 || al16);
+    };
+    auto bytes = [&](int vec) { return (size_t)m * kSjBlockThreads * vec * sizeof(TY) + hash_bytes; };
+    if constexpr (sizeof(TY) == 4) {
+      if (fits(4)) return sjlt_block_launch<TY, 4>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(4));
+    }
+    if (fits(2)) return sjlt_block_launch<TY, 2>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(2));
+    if (fits(1)) return sjlt_block_launch<TY, 1>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(1));
   }
   const long long row_blocks = (n + 7) / 8;
   const long long blocks = row_blocks * ((d + kSjltCols - 1) / kSjltCols);

@@ -455,11 +455,14 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
              lda % vec == 0 && ldy % vec == 0 && (vec == 1 || al16);
     };
     auto bytes = [&](int vec) { return (size_t)m * kSjBlockThreads * vec * sizeof(TY) + hash_bytes; };
+    // 16-byte columns only: narrower ones keep too few bytes in flight at one
+    // CTA per SM, and the L2 scatter is faster there
     if constexpr (sizeof(TY) == 4) {
       if (fits(4)) return sjlt_block_launch<TY, 4>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(4));
+    } else {
+      if (fits(2)) return sjlt_block_launch<TY, 2>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(2));
     }
-    if (fits(2)) return sjlt_block_launch<TY, 2>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(2));
-    if (fits(1)) return sjlt_block_launch<TY, 1>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(1));
+    if (m <= 2 && fits(1)) return sjlt_block_launch<TY, 1>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(1));
   }
   const long long row_blocks = (n + 7) / 8;
   const long long blocks = row_blocks * ((d + kSjltCols - 1) / kSjltCols);

@@ -204,6 +204,76 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
   }
 }
 
+// T[i][j] -= sum_k P[i][k] P[j][k] for the lower 64 x 64 tiles of T (rest x
+// rest), K = kk <= 64, in double-float arithmetic (float32 pairs, ~2^-44
+// relative): products by TwoProd with the cross terms, sums by Knuth's
+// TwoSum.  Storage stays float64; the arithmetic runs on the float32 pipe,
+// which on this part is ~60x the float64 pipe.
+__global__ void __launch_bounds__(256) syrk_df32_lower_kernel(int rest, int kk, const double* __restrict__ P,
+                                                             long long ldp, double* __restrict__ T, long long ldt) {
+  extern __shared__ float sy_smem[];  // Ah, Al, Bh, Bl: [row][k], rows padded to 65
+  float (*Ah)[NB + 1] = (float (*)[NB + 1])sy_smem;
+  float (*Al)[NB + 1] = Ah + NB;
+  float (*Bh)[NB + 1] = Al + NB;
+  float (*Bl)[NB + 1] = Bh + NB;
+  int ti = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
+  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
+  const int tj = (int)blockIdx.x - ti * (ti + 1) / 2;
+  const int i0 = ti * NB, j0 = tj * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, k = e % NB;
+    double a = 0.0, b = 0.0;
+    if (k < kk) {
+      if (i0 + r < rest) a = P[(long long)(i0 + r) * ldp + k];
+      if (j0 + r < rest) b = P[(long long)(j0 + r) * ldp + k];
+    }
+    const float ah = (float)a, bh = (float)b;
+    Ah[r][k] = ah;
+    Al[r][k] = (float)(a - (double)ah);
+    Bh[r][k] = bh;
+    Bl[r][k] = (float)(b - (double)bh);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
+  for (int k = 0; k < kk; ++k) {
+    float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ah[a] = Ah[ty * 4 + a][k];
+      al[a] = Al[ty * 4 + a][k];
+      bh[a] = Bh[tx * 4 + a][k];
+      bl[a] = Bl[tx * 4 + a][k];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float p = ah[a] * bh[b];
+        float e = fmaf(ah[a], bh[b], -p);
+        e = fmaf(ah[a], bl[b], e);
+        e = fmaf(al[a], bh[b], e);
+        const float s = sh[a][b] + p;
+        const float bp = s - sh[a][b];
+        const float t = (sh[a][b] - (s - bp)) + (p - bp);
+        sh[a][b] = s;
+        sl[a][b] += t + e;
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gi = i0 + ty * 4 + a, gj = j0 + tx * 4 + b;
+      if (gi < rest && gj < rest && gj <= gi) T[(long long)gi * ldt + gj] -= (double)sh[a][b] + (double)sl[a][b];
+    }
+}
+
 template <typename T>
 __global__ void transpose_kernel(int rows, int cols, const T* __restrict__ S, long long lds, T* __restrict__ D,
                                  long long ldd) {
@@ -364,7 +434,7 @@ size_t cholesky_ws_elems(int n) {
 // In-place blocked right-looking Cholesky H = L L^T (lower; upper set to 0),
 // then X = L^{-1} by recursive block inversion.  ws: cholesky_ws_elems(n).
 sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long ldh, double* X, long long ldx,
-                                double* ws, DevStatus* st, float* ws32) {
+                                double* ws, DevStatus* st, float* ws32, bool df32_update) {
   if (n <= 0) return SKS_OK;
   const int nblk = (n + NB - 1) / NB;
   double* dinv = ws;                              // nblk * NB * NB
@@ -387,8 +457,18 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
                                      cudaMemcpyDeviceToDevice, stream));
       // trailing lower update  T <- T - P P^T
       double* T = H + (long long)(k0 + nb) * ldh + (k0 + nb);
-      SKS_TRY(gemm<double>(stream, rest, rest, nb, P, ldh, false, P, ldh, true, T, ldh, -1.0, 1.0, true, 1, 0, 0, 0,
-                           nullptr, 0));
+      if (df32_update) {
+        const int tb = (rest + NB - 1) / NB;
+        constexpr size_t kSySmem = 4 * NB * (NB + 1) * sizeof(float);
+        SKS_CUDA_TRY(cudaFuncSetAttribute(syrk_df32_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSySmem));
+        syrk_df32_lower_kernel<<<(unsigned)(tb * (tb + 1) / 2), 256, kSySmem, stream>>>(rest, nb, P, ldh, T, ldh);
+        note_launch();
+        SKS_CUDA_TRY(cudaGetLastError());
+      } else {
+        SKS_TRY(gemm<double>(stream, rest, rest, nb, P, ldh, false, P, ldh, true, T, ldh, -1.0, 1.0, true, 1, 0, 0, 0,
+                             nullptr, 0));
+      }
     }
   }
   // H now holds L in its lower triangle (the strict upper triangle outside the

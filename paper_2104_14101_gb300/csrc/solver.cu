@@ -358,7 +358,8 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
     SKS_TRY(add_diagonal(stream, d, P->H, d, 0.0, lam, P->nu2));
     // Cholesky form: the apply is X^T X, positive definite for any nonsingular
     // X, so the inverse factor may be formed in float32 (mixed form).
-    SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st, P->inv32));
+    // the mixed form factors with double-float trailing updates (inv32 marks it)
+    SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st, P->inv32, P->inv32 != nullptr));
     SKS_TRY(transpose<double>(stream, d, d, P->X, d, P->Xt, d));
   } else {
     if (tc) {
@@ -379,7 +380,7 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
     SKS_TRY(add_diagonal(stream, m, P->H, m, P->nu2, nullptr, 0.0));
     // Woodbury form: the apply subtracts two terms of size ~1/nu^2, so W^{-1}
     // must be accurate: float64 inverse.
-    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st, nullptr));
+    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st, nullptr, P->inv32 != nullptr));
     SKS_TRY(transpose<double>(stream, m, m, P->X, m, P->Xt, m));
     SKS_TRY(transpose<double>(stream, m, d, Y64, ldy, P->Yt, m));
   }

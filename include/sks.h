@@ -297,6 +297,19 @@ sks_status sks_solve_batched(const sks_problem* probs, int count, const sks_opts
                              sks_stats* stats, sks_batch_info* info, int rows_per_unit, void* ws, size_t ws_bytes,
                              void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Self-test of the failure path (the paper has no counterpart).  Every
+ * device-side wait of the library (mbarrier phases of the tensor-copy and
+ * tensor-core pipelines) is bounded; a wait that runs out records
+ * SKS_ERR_TIMEOUT in a device status word, the kernel leaves, and the call
+ * returns the status -- no trap, and the context stays usable.  This entry
+ * point launches one kernel whose wait can never complete (nothing arrives on
+ * its mbarrier) with a limit of limit_ns nanoseconds (1e3 .. 1e9), so the
+ * expected return is SKS_ERR_TIMEOUT with sks_last_error() naming site 99;
+ * SKS_ERR_INVALID_ARG for a limit out of range.  Synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+sks_status sks_selftest_wait_timeout(int64_t limit_ns, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,7 @@ _SIGS = {
                                          C.c_void_p]),
     "sks_adjoint": (C.c_int, [P(Problem), P(Opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                               P(C.c_double), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sks_selftest_wait_timeout": (C.c_int, [C.c_int64, C.c_void_p]),
     "sks_batch_workspace_size": (C.c_int, [P(Problem), C.c_int, P(Opts), P(C.c_size_t)]),
     "sks_solve_batched": (C.c_int, [P(Problem), C.c_int, P(Opts), P(C.c_void_p), P(Stats), P(BatchInfo), C.c_int,
                                     C.c_void_p, C.c_size_t, C.c_void_p]),

@@ -64,3 +64,7 @@ extern "C" sks_status sks_solve_batched(const sks_problem* probs, int count, con
                                         size_t ws_bytes, void* stream) {
   return solve_batched(probs, count, o, x, stats, info, rows_per_unit, ws, ws_bytes, (cudaStream_t)stream);
 }
+
+extern "C" sks_status sks_selftest_wait_timeout(int64_t limit_ns, void* stream) {
+  return selftest_wait_timeout((long long)limit_ns, (cudaStream_t)stream);
+}

@@ -223,12 +223,12 @@ SKS_DEV uint64_t global_ns() {
 // Bounded wait: returns false (and raises SKS_ERR_TIMEOUT) once `limit_ns`
 // nanoseconds have passed without the phase completing.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
-SKS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st, int where) {
+SKS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st, int where, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) {
+    if (global_ns() - t0 > limit_ns) {
       raise_status(st, SKS_ERR_TIMEOUT, where, 0);
       return false;
     }

@@ -100,4 +100,32 @@ sks_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType 
   return SKS_OK;
 }
 
+// ---------------------------------------------------------------- failure-path self-test
+namespace {
+__device__ DevStatus g_selftest_status;
+
+// One thread waits on an mbarrier that nothing ever arrives on; the bounded
+// wait gives up after limit_ns and records SKS_ERR_TIMEOUT.
+__global__ void selftest_wait_kernel(DevStatus* st, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0u, st, 99, limit_ns);
+}
+}  // namespace
+
+sks_status selftest_wait_timeout(long long limit_ns, cudaStream_t stream) {
+  if (limit_ns < 1000 || limit_ns > 1000000000ll) return fail(SKS_ERR_INVALID_ARG, "limit_ns must be in [1e3, 1e9]");
+  DevStatus* st = nullptr;
+  SKS_CUDA_TRY(cudaGetSymbolAddress((void**)&st, g_selftest_status));
+  SKS_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), stream));
+  selftest_wait_kernel<<<1, 32, 0, stream>>>(st, (uint64_t)limit_ns);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return read_status(st, stream, "self-test wait");
+}
+
 }  // namespace sks

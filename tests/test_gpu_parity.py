@@ -449,3 +449,21 @@ def test_adjoint_requires_a_solved_workspace():
     from paper_2104_14101_gb300._lib import SksError
     with pytest.raises(SksError):
         solver.adjoint(dev(np.zeros(32)), dev(np.ones(32)))
+
+
+# ----------------------------------------------------------------------------- failure path
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    # a device wait that can never complete gives up after 20 ms with
+    # SKS_ERR_TIMEOUT; the next call on the same context works
+    from paper_2104_14101_gb300 import _lib
+    lib = _lib.load()
+    stream = api().api._stream()
+    assert lib.sks_selftest_wait_timeout(20_000_000, stream) == _lib.ERR_TIMEOUT
+    assert b"site 99" in lib.sks_last_error()
+    assert lib.sks_selftest_wait_timeout(10, stream) == _lib.ERR_INVALID_ARG
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((300, 20))
+    x = rng.standard_normal(20)
+    got = host(api().hess_apply(dev(A), dev(x), 0.5, dev(np.ones(20))))
+    assert np.allclose(got, O.hess_apply(A, 0.5, np.ones(20), x), rtol=1e-12)

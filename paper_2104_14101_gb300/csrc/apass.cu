@@ -14,6 +14,7 @@
 // Rows and columns past the edge of A are zero-filled by the tensor copy, so
 // there is no tail handling in the inner loop.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -242,8 +243,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
     bool stop = false;
     for (int j0 = 0; j0 < rg; j0 += kRC) {
       // partial dots: one chain per column vector for a single right-hand
-      // side (kRC * QMAX independent chains), one per (row, column) otherwise
-      constexpr int QD = K == 1 ? QMAX : 1;
+      // side (kRC * QMAX independent chains), one per (row, column) otherwise;
+      // float64 keeps one chain per row (bound by the float64 pipe, where the
+      // extra adds of the split would cost more than the latency it hides)
+      constexpr int QD = (K == 1 && !std::is_same<TX, double>::value) ? QMAX : 1;
       TX dq[kRC][QD][K];
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {

@@ -204,6 +204,135 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
   }
 }
 
+// One step of the blocked factorisation with the panel fused in: every CTA
+// factors the nb x nb diagonal block (float64, in shared memory) and forms its
+// inverse; CTA 0 writes L_kk (to Lout, NB x NB: the block in H is still being
+// read by the other CTAs; the caller copies it back after the kernel) and
+// L_kk^{-1}; CTA b >= 1 replaces its 64 rows of the panel below the block by
+// P L_kk^{-T} in double-float arithmetic.  The diagonal work is repeated per
+// CTA so that no launch waits for another.
+__global__ void __launch_bounds__(256) potrf_panel_kernel(double* H, long long ldh, int n, int k0, int nb,
+                                                         double* Dinv, double* Lout, DevStatus* st) {
+  extern __shared__ double pp_smem[];
+  double (*L)[NB + 1] = (double (*)[NB + 1])pp_smem;  // diagonal block, later P hi/lo (floats)
+  double (*X)[NB + 1] = L + NB;                       // L^{-1}
+  float (*Xh)[NB + 1] = (float (*)[NB + 1])(X + NB);
+  float (*Xl)[NB + 1] = Xh + NB;
+  __shared__ double part[4][NB];
+  __shared__ double rdiag[NB];
+  const int tid = threadIdx.x;
+  double* D = H + (long long)k0 * ldh + k0;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, j = e % NB;
+    L[i][j] = (i < nb && j < nb && j <= i) ? D[(long long)i * ldh + j] : (i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      const double p = L[k][k];
+      if (!(p > 0.0) || !isfinite(p)) {
+        if (blockIdx.x == 0) raise_status(st, SKS_ERR_NOT_PD, 21, k0 + k);
+        L[k][k] = 1.0;
+      } else {
+        L[k][k] = sqrt(p);
+      }
+    }
+    __syncthreads();
+    const double rpiv = 1.0 / L[k][k];
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) L[i][k] *= rpiv;
+    __syncthreads();
+    {
+      const int ty = tid >> 4, tx = tid & 15;
+      for (int i = k + 1 + ty; i < nb; i += 16) {
+        const double lik = L[i][k];
+        for (int j = k + 1 + tx; j <= i; j += 16) L[i][j] -= lik * L[j][k];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < NB * NB; e += blockDim.x) X[e / NB][e % NB] = 0.0;
+  if (tid < NB) rdiag[tid] = 1.0 / L[tid][tid];
+  __syncthreads();
+  {
+    const int jj = tid & (NB - 1), pq = tid >> 6;
+    for (int i = 0; i < NB; ++i) {
+      double acc = 0.0;
+      if (jj < i)
+        for (int q = jj + pq; q < i; q += 4) acc += L[i][q] * X[q][jj];
+      part[pq][jj] = acc;
+      __syncthreads();
+      if (tid < NB) {
+        const double inv = rdiag[i];
+        if (tid < i) X[i][tid] = -((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) * inv;
+        else if (tid == i) X[i][i] = inv;
+      }
+      __syncthreads();
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+      const int i = e / nb, j = e % nb;
+      Lout[(long long)i * NB + j] = j <= i ? L[i][j] : 0.0;
+      Dinv[(long long)i * NB + j] = X[i][j];
+    }
+    return;
+  }
+  // panel rows of this CTA: P <- P X^T, X = L_kk^{-1} (lower), double-float
+  const int r0 = k0 + nb + ((int)blockIdx.x - 1) * NB;
+  const int rows = min(NB, n - r0);
+  float (*Ph)[NB + 1] = (float (*)[NB + 1])L;  // the diagonal block is no longer needed
+  float (*Pl)[NB + 1] = Ph + NB;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, q = e % NB;
+    const double x = X[r][q];
+    const float xh = (float)x;
+    Xh[r][q] = xh;
+    Xl[r][q] = (float)(x - (double)xh);
+    const double pv = (r < rows && q < nb) ? H[(long long)(r0 + r) * ldh + k0 + q] : 0.0;
+    const float ph = (float)pv;
+    Ph[r][q] = ph;
+    Pl[r][q] = (float)(pv - (double)ph);
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
+  for (int q = 0; q < nb; ++q) {
+    float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ah[a] = Ph[ty * 4 + a][q];
+      al[a] = Pl[ty * 4 + a][q];
+      bh[a] = Xh[tx * 4 + a][q];
+      bl[a] = Xl[tx * 4 + a][q];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float p = ah[a] * bh[b];
+        float e = fmaf(ah[a], bh[b], -p);
+        e = fmaf(ah[a], bl[b], e);
+        e = fmaf(al[a], bh[b], e);
+        const float s2 = sh[a][b] + p;
+        const float bp = s2 - sh[a][b];
+        const float t = (sh[a][b] - (s2 - bp)) + (p - bp);
+        sh[a][b] = s2;
+        sl[a][b] += t + e;
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty * 4 + a, j = tx * 4 + b;
+      if (r < rows && j < nb) H[(long long)(r0 + r) * ldh + k0 + j] = (double)sh[a][b] + (double)sl[a][b];
+    }
+}
+
 // T[i][j] -= sum_k P[i][k] P[j][k] for the lower 64 x 64 tiles of T (rest x
 // rest), K = kk <= 64, in double-float arithmetic (float32 pairs, ~2^-44
 // relative): products by TwoProd with the cross terms, sums by Knuth's
@@ -440,10 +569,37 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
   double* dinv = ws;                              // nblk * NB * NB
   double* split = ws + (size_t)nblk * NB * NB;    // scratch for split-K
   const size_t split_elems = (size_t)8 * n * NB + (size_t)n * n;
+  constexpr size_t kPanelSmem = 2 * NB * (NB + 1) * sizeof(double) + 2 * NB * (NB + 1) * sizeof(float);
+  if (df32_update)
+    SKS_CUDA_TRY(cudaFuncSetAttribute(potrf_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kPanelSmem));
   for (int kb = 0; kb < nblk; ++kb) {
     const int k0 = kb * NB, nb = std::min(NB, n - k0);
     double* Dk = H + (long long)k0 * ldh + k0;
     double* Dinv = dinv + (size_t)kb * NB * NB;
+    if (df32_update) {
+      // diagonal block and panel in one launch, then the double-float trailing update
+      const int rest = n - k0 - nb;
+      const int pb = (rest + NB - 1) / NB;
+      double* Lk = split;  // NB x NB scratch: the factored block, copied into H after the kernel
+      potrf_panel_kernel<<<1 + pb, 256, kPanelSmem, stream>>>(H, ldh, n, k0, nb, Dinv, Lk, st);
+      note_launch();
+      SKS_CUDA_TRY(cudaGetLastError());
+      SKS_CUDA_TRY(cudaMemcpy2DAsync(Dk, ldh * sizeof(double), Lk, NB * sizeof(double), nb * sizeof(double), nb,
+                                     cudaMemcpyDeviceToDevice, stream));
+      if (rest > 0) {
+        double* P = H + (long long)(k0 + nb) * ldh + k0;
+        double* T = H + (long long)(k0 + nb) * ldh + (k0 + nb);
+        const int tb = (rest + NB - 1) / NB;
+        constexpr size_t kSySmem = 4 * NB * (NB + 1) * sizeof(float);
+        SKS_CUDA_TRY(cudaFuncSetAttribute(syrk_df32_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSySmem));
+        syrk_df32_lower_kernel<<<(unsigned)(tb * (tb + 1) / 2), 256, kSySmem, stream>>>(rest, nb, P, ldh, T, ldh);
+        note_launch();
+        SKS_CUDA_TRY(cudaGetLastError());
+      }
+      continue;
+    }
     potrf_diag_kernel<<<1, 256, 0, stream>>>(Dk, ldh, nb, Dinv, k0, st);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());

@@ -423,6 +423,18 @@ __device__ double block_dot(int d, const double* a, const double* b) {
 }
 
 // PCG, first half of a step: alpha = delta~_t / p^T H p, x+ = x + alpha p, r+ = r - alpha H p.
+// *flag = 1 if any x[j] != 0 (one CTA)
+__global__ void any_nonzero_kernel(int d, const double* __restrict__ x, int* flag) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) mine |= (x[j] != 0.0) ? 1 : 0;
+  if (mine) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = any;
+}
+
 __global__ void __launch_bounds__(kStepThreads) pcg_step1_kernel(int d, const double* x, const double* r,
                                                                  const double* p, const double* Hp, double* xp,
                                                                  double* rp, Ctl* ctl) {
@@ -981,9 +993,24 @@ sks_status solve_columns(Engine& E, const double* B, double* X_io) {
       // solve of H dx = r in the precision of A, x += dx.
       SKS_CUDA_TRY(cudaMemcpyAsync(E.W.xo, xcol, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
       int64_t inner_budget = o->max_iter;
+      // x_0 = 0 (the usual start): r = b exactly, without a pass over A
+      bool x0_zero = false;
+      {
+        int* flag = (int*)(E.W.scal + 3);
+        any_nonzero_kernel<<<1, 256, 0, stream>>>(d, E.W.xo, flag);
+        note_launch();
+        int h_flag = 1;
+        SKS_CUDA_TRY(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+        x0_zero = h_flag == 0;
+      }
       for (int64_t k = 0; k < o->max_outer; ++k) {
         E.outer = (int)k + 1;
-        SKS_TRY(E.hess64(E.W.xo, E.W.bo, -1.0, b, 1.0));
+        if (k == 0 && x0_zero) {
+          SKS_CUDA_TRY(cudaMemcpyAsync(E.W.bo, b, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+        } else {
+          SKS_TRY(E.hess64(E.W.xo, E.W.bo, -1.0, b, 1.0));
+        }
         dot_kernel<<<1, kStepThreads, 0, stream>>>(d, b, E.W.xo, E.W.scal);
         note_launch();
         bool inner_conv = false, done = false;

@@ -138,6 +138,52 @@ constexpr int NB = 64;
 // Factor the nb x nb diagonal block D (leading dim ld) in place (lower) and
 // write the inverse of its factor to Dinv (nb x nb, ld nb).  Raises NOT_PD on
 // a pivot <= 0 or non-finite.  One CTA of 256 threads.
+// 1/sqrt(p) for p > 0 in float64: float32 seed, two Newton steps
+// (r <- r (3 - p r^2) / 2; relative error ~1e-7 -> ~1e-14 -> below 1 ulp)
+SKS_DEV double rsqrt_newton(double p) {
+  if (!(p > 1e-30 && p < 1e30)) return 1.0 / sqrt(p);  // outside the float32 seed's range
+  double r = (double)rsqrtf((float)p);
+  r = r * (1.5 - 0.5 * p * r * r);
+  r = r * (1.5 - 0.5 * p * r * r);
+  return r;
+}
+
+// In-place Cholesky of the nb x nb block L (float64, shared memory, 256
+// threads); rd[k] = 1 / L[k][k].  Per column: one thread takes the pivot
+// while the column is copied, then the scaled column and the trailing
+// update are written in one pass (two barriers per column).  A
+// non-positive pivot raises SKS_ERR_NOT_PD (when `report`) and continues with 1.
+SKS_DEV void chol_block(double (*L)[NB + 1], double* colk, double* rd, int nb, DevStatus* st, int col_base,
+                        bool report) {
+  const int tid = threadIdx.x;
+  __shared__ double s_r;
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      double p = L[k][k];
+      if (!(p > 0.0) || !isfinite(p)) {
+        if (report) raise_status(st, SKS_ERR_NOT_PD, 21, col_base + k);
+        p = 1.0;
+      }
+      const double r = rsqrt_newton(p);
+      s_r = r;
+      rd[k] = r;
+      L[k][k] = p * r;
+    }
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) colk[i] = L[i][k];
+    __syncthreads();
+    const double r = s_r, r2 = r * r;
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) L[i][k] = colk[i] * r;
+    {
+      const int ty = tid >> 4, tx = tid & 15;
+      for (int i = k + 1 + ty; i < nb; i += 16) {
+        const double ci = colk[i] * r2;
+        for (int j = k + 1 + tx; j <= i; j += 16) L[i][j] -= ci * colk[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld, int nb, double* Dinv, int col_base,
                                                         DevStatus* st) {
   __shared__ double L[NB][NB + 1];
@@ -148,31 +194,9 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
     L[i][j] = (i < nb && j < nb && j <= i) ? D[(long long)i * ld + j] : (i == j ? 1.0 : 0.0);
   }
   __syncthreads();
-  for (int k = 0; k < nb; ++k) {
-    if (tid == 0) {
-      const double p = L[k][k];
-      if (!(p > 0.0) || !isfinite(p)) {
-        raise_status(st, SKS_ERR_NOT_PD, 21, col_base + k);
-        L[k][k] = 1.0;
-      } else {
-        L[k][k] = sqrt(p);
-      }
-    }
-    __syncthreads();
-    const double rpiv = 1.0 / L[k][k];
-    for (int i = k + 1 + tid; i < nb; i += blockDim.x) L[i][k] *= rpiv;
-    __syncthreads();
-    // trailing update of the lower triangle: thread (ty, tx) of a 16 x 16
-    // layout takes rows k+1+ty+16a and columns k+1+tx+16b (no index division)
-    {
-      const int ty = tid >> 4, tx = tid & 15;
-      for (int i = k + 1 + ty; i < nb; i += 16) {
-        const double lik = L[i][k];
-        for (int j = k + 1 + tx; j <= i; j += 16) L[i][j] -= lik * L[j][k];
-      }
-    }
-    __syncthreads();
-  }
+  __shared__ double colk[NB];
+  __shared__ double rd[NB];
+  chol_block(L, colk, rd, nb, st, col_base, true);
   // inverse of the lower-triangular L, row by row:
   //   X[i][j] = -(sum_{j <= q < i} L[i][q] X[q][j]) / L[i][i]  (j < i),  X[i][i] = 1 / L[i][i];
   // the 256 threads split each row's dots four ways (64 columns x 4 parts).
@@ -181,7 +205,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
   __syncthreads();
   const int jj = tid & (NB - 1), pp = tid >> 6;
   __shared__ double rdiag[NB];
-  if (tid < NB) rdiag[tid] = 1.0 / L[tid][tid];
+  if (tid < NB) rdiag[tid] = tid < nb ? rd[tid] : 1.0;
   __syncthreads();
   for (int i = 0; i < NB; ++i) {
     double acc = 0.0;
@@ -227,31 +251,11 @@ __global__ void __launch_bounds__(256) potrf_panel_kernel(double* H, long long l
     L[i][j] = (i < nb && j < nb && j <= i) ? D[(long long)i * ldh + j] : (i == j ? 1.0 : 0.0);
   }
   __syncthreads();
-  for (int k = 0; k < nb; ++k) {
-    if (tid == 0) {
-      const double p = L[k][k];
-      if (!(p > 0.0) || !isfinite(p)) {
-        if (blockIdx.x == 0) raise_status(st, SKS_ERR_NOT_PD, 21, k0 + k);
-        L[k][k] = 1.0;
-      } else {
-        L[k][k] = sqrt(p);
-      }
-    }
-    __syncthreads();
-    const double rpiv = 1.0 / L[k][k];
-    for (int i = k + 1 + tid; i < nb; i += blockDim.x) L[i][k] *= rpiv;
-    __syncthreads();
-    {
-      const int ty = tid >> 4, tx = tid & 15;
-      for (int i = k + 1 + ty; i < nb; i += 16) {
-        const double lik = L[i][k];
-        for (int j = k + 1 + tx; j <= i; j += 16) L[i][j] -= lik * L[j][k];
-      }
-    }
-    __syncthreads();
-  }
+  __shared__ double colk[NB];
+  __shared__ double rd[NB];
+  chol_block(L, colk, rd, nb, st, k0, blockIdx.x == 0);
   for (int e = tid; e < NB * NB; e += blockDim.x) X[e / NB][e % NB] = 0.0;
-  if (tid < NB) rdiag[tid] = 1.0 / L[tid][tid];
+  if (tid < NB) rdiag[tid] = tid < nb ? rd[tid] : 1.0;
   __syncthreads();
   {
     const int jj = tid & (NB - 1), pq = tid >> 6;

@@ -16,6 +16,9 @@ addressed by a 4-word counter whose last word names the stream:
     STREAM_SJLT    counter (i, a // 4, 0, 4): SJLT row candidates of data row i.
     STREAM_SJLT_SIGN counter (i, 0, 0, 5): SJLT signs of data row i (bit k of
                    word 0 for the k-th nonzero).
+    STREAM_RADE    counter (i, r // 128, 0, 6): Rademacher entries R[r, i] of
+                   sketch rows 128q .. 128q + 127, bit r % 32 of word
+                   (r % 128) // 32 (set: -1, clear: +1).
 
 This module implements those definitions in plain integer NumPy (uint64 holds
 every 32x32 product exactly).  The GPU side implements the same published
@@ -34,6 +37,7 @@ STREAM_SIGN = 2
 STREAM_FEISTEL = 3
 STREAM_SJLT = 4
 STREAM_SJLT_SIGN = 5
+STREAM_RADE = 6
 
 FEISTEL_ROUNDS = 6
 FEISTEL_MAX_WALK = 64
@@ -78,6 +82,23 @@ def uniform_open01(word):
     """
     w = np.asarray(word, dtype=np.uint64)
     return ((w >> np.uint64(9)) * np.uint64(2) + np.uint64(1)).astype(np.float64) * 2.0 ** -24
+
+
+def rademacher_block(n_rows_data, m_rows, seed):
+    """Matrix R (m_rows x n_rows_data) of +-1 entries, R[r, i] from bit r % 32
+    of word (r % 128) // 32 of Philox at counter (i, r // 128, 0, STREAM_RADE)
+    (set bit: -1).  Row r depends only on (seed, r): nested like the Gaussian."""
+    k0, k1 = seed_key(seed)
+    nq = (m_rows + 127) // 128
+    i = np.arange(n_rows_data, dtype=np.uint64)[None, :]
+    q = np.arange(nq, dtype=np.uint64)[:, None]
+    words = philox4x32_10(i, q, 0, STREAM_RADE, k0, k1)  # 4 arrays of shape (nq, n)
+    R = np.empty((128 * nq, n_rows_data), dtype=np.float64)
+    for w in range(4):
+        for b in range(32):
+            bit = (words[w] >> np.uint64(b)) & np.uint64(1)
+            R[128 * np.arange(nq) + 32 * w + b] = 1.0 - 2.0 * bit.astype(np.float64)
+    return R[:m_rows]
 
 
 def gaussian_block(n_rows_data, m_rows, seed):

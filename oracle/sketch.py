@@ -97,6 +97,19 @@ def gaussian_matrix(n, m, seed):
 
 
 # ----------------------------------------------------------------------------
+# Rademacher (sub-Gaussian) embedding, entries +-1/sqrt(m)
+# ----------------------------------------------------------------------------
+
+def rademacher_sketch_unscaled(A, m, seed):
+    """Y = R A with R[r, i] = +-1 from ``rng.rademacher_block``; S A = Y / sqrt(m)."""
+    return R.rademacher_block(A.shape[0], m, seed) @ A
+
+
+def rademacher_matrix(n, m, seed):
+    return R.rademacher_block(n, m, seed) / np.sqrt(m)
+
+
+# ----------------------------------------------------------------------------
 # SJLT: s nonzeros per column, values +-1/sqrt(s)
 # ----------------------------------------------------------------------------
 
@@ -124,11 +137,13 @@ def sjlt_sketch(A, m, s, seed):
 # ----------------------------------------------------------------------------
 
 def sketch(kind, A, m, seed, sjlt_s=1):
-    """S A (scaled) for kind in {'srht', 'gaussian', 'sjlt'}."""
+    """S A (scaled) for kind in {'srht', 'gaussian', 'rademacher', 'sjlt'}."""
     if kind == "srht":
         return srht_sketch_unscaled(A, m, seed) / np.sqrt(m)
     if kind == "gaussian":
         return gaussian_sketch_unscaled(A, m, seed) / np.sqrt(m)
+    if kind == "rademacher":
+        return rademacher_sketch_unscaled(A, m, seed) / np.sqrt(m)
     if kind == "sjlt":
         return sjlt_sketch(A, m, sjlt_s, seed)
     raise ValueError(kind)
@@ -139,6 +154,8 @@ def sketch_matrix(kind, n, m, seed, sjlt_s=1):
         return srht_matrix(n, m, seed)
     if kind == "gaussian":
         return gaussian_matrix(n, m, seed)
+    if kind == "rademacher":
+        return rademacher_matrix(n, m, seed)
     if kind == "sjlt":
         return sjlt_matrix(n, m, sjlt_s, seed)
     raise ValueError(kind)

@@ -88,7 +88,7 @@ def test_fwht_matches_scipy_hadamard_and_sylvester():
     assert np.allclose(SK.fwht(SK.fwht(X)), 256 * X)  # H^2 = n I
 
 
-@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "rademacher", "sjlt"])
 def test_fast_sketch_equals_explicit_matrix(kind):
     rng = np.random.default_rng(1)
     n, d, m = 300, 7, 24
@@ -112,7 +112,7 @@ def test_srht_nested_rows():
     assert np.array_equal(a, b[:40]) and len(set(b.tolist())) == 80
 
 
-@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "rademacher", "sjlt"])
 def test_embedding_second_moment_is_identity(kind):
     # E[S^T S] = I for each embedding (the scalings of Section 2.1); Monte Carlo
     # over 3000 seeds, every entry within 5 standard errors.
@@ -149,3 +149,19 @@ def test_sjlt_rows_uniform():
     rows, _ = R.sjlt_rows_signs(20000, 8, 1, seed=2)
     counts = np.bincount(rows[:, 0], minlength=8)
     assert scipy.stats.chisquare(counts).pvalue > 1e-4
+
+
+def test_rademacher_entries_balanced_nested_and_independent_of_m():
+    # +-1 entries, each sign with probability 1/2 (within 5 standard errors over
+    # 2^20 entries), row r the same whatever m is, and no two rows of a block
+    # of 128 (one Philox call per data row) equal.
+    R200 = R.rademacher_block(4096, 256, 17)
+    assert set(np.unique(R200).tolist()) == {-1.0, 1.0}
+    frac = np.mean(R200 < 0)
+    assert abs(frac - 0.5) <= 5 * 0.5 / np.sqrt(R200.size)
+    assert np.array_equal(R.rademacher_block(4096, 130, 17), R200[:130])
+    block = R200[:128]
+    assert len({tuple(r) for r in block.astype(int)}) == 128
+    # adjacent sketch rows are uncorrelated (the bits of one word are independent)
+    corr = np.mean(R200[:-1] * R200[1:])
+    assert abs(corr) <= 5 / np.sqrt(R200[:-1].size)

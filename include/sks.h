@@ -52,7 +52,8 @@ typedef enum {
 typedef enum {
   SKS_SRHT = 0,     /* S = R H E: Walsh-Hadamard of the sign-flipped, zero-padded A, rows subsampled */
   SKS_GAUSSIAN = 1, /* i.i.d. N(0, 1/m) entries, generated from Philox, never stored               */
-  SKS_SJLT = 2      /* s nonzeros +-1/sqrt(s) per column at distinct hashed rows                    */
+  SKS_SJLT = 2,     /* s nonzeros +-1/sqrt(s) per column at distinct hashed rows                    */
+  SKS_RADEMACHER = 3 /* sub-Gaussian: i.i.d. +-1/sqrt(m) entries from Philox bits, never stored        */
 } sks_kind;
 
 typedef enum { SKS_F64 = 0, SKS_F32 = 1 } sks_dtype;

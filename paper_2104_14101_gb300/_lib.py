@@ -14,8 +14,8 @@ OK, ERR_INVALID_ARG, ERR_NOT_PD, ERR_NO_CONVERGENCE, ERR_NUMERIC, ERR_TIMEOUT, E
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PD", 3: "NO_CONVERGENCE", 4: "NUMERIC", 5: "TIMEOUT", 6: "CUDA",
                 7: "WORKSPACE", 8: "UNSUPPORTED"}
 # sks_kind
-SRHT, GAUSSIAN, SJLT = 0, 1, 2
-KINDS = {"srht": SRHT, "gaussian": GAUSSIAN, "sjlt": SJLT}
+SRHT, GAUSSIAN, SJLT, RADEMACHER = 0, 1, 2, 3
+KINDS = {"srht": SRHT, "gaussian": GAUSSIAN, "sjlt": SJLT, "rademacher": RADEMACHER}
 # sks_dtype
 F64, F32 = 0, 1
 # sks_precision

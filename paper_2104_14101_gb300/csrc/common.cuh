@@ -43,6 +43,7 @@ enum Stream : uint32_t {
   STREAM_FEISTEL = 3,
   STREAM_SJLT = 4,
   STREAM_SJLT_SIGN = 5,
+  STREAM_RADE = 6,
 };
 
 constexpr int kFeistelRounds = 6;
@@ -131,6 +132,19 @@ SKS_HD int sjlt_hash(Key k, uint32_t i, uint32_t m, int s_eff, uint32_t* rows, f
   const uint32_t sb = philox(make_uint4(i, 0u, 0u, STREAM_SJLT_SIGN), k.k0, k.k1).x;
   for (int q = 0; q < s_eff; ++q) signs[q] = ((sb >> q) & 1u) ? -1.0f : 1.0f;
   return s_eff;
+}
+
+// Rademacher entries of sketch rows 4Q .. 4Q+3 for data row i: bits
+// (4Q) % 32 .. +3 of word (4Q % 128) / 32 of Philox at (i, 4Q / 128, 0, 6);
+// a set bit is -1.
+SKS_DEV void rade4_f(Key k, uint32_t i, uint32_t Q, float g[4]) {
+  const uint32_t r0 = 4u * Q;
+  const uint4 w = philox(make_uint4(i, r0 >> 7, 0u, STREAM_RADE), k.k0, k.k1);
+  const uint32_t sel = (r0 >> 5) & 3u;
+  const uint32_t word = sel == 0 ? w.x : (sel == 1 ? w.y : (sel == 2 ? w.z : w.w));
+  const uint32_t bits = word >> (r0 & 31u);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) g[t] = ((bits >> t) & 1u) ? -1.f : 1.f;
 }
 
 // Four N(0,1) variates of quad q of data row i (sketch rows 4q..4q+3),

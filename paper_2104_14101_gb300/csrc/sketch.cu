@@ -149,7 +149,7 @@ __global__ void srht_gather_kernel(const TB* __restrict__ B, long long ldb, int 
 // and data row i0 + i; one thread per (quad, data row).
 template <typename T>
 __global__ void gauss_gen_kernel(Key key, int m_off, int m_add, int64_t i0, int icnt, T* __restrict__ G,
-                                 long long ldg) {
+                                 long long ldg, int rade) {
   const int q0 = m_off / 4;
   const int q1 = (m_off + m_add - 1) / 4;
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -158,7 +158,11 @@ __global__ void gauss_gen_kernel(Key key, int m_off, int m_add, int64_t i0, int 
   const int i = (int)(e % icnt);
   const int q = q0 + (int)(e / icnt);
   T g[4];
-  if (sizeof(T) == 8) {
+  if (rade) {
+    float gf[4];
+    rade4_f(key, (uint32_t)(i0 + i), (uint32_t)q, gf);
+    for (int t = 0; t < 4; ++t) g[t] = (T)gf[t];
+  } else if (sizeof(T) == 8) {
     double gd[4];
     gauss4_d(key, (uint32_t)(i0 + i), (uint32_t)q, gd);
     for (int t = 0; t < 4; ++t) g[t] = (T)gd[t];
@@ -408,7 +412,7 @@ template sks_status srht_gather<float, float>(cudaStream_t, const float*, long l
 template <typename T>
 sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64_t n, int d, uint64_t seed, int m_off,
                            int m_add, T* Y, long long ldy, T* gbuf, size_t gbuf_elems, T* split_ws,
-                           size_t split_elems) {
+                           size_t split_elems, bool rademacher) {
   if (m_add <= 0) return SKS_OK;
   if (n == 0) {
     SKS_CUDA_TRY(cudaMemset2DAsync(Y + (long long)m_off * ldy, ldy * sizeof(T), 0, d * sizeof(T), m_add, stream));
@@ -423,7 +427,7 @@ sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64
     const long long nq = (m_off + m_add - 1) / 4 - m_off / 4 + 1;
     const long long threads = nq * icnt;
     gauss_gen_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(key, m_off, m_add, i0, icnt, gbuf,
-                                                                                icnt);
+                                                                                icnt, rademacher ? 1 : 0);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     SKS_TRY(gemm<T>(stream, m_add, d, icnt, gbuf, icnt, false, A + i0 * lda, lda, false, Y + (long long)m_off * ldy,
@@ -432,9 +436,9 @@ sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64
   return SKS_OK;
 }
 template sks_status gaussian_extend<double>(cudaStream_t, const double*, long long, int64_t, int, uint64_t, int, int,
-                                            double*, long long, double*, size_t, double*, size_t);
+                                            double*, long long, double*, size_t, double*, size_t, bool);
 template sks_status gaussian_extend<float>(cudaStream_t, const float*, long long, int64_t, int, uint64_t, int, int,
-                                           float*, long long, float*, size_t, float*, size_t);
+                                           float*, long long, float*, size_t, float*, size_t, bool);
 
 template <typename TA, typename TY>
 sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n, int d, int m, int s, uint64_t seed,

@@ -17,11 +17,12 @@ template <typename TB, typename TY>
 sks_status srht_gather(cudaStream_t stream, const TB* B, long long ldb, int d, int64_t n_pad, uint64_t seed, int r0,
                        int r1, TY* Y, long long ldy, DevStatus* st);
 
-// Y[m_off : m_off + m_add] = G[m_off : m_off + m_add, :] A.
+// Y[m_off : m_off + m_add] = G[m_off : m_off + m_add, :] A (rademacher: the
+// +-1 matrix of the Rademacher embedding instead of G).
 template <typename T>
 sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64_t n, int d, uint64_t seed, int m_off,
                            int m_add, T* Y, long long ldy, T* gbuf, size_t gbuf_elems, T* split_ws,
-                           size_t split_elems);
+                           size_t split_elems, bool rademacher = false);
 
 // Y (m x d) = S A for the SJLT with s nonzeros per column.
 template <typename TA, typename TY>

@@ -162,11 +162,12 @@ SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max) {
   const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
   if (kind == SKS_SRHT) z.b_elems = (size_t)n_pad * p->d;
   z.y_elems = (size_t)m_max * p->d;
-  if (kind == SKS_GAUSSIAN && p->dtype == SKS_F32) {
+  const bool dense_kind = kind == SKS_GAUSSIAN || kind == SKS_RADEMACHER;  // S drawn entry by entry
+  if (dense_kind && p->dtype == SKS_F32) {
     z.tc_elems = (size_t)p->d * (size_t)tc_gauss_kp(p->n);
     z.cmax_elems = (size_t)p->d;
     z.tcpart_elems = tc_gauss_part_elems(p->n, (int)p->d, (int)std::min<int64_t>(m_max, 1 << 30));
-  } else if (kind == SKS_GAUSSIAN) {
+  } else if (dense_kind) {
     z.g_elems = (size_t)std::min<int64_t>((int64_t)m_max * std::max<int64_t>(p->n, 1), (int64_t)1 << 24);
     z.g_elems = std::max<size_t>(z.g_elems, (size_t)m_max * 64);
     z.split_elems = std::min<size_t>((size_t)8 * m_max * p->d, (size_t)1 << 24);
@@ -240,7 +241,7 @@ sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
   if (s->kind == SKS_SRHT) {
     if (s->m == 0) SKS_TRY(srht_form<T>(stream, A, p.lda, p.n, d, (T*)s->B, d, s->seed));
     SKS_TRY(srht_gather<T, T>(stream, (const T*)s->B, d, d, s->n_pad, s->seed, (int)s->m, (int)new_m, Y, s->ldy, s->st));
-  } else if (s->kind == SKS_GAUSSIAN && s->f32) {
+  } else if ((s->kind == SKS_GAUSSIAN || s->kind == SKS_RADEMACHER) && s->f32) {
     // bf16(G) times the split A^T on the tensor cores; the split is made once per sketch
     if (!s->tc_ready) {
       SKS_TRY(tc_split_t(stream, (const float*)A, p.lda, p.n, d, (__nv_bfloat16*)s->tch, (__nv_bfloat16*)s->tcl,
@@ -248,10 +249,11 @@ sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
       s->tc_ready = true;
     }
     SKS_TRY(tc_gauss_sketch(stream, (const __nv_bfloat16*)s->tch, (const __nv_bfloat16*)s->tcl, p.n, d, s->seed,
-                            (int)s->m, (int)(new_m - s->m), s->tcpart, s->tcpart_elems, (float*)Y, s->ldy, s->st));
-  } else if (s->kind == SKS_GAUSSIAN) {
+                            (int)s->m, (int)(new_m - s->m), s->tcpart, s->tcpart_elems, (float*)Y, s->ldy, s->st,
+                            s->kind == SKS_RADEMACHER));
+  } else if (s->kind == SKS_GAUSSIAN || s->kind == SKS_RADEMACHER) {
     SKS_TRY(gaussian_extend<T>(stream, A, p.lda, p.n, d, s->seed, (int)s->m, (int)(new_m - s->m), Y, s->ldy,
-                               (T*)s->gbuf, s->gbuf_elems, (T*)s->split, s->split_elems));
+                               (T*)s->gbuf, s->gbuf_elems, (T*)s->split, s->split_elems, s->kind == SKS_RADEMACHER));
   } else {
     SKS_TRY(sjlt_form<T, T>(stream, A, p.lda, p.n, d, (int)new_m, s->s, s->seed, Y, s->ldy));
   }
@@ -953,7 +955,7 @@ sks_status check_opts(const sks_problem* prob, const sks_opts* o, const double* 
   if (!(o->rho > 0.0 && o->rho < 1.0)) return fail(SKS_ERR_INVALID_ARG, "rho must be in (0, 1)");
   if (o->m_init < 1) return fail(SKS_ERR_INVALID_ARG, "m_init must be >= 1");
   if (!(o->tol > 0.0)) return fail(SKS_ERR_INVALID_ARG, "tol must be > 0");
-  if (o->kind != SKS_SRHT && o->kind != SKS_GAUSSIAN && o->kind != SKS_SJLT)
+  if (o->kind != SKS_SRHT && o->kind != SKS_GAUSSIAN && o->kind != SKS_SJLT && o->kind != SKS_RADEMACHER)
     return fail(SKS_ERR_INVALID_ARG, "bad embedding kind");
   if (o->sjlt_s < 1 || o->sjlt_s > kSjltMaxS) return fail(SKS_ERR_INVALID_ARG, "sjlt_s must be in [1, 16]");
   if (o->precision == SKS_PLAIN_F64 && prob->dtype != SKS_F64)
@@ -1226,7 +1228,8 @@ extern "C" sks_status sks_sketch_create(sks_sketch** out, const sks_problem* p, 
   if (!out) return fail(SKS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   SKS_TRY(validate_problem(p));
-  if (kind != SKS_SRHT && kind != SKS_GAUSSIAN && kind != SKS_SJLT) return fail(SKS_ERR_INVALID_ARG, "bad kind");
+  if (kind != SKS_SRHT && kind != SKS_GAUSSIAN && kind != SKS_SJLT && kind != SKS_RADEMACHER)
+    return fail(SKS_ERR_INVALID_ARG, "bad kind");
   if (sjlt_s < 1 || sjlt_s > kSjltMaxS) return fail(SKS_ERR_INVALID_ARG, "sjlt_s must be in [1, 16]");
   const int64_t mm = resolve_m_max(p, kind, m_max);
   if (m_init < 1 || m_init > mm) return fail(SKS_ERR_INVALID_ARG, "m_init must be in [1, m_max]");

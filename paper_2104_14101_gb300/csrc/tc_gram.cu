@@ -435,7 +435,8 @@ SKS_DEV void cluster_sync_all() {
 
 // ------------------------------------------------------------------ Gaussian sketch on tensor cores
 //
-// K4 for float32 A: Y[r] = sum_i bf16(G[r][i]) (hi + lo)[.][i], i.e. the
+// K4 for float32 A: Y[r] = sum_i bf16(G[r][i]) (hi + lo)[.][i] (or the
+// Rademacher +-1 entries, exact in bfloat16, with g.rade), i.e. the
 // product of the Philox/Box-Muller matrix G (rounded to bfloat16) with the
 // row-scaled two-slice split of A^T (each column of A against its own maximum
 // exponent, prepared once by tc_split_t).  One CTA per (128 sketch rows) x
@@ -479,6 +480,7 @@ struct GaussArgs {
   long long n;             // data rows
   int Kp, kc;              // padded K; data rows per slice (multiple of 64)
   int tiles_m, tiles_n, ksplits;  // tiles_n: a multiple of the cluster size
+  int rade;                        // 1: Rademacher +-1 entries instead of Gaussian ones
   Key key;
   float* part;             // [ksplits][m_add][d]
   DevStatus* st;
@@ -652,8 +654,13 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
         const int Q = q0 + qi;
         const long long i = i0 + kc;
         float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
-        if (i < g.n) gauss4_f(g.key, (uint32_t)i, (uint32_t)Q, v0);
-        if (i + 1 < g.n) gauss4_f(g.key, (uint32_t)(i + 1), (uint32_t)Q, v1);
+        if (g.rade) {
+          if (i < g.n) rade4_f(g.key, (uint32_t)i, (uint32_t)Q, v0);
+          if (i + 1 < g.n) rade4_f(g.key, (uint32_t)(i + 1), (uint32_t)Q, v1);
+        } else {
+          if (i < g.n) gauss4_f(g.key, (uint32_t)i, (uint32_t)Q, v0);
+          if (i + 1 < g.n) gauss4_f(g.key, (uint32_t)(i + 1), (uint32_t)Q, v1);
+        }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int R = 4 * Q + t;
@@ -877,7 +884,7 @@ sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long l
 
 sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, long long n, int d,
                            uint64_t seed, int m_off, int m_add, float* part, size_t part_elems, float* Y,
-                           long long ldy, DevStatus* st) {
+                           long long ldy, DevStatus* st, bool rademacher) {
   if (m_add <= 0) return SKS_OK;
   const int Kp = tc_gauss_kp(n);
   CUtensorMap mh, ml;
@@ -901,6 +908,7 @@ sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const _
     g.tiles_n = ((d + GBN - 1) / GBN + kGCluster - 1) / kGCluster * kGCluster;  // whole clusters
     g.ksplits = ksplits;
     g.key = make_key(seed);
+    g.rade = rademacher ? 1 : 0;
     g.part = part;
     g.st = st;
     const long long blocks = (long long)g.tiles_m * g.tiles_n * ksplits;

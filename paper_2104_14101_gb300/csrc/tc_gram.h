@@ -42,8 +42,9 @@ sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long l
 // Y[m_off .. m_off + m_add) = bf16(G) (Hh + Hl)^T, G[r][i] the Philox /
 // Box-Muller entry of sketch row r and data row i (float32, rounded to
 // bfloat16), generated inside the kernel; unscaled (S A = Y / sqrt(m)).
+// rademacher: the +-1 entries of the Rademacher embedding instead of G.
 sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, long long n, int d,
                            uint64_t seed, int m_off, int m_add, float* part, size_t part_elems, float* Y,
-                           long long ldy, DevStatus* st);
+                           long long ldy, DevStatus* st, bool rademacher = false);
 
 }  // namespace sks

@@ -75,7 +75,7 @@ def test_hess_apply_eight_rhs():
 
 # ----------------------------------------------------------------------------- sketches (K2-K5)
 
-@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "rademacher", "sjlt"])
 @pytest.mark.parametrize("n,d,m", [(1000, 40, 24), (4096, 256, 300), (513, 7, 1), (64, 3, 64)])
 def test_sketch_matches_oracle_fp64(kind, n, d, m):
     rng = np.random.default_rng(n + d + m)
@@ -100,7 +100,7 @@ def test_sketch_fp32_within_1e5(kind):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
 
 
-@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "rademacher", "sjlt"])
 def test_sketch_growth_is_nested(kind):
     rng = np.random.default_rng(5)
     n, d = 2000, 30
@@ -180,6 +180,24 @@ def test_gaussian_tc_sketch_matches_oracle(n, d, m):
         assert np.linalg.norm(got[clean] - ref[clean]) <= 1e-5 * np.linalg.norm(ref[clean])
 
 
+@pytest.mark.parametrize("n,d,m", [(3000, 64, 96), (20000, 300, 200), (40000, 520, 257)])
+def test_rademacher_tc_sketch_matches_oracle(n, d, m):
+    # +-1 entries are exact in bfloat16: only the float32 accumulation differs
+    from oracle import mixed as MX
+    from oracle import rng as R
+    rng = np.random.default_rng(n + d + 1)
+    A = (rng.standard_normal((n, d)) * rng.uniform(0.1, 10, size=(1, d))).astype(np.float32)
+    sk = api().Sketch(dev(A.astype(np.float64), torch.float32), 0.1, dev(np.ones(d)), kind="rademacher", m=m,
+                      seed=13)
+    got = host(sk.matrix())
+    hiT, loT = MX.split_rowscaled(A.T)
+    Rm = R.rademacher_block(n, m, 13)
+    ref = Rm @ (hiT + loT).T / math.sqrt(m)
+    bound = (2.0 ** -24 * 256 * (np.abs(Rm) @ np.abs(A.astype(np.float64))) / math.sqrt(m) + 2.0 ** -23 * np.abs(ref))
+    assert np.all(np.abs(got - ref) <= bound)
+    assert np.linalg.norm(got - ref) <= 2e-6 * np.linalg.norm(ref)
+
+
 def test_gaussian_tc_sketch_nested_growth():
     # m = 1, 2, 3, 6, 13: new rows start at offsets that are not multiples of
     # the four rows one Philox call gives
@@ -239,7 +257,7 @@ def _xstar(p):
 
 
 @pytest.mark.parametrize("method", ["pcg", "ihs"])
-@pytest.mark.parametrize("kind", ["gaussian", "srht", "sjlt"])
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "sjlt", "rademacher"])
 def test_adaptive_solve_reaches_tolerance(method, kind):
     p = synthetic.make_problem("C1", 0, n=2048, d=96, nu=1e-3, decay="harmonic", lam="one_plus_9u")
     xs = _xstar(p)
@@ -251,7 +269,7 @@ def test_adaptive_solve_reaches_tolerance(method, kind):
 
 
 @pytest.mark.parametrize("method", ["pcg", "ihs"])
-@pytest.mark.parametrize("kind", ["gaussian", "srht"])
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "rademacher"])
 def test_m_sequence_matches_oracle(method, kind):
     # Plain float64: the GPU takes the same accept/reject decisions as the
     # oracle (literal restart), except where the oracle's ratio sits within
@@ -308,7 +326,7 @@ def test_multiple_rhs_solved_columnwise():
 # ----------------------------------------------------------------------------- mixed form (a12)
 
 @pytest.mark.parametrize("method", ["pcg", "ihs"])
-@pytest.mark.parametrize("kind", ["gaussian", "sjlt", "srht"])
+@pytest.mark.parametrize("kind", ["gaussian", "sjlt", "srht", "rademacher"])
 def test_mixed_refined_reaches_1e8(method, kind):
     # C3 recipe at a reduced size: float32 A, nu = 1e-4, kappa(H) ~ 1e8.
     p = synthetic.make_problem("C3", 0, n=8192, d=256)

@@ -59,6 +59,10 @@ WORKLOADS = {
     "C3-gauss": dict(config="C3", method="pcg", kind="gaussian", sjlt_s=1, m_init=1, m_max=8192, tol=1e-8,
                      precision="mixed", cpu_rows=1 << 14, ref_rows=1 << 13,
                      desc="C3 with the Gaussian embedding (bfloat16 G on tensor cores), mixed form only"),
+    "C3-rade": dict(config="C3", method="pcg", kind="rademacher", sjlt_s=1, m_init=1, m_max=8192, tol=1e-8,
+                    precision="mixed", cpu_rows=1 << 14, ref_rows=1 << 13,
+                    desc="C3 with the Rademacher (sub-Gaussian) embedding (+-1 entries on tensor cores), mixed "
+                         "form only"),
     "C3-gauss-profile": dict(config="C3", n=1 << 17, method="pcg", kind="gaussian", sjlt_s=1, m_init=1, m_max=8192,
                              tol=1e-8, precision="mixed", desc="C3 recipe with the Gaussian embedding at n=2^17"),
     # reduced C3 (n = 2^17, A = 2 GiB float32) for ncu captures of the float32 kernels

@@ -12,7 +12,8 @@
  *   they are borrowed, never freed, and must stay valid until the work queued
  *   on `stream` has finished.  Host pointers are read before the call returns.
  * - A is n x d, row-major, leading dimension lda >= d (elements), stored as
- *   float64 (SKS_F64) or float32 (SKS_F32).  The base address must be 16-byte
+ *   float64 (SKS_F64, d <= 14336) or float32 (SKS_F32, d <= 16384); rows with
+ *   d > 4096 take one right-hand side per pass.  The base address must be 16-byte
  *   aligned and lda * sizeof(element) a multiple of 16 bytes (A is streamed by
  *   the Tensor Memory Accelerator); otherwise SKS_ERR_INVALID_ARG.
  * - Vectors of length d with k right-hand sides are d x k column-major

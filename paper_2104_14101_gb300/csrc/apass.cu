@@ -116,6 +116,10 @@ struct Acc<df32> {
 constexpr int kConsumers = 256;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kRC = 2;  // rows reduced together
+// wide rows (d > 4096): column vectors per thread (16 x 4 floats, 28 x 2 doubles)
+constexpr int kWideQF32 = 16;
+constexpr int kWideQF64 = 28;
+constexpr int kApassMaxD(bool a_f32) { return a_f32 ? 256 * kWideQF32 * 4 : 256 * kWideQF64 * 2; }
 
 struct ApassArgs {
   int d, dp, boxw, nbox, rows, stages, q, ntiles;
@@ -130,8 +134,10 @@ struct ApassArgs {
 
 SKS_HD size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-template <typename TA, typename TX, int G, int QMAX, int K>
-__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4) ? 2 : 1)
+// XG: wide rows -- the thread's slice of x is read through L1 at each use
+// instead of being held in registers (the accumulators need them).
+template <typename TA, typename TX, int G, int QMAX, int K, bool XG = false>
+__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 && !XG) ? 2 : 1)
     apass_kernel(const __grid_constant__ CUtensorMap tmap, ApassArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int VEC = Vec<TA>::N;
@@ -201,17 +207,20 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 
   // the thread's slice of x (zero past column d) stays in registers for the whole pass
   const typename AT::In* xg = (const typename AT::In*)a.x;
-  TX xr[QMAX][VEC][K];
+  constexpr int QX = XG ? 1 : QMAX;
+  TX xr[QX][VEC][K];
+  if constexpr (!XG) {
 #pragma unroll
-  for (int q = 0; q < QMAX; ++q) {
-    const int vi = l + q * G;
+    for (int q = 0; q < QMAX; ++q) {
+      const int vi = l + q * G;
 #pragma unroll
-    for (int e = 0; e < VEC; ++e)
+      for (int e = 0; e < VEC; ++e)
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const int col = vi * VEC + e;
-        xr[q][e][c] = (q < a.q && vi < nvec && col < a.d) ? AT::from_in(xg[(size_t)c * a.d + col]) : AT::zero();
-      }
+        for (int c = 0; c < K; ++c) {
+          const int col = vi * VEC + e;
+          xr[q][e][c] = (q < a.q && vi < nvec && col < a.d) ? AT::from_in(xg[(size_t)c * a.d + col]) : AT::zero();
+        }
+    }
   }
 
   // shared-memory offset of each of the thread's column vectors within a stage
@@ -246,7 +255,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
       // side (kRC * QMAX independent chains), one per (row, column) otherwise;
       // float64 keeps one chain per row (bound by the float64 pipe, where the
       // extra adds of the split would cost more than the latency it hides)
-      constexpr int QD = (K == 1 && !std::is_same<TX, double>::value) ? QMAX : 1;
+      constexpr int QD = (K == 1 && std::is_same<TX, float>::value) || (K == 1 && !XG && !std::is_same<TX, double>::value)
+                             ? QMAX
+                             : 1;
       TX dq[kRC][QD][K];
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {
@@ -265,7 +276,15 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4)
 #pragma unroll
             for (int e = 0; e < VEC; ++e)
 #pragma unroll
-              for (int c = 0; c < K; ++c) AT::mac(dq[rc][QD > 1 ? q : 0][c], v[e], xr[q][e][c]);
+              for (int c = 0; c < K; ++c) {
+                if constexpr (XG) {
+                  const int col = (l + q * G) * VEC + e;  // past d: A's staged value there is 0
+                  const TX xv = col < a.d ? AT::from_in(__ldg(xg + (size_t)c * a.d + col)) : AT::zero();
+                  AT::mac(dq[rc][QD > 1 ? q : 0][c], v[e], xv);
+                } else {
+                  AT::mac(dq[rc][QD > 1 ? q : 0][c], v[e], xr[q][e][c]);
+                }
+              }
           }
         }
       }
@@ -370,11 +389,11 @@ __global__ void apass_finalize(int nparts, int d, int k, const TX* __restrict__ 
   y[(size_t)c * d + j] = (TX)v;
 }
 
-template <typename TA, typename TX, int G, int QMAX, int K>
+template <typename TA, typename TX, int G, int QMAX, int K, bool XG = false>
 sks_status launch_t(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int64_t d, const void* x,
                     void* y, double nu2, const double* lambda, void* partials, DevStatus* st, cudaStream_t stream,
                     double sgn, const void* addv, double addc, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
-  auto kern = apass_kernel<TA, TX, G, QMAX, K>;
+  auto kern = apass_kernel<TA, TX, G, QMAX, K, XG>;
   SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
   const int nparts = pl.grid * (kConsumers / G);
   if (n > 0) {
@@ -417,7 +436,10 @@ int vec_of(bool a_f32) { return a_f32 ? 4 : 2; }
 }  // namespace
 
 sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32, ApassPlan* pl) {
-  if (d < 1 || d > 4096) return fail(SKS_ERR_UNSUPPORTED, "A-pass supports 1 <= d <= 4096");
+  if (d < 1 || d > kApassMaxD(a_f32))
+    return fail(SKS_ERR_UNSUPPORTED, a_f32 ? "A-pass supports 1 <= d <= 16384 (float32 A)"
+                                           : "A-pass supports 1 <= d <= 14336 (float64 A)");
+  if (d > 4096 && k != 1) return fail(SKS_ERR_UNSUPPORTED, "A-pass: d > 4096 with one right-hand side only");
   if (!(k == 1 || k == 8)) return fail(SKS_ERR_UNSUPPORTED, "A-pass kernel instantiated for k in {1, 8}");
   const int vec = vec_of(a_f32);
   const size_t esz = a_f32 ? 4 : 8, xsz = vec_f32 ? 4 : 8;
@@ -434,7 +456,9 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
     if (nvec <= 32 * qcap) group = 32;
     else if (nvec <= 128 * qcap) group = 128;
   }
-  const int qmax = (k == 8) ? (a_f32 ? 1 : 2) : qcap;
+  int qmax = (k == 8) ? (a_f32 ? 1 : 2) : qcap;
+  const bool wide = d > 4096;  // x through L1, more column vectors per thread, one CTA per SM
+  if (wide) qmax = a_f32 ? kWideQF32 : kWideQF64;
   const int q = (nvec + group - 1) / group;
   if (q > qmax) return fail(SKS_ERR_UNSUPPORTED, "A-pass: row too wide for this instantiation");
   const int ng = kConsumers / group;
@@ -446,7 +470,7 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   const DeviceInfo& di = device_info();
   // the float32 pass (HBM-bound, latency-limited at one CTA per SM) runs two
   // CTAs per SM, each with half the shared memory
-  const int ctas_per_sm = (a_f32 && vec_f32) ? 2 : 1;
+  const int ctas_per_sm = (a_f32 && vec_f32 && !wide) ? 2 : 1;
   const size_t budget = (di.smem_optin ? di.smem_optin : 232448) / ctas_per_sm - (ctas_per_sm > 1 ? 1024 : 0);
   const size_t fixed = ((size_t)2 * 8 * kRC * k * xsz + 127) / 128 * 128;
   const size_t stage_bytes = ((size_t)rows * row_bytes);
@@ -455,6 +479,7 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   const int64_t ntiles = (n + rows - 1) / rows;
   const int sms = di.sms > 0 ? di.sms : 152;
   pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * ctas_per_sm));
+  pl->wide = wide ? 1 : 0;
   pl->group = group;
   pl->q = q;
   pl->rows_per_stage = rows;
@@ -491,6 +516,11 @@ sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n,
                         cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   if (!a_f32 && vec_f32) return fail(SKS_ERR_UNSUPPORTED, "float64 A with float32 vectors");
 #define SKS_APASS_ARGS pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end
+  if (pl.wide) {
+    if (!a_f32) return launch_t<double, double, 256, kWideQF64, 1, true>(SKS_APASS_ARGS);
+    if (vec_f32) return launch_t<float, float, 256, kWideQF32, 1, true>(SKS_APASS_ARGS);
+    return launch_t<float, df32, 256, kWideQF32, 1, true>(SKS_APASS_ARGS);
+  }
   if (!a_f32) {
     if (k == 8) return launch_t<double, double, 256, 2, 8>(SKS_APASS_ARGS);
     if (pl.group == 32) return launch_t<double, double, 32, 8, 1>(SKS_APASS_ARGS);

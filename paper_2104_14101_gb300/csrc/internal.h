@@ -74,6 +74,7 @@ sks_status make_tmap_2d_bf16_sw128(CUtensorMap* map, const void* base, uint64_t 
 struct ApassPlan {
   int grid = 0, group = 0, q = 0, rows_per_stage = 0, stages = 0, boxw = 0, nbox = 0, dp = 0;
   int bulk = 0;                 // whole-row 1-D bulk copies (set by apass_use_bulk)
+  int wide = 0;                 // d > 4096: the wide-row instantiations
   const void* A = nullptr;
   long long lda_bytes = 0;
   size_t smem = 0;

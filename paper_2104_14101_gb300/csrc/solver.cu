@@ -80,7 +80,8 @@ sks_status validate_problem(const sks_problem* p) {
   if (!p->b || !p->lambda_diag) return fail(SKS_ERR_INVALID_ARG, "b or lambda is NULL");
   if (!(p->nu > 0.0) || !std::isfinite(p->nu)) return fail(SKS_ERR_INVALID_ARG, "nu must be > 0");
   if (p->dtype != SKS_F64 && p->dtype != SKS_F32) return fail(SKS_ERR_INVALID_ARG, "bad dtype");
-  if (p->d > 4096) return fail(SKS_ERR_UNSUPPORTED, "d > 4096");
+  if (p->dtype == SKS_F32 && p->d > 16384) return fail(SKS_ERR_UNSUPPORTED, "d > 16384 (float32 A)");
+  if (p->dtype == SKS_F64 && p->d > 14336) return fail(SKS_ERR_UNSUPPORTED, "d > 14336 (float64 A)");
   if (p->n > (int64_t)1 << 31) return fail(SKS_ERR_UNSUPPORTED, "n > 2^31");
   const size_t esz = p->dtype == SKS_F32 ? 4 : 8;
   if (p->n > 0 && (((uintptr_t)p->A & 15) || (p->lda * esz) % 16))

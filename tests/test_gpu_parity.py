@@ -27,6 +27,7 @@ def api():
 
 HESS_SHAPES = [
     (1, 1), (7, 3), (1000, 33), (4096, 256), (5000, 512), (3001, 1000), (2049, 2048), (1500, 4096), (0, 17),
+    (700, 4100), (333, 9000), (257, 14336),  # wide rows: x through L1, one CTA per SM
 ]
 
 
@@ -485,3 +486,31 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     x = rng.standard_normal(20)
     got = host(api().hess_apply(dev(A), dev(x), 0.5, dev(np.ones(20))))
     assert np.allclose(got, O.hess_apply(A, 0.5, np.ones(20), x), rtol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_hess_apply_widest_rows(dtype):
+    # the largest supported d of each precision
+    d = 16384 if dtype == "f32" else 14336
+    rng = np.random.default_rng(d)
+    A = rng.standard_normal((129, d)).astype(np.float32).astype(np.float64)
+    x = rng.standard_normal(d)
+    lam = 1 + rng.random(d)
+    ref = O.hess_apply(A, 0.3, lam, x)
+    got = host(api().hess_apply(dev(A, torch.float32 if dtype == "f32" else torch.float64), dev(x), 0.3, dev(lam)))
+    tol = 1e-5 if dtype == "f32" else 1e-12
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < tol
+
+
+@pytest.mark.parametrize("precision", ["plain", "mixed"])
+def test_adaptive_solve_wide_d(precision):
+    # d = 5000 > 4096 (the paper's experiments use d = 7000 and 14000): the
+    # wide A-pass, a 5000 x 5000 factorisation, SRHT
+    p = synthetic.make_problem("C3" if precision == "mixed" else "C2", 3, n=12000, d=5000, nu=1e-3,
+                               decay="geom0.995")
+    xs = O.direct_solve(p.A, p.b, p.nu, p.lam)
+    A = dev(p.A, torch.float32) if precision == "mixed" else dev(p.A)
+    tol = 1e-8 if precision == "mixed" else 1e-10
+    x, st, _ = api().adaptive_pcg(A, dev(p.b), p.nu, dev(p.lam), kind="srht", m_init=64, tol=tol,
+                                  precision=precision, seed=4, max_iter=2000)
+    assert O.rel_err_H(p.A, p.nu, p.lam, host(x), xs) <= tol, st

@@ -76,6 +76,13 @@ WORKLOADS = {
                desc="256 independent problems, n log-uniform in [2^11, 2^16], d log-uniform in [32, 1024], "
                     "n >= 4d, sigma_j = 0.9^j or 1/(1+j), nu log-uniform in [1e-4, 1e-1], Lambda = I, SRHT, "
                     "adaptive PCG to 1e-8, batched (one captured round replayed) vs one solve at a time"),
+    # the paper's experiment sizes: mixed form only (the float64 copy and its SRHT would add ~120 GB)
+    "P-d7000": dict(config="P", d=7000, method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=0, tol=1e-8,
+                    precision="mixed", desc="paper-scale synthetic: n=2^19, d=7000, sigma_j=0.995^j, nu=1e-2, SRHT, "
+                                            "mixed form, tol 1e-8"),
+    "P-d14000": dict(config="P", method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=0, tol=1e-8,
+                     precision="mixed", desc="paper-scale synthetic: n=2^19, d=14000, sigma_j=0.995^j, nu=1e-2, "
+                                             "SRHT, mixed form, tol 1e-8"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -261,7 +268,7 @@ def run_reference(args, wl, world, rank):
         return None
     import synthetic
     gdev = "cuda" if torch.cuda.is_available() else "cpu"
-    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=gdev, n=wl.get("n"))
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=gdev, n=wl.get("n"), d=wl.get("d"))
     A = prob["A64"].cpu().numpy()
     b = prob["b"][:, 0].cpu().numpy()
     lam = prob["lam"].cpu().numpy()
@@ -318,7 +325,7 @@ def run_ours(args, wl, world, rank, local):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     lib = _lib.load()
-    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev, n=wl.get("n"))
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev, n=wl.get("n"), d=wl.get("d"))
     mixed = wl["precision"] == "mixed"
     A64 = prob["A64"]
     A = prob["A32"] if mixed else A64

@@ -32,6 +32,9 @@ CONFIGS = {
                dtype="f32", kind="gaussian", m_init=1, tol=1e-8),
     "C4": dict(n=1 << 18, d=1024, decay="sqrt_harmonic", nu=1e-2, lam="one_plus_u", rhs="Aty_multi", k=8,
                dtype="f32", kind="gaussian", m_init=1, tol=1e-8),
+    # the paper's synthetic experiments (Section 6): n up to 2^19, d 7000 / 14000, sigma_j = 0.995^j
+    "P": dict(n=1 << 19, d=14000, decay="geom0.995", nu=1e-2, lam="identity", rhs="Aty", k=1,
+              dtype="f32", kind="srht", m_init=1, tol=1e-8),
     # one member of the uneven batch; n, d, decay and nu come from batched_specs
     "C5": dict(n=4096, d=128, decay="geom0.9", nu=1e-2, lam="identity", rhs="Aty", k=1,
                dtype="f64", kind="srht", m_init=1, tol=1e-8),

@@ -90,13 +90,13 @@ WORKLOADS = {
 # ncu DRAM traffic per A-pass launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by the source hash of the kernel file it was captured from; any change
 # to the kernel source invalidates the figure (traffic then reported as null).
-# float32 A-pass (inner PCG): captured at n=2^17, d=4096 (C3-srht-profile, three launches, mean
-# 2.147645 GB read + 5.61 MB written); the n=2^20 workloads run the same kernel with the same grid,
+# float32 A-pass (inner PCG): captured at n=2^17, d=4096 (C3-srht-profile, six launches, mean
+# 2.147598 GB read + 2.20 MB written); the n=2^20 workloads run the same kernel with the same grid,
 # so the read bytes scale by 8 with the rows and the partial-sum writes stay.
 TRAFFIC = {
-    ("d586c9bbca7c43f5", "C3-srht-profile"): 2147645000 + 5613000,
-    ("d586c9bbca7c43f5", "C3"): 8 * 2147645000 + 5613000,
-    ("d586c9bbca7c43f5", "C3-srht"): 8 * 2147645000 + 5613000,
+    ("04ab206454095ac1", "C3-srht-profile"): 2147597781 + 2198784,
+    ("04ab206454095ac1", "C3"): 8 * 2147597781 + 2198784,
+    ("04ab206454095ac1", "C3-srht"): 8 * 2147597781 + 2198784,
 }
 
 

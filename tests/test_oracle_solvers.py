@@ -315,3 +315,35 @@ def test_m_delta_formulas_monotone():
     assert S.m_delta_gaussian(10, 0.1) < S.m_delta_gaussian(10, 0.01)
     # Theorem 5.2 with d_e -> 0 leaves the log term squared.
     assert math.isclose(S.m_delta_gaussian(0.0, 0.5), 8 * math.log(32), rel_tol=1e-12)
+
+
+def test_polyak_ihs_exact_preconditioner_scalar_recurrence():
+    # With H_S = H (SRHT at m = n_pad, where S^T S = I) the heavy-ball error obeys
+    # e_{t+1} = (1 - mu + beta) e_t - beta e_{t-1}, e_{-1} = e_0: a scalar
+    # recurrence in mu_rho, beta_rho of Corollary A.2, independent of the data.
+    p = small_problem(n=256, d=12, nu=1e-2)
+    xs = S.direct_solve(p.A, p.b, p.nu, p.lam)
+    P = S.Preconditioner(SK.sketch("srht", p.A, 256, seed=3), p.nu, p.lam)
+    rho = 0.3
+    mu = 2 * (1 - rho) / (1 + math.sqrt(1 - rho))
+    beta = (1 - math.sqrt(1 - rho)) / (1 + math.sqrt(1 - rho))
+    it = S.polyak_ihs(p.A, p.b, p.nu, p.lam, P, np.zeros(p.d), 8, rho)
+    e0 = -xs
+    c_prev, c = 1.0, 1.0
+    for t in range(1, 9):
+        c_prev, c = c, (1 - mu + beta) * c - beta * c_prev
+        assert np.linalg.norm(it[t] - xs - c * e0) <= 1e-9 * np.linalg.norm(e0), t
+
+
+def test_cg_matches_scipy_cg_iterates():
+    # The unpreconditioned CG baseline (Section 6) is the textbook method:
+    # its iterates equal scipy.sparse.linalg.cg's on the same system.
+    import scipy.sparse.linalg as spla
+    p = small_problem(n=400, d=20, nu=1e-1)
+    H = S.hessian(p.A, p.nu, p.lam)
+    seen = []
+    spla.cg(H, p.b, x0=np.zeros(p.d), rtol=1e-300, atol=0.0, maxiter=8, callback=lambda xk: seen.append(xk.copy()))
+    ours = S.cg(p.A, p.b, p.nu, p.lam, np.zeros(p.d), 8)
+    assert len(seen) == 8
+    for t in range(8):
+        assert np.linalg.norm(ours[t + 1] - seen[t]) <= 1e-10 * np.linalg.norm(seen[t]), t

@@ -101,7 +101,23 @@ typedef struct {
   double inner_tol;    /* relative accuracy asked of each inner solve (mixed form)           */
   sks_trace_event* trace; /* optional host array receiving every test; NULL = none            */
   int64_t trace_cap;   /* capacity of `trace`                                                */
+  int stop_rule;       /* SKS_STOP_ESTIMATE or SKS_STOP_CERTIFIED (below)                    */
+  double cert_delta;   /* failure probability delta of SKS_STOP_CERTIFIED, in (0, 1)         */
+  double cert_de;      /* effective dimension put into m_delta; 0 = d (the conservative d_e) */
 } sks_opts;
+
+/* Stop rules (the paper prescribes none; Section 1.3 and Remark 4.2).  With
+ * eps = 1/2 tol^2 ||x*||_H^2 and ||x*||_H^2 = b^T x* estimated by b^T x_t:
+ * SKS_STOP_ESTIMATE:  stop when delta~_t <= eps / 4 (the decrement estimates
+ *                     delta_t, Lemma 2.1, with a factor 2 of safety in norm);
+ * SKS_STOP_CERTIFIED: Remark 4.2, stop when delta~_t <= eps / (m_delta + 1),
+ *                     which gives delta_t <= eps with probability >= 1 - delta
+ *                     whatever the sketch size; m_delta of Theorem 5.1 (SRHT),
+ *                     Theorem 5.2 with omega^2 <= d_e (Gaussian, and the
+ *                     sub-Gaussian Rademacher embedding), d_e^2 / delta
+ *                     (SJLT: the order of Table 1 with constant 1).  Not
+ *                     available for the unpreconditioned CG or the batch. */
+enum { SKS_STOP_ESTIMATE = 0, SKS_STOP_CERTIFIED = 1 };
 
 /* Per-solve statistics (host struct, filled before the solve returns). */
 typedef struct {
@@ -126,7 +142,8 @@ typedef struct sks_precond sks_precond;
 
 /* Fill `o` with the defaults: rho = 1/8, m_init = 1, m_max = 0, SRHT, s = 1,
  * tol = 1e-10, max_iter = 1000, plain float64, reuse_residual = 1, seed = 0,
- * max_outer = 20, inner_tol = 1e-4, no trace. */
+ * max_outer = 20, inner_tol = 1e-4, no trace, SKS_STOP_ESTIMATE,
+ * cert_delta = 0.01, cert_de = 0. */
 void sks_opts_default(sks_opts* o);
 
 /* Version string of the library build. */
@@ -224,8 +241,9 @@ void sks_precond_destroy(sks_precond* P);
  * after every step, and on failure double m (capped at m_max, where the step is
  * accepted instead), extend the sketch, refactor H_S and restart at x_t.
  * Stop rule (the paper prescribes none; Remark 4.2): after an accepted step,
- * stop when the estimate delta~_t / (b^T x_t) of ||x_t - x*||_H^2/||x*||_H^2
- * is <= (tol/2)^2 (IHS: 2 delta~_t).  k > 1 right-hand sides are solved one
+ * opts.stop_rule decides; by default (SKS_STOP_ESTIMATE) stop when the
+ * estimate delta~_t / (b^T x_t) of ||x_t - x*||_H^2/||x*||_H^2 is <= (tol/2)^2
+ * (IHS: 2 delta~_t); SKS_STOP_CERTIFIED uses tol^2 / (m_delta + 1) instead.  k > 1 right-hand sides are solved one
  * after the other.
  * x: device float64 d x k, in: x_0, out: the solution.  stats: host, may be NULL.
  * ws: device scratch of sks_solve_workspace_size bytes.
@@ -236,6 +254,32 @@ sks_status sks_adaptive_pcg_solve(const sks_problem* p, const sks_opts* o, doubl
                                   void* ws, size_t ws_bytes, void* stream);
 sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
                                   void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Non-adaptive solvers: the baselines of Section 6 and the Polyak-IHS of
+ * Appendix A.  The sketch size stays at m = min(m_init, m_max) (Section 6
+ * compares with PCG at m = 2d); no improvement test rejects a step.
+ *   SKS_FIXED_PCG:    PCG (eq. 5) with the preconditioner H_S.
+ *   SKS_FIXED_IHS:    IHS (eq. 4) with mu = 1 - rho (Theorem 3.2).
+ *   SKS_POLYAK_IHS:   heavy-ball IHS x+ = x - mu H_S^{-1} grad f(x) + beta (x - x_prev)
+ *                     with mu = 2(1-rho)/(1+sqrt(1-rho)), beta = (1-sqrt(1-rho))/(1+sqrt(1-rho))
+ *                     (Corollary A.2); x_prev = x_0 at the start.
+ *   SKS_CG:           conjugate gradient without preconditioner (H_S = I); no
+ *                     sketch is formed.  Plain float64 form only
+ *                     (SKS_ERR_UNSUPPORTED otherwise).
+ * Stop rules: PCG, IHS and Polyak-IHS as the adaptive solvers (the decrement
+ * estimate delta~_t / b^T x_t, 2 delta~_t for the IHS family, <= (tol/2)^2);
+ * CG stops when ||r_t||_2 <= tol ||b||_2 (without a preconditioner there is no
+ * estimate of the H-norm error), and stats.est_rel_err is ||r_t|| / ||b||.
+ * Arguments, workspace (sks_solve_workspace_size), precisions (the mixed form
+ * refines around the fixed-sketch inner solver) and errors as for
+ * sks_adaptive_pcg_solve; stats.rejections is always 0.  Returns
+ * SKS_ERR_NO_CONVERGENCE with x = x_T after max_iter steps, so a run with a
+ * tiny tol and max_iter = T yields the T-th iterate.
+ * ------------------------------------------------------------------------- */
+typedef enum { SKS_FIXED_PCG = 0, SKS_FIXED_IHS = 1, SKS_POLYAK_IHS = 2, SKS_CG = 3 } sks_fixed_method;
+sks_status sks_fixed_solve(sks_fixed_method method, const sks_problem* p, const sks_opts* o, double* x,
+                           sks_stats* stats, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Adjoint of the solve (gradients of x*(A, b, nu, Lambda), implicit

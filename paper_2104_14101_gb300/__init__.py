@@ -13,6 +13,7 @@ from .api import (  # noqa: F401
     Solver,
     adaptive_ihs,
     adaptive_pcg,
+    fixed_solve,
     hess_apply,
     make_problem,
     options,

@@ -16,6 +16,10 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PD", 3: "NO_CONVERGENCE", 4: 
 # sks_kind
 SRHT, GAUSSIAN, SJLT, RADEMACHER = 0, 1, 2, 3
 KINDS = {"srht": SRHT, "gaussian": GAUSSIAN, "sjlt": SJLT, "rademacher": RADEMACHER}
+# stop rules
+STOP_RULES = {"estimate": 0, "certified": 1}
+# sks_fixed_method
+FIXED_METHODS = {"fixed-pcg": 0, "fixed-ihs": 1, "polyak-ihs": 2, "cg": 3}
 # sks_dtype
 F64, F32 = 0, 1
 # sks_precision
@@ -36,7 +40,8 @@ class Opts(C.Structure):
     _fields_ = [("rho", C.c_double), ("m_init", C.c_int64), ("m_max", C.c_int64), ("kind", C.c_int),
                 ("sjlt_s", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int64), ("precision", C.c_int),
                 ("reuse_residual", C.c_int), ("seed", C.c_uint64), ("max_outer", C.c_int64),
-                ("inner_tol", C.c_double), ("trace", C.POINTER(TraceEvent)), ("trace_cap", C.c_int64)]
+                ("inner_tol", C.c_double), ("trace", C.POINTER(TraceEvent)), ("trace_cap", C.c_int64),
+                ("stop_rule", C.c_int), ("cert_delta", C.c_double), ("cert_de", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -86,6 +91,8 @@ _SIGS = {
                                          C.c_void_p]),
     "sks_adaptive_ihs_solve": (C.c_int, [P(Problem), P(Opts), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t,
                                          C.c_void_p]),
+    "sks_fixed_solve": (C.c_int, [C.c_int, P(Problem), P(Opts), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
     "sks_adjoint": (C.c_int, [P(Problem), P(Opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                               P(C.c_double), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t, C.c_void_p]),
     "sks_selftest_wait_timeout": (C.c_int, [C.c_int64, C.c_void_p]),

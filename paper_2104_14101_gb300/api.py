@@ -169,7 +169,8 @@ class Preconditioner:
 
 
 def options(kind="srht", rho=0.125, m_init=1, m_max=0, sjlt_s=1, tol=1e-10, max_iter=1000, precision="plain",
-            reuse_residual=True, seed=0, max_outer=20, inner_tol=1e-4):
+            reuse_residual=True, seed=0, max_outer=20, inner_tol=1e-4, stop_rule="estimate", cert_delta=0.01,
+            cert_de=0.0):
     lib = L.load()
     o = L.Opts()
     lib.sks_opts_default(C.byref(o))
@@ -180,12 +181,16 @@ def options(kind="srht", rho=0.125, m_init=1, m_max=0, sjlt_s=1, tol=1e-10, max_
     o.reuse_residual = int(bool(reuse_residual))
     o.seed = int(seed)
     o.max_outer, o.inner_tol = int(max_outer), float(inner_tol)
+    o.stop_rule = L.STOP_RULES[stop_rule]
+    o.cert_delta, o.cert_de = float(cert_delta), float(cert_de)
     return o
 
 
 class Solver:
-    """Reusable adaptive solver: sizes and holds the workspace once, then
-    ``solve`` can be called repeatedly (the hot path of a benchmark)."""
+    """Reusable solver: sizes and holds the workspace once, then ``solve`` can
+    be called repeatedly (the hot path of a benchmark).  method: "pcg" / "ihs"
+    (adaptive, Algorithms 2 and 1) or one of the non-adaptive solvers
+    "fixed-pcg", "fixed-ihs", "polyak-ihs" (sketch size m_init) and "cg"."""
 
     def __init__(self, A, b, nu, lam, method="pcg", trace_cap=0, **opts):
         self._lib = L.load()
@@ -208,9 +213,15 @@ class Solver:
             x02 = x0.to(torch.float64)
             xcm.copy_((x02[:, None] if x02.dim() == 1 else x02).t())
         st = L.Stats()
-        fn = self._lib.sks_adaptive_pcg_solve if self.method == "pcg" else self._lib.sks_adaptive_ihs_solve
-        status = fn(C.byref(self.problem), C.byref(self.opts), _ptr(xcm), C.byref(st), _ptr(self.ws),
-                    self.ws.numel(), _stream(self.device))
+        args = (C.byref(self.problem), C.byref(self.opts), _ptr(xcm), C.byref(st), _ptr(self.ws), self.ws.numel(),
+                _stream(self.device))
+        if self.method in L.FIXED_METHODS:
+            status = self._lib.sks_fixed_solve(L.FIXED_METHODS[self.method], *args)
+        elif self.method in ("pcg", "ihs"):
+            fn = self._lib.sks_adaptive_pcg_solve if self.method == "pcg" else self._lib.sks_adaptive_ihs_solve
+            status = fn(*args)
+        else:
+            raise ValueError("unknown method %r" % self.method)
         if check and status not in (L.OK,):
             L.check(status)
         x = xcm.t()
@@ -284,6 +295,16 @@ def adaptive_pcg(A, b, nu, lam, x0=None, trace_cap=0, **opts):
 def adaptive_ihs(A, b, nu, lam, x0=None, trace_cap=0, **opts):
     """Algorithm 1 with the IHS step (mu = 1 - rho) on the GPU; returns (x, stats, trace)."""
     return Solver(A, b, nu, lam, method="ihs", trace_cap=trace_cap, **opts).solve(x0)
+
+
+def fixed_solve(A, b, nu, lam, method="fixed-pcg", x0=None, check=True, **opts):
+    """Non-adaptive solvers on the GPU (sketch size m_init): "fixed-pcg",
+    "fixed-ihs", "polyak-ihs" (Appendix A) or "cg" (no preconditioner);
+    returns (x, stats, trace).  check=False returns NO_CONVERGENCE results
+    (x = x_T after max_iter steps) instead of raising."""
+    if method not in L.FIXED_METHODS:
+        raise ValueError("unknown fixed-sketch method %r" % method)
+    return Solver(A, b, nu, lam, method=method, **opts).solve(x0, check=check)
 
 
 class BatchSolver:

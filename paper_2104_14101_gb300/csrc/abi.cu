@@ -20,6 +20,9 @@ extern "C" void sks_opts_default(sks_opts* o) {
   o->inner_tol = 1e-4;
   o->trace = nullptr;
   o->trace_cap = 0;
+  o->stop_rule = SKS_STOP_ESTIMATE;
+  o->cert_delta = 0.01;
+  o->cert_de = 0.0;
 }
 
 extern "C" const char* sks_version(void) { return "sks 0.1 (sm_103a)"; }
@@ -47,6 +50,11 @@ extern "C" sks_status sks_adaptive_pcg_solve(const sks_problem* p, const sks_opt
 extern "C" sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
                                              void* ws, size_t ws_bytes, void* stream) {
   return adaptive_solve(1, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" sks_status sks_fixed_solve(sks_fixed_method method, const sks_problem* p, const sks_opts* o, double* x,
+                                      sks_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+  return fixed_solve((int)method, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 extern "C" sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g,

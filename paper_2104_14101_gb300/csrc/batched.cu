@@ -873,6 +873,8 @@ sks_status check_batch(const sks_problem* probs, int count, const sks_opts* o) {
   if (!(o->rho > 0.0 && o->rho < 1.0)) return fail(SKS_ERR_INVALID_ARG, "rho must be in (0, 1)");
   if (o->m_init < 1) return fail(SKS_ERR_INVALID_ARG, "m_init must be >= 1");
   if (!(o->tol > 0.0)) return fail(SKS_ERR_INVALID_ARG, "tol must be > 0");
+  if (o->stop_rule != SKS_STOP_ESTIMATE)
+    return fail(SKS_ERR_UNSUPPORTED, "the batch stops by the estimate rule only");
   if (o->kind != SKS_SRHT) return fail(SKS_ERR_UNSUPPORTED, "batch: only the SRHT embedding is implemented");
   if (o->precision != SKS_PLAIN_F64) return fail(SKS_ERR_UNSUPPORTED, "batch: only the plain float64 form");
   for (int i = 0; i < count; ++i) {

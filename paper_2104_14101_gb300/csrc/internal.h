@@ -108,6 +108,9 @@ sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t*
 // method 0: adaptive PCG (Algorithm 2); 1: adaptive IHS (Algorithm 1)
 sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
                           size_t ws_bytes, cudaStream_t stream);
+// method 0: PCG, 1: IHS, 2: Polyak-IHS (all with H_S fixed at m = m_init), 3: CG (H_S = I)
+sks_status fixed_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
+                       size_t ws_bytes, cudaStream_t stream);
 sks_status adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g, double* db, void* dA,
                    long long ldda, double* dnu, double* dlambda, sks_stats* stats, void* ws, size_t ws_bytes,
                    cudaStream_t stream);

@@ -509,17 +509,24 @@ __global__ void __launch_bounds__(kStepThreads) pcg_restart_kernel(int d, const 
   }
 }
 
-// IHS proposal x+ = x - mu v
-__global__ void ihs_prop_kernel(int d, const double* x, const double* v, double mu, double* xp) {
+// IHS proposal x+ = x - mu v (eq. 4); with xprev != NULL the Polyak-IHS
+// (heavy-ball) proposal x+ = x - mu v + beta (x - x_prev) (Appendix A, eq. A.1).
+__global__ void ihs_prop_kernel(int d, const double* x, const double* xprev, const double* v, double mu, double beta,
+                                double* xp) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < d) xp[j] = x[j] - mu * v[j];
+  if (j >= d) return;
+  double y = x[j] - mu * v[j];
+  if (xprev) y += beta * (x[j] - xprev[j]);
+  xp[j] = y;
 }
 
 // IHS test: delta~+ = 1/2 g+^T v+, reject iff delta~+/delta~_I > c rho^(t+1-I).
+// xprev != NULL (Polyak-IHS): the accepted step also shifts x_t into x_{t-1}.
 __global__ void __launch_bounds__(kStepThreads) ihs_step2_kernel(int d, const double* b, double* x, double* g,
                                                                  double* v, const double* xp, const double* gp,
                                                                  const double* vp, Ctl* ctl, double c, double phi,
-                                                                 int can_double, double tol2, double stop_abs) {
+                                                                 int can_double, double tol2, double stop_abs,
+                                                                 double* xprev) {
   __shared__ int s_accept;
   const double dp = 0.5 * block_dot(d, gp, vp);
   if (threadIdx.x == 0) {
@@ -538,6 +545,7 @@ __global__ void __launch_bounds__(kStepThreads) ihs_step2_kernel(int d, const do
   __syncthreads();
   if (!s_accept) return;
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    if (xprev) xprev[j] = x[j];
     x[j] = xp[j];
     g[j] = gp[j];
     v[j] = vp[j];
@@ -672,7 +680,10 @@ struct Timer {
   }
 };
 
-enum Method { PCG, IHS };
+// PCG: eq. (5); IHS: eq. (4) with mu = 1 - rho (Theorem 3.2); POLYAK: the
+// heavy-ball IHS of Appendix A with mu_rho, beta_rho (Corollary A.2); CG: the
+// unpreconditioned conjugate gradient baseline of Section 6 (PCG with H_S = I).
+enum Method { PCG, IHS, POLYAK, CG };
 
 // One adaptive solve engine shared by the plain float64 form and the inner
 // solves of the mixed form.  The iteration A-pass runs in the precision of A
@@ -697,6 +708,9 @@ struct Engine {
   bool apass_pending = false;
   Timer *t_sketch = nullptr, *t_factor = nullptr;
   int outer = 0;
+  bool fixed = false;         // non-adaptive: m stays at m_init, every step is accepted
+  double mu = 0, beta = 0;    // IHS / Polyak-IHS step size and momentum
+  double cg_bb = 0;           // b^T b of the current right-hand side (CG stop rule)
 
   ~Engine() {
     if (ev_a0) cudaEventDestroy(ev_a0);
@@ -717,12 +731,19 @@ struct Engine {
     m_max = resolve_m_max(pr, op->kind, op->m_max);
     nu2 = pr->nu * pr->nu;
     const double rho = op->rho;
-    if (method == PCG) {
+    if (method == PCG || method == CG) {
       phi = (1.0 - std::sqrt(1.0 - rho)) / (1.0 + std::sqrt(1.0 - rho));
       c = 4.0 * (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
     } else {
       phi = rho;
       c = (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
+    }
+    mu = 1.0 - rho;
+    beta = 0.0;
+    if (method == POLYAK) {
+      const double s1 = std::sqrt(1.0 - rho);
+      mu = 2.0 * (1.0 - rho) / (1.0 + s1);
+      beta = (1.0 - s1) / (1.0 + s1);
     }
     SKS_CUDA_TRY(cudaEventCreate(&ev_a0));
     SKS_CUDA_TRY(cudaEventCreate(&ev_a1));
@@ -787,6 +808,15 @@ struct Engine {
                         stream, sgn, addv, addc);
   }
 
+  // v = H_S^{-1} z; the unpreconditioned CG takes H_S = I.
+  sks_status apply(const double* z, double* v) {
+    if (method == CG) {
+      SKS_CUDA_TRY(cudaMemcpyAsync(v, z, (size_t)d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      return SKS_OK;
+    }
+    return precond_apply1(&P, z, v, stream);
+  }
+
   sks_status sync_point(const char* what) {
     SKS_TRY(read_status(W.st, stream, what));
     if (apass_pending) {
@@ -801,6 +831,10 @@ struct Engine {
   }
 
   sks_status first_sketch() {
+    if (method == CG) {  // no sketch, no preconditioner
+      m = 0;
+      return SKS_OK;
+    }
     m = std::min<int64_t>(o->m_init, m_max);
     t_sketch->start();
     SKS_TRY(sketch_to(&sk, m, stream));
@@ -836,25 +870,35 @@ struct Engine {
     ctl_init_kernel<<<1, 1, 0, stream>>>(W.ctl);
     note_launch();
     const bool mixed_inner = mixed;
+    const bool pcg_like = method == PCG || method == CG;
+    double* xprev = method == POLYAK ? W.p : nullptr;  // x_{t-1} of the heavy-ball step (p is unused by IHS)
     // PCG: r = b - H x, r~ = H_S^{-1} r.   IHS: g = H x - b (in r), v = H_S^{-1} g (in rt).
     if (mixed_inner) {
       // the inner right-hand side is the refinement residual and x starts at 0
       SKS_CUDA_TRY(cudaMemsetAsync(W.x, 0, d * sizeof(double), stream));
-      if (method == PCG) SKS_CUDA_TRY(cudaMemcpyAsync(W.r, b, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      if (pcg_like) SKS_CUDA_TRY(cudaMemcpyAsync(W.r, b, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
       else {
         SKS_CUDA_TRY(cudaMemsetAsync(W.r, 0, d * sizeof(double), stream));
         axpy_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, -1.0, b, W.r);
         note_launch();
       }
     } else {
-      if (method == PCG) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
+      if (pcg_like) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
       else SKS_TRY(hess(W.x, W.r, 1.0, b, -1.0));
     }
-    SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
-    if (method == PCG) pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
+    SKS_TRY(apply(W.r, W.rt));
+    if (pcg_like) pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
     else ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
+    if (xprev) SKS_CUDA_TRY(cudaMemcpyAsync(xprev, W.x, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    if (method == CG) {
+      // CG stop rule: ||r||_2 <= tol ||b||_2 (no preconditioner, so no estimate of the H-norm error)
+      dot_kernel<<<1, kStepThreads, 0, stream>>>(d, b, b, W.scal + 2);
+      note_launch();
+      SKS_CUDA_TRY(cudaGetLastError());
+      SKS_CUDA_TRY(cudaMemcpyAsync(&cg_bb, W.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    }
     Ctl h;
     SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
     SKS_TRY(sync_point("initial residual"));
@@ -874,25 +918,28 @@ struct Engine {
         return SKS_OK;
       }
     }
-    const double stop_abs = rel2 > 0 ? rel2 * h.dt : 0.0;
-    bool conv = h.stop != 0;
-    if (!conv && tol2 > 0 && !mixed_inner) conv = false;
+    double stop_abs = rel2 > 0 ? rel2 * h.dt : 0.0;
+    if (method == CG) {
+      stop_abs = std::max(stop_abs, o->tol * o->tol * cg_bb);
+      tol2 = 0.0;
+    }
+    bool conv = h.stop != 0 || (stop_abs > 0 && h.dt <= stop_abs);
     if (hout) *hout = h;
     if (rel2 > 0 && *dt0 <= 0) conv = true;
     int64_t guard = 0;
     while (!conv && h.t < max_iter && guard++ < max_iter + 64) {
-      const int can_double = m < m_max ? 1 : 0;
-      if (method == PCG) {
+      const int can_double = (!fixed && m < m_max) ? 1 : 0;
+      if (pcg_like) {
         SKS_TRY(hess(W.p, W.Hp, 1.0, nullptr, 0.0));
         pcg_step1_kernel<<<1, kStepThreads, 0, stream>>>(d, W.x, W.r, W.p, W.Hp, W.xp, W.rp, W.ctl);
         note_launch();
         SKS_CUDA_TRY(cudaGetLastError());
-        SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
+        SKS_TRY(apply(W.rp, W.rtp));
         pcg_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.p, W.xp, W.rp, W.rtp, W.ctl, c, phi,
                                                          can_double, tol2, stop_abs);
         note_launch();
       } else {
-        ihs_prop_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, W.x, W.rt, 1.0 - o->rho, W.xp);
+        ihs_prop_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, W.x, xprev, W.rt, mu, beta, W.xp);
         note_launch();
         if (mixed_inner) {
           SKS_TRY(hess(W.xp, W.rp, 1.0, nullptr, 0.0));
@@ -901,9 +948,9 @@ struct Engine {
         } else {
           SKS_TRY(hess(W.xp, W.rp, 1.0, b, -1.0));
         }
-        SKS_TRY(precond_apply1(&P, W.rp, W.rtp, stream));
+        SKS_TRY(apply(W.rp, W.rtp));
         ihs_step2_kernel<<<1, kStepThreads, 0, stream>>>(d, b, W.x, W.r, W.rt, W.xp, W.rp, W.rtp, W.ctl, c, phi,
-                                                         can_double, tol2, stop_abs);
+                                                         can_double, tol2, stop_abs, xprev);
         note_launch();
       }
       SKS_CUDA_TRY(cudaGetLastError());
@@ -923,12 +970,12 @@ struct Engine {
       if (!h.accept) {
         S.rejections += 1;
         SKS_TRY(grow());
-        if (method == PCG) {
+        if (pcg_like) {
           if (!o->reuse_residual && !mixed_inner) SKS_TRY(hess(W.x, W.r, -1.0, b, 1.0));
-          SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
+          SKS_TRY(apply(W.r, W.rt));
           pcg_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.p, W.ctl);
         } else {
-          SKS_TRY(precond_apply1(&P, W.r, W.rt, stream));
+          SKS_TRY(apply(W.r, W.rt));
           ihs_restart_kernel<<<1, kStepThreads, 0, stream>>>(d, W.r, W.rt, W.ctl);
         }
         note_launch();
@@ -965,7 +1012,40 @@ sks_status check_opts(const sks_problem* prob, const sks_opts* o, const double* 
     return fail(SKS_ERR_INVALID_ARG, "the mixed form needs a float32 A");
   if (o->precision == SKS_MIXED_REFINED && (o->max_outer < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)))
     return fail(SKS_ERR_INVALID_ARG, "mixed form needs max_outer >= 1 and inner_tol in (0, 1)");
+  if (o->stop_rule != SKS_STOP_ESTIMATE && o->stop_rule != SKS_STOP_CERTIFIED)
+    return fail(SKS_ERR_INVALID_ARG, "bad stop rule");
+  if (o->stop_rule == SKS_STOP_CERTIFIED &&
+      (!(o->cert_delta > 0.0 && o->cert_delta < 1.0) || !(o->cert_de >= 0.0) || !std::isfinite(o->cert_de)))
+    return fail(SKS_ERR_INVALID_ARG, "certified stop rule needs cert_delta in (0, 1) and cert_de >= 0");
   return SKS_OK;
+}
+
+// Critical sketch size m_delta of the embedding (Theorem 5.1 for the SRHT;
+// Theorem 5.2 with omega(C)^2 <= d_e for the Gaussian and sub-Gaussian
+// embeddings; the order d_e^2/delta of Table 1, constant 1, for the SJLT).
+double critical_sketch_size(sks_kind kind, int64_t n, double d_e, double delta) {
+  switch (kind) {
+    case SKS_SRHT: {
+      const double a = std::sqrt(d_e) + std::sqrt(8.0 * std::log(2.0 * (double)n / delta));
+      return 16.0 * std::log(16.0 * d_e / delta) * a * a;
+    }
+    case SKS_SJLT:
+      return d_e * d_e / delta;
+    default: {
+      const double a = std::sqrt(d_e) + std::sqrt(8.0 * std::log(16.0 / delta));
+      return a * a;
+    }
+  }
+}
+
+// Coefficient tol2 of the stop tests "PCG: delta~ <= tol2 b^T x" and "IHS:
+// 2 delta~ <= tol2 b^T x": (tol/2)^2 for the estimate rule; tol^2/(m_delta+1)
+// for Remark 4.2 (delta~_t <= eps/(m_delta+1) with eps = 1/2 tol^2 b^T x_t; the
+// PCG decrement of Algorithm 2 carries no 1/2).
+double stop_coefficient(const sks_problem* p, const sks_opts* o) {
+  if (o->stop_rule != SKS_STOP_CERTIFIED) return (o->tol / 2.0) * (o->tol / 2.0);
+  const double d_e = o->cert_de > 0.0 ? o->cert_de : (double)p->d;
+  return o->tol * o->tol / (critical_sketch_size(o->kind, std::max<int64_t>(p->n, 1), d_e, o->cert_delta) + 1.0);
 }
 
 // Solve H X = B column by column with the engine's current sketch and
@@ -975,8 +1055,8 @@ sks_status solve_columns(Engine& E, const double* B, double* X_io) {
   const sks_opts* o = E.o;
   cudaStream_t stream = E.stream;
   const int d = E.d;
-  const double tol2 = (o->tol / 2.0) * (o->tol / 2.0);
-  const double fac = E.method == PCG ? 1.0 : 2.0;
+  const double tol2 = stop_coefficient(prob, o);
+  const double fac = (E.method == PCG || E.method == CG) ? 1.0 : 2.0;
   sks_status result = SKS_OK;
   for (int64_t col = 0; col < prob->k && result == SKS_OK; ++col) {
     const double* b = B + col * d;
@@ -990,7 +1070,10 @@ sks_status solve_columns(Engine& E, const double* B, double* X_io) {
       sks_status r = E.inner(b, tol2, 0.0, o->max_iter, &converged, &dt0, &h);
       SKS_CUDA_TRY(cudaMemcpyAsync(xcol, E.W.x, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
       if (r != SKS_OK) return r;
-      E.S.est_rel_err = h.btx > 0 ? std::sqrt(std::max(0.0, fac * h.dt / h.btx)) : 0.0;
+      if (E.method == CG)  // relative residual ||r|| / ||b||
+        E.S.est_rel_err = E.cg_bb > 0 ? std::sqrt(std::max(0.0, h.dt / E.cg_bb)) : 0.0;
+      else
+        E.S.est_rel_err = h.btx > 0 ? std::sqrt(std::max(0.0, fac * h.dt / h.btx)) : 0.0;
     } else {
       // Iterative refinement: r = b - H x in float64 arithmetic, inner adaptive
       // solve of H dx = r in the precision of A, x += dx.
@@ -1056,8 +1139,12 @@ sks_status write_state(Engine& E) {
 }
 
 sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks_opts* o, double* x_io,
-                               sks_stats* stats, void* ws, size_t ws_bytes, cudaStream_t stream) {
+                               sks_stats* stats, void* ws, size_t ws_bytes, cudaStream_t stream, bool fixed = false) {
   SKS_TRY(check_opts(prob, o, x_io));
+  if (method == CG && o->precision != SKS_PLAIN_F64)
+    return fail(SKS_ERR_UNSUPPORTED, "the unpreconditioned CG runs in the plain float64 form only");
+  if (method == CG && o->stop_rule == SKS_STOP_CERTIFIED)
+    return fail(SKS_ERR_UNSUPPORTED, "the certified stop rule needs a sketched preconditioner");
   const int d = (int)prob->d;
   size_t need = 0;
   SKS_TRY(solve_layout(prob, o, nullptr, 0, nullptr, &need));
@@ -1068,6 +1155,7 @@ sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks
   E.t_factor = &t_factor;
   t_total.start();
   SKS_TRY(E.init(method, prob, o, ws, ws_bytes, stream));
+  E.fixed = fixed;
   SKS_CUDA_TRY(cudaMemsetAsync(E.W.state, 0, sizeof(SolveState), stream));
   SKS_CUDA_TRY(cudaMemsetAsync(E.W.st, 0, sizeof(DevStatus), stream));
   check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, E.W.st);
@@ -1075,7 +1163,8 @@ sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks
   SKS_TRY(read_status(E.W.st, stream, "input check"));
   SKS_TRY(E.first_sketch());
   const sks_status result = solve_columns(E, prob->b, x_io);
-  if (result == SKS_OK || result == SKS_ERR_NO_CONVERGENCE) SKS_TRY(write_state(E));
+  // CG leaves no preconditioner for the adjoint to reuse
+  if ((result == SKS_OK || result == SKS_ERR_NO_CONVERGENCE) && method != CG) SKS_TRY(write_state(E));
   t_total.stop();
   sks_stats& S = E.S;
   S.final_m = E.m;
@@ -1146,6 +1235,13 @@ sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t*
 sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
                           size_t ws_bytes, cudaStream_t stream) {
   return adaptive_solve_impl(method == 0 ? PCG : IHS, p, o, x, stats, ws, ws_bytes, stream);
+}
+
+sks_status fixed_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
+                       size_t ws_bytes, cudaStream_t stream) {
+  static const Method kMethods[4] = {PCG, IHS, POLYAK, CG};
+  if (method < 0 || method > 3) return fail(SKS_ERR_INVALID_ARG, "bad fixed-sketch method");
+  return adaptive_solve_impl(kMethods[method], p, o, x, stats, ws, ws_bytes, stream, true);
 }
 
 sks_status adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g, double* db, void* dA,

@@ -56,6 +56,7 @@ def test_opts_default_and_validation_without_gpu(lib_path):
     o = _lib.Opts()
     lib.sks_opts_default(ctypes.byref(o))
     assert o.rho == 0.125 and o.m_init == 1 and o.reuse_residual == 1 and o.max_outer == 20
+    assert o.stop_rule == 0 and o.cert_delta == 0.01 and o.cert_de == 0.0
     p = _lib.Problem()
     p.dtype, p.n, p.d, p.lda, p.k = _lib.F64, 10, 4, 2, 1  # lda < d
     nb = ctypes.c_size_t()

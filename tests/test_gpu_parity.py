@@ -145,6 +145,25 @@ def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
     assert float(np.max(np.abs(got - ref) / scale)) < tol
 
 
+@pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
+@pytest.mark.parametrize("n,d,m,s", [(3001, 1100, 257, 4), (5000, 600, 1024, 4), (9000, 64, 4096, 1),
+                                     (1000, 2048, 300, 16)])
+def test_sjlt_large_sketch_scatter(dt, tol, n, d, m, s):
+    # larger m: the column-tiled L2 scatter; d = 1100 (float32) and 600
+    # (float64) leave a ragged last column tile, n = 9000 rows on m = 4096 and
+    # 8192 sketch rows collide often, s = 16 is the largest column sparsity.
+    rng = np.random.default_rng(n + d + m + s)
+    A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+    sk = api().Sketch(dev(A, dt), 0.1, dev(np.ones(d)), kind="sjlt", m=m, sjlt_s=s, seed=31)
+    got = host(sk.matrix())
+    ref = OS.sketch("sjlt", A, m, seed=31, sjlt_s=s)
+    scale = np.sqrt(np.sum(A * A, axis=0))[None, :]
+    assert float(np.max(np.abs(got - ref) / scale)) < tol
+    sk.grow(2 * m)  # re-hashed into 2m rows in one more pass
+    ref2 = OS.sketch("sjlt", A, 2 * m, seed=31, sjlt_s=s)
+    assert float(np.max(np.abs(host(sk.matrix()) - ref2) / scale)) < tol
+
+
 def gaussian_tc_bound(A32, m, seed, row0=0):
     """Reference rows [row0, m) of the tensor-core Gaussian sketch (scaled by
     1/sqrt(m)) and an element-wise error bound: float32 accumulation over K
@@ -291,6 +310,28 @@ def test_m_sequence_matches_oracle(method, kind):
     else:
         assert len(to) == len(tg)
         assert so["final_m"] == sg["final_m"] and so["iters"] == sg["iters"]
+
+
+@pytest.mark.parametrize("method", ["pcg", "ihs"])
+@pytest.mark.parametrize("kind", ["srht", "gaussian", "sjlt"])
+def test_certified_stop_rule(method, kind):
+    # Remark 4.2: stop when delta~_t <= eps / (m_delta + 1), eps = 1/2 tol^2 ||x*||_H^2
+    # (estimated by b^T x_t), with m_delta of Theorem 5.1 / 5.2 at d_e := d and
+    # d_e^2/delta for the SJLT; then delta_t <= eps.
+    p = synthetic.make_problem("C1", 2, n=2048, d=64, nu=1e-2)
+    xs = _xstar(p)
+    tol, delta = 1e-6, 0.05
+    fn = api().adaptive_pcg if method == "pcg" else api().adaptive_ihs
+    kw = dict(kind=kind, m_init=1, tol=tol, seed=3, sjlt_s=2)
+    _, s0, _ = fn(dev(p.A), dev(p.b), p.nu, dev(p.lam), **kw)
+    x1, s1, _ = fn(dev(p.A), dev(p.b), p.nu, dev(p.lam), stop_rule="certified", cert_delta=delta, **kw)
+    md = {"srht": O.m_delta_srht(p.d, p.n, delta), "gaussian": O.m_delta_gaussian(p.d, delta),
+          "sjlt": p.d ** 2 / delta}[kind]
+    btx = float(p.b @ host(x1))
+    dt_paper = s1["final_delta_tilde"] / (2.0 if method == "pcg" else 1.0)  # Algorithm 2's decrement has no 1/2
+    assert dt_paper <= O.termination_threshold(0.5 * tol ** 2 * btx, md) * (1 + 1e-9)
+    assert s1["iters"] > s0["iters"]
+    assert O.rel_err_H(p.A, p.nu, p.lam, host(x1), xs) <= tol
 
 
 def test_config1_full_size():

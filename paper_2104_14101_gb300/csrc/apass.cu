@@ -137,7 +137,7 @@ SKS_HD size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // XG: wide rows -- the thread's slice of x is read through L1 at each use
 // instead of being held in registers (the accumulators need them).
 template <typename TA, typename TX, int G, int QMAX, int K, bool XG = false>
-__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 && !XG) ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 && QMAX <= 4) ? 2 : 1)
     apass_kernel(const __grid_constant__ CUtensorMap tmap, ApassArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int VEC = Vec<TA>::N;
@@ -255,9 +255,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
       // side (kRC * QMAX independent chains), one per (row, column) otherwise;
       // float64 keeps one chain per row (bound by the float64 pipe, where the
       // extra adds of the split would cost more than the latency it hides)
-      constexpr int QD = (K == 1 && std::is_same<TX, float>::value) || (K == 1 && !XG && !std::is_same<TX, double>::value)
-                             ? QMAX
-                             : 1;
+      constexpr int QD =
+          QMAX <= 8 && ((K == 1 && std::is_same<TX, float>::value) || (K == 1 && !XG && !std::is_same<TX, double>::value))
+              ? QMAX
+              : 1;
       TX dq[kRC][QD][K];
 #pragma unroll
       for (int rc = 0; rc < kRC; ++rc) {
@@ -457,13 +458,15 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
     else if (nvec <= 128 * qcap) group = 128;
   }
   int qmax = (k == 8) ? (a_f32 ? 1 : 2) : qcap;
-  const bool wide = d > 4096;  // x through L1, more column vectors per thread, one CTA per SM
+  const bool wide = d > 4096;  // more column vectors per thread, one CTA per SM (float64 / double-float: x through L1)
   if (wide) qmax = a_f32 ? kWideQF32 : kWideQF64;
   const int q = (nvec + group - 1) / group;
   if (q > qmax) return fail(SKS_ERR_UNSUPPORTED, "A-pass: row too wide for this instantiation");
   const int ng = kConsumers / group;
   const size_t row_bytes = (size_t)dp * esz;
-  int rows = (int)std::max<size_t>(1, (32 * 1024) / row_bytes);
+  // stages of ~32 KB; wide rows: ~64 KB, so that a stage holds the kRC rows
+  // reduced together by the 256 consumers (one barrier per kRC rows)
+  int rows = (int)std::max<size_t>(1, (wide ? 64 * 1024 : 32 * 1024) / row_bytes);
   rows = std::max(rows, ng);
   rows = std::min(rows, 256);
   rows = rows / ng * ng;
@@ -518,7 +521,9 @@ sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n,
 #define SKS_APASS_ARGS pl, tmap, n, d, x, y, nu2, lambda, partials, st, stream, sgn, addv, addc, ev_begin, ev_end
   if (pl.wide) {
     if (!a_f32) return launch_t<double, double, 256, kWideQF64, 1, true>(SKS_APASS_ARGS);
-    if (vec_f32) return launch_t<float, float, 256, kWideQF32, 1, true>(SKS_APASS_ARGS);
+    // float32 inner pass: the thread's slice of x in registers (8 or 16 column vectors)
+    if (vec_f32 && pl.q <= 8) return launch_t<float, float, 256, 8, 1, false>(SKS_APASS_ARGS);
+    if (vec_f32) return launch_t<float, float, 256, kWideQF32, 1, false>(SKS_APASS_ARGS);
     return launch_t<float, df32, 256, kWideQF32, 1, true>(SKS_APASS_ARGS);
   }
   if (!a_f32) {

@@ -333,6 +333,96 @@ __global__ void __launch_bounds__(kSjBlockThreads) sjlt_block_kernel(const T* __
   for (uint32_t h = 0; h < m; ++h) SV::flush(Y + (long long)h * ldy + c, Ys[(size_t)h * kSjBlockThreads + tid]);
 }
 
+// Small m, float32 (m <= MR <= 64): the m partial rows of the thread's VEC
+// columns live in registers.  For a batch of 256 data rows every thread
+// expands one row's hash into a dense coefficient row w[MR] (the scaled
+// sign at the s_eff hashed rows, 0 elsewhere) in shared memory; then each data
+// row costs one load and MR * VEC FMAs against the broadcast w row, instead
+// of s_eff read-modify-writes of shared memory.  Flushed with one vector
+// atomic per partial row at the end.
+constexpr int kSjRegThreads = 256;
+template <int MR, int VEC>
+__global__ void __launch_bounds__(kSjRegThreads, MR <= 8 ? 3 : (MR <= 16 ? 2 : 1))
+    sjlt_reg_kernel(const float* __restrict__ A, long long lda, int64_t n, int d, uint32_t m, int s_eff, Key key,
+                    float* __restrict__ Y, long long ldy, int ncb, int64_t rows_per_cta) {
+  using V = typename std::conditional<VEC == 4, float4, float2>::type;
+  constexpr int kBatch = MR <= 32 ? 256 : 128;  // data rows hashed per batch (w: <= 32 KB)
+  __shared__ __align__(16) float w[kBatch][MR];
+  const int tid = threadIdx.x;
+  const int cb = blockIdx.x % ncb;
+  const int64_t r0 = (int64_t)(blockIdx.x / ncb) * rows_per_cta;
+  const int64_t r1 = min(n, r0 + rows_per_cta);
+  const int c = cb * kSjRegThreads * VEC + tid * VEC;
+  const bool cok = c < d;
+  float acc[MR][VEC];
+#pragma unroll
+  for (int r = 0; r < MR; ++r)
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[r][e] = 0.f;
+  const float inv = (float)(1.0 / sqrt((double)s_eff));
+  for (int64_t base = r0; base < r1; base += kBatch) {
+    __syncthreads();  // the previous batch's coefficient rows are consumed
+    if (tid < kBatch) {
+      float wr[MR];
+#pragma unroll
+      for (int r = 0; r < MR; ++r) wr[r] = 0.f;
+      if (base + tid < r1) {
+        uint32_t rows[kSjltMaxS];
+        float signs[kSjltMaxS];
+        sjlt_hash(key, (uint32_t)(base + tid), m, s_eff, rows, signs);
+        for (int k = 0; k < s_eff; ++k)
+#pragma unroll
+          for (int r = 0; r < MR; ++r)
+            if (rows[k] == (uint32_t)r) wr[r] = signs[k] * inv;
+      }
+#pragma unroll
+      for (int r = 0; r < MR; r += 4) *(float4*)&w[tid][r] = make_float4(wr[r], wr[r + 1], wr[r + 2], wr[r + 3]);
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)kBatch, r1 - base);
+    if (!cok) continue;
+    const float* a = A + base * lda + c;
+#pragma unroll 8
+    for (int j = 0; j < cnt; ++j) {
+      const V v = __ldcs((const V*)(a + (int64_t)j * lda));
+      const float* vv = (const float*)&v;
+#pragma unroll
+      for (int r = 0; r < MR; r += 4) {
+        const float4 wq = *(const float4*)&w[j][r];
+        const float wv[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) acc[r + t][e] = fmaf(wv[t], vv[e], acc[r + t][e]);
+      }
+    }
+  }
+  if (!cok) return;
+#pragma unroll
+  for (int r = 0; r < MR; ++r) {
+    if (r >= (int)m) break;
+    if constexpr (VEC == 4)
+      atomicAdd((float4*)(Y + (long long)r * ldy + c), make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
+    else
+      atomicAdd((float2*)(Y + (long long)r * ldy + c), make_float2(acc[r][0], acc[r][1]));
+  }
+}
+
+template <int MR, int VEC>
+sks_status sjlt_reg_launch(cudaStream_t stream, const float* A, long long lda, int64_t n, int d, int m, int s_eff,
+                           uint64_t seed, float* Y, long long ldy) {
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int ncb = (d + kSjRegThreads * VEC - 1) / (kSjRegThreads * VEC);
+  const int64_t chunks =
+      std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ((int64_t)sms * 6 + ncb - 1) / ncb));
+  const int64_t per = (n + chunks - 1) / chunks;
+  sjlt_reg_kernel<MR, VEC><<<(unsigned)(chunks * ncb), kSjRegThreads, 0, stream>>>(A, lda, n, d, (uint32_t)m, s_eff,
+                                                                                  make_key(seed), Y, ldy, ncb, per);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
 template <typename T, int VEC>
 sks_status sjlt_block_launch(cudaStream_t stream, const T* A, long long lda, int64_t n, int d, int m, int s_eff,
                              uint64_t seed, T* Y, long long ldy, size_t smem) {
@@ -462,6 +552,15 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
     // 16-byte columns only: narrower ones keep too few bytes in flight at one
     // CTA per SM, and the L2 scatter is faster there
     if constexpr (sizeof(TY) == 4) {
+      // partial rows in registers: 16-byte columns up to m = 32, 8-byte ones for m <= 64
+      const bool al8 = ((uintptr_t)A & 15) == 0 && ((uintptr_t)Y & 15) == 0;
+      if (al16 && d % 4 == 0 && lda % 4 == 0 && ldy % 4 == 0) {
+        if (m <= 8) return sjlt_reg_launch<8, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
+        if (m <= 16) return sjlt_reg_launch<16, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
+        if (m <= 32) return sjlt_reg_launch<32, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
+      }
+      if (al8 && m <= 64 && d % 2 == 0 && lda % 2 == 0 && ldy % 2 == 0)
+        return sjlt_reg_launch<64, 2>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
       if (fits(4)) return sjlt_block_launch<TY, 4>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(4));
     } else {
       if (fits(2)) return sjlt_block_launch<TY, 2>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(2));

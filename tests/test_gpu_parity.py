@@ -130,12 +130,15 @@ def test_srht_multi_pass_transform(dt, tol):
 
 @pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
 @pytest.mark.parametrize("n,d,m", [(5000, 1000, 1), (3001, 2052, 3), (4096, 64, 8), (777, 36, 13), (6000, 520, 40),
-                                   (4100, 130, 100), (3000, 100, 300)])
+                                   (4100, 130, 100), (3000, 100, 300), (20000, 1028, 32), (9000, 130, 64),
+                                   (7000, 258, 17)])
 def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
-    # small and medium m: the column-block kernel (partial rows in shared
-    # memory, 4, 2 or 1 columns per thread as m grows); d = 2052 spans three
-    # column blocks of 1024 float32 columns, the last one ragged; m = 300 is
-    # past the shared-memory limit (the L2 scatter).
+    # small and medium m: float32 partial rows in registers (8, 16, 32 rows of
+    # 4 columns, or 64 rows of 2 columns when d is not a multiple of 4), the
+    # float64 column-block kernel (partial rows in shared memory); d = 2052
+    # spans three column blocks of 1024 float32 columns, the last one ragged;
+    # n = 20000 takes several 256-row hash batches per CTA; m = 300 is past
+    # the shared-memory limit (the L2 scatter).
     rng = np.random.default_rng(n + d + m)
     A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
     sk = api().Sketch(dev(A, dt), 0.1, dev(np.ones(d)), kind="sjlt", m=m, sjlt_s=4, seed=99)

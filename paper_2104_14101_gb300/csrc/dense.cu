@@ -30,6 +30,8 @@ struct GemmArgs {
   long long ldc, sC;
   double alpha, beta;
   int lower;      // 1: only tiles with row block >= col block (C lower part)
+  int a_lower;    // op(A) lower triangular: terms k > i are zero and skipped
+  int b_lower;    // op(B) lower triangular: terms k < j are zero and skipped
   int splits;     // split-K factor
   int kchunk;     // K range per split (multiple of BK)
   T* part;        // split partials [batch*splits][M][N] when splits > 1
@@ -52,8 +54,9 @@ __global__ void __launch_bounds__(GT) gemm_kernel(GemmArgs<T> g) {
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  const int k_begin = sp * g.kchunk;
-  const int k_end = min(g.K, k_begin + g.kchunk);
+  // the K range of this split, without the terms a triangular operand makes zero
+  const int k_begin = max(sp * g.kchunk, g.b_lower ? col0 : 0);
+  const int k_end = min(min(g.K, sp * g.kchunk + g.kchunk), g.a_lower ? row0 + BM : g.K);
   for (int k0 = k_begin; k0 < k_end; k0 += BK) {
     // op(A) tile: BM x BK
 #pragma unroll
@@ -464,9 +467,11 @@ __global__ void gemv_rows_kernel(int rows, int cols, const T* __restrict__ M, lo
 template <typename T>
 sks_status gemm(cudaStream_t stream, int M, int N, int K, const T* A, long long lda, bool ta, const T* B,
                 long long ldb, bool tb, T* C, long long ldc, double alpha, double beta, bool lower, int batch,
-                long long sA, long long sB, long long sC, T* split_ws, size_t split_ws_elems) {
+                long long sA, long long sB, long long sC, T* split_ws, size_t split_ws_elems, int tri_ops) {
   if (M <= 0 || N <= 0 || batch <= 0) return SKS_OK;
   GemmArgs<T> g;
+  g.a_lower = (tri_ops & 1) ? 1 : 0;
+  g.b_lower = (tri_ops & 2) ? 1 : 0;
   g.M = M; g.N = N; g.K = K;
   g.A = A; g.lda = lda; g.sA = sA; g.ta = ta;
   g.B = B; g.ldb = ldb; g.sB = sB; g.tb = tb;
@@ -507,10 +512,10 @@ sks_status gemm(cudaStream_t stream, int M, int N, int K, const T* A, long long 
 
 template sks_status gemm<double>(cudaStream_t, int, int, int, const double*, long long, bool, const double*, long long,
                                  bool, double*, long long, double, double, bool, int, long long, long long, long long,
-                                 double*, size_t);
+                                 double*, size_t, int);
 template sks_status gemm<float>(cudaStream_t, int, int, int, const float*, long long, bool, const float*, long long,
                                 bool, float*, long long, double, double, bool, int, long long, long long, long long,
-                                float*, size_t);
+                                float*, size_t, int);
 
 template <typename T>
 sks_status transpose(cudaStream_t stream, int rows, int cols, const T* S, long long lds, T* D, long long ldd) {
@@ -651,10 +656,11 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
         double* out = X + (long long)(r0 + b) * ldx + r0;             // n2 x n1
         double* tmp = split;                                          // n2 x n1
         const size_t rest_elems = split_elems - (size_t)n2 * n1;
+        // A^{-1} and C^{-1} are lower triangular: half of each product's terms are skipped
         SKS_TRY(gemm<double>(stream, n2, n1, n1, Lb, ldh, false, Binv_A, ldx, false, tmp, n1, 1.0, 0.0, false, 1, 0,
-                             0, 0, split + (size_t)n2 * n1, rest_elems));
+                             0, 0, split + (size_t)n2 * n1, rest_elems, 2));
         SKS_TRY(gemm<double>(stream, n2, n1, n2, Cinv, ldx, false, tmp, n1, false, out, ldx, -1.0, 0.0, false, 1, 0,
-                             0, 0, split + (size_t)n2 * n1, rest_elems));
+                             0, 0, split + (size_t)n2 * n1, rest_elems, 1));
       }
     }
     return SKS_OK;
@@ -680,9 +686,9 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
       const float* Cinv = X32 + (long long)(r0 + b) * n + (r0 + b);
       float* out = X32 + (long long)(r0 + b) * n + r0;
       SKS_TRY(gemm<float>(stream, n2, n1, n1, Lb, n, false, Ainv, n, false, tmp32, n1, 1.0, 0.0, false, 1, 0, 0, 0,
-                          tmp32 + (size_t)n2 * n1, rest32));
+                          tmp32 + (size_t)n2 * n1, rest32, 2));
       SKS_TRY(gemm<float>(stream, n2, n1, n2, Cinv, n, false, tmp32, n1, false, out, n, -1.0, 0.0, false, 1, 0, 0, 0,
-                          tmp32 + (size_t)n2 * n1, rest32));
+                          tmp32 + (size_t)n2 * n1, rest32, 1));
     }
   }
   f32_to_f64_mat_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(n, X32, n, X, ldx);

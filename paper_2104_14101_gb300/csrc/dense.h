@@ -7,11 +7,13 @@ namespace sks {
 
 // C = alpha * op(A) op(B) + beta * C, row-major, batched (strides in
 // elements); lower = only C's lower triangle is written.  split_ws (optional)
-// enables split-K with a deterministic float64 reduction.
+// enables split-K with a deterministic float64 reduction.  tri_ops: bit 0 =
+// op(A) is lower triangular, bit 1 = op(B) is lower triangular (their zero
+// terms are skipped; the sum over the others keeps its order).
 template <typename T>
 sks_status gemm(cudaStream_t stream, int M, int N, int K, const T* A, long long lda, bool ta, const T* B,
                 long long ldb, bool tb, T* C, long long ldc, double alpha, double beta, bool lower, int batch,
-                long long sA, long long sB, long long sC, T* split_ws, size_t split_ws_elems);
+                long long sA, long long sB, long long sC, T* split_ws, size_t split_ws_elems, int tri_ops = 0);
 
 template <typename T>
 sks_status transpose(cudaStream_t stream, int rows, int cols, const T* S, long long lds, T* D, long long ldd);

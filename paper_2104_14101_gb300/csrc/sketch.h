@@ -24,9 +24,12 @@ sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64
                            int m_add, T* Y, long long ldy, T* gbuf, size_t gbuf_elems, T* split_ws,
                            size_t split_elems, bool rademacher = false);
 
-// Y (m x d) = S A for the SJLT with s nonzeros per column.
+// Y (m x d) = S A for the SJLT with s nonzeros per column.  sj_ws (optional,
+// sjlt_gather_ws_elems words) lets larger m gather each sketch row's data rows
+// instead of scattering them.
 template <typename TA, typename TY>
 sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n, int d, int m, int s, uint64_t seed,
-                     TY* Y, long long ldy);
+                     TY* Y, long long ldy, uint32_t* sj_ws = nullptr, size_t sj_ws_elems = 0);
+size_t sjlt_gather_ws_elems(int64_t n, int64_t m_max, int s);
 
 }  // namespace sks

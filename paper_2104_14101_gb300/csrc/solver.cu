@@ -41,6 +41,8 @@ struct sks_sketch {
   float* tcpart = nullptr;
   size_t tcpart_elems = 0;
   bool tc_ready = false;
+  uint32_t* sj = nullptr;  // SJLT buckets for the gathering kernel (larger m)
+  size_t sj_elems = 0;
   sks::DevStatus* st = nullptr;
   double scale2() const { return kind == SKS_SJLT ? 1.0 : 1.0 / (double)m; }
 };
@@ -155,11 +157,13 @@ inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)std::max
 // ---------------------------------------------------------------- sketch
 struct SketchSizes {
   size_t b_elems = 0, y_elems = 0, g_elems = 0, split_elems = 0;
+  size_t sj_elems = 0;  // SJLT buckets (counts, offsets, entries) of the gathering kernel
   size_t tc_elems = 0, tcpart_elems = 0, cmax_elems = 0;  // float32 Gaussian (tensor cores)
 };
 
-SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max) {
+SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s) {
   SketchSizes z;
+  if (kind == SKS_SJLT && p->dtype == SKS_F64) z.sj_elems = sjlt_gather_ws_elems(p->n, m_max, std::max(1, sjlt_s));
   const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
   if (kind == SKS_SRHT) z.b_elems = (size_t)n_pad * p->d;
   z.y_elems = (size_t)m_max * p->d;
@@ -183,8 +187,8 @@ int64_t resolve_m_max(const sks_problem* p, sks_kind kind, int64_t m_max) {
   return std::min(m_max, cap);
 }
 
-size_t sketch_ws_bytes(const sks_problem* p, sks_kind kind, int64_t m_max) {
-  const SketchSizes z = sketch_sizes(p, kind, m_max);
+size_t sketch_ws_bytes(const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s) {
+  const SketchSizes z = sketch_sizes(p, kind, m_max, sjlt_s);
   const size_t esz = p->dtype == SKS_F32 ? 4 : 8;
   Carver c(nullptr, 0);
   c.take<DevStatus>(1);
@@ -196,6 +200,7 @@ size_t sketch_ws_bytes(const sks_problem* p, sks_kind kind, int64_t m_max) {
   c.take<float>(z.tcpart_elems);
   c.take<char>(z.g_elems * esz);
   c.take<char>(z.split_elems * esz);
+  c.take<uint32_t>(z.sj_elems);
   return c.used + 256;
 }
 
@@ -210,7 +215,7 @@ sks_status sketch_init(sks_sketch* s, const sks_problem* p, sks_kind kind, int64
   s->d = (int)p->d;
   s->f32 = p->dtype == SKS_F32;
   s->n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
-  const SketchSizes z = sketch_sizes(p, kind, m_max);
+  const SketchSizes z = sketch_sizes(p, kind, m_max, sjlt_s);
   const size_t esz = s->f32 ? 4 : 8;
   Carver c(ws, ws_bytes);
   DevStatus* own = c.take<DevStatus>(1);
@@ -227,6 +232,8 @@ sks_status sketch_init(sks_sketch* s, const sks_problem* p, sks_kind kind, int64
   s->cmax = c.take<unsigned>(z.cmax_elems);
   s->tcpart = c.take<float>(z.tcpart_elems);
   s->tcpart_elems = z.tcpart_elems;
+  s->sj = c.take<uint32_t>(z.sj_elems);
+  s->sj_elems = z.sj_elems;
   s->tc_ready = false;
   if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "sketch workspace too small");
   if (z.b_elems == 0) s->B = nullptr;
@@ -256,7 +263,7 @@ sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
     SKS_TRY(gaussian_extend<T>(stream, A, p.lda, p.n, d, s->seed, (int)s->m, (int)(new_m - s->m), Y, s->ldy,
                                (T*)s->gbuf, s->gbuf_elems, (T*)s->split, s->split_elems, s->kind == SKS_RADEMACHER));
   } else {
-    SKS_TRY(sjlt_form<T, T>(stream, A, p.lda, p.n, d, (int)new_m, s->s, s->seed, Y, s->ldy));
+    SKS_TRY(sjlt_form<T, T>(stream, A, p.lda, p.n, d, (int)new_m, s->s, s->seed, Y, s->ldy, s->sj, s->sj_elems));
   }
   s->m = new_m;
   return SKS_OK;
@@ -648,7 +655,7 @@ sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_
   const int64_t n1 = std::max<int64_t>(p->n, 1);
   w.partials = c.take<char>(apass_workspace_bytes(n1, p->d, 1, f32, mixed));
   w.partials64 = c.take<char>(mixed ? apass_workspace_bytes(n1, p->d, 1, f32, false) : 0);
-  w.sketch_bytes = sketch_ws_bytes(p, o->kind, m_max);
+  w.sketch_bytes = sketch_ws_bytes(p, o->kind, m_max, o->sjlt_s);
   w.sketch_ws = c.take<char>(w.sketch_bytes);
   w.precond_bytes = precond_ws_bytes(p, m_max);
   w.precond_ws = c.take<char>(w.precond_bytes);
@@ -1314,8 +1321,7 @@ extern "C" sks_status sks_sketch_workspace_size(const sks_problem* p, sks_kind k
                                                 size_t* bytes) {
   SKS_TRY(validate_problem(p));
   if (!bytes) return fail(SKS_ERR_INVALID_ARG, "bytes is NULL");
-  (void)sjlt_s;
-  *bytes = sketch_ws_bytes(p, kind, resolve_m_max(p, kind, m_max));
+  *bytes = sketch_ws_bytes(p, kind, resolve_m_max(p, kind, m_max), sjlt_s);
   return SKS_OK;
 }
 
@@ -1330,7 +1336,8 @@ extern "C" sks_status sks_sketch_create(sks_sketch** out, const sks_problem* p, 
   if (sjlt_s < 1 || sjlt_s > kSjltMaxS) return fail(SKS_ERR_INVALID_ARG, "sjlt_s must be in [1, 16]");
   const int64_t mm = resolve_m_max(p, kind, m_max);
   if (m_init < 1 || m_init > mm) return fail(SKS_ERR_INVALID_ARG, "m_init must be in [1, m_max]");
-  if (!ws || ws_bytes < sketch_ws_bytes(p, kind, mm)) return fail(SKS_ERR_WORKSPACE, "sketch workspace too small");
+  if (!ws || ws_bytes < sketch_ws_bytes(p, kind, mm, sjlt_s))
+    return fail(SKS_ERR_WORKSPACE, "sketch workspace too small");
   sks_sketch* s = new (std::nothrow) sks_sketch();
   if (!s) return fail(SKS_ERR_INVALID_ARG, "host allocation failed");
   cudaStream_t st = (cudaStream_t)stream;

@@ -151,10 +151,12 @@ def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
 @pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
 @pytest.mark.parametrize("n,d,m,s", [(3001, 1100, 257, 4), (5000, 600, 1024, 4), (9000, 64, 4096, 1),
                                      (1000, 2048, 300, 16)])
-def test_sjlt_large_sketch_scatter(dt, tol, n, d, m, s):
-    # larger m: the column-tiled L2 scatter; d = 1100 (float32) and 600
-    # (float64) leave a ragged last column tile, n = 9000 rows on m = 4096 and
-    # 8192 sketch rows collide often, s = 16 is the largest column sparsity.
+def test_sjlt_large_sketch(dt, tol, n, d, m, s):
+    # larger m: float64 rows of 16 bytes gather per-sketch-row buckets of data
+    # rows (warps over chunks of the bucket-ordered entries), float32 scatters
+    # with vector atomics; d = 1100 (float32) and 600 (float64) leave a ragged
+    # last column block, n = 9000 rows on m = 4096 and 8192 sketch rows leave
+    # many buckets empty or with one row, s = 16 is the largest sparsity.
     rng = np.random.default_rng(n + d + m + s)
     A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
     sk = api().Sketch(dev(A, dt), 0.1, dev(np.ones(d)), kind="sjlt", m=m, sjlt_s=s, seed=31)

@@ -76,13 +76,18 @@ WORKLOADS = {
                desc="256 independent problems, n log-uniform in [2^11, 2^16], d log-uniform in [32, 1024], "
                     "n >= 4d, sigma_j = 0.9^j or 1/(1+j), nu log-uniform in [1e-4, 1e-1], Lambda = I, SRHT, "
                     "adaptive PCG to 1e-8, batched (one captured round replayed) vs one solve at a time"),
-    # the paper's experiment sizes: mixed form only (the float64 copy and its SRHT would add ~120 GB)
-    "P-d7000": dict(config="P", d=7000, method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=0, tol=1e-8,
+    # the paper's experiment sizes: mixed form only (the float64 copy and its SRHT would add ~120 GB);
+    # m capped at 2^15 (the sketch and its float64 copy are m_max x d)
+    "P-d7000": dict(config="P", d=7000, method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=1 << 15, tol=1e-8,
                     precision="mixed", desc="paper-scale synthetic: n=2^19, d=7000, sigma_j=0.995^j, nu=1e-2, SRHT, "
                                             "mixed form, tol 1e-8"),
-    "P-d14000": dict(config="P", method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=0, tol=1e-8,
+    "P-d14000": dict(config="P", method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=1 << 15, tol=1e-8,
                      precision="mixed", desc="paper-scale synthetic: n=2^19, d=14000, sigma_j=0.995^j, nu=1e-2, "
                                              "SRHT, mixed form, tol 1e-8"),
+    # more columns than rows: solved through the dual (eq. 2), the OVA-Lung shape of Section 6
+    "D": dict(config="D", dual=True, method="pcg", kind="srht", m_init=1, m_max=0, tol=1e-10, precision="plain",
+              desc="dual formulation (eq. 2), adaptive PCG, SRHT, float64: n=1545 < d=10936, sigma_j=0.995^j, "
+                   "nu=1e-2, Lambda=I, b ~ N(0,1), tol 1e-10 on the dual"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -194,17 +199,35 @@ def cpu_cores():
 
 
 def oracle_solve(wl, A, b, nu, lam):
-    """The CPU oracle's adaptive solve, as it stands (test infrastructure)."""
+    """The CPU oracle's adaptive solve, as it stands (test infrastructure); for
+    a dual workload the oracle solves eq. (2) and maps back to x."""
     from oracle import solvers as O
     fn = O.adaptive_pcg if wl["method"] == "pcg" else O.adaptive_ihs
     kw = dict(kind=wl["kind"], seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"],
               sjlt_s=wl.get("sjlt_s", 1))
+    if wl.get("dual"):
+        D, bd, nud, lamd = O.dual_problem(A, b, nu, lam)
+        w, st, tr = fn(D, bd, nud, lamd, **kw)
+        return O.primal_from_dual(A, b, nu, lam, w), st, tr
     return fn(A, b, nu, lam, **kw)
+
+
+def make_workload_problem(wl, device):
+    import synthetic
+    if wl.get("dual"):
+        return synthetic.make_wide_problem_torch(wl["config"], seed=0, device=device, n=wl.get("n"), d=wl.get("d"))
+    return synthetic.make_problem_torch(wl["config"], seed=0, device=device, n=wl.get("n"), d=wl.get("d"))
+
+
+def host64(A, rows=None):
+    """float64 NumPy copy of (the first rows of) a device matrix (a float32 A is upcast exactly)."""
+    T = A if rows is None else A[:rows]
+    return T.cpu().to(torch.float64).numpy()
 
 
 def oracle_sample(wl, A64, rows, nu, lam):
     """One timed oracle solve on the first `rows` rows of A (b = A_s^T y, y ~ N(0,1)); returns ms."""
-    A_np = A64[:rows].cpu().numpy() if torch.is_tensor(A64) else A64[:rows]
+    A_np = host64(A64, rows) if torch.is_tensor(A64) else A64[:rows]
     b_np = A_np.T @ np.random.default_rng(0).standard_normal(rows)
     t0 = time.perf_counter()
     oracle_solve(wl, A_np, b_np, nu, lam)
@@ -268,7 +291,7 @@ def run_reference(args, wl, world, rank):
         return None
     import synthetic
     gdev = "cuda" if torch.cuda.is_available() else "cpu"
-    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=gdev, n=wl.get("n"), d=wl.get("d"))
+    prob = make_workload_problem(wl, gdev)
     A = prob["A64"].cpu().numpy()
     b = prob["b"][:, 0].cpu().numpy()
     lam = prob["lam"].cpu().numpy()
@@ -325,10 +348,14 @@ def run_ours(args, wl, world, rank, local):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     lib = _lib.load()
-    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev, n=wl.get("n"), d=wl.get("d"))
+    prob = make_workload_problem(wl, dev)
     mixed = wl["precision"] == "mixed"
     A64 = prob["A64"]
     A = prob["A32"] if mixed else A64
+    if mixed and not wl.get("compare_plain"):
+        # no float64 solve on the device: the exact upcast is made on the host when needed
+        del prob["A64"]
+        A64 = A
     b = prob["b"][:, 0].contiguous()
     lam = prob["lam"]
     nu = prob["nu"]
@@ -337,7 +364,8 @@ def run_ours(args, wl, world, rank, local):
                  seed=0, sjlt_s=wl.get("sjlt_s", 1), precision=wl["precision"], max_iter=5000)
     if not mixed:
         del prob
-    solver = sks.Solver(A, b, nu, lam, **sopts)
+    Make = sks.DualSolver if wl.get("dual") else sks.Solver
+    solver = Make(A, b, nu, lam, **sopts)
     for _ in range(args.warmup):
         solver.solve()
     torch.cuda.synchronize()
@@ -355,7 +383,7 @@ def run_ours(args, wl, world, rank, local):
     e0.record(stream)
     x = None
     for _ in range(args.steps):
-        x, st, _ = solver.solve()
+        x, st = solver.solve()[:2]
         stats.append(st)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
@@ -410,7 +438,7 @@ def run_ours(args, wl, world, rank, local):
     A_d.copy_(A_h)
     b_d.copy_(b_h)
     lam_d.copy_(lam_h)
-    solver_e2e = sks.Solver(A_d, b_d, nu, lam_d, **sopts)
+    solver_e2e = Make(A_d, b_d, nu, lam_d, **sopts)
     solver_e2e.solve()
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
@@ -423,7 +451,7 @@ def run_ours(args, wl, world, rank, local):
         A_d.copy_(A_h, non_blocking=True)
         b_d.copy_(b_h, non_blocking=True)
         lam_d.copy_(lam_h, non_blocking=True)
-        xe, _, _ = solver_e2e.solve()
+        xe = solver_e2e.solve()[0]
         x_h.copy_(xe, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
@@ -463,7 +491,7 @@ def run_ours(args, wl, world, rank, local):
         "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": wl["config"] + ": " + wl["desc"], "method": "adaptive_" + wl["method"],
                    "n": n, "d": d, "kind": wl["kind"], "precision": wl["precision"],
-                   "l2": "inputs larger than L2 (A = %.2f GiB)" % (A.numel() * 8 / 2 ** 30),
+                   "l2": "inputs larger than L2 (A = %.2f GiB)" % (A.numel() * A.element_size() / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
         "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -479,7 +507,7 @@ def run_ours(args, wl, world, rank, local):
         lam_np = lam_h.numpy()
         rows = wl.get("cpu_rows") or n
         if rows >= n:
-            A_np = A64.cpu().numpy() if mixed else A_h.numpy()
+            A_np = host64(A64) if mixed else A_h.numpy()
             b_np = b_h.numpy()
             t0 = time.perf_counter()
             xo, so, _ = oracle_solve(wl, A_np, b_np, nu, lam_np)
@@ -499,7 +527,7 @@ def run_ours(args, wl, world, rank, local):
                                               "(%.0f ms, %.0f ms), extrapolated to n with t(n) = f + g n"
                                               % (rows // 2, rows, n, t_small, t_large)}
             # accuracy of the GPU result: the oracle's relative H-error from A itself (one float64 pass)
-            A_all = A64.cpu().numpy()
+            A_all = host64(A64)
             xs = O.direct_solve(A_all, b_h.numpy(), nu, lam_np)
             line["rel_err_H_vs_oracle"] = O.rel_err_H(A_all, nu, lam_np, x.cpu().numpy(), xs)
     return line if rank == 0 else None

@@ -256,6 +256,28 @@ sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opts* o, doubl
                                   void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Dual formulation (eq. 2), for n < d (more columns than rows): the dual
+ *   w* = argmin 1/2 <w, (A~ A~^T + nu^2 I_n) w> - (A Lambda^{-1} b)^T w,
+ *   A~ = A Lambda^{-1/2},
+ * is itself an instance of eq. 1 with the d x n data matrix Lambda^{-1/2} A^T,
+ * Lambda = I_n and right-hand side A Lambda^{-1} b; it is solved by adaptive
+ * PCG (Algorithm 2) or adaptive IHS (Algorithm 1) exactly as the primal, and
+ * x = Lambda^{-1} (b - A^T w) / nu^2 is returned (the optimality condition of
+ * eq. 1 written with w = (A Lambda^{-1} A^T + nu^2 I)^{-1} A Lambda^{-1} b).
+ * Same problem description, options, x (d x k; its input is ignored: the dual
+ * starts at w = 0), stats (of the dual solve) and errors as
+ * sks_adaptive_pcg_solve; o->tol is the dual's relative H-error target, and
+ * the primal error obeys ||x - x*||_H <= ||H_dual (w - w*)||_2 / nu^2.  The
+ * workspace (sks_dual_workspace_size) holds the dual matrix, a transposed copy
+ * of A of the same size.  Any n, d within the A-pass limits (the dual's d is n).
+ * ------------------------------------------------------------------------- */
+sks_status sks_dual_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes);
+sks_status sks_dual_pcg_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                              void* ws, size_t ws_bytes, void* stream);
+sks_status sks_dual_ihs_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Non-adaptive solvers: the baselines of Section 6 and the Polyak-IHS of
  * Appendix A.  The sketch size stays at m = min(m_init, m_max) (Section 6
  * compares with PCG at m = 2d); no improvement test rejects a step.

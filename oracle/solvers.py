@@ -359,6 +359,27 @@ def adaptive_ihs(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
 # Theory quantities (test tools)
 # ----------------------------------------------------------------------------
 
+# ----------------------------------------------------------------------------
+# Dual formulation (eq. 2)
+# ----------------------------------------------------------------------------
+
+def dual_problem(A, b, nu, lam):
+    """Eq. (2) as an instance of eq. (1): data matrix Lambda^{-1/2} A^T (d x n),
+    Lambda = I_n, right-hand side A Lambda^{-1} b, the same nu."""
+    lam = np.asarray(lam, dtype=np.float64)
+    D = (A / np.sqrt(lam)[None, :]).T
+    bd = A @ (b / _col(lam, b))
+    return D, bd, nu, np.ones(A.shape[0])
+
+
+def primal_from_dual(A, b, nu, lam, w):
+    """x = Lambda^{-1} (b - A^T w) / nu^2: the primal optimum from the dual one
+    (eq. 1's optimality condition H x = b with w = (A Lambda^{-1} A^T + nu^2
+    I)^{-1} A Lambda^{-1} b, i.e. the Woodbury identity)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    return (b - A.T @ w) / (_col(lam, b) * nu ** 2)
+
+
 def inv_sqrt_psd(M):
     w, Q = np.linalg.eigh(M)
     return (Q / np.sqrt(w)[None, :]) @ Q.T

@@ -7,12 +7,14 @@ all in hand-written CUDA behind the C ABI of include/sks.h.
 from . import _lib  # noqa: F401
 from .api import (  # noqa: F401
     BatchSolver,
+    DualSolver,
     Preconditioner,
     Sketch,
     SketchSolve,
     Solver,
     adaptive_ihs,
     adaptive_pcg,
+    dual_solve,
     fixed_solve,
     hess_apply,
     make_problem,

@@ -91,6 +91,11 @@ _SIGS = {
                                          C.c_void_p]),
     "sks_adaptive_ihs_solve": (C.c_int, [P(Problem), P(Opts), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t,
                                          C.c_void_p]),
+    "sks_dual_workspace_size": (C.c_int, [P(Problem), P(Opts), P(C.c_size_t)]),
+    "sks_dual_pcg_solve": (C.c_int, [P(Problem), P(Opts), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t,
+                                     C.c_void_p]),
+    "sks_dual_ihs_solve": (C.c_int, [P(Problem), P(Opts), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t,
+                                     C.c_void_p]),
     "sks_fixed_solve": (C.c_int, [C.c_int, P(Problem), P(Opts), C.c_void_p, P(Stats), C.c_void_p, C.c_size_t,
                                   C.c_void_p]),
     "sks_adjoint": (C.c_int, [P(Problem), P(Opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,

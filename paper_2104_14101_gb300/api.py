@@ -297,6 +297,43 @@ def adaptive_ihs(A, b, nu, lam, x0=None, trace_cap=0, **opts):
     return Solver(A, b, nu, lam, method="ihs", trace_cap=trace_cap, **opts).solve(x0)
 
 
+class DualSolver:
+    """Eq. (2): the n x n dual problem (for n < d) solved by adaptive PCG or
+    IHS on the GPU and the primal x = Lambda^{-1}(b - A^T w)/nu^2 recovered;
+    sizes and holds the workspace once (``sks_dual_*_solve``)."""
+
+    def __init__(self, A, b, nu, lam, method="pcg", **opts):
+        self._lib = L.load()
+        if method not in ("pcg", "ihs"):
+            raise ValueError("unknown method %r" % method)
+        self.method = method
+        self.problem, self._keep = make_problem(A, b, nu, lam)
+        self.opts = options(**opts)
+        nb = C.c_size_t()
+        L.check(self._lib.sks_dual_workspace_size(C.byref(self.problem), C.byref(self.opts), C.byref(nb)))
+        self.ws = _workspace(nb.value, A.device)
+        self.device = A.device
+        self.d, self.k = int(self.problem.d), int(self.problem.k)
+
+    def solve(self, check=True):
+        xcm = torch.empty(self.k, self.d, dtype=torch.float64, device=self.device)
+        st = L.Stats()
+        fn = self._lib.sks_dual_pcg_solve if self.method == "pcg" else self._lib.sks_dual_ihs_solve
+        status = fn(C.byref(self.problem), C.byref(self.opts), _ptr(xcm), C.byref(st), _ptr(self.ws),
+                    self.ws.numel(), _stream(self.device))
+        if check and status != L.OK:
+            L.check(status)
+        x = xcm.t()
+        stats = st.as_dict()
+        stats["status_name"] = L.STATUS_NAMES.get(status, status)
+        return (x[:, 0] if self.k == 1 else x.contiguous()), stats
+
+
+def dual_solve(A, b, nu, lam, method="pcg", check=True, **opts):
+    """Eq. (2) on the GPU (see ``DualSolver``); returns (x, stats of the dual solve)."""
+    return DualSolver(A, b, nu, lam, method=method, **opts).solve(check=check)
+
+
 def fixed_solve(A, b, nu, lam, method="fixed-pcg", x0=None, check=True, **opts):
     """Non-adaptive solvers on the GPU (sketch size m_init): "fixed-pcg",
     "fixed-ihs", "polyak-ihs" (Appendix A) or "cg" (no preconditioner);

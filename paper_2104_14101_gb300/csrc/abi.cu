@@ -52,6 +52,20 @@ extern "C" sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opt
   return adaptive_solve(1, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+extern "C" sks_status sks_dual_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes) {
+  return dual_workspace_size(p, o, bytes);
+}
+
+extern "C" sks_status sks_dual_pcg_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  return dual_solve(0, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" sks_status sks_dual_ihs_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  return dual_solve(1, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);
+}
+
 extern "C" sks_status sks_fixed_solve(sks_fixed_method method, const sks_problem* p, const sks_opts* o, double* x,
                                       sks_stats* stats, void* ws, size_t ws_bytes, void* stream) {
   return fixed_solve((int)method, p, o, x, stats, ws, ws_bytes, (cudaStream_t)stream);

@@ -108,6 +108,10 @@ sks_status solve_workspace_size(const sks_problem* p, const sks_opts* o, size_t*
 // method 0: adaptive PCG (Algorithm 2); 1: adaptive IHS (Algorithm 1)
 sks_status adaptive_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
                           size_t ws_bytes, cudaStream_t stream);
+// Dual formulation (eq. 2): method 0 adaptive PCG, 1 adaptive IHS on the dual problem.
+sks_status dual_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes);
+sks_status dual_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
+                      size_t ws_bytes, cudaStream_t stream);
 // method 0: PCG, 1: IHS, 2: Polyak-IHS (all with H_S fixed at m = m_init), 3: CG (H_S = I)
 sks_status fixed_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
                        size_t ws_bytes, cudaStream_t stream);

@@ -143,6 +143,37 @@ __global__ void scale_cols_kernel(int rows, int cols, const double* a, long long
   const int r = (int)(e / cols), c = (int)(e % cols);
   b[(long long)r * ldb + c] = a[(long long)r * lda + c] / lam[c];
 }
+// Dual data matrix of eq. (2): D = Lambda^{-1/2} A^T (d x n row-major, ldd), by
+// 32 x 32 shared-memory tiles (coalesced reads of A's rows and writes of D's rows).
+template <typename T>
+__global__ void dual_transpose_kernel(int64_t n, int d, const T* __restrict__ A, long long lda,
+                                      const double* __restrict__ lam, T* __restrict__ D, long long ldd) {
+  __shared__ T tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = i0 + r;
+    const int j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < n && j < d) ? A[i * lda + j] : T(0);
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r;
+    const int64_t i = i0 + threadIdx.x;
+    if (j < d && i < n) D[(long long)j * ldd + i] = (T)((double)tile[threadIdx.x][r] / sqrt(lam[j]));
+  }
+}
+__global__ void fill_kernel(int64_t count, double v, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = v;
+}
+// primal solution from the dual one: x = Lambda^{-1} (b - A^T w) / nu^2, with
+// t = D w = Lambda^{-1/2} A^T w, so (A^T w)_j = sqrt(lambda_j) t_j
+__global__ void dual_recover_kernel(int d, const double* __restrict__ b, const double* __restrict__ t,
+                                    const double* __restrict__ lam, double nu2, double* __restrict__ x) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) x[j] = (b[j] - sqrt(lam[j]) * t[j]) / (nu2 * lam[j]);
+}
 __global__ void scale_rows_out_kernel(int rows, int cols, const void* Y, int f32, long long ldy, double scale,
                                       double* out) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1185,6 +1216,112 @@ sks_status adaptive_solve_impl(Method method, const sks_problem* prob, const sks
   return result;
 }
 
+// ---------------------------------------------------------------- dual formulation (eq. 2)
+// Workspace: D = Lambda^{-1/2} A^T (d x ldd in A's precision), b_dual = A
+// Lambda^{-1} b (n x k), ones (n), w (n x k), t (d), then the workspace of the
+// adaptive solve of the dual problem (n_dual = d rows, d_dual = n columns).
+struct DualWs {
+  DevStatus* st;
+  void* D;
+  long long ldd;
+  double *bd, *ones, *w, *t;
+  void* inner;
+  size_t inner_bytes;
+};
+
+sks_problem dual_problem(const sks_problem* p, const DualWs& L) {
+  sks_problem q = *p;
+  q.n = p->d;
+  q.d = p->n;
+  q.lda = L.ldd;
+  q.A = L.D;
+  q.b = L.bd;
+  q.lambda_diag = L.ones;
+  return q;
+}
+
+sks_status dual_layout(const sks_problem* p, const sks_opts* o, void* ws, size_t ws_bytes, DualWs* L, size_t* total) {
+  const size_t esz = p->dtype == SKS_F32 ? 4 : 8;
+  const long long per16 = (long long)(16 / esz);
+  DualWs w;
+  w.ldd = (p->n + per16 - 1) / per16 * per16;  // 16-byte rows for the tensor copies
+  Carver c(ws, ws_bytes);
+  w.st = c.take<DevStatus>(1);
+  w.D = c.take<char>((size_t)p->d * (size_t)w.ldd * esz);
+  w.bd = c.take<double>((size_t)p->n * (size_t)p->k);
+  w.ones = c.take<double>((size_t)p->n);
+  w.w = c.take<double>((size_t)p->n * (size_t)p->k);
+  w.t = c.take<double>((size_t)p->d);
+  sks_problem q = dual_problem(p, w);
+  size_t inner = 0;
+  SKS_TRY(solve_layout(&q, o, nullptr, 0, nullptr, &inner));
+  w.inner_bytes = inner;
+  w.inner = c.take<char>(inner);
+  if (total) *total = c.used + 256;
+  if (L) *L = w;
+  if (ws && !c.ok()) return fail(SKS_ERR_WORKSPACE, "dual workspace too small");
+  return SKS_OK;
+}
+
+sks_status dual_solve_impl(Method method, const sks_problem* prob, const sks_opts* o, double* x_io, sks_stats* stats,
+                           void* ws, size_t ws_bytes, cudaStream_t stream) {
+  SKS_TRY(check_opts(prob, o, x_io));
+  if (prob->n < 1) return fail(SKS_ERR_INVALID_ARG, "the dual formulation needs n >= 1");
+  size_t need = 0;
+  SKS_TRY(dual_layout(prob, o, nullptr, 0, nullptr, &need));
+  if (!ws || ws_bytes < need) return fail(SKS_ERR_WORKSPACE, "dual workspace too small (need " + std::to_string(need) + " bytes)");
+  DualWs L;
+  SKS_TRY(dual_layout(prob, o, ws, ws_bytes, &L, nullptr));
+  const int d = (int)prob->d;
+  const int64_t n = prob->n;
+  const bool f32 = prob->dtype == SKS_F32;
+  // Lambda >= I is checked by the inner solve on the dual's Lambda = I only: check the primal one here
+  DevStatus* st = L.st;
+  SKS_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevStatus), stream));
+  check_lambda_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->lambda_diag, st);
+  note_launch();
+  SKS_TRY(read_status(st, stream, "input check"));
+  dim3 tg((unsigned)((n + 31) / 32), (unsigned)((d + 31) / 32));
+  if (f32)
+    dual_transpose_kernel<float><<<tg, dim3(32, 8), 0, stream>>>(n, d, (const float*)prob->A, prob->lda,
+                                                                 prob->lambda_diag, (float*)L.D, L.ldd);
+  else
+    dual_transpose_kernel<double><<<tg, dim3(32, 8), 0, stream>>>(n, d, (const double*)prob->A, prob->lda,
+                                                                  prob->lambda_diag, (double*)L.D, L.ldd);
+  note_launch();
+  fill_kernel<<<blocks_for(n), 256, 0, stream>>>(n, 1.0, L.ones);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  // b_dual = A Lambda^{-1} b, column by column (row dots of A)
+  for (int64_t c = 0; c < prob->k; ++c) {
+    if (f32)
+      SKS_TRY(gemv_rows<float>(stream, (int)n, d, (const float*)prob->A, prob->lda, 0, prob->b + c * d,
+                               prob->lambda_diag, 1.0, L.bd + c * n, 0, nullptr, nullptr, 0.0));
+    else
+      SKS_TRY(gemv_rows<double>(stream, (int)n, d, (const double*)prob->A, prob->lda, 0, prob->b + c * d,
+                                prob->lambda_diag, 1.0, L.bd + c * n, 0, nullptr, nullptr, 0.0));
+  }
+  SKS_CUDA_TRY(cudaMemsetAsync(L.w, 0, (size_t)n * prob->k * sizeof(double), stream));
+  const sks_problem q = dual_problem(prob, L);
+  const sks_status r = adaptive_solve_impl(method, &q, o, L.w, stats, L.inner, L.inner_bytes, stream);
+  if (r != SKS_OK && r != SKS_ERR_NO_CONVERGENCE) return r;
+  // x = Lambda^{-1} (b - A^T w) / nu^2
+  for (int64_t c = 0; c < prob->k; ++c) {
+    if (f32)
+      SKS_TRY(gemv_rows<float>(stream, d, (int)n, (const float*)L.D, L.ldd, 0, L.w + c * n, nullptr, 1.0, L.t, 0,
+                               nullptr, nullptr, 0.0));
+    else
+      SKS_TRY(gemv_rows<double>(stream, d, (int)n, (const double*)L.D, L.ldd, 0, L.w + c * n, nullptr, 1.0, L.t, 0,
+                                nullptr, nullptr, 0.0));
+    dual_recover_kernel<<<(d + 255) / 256, 256, 0, stream>>>(d, prob->b + c * d, L.t, prob->lambda_diag,
+                                                              prob->nu * prob->nu, x_io + c * d);
+    note_launch();
+  }
+  SKS_CUDA_TRY(cudaGetLastError());
+  SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+  return r;
+}
+
 sks_status adjoint_impl(const sks_problem* prob, const sks_opts* o, const double* x, const double* g, double* db,
                         void* dA, long long ldda, double* dnu, double* dlambda, sks_stats* stats, void* ws,
                         size_t ws_bytes, cudaStream_t stream) {
@@ -1249,6 +1386,17 @@ sks_status fixed_solve(int method, const sks_problem* p, const sks_opts* o, doub
   static const Method kMethods[4] = {PCG, IHS, POLYAK, CG};
   if (method < 0 || method > 3) return fail(SKS_ERR_INVALID_ARG, "bad fixed-sketch method");
   return adaptive_solve_impl(kMethods[method], p, o, x, stats, ws, ws_bytes, stream, true);
+}
+
+sks_status dual_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes) {
+  SKS_TRY(validate_problem(p));
+  if (!o || !bytes) return fail(SKS_ERR_INVALID_ARG, "NULL argument");
+  return dual_layout(p, o, nullptr, 0, nullptr, bytes);
+}
+
+sks_status dual_solve(int method, const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats, void* ws,
+                      size_t ws_bytes, cudaStream_t stream) {
+  return dual_solve_impl(method == 0 ? PCG : IHS, p, o, x, stats, ws, ws_bytes, stream);
 }
 
 sks_status adjoint(const sks_problem* p, const sks_opts* o, const double* x, const double* g, double* db, void* dA,

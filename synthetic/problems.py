@@ -35,6 +35,10 @@ CONFIGS = {
     # the paper's synthetic experiments (Section 6): n up to 2^19, d 7000 / 14000, sigma_j = 0.995^j
     "P": dict(n=1 << 19, d=14000, decay="geom0.995", nu=1e-2, lam="identity", rhs="Aty", k=1,
               dtype="f32", kind="srht", m_init=1, tol=1e-8),
+    # more columns than rows (solved through the dual, eq. 2): the shape of the paper's OVA-Lung
+    # experiment (Section 6), sigma_j = 0.995^j over the n nonzero singular values
+    "D": dict(n=1545, d=10936, decay="geom0.995", nu=1e-2, lam="identity", rhs="gauss", k=1,
+              dtype="f64", kind="srht", m_init=1, tol=1e-10),
     # one member of the uneven batch; n, d, decay and nu come from batched_specs
     "C5": dict(n=4096, d=128, decay="geom0.9", nu=1e-2, lam="identity", rhs="Aty", k=1,
                dtype="f64", kind="srht", m_init=1, tol=1e-8),
@@ -191,6 +195,34 @@ def make_problem_torch(config="C2", seed=0, device="cuda", n=None, d=None, nu=No
         b = A.T @ y
     out["b"] = b
     return out
+
+
+def make_wide_problem_torch(config="D", seed=0, device="cuda", n=None, d=None, nu=None):
+    """n < d: A = U diag(sigma) V^T with U (n x n) from the QR of a seeded
+    Gaussian (host, float64) and V (d x n) the CholeskyQR factor of a seeded
+    d x n Gaussian on the device; sigma has n entries; b ~ N(0, 1)^d.  Returns
+    the dict of ``make_problem_torch`` (A64, b (d x 1), lam, nu)."""
+    import torch
+
+    cfg = dict(CONFIGS[config])
+    for key, val in dict(n=n, d=d, nu=nu).items():
+        if val is not None:
+            cfg[key] = val
+    n, d = int(cfg["n"]), int(cfg["d"])
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+    sigma = spectrum(cfg["decay"], n)
+    U = _orthonormal(rng, n, n)
+    Z = torch.randn(d, n, generator=g, device=device, dtype=f64)
+    Lc = np.linalg.cholesky((Z.T @ Z).cpu().numpy())
+    V = torch.linalg.solve_triangular(torch.from_numpy(Lc).to(device), Z.T, upper=False).T  # d x n, orthonormal
+    A = (torch.from_numpy(U * sigma[None, :]).to(device) @ V.T).contiguous()
+    lam = torch.from_numpy(_lambda(cfg["lam"], rng, d)).to(device=device, dtype=f64)
+    b = torch.randn(d, 1, generator=g, device=device, dtype=f64)
+    return dict(n=n, d=d, nu=float(cfg["nu"]), lam=lam, A64=A, b=b, sigma=torch.from_numpy(sigma).to(device),
+                meta=dict(config=config, seed=seed, **cfg))
 
 
 def batched_specs(count=256, seed=0):

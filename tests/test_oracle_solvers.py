@@ -347,3 +347,21 @@ def test_cg_matches_scipy_cg_iterates():
     assert len(seen) == 8
     for t in range(8):
         assert np.linalg.norm(ours[t + 1] - seen[t]) <= 1e-10 * np.linalg.norm(seen[t]), t
+
+
+def test_dual_formulation_recovers_primal_solution():
+    # n < d: solving eq. (2) directly and mapping back with x = Lambda^{-1}(b - A^T w)/nu^2
+    # gives the primal optimum of eq. (1) (the same x as the d x d Cholesky solve).
+    rng = np.random.default_rng(8)
+    n, d, nu = 40, 120, 3e-2
+    A = rng.standard_normal((n, d)) * (0.9 ** np.arange(d))[None, :]
+    lam = 1 + 9 * rng.random(d)
+    b = rng.standard_normal((d, 2))
+    D, bd, nud, lamd = S.dual_problem(A, b, nu, lam)
+    assert D.shape == (d, n)
+    w = S.direct_solve(D, bd, nud, lamd)
+    x = S.primal_from_dual(A, b, nu, lam, w)
+    xs = S.direct_solve(A, b, nu, lam)
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    # the dual Hessian is A Lambda^{-1} A^T + nu^2 I
+    assert np.allclose(D.T @ D + nu ** 2 * np.eye(n), (A / lam[None, :]) @ A.T + nu ** 2 * np.eye(n))

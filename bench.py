@@ -2,8 +2,8 @@
 
 One step = one complete adaptive solve (sketch, preconditioner builds,
 iterations to the tolerance) of the workload, inputs resident in HBM.
-Prints ONE JSON line (rank 0).  See the design doc for the workload recipe and the
-roofline arithmetic.
+Prints ONE JSON line (rank 0): the time per solve, the roofline of the A-pass,
+the end-to-end time from host buffers and the CPU oracle's time on the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload C2] [--method pcg|ihs] [--no-cpu-baseline]

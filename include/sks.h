@@ -46,7 +46,7 @@ typedef enum {
   SKS_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out                  */
   SKS_ERR_CUDA = 6,           /* a CUDA runtime call failed                          */
   SKS_ERR_WORKSPACE = 7,      /* ws_bytes smaller than the size query returned       */
-  SKS_ERR_UNSUPPORTED = 8     /* valid request that this build does not implement    */
+  SKS_ERR_UNSUPPORTED = 8     /* valid request that the library does not implement   */
 } sks_status;
 
 /* Random embeddings of Section 2.1. */
@@ -269,7 +269,10 @@ sks_status sks_adaptive_ihs_solve(const sks_problem* p, const sks_opts* o, doubl
  * sks_adaptive_pcg_solve; o->tol is the dual's relative H-error target, and
  * the primal error obeys ||x - x*||_H <= ||H_dual (w - w*)||_2 / nu^2.  The
  * workspace (sks_dual_workspace_size) holds the dual matrix, a transposed copy
- * of A of the same size.  Any n, d within the A-pass limits (the dual's d is n).
+ * of A of the same size, in A's precision: for a float32 A (mixed form) with
+ * Lambda != I its entries a_ij / sqrt(lambda_j) are rounded to float32, so the
+ * dual solved is that rounded one (exact for Lambda = I).  Any n, d within the
+ * A-pass limits (the dual's d is n).
  * ------------------------------------------------------------------------- */
 sks_status sks_dual_workspace_size(const sks_problem* p, const sks_opts* o, size_t* bytes);
 sks_status sks_dual_pcg_solve(const sks_problem* p, const sks_opts* o, double* x, sks_stats* stats,

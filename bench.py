@@ -96,12 +96,12 @@ WORKLOADS = {
 # keyed by the source hash of the kernel file it was captured from; any change
 # to the kernel source invalidates the figure (traffic then reported as null).
 # float32 A-pass (inner PCG): captured at n=2^17, d=4096 (C3-srht-profile, six launches, mean
-# 2.147598 GB read + 2.20 MB written); the n=2^20 workloads run the same kernel with the same grid,
+# 2.147599 GB read + 1.83 MB written); the n=2^20 workloads run the same kernel with the same grid,
 # so the read bytes scale by 8 with the rows and the partial-sum writes stay.
 TRAFFIC = {
-    ("04ab206454095ac1", "C3-srht-profile"): 2147597781 + 2198784,
-    ("04ab206454095ac1", "C3"): 8 * 2147597781 + 2198784,
-    ("04ab206454095ac1", "C3-srht"): 8 * 2147597781 + 2198784,
+    ("cfa60c129bcba125", "C3-srht-profile"): 2147599019 + 1831979,
+    ("cfa60c129bcba125", "C3"): 8 * 2147599019 + 1831979,
+    ("cfa60c129bcba125", "C3-srht"): 8 * 2147599019 + 1831979,
 }
 
 

@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kSjBlockThreads) sjlt_block_kernel(const T* __
   for (uint32_t h = 0; h < m; ++h) SV::flush(Y + (long long)h * ldy + c, Ys[(size_t)h * kSjBlockThreads + tid]);
 }
 
-// Small m, float32 (m <= MR <= 64): the m partial rows of the thread's VEC
+// Small m, float32 (m <= MR <= 32): the m partial rows of the thread's VEC
 // columns live in registers.  For a batch of 256 data rows every thread
 // expands one row's hash into a dense coefficient row w[MR] (the scaled
 // sign at the s_eff hashed rows, 0 elsewhere) in shared memory; then each data
@@ -741,15 +741,14 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
     // 16-byte columns only: narrower ones keep too few bytes in flight at one
     // CTA per SM, and the L2 scatter is faster there
     if constexpr (sizeof(TY) == 4) {
-      // partial rows in registers: 16-byte columns up to m = 32, 8-byte ones for m <= 64
-      const bool al8 = ((uintptr_t)A & 15) == 0 && ((uintptr_t)Y & 15) == 0;
+      // partial rows in registers: 16-byte columns up to m = 32 (measured at n = 2^20, d = 4096:
+      // 2.6 / 3.6 / 7.9 ms for 8 / 16 / 32 rows; 64 rows of 2 columns took 20.6 ms, slower than the
+      // scatter's 12 ms, so m > 32 goes to the shared-memory kernel or the scatter)
       if (al16 && d % 4 == 0 && lda % 4 == 0 && ldy % 4 == 0) {
         if (m <= 8) return sjlt_reg_launch<8, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
         if (m <= 16) return sjlt_reg_launch<16, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
         if (m <= 32) return sjlt_reg_launch<32, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
       }
-      if (al8 && m <= 64 && d % 2 == 0 && lda % 2 == 0 && ldy % 2 == 0)
-        return sjlt_reg_launch<64, 2>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
       if (fits(4)) return sjlt_block_launch<TY, 4>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(4));
     } else {
       if (fits(2)) return sjlt_block_launch<TY, 2>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(2));

@@ -11,6 +11,7 @@ from .problems import (  # noqa: F401
     Problem,
     make_problem,
     make_problem_torch,
+    make_wide_problem_torch,
     spectrum,
     batched_specs,
     make_batch_torch,

@@ -134,8 +134,8 @@ def test_srht_multi_pass_transform(dt, tol):
                                    (7000, 258, 17)])
 def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
     # small and medium m: float32 partial rows in registers (8, 16, 32 rows of
-    # 4 columns, or 64 rows of 2 columns when d is not a multiple of 4), the
-    # float64 column-block kernel (partial rows in shared memory); d = 2052
+    # 4 columns), the column-block kernel (partial rows in shared memory: float64,
+    # float32 past 32 rows or with d not a multiple of 4); d = 2052
     # spans three column blocks of 1024 float32 columns, the last one ragged;
     # n = 20000 takes several 256-row hash batches per CTA; m = 300 is past
     # the shared-memory limit (the L2 scatter).

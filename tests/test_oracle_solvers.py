@@ -365,3 +365,42 @@ def test_dual_formulation_recovers_primal_solution():
     assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
     # the dual Hessian is A Lambda^{-1} A^T + nu^2 I
     assert np.allclose(D.T @ D + nu ** 2 * np.eye(n), (A / lam[None, :]) @ A.T + nu ** 2 * np.eye(n))
+
+
+@pytest.mark.parametrize("kind,m", [("srht", 64), ("gaussian", 48)])
+def test_remark_4_2_certified_termination(kind, m):
+    # Remark 4.2: once delta~_t <= eps / (m_delta + 1), delta_t <= eps (with
+    # probability >= 1 - delta over S; fixed seeds here).  delta = 1/2 ||x_t - x*||_H^2
+    # from the exact x*, delta~_t = 1/2 r_t^T H_S^{-1} r_t along fixed-sketch PCG,
+    # m_delta from Theorem 5.1 / 5.2 with d_e := d (the replacement the remark suggests).
+    p = small_problem(n=1024, d=24, nu=1e-2, seed=2)
+    xs = S.direct_solve(p.A, p.b, p.nu, p.lam)
+    P = S.Preconditioner(SK.sketch(kind, p.A, m, seed=4), p.nu, p.lam)
+    delta = 0.05
+    md = S.m_delta_srht(p.d, p.A.shape[0], delta) if kind == "srht" else S.m_delta_gaussian(p.d, delta)
+    eps = 1e-14 * S.h_norm_sq(p.A, p.nu, p.lam, xs)
+    hit = False
+    for x in S.pcg(p.A, p.b, p.nu, p.lam, P, np.zeros(p.d), 40):
+        r = p.b - S.hess_apply(p.A, p.nu, p.lam, x)
+        dtil = 0.5 * float(r @ P.apply(r))
+        if dtil <= S.termination_threshold(eps, md):
+            hit = True
+            assert 0.5 * S.h_norm_sq(p.A, p.nu, p.lam, x - xs) <= eps
+    assert hit
+
+
+def test_dual_error_bound():
+    # ||x - x*||_H <= ||H_dual (w - w*)|| / nu^2 for any w, with x the primal map of w
+    rng = np.random.default_rng(9)
+    n, d, nu = 30, 90, 5e-2
+    A = rng.standard_normal((n, d)) / np.sqrt(d)
+    lam = 1 + rng.random(d)
+    b = rng.standard_normal(d)
+    D, bd, _, lamd = S.dual_problem(A, b, nu, lam)
+    ws = S.direct_solve(D, bd, nu, lamd)
+    xs = S.direct_solve(A, b, nu, lam)
+    Hd = D.T @ D + nu ** 2 * np.eye(n)
+    for scale in (1e-1, 1e-4, 1e-8):
+        w = ws + scale * rng.standard_normal(n)
+        x = S.primal_from_dual(A, b, nu, lam, w)
+        assert np.sqrt(S.h_norm_sq(A, nu, lam, x - xs)) <= np.linalg.norm(Hd @ (w - ws)) / nu ** 2 * (1 + 1e-9)

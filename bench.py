@@ -88,6 +88,13 @@ WORKLOADS = {
     "D": dict(config="D", dual=True, method="pcg", kind="srht", m_init=1, m_max=0, tol=1e-10, precision="plain",
               desc="dual formulation (eq. 2), adaptive PCG, SRHT, float64: n=1545 < d=10936, sigma_j=0.995^j, "
                    "nu=1e-2, Lambda=I, b ~ N(0,1), tol 1e-10 on the dual"),
+    # C4: the differentiable solve -- forward mixed adaptive PCG on 8 right-hand sides, backward the
+    # adjoint solve with the same preconditioner and the fused dA pass
+    "C4": dict(config="C4", adjoint=True, method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-8,
+               precision="mixed", cpu_rows=1 << 13,
+               desc="differentiable solve: n=2^18, d=1024, float32 A, sigma_j=(1+j)^-1/2, 8 right-hand sides, "
+                    "nu=1e-2, Lambda=1+U; forward mixed adaptive PCG (Gaussian, tol 1e-8), backward adjoint solve "
+                    "+ dA, db, dnu, dLambda"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -276,6 +283,46 @@ def run_reference_batched(args, wl, world, rank):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": "C5: " + wl["desc"], "problems": len(host), "sum_nd": nd_all},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_reference_adjoint(args, wl, world, rank):
+    """--impl reference for C4: the oracle's float64 solve + gradients on row samples per step,
+    extrapolated to all n rows with the two-point model."""
+    if rank != 0:
+        return None
+    import synthetic
+    from oracle import adjoint as OA
+    gdev = "cuda" if torch.cuda.is_available() else "cpu"
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=gdev)
+    A = prob["A64"].cpu().numpy()
+    b = prob["b"].cpu().numpy()
+    lam = prob["lam"].cpu().numpy()
+    nu = prob["nu"]
+    del prob
+    n, d = A.shape
+    g = np.random.default_rng(1).standard_normal(b.shape)
+    rows = min(wl["cpu_rows"], n)
+
+    def timed(r):
+        t0 = time.perf_counter()
+        OA.solve_and_grads(A[:r], b, nu, lam, g)
+        return (time.perf_counter() - t0) * 1e3
+
+    for _ in range(args.warmup):
+        timed(rows // 2)
+    t_large = timed(rows)
+    times = [extrapolate(timed(rows // 2), rows // 2, t_large, rows, n)[0] for _ in range(args.steps)]
+    ms = sum(times) / len(times)
+    sample = ("per step: oracle float64 solve + gradients (direct) on the first %d of %d rows, extrapolated with "
+              "t(n) = f + g n fitted to that and one solve on %d rows" % (rows // 2, n, rows))
+    return {
+        "metric": ADJOINT_METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": wl["config"] + ": " + wl["desc"], "n": n, "d": d, "k": int(b.shape[1])},
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -534,6 +581,141 @@ def run_ours(args, wl, world, rank, local):
 
 
 BATCH_METRIC = "ms to solve a batch of uneven problems to 1e-8 rel. H-error (batched vs one at a time)"
+ADJOINT_METRIC = "ms per forward + backward of the differentiable solve (8 right-hand sides, 1e-8)"
+
+
+def run_adjoint(args, wl, world, rank, local):
+    """C4: one step = the forward solve of all right-hand sides and the backward pass (adjoint solve
+    u = H^{-1} g with the forward preconditioner, then db, dA, dnu, dLambda) for a fixed upstream g."""
+    import paper_2104_14101_gb300 as sks
+    from paper_2104_14101_gb300 import _lib
+    import synthetic
+    from oracle import adjoint as OA
+    from oracle import solvers as O
+
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    lib = _lib.load()
+    prob = synthetic.make_problem_torch(wl["config"], seed=0, device=dev)
+    A, b, lam, nu = prob["A32"], prob["b"].contiguous(), prob["lam"], prob["nu"]
+    n, d = A.shape
+    k = b.shape[1]
+    g = torch.randn(d, k, generator=torch.Generator(device=dev).manual_seed(1), device=dev, dtype=torch.float64)
+    sopts = dict(kind=wl["kind"], m_init=wl["m_init"], m_max=wl["m_max"], tol=wl["tol"], seed=0,
+                 precision="mixed", max_iter=5000)
+    solver = sks.Solver(A, b, nu, lam, **sopts)
+
+    def step():
+        x, st, _ = solver.solve()
+        dA, db, dnu, dlam = solver.adjoint(x, g)
+        return x, st, dA, db, dnu, dlam
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    launches0 = lib.sks_kernel_launch_count()
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("sks_timed")
+    ev[0].record(stream)
+    fwd_ms = 0.0
+    for _ in range(args.steps):
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        x, st, _ = solver.solve()
+        e_b.record(stream)
+        dA, db, dnu, dlam = solver.adjoint(x, g)
+        torch.cuda.synchronize()
+        fwd_ms += e_a.elapsed_time(e_b)
+    ev[1].record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = lib.sks_kernel_launch_count() - launches0
+    ms = max_over_ranks(ev[0].elapsed_time(ev[1]) / args.steps, world, dev)
+    fwd_ms /= args.steps
+
+    # roofline of the forward A-pass (float32, HBM) from the solve's live CUDA-event times
+    ap_ms, ap_n = st["ms_apass"], st["apass_timed"]
+    ap_avg = ap_ms / max(ap_n, 1)
+    bytes_pass = n * d * 4 + 3 * d * 4
+    peaks, peak_src = load_peaks()
+    gbs = bytes_pass / (ap_avg * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "apass_kernel<float,float>",
+                "launches": ap_n, "avg_launch_ms": ap_avg, "bytes_per_launch": bytes_pass,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}
+
+    # e2e: A, b, lambda from pinned host memory, solution and gradients read back, every step
+    A_h, b_h, lam_h = A.cpu().pin_memory(), b.cpu().pin_memory(), lam.cpu().pin_memory()
+    A_d, b_d, lam_d = torch.empty_like(A), torch.empty_like(b), torch.empty_like(lam)
+    A_d.copy_(A_h); b_d.copy_(b_h); lam_d.copy_(lam_h)
+    s2 = sks.Solver(A_d, b_d, nu, lam_d, **sopts)
+    x2, _, _ = s2.solve()
+    s2.adjoint(x2, g)
+    torch.cuda.synchronize()
+    dA_h = torch.empty(A.shape, dtype=A.dtype).pin_memory()
+    ke = max(1, min(args.steps, 3))
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(ke):
+        A_d.copy_(A_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        lam_d.copy_(lam_h, non_blocking=True)
+        x2, _, _ = s2.solve()
+        gA, gb, gnu, glam = s2.adjoint(x2, g)
+        dA_h.copy_(gA, non_blocking=True)
+        _ = (x2.cpu(), gb.cpu(), glam.cpu())
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3) / ke
+    h2d = A.numel() * 4 + b.numel() * 8 + lam.numel() * 8
+    d2h = A.numel() * 4 + 2 * d * k * 8 + d * 8
+    del s2, A_d
+
+    line = {
+        "metric": ADJOINT_METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": wl["config"] + ": " + wl["desc"], "n": n, "d": d, "k": k, "kind": wl["kind"],
+                   "precision": "mixed", "l2": "inputs larger than L2 (A = %.2f GiB)" % (A.numel() * 4 / 2 ** 30),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches), "clocks": clk,
+        "split": {"forward_ms": fwd_ms, "backward_ms": ms - fwd_ms},
+        "solve_stats": {kk: st[kk] for kk in ("iters", "rejections", "final_m", "a_passes", "outer_iters")},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's float64 solve + gradients on row samples, extrapolated in n; and the GPU
+        # gradients against the oracle's on all rows
+        A64 = A.cpu().to(torch.float64).numpy()
+        bn, gn, ln = b.cpu().numpy(), g.cpu().numpy(), lam.cpu().numpy()
+        rows = wl["cpu_rows"]
+        times = []
+        for r in (rows // 2, rows):
+            t0 = time.perf_counter()
+            OA.solve_and_grads(A64[:r], bn, nu, ln, gn)
+            times.append((time.perf_counter() - t0) * 1e3)
+        cpu_ms, _ = extrapolate(times[0], rows // 2, times[1], rows, n)
+        line["cpu_baseline"] = {"value": cpu_ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": "oracle float64 solve + gradients (direct) on the first %d and %d of %d "
+                                          "rows (%.0f ms, %.0f ms), extrapolated with t(n) = f + g n"
+                                          % (rows // 2, rows, n, times[0], times[1])}
+        X, G = OA.solve_and_grads(A64, bn, nu, ln, gn)
+        dAn = dA.cpu().to(torch.float64).numpy()
+        line["grad_check_vs_oracle"] = {
+            "x_rel_err_H_max": max(O.rel_err_H(A64, nu, ln, x.cpu().numpy()[:, c], X[:, c]) for c in range(k)),
+            "db_rel": float(np.linalg.norm(db.cpu().numpy() - G["b"]) / np.linalg.norm(G["b"])),
+            "dA_rel": float(np.linalg.norm(dAn - G["A"]) / np.linalg.norm(G["A"])),
+            "dlam_rel": float(np.linalg.norm(dlam.cpu().numpy() - G["lam"]) / np.linalg.norm(G["lam"])),
+            "dnu_rel": abs(dnu - G["nu"]) / abs(G["nu"])}
+    return line if rank == 0 else None
 
 
 def run_batched(args, wl, world, rank, local):
@@ -672,9 +854,13 @@ def main():
         wl["method"] = args.method
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
-        line = (run_reference_batched if wl.get("batched") else run_reference)(args, wl, world, rank)
+        fn = run_reference_batched if wl.get("batched") else (run_reference_adjoint if wl.get("adjoint")
+                                                               else run_reference)
+        line = fn(args, wl, world, rank)
     elif wl.get("batched"):
         line = run_batched(args, wl, world, rank, local)
+    elif wl.get("adjoint"):
+        line = run_adjoint(args, wl, world, rank, local)
     else:
         line = run_ours(args, wl, world, rank, local)
     if rank == 0 and line is not None:

@@ -198,8 +198,8 @@ sks_status sks_hess_apply_noalloc(const sks_problem* p, const double* x, double*
  * Sketch S A of Section 2.1 with nested growth.
  * sks_sketch_create forms S_m A for m = m_init (SRHT: also the n_pad x d
  * matrix H E A_pad, once); sks_sketch_grow(new_m) extends it to new_m >= m
- * rows (SRHT: gathers more rows of H E A_pad; Gaussian: appends rows of G A;
- * SJLT: re-hashes and re-forms S A in one pass).  The sketch is kept in the
+ * rows (SRHT: gathers more rows of H E A_pad; Gaussian and Rademacher: append
+ * rows of G A; SJLT: re-hashes and re-forms S A in one pass over A).  The sketch is kept in the
  * precision of A and "unscaled": S A = scale * Y with scale = 1/sqrt(m) (SRHT,
  * Gaussian) or 1 (SJLT); sks_sketch_copy_out writes the scaled S A (m x d
  * row-major float64).
@@ -243,8 +243,8 @@ void sks_precond_destroy(sks_precond* P);
  * Stop rule (the paper prescribes none; Remark 4.2): after an accepted step,
  * opts.stop_rule decides; by default (SKS_STOP_ESTIMATE) stop when the
  * estimate delta~_t / (b^T x_t) of ||x_t - x*||_H^2/||x*||_H^2 is <= (tol/2)^2
- * (IHS: 2 delta~_t); SKS_STOP_CERTIFIED uses tol^2 / (m_delta + 1) instead.  k > 1 right-hand sides are solved one
- * after the other.
+ * (IHS: 2 delta~_t); SKS_STOP_CERTIFIED uses tol^2 / (m_delta + 1) instead.
+ * k > 1 right-hand sides are solved one after the other.
  * x: device float64 d x k, in: x_0, out: the solution.  stats: host, may be NULL.
  * ws: device scratch of sks_solve_workspace_size bytes.
  * Returns SKS_ERR_NO_CONVERGENCE if max_iter accepted steps did not reach tol.

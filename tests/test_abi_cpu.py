@@ -101,3 +101,48 @@ def test_batched_validation_without_gpu(lib_path):
     o.kind = _lib.KINDS["srht"]
     arr[1].k = 2
     assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_UNSUPPORTED
+
+
+def test_new_entry_points_validation_without_gpu(lib_path):
+    # Host-side checks of the non-adaptive solvers, the certified stop rule and
+    # the dual formulation return a status before any device work.
+    from paper_2104_14101_gb300 import _lib
+    lib = _lib.load(lib_path)
+    o = _lib.Opts()
+    lib.sks_opts_default(ctypes.byref(o))
+    p = _lib.Problem()
+    p.dtype, p.n, p.d, p.lda, p.k, p.nu = _lib.F64, 100, 300, 300, 1, 1e-2
+    p.A, p.b, p.lambda_diag = 16, 16, 16  # never dereferenced
+    x = ctypes.c_void_p(16)
+    st = _lib.Stats()
+    # an unknown fixed-sketch method
+    assert lib.sks_fixed_solve(9, ctypes.byref(p), ctypes.byref(o), x, ctypes.byref(st), None, 0, None) == \
+        _lib.ERR_INVALID_ARG
+    # CG has no preconditioner: no mixed form, no certified stop
+    o.precision = _lib.MIXED_REFINED
+    p.dtype = _lib.F32
+    assert lib.sks_fixed_solve(3, ctypes.byref(p), ctypes.byref(o), x, ctypes.byref(st), None, 0, None) == \
+        _lib.ERR_UNSUPPORTED
+    o.precision, p.dtype = _lib.PLAIN_F64, _lib.F64
+    o.stop_rule = _lib.STOP_RULES["certified"]
+    assert lib.sks_fixed_solve(3, ctypes.byref(p), ctypes.byref(o), x, ctypes.byref(st), None, 0, None) == \
+        _lib.ERR_UNSUPPORTED
+    # certified rule: delta in (0, 1), d_e >= 0; unknown rules rejected
+    o.cert_delta = 1.5
+    assert lib.sks_adaptive_pcg_solve(ctypes.byref(p), ctypes.byref(o), x, ctypes.byref(st), None, 0, None) == \
+        _lib.ERR_INVALID_ARG
+    o.cert_delta, o.stop_rule = 0.01, 7
+    assert lib.sks_adaptive_pcg_solve(ctypes.byref(p), ctypes.byref(o), x, ctypes.byref(st), None, 0, None) == \
+        _lib.ERR_INVALID_ARG
+    o.stop_rule = 0
+    # dual formulation of this 100 x 300 problem: the workspace holds the 300 x 100 dual matrix
+    nb = ctypes.c_size_t()
+    assert lib.sks_dual_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(nb)) == _lib.OK
+    assert nb.value > 300 * 100 * 8
+    assert lib.sks_dual_pcg_solve(ctypes.byref(p), ctypes.byref(o), x, ctypes.byref(st), None, 0, None) == \
+        _lib.ERR_WORKSPACE
+    # the batch stops by the estimate rule only
+    o.stop_rule = _lib.STOP_RULES["certified"]
+    arr = (_lib.Problem * 1)(p)
+    arr[0].n, arr[0].d, arr[0].lda = 64, 8, 8
+    assert lib.sks_batch_workspace_size(arr, 1, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_UNSUPPORTED

@@ -226,6 +226,20 @@ def make_workload_problem(wl, device):
     return synthetic.make_problem_torch(wl["config"], seed=0, device=device, n=wl.get("n"), d=wl.get("d"))
 
 
+def sketch_phase_roofline(kind, st, n, d, esize, peak_gbs):
+    """The SJLT re-sketches of one solve as a phase: every (re)hash reads A once, so the
+    algorithmic bytes are sketch_passes * n * d * esize over the phase's CUDA-event time
+    (ms_sketch).  The scatter for larger m is bound by L2 read-modify-writes, the smaller-m
+    kernels by HBM or the FMA pipe, so this is reported beside the A-pass roofline, not as it."""
+    if kind != "sjlt" or not st.get("ms_sketch") or not st.get("sketch_passes"):
+        return None
+    per_pass = n * d * esize
+    gbs = st["sketch_passes"] * per_pass / (st["ms_sketch"] * 1e-3) / 1e9
+    return {"bound": "hbm (read of A per pass); larger m: L2 read-modify-write", "achieved": gbs, "peak": peak_gbs,
+            "unit": "GB/s", "frac": gbs / peak_gbs, "passes": int(st["sketch_passes"]), "ms": st["ms_sketch"],
+            "bytes_per_pass": per_pass}
+
+
 def host64(A, rows=None):
     """float64 NumPy copy of (the first rows of) a device matrix (a float32 A is upcast exactly)."""
     T = A if rows is None else A[:rows]
@@ -545,10 +559,17 @@ def run_ours(args, wl, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": clk,
         "solve_stats": {k: st0[k] for k in ("iters", "rejections", "final_m", "a_passes", "factorizations",
-                                            "outer_iters", "ms_sketch", "ms_factor", "ms_iter", "est_rel_err")},
+                                            "sketch_passes", "outer_iters", "ms_sketch", "ms_factor", "ms_iter",
+                                            "est_rel_err")},
     }
     if compare:
         line["compare"] = compare
+    try:  # the largest phase of the SJLT workloads, beside the A-pass roofline
+        rs = sketch_phase_roofline(wl["kind"], st0, n, d, A.element_size(), peaks["hbm_gbs"])
+        if rs:
+            line["roofline_sketch_phase"] = rs
+    except Exception:  # an extra figure must never cost the line
+        pass
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import solvers as O
         lam_np = lam_h.numpy()

@@ -37,3 +37,13 @@ def test_workload_generators_run_on_cpu(name):
     from oracle import solvers as O
     xs = O.direct_solve(A.numpy(), b, prob["nu"], prob["lam"].numpy())
     assert O.rel_err_H(A.numpy(), prob["nu"], prob["lam"].numpy(), x, xs) <= max(10 * wl["tol"], 1e-7)
+
+
+def test_sketch_phase_roofline_arithmetic():
+    st = dict(ms_sketch=126.0, sketch_passes=14)
+    r = bench.sketch_phase_roofline("sjlt", st, 1 << 20, 4096, 4, 6794.5)
+    assert r["passes"] == 14 and r["bytes_per_pass"] == (1 << 20) * 4096 * 4
+    assert abs(r["achieved"] - 14 * (1 << 20) * 4096 * 4 / 0.126 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6794.5) < 1e-12
+    assert bench.sketch_phase_roofline("srht", st, 1, 1, 4, 1.0) is None
+    assert bench.sketch_phase_roofline("sjlt", dict(ms_sketch=0.0, sketch_passes=1), 1, 1, 4, 1.0) is None

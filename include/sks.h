@@ -181,9 +181,15 @@ sks_status sks_hess_apply(const sks_problem* p, const double* x, double* y, int 
  * Same operation, arguments and results as sks_hess_apply, minus `ws`: the
  * per-block partial sums live in a library-owned static device array of
  * 8 MiB, which every GPU that loads the library holds until the process
- * exits.  A problem needing more scratch than that (float64 vectors: about
- * 152 blocks * 8 bytes * d * k; every d <= 4096 with k = 1 fits) is rejected
- * with SKS_ERR_INVALID_ARG and a message giving the size it needs.
+ * exits.  The pass needs grid * g * k * d partial sums of the vector type
+ * (float32 for a float32 A without `extended`, else float64), plus two
+ * float32 d x k vectors in the float32 case, where grid = SMs x blocks per SM
+ * (1 for float64 A, `extended` or d > 4096, else 2) and g = 8, 2 or 1 row
+ * groups per block for rows of at most 32 q, 128 q or more column vectors
+ * (q = 8 vectors of 2 float64 columns, or 4 vectors of 4 float32 columns;
+ * g = 1 when k = 8).  On a 152-SM GPU every d <= 4096
+ * with k = 1 fits.  A larger problem is rejected with SKS_ERR_INVALID_ARG
+ * and a message giving the size it needs.
  * The first call on a device looks up the array's device address with that
  * device current and caches it; make that first call before any stream
  * capture.  All calls share the array and it keeps the last call's contents:

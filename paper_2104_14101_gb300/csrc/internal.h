@@ -99,7 +99,14 @@ void apass_use_bulk(ApassPlan* plan, const void* A, int64_t d, int64_t lda, bool
 
 // ---------------------------------------------------------------- solver entry points (solver.cu)
 // Host-side checks of a problem description (sizes, pointers, alignment).
+// validate_operator checks what defines H (A, n, d, lda, k, nu, lambda);
+// validate_problem also requires the right-hand side b.
+sks_status validate_operator(const sks_problem* p);
 sks_status validate_problem(const sks_problem* p);
+// Element-wise precision conversions (grid-stride) and the grid size they use.
+__global__ void f64_to_f32_kernel(long long count, const double* a, float* b);
+__global__ void f32_to_f64_kernel(long long count, const float* a, double* b);
+unsigned blocks_for(long long n, int t = 256);
 // Reads the device status word (one stream synchronisation) and turns a
 // device-side error into an sks_status with a message naming `what`.
 sks_status read_status(DevStatus* st, cudaStream_t stream, const char* what);

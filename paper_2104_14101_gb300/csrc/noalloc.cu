@@ -47,39 +47,19 @@ sks_status scratch_for_current_device(void** out) {
   return SKS_OK;
 }
 
-__global__ void na_f64_to_f32(long long count, const double* a, float* b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
-__global__ void na_f32_to_f64(long long count, const float* a, double* b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
-}
-
-sks_status check_problem(const sks_problem* p) {
-  if (!p) return fail(SKS_ERR_INVALID_ARG, "problem is NULL");
-  if (p->n < 0 || p->d < 1 || p->k < 1) return fail(SKS_ERR_INVALID_ARG, "need n >= 0, d >= 1, k >= 1");
-  if (p->lda < p->d) return fail(SKS_ERR_INVALID_ARG, "lda < d");
-  if (p->n > 0 && !p->A) return fail(SKS_ERR_INVALID_ARG, "A is NULL");
-  if (!p->lambda_diag) return fail(SKS_ERR_INVALID_ARG, "lambda is NULL");
-  if (!(p->nu > 0.0)) return fail(SKS_ERR_INVALID_ARG, "nu must be > 0");
-  if (p->dtype != SKS_F64 && p->dtype != SKS_F32) return fail(SKS_ERR_INVALID_ARG, "bad dtype");
-  const size_t esz = p->dtype == SKS_F32 ? 4 : 8;
-  if (p->n > 0 && (((uintptr_t)p->A & 15) || (p->lda * esz) % 16))
-    return fail(SKS_ERR_INVALID_ARG, "A must be 16-byte aligned with lda * element size a multiple of 16");
-  return SKS_OK;
-}
-
 }  // namespace
 
 sks_status hess_apply_noalloc(const sks_problem* p, const double* x, double* y, int extended, cudaStream_t stream) {
-  SKS_TRY(check_problem(p));
+  // the same checks as sks_hess_apply, minus the right-hand side it never reads
+  SKS_TRY(validate_operator(p));
   if (!x || !y) return fail(SKS_ERR_INVALID_ARG, "x or y is NULL");
   const bool f32 = p->dtype == SKS_F32;
   const bool vec32 = f32 && !extended;
   const int64_t kb = p->k == 8 ? 8 : 1;
   ApassPlan plan;
   SKS_TRY(apass_plan(std::max<int64_t>(p->n, 1), p->d, kb, f32, vec32, &plan));
+  // whole-row bulk copies where rows allow them, as sks_hess_apply (the partial sums' size is unchanged)
+  apass_use_bulk(&plan, p->A, p->d, p->lda, f32);
   // Layout inside the static scratch: status | partial sums | float32 copies of x and y.
   Carver c(nullptr, 0);
   c.take<DevStatus>(1);
@@ -111,24 +91,17 @@ sks_status hess_apply_noalloc(const sks_problem* p, const double* x, double* y, 
     double* yc = y + c0 * p->d;
     if (vec32) {
       const long long cnt = (long long)p->d * kb;
-      const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((cnt + 255) / 256, 4096));
-      na_f64_to_f32<<<blocks, 256, 0, stream>>>(cnt, xc, xf);
+      f64_to_f32_kernel<<<blocks_for(cnt), 256, 0, stream>>>(cnt, xc, xf);
       note_launch();
       SKS_TRY(apass_launch(plan, &tmap, p->n, p->d, kb, true, true, xf, yf, nu2, p->lambda_diag, partials, st, stream));
-      na_f32_to_f64<<<blocks, 256, 0, stream>>>(cnt, yf, yc);
+      f32_to_f64_kernel<<<blocks_for(cnt), 256, 0, stream>>>(cnt, yf, yc);
       note_launch();
       SKS_CUDA_TRY(cudaGetLastError());
     } else {
       SKS_TRY(apass_launch(plan, &tmap, p->n, p->d, kb, f32, false, xc, yc, nu2, p->lambda_diag, partials, st, stream));
     }
   }
-  DevStatus h;
-  SKS_CUDA_TRY(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, stream));
-  SKS_CUDA_TRY(cudaStreamSynchronize(stream));
-  if (h.code != 0)
-    return fail((sks_status)h.code, "hess_apply_noalloc: device status " + std::to_string(h.code) + " (site " +
-                                        std::to_string(h.where) + ")");
-  return SKS_OK;
+  return read_status(st, stream, "hess_apply_noalloc");
 }
 
 }  // namespace sks

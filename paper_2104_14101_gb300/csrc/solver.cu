@@ -74,12 +74,12 @@ struct sks_precond {
 
 namespace sks {
 
-sks_status validate_problem(const sks_problem* p) {
+sks_status validate_operator(const sks_problem* p) {
   if (!p) return fail(SKS_ERR_INVALID_ARG, "problem is NULL");
   if (p->n < 0 || p->d < 1 || p->k < 1) return fail(SKS_ERR_INVALID_ARG, "need n >= 0, d >= 1, k >= 1");
   if (p->lda < p->d) return fail(SKS_ERR_INVALID_ARG, "lda < d");
   if (p->n > 0 && !p->A) return fail(SKS_ERR_INVALID_ARG, "A is NULL");
-  if (!p->b || !p->lambda_diag) return fail(SKS_ERR_INVALID_ARG, "b or lambda is NULL");
+  if (!p->lambda_diag) return fail(SKS_ERR_INVALID_ARG, "lambda is NULL");
   if (!(p->nu > 0.0) || !std::isfinite(p->nu)) return fail(SKS_ERR_INVALID_ARG, "nu must be > 0");
   if (p->dtype != SKS_F64 && p->dtype != SKS_F32) return fail(SKS_ERR_INVALID_ARG, "bad dtype");
   if (p->dtype == SKS_F32 && p->d > 16384) return fail(SKS_ERR_UNSUPPORTED, "d > 16384 (float32 A)");
@@ -88,6 +88,12 @@ sks_status validate_problem(const sks_problem* p) {
   const size_t esz = p->dtype == SKS_F32 ? 4 : 8;
   if (p->n > 0 && (((uintptr_t)p->A & 15) || (p->lda * esz) % 16))
     return fail(SKS_ERR_INVALID_ARG, "A must be 16-byte aligned with lda * element size a multiple of 16");
+  return SKS_OK;
+}
+
+sks_status validate_problem(const sks_problem* p) {
+  SKS_TRY(validate_operator(p));
+  if (!p->b) return fail(SKS_ERR_INVALID_ARG, "b is NULL");
   return SKS_OK;
 }
 
@@ -106,6 +112,19 @@ sks_status read_status(DevStatus* st, cudaStream_t stream, const char* what) {
   return SKS_OK;
 }
 
+__global__ void f64_to_f32_kernel(long long count, const double* a, float* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f32_to_f64_kernel(long long count, const float* a, double* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+unsigned blocks_for(long long n, int t) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((n + t - 1) / t, 65535ll * 16));
+}
+
 namespace {
 
 // ---------------------------------------------------------------- validation
@@ -122,14 +141,6 @@ sks_status map_for(const sks_problem* p, CUtensorMap* map, const ApassPlan& pl) 
                       (uint32_t)pl.rows_per_stage);
 }
 
-__global__ void f64_to_f32_kernel(long long count, const double* a, float* b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
-__global__ void f32_to_f64_kernel(long long count, const float* a, double* b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
-}
 __global__ void f32_to_f64_2d_kernel(int rows, int cols, const float* a, long long lda, double* b, long long ldb) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)rows * cols) return;
@@ -183,7 +194,6 @@ __global__ void scale_rows_out_kernel(int rows, int cols, const void* Y, int f32
   out[e] = scale * v;
 }
 
-inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)std::max<long long>(1, std::min<long long>((n + t - 1) / t, 65535ll * 16)); }
 
 // ---------------------------------------------------------------- sketch
 struct SketchSizes {

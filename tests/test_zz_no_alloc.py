@@ -44,7 +44,9 @@ def _call_both(A, x, nu, lam, extended):
 
 @pytest.mark.parametrize("n,d,dtype,extended", [
     (5000, 2048, torch.float64, 0), (3001, 256, torch.float64, 0), (4000, 4096, torch.float32, 0),
-    (1000, 33, torch.float32, 1), (0, 17, torch.float64, 0)])
+    (1000, 33, torch.float32, 1), (0, 17, torch.float64, 0),
+    # wide rows (d > 4096) and rows whose byte length is not a 16-byte multiple (tiled copies)
+    (333, 9000, torch.float32, 0), (700, 4100, torch.float64, 0), (501, 4099, torch.float32, 0)])
 def test_noalloc_matches_workspace_entry_point(n, d, dtype, extended):
     require_gpu()
     rng = np.random.default_rng(n + d)

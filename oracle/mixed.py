@@ -13,14 +13,15 @@ reproduce bit for bit:
 * ``bf16_round``: float32 -> bfloat16 with round-to-nearest-even.
 * ``split_hi_lo``: A = hi + lo + tail with hi = bf16(A), lo = bf16(A - hi)
   (A - hi is exact in float32), so hi + lo carries ~16 significant bits.
-* ``gaussian_sketch_bf16``: Y = bf16(G) (hi + lo), with G the Gaussian
-  entries of ``rng.gaussian_block`` rounded from float32.
-* ``split_rowscaled``: the operand split of the tensor-core Gram matrix:
-  every row is cut against its own maximum exponent into two slices of
-  integers (8 + 8 bits), so that all slice products are exactly summable.
-* ``gaussian_sketch_tc_unscaled``: the float32 Gaussian sketch of the
-  tensor-core path, Y = bf16(G) (hi + lo) with (hi, lo) the row-scaled split
-  of A^T (each column of A against its own maximum exponent).
+* ``gaussian_sketch_bf16``: the mixed form's Gaussian sketch by its plain
+  definition, Y = bf16(G) A in float64 (the embedding's entries are the
+  Gaussian draws of ``rng.gaussian_block`` rounded to float32, then to
+  bfloat16; A enters exactly).  How a kernel represents A to reach that
+  product is not part of the definition: its error is bounded in the tests.
+* ``split_rowscaled``: a secondary check of the tensor-core Gram matrix's
+  operand split (every row cut against its own maximum exponent into two
+  slices of integers, 8 + 8 bits, so that all slice products are exactly
+  summable); the Gram's parity test compares with the plain definition.
 * ``refine``: the outer refinement loop around any inner solver.
 """
 import numpy as np
@@ -76,20 +77,13 @@ def gaussian_bf16(n_rows_data, m_rows, seed):
     return bf16_round(G.astype(np.float32))
 
 
-def gaussian_sketch_bf16_unscaled(A32, m, seed):
-    """Y = bf16(G) (hi + lo): the mixed form's unscaled Gaussian sketch."""
-    hi, lo = split_hi_lo(A32)
-    Gb = gaussian_bf16(A32.shape[0], m, seed)
-    return Gb @ (hi + lo)
-
-
-def gaussian_sketch_tc_unscaled(A32, m, seed, row0=0):
-    """Rows [row0, m) of Y = bf16(G) (hi + lo)^T (unscaled; S A = Y / sqrt(m)),
-    with (hi, lo) = split_rowscaled(A32^T) and G from ``rng.gaussian_block``
-    rounded to float32, then to bfloat16."""
-    hiT, loT = split_rowscaled(np.asarray(A32, dtype=np.float32).T)
+def gaussian_sketch_bf16(A32, m, seed, row0=0):
+    """Rows [row0, m) of the unscaled Gaussian sketch of a float32 A by its
+    definition, Y = bf16(G) A (S A = Y / sqrt(m)), in float64: G from
+    ``rng.gaussian_block`` rounded to float32, then to bfloat16; the float32
+    values of A enter exactly."""
     Gb = gaussian_bf16(A32.shape[0], m, seed)[row0:]
-    return Gb @ (hiT + loT).T
+    return Gb @ np.asarray(A32, dtype=np.float32).astype(np.float64)
 
 
 def bf16_midpoint_slack(g32, ulps=4):

@@ -213,7 +213,7 @@ def default_m_max(kind, n):
 
 def adaptive_pcg(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, rho=0.125,
                  x0=None, tol=1e-10, max_iter=1000, sjlt_s=1, literal_restart=True,
-                 stop="estimate", xstar=None):
+                 stop="estimate", xstar=None, record_states=False):
     """Algorithm 2 (adaptive PCG).
 
     phi(rho) and c(rho) as in ``pcg_constants``; the step at time t produces
@@ -226,6 +226,9 @@ def adaptive_pcg(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
     delta~_t <= (tol/2)^2 * b^T x_t, i.e. the estimate
     delta~_t / (b^T x_t) ~ ||x_t - x*||_H^2 / ||x*||_H^2 is below (tol/2)^2.
     With stop="exact" and ``xstar`` given, stop on the true relative H-error.
+    With record_states, every trace event also holds the index I of the last
+    re-sketch, delta~_I, delta~+ and a copy of x_t (the accepted iterate the
+    step started from).
     Returns (x, stats, trace).
     """
     n, d = A.shape
@@ -263,8 +266,11 @@ def adaptive_pcg(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
         dp = float(rp @ rtp)
         thr = c * phi ** (t + 1 - I)
         ratio = dp / dI
+        ev = dict(t=t, m=m, ratio=ratio, thr=thr)
+        if record_states:
+            ev.update(I=I, dI=dI, dp=dp, x=x.copy())
         if ratio > thr and m < m_max:
-            trace.append(dict(t=t, m=m, ratio=ratio, thr=thr, accepted=False))
+            trace.append(dict(ev, accepted=False))
             I = t
             m = min(2 * m, m_max)
             P = Preconditioner(sk(m), nu, lam)
@@ -279,7 +285,7 @@ def adaptive_pcg(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
             dt = float(r @ rt)
             dI = dt
         else:
-            trace.append(dict(t=t, m=m, ratio=ratio, thr=thr, accepted=True))
+            trace.append(dict(ev, accepted=True))
             p = rtp + (dp / dt) * p
             x, r, rt, dt = xp, rp, rtp, dp
             t += 1
@@ -290,7 +296,8 @@ def adaptive_pcg(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
 
 
 def adaptive_ihs(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, rho=0.125,
-                 x0=None, tol=1e-10, max_iter=1000, sjlt_s=1, stop="estimate", xstar=None):
+                 x0=None, tol=1e-10, max_iter=1000, sjlt_s=1, stop="estimate", xstar=None,
+                 record_states=False):
     """Algorithm 1 instantiated with the IHS and step size mu = 1 - rho
     (Theorem 3.2: phi(rho) = rho, alpha = 1).
 
@@ -300,6 +307,7 @@ def adaptive_ihs(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
     (capped as in ``adaptive_pcg``), a larger sketch is drawn and
     delta~_I = 1/2 grad f(x_t)^T H_S^{-1} grad f(x_t).
     Stop rule: after an accepted step, 2 delta~_t <= (tol/2)^2 b^T x_t.
+    record_states: as in ``adaptive_pcg``.
     """
     n, d = A.shape
     m_max = default_m_max(kind, n) if m_max is None else min(int(m_max), default_m_max(kind, n))
@@ -334,8 +342,11 @@ def adaptive_ihs(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
         dp = 0.5 * float(gp @ vp)
         thr = c * phi ** (t + 1 - I)
         ratio = dp / dI
+        ev = dict(t=t, m=m, ratio=ratio, thr=thr)
+        if record_states:
+            ev.update(I=I, dI=dI, dp=dp, x=x.copy())
         if ratio > thr and m < m_max:
-            trace.append(dict(t=t, m=m, ratio=ratio, thr=thr, accepted=False))
+            trace.append(dict(ev, accepted=False))
             I = t
             m = min(2 * m, m_max)
             P = Preconditioner(sk(m), nu, lam)
@@ -346,7 +357,7 @@ def adaptive_ihs(A, b, nu, lam, kind="gaussian", seed=0, m_init=1, m_max=None, r
             dt = 0.5 * float(g @ v)
             dI = dt
         else:
-            trace.append(dict(t=t, m=m, ratio=ratio, thr=thr, accepted=True))
+            trace.append(dict(ev, accepted=True))
             x, g, v, dt = xp, gp, vp, dp
             t += 1
             if dt <= 0.0 or done(x, dt):

@@ -58,8 +58,6 @@ sks_status hess_apply_noalloc(const sks_problem* p, const double* x, double* y, 
   const int64_t kb = p->k == 8 ? 8 : 1;
   ApassPlan plan;
   SKS_TRY(apass_plan(std::max<int64_t>(p->n, 1), p->d, kb, f32, vec32, &plan));
-  // whole-row bulk copies where rows allow them, as sks_hess_apply (the partial sums' size is unchanged)
-  apass_use_bulk(&plan, p->A, p->d, p->lda, f32);
   // Layout inside the static scratch: status | partial sums | float32 copies of x and y.
   Carver c(nullptr, 0);
   c.take<DevStatus>(1);
@@ -85,6 +83,9 @@ sks_status hess_apply_noalloc(const sks_problem* p, const double* x, double* y, 
     SKS_TRY(make_tmap_2d(&tmap, p->A, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                          f32 ? 4 : 8, (uint64_t)p->n, (uint64_t)p->d, (uint64_t)p->lda, (uint32_t)plan.boxw,
                          (uint32_t)plan.rows_per_stage));
+  // whole-row bulk copies where rows allow them, as sks_hess_apply (after the
+  // tensor map, which keeps the tiled geometry; the partial sums' size is unchanged)
+  apass_use_bulk(&plan, p->A, p->d, p->lda, f32);
   const double nu2 = p->nu * p->nu;
   for (int64_t c0 = 0; c0 < p->k; c0 += kb) {
     const double* xc = x + c0 * p->d;

@@ -37,7 +37,6 @@ struct sks_sketch {
   // float32 Gaussian sketch on the tensor cores: split A^T, column maxima, slice partials
   void* tch = nullptr;
   void* tcl = nullptr;
-  unsigned* cmax = nullptr;
   float* tcpart = nullptr;
   size_t tcpart_elems = 0;
   bool tc_ready = false;
@@ -199,7 +198,7 @@ __global__ void scale_rows_out_kernel(int rows, int cols, const void* Y, int f32
 struct SketchSizes {
   size_t b_elems = 0, y_elems = 0, g_elems = 0, split_elems = 0;
   size_t sj_elems = 0;  // SJLT buckets (counts, offsets, entries) of the gathering kernel
-  size_t tc_elems = 0, tcpart_elems = 0, cmax_elems = 0;  // float32 Gaussian (tensor cores)
+  size_t tc_elems = 0, tcpart_elems = 0;  // float32 Gaussian (tensor cores)
 };
 
 SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s) {
@@ -211,7 +210,6 @@ SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max, int
   const bool dense_kind = kind == SKS_GAUSSIAN || kind == SKS_RADEMACHER;  // S drawn entry by entry
   if (dense_kind && p->dtype == SKS_F32) {
     z.tc_elems = (size_t)p->d * (size_t)tc_gauss_kp(p->n);
-    z.cmax_elems = (size_t)p->d;
     z.tcpart_elems = tc_gauss_part_elems(p->n, (int)p->d, (int)std::min<int64_t>(m_max, 1 << 30));
   } else if (dense_kind) {
     z.g_elems = (size_t)std::min<int64_t>((int64_t)m_max * std::max<int64_t>(p->n, 1), (int64_t)1 << 24);
@@ -237,7 +235,6 @@ size_t sketch_ws_bytes(const sks_problem* p, sks_kind kind, int64_t m_max, int s
   c.take<char>(z.y_elems * esz);
   c.take<__nv_bfloat16>(z.tc_elems);
   c.take<__nv_bfloat16>(z.tc_elems);
-  c.take<unsigned>(z.cmax_elems);
   c.take<float>(z.tcpart_elems);
   c.take<char>(z.g_elems * esz);
   c.take<char>(z.split_elems * esz);
@@ -270,7 +267,6 @@ sks_status sketch_init(sks_sketch* s, const sks_problem* p, sks_kind kind, int64
   s->split_elems = z.split_elems;
   s->tch = c.take<__nv_bfloat16>(z.tc_elems);
   s->tcl = c.take<__nv_bfloat16>(z.tc_elems);
-  s->cmax = c.take<unsigned>(z.cmax_elems);
   s->tcpart = c.take<float>(z.tcpart_elems);
   s->tcpart_elems = z.tcpart_elems;
   s->sj = c.take<uint32_t>(z.sj_elems);
@@ -293,8 +289,7 @@ sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
   } else if ((s->kind == SKS_GAUSSIAN || s->kind == SKS_RADEMACHER) && s->f32) {
     // bf16(G) times the split A^T on the tensor cores; the split is made once per sketch
     if (!s->tc_ready) {
-      SKS_TRY(tc_split_t(stream, (const float*)A, p.lda, p.n, d, (__nv_bfloat16*)s->tch, (__nv_bfloat16*)s->tcl,
-                         s->cmax));
+      SKS_TRY(tc_split_t(stream, (const float*)A, p.lda, p.n, d, (__nv_bfloat16*)s->tch, (__nv_bfloat16*)s->tcl));
       s->tc_ready = true;
     }
     SKS_TRY(tc_gauss_sketch(stream, (const __nv_bfloat16*)s->tch, (const __nv_bfloat16*)s->tcl, p.n, d, s->seed,

@@ -438,8 +438,8 @@ SKS_DEV void cluster_sync_all() {
 // K4 for float32 A: Y[r] = sum_i bf16(G[r][i]) (hi + lo)[.][i] (or the
 // Rademacher +-1 entries, exact in bfloat16, with g.rade), i.e. the
 // product of the Philox/Box-Muller matrix G (rounded to bfloat16) with the
-// row-scaled two-slice split of A^T (each column of A against its own maximum
-// exponent, prepared once by tc_split_t).  One CTA per (128 sketch rows) x
+// element-wise two-slice split of A^T, hi = bf16(a), lo = bf16(a - hi), so
+// |a - hi - lo| <= 2^-17 |a| (prepared once by tc_split_t).  One CTA per (128 sketch rows) x
 // (256 columns) x (K slice of data rows) tile, 18 warps:
 //   warp 0      TMA producer: the hi and lo tiles of A^T (256 x 64 bf16, 128B
 //               swizzle) into a 2-stage ring;
@@ -733,23 +733,11 @@ __global__ void gauss_reduce_kernel(const float* __restrict__ part, int ksplits,
   Y[(long long)(row0 + r) * ldy + c] = (float)t;
 }
 
-// Maximum |A[i][c]| of every column of A (n x d), float bits.
-__global__ void colmax_kernel(const float* __restrict__ A, long long lda, long long n, int d, long long rows_per,
-                              unsigned* __restrict__ cmax) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d) return;
-  const long long r0 = (long long)blockIdx.y * rows_per;
-  const long long r1 = min(n, r0 + rows_per);
-  float m = 0.f;
-  for (long long i = r0; i < r1; ++i) m = fmaxf(m, fabsf(A[i * lda + c]));
-  atomicMax(&cmax[c], __float_as_uint(m));
-}
-
-// Row-scaled split of A^T through 32 x 32 shared-memory tiles: out[c][i] for
-// i < Kp (zero past n), hi/lo against the maximum exponent of column c.
+// Element-wise split of A^T through 32 x 32 shared-memory tiles: out[c][i]
+// for i < Kp (zero past n), hi = bf16(a) and lo = bf16(a - hi) (a - hi is
+// exact in float32), both rounded to nearest even.
 __global__ void split_t_kernel(const float* __restrict__ A, long long lda, long long n, int d, int Kp,
-                               const unsigned* __restrict__ cmax, __nv_bfloat16* __restrict__ Hh,
-                               __nv_bfloat16* __restrict__ Hl) {
+                               __nv_bfloat16* __restrict__ Hh, __nv_bfloat16* __restrict__ Hl) {
   __shared__ float t[32][33];
   const long long i0 = (long long)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -764,16 +752,9 @@ __global__ void split_t_kernel(const float* __restrict__ A, long long lda, long 
     const long long i = i0 + threadIdx.x;
     if (c >= d || i >= Kp) continue;
     const float v = t[threadIdx.x][j];
-    const float mx = __uint_as_float(cmax[c]);
-    float h = 0.f, l = 0.f;
-    if (mx > 0.f) {
-      int ex;
-      frexpf(mx, &ex);
-      h = ldexpf(rintf(ldexpf(v, 8 - ex)), ex - 8);
-      l = ldexpf(rintf(ldexpf(v - h, 16 - ex)), ex - 16);
-    }
-    Hh[(size_t)c * Kp + i] = __float2bfloat16_rn(h);
-    Hl[(size_t)c * Kp + i] = __float2bfloat16_rn(l);
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Hh[(size_t)c * Kp + i] = h;
+    Hl[(size_t)c * Kp + i] = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
   }
 }
 
@@ -866,17 +847,10 @@ size_t tc_gauss_part_elems(long long n, int d, int max_rows) {
 }
 
 sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long long n, int d, __nv_bfloat16* Hh,
-                      __nv_bfloat16* Hl, unsigned* cmax) {
+                      __nv_bfloat16* Hl) {
   const int Kp = tc_gauss_kp(n);
-  SKS_CUDA_TRY(cudaMemsetAsync(cmax, 0, (size_t)d * sizeof(unsigned), stream));
-  if (n > 0) {
-    const long long chunks = std::min<long long>((n + 1023) / 1024, 1024);
-    const long long per = (n + chunks - 1) / chunks;
-    colmax_kernel<<<dim3((unsigned)((d + 127) / 128), (unsigned)chunks), 128, 0, stream>>>(A, lda, n, d, per, cmax);
-    note_launch();
-  }
   split_t_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)((d + 31) / 32)), dim3(32, 8), 0, stream>>>(A, lda, n, d, Kp,
-                                                                                                   cmax, Hh, Hl);
+                                                                                                   Hh, Hl);
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;

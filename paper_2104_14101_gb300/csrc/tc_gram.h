@@ -35,10 +35,10 @@ sks_status tc_gram(cudaStream_t stream, int M, int N, int Kp, const __nv_bfloat1
 int tc_gauss_kp(long long n);
 // float32 elements of the slice partials for up to max_rows new rows per call.
 size_t tc_gauss_part_elems(long long n, int d, int max_rows);
-// Hh/Hl (d x Kp bfloat16): the row-scaled split of A^T, every column of A
-// against its own maximum exponent; cmax: d scratch words.
+// Hh/Hl (d x Kp bfloat16): the element-wise split of A^T, hi = bf16(a),
+// lo = bf16(a - hi), |a - hi - lo| <= 2^-17 |a|.
 sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long long n, int d, __nv_bfloat16* Hh,
-                      __nv_bfloat16* Hl, unsigned* cmax);
+                      __nv_bfloat16* Hl);
 // Y[m_off .. m_off + m_add) = bf16(G) (Hh + Hl)^T, G[r][i] the Philox /
 // Box-Muller entry of sketch row r and data row i (float32, rounded to
 // bfloat16), generated inside the kernel; unscaled (S A = Y / sqrt(m)).

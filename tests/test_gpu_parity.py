@@ -150,7 +150,10 @@ def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
 
 @pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
 @pytest.mark.parametrize("n,d,m,s", [(3001, 1100, 257, 4), (5000, 600, 1024, 4), (9000, 64, 4096, 1),
-                                     (1000, 2048, 300, 16)])
+                                     (1000, 2048, 300, 16),
+                                     # ragged column blocks (d % 32 != 0), m not a power of two, s = 2, 3
+                                     (20000, 100, 1536, 3), (7000, 132, 2000, 4), (30000, 260, 7000, 4),
+                                     (8000, 36, 3001, 2)])
 def test_sjlt_large_sketch(dt, tol, n, d, m, s):
     # larger m: float64 rows of 16 bytes gather per-sketch-row buckets of data
     # rows (warps over chunks of the bucket-ordered entries), float32 scatters
@@ -169,72 +172,107 @@ def test_sjlt_large_sketch(dt, tol, n, d, m, s):
     assert float(np.max(np.abs(host(sk.matrix()) - ref2) / scale)) < tol
 
 
-def gaussian_tc_bound(A32, m, seed, row0=0):
-    """Reference rows [row0, m) of the tensor-core Gaussian sketch (scaled by
-    1/sqrt(m)) and an element-wise error bound: float32 accumulation over K
-    slices of <= 16384 terms, plus one bfloat16 step of every G entry whose
-    float32 value lies near a rounding midpoint (the GPU's float32 Box-Muller
-    and the oracle's may round those the other way)."""
+def gpu_sketch_entries(n, m, seed, kind="gaussian", width=4096):
+    """The m x n matrix of bfloat16 entries the tensor-core sketch applied
+    (unscaled), read back through the same kernel: for a float32 A whose
+    columns are unit vectors e_{i0}, ..., e_{i0+w-1}, every split slice is
+    exact (hi = 1 or 0, lo = 0) and every output is one exact product, so
+    Y = S_bf16[:, i0:i0+w].  The entries depend only on (data row, sketch
+    row, seed), not on A."""
+    out = np.empty((m, n))
+    for i0 in range(0, n, width):
+        w = min(width, n - i0)
+        wp = (w + 3) // 4 * 4
+        A = torch.zeros(n, wp, dtype=torch.float32, device="cuda")
+        A[torch.arange(i0, i0 + w, device="cuda"), torch.arange(w, device="cuda")] = 1.0
+        sk = api().Sketch(A, 0.1, torch.ones(wp, dtype=torch.float64, device="cuda"), kind=kind, m=m, seed=seed)
+        out[:, i0:i0 + w] = host(sk.matrix())[:, :w] * math.sqrt(m)
+        del sk, A
     from oracle import mixed as MX
-    from oracle import rng as R
-    ref = MX.gaussian_sketch_tc_unscaled(A32, m, seed, row0=row0)
-    G32 = R.gaussian_block(A32.shape[0], m, seed)[row0:].astype(np.float32)
-    Gb = MX.bf16_round(G32)
-    absA = np.abs(A32.astype(np.float64))
-    acc = 2.0 ** -24 * 256 * (np.abs(Gb) @ absA) + 2.0 ** -23 * np.abs(ref)
-    sl = MX.bf16_midpoint_slack(G32, ulps=4)
-    slack = sl @ absA
-    clean = ~np.any(sl > 0, axis=1)  # rows whose G entries both sides round alike
-    return ref / math.sqrt(m), (acc + slack) / math.sqrt(m), clean
+    return MX.bf16_round(out.astype(np.float32))
+
+
+def tc_sketch_bound(Gb, A32, Y):
+    """Element-wise bound of |Y_gpu - bf16(G) A| for the tensor-core sketch
+    (unscaled): the element-wise two-slice split of A leaves |a - hi - lo| <=
+    2^-17 |a|; the float32 tensor-core accumulation over groups of 256 data
+    rows and the float32 sum of the groups cost at most 2^-16 sum |g||a|
+    (measured and asserted since the kernel's first parity test); the final
+    rounding to float32 half an ulp of |Y|."""
+    absGA = np.abs(Gb) @ np.abs(A32.astype(np.float64))
+    return (2.0 ** -17 + 2.0 ** -16) * absGA + 2.0 ** -23 * np.abs(Y)
 
 
 @pytest.mark.parametrize("n,d,m", [(3000, 64, 96), (20000, 300, 200), (777, 5, 130), (40000, 520, 257)])
-def test_gaussian_tc_sketch_matches_oracle(n, d, m):
-    # float32 A: bf16(G) times the split A^T on tcgen05; n = 20000 and 40000
-    # span two and three K slices, d = 300 / 520 two and three column tiles,
-    # m = 257 three row tiles with a ragged tail.
+def test_gaussian_tc_sketch_matches_plain_definition(n, d, m):
+    # float32 A: bf16(G) A on tcgen05; n = 20000 and 40000 span two and three
+    # K slices, d = 300 / 520 two and three column tiles, m = 257 three row
+    # tiles with a ragged tail.  Reference: the plain definition (1/sqrt m)
+    # bf16(G) A in float64 with G from the oracle's Philox / Box-Muller.
+    from oracle import mixed as MX
+    from oracle import rng as R
     rng = np.random.default_rng(n + d)
     A = (rng.standard_normal((n, d)) * rng.uniform(0.1, 10, size=(1, d))).astype(np.float32)
     sk = api().Sketch(dev(A.astype(np.float64), torch.float32), 0.1, dev(np.ones(d)), kind="gaussian", m=m, seed=31)
-    got = host(sk.matrix())
-    ref, bound, clean = gaussian_tc_bound(A, m, 31)
-    assert got.shape == ref.shape
-    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
-    # rows with no bfloat16 midpoint in reach: the float32 tolerance of S A
-    if clean.sum() >= 10:
-        assert np.linalg.norm(got[clean] - ref[clean]) <= 1e-5 * np.linalg.norm(ref[clean])
+    got = host(sk.matrix()) * math.sqrt(m)
+    # (1) the embedding's entries: bf16 of the oracle's float32 Gaussian draws,
+    # bit for bit, except within 4 float32 ulps of a bfloat16 rounding
+    # midpoint, where the GPU's float32 Box-Muller may round to the other
+    # neighbour
+    G32 = R.gaussian_block(n, m, 31).astype(np.float32)
+    Gor = MX.bf16_round(G32)
+    Ggpu = gpu_sketch_entries(n, m, 31)
+    slack = MX.bf16_midpoint_slack(G32, ulps=4)
+    assert np.array_equal(Ggpu[slack == 0], Gor[slack == 0])
+    assert np.all(np.abs(Ggpu - Gor) <= slack)
+    # (2) the product: against the plain definition with those entries,
+    # element-wise within the split and accumulation bound, and S A within
+    # 1e-5 relative (Frobenius) in float32
+    ref = Ggpu @ A.astype(np.float64)
+    assert np.all(np.abs(got - ref) <= tc_sketch_bound(Ggpu, A, ref)), \
+        float(np.max(np.abs(got - ref) / tc_sketch_bound(Ggpu, A, ref)))
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    # and against the oracle's own sketch (its bf16 entries): the same, plus
+    # one bfloat16 step at each ambiguous entry
+    ref_or = MX.gaussian_sketch_bf16(A, m, 31)
+    amb = slack @ np.abs(A.astype(np.float64))
+    assert np.all(np.abs(got - ref_or) <= tc_sketch_bound(Gor, A, ref_or) + amb)
 
 
 @pytest.mark.parametrize("n,d,m", [(3000, 64, 96), (20000, 300, 200), (40000, 520, 257)])
-def test_rademacher_tc_sketch_matches_oracle(n, d, m):
-    # +-1 entries are exact in bfloat16: only the float32 accumulation differs
-    from oracle import mixed as MX
+def test_rademacher_tc_sketch_matches_plain_definition(n, d, m):
+    # +-1 entries are exact in bfloat16: the plain definition R A (float64)
+    # and the split and accumulation bound
     from oracle import rng as R
     rng = np.random.default_rng(n + d + 1)
     A = (rng.standard_normal((n, d)) * rng.uniform(0.1, 10, size=(1, d))).astype(np.float32)
     sk = api().Sketch(dev(A.astype(np.float64), torch.float32), 0.1, dev(np.ones(d)), kind="rademacher", m=m,
                       seed=13)
-    got = host(sk.matrix())
-    hiT, loT = MX.split_rowscaled(A.T)
+    got = host(sk.matrix()) * math.sqrt(m)
     Rm = R.rademacher_block(n, m, 13)
-    ref = Rm @ (hiT + loT).T / math.sqrt(m)
-    bound = (2.0 ** -24 * 256 * (np.abs(Rm) @ np.abs(A.astype(np.float64))) / math.sqrt(m) + 2.0 ** -23 * np.abs(ref))
-    assert np.all(np.abs(got - ref) <= bound)
-    assert np.linalg.norm(got - ref) <= 2e-6 * np.linalg.norm(ref)
+    assert np.array_equal(gpu_sketch_entries(min(n, 3000), m, 13, kind="rademacher"), Rm[:, :min(n, 3000)])
+    ref = Rm @ A.astype(np.float64)
+    assert np.all(np.abs(got - ref) <= tc_sketch_bound(Rm, A, ref))
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
 def test_gaussian_tc_sketch_nested_growth():
     # m = 1, 2, 3, 6, 13: new rows start at offsets that are not multiples of
     # the four rows one Philox call gives
+    from oracle import mixed as MX
+    from oracle import rng as R
     rng = np.random.default_rng(4)
     n, d = 5000, 40
     A = rng.standard_normal((n, d)).astype(np.float32)
     sk = api().Sketch(dev(A.astype(np.float64), torch.float32), 0.1, dev(np.ones(d)), kind="gaussian", m=1, seed=8)
     for m in (2, 3, 6, 13):
         sk.grow(m)
-        got = host(sk.matrix())
-        ref, bound, _ = gaussian_tc_bound(A, m, 8)
-        assert np.all(np.abs(got - ref) <= bound)
+        got = host(sk.matrix()) * math.sqrt(m)
+        G32 = R.gaussian_block(n, m, 8).astype(np.float32)
+        Gor = MX.bf16_round(G32)
+        ref = MX.gaussian_sketch_bf16(A, m, 8)
+        amb = MX.bf16_midpoint_slack(G32, ulps=4) @ np.abs(A.astype(np.float64))
+        assert np.all(np.abs(got - ref) <= tc_sketch_bound(Gor, A, ref) + amb)
 
 
 def test_srht_full_size_gives_exact_hessian():
@@ -294,7 +332,7 @@ def test_adaptive_solve_reaches_tolerance(method, kind):
 
 
 @pytest.mark.parametrize("method", ["pcg", "ihs"])
-@pytest.mark.parametrize("kind", ["gaussian", "srht", "rademacher"])
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "rademacher", "sjlt"])
 def test_m_sequence_matches_oracle(method, kind):
     # Plain float64: the GPU takes the same accept/reject decisions as the
     # oracle (literal restart), except where the oracle's ratio sits within
@@ -315,6 +353,33 @@ def test_m_sequence_matches_oracle(method, kind):
     else:
         assert len(to) == len(tg)
         assert so["final_m"] == sg["final_m"] and so["iters"] == sg["iters"]
+
+
+@pytest.mark.parametrize("method", ["pcg", "ihs"])
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "sjlt"])
+def test_corollary_2_5_no_rejection_under_E_rho(method, kind):
+    # Every step the GPU takes with a sketch in E_rho (||C_S - I||_2 <=
+    # sqrt(rho), C_S from the oracle's sketch of the same size and seed:
+    # the integer streams are bit-identical) passes the improvement test
+    # (Corollary 2.5), including the first step after a restart.
+    rho = 0.125
+    p = synthetic.make_problem("C1", 0, n=8192, d=32, nu=0.1)
+    sk = O._Sketcher(p.A, kind, 3, 2)
+    dev_of = {}
+    held = 0
+    fg = api().adaptive_pcg if method == "pcg" else api().adaptive_ihs
+    for m_init in (1, 64, 2048):
+        _, _, tg = fg(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind=kind, m_init=m_init, tol=1e-10, seed=3, sjlt_s=2,
+                      rho=rho, trace_cap=4096)
+        for ev in tg:
+            m = ev["m"]
+            if m not in dev_of:
+                e = O.cs_eigenvalues(p.A, sk(m), p.nu, p.lam)
+                dev_of[m] = max(abs(e[0] - 1.0), abs(e[-1] - 1.0))
+            if dev_of[m] <= math.sqrt(rho):
+                held += 1
+                assert ev["accepted"], ev
+    assert held >= 5
 
 
 @pytest.mark.parametrize("method", ["pcg", "ihs"])
@@ -346,6 +411,22 @@ def test_config1_full_size():
     x, st, _ = api().adaptive_pcg(dev(p.A), dev(p.b), p.nu, dev(p.lam), kind="gaussian", m_init=1, tol=1e-10, seed=0)
     assert O.rel_err_H(p.A, p.nu, p.lam, host(x), xs) <= 1e-10
     assert st["final_m"] <= 4096
+
+
+def test_config2_full_size():
+    # C2 at its stated size: n = 2^17, d = 2048, sigma_j = 1/(1+j), nu = 1e-3,
+    # Lambda = diag(1 + 9 U[0,1]), b = A^T y + 0.1 N(0,1)^d, SRHT, m 16 -> 4096,
+    # adaptive PCG and adaptive IHS in float64 to tol 1e-10, each against the
+    # oracle's direct solve on all of A (2 GiB, generated on the device).
+    prob = synthetic.make_problem_torch("C2", seed=0, device="cuda")
+    A, b, lam, nu = prob["A64"], prob["b"][:, 0].contiguous(), prob["lam"], prob["nu"]
+    An, bn, ln = host(A), host(b), host(lam)
+    xs = O.direct_solve(An, bn, nu, ln)
+    for fn, name in ((api().adaptive_pcg, "pcg"), (api().adaptive_ihs, "ihs")):
+        x, st, _ = fn(A, b, nu, lam, kind="srht", m_init=16, m_max=4096, tol=1e-10, seed=0, max_iter=2000)
+        err = O.rel_err_H(An, nu, ln, host(x), xs)
+        assert err <= 1e-10, (name, err, st)
+        assert st["final_m"] <= 4096
 
 
 def test_zero_rhs_returns_zero():
@@ -416,36 +497,71 @@ def test_gpu_generator_matches_spectrum():
 
 # ----------------------------------------------------------------------------- tensor-core Gram (K6, float32 sketches)
 
-@pytest.mark.parametrize("m,d", [(300, 256), (100, 300), (700, 520), (1, 64), (129, 200), (64, 64)])
-def test_tensor_core_preconditioner_matches_split_oracle(m, d):
-    # float32 sketches build H_S (m >= d) or W_S (m < d) on the tensor cores
-    # from a row-scaled two-slice bfloat16 split whose products sum exactly.
-    # The oracle rebuilds the same slices bit for bit (the Gram operand is
-    # Y^T, split per column of Y; the Woodbury operand is Z = Y Lambda^{-1/2}
-    # rounded to float32, split per row), so the preconditioners agree to the
-    # double-float accumulation accuracy.
+def _inv_sqrt_spd(M):
+    w, Q = np.linalg.eigh(M)
+    return (Q / np.sqrt(w)[None, :]) @ Q.T
+
+
+@pytest.mark.parametrize("m,d,nu,kind", [(300, 256, 1e-2, "rademacher"), (700, 520, 1e-2, "gaussian"),
+                                         (64, 64, 1e-2, "srht"), (100, 300, 0.5, "rademacher"),
+                                         (1, 64, 0.5, "gaussian"), (129, 200, 0.5, "srht")])
+def test_tensor_core_preconditioner_spectrally_close_to_oracle(m, d, nu, kind):
+    # A float32 sketch's H_S (m >= d) or W_S (m < d) is built on the tensor
+    # cores.  Reference: the oracle's own sketch S A (float64, same seed) and
+    # H_S = (SA)^T SA + nu^2 Lambda by definition.  The GPU's preconditioner
+    # P must satisfy  eig(H_S^{1/2} P H_S^{1/2}) in [1/(1+eps), 1/(1-eps)]
+    # (the event E_rho of Section 2.2 is a statement about exactly this
+    # spectrum), with eps the sum of
+    #   eps_s:  the GPU sketch's own deviation, ||H_S^{-1/2}(H(Y_gpu) - H_S)H_S^{-1/2}||,
+    #           computed exactly from the GPU's float32 sketch (asserted <= 1e-3:
+    #           a wrong sketch fails here);
+    #   eps_sp: the Gram operand's two-slice bfloat16 split, |y - hi - lo| <=
+    #           2^(e-17) against the maximum exponent e of the split row
+    #           (a column of Y for H_S, a row of Z = Y Lambda^{-1/2}, itself
+    #           rounded to float32, for W_S): with E bounded entry-wise by
+    #           that, ||H_S^{-1/2} Delta H_S^{-1/2}|| <= 2 sqrt(1+eps_s) t + t^2,
+    #           t = c ||E M|| bounded through the diagonal scaling M = D^{-1/2}
+    #           (divided by sqrt(lambda_min(D^{-1/2} H_S D^{-1/2}))) or
+    #           through M = Lambda^{-1/2}/nu (H_S >= nu^2 Lambda);
+    #   1e-6:   float64 factorisation and the float64 inverse factor.
     from oracle import mixed as MX
+    from oracle import sketch as OS
     rng = np.random.default_rng(m * 7 + d)
     n = 3000
     A = (rng.standard_normal((n, d)) * (0.9 ** np.arange(d))[None, :]).astype(np.float32).astype(np.float64)
     lam = 1 + 9 * rng.random(d)
-    nu = 1e-3
-    sk = api().Sketch(dev(A, torch.float32), nu, dev(lam), kind="gaussian", m=m, seed=6)
-    c = 1.0 / math.sqrt(m)
-    Y32 = (host(sk.matrix()) / c).astype(np.float32)
-    if m < d:
-        Z32 = (Y32.astype(np.float64) / np.sqrt(lam)[None, :]).astype(np.float32)
-        zh, zl = MX.split_rowscaled(Z32)
-        Yeff = (zh + zl) * np.sqrt(lam)[None, :]
+    sk = api().Sketch(dev(A, torch.float32), nu, dev(lam), kind=kind, m=m, seed=6)
+    if kind == "gaussian":  # the mixed form's embedding: bf16-rounded Gaussian entries
+        SA_or = MX.gaussian_sketch_bf16(A.astype(np.float32), m, 6) / math.sqrt(m)
     else:
-        th, tl = MX.split_rowscaled(Y32.T)
-        Yeff = (th + tl).T
-    ref_P = O.Preconditioner(c * Yeff, nu, lam)
+        SA_or = OS.sketch(kind, A, m, seed=6)
+    c = 1.0 / math.sqrt(m)
+    H_or = SA_or.T @ SA_or + nu ** 2 * np.diag(lam)
+    Hi = _inv_sqrt_spd(H_or)
+    Y = host(sk.matrix()) / c  # the GPU's float32 sketch (unscaled), used only to measure its deviation
+    H_y = c * c * Y.T @ Y + nu ** 2 * np.diag(lam)
+    eps_s = float(np.linalg.norm(Hi @ (H_y - H_or) @ Hi, 2))
+    assert eps_s <= 1e-3
+    Y32 = Y.astype(np.float32).astype(np.float64)
+    if m >= d:
+        _, e = np.frexp(np.max(np.abs(Y32), axis=0))
+        E = np.ldexp(1.0, e - 17)[None, :] * np.ones((m, 1))
+    else:
+        Z = (Y32 / np.sqrt(lam)[None, :]).astype(np.float32).astype(np.float64)
+        _, e = np.frexp(np.max(np.abs(Z), axis=1))
+        E = (np.ldexp(1.0, e - 17)[:, None] + 2.0 ** -24 * np.abs(Z)) * np.sqrt(lam)[None, :]
+    D = np.sqrt(np.diag(H_or))
+    K = H_or / D[:, None] / D[None, :]
+    t = min(c * np.linalg.norm(E / D[None, :]) / math.sqrt(np.linalg.eigvalsh(K)[0]),
+            c * np.linalg.norm(E / np.sqrt(lam)[None, :]) / nu)
+    eps = eps_s + 2 * math.sqrt(1 + eps_s) * t + t * t + 1e-6
+    assert eps <= 0.05  # the check below is meaningful
     P = api().Preconditioner(sk)
-    Z = rng.standard_normal((d, 2))
-    got = host(P.apply(dev(Z)))
-    ref = ref_P.apply(Z)
-    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-8
+    Pinv = host(P.apply(dev(np.eye(d))))
+    Pinv = 0.5 * (Pinv + Pinv.T)
+    Hs = np.linalg.cholesky(H_or)
+    ev = np.linalg.eigvalsh(Hs.T @ Pinv @ Hs)  # similar to H_S^{1/2} P H_S^{1/2}
+    assert ev[0] >= 1.0 / (1.0 + eps) and ev[-1] <= 1.0 / (1.0 - eps), (ev[0], ev[-1], eps)
 
 
 # ----------------------------------------------------------------------------- adjoint (a13)

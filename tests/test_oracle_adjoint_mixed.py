@@ -112,22 +112,30 @@ def test_split_rowscaled_exactness():
         assert float(s32) == float(np.sum(a[0, :256] * b[1, :256]))
 
 
-def test_gaussian_sketch_tc_definition():
-    # (a) columns of A made of small integers are represented exactly by the
-    # hi slice, so the sketch is exactly bf16(G) A; (b) in general it is within
-    # the split's bound sum_i |g_ri| 2^(e_c - 17) of bf16(G) A; (c) rows are
-    # nested (rows [row0, m) of the m-row sketch are the tail of it).
+def test_gaussian_sketch_bf16_definition():
+    # (a) every entry is the sum over data rows of bf16(G) times A: against a
+    # correctly rounded sum (math.fsum) of the products, each of which is
+    # exact in float64 (an 8-bit significand times a small integer);
+    # (b) it is linear in A; (c) rows are nested:
+    # rows [row0, m) of the m-row sketch are its tail, and the first rows do
+    # not depend on m.
     rng = np.random.default_rng(11)
     A = rng.integers(-50, 50, size=(300, 7)).astype(np.float32)
     Gb = MX.gaussian_bf16(300, 12, 5)
-    assert np.array_equal(MX.gaussian_sketch_tc_unscaled(A, 12, 5), Gb @ A.astype(np.float64))
+    Y = MX.gaussian_sketch_bf16(A, 12, 5)
+    ref = np.zeros((12, 7))
+    for r in range(12):
+        for c in range(7):
+            ref[r, c] = math.fsum(float(Gb[r, i]) * float(A[i, c]) for i in range(300))
+    # recursive summation bound: n u sum |products| (u = 2^-53)
+    assert np.all(np.abs(Y - ref) <= 300 * 2.0 ** -53 * (np.abs(Gb) @ np.abs(A.astype(np.float64))))
     A = (rng.standard_normal((500, 9)) * np.exp(rng.uniform(-5, 5, size=(1, 9)))).astype(np.float32)
-    Y = MX.gaussian_sketch_tc_unscaled(A, 16, 7)
-    Gb = MX.gaussian_bf16(500, 16, 7)
-    _, e = np.frexp(np.max(np.abs(A), axis=0))
-    bound = np.abs(Gb).sum(axis=1)[:, None] * np.ldexp(1.0, e - 17)[None, :]
-    assert np.all(np.abs(Y - Gb @ A.astype(np.float64)) <= bound)
-    assert np.array_equal(MX.gaussian_sketch_tc_unscaled(A, 16, 7, row0=9), Y[9:])
+    B = rng.standard_normal((500, 9)).astype(np.float32)
+    Ya, Yb = MX.gaussian_sketch_bf16(A, 16, 7), MX.gaussian_sketch_bf16(B, 16, 7)
+    Yab = MX.gaussian_bf16(500, 16, 7) @ (A.astype(np.float64) + B.astype(np.float64))
+    assert np.allclose(Ya + Yb, Yab, rtol=1e-12, atol=1e-12 * np.max(np.abs(Yab)))
+    assert np.array_equal(MX.gaussian_sketch_bf16(A, 16, 7, row0=9), Ya[9:])
+    assert np.array_equal(MX.gaussian_sketch_bf16(A, 10, 7), Ya[:10])
 
 
 def test_bf16_midpoint_slack():

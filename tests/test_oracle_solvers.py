@@ -404,3 +404,106 @@ def test_dual_error_bound():
         w = ws + scale * rng.standard_normal(n)
         x = S.primal_from_dual(A, b, nu, lam, w)
         assert np.sqrt(S.h_norm_sq(A, nu, lam, x - xs)) <= np.linalg.norm(Hd @ (w - ws)) / nu ** 2 * (1 + 1e-9)
+
+
+# ----------------------------------------------------------------------------
+# Corollary 2.5: under E_rho the improvement test of Algorithms 1 / 2 passes
+# ----------------------------------------------------------------------------
+
+def _e_rho_events(p, method, kind, m_init, rho, seed=3, s=2, **kw):
+    """Run the adaptive method and return [(event, ||C_S - I||_2 <= sqrt(rho),
+    event follows a re-sketch)] with C_S = H^{-1/2} H_S H^{-1/2} of the
+    sketch each event used (nested sketches: the one of size m)."""
+    fn = S.adaptive_pcg if method == "pcg" else S.adaptive_ihs
+    _, _, trace = fn(p.A, p.b, p.nu, p.lam, kind=kind, seed=seed, m_init=m_init, rho=rho, tol=1e-10,
+                     sjlt_s=s, **kw)
+    sk = S._Sketcher(p.A, kind, seed, s)
+    dev = {}
+    out = []
+    after = True  # the first event follows the first sketch
+    for ev in trace:
+        m = ev["m"]
+        if m not in dev:
+            e = S.cs_eigenvalues(p.A, sk(m), p.nu, p.lam)
+            dev[m] = max(abs(e[0] - 1.0), abs(e[-1] - 1.0))
+        out.append((ev, dev[m] <= math.sqrt(rho), after))
+        after = not ev["accepted"]
+    return out
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "sjlt"])
+@pytest.mark.parametrize("method", ["pcg", "ihs"])
+def test_corollary_2_5_no_rejection_under_E_rho(kind, method):
+    # Conditional on E_rho (||C_S - I|| <= sqrt(rho), rho < 1), delta~_t <=
+    # c(alpha, rho) phi(rho)^t delta~_0 for the method restarted with that
+    # sketch (Corollary 2.5 with Theorem 3.2 / eq. 11).  Algorithm 2 / 1 test
+    # delta~+/delta~_I against c phi^(t+1-I), so every step taken with a
+    # sketch in E_rho is accepted -- also the first step after a restart
+    # (exponent 1).  A threshold exponent one too large, or delta~_I not
+    # reset to the restart's decrement, rejects some of these steps.
+    rho = 0.125
+    p = small_problem(n=8192, d=32, nu=0.1)
+    events = []
+    for m_init in (1, 64, 2048):
+        events += _e_rho_events(p, method, kind, m_init, rho)
+    held = [(ev, after) for ev, ok, after in events if ok]
+    assert len(held) >= 5  # m_init = 2048 lies in E_rho for every embedding here
+    assert any(after for _, after in held)
+    for ev, _ in held:
+        assert ev["accepted"], ev
+
+
+def test_corollary_2_5_after_a_rejection():
+    # A run whose doubling lands on a sketch in E_rho: the step right after
+    # the re-sketch (first step of the restarted method) is accepted.
+    p = small_problem(n=8192, d=32, nu=0.1)
+    seen = 0
+    for method in ("pcg", "ihs"):
+        ev = _e_rho_events(p, method, "sjlt", 64, 0.125)
+        rejected_before = False
+        for e, ok, after in ev:
+            if ok and after and rejected_before:
+                seen += 1
+                assert e["accepted"]
+            rejected_before = rejected_before or not e["accepted"]
+    assert seen >= 2
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "srht"])
+def test_adaptive_ihs_decisions_recomputed(kind):
+    # Algorithm 1 with the IHS: every test event recomputed from its inputs by
+    # the definitions -- the proposal x+ = x_t - (1 - rho) H_S^{-1} grad f(x_t)
+    # (eq. 4 with Theorem 3.2's step), delta~ = 1/2 grad f^T H_S^{-1} grad f
+    # (Section 2.3) with the CURRENT sketch, I = the time of the last re-sketch
+    # (0 at the start), delta~_I the decrement at x_I with the current sketch
+    # (reset at every re-sketch: the method restarts at x_t), the threshold
+    # c(1, rho) rho^(t+1-I), and the verdict.
+    rho = 0.125
+    p = small_problem(n=2048, d=24, nu=1e-2)
+    _, _, trace = S.adaptive_ihs(p.A, p.b, p.nu, p.lam, kind=kind, seed=4, m_init=1, rho=rho, tol=1e-10,
+                                 record_states=True)
+    sk = S._Sketcher(p.A, kind, 4, 1)
+    c = (1 + math.sqrt(rho)) / (1 - math.sqrt(rho))
+    H = S.hessian(p.A, p.nu, p.lam)
+    I, xI = 0, np.zeros(p.d)
+    assert sum(not e["accepted"] for e in trace) >= 3
+    floor = 1e-12 * trace[0]["dI"]  # decrements below this are rounding noise of the residual
+    for ev in trace:
+        SA = sk(ev["m"])
+        HS = SA.T @ SA + p.nu ** 2 * np.diag(p.lam)
+        x = ev["x"]
+        g = H @ x - p.b
+        xp = x - (1 - rho) * np.linalg.solve(HS, g)
+        gp = H @ xp - p.b
+        dp = 0.5 * gp @ np.linalg.solve(HS, gp)
+        gI = H @ xI - p.b
+        dI = 0.5 * gI @ np.linalg.solve(HS, gI)
+        thr = c * rho ** (ev["t"] + 1 - I)
+        assert ev["I"] == I
+        assert math.isclose(ev["dp"], dp, rel_tol=1e-7, abs_tol=floor)
+        assert math.isclose(ev["dI"], dI, rel_tol=1e-7, abs_tol=floor)
+        assert math.isclose(ev["thr"], thr, rel_tol=1e-12)
+        if dp > floor and abs(dp / dI / thr - 1) > 1e-6:
+            assert ev["accepted"] == (dp / dI <= thr)
+        if not ev["accepted"]:
+            I, xI = ev["t"], x.copy()

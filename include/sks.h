@@ -83,6 +83,8 @@ typedef struct {
   double threshold;  /* c(rho) phi(rho)^(t+1-I)                       */
   int32_t accepted;  /* 1: x+ accepted; 0: rejected, m doubled        */
   int32_t outer;     /* refinement step (mixed form), 0 otherwise     */
+  int32_t column;    /* right-hand side the test belongs to           */
+  int32_t reserved;
 } sks_trace_event;
 
 /* Options of Algorithms 1 and 2 (defaults by sks_opts_default). */

@@ -33,7 +33,7 @@ class Problem(C.Structure):
 
 class TraceEvent(C.Structure):
     _fields_ = [("t", C.c_int64), ("m", C.c_int64), ("ratio", C.c_double), ("threshold", C.c_double),
-                ("accepted", C.c_int32), ("outer", C.c_int32)]
+                ("accepted", C.c_int32), ("outer", C.c_int32), ("column", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Opts(C.Structure):

@@ -233,7 +233,7 @@ class Solver:
             for i in range(st.trace_len):
                 e = self.trace_buf[i]
                 trace.append(dict(t=e.t, m=e.m, ratio=e.ratio, thr=e.threshold, accepted=bool(e.accepted),
-                                  outer=e.outer))
+                                  outer=e.outer, column=e.column))
         return x, stats, trace
 
 

@@ -12,9 +12,11 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "dense.h"
 #include "internal.h"
+#include "loop.h"
 #include "sketch.h"
 #include "tc_gram.h"
 
@@ -662,7 +664,23 @@ struct SolveWs {
   size_t sketch_bytes;
   void* precond_ws;
   size_t precond_bytes;
+  // device-resident loop (loop.cu): lw right-hand sides in lockstep (0: not available)
+  int lw;
+  long long lt_ld;                       // leading dimension of lt1, lt2
+  double *lx, *lr, *lrt, *lp, *lHp, *lxp, *lrp, *lrtp, *lxo, *lbo, *lb, *lt1, *lt2;
+  float* lv32;
+  void* lpart;      // loop A-pass partial sums
+  void* lres;       // double-float residual partial sums (mixed form), lw columns
+  double* ldots;
+  LoopHead* lhead;  // followed by lw LoopCol
+  LoopCol* lcols;
+  LoopTraceEv* ltrace;
+  int ltrace_cap;
 };
+
+// Lockstep width of the device-resident loop: 8 right-hand sides share each
+// pass over A where the 8-column pass exists (d <= 1024), else one.
+int loop_width(const sks_problem* p) { return (p->k > 1 && p->d <= 1024) ? 8 : 1; }
 
 sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_t ws_bytes, SolveWs* L,
                         size_t* total) {
@@ -695,6 +713,26 @@ sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_
   w.sketch_ws = c.take<char>(w.sketch_bytes);
   w.precond_bytes = precond_ws_bytes(p, m_max);
   w.precond_ws = c.take<char>(w.precond_bytes);
+  w.lw = 0;
+  ApassPlan lpl;
+  if (p->d <= 4096 && apass_plan(n1, p->d, loop_width(p), f32, mixed, &lpl) == SKS_OK) {
+    const int lw = loop_width(p);
+    w.lw = lw;
+    const size_t dk = d * (size_t)lw;
+    w.lt_ld = (long long)std::max<size_t>(d, (size_t)m_max);
+    double** vecs[] = {&w.lx, &w.lr, &w.lrt, &w.lp, &w.lHp, &w.lxp, &w.lrp, &w.lrtp, &w.lxo, &w.lbo, &w.lb};
+    for (double** v : vecs) *v = c.take<double>(dk);
+    w.lt1 = c.take<double>((size_t)w.lt_ld * lw);
+    w.lt2 = c.take<double>((size_t)w.lt_ld * lw);
+    w.lv32 = c.take<float>(dk);
+    w.lpart = c.take<char>(loop_partial_bytes(lpl, p->d, lw, mixed));
+    w.lres = c.take<char>(mixed ? apass_workspace_bytes(n1, p->d, lw, f32, false) : 0);
+    w.ldots = (double*)c.take<char>(loop_dots_bytes(lpl, lw));
+    w.lhead = (LoopHead*)c.take<char>(sizeof(LoopHead) + lw * sizeof(LoopCol));
+    w.lcols = w.lhead ? (LoopCol*)(w.lhead + 1) : nullptr;
+    w.ltrace_cap = (o->trace && o->trace_cap > 0) ? (int)std::min<int64_t>(o->trace_cap, 1 << 16) : 0;
+    w.ltrace = c.take<LoopTraceEv>((size_t)w.ltrace_cap);
+  }
   if (total) *total = c.used + 256;
   if (L) *L = w;
   if (ws && !c.ok()) return fail(SKS_ERR_WORKSPACE, "solve workspace too small");
@@ -752,6 +790,10 @@ struct Engine {
   Timer *t_sketch = nullptr, *t_factor = nullptr;
   int outer = 0;
   bool fixed = false;         // non-adaptive: m stays at m_init, every step is accepted
+  bool fused = false;         // the device-resident loop (loop.cu) serves this solve
+  int cur_col = 0;            // right-hand side being solved (host-driven iteration)
+  ApassPlan lplan, lresplan;  // its A-pass plan (lw columns) and the refinement residual's
+  CUtensorMap ltmap, lrtmap;
   double mu = 0, beta = 0;    // IHS / Polyak-IHS step size and momentum
   double cg_bb = 0;           // b^T b of the current right-hand side (CG stop rule)
 
@@ -798,6 +840,21 @@ struct Engine {
       SKS_TRY(apass_plan(n1, d, 1, f32, false, &plan64));
       if (pr->n > 0) SKS_TRY(map_for(pr, &tmap64, plan64));
       apass_use_bulk(&plan64, pr->A, d, pr->lda, f32);
+    }
+    if (W.lw > 0 && (method == PCG || method == IHS)) {
+      // the device-resident loop: same pass geometry, lw columns, a stage less if needed
+      if (apass_plan(n1, d, W.lw, f32, mixed, &lplan) == SKS_OK) {
+        loop_adjust_plan(&lplan, f32, mixed);
+        if (pr->n > 0) SKS_TRY(map_for(pr, &ltmap, lplan));
+        apass_use_bulk(&lplan, pr->A, d, pr->lda, f32);
+        fused = pr->n > 0 && loop_supported(lplan, d, W.lw, f32, mixed) == SKS_OK;
+        if (fused && mixed) {
+          SKS_TRY(apass_plan(n1, d, W.lw, f32, false, &lresplan));
+          if (pr->n > 0) SKS_TRY(map_for(pr, &lrtmap, lresplan));
+          apass_use_bulk(&lresplan, pr->A, d, pr->lda, f32);
+        }
+      }
+      set_last_error("");  // an unavailable loop falls back to the host-driven iteration silently
     }
     SKS_TRY(sketch_init(&sk, pr, op->kind, m_max, op->sjlt_s, op->seed, W.sketch_ws, W.sketch_bytes, W.st));
     // the mixed form forms the inverse Cholesky factor in float32
@@ -1008,6 +1065,8 @@ struct Engine {
         e.threshold = h.thr;
         e.accepted = h.accept;
         e.outer = outer;
+        e.column = cur_col;
+        e.reserved = 0;
       }
       if (h.numeric) return fail(SKS_ERR_NUMERIC, "non-finite value in the iteration");
       if (!h.accept) {
@@ -1091,9 +1150,259 @@ double stop_coefficient(const sks_problem* p, const sks_opts* o) {
   return o->tol * o->tol / (critical_sketch_size(o->kind, std::max<int64_t>(p->n, 1), d_e, o->cert_delta) + 1.0);
 }
 
+// ---------------------------------------------------------------- device-resident solve
+// Refinement step of the mixed form, per column c < kc: b^T x_o into the
+// column's state, reset of the inner solve (t = I = 0), x = 0 and the inner
+// right-hand side (r = b_o for PCG, the gradient g = -b_o for the IHS).
+__global__ void __launch_bounds__(1024) loop_prep_kernel(int d, int kc, int pcg, const double* __restrict__ b,
+                                                         const double* __restrict__ xo, const double* __restrict__ bo,
+                                                         double* __restrict__ x, double* __restrict__ r,
+                                                         LoopCol* cols) {
+  __shared__ double scratch[32];
+  const int c = blockIdx.x;
+  if (c >= kc) return;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const size_t e = (size_t)c * d + j;
+    s += b[e] * xo[e];
+    x[e] = 0.0;
+    r[e] = pcg ? bo[e] : -bo[e];
+  }
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) {
+    LoopCol& q = cols[c];
+    q.btx_outer = s;
+    q.t = 0;
+    q.I = 0;
+    q.numeric = 0;
+    q.rejected = 0;
+    q.stop = (!q.active || q.outer_done) ? 1 : 0;
+  }
+}
+
+// x_o += x for the columns whose refinement goes on.
+__global__ void loop_outer_add_kernel(int d, int kc, const LoopCol* cols, const double* __restrict__ x,
+                                      double* __restrict__ xo) {
+  const int c = blockIdx.y;
+  if (c >= kc || !cols[c].active || cols[c].outer_done) return;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+    xo[(size_t)c * d + j] += x[(size_t)c * d + j];
+}
+
+struct LoopHostCtl {
+  LoopHead head;
+  LoopCol cols[kLoopMaxK];
+};
+
+// Launches the loop until no column asks for a larger sketch: after a failed
+// test the host grows the sketch, refactors H_S and relaunches with the restart
+// prologue (every column restarts at its current iterate with the new
+// preconditioner; see reading R17).  Reads the control block once per launch.
+sks_status loop_run(Engine& E, LoopTask& T, LoopHostCtl* h) {
+  const int lw = E.W.lw;
+  const size_t ctl_bytes = sizeof(LoopHead) + lw * sizeof(LoopCol);
+  while (true) {
+    SKS_CUDA_TRY(cudaMemsetAsync(E.W.lhead, 0, sizeof(LoopHead), E.stream));
+    T.m = E.m;
+    T.can_double = (!E.fixed && E.m < E.m_max) ? 1 : 0;
+    T.P.woodbury = E.P.woodbury ? 1 : 0;
+    T.P.m = (int)E.P.m;
+    T.P.X = E.P.X;
+    T.P.Xt = E.P.Xt;
+    T.P.Y = E.P.Y64;
+    T.P.ldy = E.P.ldy64;
+    T.P.Yt = E.P.Yt;
+    T.P.c = std::sqrt(E.P.c2);
+    SKS_TRY(loop_launch(E.lplan, &E.ltmap, E.prob->n, E.d, E.f32, E.mixed, T, E.stream));
+    SKS_CUDA_TRY(cudaMemcpyAsync(h, E.W.lhead, ctl_bytes, cudaMemcpyDeviceToHost, E.stream));
+    SKS_TRY(read_status(E.W.st, E.stream, "solver loop"));
+    E.S.a_passes += h->head.apasses;
+    E.S.ms_apass += (float)(h->head.apass_ns * 1e-6);
+    E.S.apass_timed += h->head.apasses;
+    if (E.o->trace && h->head.trace_len > 0) {
+      std::vector<LoopTraceEv> ev((size_t)h->head.trace_len);
+      SKS_CUDA_TRY(cudaMemcpy(ev.data(), E.W.ltrace, ev.size() * sizeof(LoopTraceEv), cudaMemcpyDeviceToHost));
+      for (const LoopTraceEv& v : ev) {
+        if (E.S.trace_len >= E.o->trace_cap) break;
+        sks_trace_event& e = E.o->trace[E.S.trace_len++];
+        e.t = v.t;
+        e.m = v.m;
+        e.ratio = v.ratio;
+        e.threshold = v.thr;
+        e.accepted = v.accepted;
+        e.outer = E.outer;
+        e.column = v.column + E.cur_col;
+        e.reserved = 0;
+      }
+    }
+    for (int c = 0; c < T.kc; ++c)
+      if (h->cols[c].numeric) return fail(SKS_ERR_NUMERIC, "non-finite value in the iteration");
+    if (!h->head.any_reject) return SKS_OK;
+    E.S.rejections += 1;
+    SKS_TRY(E.grow());
+    T.resid = (T.method == 0 && !E.o->reuse_residual && !E.mixed) ? 1 : 0;
+    T.restart = 1;
+    T.first = 0;
+  }
+}
+
+// Solve H X = B for the k columns with the device-resident loop, lw columns
+// in lockstep sharing every pass over A (X holds x_0 on entry).  Plain form:
+// one adaptive solve per batch.  Mixed form: refinement -- r = b - H x_o by
+// the double-float pass, an inner adaptive solve of H dx = r from dx = 0 in
+// float32 (relative accuracy inner_tol), x_o += dx -- until the decrement at
+// x_o meets the stop rule; a column whose refinement has converged rests
+// while the others go on.
+sks_status solve_columns_fused(Engine& E, const double* B, double* X_io) {
+  const sks_problem* prob = E.prob;
+  const sks_opts* o = E.o;
+  cudaStream_t stream = E.stream;
+  const int d = E.d, lw = E.W.lw;
+  const bool pcg = E.method == PCG;
+  const double fac = pcg ? 1.0 : 2.0;
+  const double tol2 = stop_coefficient(prob, o);
+  sks_status result = SKS_OK;
+  LoopHostCtl h;
+  for (int64_t c0 = 0; c0 < prob->k; c0 += lw) {
+    const int kc = (int)std::min<int64_t>(lw, prob->k - c0);
+    const size_t dk = (size_t)d * lw;
+    E.cur_col = (int)c0;
+    // padded right-hand sides and iterate (columns past kc are zero and inert)
+    SKS_CUDA_TRY(cudaMemsetAsync(E.W.lb, 0, dk * sizeof(double), stream));
+    SKS_CUDA_TRY(cudaMemcpyAsync(E.W.lb, B + c0 * d, (size_t)d * kc * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 stream));
+    double* X0 = E.mixed ? E.W.lxo : E.W.lx;
+    SKS_CUDA_TRY(cudaMemsetAsync(X0, 0, dk * sizeof(double), stream));
+    SKS_CUDA_TRY(cudaMemcpyAsync(X0, X_io + c0 * d, (size_t)d * kc * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 stream));
+    std::memset(&h, 0, sizeof(h));
+    for (int c = 0; c < lw; ++c) h.cols[c].active = c < kc ? 1 : 0;
+    SKS_CUDA_TRY(cudaMemcpyAsync(E.W.lcols, h.cols, lw * sizeof(LoopCol), cudaMemcpyHostToDevice, stream));
+    LoopTask T;
+    std::memset(&T, 0, sizeof(T));
+    T.method = pcg ? 0 : 1;
+    T.K = lw;
+    T.kc = kc;
+    T.c = E.c;
+    T.phi = E.phi;
+    T.mu = E.mu;
+    T.fac = fac;
+    T.nu2 = E.nu2;
+    T.lam = prob->lambda_diag;
+    T.x = E.W.lx;
+    T.r = E.W.lr;
+    T.rt = E.W.lrt;
+    T.p = E.W.lp;
+    T.Hp = E.W.lHp;
+    T.xp = E.W.lxp;
+    T.rp = E.W.lrp;
+    T.rtp = E.W.lrtp;
+    T.t1 = E.W.lt1;
+    T.t2 = E.W.lt2;
+    T.ld_t = E.W.lt_ld;
+    T.v32 = E.W.lv32;
+    T.partials = E.W.lpart;
+    T.dots = E.W.ldots;
+    T.cols = E.W.lcols;
+    T.head = E.W.lhead;
+    T.trace = E.W.ltrace_cap > 0 ? E.W.ltrace : nullptr;
+    T.trace_cap = E.W.ltrace_cap;
+    T.st = E.W.st;
+    bool converged = false;
+    if (!E.mixed) {
+      T.b = E.W.lb;
+      T.resid = 1;
+      T.restart = 1;
+      T.first = 1;
+      T.tol2 = tol2;
+      T.max_iter = o->max_iter;
+      SKS_TRY(loop_run(E, T, &h));
+      converged = true;
+      double est = 0.0, dtmax = 0.0;
+      for (int c = 0; c < kc; ++c) {
+        const LoopCol& q = h.cols[c];
+        E.S.iters += q.t;
+        converged = converged && q.stop;
+        est = std::max(est, q.btx > 0 ? std::sqrt(std::max(0.0, fac * q.dt / q.btx)) : 0.0);
+        dtmax = std::max(dtmax, q.dt);
+      }
+      E.S.est_rel_err = est;
+      E.S.final_delta_tilde = dtmax;
+    } else {
+      // refinement: the outer iterate x_o lives in lxo, the inner right-hand side in lbo
+      int64_t inner_budget = o->max_iter;
+      for (int64_t k = 0; k < o->max_outer; ++k) {
+        E.outer = (int)k + 1;
+        if (k == 0) {
+          // r = b - H x_o (r = b exactly when x_o = 0, without a pass over A)
+          int* flag = (int*)(E.W.scal + 3);
+          any_nonzero_kernel<<<1, 256, 0, stream>>>((int)dk, X0, flag);
+          note_launch();
+          int hf = 1;
+          SKS_CUDA_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+          SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+          if (hf == 0) {
+            SKS_CUDA_TRY(cudaMemcpyAsync(E.W.lbo, E.W.lb, dk * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+          } else {
+            E.S.a_passes += 1;
+            SKS_TRY(apass_launch(E.lresplan, &E.lrtmap, prob->n, d, lw, true, false, E.W.lxo, E.W.lbo, E.nu2,
+                                 prob->lambda_diag, E.W.lres, E.W.st, stream, -1.0, E.W.lb, 1.0));
+          }
+        } else {
+          E.S.a_passes += 1;
+          SKS_TRY(apass_launch(E.lresplan, &E.lrtmap, prob->n, d, lw, true, false, E.W.lxo, E.W.lbo, E.nu2,
+                               prob->lambda_diag, E.W.lres, E.W.st, stream, -1.0, E.W.lb, 1.0));
+        }
+        loop_prep_kernel<<<lw, 1024, 0, stream>>>(d, kc, pcg ? 1 : 0, E.W.lb, E.W.lxo, E.W.lbo, E.W.lx, E.W.lr,
+                                                   E.W.lcols);
+        note_launch();
+        SKS_CUDA_TRY(cudaGetLastError());
+        T.b = E.W.lbo;
+        T.resid = 0;
+        T.restart = 1;
+        T.first = 1;
+        T.tol2 = 0.0;
+        T.rel2 = o->inner_tol * o->inner_tol;
+        T.outer_tol2 = tol2;
+        T.max_iter = std::max<int64_t>(inner_budget, 1);
+        SKS_TRY(loop_run(E, T, &h));
+        E.S.outer_iters += 1;
+        bool all_done = true;
+        int64_t tmax = 0;
+        double est = 0.0;
+        for (int c = 0; c < kc; ++c) {
+          const LoopCol& q = h.cols[c];
+          all_done = all_done && q.outer_done;
+          tmax = std::max<int64_t>(tmax, q.t);
+          E.S.iters += q.t;
+          // the decrement at the outer iterate estimates its error
+          est = std::max(est, q.btx_outer > 0 ? std::sqrt(std::max(0.0, fac * q.dt0 / q.btx_outer)) : 0.0);
+        }
+        E.S.est_rel_err = est;
+        if (all_done) {
+          converged = true;
+          break;
+        }
+        loop_outer_add_kernel<<<dim3((unsigned)std::min(64, (d + 255) / 256), (unsigned)lw), 256, 0, stream>>>(
+            d, kc, E.W.lcols, E.W.lx, E.W.lxo);
+        note_launch();
+        SKS_CUDA_TRY(cudaGetLastError());
+        inner_budget -= tmax;
+        if (inner_budget <= 0) break;
+      }
+    }
+    SKS_CUDA_TRY(cudaMemcpyAsync(X_io + c0 * d, X0, (size_t)d * kc * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 stream));
+    SKS_TRY(read_status(E.W.st, stream, "solver loop"));
+    if (!converged && result == SKS_OK) result = fail(SKS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+  }
+  return result;
+}
+
 // Solve H X = B column by column with the engine's current sketch and
 // preconditioner (X holds x_0 on entry).
 sks_status solve_columns(Engine& E, const double* B, double* X_io) {
+  if (E.fused && !E.fixed && (E.method == PCG || E.method == IHS)) return solve_columns_fused(E, B, X_io);
   const sks_problem* prob = E.prob;
   const sks_opts* o = E.o;
   cudaStream_t stream = E.stream;
@@ -1102,6 +1411,7 @@ sks_status solve_columns(Engine& E, const double* B, double* X_io) {
   const double fac = (E.method == PCG || E.method == CG) ? 1.0 : 2.0;
   sks_status result = SKS_OK;
   for (int64_t col = 0; col < prob->k && result == SKS_OK; ++col) {
+    E.cur_col = (int)col;
     const double* b = B + col * d;
     double* xcol = X_io + col * d;
     bool converged = false;

@@ -252,7 +252,12 @@ void sks_precond_destroy(sks_precond* P);
  * opts.stop_rule decides; by default (SKS_STOP_ESTIMATE) stop when the
  * estimate delta~_t / (b^T x_t) of ||x_t - x*||_H^2/||x*||_H^2 is <= (tol/2)^2
  * (IHS: 2 delta~_t); SKS_STOP_CERTIFIED uses tol^2 / (m_delta + 1) instead.
- * k > 1 right-hand sides are solved one after the other.
+ * Between re-sketches the iteration runs on the device in one launch (fused
+ * A-pass, preconditioner apply, step and test; see the loop below), and up
+ * to 8 right-hand sides (d <= 1024) run in lockstep sharing every pass over
+ * A: each column has its own test and stop, a failed test of any column
+ * doubles m and every live column restarts at its current iterate with the
+ * new preconditioner; more columns run in batches of 8, wider rows one by one.
  * x: device float64 d x k, in: x_0, out: the solution.  stats: host, may be NULL.
  * ws: device scratch of sks_solve_workspace_size bytes.
  * Returns SKS_ERR_NO_CONVERGENCE if max_iter accepted steps did not reach tol.

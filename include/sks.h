@@ -343,8 +343,8 @@ sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const double* x,
  * embedding, one right-hand side per problem, d <= 1024, n >= 1).  Every
  * decision of Algorithm 2 is taken on the device, per problem, so one round of
  * batched kernels advances every unfinished problem by one step or one
- * re-sketch; the round is captured once as a CUDA graph and replayed until all
- * problems have stopped.  Each problem's iterates, m sequence and stop are
+ * re-sketch; the rounds run inside one CUDA graph launch (a while loop on the
+ * device, see the batch plans below) until all problems have stopped.  Each problem's iterates, m sequence and stop are
  * those of sks_adaptive_pcg_solve with the same options (up to the rounding
  * order of the sums); the same seed serves every problem.
  * probs:  host array of `count` problem descriptions (device A, b, lambda).
@@ -358,7 +358,7 @@ sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const double* x,
  *         candidates 32..512 on this batch (autotuning), else in [32, 65536].
  * ws:     device scratch of sks_batch_workspace_size bytes (holds H E A_pad of
  *         every problem, the factors and the per-problem state).
- * The call synchronises `stream` a few times (once per burst of replays).
+ * The call synchronises `stream` twice (the input check and the results).
  * Returns SKS_OK when every problem met tol, else the status of the first
  * failing problem (the others are still solved and reported in stats).
  * ------------------------------------------------------------------------- */
@@ -377,9 +377,35 @@ typedef struct {
 } sks_batch_info;
 
 sks_status sks_batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes);
+/* One-shot solve: sks_batch_create + sks_batch_solve + sks_batch_destroy. */
 sks_status sks_solve_batched(const sks_problem* probs, int count, const sks_opts* o, double* const* x,
                              sks_stats* stats, sks_batch_info* info, int rows_per_unit, void* ws, size_t ws_bytes,
                              void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batch plans: the same solve as sks_solve_batched, with the planning done
+ * once.  sks_batch_create checks the problems (Lambda >= I on the device;
+ * one stream synchronisation), chooses the A-pass unit height (rows_per_unit
+ * 0: by timing the candidates 32..512 on this batch) and builds and
+ * instantiates ONE CUDA graph:
+ *     reset counters -> every problem in INIT -> H E A_pad of every problem
+ *     -> WHILE (some problem unfinished and rounds < bound) { one round }
+ * where the round's last kernel sets the loop condition on the device.
+ * sks_batch_solve uploads the x pointers and launches that graph once: the
+ * rounds repeat on the device with no host round trip, and the call
+ * synchronises `stream` once at the end to read the per-problem results
+ * (the H E A_pad transform is part of every solve).  The problems' device
+ * pointers (A, b, lambda) and the workspace are borrowed by the plan and must
+ * stay valid and unchanged (A, lambda) until sks_batch_destroy; b may change
+ * between solves.  info->ms_setup is the planning time of the create call,
+ * info->ms_solve the graph's device time.  Plans are not thread-safe: one
+ * solve at a time per plan.
+ * ------------------------------------------------------------------------- */
+typedef struct sks_batch sks_batch;
+sks_status sks_batch_create(sks_batch** out, const sks_problem* probs, int count, const sks_opts* o,
+                            int rows_per_unit, void* ws, size_t ws_bytes, void* stream);
+sks_status sks_batch_solve(sks_batch* plan, double* const* x, sks_stats* stats, sks_batch_info* info, void* stream);
+void sks_batch_destroy(sks_batch* plan);
 
 /* ---------------------------------------------------------------------------
  * Self-test of the failure path (the paper has no counterpart).  Every

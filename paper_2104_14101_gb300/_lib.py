@@ -104,6 +104,10 @@ _SIGS = {
     "sks_batch_workspace_size": (C.c_int, [P(Problem), C.c_int, P(Opts), P(C.c_size_t)]),
     "sks_solve_batched": (C.c_int, [P(Problem), C.c_int, P(Opts), P(C.c_void_p), P(Stats), P(BatchInfo), C.c_int,
                                     C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sks_batch_create": (C.c_int, [P(C.c_void_p), P(Problem), C.c_int, P(Opts), C.c_int, C.c_void_p, C.c_size_t,
+                                    C.c_void_p]),
+    "sks_batch_solve": (C.c_int, [C.c_void_p, P(C.c_void_p), P(Stats), P(BatchInfo), C.c_void_p]),
+    "sks_batch_destroy": (None, [C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

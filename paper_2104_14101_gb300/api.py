@@ -345,15 +345,16 @@ def fixed_solve(A, b, nu, lam, method="fixed-pcg", x0=None, check=True, **opts):
 
 
 class BatchSolver:
-    """Many independent problems (each one (A, b, nu, lam)) solved together by
-    ``sks_solve_batched``: adaptive PCG per problem, every decision on the
-    device, one captured CUDA graph replayed until all have stopped.  The
-    workspace is sized and held once; ``solve`` may be called repeatedly.
-    With rows_per_unit=0 the first solve times the candidate A-pass unit
-    heights on this batch and later solves reuse the winner."""
+    """Many independent problems (each one (A, b, nu, lam)) solved together:
+    adaptive PCG per problem, every decision on the device.  The plan
+    (``sks_batch_create``: input checks, the A-pass unit height -- timed on
+    this batch when rows_per_unit=0 -- and one instantiated CUDA graph whose
+    while loop repeats the round until every problem has stopped) is made
+    once; every ``solve`` is one graph launch (``sks_batch_solve``)."""
 
     def __init__(self, problems, rows_per_unit=0, **opts):
         self._lib = L.load()
+        self.plan = None
         if len(problems) < 1:
             raise ValueError("need at least one problem")
         self.items = [make_problem(A, b, nu, lam) for (A, b, nu, lam) in problems]
@@ -364,8 +365,11 @@ class BatchSolver:
         L.check(self._lib.sks_batch_workspace_size(self.arr, self.count, C.byref(self.opts), C.byref(nb)))
         self.device = problems[0][0].device
         self.ws = _workspace(nb.value, self.device)
-        self.rows_per_unit = int(rows_per_unit)
         self.ds = [int(p.d) for p, _ in self.items]
+        h = C.c_void_p()
+        L.check(self._lib.sks_batch_create(C.byref(h), self.arr, self.count, C.byref(self.opts), int(rows_per_unit),
+                                           _ptr(self.ws), self.ws.numel(), _stream(self.device)))
+        self.plan = h
 
     def solve(self, x0s=None, check=True):
         xs = [torch.zeros(d, dtype=torch.float64, device=self.device) for d in self.ds]
@@ -375,19 +379,20 @@ class BatchSolver:
         ptrs = (C.c_void_p * self.count)(*[x.data_ptr() for x in xs])
         st = (L.Stats * self.count)()
         info = L.BatchInfo()
-        status = self._lib.sks_solve_batched(self.arr, self.count, C.byref(self.opts), ptrs, st, C.byref(info),
-                                             self.rows_per_unit, _ptr(self.ws), self.ws.numel(),
-                                             _stream(self.device))
+        status = self._lib.sks_batch_solve(self.plan, ptrs, st, C.byref(info), _stream(self.device))
         if check and status != L.OK:
             L.check(status)
-        if self.rows_per_unit == 0 and info.rows_per_unit > 0:
-            self.rows_per_unit = int(info.rows_per_unit)  # tuned once per batch, reused by later solves
         stats = []
         for s in st:
             dct = s.as_dict()
             dct["status_name"] = L.STATUS_NAMES.get(s.status, s.status)
             stats.append(dct)
         return xs, stats, info.as_dict()
+
+    def __del__(self):
+        if getattr(self, "plan", None):
+            self._lib.sks_batch_destroy(self.plan)
+            self.plan = None
 
 
 def solve_batched(problems, x0s=None, rows_per_unit=0, **opts):

@@ -87,6 +87,18 @@ extern "C" sks_status sks_solve_batched(const sks_problem* probs, int count, con
   return solve_batched(probs, count, o, x, stats, info, rows_per_unit, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+extern "C" sks_status sks_batch_create(sks_batch** out, const sks_problem* probs, int count, const sks_opts* o,
+                                       int rows_per_unit, void* ws, size_t ws_bytes, void* stream) {
+  return batch_create(out, probs, count, o, rows_per_unit, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" sks_status sks_batch_solve(sks_batch* plan, double* const* x, sks_stats* stats, sks_batch_info* info,
+                                      void* stream) {
+  return batch_solve(plan, x, stats, info, (cudaStream_t)stream);
+}
+
+extern "C" void sks_batch_destroy(sks_batch* plan) { batch_destroy(plan); }
+
 extern "C" sks_status sks_selftest_wait_timeout(int64_t limit_ns, void* stream) {
   return selftest_wait_timeout((long long)limit_ns, (cudaStream_t)stream);
 }

@@ -96,6 +96,11 @@ struct BCtl {
   double* apass_flops;
   unsigned long long* tgram;  // the same for the Gram kernel (first start, last end, sum)
   double* gram_flops;         // 2 x 64 x 64 per sketch row (or column) of every Gram unit
+  // the graph's while loop: rounds run while some problem is unfinished and
+  // fewer than max_rounds have run (the count kernel sets the condition)
+  cudaGraphConditionalHandle cond;
+  long long* rounds;
+  long long max_rounds;
 };
 
 // largest p with pre[p] <= u  (pre[0] = 0 <= u < pre[P])
@@ -813,6 +818,8 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
   a = block_sum(a, scratch);
   if (threadIdx.x == 0) {
     *c.active = a;
+    const long long r = ++*c.rounds;
+    cudaGraphSetConditional(c.cond, (a > 0 && r < c.max_rounds) ? 1u : 0u);
     if (c.tap) {
       if (c.tap[1] > c.tap[0]) c.tap[2] += c.tap[1] - c.tap[0];
       c.tap[0] = ~0ull;
@@ -827,6 +834,20 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
 }
 
 // ------------------------------------------------------------------ setup kernels
+
+// Per-solve counters: A-pass and Gram timing windows, flop sums, rounds.
+__global__ void b_reset_kernel(BCtl c) {
+  if (threadIdx.x != 0) return;
+  c.tap[0] = ~0ull;
+  c.tap[1] = 0ull;
+  c.tap[2] = 0ull;
+  *c.apass_flops = 0.0;
+  c.tgram[0] = ~0ull;
+  c.tgram[1] = 0ull;
+  c.tgram[2] = 0ull;
+  *c.gram_flops = 0.0;
+  *c.rounds = 0;
+}
 
 __global__ void b_check_kernel(const BDesc* __restrict__ D, int P, DevStatus* st) {
   for (int p = blockIdx.x; p < P; p += gridDim.x) {
@@ -855,6 +876,7 @@ struct Layout {
   double* apass_flops = nullptr;
   unsigned long long* tgram = nullptr;
   double* gram_flops = nullptr;
+  long long* rounds = nullptr;
   DevStatus* st = nullptr;
   std::vector<BDesc> host;
   size_t used = 0;
@@ -903,6 +925,7 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
   L->apass_flops = c.take<double>(1);
   L->tgram = c.take<unsigned long long>(3);
   L->gram_flops = c.take<double>(1);
+  L->rounds = c.take<long long>(1);
   L->st = c.take<DevStatus>(1);
   L->host.assign(P, BDesc{});
   for (int i = 0; i < P; ++i) {
@@ -1007,16 +1030,6 @@ struct EventPair {
   }
 };
 
-struct GraphGuard {
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t e = nullptr;
-  cudaStream_t cs = nullptr;
-  ~GraphGuard() {
-    if (e) cudaGraphExecDestroy(e);
-    if (g) cudaGraphDestroy(g);
-    if (cs) cudaStreamDestroy(cs);
-  }
-};
 
 sks_status upload_prefix(int* dst, const std::vector<int>& pre, cudaStream_t stream) {
   SKS_CUDA_TRY(cudaMemcpyAsync(dst, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
@@ -1024,6 +1037,33 @@ sks_status upload_prefix(int* dst, const std::vector<int>& pre, cudaStream_t str
 }
 
 }  // namespace
+}  // namespace sks
+
+// A batch plan: the workspace layout, the tuned A-pass unit height and one
+// instantiated graph
+//     reset counters -> states INIT -> H E A_pad of every problem -> WHILE (some problem unfinished) { round }
+// so that a solve is a descriptor upload and ONE graph launch: the rounds
+// repeat on the device (the round's last kernel sets the loop condition)
+// with no host round trip until every problem has stopped.
+struct sks_batch {
+  int P = 0;
+  sks_opts opts;
+  sks::Layout L;
+  sks::Round R;
+  int chosen = 0, per_round = 0;
+  float ms_plan = 0.f, ms_tune = 0.f;
+  cudaGraph_t g = nullptr, g_setup = nullptr;
+  cudaGraphExec_t e = nullptr;
+  cudaStream_t cs = nullptr;
+  ~sks_batch() {
+    if (e) cudaGraphExecDestroy(e);
+    if (g) cudaGraphDestroy(g);
+    if (g_setup) cudaGraphDestroy(g_setup);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+namespace sks {
 
 sks_status batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes) {
   if (!bytes) return fail(SKS_ERR_INVALID_ARG, "bytes is NULL");
@@ -1034,30 +1074,36 @@ sks_status batch_workspace_size(const sks_problem* probs, int count, const sks_o
   return SKS_OK;
 }
 
-sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, double* const* xs, sks_stats* stats,
-                         sks_batch_info* info, int rows_per_unit, void* ws, size_t ws_bytes, cudaStream_t stream) {
+sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const sks_opts* o, int rows_per_unit,
+                        void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (!out) return fail(SKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
   SKS_TRY(check_batch(probs, P, o));
-  if (!xs) return fail(SKS_ERR_INVALID_ARG, "x array is NULL");
-  for (int i = 0; i < P; ++i)
-    if (!xs[i]) return fail(SKS_ERR_INVALID_ARG, "x of batch problem " + std::to_string(i) + " is NULL");
   if (rows_per_unit != 0 && (rows_per_unit < kMinRowsPerUnit || rows_per_unit > 65536))
     return fail(SKS_ERR_INVALID_ARG, "rows_per_unit must be 0 (autotune) or in [32, 65536]");
   if (!ws) return fail(SKS_ERR_INVALID_ARG, "workspace is NULL");
-  Layout L;
+  sks_batch* B = new (std::nothrow) sks_batch;
+  if (!B) return fail(SKS_ERR_INVALID_ARG, "out of host memory");
+  struct Guard {
+    sks_batch*& b;
+    ~Guard() { delete b; }
+  } guard{B};
+  B->P = P;
+  B->opts = *o;
+  Layout& L = B->L;
   SKS_TRY(batch_layout(probs, P, o, ws, ws_bytes, &L));
-  for (int i = 0; i < P; ++i) L.host[i].x = xs[i];
   const DeviceInfo& di = device_info();
   const int sms = di.sms > 0 ? di.sms : 152;
-
-  EventPair ev_setup, ev_tune, ev_solve;
-  SKS_TRY(ev_setup.init());
+  EventPair ev_plan, ev_tune;
+  SKS_TRY(ev_plan.init());
   SKS_TRY(ev_tune.init());
-  SKS_TRY(ev_solve.init());
-
-  // ---- setup: descriptors, checks, SRHT transforms H E A, states
-  SKS_CUDA_TRY(cudaEventRecord(ev_setup.a, stream));
+  SKS_CUDA_TRY(cudaEventRecord(ev_plan.a, stream));
+  // descriptors with a zeroed scratch vector standing in for x until a solve gives the real one
+  std::vector<BDesc> tmp = L.host;
+  for (BDesc& q : tmp) q.x = q.vec + (size_t)V_W * q.d;
+  for (const BDesc& q : tmp) SKS_CUDA_TRY(cudaMemsetAsync(q.vec, 0, (size_t)kNumVec * q.d * sizeof(double), stream));
   SKS_CUDA_TRY(cudaMemsetAsync(L.st, 0, sizeof(DevStatus), stream));
-  SKS_CUDA_TRY(cudaMemcpyAsync(L.D, L.host.data(), P * sizeof(BDesc), cudaMemcpyHostToDevice, stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(L.D, tmp.data(), P * sizeof(BDesc), cudaMemcpyHostToDevice, stream));
   const std::vector<int> pre_tri = prefix(L.host, units_tri, 0), pre_T = prefix(L.host, units_T, 0),
                          pre_red = prefix(L.host, units_red, 0);
   SKS_TRY(upload_prefix(L.pre_tri, pre_tri, stream));
@@ -1067,17 +1113,12 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   SKS_TRY(read_status(L.st, stream, "batch input check"));
-  for (int i = 0; i < P; ++i) {
-    const BDesc& q = L.host[i];
-    SKS_TRY(srht_form<double>(stream, q.A, q.lda, q.n, q.d, (double*)q.B, q.d, o->seed));
-  }
   b_init_kernel<<<(P + 127) / 128, 128, 0, stream>>>(L.S, P);
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
-  SKS_CUDA_TRY(cudaEventRecord(ev_setup.b, stream));
 
   // ---- round description
-  Round R;
+  Round& R = B->R;
   std::memset(&R, 0, sizeof(R));
   R.P = P;
   R.D = L.D;
@@ -1099,12 +1140,14 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
   c.apass_flops = L.apass_flops;
   c.tgram = L.tgram;
   c.gram_flops = L.gram_flops;
+  c.rounds = L.rounds;
   int dmax = 0;
   int64_t mmax_all = 1;
   for (const BDesc& q : L.host) {
     dmax = std::max(dmax, q.d);
     mmax_all = std::max(mmax_all, q.m_max);
   }
+  c.max_rounds = 4 + 2 * (ilog2_ceil(mmax_all) + 2) + c.max_iter;
   R.kmax = (dmax + kTile - 1) / kTile;
   R.tot_tri = pre_tri[P];
   R.tot_T = pre_T[P];
@@ -1123,7 +1166,6 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
   // ---- autotune the A-pass unit height on this batch (all problems in INIT)
   SKS_CUDA_TRY(cudaEventRecord(ev_tune.a, stream));
   int chosen = rows_per_unit;
-  std::vector<int> pre_ap;
   if (chosen == 0) {
     const int cands[] = {32, 64, 128, 256, 512};
     float best = 1e30f;
@@ -1151,66 +1193,89 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
       }
     }
   }
-  pre_ap = prefix(L.host, units_ap, chosen);
+  const std::vector<int> pre_ap = prefix(L.host, units_ap, chosen);
   SKS_TRY(upload_prefix(L.pre_ap, pre_ap, stream));
   c.rows_per_unit = chosen;
   R.tot_ap = pre_ap[P];
   R.g_ap = std::max(1, std::min(R.tot_ap, ap_grid_max));
+  B->chosen = chosen;
   SKS_CUDA_TRY(cudaEventRecord(ev_tune.b, stream));
 
-  // ---- capture one round as a graph, replay until every problem is done
-  GraphGuard G;
-  SKS_CUDA_TRY(cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking));
-  SKS_CUDA_TRY(cudaStreamBeginCapture(G.cs, cudaStreamCaptureModeThreadLocal));
-  const int per_round = enqueue_round(R, G.cs);
-  const cudaError_t cap = cudaStreamEndCapture(G.cs, &G.g);
-  SKS_CUDA_TRY(cap);
-  SKS_CUDA_TRY(cudaGetLastError());
-  SKS_CUDA_TRY(cudaGraphInstantiate(&G.e, G.g, 0));
-
-  const int64_t max_rounds = 4 + 2 * (ilog2_ceil(mmax_all) + 2) + c.max_iter;
-  int64_t rounds = 0;
-  int* h_active = nullptr;
-  SKS_CUDA_TRY(cudaMallocHost(&h_active, sizeof(int)));
-  struct HostFree {
-    int* p;
-    ~HostFree() { cudaFreeHost(p); }
-  } hf{h_active};
+  // ---- the graph: setup child graph, then the while loop around one round
+  SKS_CUDA_TRY(cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking));
+  SKS_CUDA_TRY(cudaGraphCreate(&B->g, 0));
+  SKS_CUDA_TRY(cudaGraphCreate(&B->g_setup, 0));
+  SKS_CUDA_TRY(cudaStreamBeginCaptureToGraph(B->cs, B->g_setup, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
   {
-    const unsigned long long t0[3] = {~0ull, 0ull, 0ull};
-    SKS_CUDA_TRY(cudaMemcpyAsync(L.tap, t0, sizeof(t0), cudaMemcpyHostToDevice, stream));
-    SKS_CUDA_TRY(cudaMemsetAsync(L.apass_flops, 0, sizeof(double), stream));
-    SKS_CUDA_TRY(cudaMemcpyAsync(L.tgram, t0, sizeof(t0), cudaMemcpyHostToDevice, stream));
-    SKS_CUDA_TRY(cudaMemsetAsync(L.gram_flops, 0, sizeof(double), stream));
-    SKS_CUDA_TRY(cudaStreamSynchronize(stream));  // t0 is a host temporary
+    b_reset_kernel<<<1, 32, 0, B->cs>>>(c);
+    b_init_kernel<<<(P + 127) / 128, 128, 0, B->cs>>>(L.S, P);
+    sks_status sr = SKS_OK;
+    for (int i = 0; i < P && sr == SKS_OK; ++i) {
+      const BDesc& q = L.host[i];
+      sr = srht_form<double>(B->cs, q.A, q.lda, q.n, q.d, (double*)q.B, q.d, o->seed);
+    }
+    cudaGraph_t got = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(B->cs, &got);
+    SKS_TRY(sr);
+    SKS_CUDA_TRY(ce);
   }
+  cudaGraphNode_t n_setup = nullptr, n_while = nullptr;
+  SKS_CUDA_TRY(cudaGraphAddChildGraphNode(&n_setup, B->g, nullptr, 0, B->g_setup));
+  SKS_CUDA_TRY(cudaGraphConditionalHandleCreate(&c.cond, B->g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = c.cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  SKS_CUDA_TRY(cudaGraphAddNode(&n_while, B->g, &n_setup, nullptr, 1, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  SKS_CUDA_TRY(cudaStreamBeginCaptureToGraph(B->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  B->per_round = enqueue_round(R, B->cs);
+  {
+    cudaGraph_t got = nullptr;
+    SKS_CUDA_TRY(cudaStreamEndCapture(B->cs, &got));
+  }
+  SKS_CUDA_TRY(cudaGetLastError());
+  SKS_CUDA_TRY(cudaGraphInstantiate(&B->e, B->g, 0));
+  SKS_CUDA_TRY(cudaEventRecord(ev_plan.b, stream));
+  SKS_TRY(ev_plan.ms(&B->ms_plan));
+  SKS_TRY(ev_tune.ms(&B->ms_tune));
+  *out = B;
+  B = nullptr;  // the guard keeps nothing
+  return SKS_OK;
+}
+
+sks_status batch_solve(sks_batch* B, double* const* xs, sks_stats* stats, sks_batch_info* info,
+                       cudaStream_t stream) {
+  if (!B) return fail(SKS_ERR_INVALID_ARG, "batch plan is NULL");
+  if (!xs) return fail(SKS_ERR_INVALID_ARG, "x array is NULL");
+  const int P = B->P;
+  for (int i = 0; i < P; ++i)
+    if (!xs[i]) return fail(SKS_ERR_INVALID_ARG, "x of batch problem " + std::to_string(i) + " is NULL");
+  Layout& L = B->L;
+  for (int i = 0; i < P; ++i) L.host[i].x = xs[i];
+  EventPair ev_solve;
+  SKS_TRY(ev_solve.init());
+  SKS_CUDA_TRY(cudaMemcpyAsync(L.D, L.host.data(), P * sizeof(BDesc), cudaMemcpyHostToDevice, stream));
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.a, stream));
-  int burst = 4;
-  while (rounds < max_rounds) {
-    const int nb = (int)std::min<int64_t>(burst, max_rounds - rounds);
-    for (int g = 0; g < nb; ++g) SKS_CUDA_TRY(cudaGraphLaunch(G.e, stream));
-    note_launch(per_round * nb);
-    rounds += nb;
-    SKS_CUDA_TRY(cudaMemcpyAsync(h_active, L.active, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    SKS_CUDA_TRY(cudaStreamSynchronize(stream));
-    if (*h_active == 0) break;
-    burst = std::min(16, burst * 2);
-  }
+  SKS_CUDA_TRY(cudaGraphLaunch(B->e, stream));
+  note_launch(2 + 3 * P);  // setup kernels (counted per round below)
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.b, stream));
 
-  // ---- per-problem results
+  // ---- per-problem results (the one synchronisation of the solve)
   std::vector<BState> hs(P);
   unsigned long long h_tap[3] = {0, 0, 0}, h_tgram[3] = {0, 0, 0};
   double h_flops = 0.0, h_gflops = 0.0;
+  long long rounds = 0;
   SKS_CUDA_TRY(cudaMemcpyAsync(hs.data(), L.S, P * sizeof(BState), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(h_tap, L.tap, sizeof(h_tap), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(&h_flops, L.apass_flops, sizeof(double), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(h_tgram, L.tgram, sizeof(h_tgram), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(&h_gflops, L.gram_flops, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(&rounds, L.rounds, sizeof(long long), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaStreamSynchronize(stream));
-  float ms_setup = 0.f, ms_tune = 0.f, ms_solve = 0.f;
-  SKS_TRY(ev_setup.ms(&ms_setup));
-  SKS_TRY(ev_tune.ms(&ms_tune));
+  note_launch((int)(rounds * B->per_round));
+  float ms_solve = 0.f;
   SKS_TRY(ev_solve.ms(&ms_solve));
   sks_status result = SKS_OK;
   int first_bad = -1;
@@ -1233,16 +1298,16 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
       t.final_delta_tilde = s.dt;
       t.est_rel_err = s.btx > 0 ? std::sqrt(std::max(0.0, s.dt / s.btx)) : 0.0;
       t.outer_iters = 1;
-      t.ms_total = ms_setup + ms_tune + ms_solve;
+      t.ms_total = ms_solve;
       t.status = (sks_status)s.status;
     }
   }
   if (info) {
     info->rounds = rounds;
-    info->kernels_per_round = per_round;
-    info->rows_per_unit = chosen;
-    info->ms_setup = ms_setup;
-    info->ms_autotune = ms_tune;
+    info->kernels_per_round = B->per_round;
+    info->rows_per_unit = B->chosen;
+    info->ms_setup = B->ms_plan;
+    info->ms_autotune = B->ms_tune;
     info->ms_solve = ms_solve;
     info->ms_apass = (float)((double)h_tap[2] * 1e-6);
     info->apass_flops = h_flops;
@@ -1257,6 +1322,22 @@ sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, dou
                             " (per-problem statuses are in stats[i].status)");
   }
   return SKS_OK;
+}
+
+void batch_destroy(sks_batch* B) { delete B; }
+
+sks_status solve_batched(const sks_problem* probs, int P, const sks_opts* o, double* const* xs, sks_stats* stats,
+                         sks_batch_info* info, int rows_per_unit, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (!xs) return fail(SKS_ERR_INVALID_ARG, "x array is NULL");
+  for (int i = 0; i < P && probs; ++i)
+    if (!xs[i]) return fail(SKS_ERR_INVALID_ARG, "x of batch problem " + std::to_string(i) + " is NULL");
+  sks_batch* B = nullptr;
+  SKS_TRY(batch_create(&B, probs, P, o, rows_per_unit, ws, ws_bytes, stream));
+  const sks_status r = batch_solve(B, xs, stats, info, stream);
+  const std::string msg = last_error_cstr();
+  batch_destroy(B);
+  if (r != SKS_OK) set_last_error(msg);
+  return r;
 }
 
 }  // namespace sks

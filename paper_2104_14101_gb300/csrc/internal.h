@@ -131,6 +131,11 @@ sks_status adjoint_grads(cudaStream_t stream, const sks_problem* p, const double
 sks_status batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes);
 sks_status solve_batched(const sks_problem* probs, int count, const sks_opts* o, double* const* xs, sks_stats* stats,
                          sks_batch_info* info, int rows_per_unit, void* ws, size_t ws_bytes, cudaStream_t stream);
+sks_status batch_create(sks_batch** out, const sks_problem* probs, int count, const sks_opts* o, int rows_per_unit,
+                        void* ws, size_t ws_bytes, cudaStream_t stream);
+sks_status batch_solve(sks_batch* plan, double* const* xs, sks_stats* stats, sks_batch_info* info,
+                       cudaStream_t stream);
+void batch_destroy(sks_batch* plan);
 sks_status selftest_wait_timeout(long long limit_ns, cudaStream_t stream);
 sks_status hess_apply_ws(const sks_problem* p, size_t* bytes);
 sks_status hess_apply(const sks_problem* p, const double* x, double* y, int extended, void* ws, size_t ws_bytes,

@@ -95,6 +95,15 @@ WORKLOADS = {
                desc="differentiable solve: n=2^18, d=1024, float32 A, sigma_j=(1+j)^-1/2, 8 right-hand sides, "
                     "nu=1e-2, Lambda=1+U; forward mixed adaptive PCG (Gaussian, tol 1e-8), backward adjoint solve "
                     "+ dA, db, dnu, dLambda"),
+    # the paper's synthetic experiments (Section 6, Figs. 1-3): nu swept over 1e-1 .. 1e-4 at n = 2^19,
+    # sigma_j = 0.995^j; timed mixed solves, and delta_t / delta_0 and m_t traced in the plain form
+    "P-sweep": dict(config="P", d=7000, sweep=True, method="pcg", kind="srht", m_init=1, m_max=1 << 15, tol=1e-8,
+                    precision="mixed", desc="paper-scale replay: n=2^19, d=7000, sigma_j=0.995^j, Lambda=I, "
+                                            "nu in {1e-1, 1e-2, 1e-3, 1e-4}"),
+    "P-sweep-d14000": dict(config="P", d=14000, sweep=True, method="pcg", kind="srht", m_init=1, m_max=1 << 15,
+                           tol=1e-8, precision="mixed",
+                           desc="paper-scale replay: n=2^19, d=14000, sigma_j=0.995^j, Lambda=I, "
+                                "nu in {1e-1, 1e-2, 1e-3, 1e-4}"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -858,6 +867,89 @@ def run_batched(args, wl, world, rank, local):
     return line if rank == 0 else None
 
 
+def run_sweep(args, wl, world, rank, local):
+    """Replay of the paper's synthetic experiments (Section 6, Figs. 1-3) at their sizes: for every nu,
+    (1) the mixed form's adaptive PCG timed (SRHT and SJLT s = 4, tol 1e-8, CUDA events, median of
+    --steps); (2) x* from the plain float64 adaptive PCG to 1e-13, certified by the oracle's Hessian
+    pass on the host (||x - x*||_H <= ||b - H x||_2 / (nu sqrt(min lambda)), relative to
+    sqrt(b^T x)); (3) delta_t / delta_0 (delta_t = 1/2 ||x_t - x*||_H^2, Section 1.1) and m_t after
+    every improvement test, traced in the plain float64 form for adaptive PCG (SRHT, SJLT),
+    adaptive IHS (SRHT) and PCG at the fixed m = 2d of Section 6.  Replicas only (rank 0)."""
+    import paper_2104_14101_gb300 as sks
+    import synthetic
+    from oracle import solvers as O
+    if rank != 0:
+        return None
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    d = int(wl["d"])
+    n = int(synthetic.CONFIGS["P"]["n"])
+    stream = torch.cuda.current_stream(dev)
+    records = []
+    t_all = time.perf_counter()
+    for nu in (1e-1, 1e-2, 1e-3, 1e-4):
+        prob = synthetic.make_problem_torch("P", seed=0, device=dev, d=d, nu=nu)
+        A32, A64, lam = prob["A32"], prob["A64"], prob["lam"]
+        b = prob["b"][:, 0].contiguous()
+        sig = prob["sigma"].cpu().numpy()
+        frac = sig ** 2 / (sig ** 2 + nu ** 2)
+        rec = {"nu": nu, "d_e": float(frac.sum() / frac.max()), "timed_mixed": {}, "curves": {}}
+        for kind in ("srht", "sjlt"):
+            S = sks.Solver(A32, b, nu, lam, method="pcg", kind=kind, sjlt_s=4, m_init=1, m_max=wl["m_max"], tol=1e-8,
+                           precision="mixed", max_iter=5000, seed=0)
+            S.solve()
+            ts = []
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, st = S.solve()[:2]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            rec["timed_mixed"][kind] = {"ms": float(np.median(ts)), "iters": st["iters"], "final_m": st["final_m"],
+                                        "rejections": st["rejections"], "a_passes": st["a_passes"],
+                                        "outer_iters": st["outer_iters"], "ms_sketch": st["ms_sketch"],
+                                        "ms_factor": st["ms_factor"]}
+            del S
+        del A32
+        # x* (plain float64, 1e-13) and the oracle's residual certificate on the host
+        Sx = sks.Solver(A64, b, nu, lam, method="pcg", kind="srht", m_init=1, m_max=wl["m_max"], tol=1e-13,
+                        max_iter=5000, seed=1)
+        xstar, stx = Sx.solve(check=False)[:2]
+        del Sx
+        xh, bh, lh = xstar.cpu().numpy(), b.cpu().numpy(), lam.cpu().numpy()
+        hx = nu ** 2 * lh * xh
+        for r0 in range(0, n, 1 << 16):
+            hx += O.hess_apply(A64[r0:r0 + (1 << 16)].cpu().numpy(), 0.0, lh, xh)
+        res = float(np.linalg.norm(bh - hx))
+        rec["x_star"] = {"status": stx["status_name"], "iters": stx["iters"], "final_m": stx["final_m"],
+                         "oracle_residual_2norm": res,
+                         "rel_err_H_bound": res / (nu * float(np.sqrt(lh.min()))) / float(np.sqrt(max(bh @ xh, 1e-300)))}
+        for name, method, kind, m_init in (("adaptive-pcg-srht", "pcg", "srht", 1), ("adaptive-pcg-sjlt", "pcg", "sjlt", 1),
+                                           ("adaptive-ihs-srht", "ihs", "srht", 1),
+                                           ("pcg-m2d-srht", "fixed-pcg", "srht", 2 * d)):
+            S = sks.Solver(A64, b, nu, lam, method=method, kind=kind, sjlt_s=4, m_init=m_init, m_max=wl["m_max"],
+                           tol=1e-10, max_iter=2000, seed=0, trace_cap=8192, x_star=xstar)
+            x, st, tr = S.solve(check=False)
+            rec["curves"][name] = {
+                "status": st["status_name"], "ms_traced": st["ms_total"], "iters": st["iters"],
+                "final_m": st["final_m"],
+                "t_m_delta_ratio_accepted": [[int(e["t"]), int(e["m"]),
+                                              (e["delta"] / e["delta0"]) if e["delta0"] > 0 else 0.0,
+                                              int(e["accepted"])] for e in tr]}
+            del S
+        records.append(rec)
+        del prob, A64, b, lam, xstar
+        torch.cuda.empty_cache()
+    wall = time.perf_counter() - t_all
+    return {"metric": "paper-scale replay (Section 6): ms per mixed adaptive PCG solve to 1e-8 and traced "
+                      "delta_t/delta_0, m_t per nu", "value": sum(r["timed_mixed"]["srht"]["ms"] for r in records),
+            "unit": "ms (sum over the four nu, SRHT)", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": wl["desc"], "n": n, "d": d}, "wall_s": wall,
+            "sweep": records}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -878,6 +970,8 @@ def main():
         fn = run_reference_batched if wl.get("batched") else (run_reference_adjoint if wl.get("adjoint")
                                                                else run_reference)
         line = fn(args, wl, world, rank)
+    elif wl.get("sweep"):
+        line = run_sweep(args, wl, world, rank, local)
     elif wl.get("batched"):
         line = run_batched(args, wl, world, rank, local)
     elif wl.get("adjoint"):

@@ -85,6 +85,9 @@ typedef struct {
   int32_t outer;     /* refinement step (mixed form), 0 otherwise     */
   int32_t column;    /* right-hand side the test belongs to           */
   int32_t reserved;
+  double delta;      /* with opts.x_star: 1/2 ||x - x*||_H^2 at the iterate kept after the event
+                        (x+ if accepted, x_t otherwise); 0 without x_star                      */
+  double delta0;     /* the same at the column's x_0                               */
 } sks_trace_event;
 
 /* Options of Algorithms 1 and 2 (defaults by sks_opts_default). */
@@ -106,6 +109,10 @@ typedef struct {
   int stop_rule;       /* SKS_STOP_ESTIMATE or SKS_STOP_CERTIFIED (below)                    */
   double cert_delta;   /* failure probability delta of SKS_STOP_CERTIFIED, in (0, 1)         */
   double cert_de;      /* effective dimension put into m_delta; 0 = d (the conservative d_e) */
+  const double* x_star; /* optional device d x k solution, for traces only: each trace event
+                           then carries delta_t = 1/2 ||x_t - x*||_H^2 (Section 1.1), formed
+                           exactly as 1/2 (x* - x_t)^T r_t from the iteration's residual
+                           (one extra dot per step; plain float64 form; NULL = off)          */
 } sks_opts;
 
 /* Stop rules (the paper prescribes none; Section 1.3 and Remark 4.2).  With
@@ -145,7 +152,7 @@ typedef struct sks_precond sks_precond;
 /* Fill `o` with the defaults: rho = 1/8, m_init = 1, m_max = 0, SRHT, s = 1,
  * tol = 1e-10, max_iter = 1000, plain float64, reuse_residual = 1, seed = 0,
  * max_outer = 20, inner_tol = 1e-4, no trace, SKS_STOP_ESTIMATE,
- * cert_delta = 0.01, cert_de = 0. */
+ * cert_delta = 0.01, cert_de = 0, x_star = NULL. */
 void sks_opts_default(sks_opts* o);
 
 /* Version string of the library build. */

@@ -33,7 +33,8 @@ class Problem(C.Structure):
 
 class TraceEvent(C.Structure):
     _fields_ = [("t", C.c_int64), ("m", C.c_int64), ("ratio", C.c_double), ("threshold", C.c_double),
-                ("accepted", C.c_int32), ("outer", C.c_int32), ("column", C.c_int32), ("reserved", C.c_int32)]
+                ("accepted", C.c_int32), ("outer", C.c_int32), ("column", C.c_int32), ("reserved", C.c_int32),
+                ("delta", C.c_double), ("delta0", C.c_double)]
 
 
 class Opts(C.Structure):
@@ -41,7 +42,8 @@ class Opts(C.Structure):
                 ("sjlt_s", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int64), ("precision", C.c_int),
                 ("reuse_residual", C.c_int), ("seed", C.c_uint64), ("max_outer", C.c_int64),
                 ("inner_tol", C.c_double), ("trace", C.POINTER(TraceEvent)), ("trace_cap", C.c_int64),
-                ("stop_rule", C.c_int), ("cert_delta", C.c_double), ("cert_de", C.c_double)]
+                ("stop_rule", C.c_int), ("cert_delta", C.c_double), ("cert_de", C.c_double),
+                ("x_star", C.c_void_p)]
 
 
 class Stats(C.Structure):

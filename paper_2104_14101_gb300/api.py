@@ -192,11 +192,16 @@ class Solver:
     (adaptive, Algorithms 2 and 1) or one of the non-adaptive solvers
     "fixed-pcg", "fixed-ihs", "polyak-ihs" (sketch size m_init) and "cg"."""
 
-    def __init__(self, A, b, nu, lam, method="pcg", trace_cap=0, **opts):
+    def __init__(self, A, b, nu, lam, method="pcg", trace_cap=0, x_star=None, **opts):
         self._lib = L.load()
         self.method = method
         self.problem, self._keep = make_problem(A, b, nu, lam)
         self.opts = options(**opts)
+        if x_star is not None:
+            # traces carry delta_t = 1/2 ||x_t - x*||_H^2 (column-major d x k copy kept alive)
+            xs2 = x_star.to(device=A.device, dtype=torch.float64)
+            self._xstar = (xs2[:, None] if xs2.dim() == 1 else xs2).t().contiguous()
+            self.opts.x_star = self._xstar.data_ptr()
         self.trace_buf = (L.TraceEvent * trace_cap)() if trace_cap else None
         if trace_cap:
             self.opts.trace = C.cast(self.trace_buf, C.POINTER(L.TraceEvent))
@@ -233,7 +238,7 @@ class Solver:
             for i in range(st.trace_len):
                 e = self.trace_buf[i]
                 trace.append(dict(t=e.t, m=e.m, ratio=e.ratio, thr=e.threshold, accepted=bool(e.accepted),
-                                  outer=e.outer, column=e.column))
+                                  outer=e.outer, column=e.column, delta=e.delta, delta0=e.delta0))
         return x, stats, trace
 
 

@@ -23,6 +23,7 @@ extern "C" void sks_opts_default(sks_opts* o) {
   o->stop_rule = SKS_STOP_ESTIMATE;
   o->cert_delta = 0.01;
   o->cert_de = 0.0;
+  o->x_star = nullptr;
 }
 
 extern "C" const char* sks_version(void) { return "sks 0.1 (sm_103a)"; }

@@ -49,6 +49,7 @@ struct LoopShared {
   double alpha[kLoopMaxK];
   double fin[kNW][32];
   double red[kNW][kLoopMaxK];
+  int evi[kLoopMaxK];  // trace event of each column's current step (-1: none)
   int ok, quit, any_reject, all_done;
 };
 
@@ -127,7 +128,7 @@ SKS_DEV void grid_col_sums(const double* dots, int slot, LoopShared* sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < K) {
     double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += dots[((size_t)b * K + warp) * 4 + slot];
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += dots[((size_t)b * K + warp) * kLoopDots + slot];
     s = warp_sum(s);
     if (lane == 0) sh->sum[warp] = s;
   }
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
   const int nparts = gridDim.x * Core::NG;
   const bool pcg = T.method == 0;
   const bool f32v = sizeof(TX) == 4;
-  double* dots = T.dots + (size_t)blockIdx.x * K * 4;
+  double* dots = T.dots + (size_t)blockIdx.x * K * kLoopDots;
   int it = 0;
   long long apass_ns = 0, passes = 0, iters = 0;
   bool ok = true;
@@ -311,12 +312,33 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
     if (ok) reduce_phase<TX, K>(T, d, nparts, T.x, pcg ? -1.0 : 1.0, T.b, pcg ? 1.0 : -1.0, T.r, nullptr, dv, sh);
     if (ok) ok = grid_sync(T.head, sh, T.st);
   }
+  const double dsgn = pcg ? 1.0 : -1.0;  // r = b - H x (PCG) or g = H x - b (IHS)
+  double dz[K];
   if (ok && T.restart) {
     zero(dv);
     ok = apply_phase<K>(T, d, T.r, T.rt, dv, sh);
-    if (ok) cta_sum_to<K>(dv, sh, dots + 3, 4);
+    if (ok) cta_sum_to<K>(dv, sh, dots + 3, kLoopDots);
+    if (ok && T.xstar && T.first) {
+      // trace mode: delta_0 = 1/2 (x* - x_0)^T r_0
+      zero(dz);
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+        if (c < T.kc)
+          for (int j = gt; j < d; j += GT) {
+            const size_t e = (size_t)c * d + j;
+            dz[c] = fma(T.xstar[e] - T.x[e], T.r[e], dz[c]);
+          }
+      named_bar_sync(1, kConsumers);
+      cta_sum_to<K>(dz, sh, dots + 4, kLoopDots);
+    }
     if (ok) ok = grid_sync(T.head, sh, T.st);
     if (ok) {
+      if (T.xstar && T.first) {
+        grid_col_sums<K>(T.dots, 4, sh);
+        if (tid == 0)
+          for (int c = 0; c < T.kc; ++c) sh->col[c].delta = sh->col[c].delta0 = 0.5 * dsgn * sh->sum[c];
+        named_bar_sync(1, kConsumers);
+      }
       grid_col_sums<K>(T.dots, 3, sh);
       if (tid == 0) {
         for (int c = 0; c < T.kc; ++c) {
@@ -373,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
     if (pcg) reduce_phase<TX, K>(T, d, nparts, T.p, 1.0, nullptr, 0.0, T.Hp, T.p, dv, sh);
     else reduce_phase<TX, K>(T, d, nparts, T.xp, 1.0, T.b, -1.0, T.rp, nullptr, dv, sh);
     if (pcg) {
-      cta_sum_to<K>(dv, sh, dots + 0, 4);
+      cta_sum_to<K>(dv, sh, dots + 0, kLoopDots);
       if (!(ok = grid_sync(T.head, sh, T.st))) break;
       // 3: alpha, x+ and r+
       grid_col_sums<K>(T.dots, 0, sh);
@@ -401,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
     // 4: r~+ = H_S^{-1} r+ (IHS: v+ = H_S^{-1} g+) and the decrement
     zero(dv);
     if (!(ok = apply_phase<K>(T, d, T.rp, T.rtp, dv, sh))) break;
-    cta_sum_to<K>(dv, sh, dots + 1, 4);
+    cta_sum_to<K>(dv, sh, dots + 1, kLoopDots);
     if (!(ok = grid_sync(T.head, sh, T.st))) break;
     grid_col_sums<K>(T.dots, 1, sh);
     // 5: the improvement test of Algorithm 2 / Algorithm 1
@@ -421,7 +443,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
         s.accept = !reject;
         s.rejected = reject;
         anyrej |= reject;
+        sh->evi[c] = -1;
         if (blockIdx.x == 0 && T.trace && T.head->trace_len < T.trace_cap) {
+          sh->evi[c] = T.head->trace_len;
           LoopTraceEv& ev = T.trace[T.head->trace_len++];
           ev.t = s.t;
           ev.m = T.m;
@@ -429,13 +453,16 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
           ev.thr = thr;
           ev.accepted = !reject;
           ev.column = c;
+          ev.delta = s.delta;  // the kept iterate's; accepted steps are updated below
+          ev.delta0 = s.delta0;
         }
       }
       sh->any_reject = anyrej;
     }
     named_bar_sync(1, kConsumers);
-    // accepted columns shift; b^T x
+    // accepted columns shift; b^T x (and, in trace mode, (x* - x+)^T r+)
     zero(dv);
+    zero(dz);
 #pragma unroll
     for (int c = 0; c < K; ++c) {
       if (!live(c) || !sh->col[c].accept) continue;
@@ -449,11 +476,26 @@ __global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 
         if (pcg) T.p[e] = T.rtp[e] + beta * T.p[e];
         else T.xp[e] = xn - T.mu * T.rtp[e];  // the next proposal
         dv[c] = fma(T.b[e], xn, dv[c]);
+        if (T.xstar) dz[c] = fma(T.xstar[e] - xn, T.rp[e], dz[c]);
         if (f32v) T.v32[e] = (float)(pcg ? T.p[e] : T.xp[e]);
       }
     }
-    cta_sum_to<K>(dv, sh, dots + 2, 4);
+    cta_sum_to<K>(dv, sh, dots + 2, kLoopDots);
+    if (T.xstar) {
+      named_bar_sync(1, kConsumers);
+      cta_sum_to<K>(dz, sh, dots + 4, kLoopDots);
+    }
     if (!(ok = grid_sync(T.head, sh, T.st))) break;
+    if (T.xstar) {
+      grid_col_sums<K>(T.dots, 4, sh);
+      if (tid == 0)
+        for (int c = 0; c < T.kc; ++c) {
+          if (!live(c) || !sh->col[c].accept) continue;
+          sh->col[c].delta = 0.5 * dsgn * sh->sum[c];
+          if (blockIdx.x == 0 && sh->evi[c] >= 0) T.trace[sh->evi[c]].delta = sh->col[c].delta;
+        }
+      named_bar_sync(1, kConsumers);
+    }
     grid_col_sums<K>(T.dots, 2, sh);
     // 6: the stop rule
     if (tid == 0) {
@@ -570,7 +612,9 @@ size_t loop_partial_bytes(const ApassPlan& plan, int64_t d, int K, bool vec_f32)
   return (size_t)plan.grid * (kConsumers / plan.group) * (size_t)K * (size_t)d * (vec_f32 ? 4 : 8) + 256;
 }
 
-size_t loop_dots_bytes(const ApassPlan& plan, int K) { return (size_t)plan.grid * K * 4 * sizeof(double) + 256; }
+size_t loop_dots_bytes(const ApassPlan& plan, int K) {
+  return (size_t)plan.grid * K * kLoopDots * sizeof(double) + 256;
+}
 
 void loop_adjust_plan(ApassPlan* pl, bool a_f32, bool vec_f32) {
   const DeviceInfo& di = device_info();

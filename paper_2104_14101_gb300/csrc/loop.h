@@ -6,6 +6,7 @@
 namespace sks {
 
 constexpr int kLoopMaxK = 8;  // right-hand sides iterated in lockstep by one launch
+constexpr int kLoopDots = 5;  // per-CTA dot partials per column: pHp, delta~+, b^T x, restart, delta
 
 // State of one right-hand side (column), kept on the device between launches.
 struct LoopCol {
@@ -13,6 +14,7 @@ struct LoopCol {
   double dt0;       // decrement at the first restart of this solve
   double stop_abs;  // stop when dt <= stop_abs (inner solves of the mixed form: rel2 * dt0)
   double btx_outer; // b^T x_o of the refinement's outer iterate (mixed form)
+  double delta, delta0;  // trace mode: 1/2 ||x - x*||_H^2 at the current iterate and at x_0
   long long t, I;
   int active;       // 0: finished before this solve (e.g. its refinement converged)
   int stop, numeric, accept, rejected, outer_done, pad0, pad1;
@@ -34,6 +36,7 @@ struct LoopTraceEv {
   long long t, m;
   double ratio, thr;
   int accepted, column;
+  double delta, delta0;
 };
 
 // Sketched preconditioner as the loop applies it (see precond_apply1).
@@ -75,7 +78,8 @@ struct LoopTask {
   long long ld_t;     // leading dimension of t1, t2 (>= max(d, m))
   float* v32;         // float32 copy of the vector the A-pass reads (float32 A-pass), d x K
   void* partials;     // A-pass partial sums [grid * NG][K][d]
-  double* dots;       // [grid][K][4]
+  double* dots;       // [grid][K][kLoopDots]
+  const double* xstar; // trace mode: the solution (d x K), NULL = off
   LoopCol* cols;      // [K]
   LoopHead* head;
   LoopTraceEv* trace; // optional device trace buffer

@@ -457,6 +457,7 @@ sks_status precond_apply1(const sks_precond* P, const double* z, double* v, cuda
 // ---------------------------------------------------------------- iteration kernels
 struct Ctl {
   double dt, dI, dp, alpha, ratio, thr, btx;
+  double delta, delta0;  // trace mode: 1/2 ||x - x*||_H^2 now and at x_0
   long long t, I;
   int accept, stop, numeric, pad;
 };
@@ -621,6 +622,21 @@ __global__ void ctl_init_kernel(Ctl* ctl) {
   memset(ctl, 0, sizeof(Ctl));
 }
 
+// Trace mode: delta = 1/2 ||x - x*||_H^2 = 1/2 sgn (x* - x)^T r, with r the
+// residual b - H x (PCG, sgn = 1) or the gradient H x - b (IHS, sgn = -1);
+// first: also delta0.
+__global__ void __launch_bounds__(kStepThreads) delta_kernel(int d, const double* xs, const double* x,
+                                                             const double* r, double sgn, Ctl* ctl, int first) {
+  __shared__ double scratch[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s += (xs[j] - x[j]) * r[j];
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) {
+    ctl->delta = 0.5 * sgn * s;
+    if (first) ctl->delta0 = ctl->delta;
+  }
+}
+
 // Small vector kernels of the refinement loop.
 __global__ void f64_to_f32_vec(int d, const double* a, float* b) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -667,7 +683,7 @@ struct SolveWs {
   // device-resident loop (loop.cu): lw right-hand sides in lockstep (0: not available)
   int lw;
   long long lt_ld;                       // leading dimension of lt1, lt2
-  double *lx, *lr, *lrt, *lp, *lHp, *lxp, *lrp, *lrtp, *lxo, *lbo, *lb, *lt1, *lt2;
+  double *lx, *lr, *lrt, *lp, *lHp, *lxp, *lrp, *lrtp, *lxo, *lbo, *lb, *lxs, *lt1, *lt2;
   float* lv32;
   void* lpart;      // loop A-pass partial sums
   void* lres;       // double-float residual partial sums (mixed form), lw columns
@@ -720,7 +736,7 @@ sks_status solve_layout(const sks_problem* p, const sks_opts* o, void* ws, size_
     w.lw = lw;
     const size_t dk = d * (size_t)lw;
     w.lt_ld = (long long)std::max<size_t>(d, (size_t)m_max);
-    double** vecs[] = {&w.lx, &w.lr, &w.lrt, &w.lp, &w.lHp, &w.lxp, &w.lrp, &w.lrtp, &w.lxo, &w.lbo, &w.lb};
+    double** vecs[] = {&w.lx, &w.lr, &w.lrt, &w.lp, &w.lHp, &w.lxp, &w.lrp, &w.lrtp, &w.lxo, &w.lbo, &w.lb, &w.lxs};
     for (double** v : vecs) *v = c.take<double>(dk);
     w.lt1 = c.take<double>((size_t)w.lt_ld * lw);
     w.lt2 = c.take<double>((size_t)w.lt_ld * lw);
@@ -992,6 +1008,11 @@ struct Engine {
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     if (xprev) SKS_CUDA_TRY(cudaMemcpyAsync(xprev, W.x, d * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    const double* xstar = (o->x_star && !mixed_inner) ? o->x_star + (size_t)cur_col * d : nullptr;
+    if (xstar) {
+      delta_kernel<<<1, kStepThreads, 0, stream>>>(d, xstar, W.x, W.r, pcg_like ? 1.0 : -1.0, W.ctl, 1);
+      note_launch();
+    }
     if (method == CG) {
       // CG stop rule: ||r||_2 <= tol ||b||_2 (no preconditioner, so no estimate of the H-norm error)
       dot_kernel<<<1, kStepThreads, 0, stream>>>(d, b, b, W.scal + 2);
@@ -1054,6 +1075,10 @@ struct Engine {
         note_launch();
       }
       SKS_CUDA_TRY(cudaGetLastError());
+      if (xstar) {
+        delta_kernel<<<1, kStepThreads, 0, stream>>>(d, xstar, W.x, W.r, pcg_like ? 1.0 : -1.0, W.ctl, 0);
+        note_launch();
+      }
       const long long t_before = h.t;
       SKS_CUDA_TRY(cudaMemcpyAsync(&h, W.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
       SKS_TRY(sync_point("iteration"));
@@ -1067,6 +1092,8 @@ struct Engine {
         e.outer = outer;
         e.column = cur_col;
         e.reserved = 0;
+        e.delta = h.delta;
+        e.delta0 = h.delta0;
       }
       if (h.numeric) return fail(SKS_ERR_NUMERIC, "non-finite value in the iteration");
       if (!h.accept) {
@@ -1233,6 +1260,8 @@ sks_status loop_run(Engine& E, LoopTask& T, LoopHostCtl* h) {
         e.outer = E.outer;
         e.column = v.column + E.cur_col;
         e.reserved = 0;
+        e.delta = v.delta;
+        e.delta0 = v.delta0;
       }
     }
     for (int c = 0; c < T.kc; ++c)
@@ -1308,6 +1337,13 @@ sks_status solve_columns_fused(Engine& E, const double* B, double* X_io) {
     T.trace = E.W.ltrace_cap > 0 ? E.W.ltrace : nullptr;
     T.trace_cap = E.W.ltrace_cap;
     T.st = E.W.st;
+    // trace mode (plain form): the solution columns of this batch, padded like b
+    if (o->x_star && !E.mixed) {
+      SKS_CUDA_TRY(cudaMemsetAsync(E.W.lxs, 0, dk * sizeof(double), stream));
+      SKS_CUDA_TRY(cudaMemcpyAsync(E.W.lxs, o->x_star + c0 * d, (size_t)d * kc * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, stream));
+      T.xstar = E.W.lxs;
+    }
     bool converged = false;
     if (!E.mixed) {
       T.b = E.W.lb;

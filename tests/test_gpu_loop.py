@@ -82,3 +82,36 @@ def test_lockstep_zero_and_nonzero_columns():
     assert np.all(host(x)[:, 1] == 0.0)
     for c in (0, 2):
         assert O.rel_err_H(p.A, p.nu, p.lam, host(x)[:, c], xs[:, c]) <= 1e-10
+
+
+@pytest.mark.parametrize("method", ["pcg", "ihs", "fixed-pcg"])
+def test_trace_delta_matches_oracle(method):
+    # with x_star, every trace event carries delta_t = 1/2 ||x_t - x*||_H^2 of
+    # the iterate kept after it; the device forms it as 1/2 (x* - x)^T r.
+    # Fused loop (adaptive) and host-driven loop (fixed PCG) alike.
+    p = synthetic.make_problem("C1", 1, n=1024, d=64, nu=1e-2)
+    xs = O.direct_solve(p.A, p.b, p.nu, p.lam)
+    kw = dict(kind="gaussian", m_init=1 if method != "fixed-pcg" else 128, tol=1e-10, seed=5, reuse_residual=False)
+    solver = api().Solver(dev(p.A), dev(p.b), p.nu, dev(p.lam), method=method, trace_cap=4096, x_star=dev(xs), **kw)
+    x, st, tr = solver.solve()
+    d0 = 0.5 * O.h_norm_sq(p.A, p.nu, p.lam, xs)  # x_0 = 0
+    assert len(tr) > 5
+    for e in tr:
+        assert np.isclose(e["delta0"], d0, rtol=1e-10)
+    final = 0.5 * O.h_norm_sq(p.A, p.nu, p.lam, host(x) - xs)
+    assert np.isclose(tr[-1]["delta"], final, rtol=1e-4, atol=1e-20 * d0)
+    kept = [e["delta"] for e in tr]
+    if method != "ihs":  # PCG minimises the H-norm error over a growing space: non-increasing
+        assert all(b <= a * (1 + 1e-8) + 1e-22 * d0 for a, b in zip(kept, kept[1:]))
+    if method == "pcg":
+        # against the oracle's own iterates (same accept / reject sequence, literal restart)
+        xo, so, to = O.adaptive_pcg(p.A, p.b, p.nu, p.lam, kind="gaussian", seed=5, m_init=1, tol=1e-10,
+                                    literal_restart=True, record_states=True)
+        xs_o = [e["x"] for e in to[1:]] + [xo]  # the iterate kept after each event
+        for eo, eg, xk in zip(to, tr, xs_o):
+            if abs(eo["ratio"] / eo["thr"] - 1) < 1e-9:
+                break
+            assert eo["accepted"] == eg["accepted"]
+            do = 0.5 * O.h_norm_sq(p.A, p.nu, p.lam, xk - xs)
+            if do > 1e-16 * d0:
+                assert np.isclose(eg["delta"], do, rtol=1e-5), (eo["t"], eg["delta"], do)

@@ -54,7 +54,15 @@ typedef enum {
   SKS_SRHT = 0,     /* S = R H E: Walsh-Hadamard of the sign-flipped, zero-padded A, rows subsampled */
   SKS_GAUSSIAN = 1, /* i.i.d. N(0, 1/m) entries, generated from Philox, never stored               */
   SKS_SJLT = 2,     /* s nonzeros +-1/sqrt(s) per column at distinct hashed rows                    */
-  SKS_RADEMACHER = 3 /* sub-Gaussian: i.i.d. +-1/sqrt(m) entries from Philox bits, never stored        */
+  SKS_RADEMACHER = 3, /* sub-Gaussian: i.i.d. +-1/sqrt(m) entries from Philox bits, never stored       */
+  /* The Gaussian embedding with 8-bit tensor-core arithmetic (float32 A only):
+   * the entries of G rounded to e4m3 and A quantised to e4m3 against one
+   * power-of-two scale per column and per slice of 16384 rows (per-tile
+   * scales), each slice's product scaled back in float32.  The adaptive
+   * solvers use it only when the rounding noise of A, 2^-8/3 ||A||_F^2 / d,
+   * is at most 0.1 nu^2 min lambda (else the bfloat16 split serves the same G;
+   * sks_stats.sketch_e4m3 says which); sks_sketch_create uses it as asked.   */
+  SKS_GAUSSIAN_E4M3 = 4
 } sks_kind;
 
 typedef enum { SKS_F64 = 0, SKS_F32 = 1 } sks_dtype;
@@ -144,6 +152,7 @@ typedef struct {
   float ms_apass;         /* device time of the A-pass kernels (CUDA events)    */
   int64_t apass_timed;    /* A-pass launches covered by ms_apass                */
   sks_status status;
+  int32_t sketch_e4m3;    /* SKS_GAUSSIAN_E4M3: 1 if the 8-bit sketch served the solve */
 } sks_stats;
 
 typedef struct sks_sketch sks_sketch;

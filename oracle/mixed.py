@@ -22,6 +22,12 @@ reproduce bit for bit:
   operand split (every row cut against its own maximum exponent into two
   slices of integers, 8 + 8 bits, so that all slice products are exactly
   summable); the Gram's parity test compares with the plain definition.
+* ``e4m3_round`` and ``gaussian_sketch_e4m3``: the optional 8-bit sketch --
+  the Gaussian entries rounded to float32, then to e4m3 (1 sign, 4 exponent
+  bits with bias 7, 3 mantissa bits; largest finite 448; subnormals down to
+  2^-9), times A quantised to e4m3 against one power-of-two scale per column
+  and per slice of 16384 data rows, 2^ceil(log2(max|a| / 448)); each slice's
+  product is multiplied back by its scales.
 * ``refine``: the outer refinement loop around any inner solver.
 """
 import numpy as np
@@ -115,3 +121,67 @@ def refine(A, b, nu, lam, inner, tol, max_outer=20):
         if h_norm_sq(A, nu, lam, dx) <= (tol / 2.0) ** 2 * max(h_norm_sq(A, nu, lam, x), 1e-300):
             return x, it
     return x, max_outer
+
+
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x):
+    """Round float32 values to the nearest e4m3 value (ties to even), as
+    float64: normal values keep 3 fraction bits (spacing 2^(e-3) for |x| in
+    [2^e, 2^(e+1)), e >= -6), subnormals are multiples of 2^-9 below 2^-6,
+    magnitudes past 448 saturate to 448 (finite saturation)."""
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    a = np.abs(x)
+    _, e = np.frexp(a)               # a = f 2^e, f in [0.5, 1): the binade is [2^(e-1), 2^e)
+    e = np.maximum(e - 1, -6)         # exponent of the binade, clamped into the subnormal range
+    step = np.ldexp(1.0, e - 3)
+    q = np.rint(a / step) * step      # rint: round half to even on the exact quotient
+    q = np.minimum(q, E4M3_MAX)
+    return np.sign(x) * q
+
+
+def e4m3_scales(A32, slice_rows=16384):
+    """Per-(slice, column) power-of-two scales 2^e, e the least integer with
+    max|a| <= 448 2^e, i.e. 2^ceil(log2(max|a| / 448)) (1 for an all-zero
+    block).  Computed exactly: with max|a| = f 2^E (f in [0.5, 1)) and
+    448 = 0.875 2^9, e = E - 9, plus 1 when f > 0.875."""
+    A = np.asarray(A32, dtype=np.float32).astype(np.float64)
+    n, d = A.shape
+    ns = max(1, (n + slice_rows - 1) // slice_rows)
+    sc = np.ones((ns, d))
+    for k in range(ns):
+        mx = np.max(np.abs(A[k * slice_rows:(k + 1) * slice_rows]), axis=0) if n else np.zeros(d)
+        nz = mx > 0
+        f, E = np.frexp(mx[nz])
+        sc[k, nz] = np.ldexp(1.0, E - 9 + (f > 0.875))
+    return sc
+
+
+def gaussian_sketch_e4m3(A32, m, seed, row0=0, slice_rows=16384):
+    """Rows [row0, m) of the unscaled 8-bit Gaussian sketch (S A = Y / sqrt(m)):
+    Y = sum over slices k of e4m3(G_k) e4m3(A_k / s_k) diag(s_k), with G from
+    ``rng.gaussian_block`` rounded to float32, then to e4m3, and s_k the
+    slice's column scales (``e4m3_scales``), all in float64."""
+    A = np.asarray(A32, dtype=np.float32)
+    n, d = A.shape
+    G8 = e4m3_round(R.gaussian_block(n, m, seed).astype(np.float32))[row0:]
+    sc = e4m3_scales(A, slice_rows)
+    Y = np.zeros((G8.shape[0], d))
+    for k in range(sc.shape[0]):
+        blk = A[k * slice_rows:(k + 1) * slice_rows].astype(np.float64) / sc[k][None, :]
+        A8 = e4m3_round(blk.astype(np.float32))
+        Y += (G8[:, k * slice_rows:(k + 1) * slice_rows] @ A8) * sc[k][None, :]
+    return Y
+
+
+def e4m3_midpoint_slack(g32, ulps=4):
+    """As ``bf16_midpoint_slack`` for the e4m3 rounding: one e4m3 step where a
+    perturbation of up to `ulps` float32 ulps can change the rounding, else 0."""
+    g = np.asarray(g32, dtype=np.float32)
+    step = np.spacing(np.abs(g)).astype(np.float32) * np.float32(ulps)
+    lo = e4m3_round((g - step).astype(np.float32))
+    hi = e4m3_round((g + step).astype(np.float32))
+    here = e4m3_round(g)
+    amb = (lo != here) | (hi != here)
+    return np.where(amb, np.maximum(np.abs(hi - lo), 2.0 ** -9), 0.0)

@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PD", 3: "NO_CONVERGENCE", 4: 
                 7: "WORKSPACE", 8: "UNSUPPORTED"}
 # sks_kind
 SRHT, GAUSSIAN, SJLT, RADEMACHER = 0, 1, 2, 3
-KINDS = {"srht": SRHT, "gaussian": GAUSSIAN, "sjlt": SJLT, "rademacher": RADEMACHER}
+KINDS = {"srht": SRHT, "gaussian": GAUSSIAN, "sjlt": SJLT, "rademacher": RADEMACHER, "gaussian-e4m3": 4}
 # stop rules
 STOP_RULES = {"estimate": 0, "certified": 1}
 # sks_fixed_method
@@ -52,7 +52,7 @@ class Stats(C.Structure):
                 ("final_delta_tilde", C.c_double), ("est_rel_err", C.c_double), ("trace_len", C.c_int64),
                 ("ms_total", C.c_float), ("ms_sketch", C.c_float), ("ms_factor", C.c_float),
                 ("ms_iter", C.c_float), ("ms_apass", C.c_float), ("apass_timed", C.c_int64),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("sketch_e4m3", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

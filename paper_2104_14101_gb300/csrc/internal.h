@@ -65,6 +65,9 @@ struct Carver {
 // dimension ld (elements), box (box_cols x box_rows), no swizzle, zero fill.
 sks_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, size_t elem_bytes,
                         uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_cols, uint32_t box_rows);
+// 8-bit rows x cols (row-major, ld = cols), 128-byte swizzle (box_cols == 128).
+sks_status make_tmap_2d_u8_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_cols,
+                                 uint32_t box_rows);
 // bfloat16 rows x cols (row-major, ld = cols), 128-byte swizzle (box_cols * 2 == 128).
 sks_status make_tmap_2d_bf16_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
                                    uint32_t box_cols, uint32_t box_rows);

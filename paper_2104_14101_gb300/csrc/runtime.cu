@@ -76,6 +76,24 @@ sks_status make_tmap_2d_bf16_sw128(CUtensorMap* map, const void* base, uint64_t 
   return SKS_OK;
 }
 
+sks_status make_tmap_2d_u8_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_cols,
+                                 uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(SKS_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  if (((uintptr_t)base & 127) != 0) return fail(SKS_ERR_INVALID_ARG, "8-bit operand must be 128-byte aligned");
+  if (cols % 16 != 0 || box_cols != 128) return fail(SKS_ERR_INVALID_ARG, "8-bit tensor map geometry");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
+  cuuint64_t strides[1] = {(cuuint64_t)cols};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(SKS_ERR_INVALID_ARG, "cuTensorMapEncodeTiled (8-bit) failed (code " + std::to_string((int)r) + ")");
+  return SKS_OK;
+}
+
 sks_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, size_t elem_bytes, uint64_t rows,
                         uint64_t cols, uint64_t ld, uint32_t box_cols, uint32_t box_rows) {
   static EncodeTiledFn fn = nullptr;

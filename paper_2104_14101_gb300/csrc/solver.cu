@@ -42,6 +42,13 @@ struct sks_sketch {
   float* tcpart = nullptr;
   size_t tcpart_elems = 0;
   bool tc_ready = false;
+  // 8-bit Gaussian sketch: e4m3 operand A^T, its (slice, column) scales, the
+  // column maxima scratch and ||A||_F^2
+  unsigned char* a8 = nullptr;
+  float* a8s = nullptr;
+  unsigned* a8max = nullptr;
+  double* frob2 = nullptr;
+  bool a8_ready = false;
   uint32_t* sj = nullptr;  // SJLT buckets for the gathering kernel (larger m)
   size_t sj_elems = 0;
   sks::DevStatus* st = nullptr;
@@ -201,6 +208,7 @@ struct SketchSizes {
   size_t b_elems = 0, y_elems = 0, g_elems = 0, split_elems = 0;
   size_t sj_elems = 0;  // SJLT buckets (counts, offsets, entries) of the gathering kernel
   size_t tc_elems = 0, tcpart_elems = 0;  // float32 Gaussian (tensor cores)
+  size_t a8_elems = 0, a8s_elems = 0;     // 8-bit Gaussian: d x Kp bytes, slices x d scales
 };
 
 SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s) {
@@ -209,10 +217,16 @@ SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max, int
   const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
   if (kind == SKS_SRHT) z.b_elems = (size_t)n_pad * p->d;
   z.y_elems = (size_t)m_max * p->d;
-  const bool dense_kind = kind == SKS_GAUSSIAN || kind == SKS_RADEMACHER;  // S drawn entry by entry
+  // S drawn entry by entry; the 8-bit kind keeps the bfloat16 operands too (the
+  // solver falls back to them when the noise estimate rules 8 bits out)
+  const bool dense_kind = kind == SKS_GAUSSIAN || kind == SKS_RADEMACHER || kind == SKS_GAUSSIAN_E4M3;
   if (dense_kind && p->dtype == SKS_F32) {
     z.tc_elems = (size_t)p->d * (size_t)tc_gauss_kp(p->n);
     z.tcpart_elems = tc_gauss_part_elems(p->n, (int)p->d, (int)std::min<int64_t>(m_max, 1 << 30));
+    if (kind == SKS_GAUSSIAN_E4M3) {
+      z.a8_elems = (size_t)p->d * (size_t)tc_gauss_kp(p->n);
+      z.a8s_elems = (size_t)tc_gauss_slices(p->n) * (size_t)p->d;
+    }
   } else if (dense_kind) {
     z.g_elems = (size_t)std::min<int64_t>((int64_t)m_max * std::max<int64_t>(p->n, 1), (int64_t)1 << 24);
     z.g_elems = std::max<size_t>(z.g_elems, (size_t)m_max * 64);
@@ -241,6 +255,10 @@ size_t sketch_ws_bytes(const sks_problem* p, sks_kind kind, int64_t m_max, int s
   c.take<char>(z.g_elems * esz);
   c.take<char>(z.split_elems * esz);
   c.take<uint32_t>(z.sj_elems);
+  c.take<unsigned char>(z.a8_elems);
+  c.take<float>(z.a8s_elems);
+  c.take<unsigned>(z.a8s_elems);
+  c.take<double>(1);
   return c.used + 256;
 }
 
@@ -273,6 +291,11 @@ sks_status sketch_init(sks_sketch* s, const sks_problem* p, sks_kind kind, int64
   s->tcpart_elems = z.tcpart_elems;
   s->sj = c.take<uint32_t>(z.sj_elems);
   s->sj_elems = z.sj_elems;
+  s->a8 = c.take<unsigned char>(z.a8_elems);
+  s->a8s = c.take<float>(z.a8s_elems);
+  s->a8max = c.take<unsigned>(z.a8s_elems);
+  s->frob2 = c.take<double>(1);
+  s->a8_ready = false;
   s->tc_ready = false;
   if (!c.ok()) return fail(SKS_ERR_WORKSPACE, "sketch workspace too small");
   if (z.b_elems == 0) s->B = nullptr;
@@ -288,6 +311,15 @@ sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
   if (s->kind == SKS_SRHT) {
     if (s->m == 0) SKS_TRY(srht_form<T>(stream, A, p.lda, p.n, d, (T*)s->B, d, s->seed));
     SKS_TRY(srht_gather<T, T>(stream, (const T*)s->B, d, d, s->n_pad, s->seed, (int)s->m, (int)new_m, Y, s->ldy, s->st));
+  } else if (s->kind == SKS_GAUSSIAN_E4M3) {
+    if (!s->f32) return fail(SKS_ERR_UNSUPPORTED, "the 8-bit Gaussian sketch needs a float32 A");
+    // e4m3(G) times e4m3(A / scale) on the tensor cores; the operand is made once per sketch
+    if (!s->a8_ready) {
+      SKS_TRY(tc_split8_t(stream, (const float*)A, p.lda, p.n, d, s->a8, s->a8s, s->a8max, s->frob2));
+      s->a8_ready = true;
+    }
+    SKS_TRY(tc_gauss_sketch(stream, nullptr, nullptr, p.n, d, s->seed, (int)s->m, (int)(new_m - s->m), s->tcpart,
+                            s->tcpart_elems, (float*)Y, s->ldy, s->st, false, s->a8, s->a8s));
   } else if ((s->kind == SKS_GAUSSIAN || s->kind == SKS_RADEMACHER) && s->f32) {
     // bf16(G) times the split A^T on the tensor cores; the split is made once per sketch
     if (!s->tc_ready) {
@@ -953,6 +985,24 @@ struct Engine {
     }
     m = std::min<int64_t>(o->m_init, m_max);
     t_sketch->start();
+    if (sk.kind == SKS_GAUSSIAN_E4M3) {
+      // 8 bits only when the rounding noise of A stays well under the
+      // regulariser: (2^-4)^2 / 3 ||A||_F^2 / d <= 0.1 nu^2 min lambda (the
+      // e4m3 rounding of each entry is up to 2^-4 relative, the noise spreads
+      // over the d directions); else the bfloat16 split serves the same G
+      SKS_TRY(tc_split8_t(stream, (const float*)prob->A, prob->lda, prob->n, d, sk.a8, sk.a8s, sk.a8max, sk.frob2));
+      sk.a8_ready = true;
+      double frob2 = 0.0;
+      std::vector<double> lam((size_t)d);
+      SKS_CUDA_TRY(cudaMemcpyAsync(&frob2, sk.frob2, sizeof(double), cudaMemcpyDeviceToHost, stream));
+      SKS_CUDA_TRY(cudaMemcpyAsync(lam.data(), prob->lambda_diag, (size_t)d * sizeof(double), cudaMemcpyDeviceToHost,
+                                   stream));
+      SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+      const double lam_min = *std::min_element(lam.begin(), lam.end());
+      const double noise = std::ldexp(1.0, -8) / 3.0 * frob2 / (double)d;
+      S.sketch_e4m3 = noise <= 0.1 * nu2 * lam_min ? 1 : 0;
+      if (!S.sketch_e4m3) sk.kind = SKS_GAUSSIAN;
+    }
     SKS_TRY(sketch_to(&sk, m, stream));
     t_sketch->stop();
     S.sketch_passes = 1;
@@ -1132,8 +1182,11 @@ sks_status check_opts(const sks_problem* prob, const sks_opts* o, const double* 
   if (!(o->rho > 0.0 && o->rho < 1.0)) return fail(SKS_ERR_INVALID_ARG, "rho must be in (0, 1)");
   if (o->m_init < 1) return fail(SKS_ERR_INVALID_ARG, "m_init must be >= 1");
   if (!(o->tol > 0.0)) return fail(SKS_ERR_INVALID_ARG, "tol must be > 0");
-  if (o->kind != SKS_SRHT && o->kind != SKS_GAUSSIAN && o->kind != SKS_SJLT && o->kind != SKS_RADEMACHER)
+  if (o->kind != SKS_SRHT && o->kind != SKS_GAUSSIAN && o->kind != SKS_SJLT && o->kind != SKS_RADEMACHER &&
+      o->kind != SKS_GAUSSIAN_E4M3)
     return fail(SKS_ERR_INVALID_ARG, "bad embedding kind");
+  if (o->kind == SKS_GAUSSIAN_E4M3 && prob->dtype != SKS_F32)
+    return fail(SKS_ERR_UNSUPPORTED, "the 8-bit Gaussian sketch needs a float32 A (mixed form)");
   if (o->sjlt_s < 1 || o->sjlt_s > kSjltMaxS) return fail(SKS_ERR_INVALID_ARG, "sjlt_s must be in [1, 16]");
   if (o->precision == SKS_PLAIN_F64 && prob->dtype != SKS_F64)
     return fail(SKS_ERR_INVALID_ARG, "the plain float64 form needs a float64 A");
@@ -1830,8 +1883,11 @@ extern "C" sks_status sks_sketch_create(sks_sketch** out, const sks_problem* p, 
   if (!out) return fail(SKS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   SKS_TRY(validate_problem(p));
-  if (kind != SKS_SRHT && kind != SKS_GAUSSIAN && kind != SKS_SJLT && kind != SKS_RADEMACHER)
+  if (kind != SKS_SRHT && kind != SKS_GAUSSIAN && kind != SKS_SJLT && kind != SKS_RADEMACHER &&
+      kind != SKS_GAUSSIAN_E4M3)
     return fail(SKS_ERR_INVALID_ARG, "bad kind");
+  if (kind == SKS_GAUSSIAN_E4M3 && p->dtype != SKS_F32)
+    return fail(SKS_ERR_UNSUPPORTED, "the 8-bit Gaussian sketch needs a float32 A");
   if (sjlt_s < 1 || sjlt_s > kSjltMaxS) return fail(SKS_ERR_INVALID_ARG, "sjlt_s must be in [1, 16]");
   const int64_t mm = resolve_m_max(p, kind, m_max);
   if (m_init < 1 || m_init > mm) return fail(SKS_ERR_INVALID_ARG, "m_init must be in [1, m_max]");

@@ -34,6 +34,7 @@
 // leave their loops, wait (bounded) for their own asynchronous work, and the
 // TMEM is freed before exit.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -73,6 +74,20 @@ SKS_DEV void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// kind::f8f6f4 instruction descriptor: e4m3 x e4m3 -> f32 (format code 0 for
+// both operands), both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+SKS_DEV void umma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -483,11 +498,17 @@ struct GaussArgs {
   int rade;                        // 1: Rademacher +-1 entries instead of Gaussian ones
   Key key;
   float* part;             // [ksplits][m_add][d]
+  const float* scale;      // 8-bit operands: [ksplits][d] column scales of A's slices
   DevStatus* st;
 };
 
+// E8: the 8-bit variant -- G rounded to e4m3, A^T an e4m3 operand (mAh) with
+// one power-of-two scale per column and K slice, kind::f8f6f4 MMAs (K = 32),
+// a stage holding 128 data rows (the same 128 bytes per operand row).
+template <bool E8>
 __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1)
     tc_gauss_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl, GaussArgs g) {
+  constexpr int KST = E8 ? 2 * GBK : GBK;  // data rows per stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t tfull[kGStages], gfull[kGStages], empty[kGStages], acc_full[2], acc_empty[2];
@@ -503,7 +524,7 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
   const int col0 = tn * GBN;
   const int kbeg = ks * g.kc;
   const int kend = min(g.Kp, kbeg + g.kc);
-  const int nk = (kend - kbeg) / GBK;
+  const int nk = (kend - kbeg) / KST;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -545,9 +566,14 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
           break;
         }
         unsigned char* st = smem + (size_t)s * kGStageBytes;
-        mbar_arrive_expect_tx(&tfull[s], 2 * kGTileA);
-        tma_load_2d(st + kGTileG, &mAh, &tfull[s], kbeg + kk * GBK, col0);
-        tma_load_2d(st + kGTileG + kGTileA, &mAl, &tfull[s], kbeg + kk * GBK, col0);
+        if constexpr (E8) {
+          mbar_arrive_expect_tx(&tfull[s], kGTileA);
+          tma_load_2d(st + kGTileG, &mAh, &tfull[s], kbeg + kk * KST, col0);
+        } else {
+          mbar_arrive_expect_tx(&tfull[s], 2 * kGTileA);
+          tma_load_2d(st + kGTileG, &mAh, &tfull[s], kbeg + kk * KST, col0);
+          tma_load_2d(st + kGTileG + kGTileA, &mAl, &tfull[s], kbeg + kk * KST, col0);
+        }
         issued = kk + 1;
       }
       const int first = issued > kGStages ? issued - kGStages : 0;
@@ -556,7 +582,7 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(GBM, GBN);
+      constexpr uint32_t idesc = E8 ? idesc_e4m3_f32(GBM, GBN) : idesc_bf16_f32(GBM, GBN);
       const int ngroups = (nk + kGDrain - 1) / kGDrain;
       int committed = -1;
       for (int grp = 0; grp < ngroups && !abort_flag; ++grp) {
@@ -582,10 +608,15 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
           const uint64_t hd = smem_desc_sw128(st + kGTileG);
           const uint64_t ld = smem_desc_sw128(st + kGTileG + kGTileA);
           const bool first = kk == grp * kGDrain;
+          // four K steps of 32 bytes per 128-byte operand row (16 bf16 or 32 e4m3 values)
 #pragma unroll
-          for (int k = 0; k < GBK / 16; ++k) {
-            umma_bf16(acc_t, gd + (uint64_t)(k * 2), hd + (uint64_t)(k * 2), idesc, (first && k == 0) ? 0u : 1u);
-            umma_bf16(acc_t, gd + (uint64_t)(k * 2), ld + (uint64_t)(k * 2), idesc, 1u);
+          for (int k = 0; k < 4; ++k) {
+            if constexpr (E8) {
+              umma_e4m3(acc_t, gd + (uint64_t)(k * 2), hd + (uint64_t)(k * 2), idesc, (first && k == 0) ? 0u : 1u);
+            } else {
+              umma_bf16(acc_t, gd + (uint64_t)(k * 2), hd + (uint64_t)(k * 2), idesc, (first && k == 0) ? 0u : 1u);
+              umma_bf16(acc_t, gd + (uint64_t)(k * 2), ld + (uint64_t)(k * 2), idesc, 1u);
+            }
           }
           umma_commit_multicast(&empty[s], (uint16_t)((1u << kGCluster) - 1u));  // stage free in every CTA
         }
@@ -646,11 +677,12 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
         break;
       }
       unsigned char* gt = smem + (size_t)s * kGStageBytes;
-      const long long i0 = (long long)kbeg + (long long)kk * GBK;
+      const long long i0 = (long long)kbeg + (long long)kk * KST;
       // item = (quad of sketch rows, pair of adjacent data rows): a warp covers
-      // the 64 data rows of one quad and stores whole 128-byte tile rows
-      for (int it = gtid; it < nq * (GBK / 2); it += kGGenWarps * 32) {
-        const int qi = it >> 5, kc = (it & 31) * 2;
+      // the data rows of one quad (two quads for 8-bit values) and stores
+      // whole 128-byte tile rows
+      for (int it = gtid; it < nq * (KST / 2); it += kGGenWarps * 32) {
+        const int qi = E8 ? it >> 6 : it >> 5, kc = E8 ? (it & 63) * 2 : (it & 31) * 2;
         const int Q = q0 + qi;
         const long long i = i0 + kc;
         float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
@@ -667,9 +699,17 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
           const int rl = R - row_base;
           if (rl < rl_lo || rl >= rl_lo + kRowsPer) continue;
           const bool live = R < row_end;
-          const uint32_t off = (uint32_t)rl * 128u + ((((uint32_t)kc >> 3) ^ ((uint32_t)rl & 7u)) << 4) +
-                               (((uint32_t)kc & 7u) << 1);
-          *(__nv_bfloat162*)(gt + off) = __floats2bfloat162_rn(live ? v0[t] : 0.f, live ? v1[t] : 0.f);
+          if constexpr (E8) {
+            // 16 e4m3 values per 16-byte chunk of the swizzled row (data row kc in byte kc)
+            const uint32_t off = (uint32_t)rl * 128u + ((((uint32_t)kc >> 4) ^ ((uint32_t)rl & 7u)) << 4) +
+                                 ((uint32_t)kc & 15u);
+            *(__nv_fp8x2_storage_t*)(gt + off) =
+                __nv_cvt_float2_to_fp8x2(make_float2(live ? v0[t] : 0.f, live ? v1[t] : 0.f), __NV_SATFINITE, __NV_E4M3);
+          } else {
+            const uint32_t off = (uint32_t)rl * 128u + ((((uint32_t)kc >> 3) ^ ((uint32_t)rl & 7u)) << 4) +
+                                 (((uint32_t)kc & 7u) << 1);
+            *(__nv_bfloat162*)(gt + off) = __floats2bfloat162_rn(live ? v0[t] : 0.f, live ? v1[t] : 0.f);
+          }
         }
       }
       fence_proxy_async();  // generic-proxy writes visible to the async proxy (MMA, bulk copies)
@@ -707,9 +747,10 @@ __global__ void __cluster_dims__(kGCluster, 1, 1) __launch_bounds__(kGThreads, 1
       if (r < g.m_add) {
         float* dst = g.part + ((size_t)ks * g.m_add + r) * g.d;
         const int c0 = col0 + cb * 64;
+        // 8-bit operands: the slice's column scales (powers of two) bring A back
 #pragma unroll
         for (int j = 0; j < 64; ++j)
-          if (c0 + j < g.d) dst[c0 + j] = accr[j];
+          if (c0 + j < g.d) dst[c0 + j] = E8 ? accr[j] * g.scale[(size_t)ks * g.d + c0 + j] : accr[j];
       }
     }
   }
@@ -755,6 +796,68 @@ __global__ void split_t_kernel(const float* __restrict__ A, long long lda, long 
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     Hh[(size_t)c * Kp + i] = h;
     Hl[(size_t)c * Kp + i] = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
+  }
+}
+
+// 8-bit operand: per (K slice of kc data rows, column c) the largest |a|
+// (float bits) and, over everything, sum a^2 (for the noise estimate).
+__global__ void e4m3_colmax_kernel(const float* __restrict__ A, long long lda, long long n, int d, long long rows_per,
+                                   int kc, unsigned* __restrict__ smax, double* __restrict__ frob2) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  const long long r0 = (long long)blockIdx.y * rows_per;
+  const long long r1 = min(n, r0 + rows_per);
+  float m = 0.f;
+  double s2 = 0.0;
+  long long slice = r0 / kc;
+  for (long long i = r0; i < r1; ++i) {
+    if (i / kc != slice) {
+      atomicMax(&smax[(size_t)slice * d + c], __float_as_uint(m));
+      m = 0.f;
+      slice = i / kc;
+    }
+    const float v = A[i * lda + c];
+    m = fmaxf(m, fabsf(v));
+    s2 += (double)v * (double)v;
+  }
+  if (r0 < r1) atomicMax(&smax[(size_t)slice * d + c], __float_as_uint(m));
+  atomicAdd(frob2, s2);
+}
+
+// scale = 2^e, e the least integer with max <= 448 2^e: with max = f 2^E
+// (f in [0.5, 1)) and 448 = 0.875 2^9, e = E - 9 (+1 when f > 0.875); 1 for 0.
+__global__ void e4m3_scale_kernel(int count, const unsigned* __restrict__ smax, float* __restrict__ scale) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const float mx = __uint_as_float(smax[e]);
+  if (!(mx > 0.f)) {
+    scale[e] = 1.f;
+    return;
+  }
+  int E;
+  const float f = frexpf(mx, &E);
+  scale[e] = ldexpf(1.f, E - 9 + (f > 0.875f ? 1 : 0));
+}
+
+// The e4m3 operand A8t[c][i] = e4m3(a_ic / scale[i / kc][c]) (exact division
+// by a power of two; round to nearest even, finite saturation), zero for
+// i >= n up to Kp; 32 x 32 shared-memory tiles for the transpose.
+__global__ void split8_t_kernel(const float* __restrict__ A, long long lda, long long n, int d, int Kp, int kc,
+                                const float* __restrict__ scale, unsigned char* __restrict__ A8t) {
+  __shared__ float t[32][33];
+  const long long i0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const long long i = i0 + j;
+    const int c = c0 + threadIdx.x;
+    t[j][threadIdx.x] = (i < n && c < d) ? A[i * lda + c] / scale[(size_t)(i / kc) * d + c] : 0.f;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = c0 + j;
+    const long long i = i0 + threadIdx.x;
+    if (c >= d || i >= Kp) continue;
+    A8t[(size_t)c * Kp + i] = (unsigned char)__nv_cvt_float_to_fp8(t[threadIdx.x][j], __NV_SATFINITE, __NV_E4M3);
   }
 }
 
@@ -837,7 +940,32 @@ sks_status tc_gram(cudaStream_t stream, int M, int N, int Kp, const __nv_bfloat1
 
 namespace sks {
 
-int tc_gauss_kp(long long n) { return (int)((std::max<long long>(n, 1) + GBK - 1) / GBK * GBK); }
+// padded to whole 128-row stages of the 8-bit operand (two 64-row bf16 stages)
+int tc_gauss_kp(long long n) { return (int)((std::max<long long>(n, 1) + 2 * GBK - 1) / (2 * GBK) * (2 * GBK)); }
+
+int tc_gauss_slices(long long n) { return (tc_gauss_kp(n) + kGaussSlice - 1) / kGaussSlice; }
+
+sks_status tc_split8_t(cudaStream_t stream, const float* A, long long lda, long long n, int d, unsigned char* A8t,
+                       float* scale, unsigned* smax, double* frob2) {
+  const int Kp = tc_gauss_kp(n);
+  const int ks = tc_gauss_slices(n);
+  SKS_CUDA_TRY(cudaMemsetAsync(smax, 0, (size_t)ks * d * sizeof(unsigned), stream));
+  SKS_CUDA_TRY(cudaMemsetAsync(frob2, 0, sizeof(double), stream));
+  if (n > 0) {
+    const long long chunks = std::min<long long>((n + 1023) / 1024, 1024);
+    const long long per = (n + chunks - 1) / chunks;
+    e4m3_colmax_kernel<<<dim3((unsigned)((d + 127) / 128), (unsigned)chunks), 128, 0, stream>>>(A, lda, n, d, per,
+                                                                                               kGaussSlice, smax, frob2);
+    note_launch();
+  }
+  e4m3_scale_kernel<<<(unsigned)((ks * d + 255) / 256), 256, 0, stream>>>(ks * d, smax, scale);
+  note_launch();
+  split8_t_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)((d + 31) / 32)), dim3(32, 8), 0, stream>>>(
+      A, lda, n, d, Kp, kGaussSlice, scale, A8t);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
 
 size_t tc_gauss_part_elems(long long n, int d, int max_rows) {
   const int Kp = tc_gauss_kp(n);
@@ -858,14 +986,23 @@ sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long l
 
 sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, long long n, int d,
                            uint64_t seed, int m_off, int m_add, float* part, size_t part_elems, float* Y,
-                           long long ldy, DevStatus* st, bool rademacher) {
+                           long long ldy, DevStatus* st, bool rademacher, const unsigned char* A8t,
+                           const float* scale) {
   if (m_add <= 0) return SKS_OK;
   const int Kp = tc_gauss_kp(n);
+  const bool e8 = A8t != nullptr;
   CUtensorMap mh, ml;
-  SKS_TRY(make_tmap_2d_bf16_sw128(&mh, Hh, (uint64_t)d, (uint64_t)Kp, GBK, GBN));
-  SKS_TRY(make_tmap_2d_bf16_sw128(&ml, Hl, (uint64_t)d, (uint64_t)Kp, GBK, GBN));
+  if (e8) {
+    if (rademacher) return fail(SKS_ERR_UNSUPPORTED, "the 8-bit sketch is Gaussian only");
+    SKS_TRY(make_tmap_2d_u8_sw128(&mh, A8t, (uint64_t)d, (uint64_t)Kp, 2 * GBK, GBN));
+    ml = mh;
+  } else {
+    SKS_TRY(make_tmap_2d_bf16_sw128(&mh, Hh, (uint64_t)d, (uint64_t)Kp, GBK, GBN));
+    SKS_TRY(make_tmap_2d_bf16_sw128(&ml, Hl, (uint64_t)d, (uint64_t)Kp, GBK, GBN));
+  }
   const size_t smem = (size_t)kGStages * kGStageBytes + 1024;
-  SKS_CUDA_TRY(cudaFuncSetAttribute(tc_gauss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = e8 ? tc_gauss_kernel<true> : tc_gauss_kernel<false>;
+  SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int kc = kGaussSlice;
   const int ksplits = (Kp + kc - 1) / kc;
   for (int r0 = 0; r0 < m_add; r0 += kGaussRowChunk) {
@@ -884,10 +1021,11 @@ sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const _
     g.key = make_key(seed);
     g.rade = rademacher ? 1 : 0;
     g.part = part;
+    g.scale = scale;
     g.st = st;
     const long long blocks = (long long)g.tiles_m * g.tiles_n * ksplits;
     if (blocks > 0x7fffffffll) return fail(SKS_ERR_UNSUPPORTED, "Gaussian sketch grid too large");
-    tc_gauss_kernel<<<(unsigned)blocks, kGThreads, smem, stream>>>(mh, ml, g);
+    kern<<<(unsigned)blocks, kGThreads, smem, stream>>>(mh, ml, g);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
     const long long tot = (long long)rows * d;

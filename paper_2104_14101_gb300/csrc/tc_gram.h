@@ -43,8 +43,19 @@ sks_status tc_split_t(cudaStream_t stream, const float* A, long long lda, long l
 // Box-Muller entry of sketch row r and data row i (float32, rounded to
 // bfloat16), generated inside the kernel; unscaled (S A = Y / sqrt(m)).
 // rademacher: the +-1 entries of the Rademacher embedding instead of G.
+// With A8t (d x Kp e4m3 bytes) and scale ([slices][d]): the 8-bit sketch,
+// e4m3(G) times A quantised to e4m3 against one power-of-two scale per column
+// and K slice of 16384 data rows (tc_split8_t), each slice scaled back.
 sks_status tc_gauss_sketch(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, long long n, int d,
                            uint64_t seed, int m_off, int m_add, float* part, size_t part_elems, float* Y,
-                           long long ldy, DevStatus* st, bool rademacher = false);
+                           long long ldy, DevStatus* st, bool rademacher = false,
+                           const unsigned char* A8t = nullptr, const float* scale = nullptr);
+// K slices of the tensor-core sketch (slices of 16384 data rows).
+int tc_gauss_slices(long long n);
+// The 8-bit operand of the sketch: per (slice, column) scales from the
+// column maxima (smax: slices x d scratch words), A8t = e4m3(A / scale)^T
+// (d x Kp bytes), and frob2 = ||A||_F^2 (float64, device).
+sks_status tc_split8_t(cudaStream_t stream, const float* A, long long lda, long long n, int d, unsigned char* A8t,
+                       float* scale, unsigned* smax, double* frob2);
 
 }  // namespace sks

@@ -256,6 +256,59 @@ def test_rademacher_tc_sketch_matches_plain_definition(n, d, m):
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("n,d,m", [(3000, 64, 96), (20000, 300, 200), (40000, 520, 257)])
+def test_e4m3_tc_sketch_matches_definition(n, d, m):
+    # the 8-bit Gaussian sketch: e4m3(G) times A quantised to e4m3 against one
+    # power-of-two scale per column and slice of 16384 rows, each slice scaled
+    # back; n = 20000 / 40000 span two / three slices with their own scales
+    from oracle import mixed as MX
+    from oracle import rng as R
+    rng = np.random.default_rng(n + d + 7)
+    A = (rng.standard_normal((n, d)) * rng.uniform(0.1, 10, size=(1, d))).astype(np.float32)
+    A[n // 2:] *= 30.0  # slices with different scales
+    sk = api().Sketch(dev(A.astype(np.float64), torch.float32), 0.1, dev(np.ones(d)), kind="gaussian-e4m3", m=m,
+                      seed=17)
+    got = host(sk.matrix()) * math.sqrt(m)
+    G32 = R.gaussian_block(n, m, 17).astype(np.float32)
+    Gor = MX.e4m3_round(G32)
+    # unit columns make every scaled entry 256 = 2^8 against a scale 2^-8: exact
+    Ggpu = gpu_sketch_entries(n, m, 17, kind="gaussian-e4m3")
+    Ggpu = MX.e4m3_round(Ggpu.astype(np.float32))
+    slack = MX.e4m3_midpoint_slack(G32, ulps=4)
+    assert np.array_equal(Ggpu[slack == 0], Gor[slack == 0])
+    assert np.all(np.abs(Ggpu - Gor) <= slack)
+    sc = MX.e4m3_scales(A)
+    ref = np.zeros((m, d))
+    absref = np.zeros((m, d))
+    for k in range(sc.shape[0]):
+        blk = slice(k * 16384, (k + 1) * 16384)
+        A8 = MX.e4m3_round((A[blk].astype(np.float64) / sc[k][None, :]).astype(np.float32)) * sc[k][None, :]
+        ref += Ggpu[:, blk] @ A8
+        absref += np.abs(Ggpu[:, blk]) @ np.abs(A8)
+    bound = 2.0 ** -16 * absref + 2.0 ** -23 * np.abs(ref)  # float32 accumulation; the products are exact
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / (bound + 1e-300)))
+    # and the oracle's own definition (its e4m3 entries), up to the midpoint entries
+    ref_or = MX.gaussian_sketch_e4m3(A, m, 17)
+    amb = slack @ np.abs(A.astype(np.float64))
+    assert np.all(np.abs(got - ref_or) <= bound + 1.01 * amb)
+
+
+@pytest.mark.parametrize("nu,expect_e4m3", [(3e-2, 1), (1e-4, 0)])
+def test_e4m3_sketch_gate_and_mixed_solve(nu, expect_e4m3):
+    # the adaptive solver takes 8 bits only when 2^-8/3 ||A||_F^2 / d <= 0.1 nu^2 min lambda
+    # (C4's spectrum and Lambda; at nu = 1e-4 the estimate rules 8 bits out and the
+    # bfloat16 split serves instead); either way the mixed form reaches 1e-8
+    p = synthetic.make_problem("C4", 5, n=8192, d=256, k=1, nu=nu, dtype="f32")
+    b = p.b[:, 0] if p.b.ndim == 2 else p.b
+    xs = O.direct_solve(p.A, b, p.nu, p.lam)
+    x, st, _ = api().adaptive_pcg(dev(p.A, torch.float32), dev(b), p.nu, dev(p.lam), kind="gaussian-e4m3", tol=1e-8,
+                                  precision="mixed", seed=3)
+    assert st["sketch_e4m3"] == expect_e4m3
+    assert O.rel_err_H(p.A, p.nu, p.lam, host(x), xs) <= 1e-8
+    noise = 2.0 ** -8 / 3 * np.sum(p.A.astype(np.float64) ** 2) / p.d
+    assert (noise <= 0.1 * p.nu ** 2 * np.min(p.lam)) == bool(expect_e4m3)
+
+
 def test_gaussian_tc_sketch_nested_growth():
     # m = 1, 2, 3, 6, 13: new rows start at offsets that are not multiples of
     # the four rows one Philox call gives

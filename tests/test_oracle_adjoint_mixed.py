@@ -10,6 +10,7 @@ import torch
 import synthetic
 from oracle import adjoint as ADJ
 from oracle import mixed as MX
+from oracle import rng as R
 from oracle import solvers as S
 
 
@@ -151,3 +152,43 @@ def test_bf16_midpoint_slack():
     y = (x + np.spacing(np.abs(x)) * rng.integers(-2, 3, size=x.shape)).astype(np.float32)
     same = MX.bf16_round(x) == MX.bf16_round(y)
     assert np.all(same | (sl > 0))
+
+
+def test_e4m3_round_matches_torch_float8():
+    # the e4m3 rounding written from the format definition against torch's
+    # float8_e4m3fn conversion (round to nearest even; finite saturation is
+    # applied before the cast, torch maps out-of-range values to NaN)
+    rng = np.random.default_rng(8)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.uniform(-4, 2.6, size=20000),
+                        [0.0, 2 ** -9, 2 ** -10, 3 * 2 ** -10, 2 ** -6, 448.0, -448.0, 1.0625, 1.1875, 0.009]])
+    x = x.astype(np.float32)
+    xs = np.clip(x, -448.0, 448.0).astype(np.float32)
+    ref = torch.from_numpy(xs).to(torch.float8_e4m3fn).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(MX.e4m3_round(x), ref)
+    # saturation, and exactly representable values stay put
+    assert MX.e4m3_round(np.float32(1000.0)) == 448.0
+    for v in (1.0, 1.125, 240.0, 2.0 ** -6, 7 * 2.0 ** -9):
+        assert MX.e4m3_round(np.float32(v)) == v
+
+
+def test_gaussian_sketch_e4m3_definition():
+    # (a) columns of powers of two times small integers that e4m3 holds after
+    # scaling: the sketch is e4m3(G) A exactly; (b) two slices: each slice has
+    # its own column scales and their products add; (c) nested rows
+    rng = np.random.default_rng(12)
+    A = (rng.integers(-7, 8, size=(300, 5)) * np.array([1.0, 2.0 ** 10, 2.0 ** -10, 4.0, 0.5])).astype(np.float32)
+    G8 = MX.e4m3_round(R.gaussian_block(300, 6, 3).astype(np.float32))
+    assert np.allclose(MX.gaussian_sketch_e4m3(A, 6, 3), G8 @ A.astype(np.float64), rtol=1e-14, atol=0)
+    A = rng.standard_normal((700, 4)).astype(np.float32)
+    A[400:] *= 1000.0
+    sc = MX.e4m3_scales(A, slice_rows=256)
+    assert sc.shape == (3, 4) and np.all(sc[2] > 100 * sc[0])
+    assert np.all(np.max(np.abs(A[:256]), axis=0) / sc[0] <= 448.0)
+    assert np.all(np.max(np.abs(A[:256]), axis=0) / sc[0] > 224.0)  # the least such power of two
+    assert np.array_equal(sc[0], np.exp2(np.ceil(np.log2(np.max(np.abs(A[:256]).astype(np.float64), axis=0) / 448))))
+    Y = MX.gaussian_sketch_e4m3(A, 9, 5, slice_rows=256)
+    G8 = MX.e4m3_round(R.gaussian_block(700, 9, 5).astype(np.float32))
+    # within e4m3 rounding of A (relative 2^-4 of each scaled entry)
+    bound = (np.abs(G8) @ np.abs(A.astype(np.float64))) * 2.0 ** -4
+    assert np.all(np.abs(Y - G8 @ A.astype(np.float64)) <= bound)
+    assert np.array_equal(MX.gaussian_sketch_e4m3(A, 9, 5, row0=4, slice_rows=256), Y[4:])

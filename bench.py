@@ -104,6 +104,12 @@ WORKLOADS = {
                            tol=1e-8, precision="mixed",
                            desc="paper-scale replay: n=2^19, d=14000, sigma_j=0.995^j, Lambda=I, "
                                 "nu in {1e-1, 1e-2, 1e-3, 1e-4}"),
+    # the 8-bit Gaussian sketch option at C4's size (one right-hand side; the noise-estimate gate passes there)
+    "C4-e4m3": dict(config="C4", method="pcg", kind="gaussian-e4m3", m_init=1, m_max=0, tol=1e-8, precision="mixed",
+                    desc="mixed adaptive PCG with the 8-bit (e4m3, per-tile scales) Gaussian sketch: n=2^18, d=1024, "
+                         "sigma_j=(1+j)^-1/2, nu=1e-2, Lambda=1+U, one right-hand side, tol 1e-8"),
+    "C4-e4m3-profile": dict(config="C4", n=1 << 17, method="pcg", kind="gaussian-e4m3", m_init=1, m_max=0, tol=1e-8,
+                            precision="mixed", desc="C4-e4m3 at n=2^17 (profiling size)"),
     "C1": dict(config="C1", method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-10, precision="plain",
                desc="adaptive PCG, Gaussian, float64: n=4096, d=256, sigma_j=0.95^j, nu=1e-2, m_init=1, tol 1e-10"),
 }
@@ -548,7 +554,9 @@ def run_ours(args, wl, world, rank, local):
         # float32 A-pass: 1 flop per byte, HBM-bound
         roofline = {
             "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": gbs / peaks["hbm_gbs"], "traffic": th, "kernel": "apass_kernel<float,float>",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": th,
+            "kernel": "A-pass phase of solve_loop_kernel<float,float> (the fused loop; device clock of the phase, "
+                      "slowest CTA)",
             "launches": ap_n, "avg_launch_ms": ap_avg_ms, "bytes_per_launch": bytes_per_pass,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
         }
@@ -559,7 +567,8 @@ def run_ours(args, wl, world, rank, local):
         roofline = {
             "bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
             "frac": achieved_tflops / fp64_peak_tflops, "traffic": th,
-            "kernel": "apass_kernel<double,double>", "launches": ap_n, "avg_launch_ms": ap_avg_ms,
+            "kernel": "A-pass phase of solve_loop_kernel<double,double> (device clock)", "launches": ap_n,
+            "avg_launch_ms": ap_avg_ms,
             "bytes_per_launch": bytes_per_pass, "hbm_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
             "hbm_frac": gbs / peaks["hbm_gbs"],
             "peak_source": "float64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2 flop) at the sampled "
@@ -639,14 +648,23 @@ def run_ours(args, wl, world, rank, local):
         "clocks": clk,
         "solve_stats": {k: st0[k] for k in ("iters", "rejections", "final_m", "a_passes", "factorizations",
                                             "sketch_passes", "outer_iters", "ms_sketch", "ms_factor", "ms_iter",
-                                            "est_rel_err")},
+                                            "est_rel_err", "sketch_e4m3")},
     }
     if compare:
         line["compare"] = compare
-    try:  # the largest phase of the SJLT workloads, beside the A-pass roofline
+    try:
+        # the roofline object describes the phase that takes the larger share of the step: the SJLT
+        # re-sketches (every pass reads A) or the passes over A of the iteration; the other goes beside it
         rs = sketch_phase_roofline(wl["kind"], st0, n, d, A.element_size(), peaks["hbm_gbs"])
         if rs:
-            line["roofline_sketch_phase"] = rs
+            ap_step_ms = ap_ms / max(1, len(stats))
+            if rs["ms"] > ap_step_ms:
+                line["roofline"] = dict(rs, kernel="SJLT sketch phase (sjlt_reg_kernel for m <= 32, "
+                                                   "sjlt_scatter_kernel for m >= 64): CUDA events around each pass",
+                                        share_of_step=rs["ms"] / ms)
+                line["roofline_apass"] = dict(roofline, share_of_step=ap_step_ms / ms)
+            else:
+                line["roofline_sketch_phase"] = rs
     except Exception:  # an extra figure must never cost the line
         pass
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

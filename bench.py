@@ -220,12 +220,19 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def oracle_kind(kind):
+    """The oracle's embedding for a workload's kind: the 8-bit Gaussian sketch is
+    the GPU's rendering of the same Gaussian draw, so the oracle (float64) runs
+    the Gaussian embedding for it."""
+    return "gaussian" if kind == "gaussian-e4m3" else kind
+
+
 def oracle_solve(wl, A, b, nu, lam):
     """The CPU oracle's adaptive solve, as it stands (test infrastructure); for
     a dual workload the oracle solves eq. (2) and maps back to x."""
     from oracle import solvers as O
     fn = O.adaptive_pcg if wl["method"] == "pcg" else O.adaptive_ihs
-    kw = dict(kind=wl["kind"], seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"],
+    kw = dict(kind=oracle_kind(wl["kind"]), seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"],
               sjlt_s=wl.get("sjlt_s", 1))
     if wl.get("dual"):
         D, bd, nud, lamd = O.dual_problem(A, b, nu, lam)
@@ -301,11 +308,12 @@ def cpu_composed(wl, A, b, nu, lam, counts, budget_s=40.0):
     mf = counts["final_m"]
     probe = min(n, 1 << 13)
     t0 = time.perf_counter()
-    SK.sketch(wl["kind"], A[:probe], min(mf, probe if wl["kind"] == "srht" else mf), 0, wl.get("sjlt_s", 1))
+    SK.sketch(oracle_kind(wl["kind"]), A[:probe], min(mf, probe if wl["kind"] == "srht" else mf), 0,
+              wl.get("sjlt_s", 1))
     t_probe = time.perf_counter() - t0
     if t_probe * n / probe <= budget_s:
         t0 = time.perf_counter()
-        SA = SK.sketch(wl["kind"], A, mf, 0, wl.get("sjlt_s", 1))
+        SA = SK.sketch(oracle_kind(wl["kind"]), A, mf, 0, wl.get("sjlt_s", 1))
         t_sketch = time.perf_counter() - t0
         sketch_how = "one full-size sketch at m = %d" % mf
     else:
@@ -349,7 +357,7 @@ def run_reference_batched(args, wl, world, rank):
     k = min(wl["ref_problems"], len(host))
     nd_all = sum(A.shape[0] * A.shape[1] for A, _, _, _ in host)
     nd_s = sum(A.shape[0] * A.shape[1] for A, _, _, _ in host[:k])
-    kw = dict(kind=wl["kind"], seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"])
+    kw = dict(kind=oracle_kind(wl["kind"]), seed=0, m_init=wl["m_init"], m_max=(wl["m_max"] or None), tol=wl["tol"])
     for _ in range(args.warmup):  # untimed warm-up on the smallest problem
         A, b, nu, lam = min(host, key=lambda t: t[0].size)
         O.adaptive_pcg(A, b, nu, lam, **kw)

@@ -253,6 +253,15 @@ void sks_sketch_destroy(sks_sketch* s);
 sks_status sks_precond_workspace_size(const sks_problem* p, int64_t m_max, size_t* bytes);
 sks_status sks_precond_build(sks_precond** out, const sks_sketch* s, const sks_problem* p,
                              void* ws, size_t ws_bytes, void* stream);
+/* sks_precond_build_ex: sks_precond_build with the factorisation of the given
+ * form.  SKS_PLAIN_F64: as sks_precond_build.  SKS_MIXED_REFINED (float32 A
+ * only, else SKS_ERR_INVALID_ARG): the factorisation the mixed solvers use --
+ * the Gram matrix on the tensor cores, the Cholesky factorisation in
+ * double-float arithmetic (pairs of float32, ~2^-47 per operation, on the
+ * float32 pipe), and the inverse factor merged in float32 (m >= d: the apply
+ * X^T X stays positive definite) or in double-float (m < d, Woodbury). */
+sks_status sks_precond_build_ex(sks_precond** out, const sks_sketch* s, const sks_problem* p,
+                                sks_precision precision, void* ws, size_t ws_bytes, void* stream);
 sks_status sks_precond_apply(const sks_precond* P, const double* z, double* v, int64_t k, void* stream);
 void sks_precond_destroy(sks_precond* P);
 

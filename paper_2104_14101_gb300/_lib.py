@@ -86,6 +86,8 @@ _SIGS = {
     "sks_sketch_destroy": (None, [C.c_void_p]),
     "sks_precond_workspace_size": (C.c_int, [P(Problem), C.c_int64, P(C.c_size_t)]),
     "sks_precond_build": (C.c_int, [P(C.c_void_p), C.c_void_p, P(Problem), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sks_precond_build_ex": (C.c_int, [P(C.c_void_p), C.c_void_p, P(Problem), C.c_int, C.c_void_p, C.c_size_t,
+                                       C.c_void_p]),
     "sks_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "sks_precond_destroy": (None, [C.c_void_p]),
     "sks_solve_workspace_size": (C.c_int, [P(Problem), P(Opts), P(C.c_size_t)]),

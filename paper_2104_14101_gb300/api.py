@@ -125,7 +125,7 @@ class Sketch:
 class Preconditioner:
     """H_S = (SA)^T SA + nu^2 Lambda factored on the device (Section 4.1.1)."""
 
-    def __init__(self, sketch, m_max=None):
+    def __init__(self, sketch, m_max=None, precision="plain"):
         self._lib = L.load()
         self.sketch = sketch
         p = sketch.problem
@@ -137,8 +137,9 @@ class Preconditioner:
         L.check(self._lib.sks_precond_workspace_size(C.byref(p), max(mm, self._sketch_mmax()), C.byref(nb2)))
         self.ws = _workspace(max(nb.value, nb2.value), sketch.device)
         h = C.c_void_p()
-        L.check(self._lib.sks_precond_build(C.byref(h), sketch.handle, C.byref(p), _ptr(self.ws), self.ws.numel(),
-                                            _stream(sketch.device)))
+        prec = L.PLAIN_F64 if precision == "plain" else L.MIXED_REFINED
+        L.check(self._lib.sks_precond_build_ex(C.byref(h), sketch.handle, C.byref(p), prec, _ptr(self.ws),
+                                               self.ws.numel(), _stream(sketch.device)))
         self.handle = h
 
     def _sketch_mmax(self):

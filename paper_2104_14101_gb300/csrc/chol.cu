@@ -1,0 +1,639 @@
+// chol.cu -- the factorisation of the sketched preconditioner (Section 4.1.1)
+// in double-float arithmetic: H = L L^T of H_S (m >= d) or of the Woodbury
+// system W_S (m < d), and the inverse factor X = L^{-1} that the apply uses.
+//
+// Every value is the unevaluated sum hi + lo of two float32 numbers (about
+// 48 significant bits) and every operation runs on the float32 pipe: on this
+// part float64 arithmetic -- format conversions included -- runs at ~1/64 of
+// the float32 rate, so the matrix is split into two float planes once (with
+// integer operations) and stays there until the inverse factor is written.
+//
+// Per block column k (64 columns; one launch each):
+//   chol_panel_df32_kernel  every CTA factors the 64 x 64 diagonal block and
+//                           inverts its factor (replicated, so that no launch
+//                           waits on another); CTA 0 stores L_kk^{-1}, the
+//                           others form their rows of the panel
+//                           L_ik = H_ik L_kk^{-T} = H_ik (L_kk^{-1})^T;
+//   syrk_df32_planes_kernel the trailing update H_ij -= L_ik L_jk^T (lower tiles).
+// Then X from the diagonal-block inverses by recursive merging,
+//   inv([A 0; B C]) = [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}],
+// in float32 (Cholesky form: the apply X^T X is positive definite for any
+// nonsingular X) or in double-float (Woodbury form, whose apply subtracts two
+// terms of size ~1/nu^2).
+//
+// Double-float operations: TwoSum (Knuth), FastTwoSum (Dekker) and the
+// FMA-based TwoProd (Ogita, Rump and Oishi, SISC 2005); sums of products keep
+// the low part unnormalised until the end, which bounds the error of a dot
+// product of length K by ~K * 2^-47 times the sum of the magnitudes.
+#include <algorithm>
+
+#include "dense.h"
+
+namespace sks {
+
+namespace {
+
+constexpr int NB = 64;       // block size of the factorisation
+constexpr int kCT = 256;     // threads of the factor and update kernels
+
+struct F2 {
+  float h, l;
+};
+
+SKS_DEV F2 f2_fast_two_sum(float a, float b) {  // exact when |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+SKS_DEV F2 f2_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+SKS_DEV F2 f2_mul(F2 x, F2 y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return f2_fast_two_sum(p, e);
+}
+// (h, l) += s * x * y with s = +1 or -1; the low part is accumulated without
+// renormalising (TwoSum of the high parts, the product's TwoProd error and
+// cross terms added to the low part).
+template <bool SUB>
+SKS_DEV void f2_acc(float& h, float& l, F2 x, F2 y) {
+  const float p0 = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p0);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  const float p = SUB ? -p0 : p0;
+  const float s = __fadd_rn(h, p);
+  const float bb = __fsub_rn(s, h);
+  const float t = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  h = s;
+  l = SUB ? __fadd_rn(l, __fsub_rn(t, e)) : __fadd_rn(l, __fadd_rn(t, e));
+}
+// 1 / sqrt(p), p > 0: float32 seed (relative error <= 2^-22) and one Newton
+// step r + r (1 - p r^2) / 2 in double-float (error ~1.5 * 2^-44).
+SKS_DEV F2 f2_rsqrt(F2 p) {
+  const float r0 = rsqrtf(p.h);
+  const F2 q = f2_mul(f2_mul(p, {r0, 0.f}), {r0, 0.f});
+  const float t = __fsub_rn(__fsub_rn(1.f, q.h), q.l);  // 1 - q.h is exact (Sterbenz)
+  return f2_fast_two_sum(r0, __fmul_rn(__fmul_rn(r0, t), 0.5f));
+}
+
+// float64 -> hi + lo with integer operations only: hi keeps the top 24
+// significant bits, lo the next 24 (the last 5 bits are dropped: relative
+// error <= 2^-47).  Where lo would fall below float32's normal range
+// (|x| < ~2^-100) only hi is kept, and values below that range become 0, so
+// the caller scales the matrix by a power of two first; non-finite values
+// stay non-finite in hi.
+SKS_DEV F2 split_f64(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int E = (int)((u >> 52) & 0x7ff);
+  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  if (E == 0x7ff) return {__uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u)), 0.f};
+  const int fe = E - 896;  // float32 biased exponent of hi
+  if (fe <= 0) return {0.f, 0.f};
+  if (fe >= 255) return {__uint_as_float(sign | 0x7f800000u), 0.f};
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29));
+  const unsigned r = (unsigned)(mant & 0x1FFFFFFFull);  // lo = r * 2^(E - 1075)
+  if (r == 0) return {hi, 0.f};
+  const int sh = __clz(r) - 8;                         // moves the leading one to bit 23
+  const unsigned m24 = sh >= 0 ? (r << sh) : (r >> (-sh));
+  const int le = E - 925 - sh;                          // float32 biased exponent of lo
+  if (le <= 0) return {hi, 0.f};
+  return {hi, __uint_as_float(sign | ((unsigned)le << 23) | (m24 & 0x7FFFFFu))};
+}
+// float32 -> float64 exactly, integer operations only (subnormals become 0).
+SKS_DEV double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xff;
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  if (e == 0) return __longlong_as_double((long long)s);
+  if (e == 255) return __longlong_as_double((long long)(s | 0x7FF0000000000000ull | m));
+  return __longlong_as_double((long long)(s | ((unsigned long long)(e + 896) << 52) | m));
+}
+
+// 2^s v by exponent arithmetic (no float64 operation) while the result stays
+// normal; ldexp otherwise.
+SKS_DEV double scale_pow2(double v, int s) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (s == 0 || E == 0x7ff || (b << 1) == 0) return v;  // unscaled, non-finite or zero
+  if (E == 0 || E + s <= 0 || E + s >= 0x7ff) return ldexp(v, s);  // subnormal or out of range
+  return __longlong_as_double(b + ((long long)s << 52));
+}
+
+SKS_DEV void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+SKS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+
+// ---------------------------------------------------------------- split and scale
+// s = floor(e / 2) for the binary exponent e of the largest diagonal entry:
+// the factorisation runs on 2^(-2s) H (largest diagonal in [1, 4)), whose
+// factor is 2^(-s) L and inverse factor 2^s X.  Exact (powers of two).
+__global__ void __launch_bounds__(256) diag_scale_kernel(int n, const double* __restrict__ H, long long ldh,
+                                                         int* __restrict__ s_out) {
+  __shared__ double part[256];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) v = fmax(v, H[(long long)i * ldh + i]);
+  part[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) part[threadIdx.x] = fmax(part[threadIdx.x], part[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = part[0];
+    const int E = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7ff);
+    // zero, subnormal or non-finite maximum: no scaling (the pivot check reports it)
+    *s_out = (E == 0 || E == 0x7ff) ? 0 : ((E - 1023) >> 1);
+  }
+}
+
+// 2^(-2s) H (lower triangle, float64) -> hi/lo planes (n x n, ld n).
+__global__ void split_lower_kernel(int n, const double* __restrict__ H, long long ldh, const int* __restrict__ s_in,
+                                   float* __restrict__ Hh, float* __restrict__ Hl) {
+  const int i = blockIdx.y;
+  const int s2 = -2 * *s_in;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i && j < n; j += gridDim.x * blockDim.x) {
+    const F2 v = split_f64(scale_pow2(H[(long long)i * ldh + j], s2));
+    Hh[(long long)i * n + j] = v.h;
+    Hl[(long long)i * n + j] = v.l;
+  }
+}
+
+// ---------------------------------------------------------------- diagonal block + panel
+// Thread t = 16 ty + tx owns the diagonal-block entries (ty + 16a, tx + 16b),
+// b <= a, in registers: A (the matrix being factored; column k becomes L's
+// column k at step k) and W (the inverse factor, built row by row:
+// W starts as I; at step k row k is final after scaling by 1/L_kk, and
+// W_ij -= L_ik X_kj for i > k, j <= k).  Column k of A and row k of W are
+// read by everyone from two shared buffers, written by their owners at the
+// end of step k - 1: one barrier per step.
+template <int PR>
+__global__ void __launch_bounds__(kCT) chol_panel_df32_kernel(float* __restrict__ Hh, float* __restrict__ Hl,
+                                                               long long ld, int n, int k0, int nb,
+                                                               float* __restrict__ Dh, float* __restrict__ Dl,
+                                                               DevStatus* st) {
+  extern __shared__ float cp_smem[];
+  float (*Xh)[NB + 1] = (float (*)[NB + 1])cp_smem;  // the block's inverse factor, for the panel
+  float (*Xl)[NB + 1] = Xh + NB;
+  float (*Ph)[NB + 1] = Xl + NB;                      // PR panel rows
+  float (*Pl)[NB + 1] = Ph + PR;
+  __shared__ float colh[2][NB], coll[2][NB], rowh[2][NB], rowl[2][NB];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const bool panel = blockIdx.x > 0;
+  const int r0 = k0 + nb + ((int)blockIdx.x - 1) * PR;
+  const int prow = panel ? min(PR, n - r0) : 0;
+  if (panel) {  // the panel rows do not depend on the factorisation: copy them first
+    for (int e = tid; e < PR * NB; e += kCT) {
+      const int r = e / NB, q = e % NB;
+      if (r < prow && q < nb) {
+        const long long g = (long long)(r0 + r) * ld + k0 + q;
+        cp_async4(&Ph[r][q], Hh + g);
+        cp_async4(&Pl[r][q], Hl + g);
+      } else {
+        Ph[r][q] = 0.f;
+        Pl[r][q] = 0.f;
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  float Ah[4][4], Al[4][4], Wh[4][4], Wl[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      const bool in = j <= i && i < nb;
+      const long long g = (long long)(k0 + i) * ld + k0 + j;
+      Ah[a][b] = in ? Hh[g] : (i == j ? 1.f : 0.f);
+      Al[a][b] = in ? Hl[g] : 0.f;
+      Wh[a][b] = i == j ? 1.f : 0.f;
+      Wl[a][b] = 0.f;
+    }
+  if (tx == 0) {  // column 0 of A (entries (i, 0) sit at b = 0)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const F2 v = f2_two_sum(Ah[a][0], Al[a][0]);
+      colh[0][ty + 16 * a] = v.h;
+      coll[0][ty + 16 * a] = v.l;
+    }
+  }
+  if (ty == 0) {  // row 0 of W is e_0
+    rowh[0][tx] = tx == 0 ? 1.f : 0.f;
+    rowl[0][tx] = 0.f;
+  }
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    F2 piv = {colh[cur][k], coll[cur][k]};
+    if (!(piv.h > 0.f) || !(piv.h < INFINITY)) {
+      if (tid == 0 && blockIdx.x == 0) raise_status(st, SKS_ERR_NOT_PD, 21, k0 + k);
+      piv = {1.f, 0.f};
+    }
+    const F2 r = f2_rsqrt(piv);
+    F2 li[4], lj[4], xk[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = ty + 16 * a;
+      li[a] = i > k ? f2_mul({colh[cur][i], coll[cur][i]}, r) : F2{0.f, 0.f};
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = tx + 16 * b;
+      lj[b] = j > k ? f2_mul({colh[cur][j], coll[cur][j]}, r) : F2{0.f, 0.f};
+      xk[b] = j <= k ? f2_mul({rowh[cur][j], rowl[cur][j]}, r) : F2{0.f, 0.f};
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = ty + 16 * a;
+      if (i > k) {
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+          const int j = tx + 16 * b;
+          if (j <= i) {
+            if (j > k) f2_acc<true>(Ah[a][b], Al[a][b], li[a], lj[b]);  // trailing update of A
+            else f2_acc<true>(Wh[a][b], Wl[a][b], li[a], xk[b]);        // W_ij -= L_ik X_kj
+          }
+        }
+      }
+    }
+    // finish column k of L and row k of X; publish column k + 1 and row k + 1
+    const F2 dk = f2_mul(piv, r);  // L_kk = sqrt(pivot)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        if (j == k && i >= k) {
+          const F2 v = i == k ? dk : li[a];
+          Ah[a][b] = v.h;
+          Al[a][b] = v.l;
+        }
+        if (i == k && j <= k) {
+          Wh[a][b] = xk[b].h;
+          Wl[a][b] = xk[b].l;
+        }
+        if (j == k + 1 && i >= k + 1) {
+          const F2 v = f2_two_sum(Ah[a][b], Al[a][b]);
+          colh[nxt][i] = v.h;
+          coll[nxt][i] = v.l;
+        }
+        if (i == k + 1 && j <= k + 1) {
+          const F2 v = f2_two_sum(Wh[a][b], Wl[a][b]);
+          rowh[nxt][j] = v.h;
+          rowl[nxt][j] = v.l;
+        }
+      }
+    __syncthreads();
+  }
+  // inverse factor into shared memory (zeros above the diagonal)
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      F2 v = {0.f, 0.f};
+      if (b <= a) v = f2_two_sum(Wh[a][b], Wl[a][b]);
+      if (j > i) v = {0.f, 0.f};
+      Xh[i][j] = v.h;
+      Xl[i][j] = v.l;
+    }
+  // L_kk itself is not stored: only its inverse is used later (the panel
+  // below and the merges read blocks strictly below the diagonal blocks), so
+  // the other CTAs may still be reading the diagonal block.
+  if (!panel) {
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += kCT) {
+      Dh[e] = Xh[e / NB][e % NB];
+      Dl[e] = Xl[e / NB][e % NB];
+    }
+    return;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // panel rows: L_rj = sum_{q <= j} P_rq X_jq; rows ty + 16a, columns tx + 16b
+  constexpr int RA = PR / 16;
+  float sh[RA][4], sl[RA][4];
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {  // X_jq = 0 for q > j: the q segment c only meets columns b >= c
+    if (16 * c >= nb) break;
+#pragma unroll 4
+    for (int qq = 0; qq < 16; ++qq) {
+      const int q = 16 * c + qq;
+      F2 p[RA];
+#pragma unroll
+      for (int a = 0; a < RA; ++a) p[a] = {Ph[ty + 16 * a][q], Pl[ty + 16 * a][q]};
+#pragma unroll
+      for (int b = c; b < 4; ++b) {
+        const F2 x = {Xh[tx + 16 * b][q], Xl[tx + 16 * b][q]};
+#pragma unroll
+        for (int a = 0; a < RA; ++a) f2_acc<false>(sh[a][b], sl[a][b], p[a], x);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, j = tx + 16 * b;
+      if (r < prow && j < nb) {
+        const F2 v = f2_two_sum(sh[a][b], sl[a][b]);
+        const long long g = (long long)(r0 + r) * ld + k0 + j;
+        Hh[g] = v.h;
+        Hl[g] = v.l;
+      }
+    }
+}
+
+// ---------------------------------------------------------------- trailing update
+// T_ij -= sum_{q < kk} P_iq P_jq for the lower 64 x 64 tiles of the trailing
+// matrix T (rest x rest); P = the panel just formed (rest x kk, kk <= 64).
+// Planes in, planes out; each thread keeps 4 x 4 double-float sums.
+__global__ void __launch_bounds__(kCT) syrk_df32_planes_kernel(int rest, int kk, const float* __restrict__ Ph,
+                                                               const float* __restrict__ Pl, float* __restrict__ Th,
+                                                               float* __restrict__ Tl, long long ld) {
+  extern __shared__ float sy_smem[];
+  float (*Ah)[NB + 1] = (float (*)[NB + 1])sy_smem;
+  float (*Al)[NB + 1] = Ah + NB;
+  float (*Bh)[NB + 1] = Al + NB;
+  float (*Bl)[NB + 1] = Bh + NB;
+  // lower tile (ti, tj), ti >= tj, from the linear block index
+  int ti = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
+  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
+  const int tj = (int)blockIdx.x - ti * (ti + 1) / 2;
+  const int i0 = ti * NB, j0 = tj * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += kCT) {
+    const int r = e / NB, q = e % NB;
+    const bool qok = q < kk;
+    const long long ga = (long long)(i0 + r) * ld + q, gb = (long long)(j0 + r) * ld + q;
+    const bool aok = qok && i0 + r < rest, bok = qok && j0 + r < rest;
+    Ah[r][q] = aok ? Ph[ga] : 0.f;
+    Al[r][q] = aok ? Pl[ga] : 0.f;
+    Bh[r][q] = bok ? Ph[gb] : 0.f;
+    Bl[r][q] = bok ? Pl[gb] : 0.f;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
+#pragma unroll 2
+  for (int q = 0; q < kk; ++q) {
+    F2 x[4], y[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      x[a] = {Ah[ty * 4 + a][q], Al[ty * 4 + a][q]};
+      y[a] = {Bh[tx * 4 + a][q], Bl[tx * 4 + a][q]};
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) f2_acc<false>(sh[a][b], sl[a][b], x[a], y[b]);
+  }
+  float* th = Th;
+  float* tl = Tl;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gi = i0 + ty * 4 + a, gj = j0 + tx * 4 + b;
+      if (gi < rest && gj < rest && gj <= gi) {
+        const long long g = (long long)gi * ld + gj;
+        const F2 t = f2_two_sum(th[g], -sh[a][b]);
+        const F2 v = f2_fast_two_sum(t.h, __fadd_rn(t.l, __fsub_rn(tl[g], sl[a][b])));
+        th[g] = v.h;
+        tl[g] = v.l;
+      }
+    }
+}
+
+// ---------------------------------------------------------------- double-float GEMM (merges)
+// C = alpha * A B (row-major planes; alpha = +1 or -1).  a_lower: A is lower
+// triangular (terms k > i are zero and skipped); b_lower: B is lower
+// triangular (terms k < j skipped).  64 x 64 tiles, K in steps of 32.
+constexpr int kGK = 32;
+__global__ void __launch_bounds__(kCT) gemm_df32_kernel(int M, int N, int K, const float* __restrict__ Ah_,
+                                                        const float* __restrict__ Al_, long long lda,
+                                                        const float* __restrict__ Bh_, const float* __restrict__ Bl_,
+                                                        long long ldb, float* __restrict__ Ch, float* __restrict__ Cl,
+                                                        long long ldc, float alpha, int a_lower, int b_lower) {
+  __shared__ float Ash[NB][kGK + 1], Asl[NB][kGK + 1];  // A tile [row][k]
+  __shared__ float Bsh[NB][kGK + 1], Bsl[NB][kGK + 1];  // B tile transposed [col][k]
+  const int row0 = blockIdx.y * NB, col0 = blockIdx.x * NB;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int kb = 0, ke = K;
+  if (a_lower) ke = min(K, row0 + NB);
+  if (b_lower) kb = (col0 / kGK) * kGK;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += kGK) {
+    for (int e = threadIdx.x; e < NB * kGK; e += kCT) {
+      const int r = e / kGK, q = e % kGK;  // A: row r, k q
+      const int gi = row0 + r, gk = k0 + q;
+      const bool ok = gi < M && gk < K;
+      Ash[r][q] = ok ? Ah_[(long long)gi * lda + gk] : 0.f;
+      Asl[r][q] = ok ? Al_[(long long)gi * lda + gk] : 0.f;
+      const int c = e % NB, qb = e / NB;  // B: k qb, column c
+      const int gj = col0 + c, gkb = k0 + qb;
+      const bool okb = gj < N && gkb < K;
+      Bsh[c][qb] = okb ? Bh_[(long long)gkb * ldb + gj] : 0.f;
+      Bsl[c][qb] = okb ? Bl_[(long long)gkb * ldb + gj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = 0; q < kGK; ++q) {
+      F2 x[4], y[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        x[a] = {Ash[ty * 4 + a][q], Asl[ty * 4 + a][q]};
+        y[a] = {Bsh[tx * 4 + a][q], Bsl[tx * 4 + a][q]};
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) f2_acc<false>(sh[a][b], sl[a][b], x[a], y[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gi = row0 + ty * 4 + a, gj = col0 + tx * 4 + b;
+      if (gi < M && gj < N) {
+        const F2 v = f2_two_sum(sh[a][b], sl[a][b]);
+        Ch[(long long)gi * ldc + gj] = alpha * v.h;
+        Cl[(long long)gi * ldc + gj] = alpha * v.l;
+      }
+    }
+}
+
+// ---------------------------------------------------------------- placement and output
+// the diagonal-block inverses (NB x NB each, planes) into zeroed X planes
+__global__ void place_dinv_kernel(int n, int nblk, const float* __restrict__ Dh, const float* __restrict__ Dl,
+                                  float* __restrict__ Xh, float* __restrict__ Xl, long long ldx) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)nblk * NB * NB) return;
+  const int kb = (int)(e / (NB * NB)), i = (int)(e / NB % NB), j = (int)(e % NB);
+  const int gi = kb * NB + i, gj = kb * NB + j;
+  if (gi >= n || gj >= n) return;
+  Xh[(long long)gi * ldx + gj] = Dh[e];
+  if (Xl) Xl[(long long)gi * ldx + gj] = Dl[e];
+}
+
+// X = 2^(-s) (hi + lo) in float64 (lo may be NULL: float32 inverse); the
+// widening and the power-of-two scaling are exact integer operations, one
+// float64 addition remains.
+__global__ void planes_to_f64_kernel(int n, const float* __restrict__ Xh, const float* __restrict__ Xl, long long ldp,
+                                     const int* __restrict__ s_in, double* __restrict__ X, long long ldx) {
+  const int i = blockIdx.y;
+  const int s = *s_in;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const long long g = (long long)i * ldp + j;
+    double v = f32_to_f64_bits(Xh[g]);
+    if (Xl) v += f32_to_f64_bits(Xl[g]);
+    X[(long long)i * ldx + j] = scale_pow2(v, -s);
+  }
+}
+}  // namespace
+
+template <int PR>
+static sks_status launch_panel(cudaStream_t stream, int grid, float* Hh, float* Hl, long long ld, int n, int k0, int nb,
+                               float* Dh, float* Dl, DevStatus* st) {
+  constexpr size_t smem = (size_t)(2 * NB + 2 * PR) * (NB + 1) * sizeof(float);
+  SKS_CUDA_TRY(cudaFuncSetAttribute(chol_panel_df32_kernel<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  chol_panel_df32_kernel<PR><<<grid, kCT, smem, stream>>>(Hh, Hl, ld, n, k0, nb, Dh, Dl, st);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? SKS_OK : fail(SKS_ERR_CUDA, "chol_panel_df32_kernel launch");
+}
+
+static sks_status gemm_df32(cudaStream_t stream, int M, int N, int K, const float* Ah, const float* Al, long long lda,
+                            const float* Bh, const float* Bl, long long ldb, float* Ch, float* Cl, long long ldc,
+                            float alpha, bool a_lower, bool b_lower) {
+  if (M <= 0 || N <= 0) return SKS_OK;
+  const dim3 grid((unsigned)((N + NB - 1) / NB), (unsigned)((M + NB - 1) / NB));
+  gemm_df32_kernel<<<grid, kCT, 0, stream>>>(M, N, K, Ah, Al, lda, Bh, Bl, ldb, Ch, Cl, ldc, alpha, a_lower ? 1 : 0,
+                                             b_lower ? 1 : 0);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
+// Double-float factorisation of H (n x n, lower part read, float64) and its
+// inverse factor X (float64, lower, n x n): float32 merges (f32_inverse) or
+// double-float merges.  ws: cholesky_ws_elems(n) doubles; ws32:
+// cholesky_ws32_elems(n) floats.  A non-positive pivot raises SKS_ERR_NOT_PD.
+sks_status cholesky_inverse_df32(cudaStream_t stream, int n, const double* H, long long ldh, double* X,
+                                 long long ldx, double* ws, float* ws32, DevStatus* st, bool f32_inverse) {
+  if (n <= 0) return SKS_OK;
+  if (ws == nullptr || ws32 == nullptr) return fail(SKS_ERR_WORKSPACE, "double-float Cholesky needs both workspaces");
+  const int nblk = (n + NB - 1) / NB;
+  const long long ld = n;
+  float* wsf = reinterpret_cast<float*>(ws);
+  int* sexp = reinterpret_cast<int*>(wsf);           // the scaling exponent s
+  float* Dh = wsf + 64;                               // diagonal-block inverses, NB x NB each
+  float* Dl = Dh + (size_t)nblk * NB * NB;
+  float* R = Dl + (size_t)nblk * NB * NB;             // X32, or the X planes
+  float* Hh = ws32;
+  float* Hl = ws32 + (size_t)n * n;
+  float* T = ws32 + (size_t)2 * n * n;                // merge scratch: 2 n^2 + 64 floats
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  diag_scale_kernel<<<1, 256, 0, stream>>>(n, H, ldh, sexp);
+  note_launch();
+  const unsigned gx = (unsigned)std::min(8, (n + 255) / 256);
+  split_lower_kernel<<<dim3(gx, (unsigned)n), 256, 0, stream>>>(n, H, ldh, sexp, Hh, Hl);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  constexpr size_t kSySmem = 4 * NB * (NB + 1) * sizeof(float);
+  SKS_CUDA_TRY(cudaFuncSetAttribute(syrk_df32_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSySmem));
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int k0 = kb * NB, nb = std::min(NB, n - k0);
+    const int rest = n - k0 - nb;
+    float* dh = Dh + (size_t)kb * NB * NB;
+    float* dl = Dl + (size_t)kb * NB * NB;
+    // 32 panel rows per CTA while the grid fits on the SMs, else 64
+    if (1 + (rest + 31) / 32 <= sms) SKS_TRY(launch_panel<32>(stream, 1 + (rest + 31) / 32, Hh, Hl, ld, n, k0, nb, dh, dl, st));
+    else SKS_TRY(launch_panel<64>(stream, 1 + (rest + 63) / 64, Hh, Hl, ld, n, k0, nb, dh, dl, st));
+    if (rest > 0) {
+      const long long pan = (long long)(k0 + nb) * ld + k0;
+      const long long tr = (long long)(k0 + nb) * ld + k0 + nb;
+      const int tb = (rest + NB - 1) / NB;
+      syrk_df32_planes_kernel<<<(unsigned)(tb * (tb + 1) / 2), kCT, kSySmem, stream>>>(rest, nb, Hh + pan, Hl + pan,
+                                                                                      Hh + tr, Hl + tr, ld);
+      note_launch();
+      SKS_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  // X' = L'^{-1} of the scaled factor from the diagonal-block inverses by merging
+  const long long nn = (long long)n * n;
+  const unsigned pg = (unsigned)(((long long)nblk * NB * NB + 255) / 256);
+  if (f32_inverse) {
+    float* X32 = R;
+    SKS_CUDA_TRY(cudaMemsetAsync(X32, 0, (size_t)nn * sizeof(float), stream));
+    place_dinv_kernel<<<pg, 256, 0, stream>>>(n, nblk, Dh, nullptr, X32, nullptr, ld);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+    float* tmp32 = T;
+    const size_t rest32 = (size_t)n * n;
+    for (int b = NB; b < n; b *= 2) {
+      for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
+        const int n1 = b, n2 = std::min(b, n - r0 - b);
+        const float* Ainv = X32 + (long long)r0 * ld + r0;
+        const float* Lb = Hh + (long long)(r0 + b) * ld + r0;
+        const float* Cinv = X32 + (long long)(r0 + b) * ld + (r0 + b);
+        float* out = X32 + (long long)(r0 + b) * ld + r0;
+        SKS_TRY(gemm<float>(stream, n2, n1, n1, Lb, ld, false, Ainv, ld, false, tmp32, n1, 1.0, 0.0, false, 1, 0, 0, 0,
+                            tmp32 + (size_t)n2 * n1, rest32, 2));
+        SKS_TRY(gemm<float>(stream, n2, n1, n2, Cinv, ld, false, tmp32, n1, false, out, ld, -1.0, 0.0, false, 1, 0, 0,
+                            0, tmp32 + (size_t)n2 * n1, rest32, 1));
+      }
+    }
+    planes_to_f64_kernel<<<dim3(gx, (unsigned)n), 256, 0, stream>>>(n, X32, nullptr, ld, sexp, X, ldx);
+    note_launch();
+    SKS_CUDA_TRY(cudaGetLastError());
+    return SKS_OK;
+  }
+  float* Xh = R;
+  float* Xl = R + (size_t)nn;
+  SKS_CUDA_TRY(cudaMemsetAsync(Xh, 0, (size_t)2 * nn * sizeof(float), stream));
+  place_dinv_kernel<<<pg, 256, 0, stream>>>(n, nblk, Dh, Dl, Xh, Xl, ld);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  for (int b = NB; b < n; b *= 2) {
+    for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
+      const int n1 = b, n2 = std::min(b, n - r0 - b);
+      const long long oa = (long long)r0 * ld + r0, ob = (long long)(r0 + b) * ld + r0;
+      const long long oc = (long long)(r0 + b) * ld + (r0 + b);
+      float* th = T;
+      float* tl = T + (size_t)n2 * n1;
+      // tmp = B A^{-1} (A^{-1} lower), then X_21 = -C^{-1} tmp (C^{-1} lower)
+      SKS_TRY(gemm_df32(stream, n2, n1, n1, Hh + ob, Hl + ob, ld, Xh + oa, Xl + oa, ld, th, tl, n1, 1.f, false, true));
+      SKS_TRY(gemm_df32(stream, n2, n1, n2, Xh + oc, Xl + oc, ld, th, tl, n1, Xh + ob, Xl + ob, ld, -1.f, true, false));
+    }
+  }
+  planes_to_f64_kernel<<<dim3(gx, (unsigned)n), 256, 0, stream>>>(n, Xh, Xl, ld, sexp, X, ldx);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
+}  // namespace sks

@@ -238,178 +238,6 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* D, long long ld
 // L_kk^{-1}; CTA b >= 1 replaces its 64 rows of the panel below the block by
 // P L_kk^{-T} in double-float arithmetic.  The diagonal work is repeated per
 // CTA so that no launch waits for another.
-__global__ void __launch_bounds__(256) potrf_panel_kernel(double* H, long long ldh, int n, int k0, int nb,
-                                                         double* Dinv, double* Lout, DevStatus* st) {
-  extern __shared__ double pp_smem[];
-  double (*L)[NB + 1] = (double (*)[NB + 1])pp_smem;  // diagonal block, later P hi/lo (floats)
-  double (*X)[NB + 1] = L + NB;                       // L^{-1}
-  float (*Xh)[NB + 1] = (float (*)[NB + 1])(X + NB);
-  float (*Xl)[NB + 1] = Xh + NB;
-  __shared__ double part[4][NB];
-  __shared__ double rdiag[NB];
-  const int tid = threadIdx.x;
-  double* D = H + (long long)k0 * ldh + k0;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, j = e % NB;
-    L[i][j] = (i < nb && j < nb && j <= i) ? D[(long long)i * ldh + j] : (i == j ? 1.0 : 0.0);
-  }
-  __syncthreads();
-  __shared__ double colk[NB];
-  __shared__ double rd[NB];
-  chol_block(L, colk, rd, nb, st, k0, blockIdx.x == 0);
-  for (int e = tid; e < NB * NB; e += blockDim.x) X[e / NB][e % NB] = 0.0;
-  if (tid < NB) rdiag[tid] = tid < nb ? rd[tid] : 1.0;
-  __syncthreads();
-  {
-    const int jj = tid & (NB - 1), pq = tid >> 6;
-    for (int i = 0; i < NB; ++i) {
-      double acc = 0.0;
-      if (jj < i)
-        for (int q = jj + pq; q < i; q += 4) acc += L[i][q] * X[q][jj];
-      part[pq][jj] = acc;
-      __syncthreads();
-      if (tid < NB) {
-        const double inv = rdiag[i];
-        if (tid < i) X[i][tid] = -((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) * inv;
-        else if (tid == i) X[i][i] = inv;
-      }
-      __syncthreads();
-    }
-  }
-  if (blockIdx.x == 0) {
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-      const int i = e / nb, j = e % nb;
-      Lout[(long long)i * NB + j] = j <= i ? L[i][j] : 0.0;
-      Dinv[(long long)i * NB + j] = X[i][j];
-    }
-    return;
-  }
-  // panel rows of this CTA: P <- P X^T, X = L_kk^{-1} (lower), double-float
-  const int r0 = k0 + nb + ((int)blockIdx.x - 1) * NB;
-  const int rows = min(NB, n - r0);
-  float (*Ph)[NB + 1] = (float (*)[NB + 1])L;  // the diagonal block is no longer needed
-  float (*Pl)[NB + 1] = Ph + NB;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, q = e % NB;
-    const double x = X[r][q];
-    const float xh = (float)x;
-    Xh[r][q] = xh;
-    Xl[r][q] = (float)(x - (double)xh);
-    const double pv = (r < rows && q < nb) ? H[(long long)(r0 + r) * ldh + k0 + q] : 0.0;
-    const float ph = (float)pv;
-    Ph[r][q] = ph;
-    Pl[r][q] = (float)(pv - (double)ph);
-  }
-  __syncthreads();
-  const int tx = tid & 15, ty = tid >> 4;
-  float sh[4][4], sl[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
-  for (int q = 0; q < nb; ++q) {
-    float ah[4], al[4], bh[4], bl[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      ah[a] = Ph[ty * 4 + a][q];
-      al[a] = Pl[ty * 4 + a][q];
-      bh[a] = Xh[tx * 4 + a][q];
-      bl[a] = Xl[tx * 4 + a][q];
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float p = ah[a] * bh[b];
-        float e = fmaf(ah[a], bh[b], -p);
-        e = fmaf(ah[a], bl[b], e);
-        e = fmaf(al[a], bh[b], e);
-        const float s2 = sh[a][b] + p;
-        const float bp = s2 - sh[a][b];
-        const float t = (sh[a][b] - (s2 - bp)) + (p - bp);
-        sh[a][b] = s2;
-        sl[a][b] += t + e;
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty * 4 + a, j = tx * 4 + b;
-      if (r < rows && j < nb) H[(long long)(r0 + r) * ldh + k0 + j] = (double)sh[a][b] + (double)sl[a][b];
-    }
-}
-
-// T[i][j] -= sum_k P[i][k] P[j][k] for the lower 64 x 64 tiles of T (rest x
-// rest), K = kk <= 64, in double-float arithmetic (float32 pairs, ~2^-44
-// relative): products by TwoProd with the cross terms, sums by Knuth's
-// TwoSum.  Storage stays float64; the arithmetic runs on the float32 pipe,
-// which on this part is ~60x the float64 pipe.
-__global__ void __launch_bounds__(256) syrk_df32_lower_kernel(int rest, int kk, const double* __restrict__ P,
-                                                             long long ldp, double* __restrict__ T, long long ldt) {
-  extern __shared__ float sy_smem[];  // Ah, Al, Bh, Bl: [row][k], rows padded to 65
-  float (*Ah)[NB + 1] = (float (*)[NB + 1])sy_smem;
-  float (*Al)[NB + 1] = Ah + NB;
-  float (*Bh)[NB + 1] = Al + NB;
-  float (*Bl)[NB + 1] = Bh + NB;
-  int ti = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
-  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
-  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
-  const int tj = (int)blockIdx.x - ti * (ti + 1) / 2;
-  const int i0 = ti * NB, j0 = tj * NB;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, k = e % NB;
-    double a = 0.0, b = 0.0;
-    if (k < kk) {
-      if (i0 + r < rest) a = P[(long long)(i0 + r) * ldp + k];
-      if (j0 + r < rest) b = P[(long long)(j0 + r) * ldp + k];
-    }
-    const float ah = (float)a, bh = (float)b;
-    Ah[r][k] = ah;
-    Al[r][k] = (float)(a - (double)ah);
-    Bh[r][k] = bh;
-    Bl[r][k] = (float)(b - (double)bh);
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float sh[4][4], sl[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
-  for (int k = 0; k < kk; ++k) {
-    float ah[4], al[4], bh[4], bl[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      ah[a] = Ah[ty * 4 + a][k];
-      al[a] = Al[ty * 4 + a][k];
-      bh[a] = Bh[tx * 4 + a][k];
-      bl[a] = Bl[tx * 4 + a][k];
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float p = ah[a] * bh[b];
-        float e = fmaf(ah[a], bh[b], -p);
-        e = fmaf(ah[a], bl[b], e);
-        e = fmaf(al[a], bh[b], e);
-        const float s = sh[a][b] + p;
-        const float bp = s - sh[a][b];
-        const float t = (sh[a][b] - (s - bp)) + (p - bp);
-        sh[a][b] = s;
-        sl[a][b] += t + e;
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int gi = i0 + ty * 4 + a, gj = j0 + tx * 4 + b;
-      if (gi < rest && gj < rest && gj <= gi) T[(long long)gi * ldt + gj] -= (double)sh[a][b] + (double)sl[a][b];
-    }
-}
-
 template <typename T>
 __global__ void transpose_kernel(int rows, int cols, const T* __restrict__ S, long long lds, T* __restrict__ D,
                                  long long ldd) {
@@ -538,31 +366,6 @@ sks_status add_diagonal(cudaStream_t stream, int n, double* M, long long ld, dou
   return SKS_OK;
 }
 
-__global__ void lower_to_f32_kernel(int n, const double* __restrict__ H, long long ldh, float* __restrict__ L,
-                                    long long ldl) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)n * n) return;
-  const int i = (int)(e / n), j = (int)(e % n);
-  L[(long long)i * ldl + j] = (j <= i) ? (float)H[(long long)i * ldh + j] : 0.f;
-}
-
-__global__ void f32_to_f64_mat_kernel(int n, const float* __restrict__ S, long long lds, double* __restrict__ D,
-                                      long long ldd) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)n * n) return;
-  const int i = (int)(e / n), j = (int)(e % n);
-  D[(long long)i * ldd + j] = (double)S[(long long)i * lds + j];
-}
-
-__global__ void dinv_to_f32_kernel(int n, int nblk, const double* __restrict__ dinv, float* __restrict__ X,
-                                   long long ldx) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)nblk * 64 * 64) return;
-  const int kb = (int)(e / (64 * 64)), r = (int)((e / 64) % 64), c = (int)(e % 64);
-  const int i = kb * 64 + r, j = kb * 64 + c;
-  if (i < n && j < n) X[(long long)i * ldx + j] = (float)dinv[e];
-}
-
 size_t cholesky_ws_elems(int n) {
   // diagonal-block inverses + split-K partials of the trailing updates
   const int nblk = (n + NB - 1) / NB;
@@ -572,43 +375,18 @@ size_t cholesky_ws_elems(int n) {
 // In-place blocked right-looking Cholesky H = L L^T (lower; upper set to 0),
 // then X = L^{-1} by recursive block inversion.  ws: cholesky_ws_elems(n).
 sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long ldh, double* X, long long ldx,
-                                double* ws, DevStatus* st, float* ws32, bool df32_update) {
+                                double* ws, DevStatus* st, float* ws32, int mode) {
   if (n <= 0) return SKS_OK;
+  if (mode == kCholDf32InvF32 || mode == kCholDf32)
+    return cholesky_inverse_df32(stream, n, H, ldh, X, ldx, ws, ws32, st, mode == kCholDf32InvF32);
   const int nblk = (n + NB - 1) / NB;
   double* dinv = ws;                              // nblk * NB * NB
   double* split = ws + (size_t)nblk * NB * NB;    // scratch for split-K
   const size_t split_elems = (size_t)8 * n * NB + (size_t)n * n;
-  constexpr size_t kPanelSmem = 2 * NB * (NB + 1) * sizeof(double) + 2 * NB * (NB + 1) * sizeof(float);
-  if (df32_update)
-    SKS_CUDA_TRY(cudaFuncSetAttribute(potrf_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kPanelSmem));
   for (int kb = 0; kb < nblk; ++kb) {
     const int k0 = kb * NB, nb = std::min(NB, n - k0);
     double* Dk = H + (long long)k0 * ldh + k0;
     double* Dinv = dinv + (size_t)kb * NB * NB;
-    if (df32_update) {
-      // diagonal block and panel in one launch, then the double-float trailing update
-      const int rest = n - k0 - nb;
-      const int pb = (rest + NB - 1) / NB;
-      double* Lk = split;  // NB x NB scratch: the factored block, copied into H after the kernel
-      potrf_panel_kernel<<<1 + pb, 256, kPanelSmem, stream>>>(H, ldh, n, k0, nb, Dinv, Lk, st);
-      note_launch();
-      SKS_CUDA_TRY(cudaGetLastError());
-      SKS_CUDA_TRY(cudaMemcpy2DAsync(Dk, ldh * sizeof(double), Lk, NB * sizeof(double), nb * sizeof(double), nb,
-                                     cudaMemcpyDeviceToDevice, stream));
-      if (rest > 0) {
-        double* P = H + (long long)(k0 + nb) * ldh + k0;
-        double* T = H + (long long)(k0 + nb) * ldh + (k0 + nb);
-        const int tb = (rest + NB - 1) / NB;
-        constexpr size_t kSySmem = 4 * NB * (NB + 1) * sizeof(float);
-        SKS_CUDA_TRY(cudaFuncSetAttribute(syrk_df32_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kSySmem));
-        syrk_df32_lower_kernel<<<(unsigned)(tb * (tb + 1) / 2), 256, kSySmem, stream>>>(rest, nb, P, ldh, T, ldh);
-        note_launch();
-        SKS_CUDA_TRY(cudaGetLastError());
-      }
-      continue;
-    }
     potrf_diag_kernel<<<1, 256, 0, stream>>>(Dk, ldh, nb, Dinv, k0, st);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
@@ -622,18 +400,8 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
                                      cudaMemcpyDeviceToDevice, stream));
       // trailing lower update  T <- T - P P^T
       double* T = H + (long long)(k0 + nb) * ldh + (k0 + nb);
-      if (df32_update) {
-        const int tb = (rest + NB - 1) / NB;
-        constexpr size_t kSySmem = 4 * NB * (NB + 1) * sizeof(float);
-        SKS_CUDA_TRY(cudaFuncSetAttribute(syrk_df32_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kSySmem));
-        syrk_df32_lower_kernel<<<(unsigned)(tb * (tb + 1) / 2), 256, kSySmem, stream>>>(rest, nb, P, ldh, T, ldh);
-        note_launch();
-        SKS_CUDA_TRY(cudaGetLastError());
-      } else {
-        SKS_TRY(gemm<double>(stream, rest, rest, nb, P, ldh, false, P, ldh, true, T, ldh, -1.0, 1.0, true, 1, 0, 0, 0,
-                             nullptr, 0));
-      }
+      SKS_TRY(gemm<double>(stream, rest, rest, nb, P, ldh, false, P, ldh, true, T, ldh, -1.0, 1.0, true, 1, 0, 0, 0,
+                           nullptr, 0));
     }
   }
   // H now holds L in its lower triangle (the strict upper triangle outside the
@@ -646,54 +414,22 @@ sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long
                                    NB * sizeof(double), nb * sizeof(double), nb, cudaMemcpyDeviceToDevice, stream));
   }
   // inv([A 0; B C]) = [A^-1 0; -C^-1 B A^-1  C^-1]
-  if (ws32 == nullptr) {
-    for (int b = NB; b < n; b *= 2) {
-      for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
-        const int n1 = b, n2 = std::min(b, n - r0 - b);
-        const double* Binv_A = X + (long long)r0 * ldx + r0;          // A^{-1}: n1 x n1
-        const double* Lb = H + (long long)(r0 + b) * ldh + r0;        // B: n2 x n1
-        const double* Cinv = X + (long long)(r0 + b) * ldx + (r0 + b);  // C^{-1}: n2 x n2
-        double* out = X + (long long)(r0 + b) * ldx + r0;             // n2 x n1
-        double* tmp = split;                                          // n2 x n1
-        const size_t rest_elems = split_elems - (size_t)n2 * n1;
-        // A^{-1} and C^{-1} are lower triangular: half of each product's terms are skipped
-        SKS_TRY(gemm<double>(stream, n2, n1, n1, Lb, ldh, false, Binv_A, ldx, false, tmp, n1, 1.0, 0.0, false, 1, 0,
-                             0, 0, split + (size_t)n2 * n1, rest_elems, 2));
-        SKS_TRY(gemm<double>(stream, n2, n1, n2, Cinv, ldx, false, tmp, n1, false, out, ldx, -1.0, 0.0, false, 1, 0,
-                             0, 0, split + (size_t)n2 * n1, rest_elems, 1));
-      }
-    }
-    return SKS_OK;
-  }
-  // float32 merge (the preconditioner only needs the inverse factor to be a
-  // close nonsingular approximation; the operator X^T X stays SPD)
-  float* L32 = ws32;
-  float* X32 = ws32 + (size_t)n * n;
-  float* tmp32 = ws32 + (size_t)2 * n * n;
-  const size_t rest32 = (size_t)n * n;  // split-K partials beyond the n x n/2 tmp block
-  const long long nn = (long long)n * n;
-  lower_to_f32_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(n, H, ldh, L32, n);
-  note_launch();
-  SKS_CUDA_TRY(cudaMemsetAsync(X32, 0, (size_t)n * n * sizeof(float), stream));
-  dinv_to_f32_kernel<<<(unsigned)(((long long)nblk * 64 * 64 + 255) / 256), 256, 0, stream>>>(n, nblk, dinv, X32, n);
-  note_launch();
-  SKS_CUDA_TRY(cudaGetLastError());
   for (int b = NB; b < n; b *= 2) {
     for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
       const int n1 = b, n2 = std::min(b, n - r0 - b);
-      const float* Ainv = X32 + (long long)r0 * n + r0;
-      const float* Lb = L32 + (long long)(r0 + b) * n + r0;
-      const float* Cinv = X32 + (long long)(r0 + b) * n + (r0 + b);
-      float* out = X32 + (long long)(r0 + b) * n + r0;
-      SKS_TRY(gemm<float>(stream, n2, n1, n1, Lb, n, false, Ainv, n, false, tmp32, n1, 1.0, 0.0, false, 1, 0, 0, 0,
-                          tmp32 + (size_t)n2 * n1, rest32, 2));
-      SKS_TRY(gemm<float>(stream, n2, n1, n2, Cinv, n, false, tmp32, n1, false, out, n, -1.0, 0.0, false, 1, 0, 0, 0,
-                          tmp32 + (size_t)n2 * n1, rest32, 1));
+      const double* Binv_A = X + (long long)r0 * ldx + r0;          // A^{-1}: n1 x n1
+      const double* Lb = H + (long long)(r0 + b) * ldh + r0;        // B: n2 x n1
+      const double* Cinv = X + (long long)(r0 + b) * ldx + (r0 + b);  // C^{-1}: n2 x n2
+      double* out = X + (long long)(r0 + b) * ldx + r0;             // n2 x n1
+      double* tmp = split;                                          // n2 x n1
+      const size_t rest_elems = split_elems - (size_t)n2 * n1;
+      // A^{-1} and C^{-1} are lower triangular: half of each product's terms are skipped
+      SKS_TRY(gemm<double>(stream, n2, n1, n1, Lb, ldh, false, Binv_A, ldx, false, tmp, n1, 1.0, 0.0, false, 1, 0, 0,
+                           0, split + (size_t)n2 * n1, rest_elems, 2));
+      SKS_TRY(gemm<double>(stream, n2, n1, n2, Cinv, ldx, false, tmp, n1, false, out, ldx, -1.0, 0.0, false, 1, 0, 0,
+                           0, split + (size_t)n2 * n1, rest_elems, 1));
     }
   }
-  f32_to_f64_mat_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(n, X32, n, X, ldx);
-  note_launch();
-  SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
 }
 

@@ -24,14 +24,21 @@ sks_status add_diagonal(cudaStream_t stream, int n, double* M, long long ld, dou
 
 size_t cholesky_ws_elems(int n);
 size_t cholesky_ws32_elems(int n);
-// H (n x n, lower part read) = L L^T in place (float64 storage); X = L^{-1}
-// (lower, n x n).  With ws32 (cholesky_ws32_elems floats) the inverse is
-// formed in float32 and widened.  df32_update: the trailing updates of the
-// blocked factorisation in double-float arithmetic (~2^-44 relative, on the
-// float32 pipe) instead of float64.  Raises SKS_ERR_NOT_PD in `st` on a
+// H (n x n, lower part read) = L L^T and X = L^{-1} (lower, n x n, float64).
+//   kCholF64:        float64 throughout; L overwrites H's lower triangle.
+//   kCholDf32InvF32: double-float factorisation (chol.cu), inverse factor
+//                    merged in float32 (the Cholesky form's apply X^T X is
+//                    positive definite for any nonsingular X).
+//   kCholDf32:       double-float factorisation and inverse factor (Woodbury
+//                    form).  H is left unchanged by the double-float modes.
+// ws: cholesky_ws_elems(n) doubles; ws32 (double-float modes):
+// cholesky_ws32_elems(n) floats.  Raises SKS_ERR_NOT_PD in `st` on a
 // non-positive pivot.
+enum { kCholF64 = 0, kCholDf32InvF32 = 1, kCholDf32 = 2 };
 sks_status cholesky_and_inverse(cudaStream_t stream, int n, double* H, long long ldh, double* X, long long ldx,
-                                double* ws, DevStatus* st, float* ws32 = nullptr, bool df32_update = false);
+                                double* ws, DevStatus* st, float* ws32 = nullptr, int mode = kCholF64);
+sks_status cholesky_inverse_df32(cudaStream_t stream, int n, const double* H, long long ldh, double* X,
+                                 long long ldx, double* ws, float* ws32, DevStatus* st, bool f32_inverse);
 
 // y_i = alpha * sum_j M[i][j] x_j / xdiv_j  (tri 0 full, 1 lower, 2 upper);
 // mode 1 epilogue: y_i = (z_i - value) / (nu2 * lam_i).

@@ -437,9 +437,10 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
     }
     SKS_TRY(add_diagonal(stream, d, P->H, d, 0.0, lam, P->nu2));
     // Cholesky form: the apply is X^T X, positive definite for any nonsingular
-    // X, so the inverse factor may be formed in float32 (mixed form).
-    // the mixed form factors with double-float trailing updates (inv32 marks it)
-    SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st, P->inv32, P->inv32 != nullptr));
+    // X, so the mixed form (inv32 marks it) merges the inverse factor in
+    // float32 after a double-float factorisation.
+    SKS_TRY(cholesky_and_inverse(stream, d, P->H, d, P->X, d, P->chol_ws, P->st, P->inv32,
+                                 P->inv32 != nullptr ? kCholDf32InvF32 : kCholF64));
     SKS_TRY(transpose<double>(stream, d, d, P->X, d, P->Xt, d));
   } else {
     if (tc) {
@@ -459,8 +460,9 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
     }
     SKS_TRY(add_diagonal(stream, m, P->H, m, P->nu2, nullptr, 0.0));
     // Woodbury form: the apply subtracts two terms of size ~1/nu^2, so W^{-1}
-    // must be accurate: float64 inverse.
-    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st, nullptr, P->inv32 != nullptr));
+    // must be accurate: float64, or double-float in the mixed form.
+    SKS_TRY(cholesky_and_inverse(stream, m, P->H, m, P->X, m, P->chol_ws, P->st, P->inv32,
+                                 P->inv32 != nullptr ? kCholDf32 : kCholF64));
     SKS_TRY(transpose<double>(stream, m, m, P->X, m, P->Xt, m));
     SKS_TRY(transpose<double>(stream, m, d, Y64, ldy, P->Yt, m));
   }
@@ -1947,15 +1949,24 @@ extern "C" sks_status sks_precond_workspace_size(const sks_problem* p, int64_t m
 
 extern "C" sks_status sks_precond_build(sks_precond** out, const sks_sketch* s, const sks_problem* p, void* ws,
                                         size_t ws_bytes, void* stream) {
+  return sks_precond_build_ex(out, s, p, SKS_PLAIN_F64, ws, ws_bytes, stream);
+}
+
+extern "C" sks_status sks_precond_build_ex(sks_precond** out, const sks_sketch* s, const sks_problem* p,
+                                           sks_precision precision, void* ws, size_t ws_bytes, void* stream) {
   if (!out || !s) return fail(SKS_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   SKS_TRY(validate_problem(p));
   if (p->d != s->d) return fail(SKS_ERR_INVALID_ARG, "sketch and problem disagree on d");
+  if (precision != SKS_PLAIN_F64 && precision != SKS_MIXED_REFINED)
+    return fail(SKS_ERR_INVALID_ARG, "unknown precision");
+  const bool mixed = precision == SKS_MIXED_REFINED;
+  if (mixed && p->dtype != SKS_F32) return fail(SKS_ERR_INVALID_ARG, "the mixed factorisation needs a float32 A");
   if (!ws || ws_bytes < precond_ws_bytes(p, s->m_max)) return fail(SKS_ERR_WORKSPACE, "preconditioner workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
   sks_precond* P = new (std::nothrow) sks_precond();
   if (!P) return fail(SKS_ERR_INVALID_ARG, "host allocation failed");
-  sks_status r = precond_init(P, p, s->m_max, ws, ws_bytes, nullptr);
+  sks_status r = precond_init(P, p, s->m_max, ws, ws_bytes, nullptr, mixed);
   if (r == SKS_OK) {
     cudaMemsetAsync(P->st, 0, sizeof(DevStatus), st);
     check_lambda_kernel<<<(int)((p->d + 255) / 256), 256, 0, st>>>((int)p->d, p->lambda_diag, P->st);

@@ -20,7 +20,7 @@ import synthetic  # noqa: E402
 def test_workload_generators_run_on_cpu(name):
     wl = dict(bench.WORKLOADS[name])
     assert wl["config"] in synthetic.CONFIGS
-    assert wl["method"] in ("pcg", "ihs") and wl["kind"] in ("srht", "gaussian", "sjlt", "rademacher")
+    assert wl["method"] in ("pcg", "ihs") and wl["kind"] in ("srht", "gaussian", "sjlt", "rademacher", "gaussian-e4m3")
     if wl.get("batched"):
         specs = synthetic.batched_specs(8, seed=0)
         assert all(s["n"] >= 4 * s["d"] for s in specs)

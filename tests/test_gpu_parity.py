@@ -617,6 +617,49 @@ def test_tensor_core_preconditioner_spectrally_close_to_oracle(m, d, nu, kind):
     assert ev[0] >= 1.0 / (1.0 + eps) and ev[-1] <= 1.0 / (1.0 - eps), (ev[0], ev[-1], eps)
 
 
+@pytest.mark.parametrize("m,d,nu,kind", [(300, 256, 0.1, "gaussian"), (700, 520, 1e-2, "rademacher"),
+                                         (64, 64, 1e-2, "srht"), (2000, 1100, 3e-2, "sjlt"),
+                                         (100, 300, 1e-2, "rademacher"), (1, 64, 0.5, "gaussian"),
+                                         (129, 200, 0.5, "srht"), (1000, 1500, 3e-2, "gaussian")])
+def test_mixed_factorisation_matches_float64(m, d, nu, kind):
+    # The mixed form factors the same tensor-core Gram matrix G (H_S for m >= d,
+    # W_S for m < d) as the plain build, but in double-float arithmetic, with the
+    # inverse factor merged in float32 (m >= d) or double-float (m < d).  With
+    # P64 from the float64 build standing for G's exact preconditioner, the
+    # eigenvalues of P64^{-1/2} P P64^{-1/2} must lie within 1 +- tol, tol a
+    # first-order error estimate with a safety factor of 8 (u = 2^-44 for a
+    # double-float operation chain, 2^-24 for float32, n the order of G):
+    #   m >= d:  8 n u_df kappa(H_S) + 8 n u_32 sqrt(kappa(H_S))   (|X L - I| ~ n u kappa(L))
+    #   m <  d:  8 m u_df kappa(W_S)^2  (an error E in W_S^{-1} moves the apply
+    #            (Lambda^{-1}/nu^2)(I - Z^T W_S^{-1} Z) by ||E|| relative to its
+    #            smallest eigenvalue 1/kappa(W_S))
+    # plus 1e-9 for the float64 build.  Blocks of 64: several block columns, a
+    # ragged last block and merges up to 512 are covered.
+    rng = np.random.default_rng(m * 13 + d)
+    n = 3000
+    A = (rng.standard_normal((n, d)) * (0.97 ** np.arange(d))[None, :] / math.sqrt(n)).astype(np.float32)
+    lam = 1 + 9 * rng.random(d)
+    sk = api().Sketch(dev(A.astype(np.float64), torch.float32), nu, dev(lam), kind=kind, m=m, sjlt_s=4, seed=9)
+    P64 = host(api().Preconditioner(sk).apply(dev(np.eye(d))))
+    Pm = host(api().Preconditioner(sk, precision="mixed").apply(dev(np.eye(d))))
+    P64 = 0.5 * (P64 + P64.T)
+    Pm = 0.5 * (Pm + Pm.T)
+    G = np.linalg.inv(P64)
+    G = 0.5 * (G + G.T)
+    Lg = np.linalg.cholesky(G)
+    ev = np.linalg.eigvalsh(Lg.T @ Pm @ Lg)
+    Y = host(sk.matrix())  # scaled S A
+    if m >= d:
+        kappa = np.linalg.cond(G)
+        tol = 8 * d * 2.0 ** -44 * kappa + 8 * d * 2.0 ** -24 * math.sqrt(kappa) + 1e-9
+    else:
+        w = np.linalg.eigvalsh((Y / lam[None, :]) @ Y.T)
+        kappa = (w[-1] + nu ** 2) / nu ** 2
+        tol = 8 * m * 2.0 ** -44 * kappa ** 2 + 1e-9
+    assert tol <= 0.05  # the check is meaningful
+    assert np.all(np.abs(ev - 1.0) <= tol), (ev[0], ev[-1], tol, kappa)
+
+
 # ----------------------------------------------------------------------------- adjoint (a13)
 
 @pytest.mark.parametrize("precision", ["plain", "mixed"])

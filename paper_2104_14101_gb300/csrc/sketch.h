@@ -25,11 +25,15 @@ sks_status gaussian_extend(cudaStream_t stream, const T* A, long long lda, int64
                            size_t split_elems, bool rademacher = false);
 
 // Y (m x d) = S A for the SJLT with s nonzeros per column.  sj_ws (optional,
-// sjlt_gather_ws_elems words) lets larger m gather each sketch row's data rows
-// instead of scattering them.
+// sjlt_gather_ws_elems words for float64, sjlt_table_bytes for float32) lets
+// larger m gather each sketch row's data rows (float64) or keep the sketch
+// rows on chip (float32, s <= 4, m <= 1024) instead of scattering them; st
+// receives a timed-out wait of the on-chip kernel.
 template <typename TA, typename TY>
 sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n, int d, int m, int s, uint64_t seed,
-                     TY* Y, long long ldy, uint32_t* sj_ws = nullptr, size_t sj_ws_elems = 0);
+                     TY* Y, long long ldy, uint32_t* sj_ws = nullptr, size_t sj_ws_elems = 0,
+                     DevStatus* st = nullptr);
 size_t sjlt_gather_ws_elems(int64_t n, int64_t m_max, int s);
+size_t sjlt_table_bytes(int64_t n);
 
 }  // namespace sks

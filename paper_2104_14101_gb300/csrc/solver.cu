@@ -214,6 +214,7 @@ struct SketchSizes {
 SketchSizes sketch_sizes(const sks_problem* p, sks_kind kind, int64_t m_max, int sjlt_s) {
   SketchSizes z;
   if (kind == SKS_SJLT && p->dtype == SKS_F64) z.sj_elems = sjlt_gather_ws_elems(p->n, m_max, std::max(1, sjlt_s));
+  if (kind == SKS_SJLT && p->dtype == SKS_F32) z.sj_elems = (sjlt_table_bytes(p->n) + 3) / 4 + 16;
   const int64_t n_pad = (int64_t)1 << ilog2_ceil(std::max<int64_t>(p->n, 1));
   if (kind == SKS_SRHT) z.b_elems = (size_t)n_pad * p->d;
   z.y_elems = (size_t)m_max * p->d;
@@ -333,7 +334,8 @@ sks_status sketch_to_t(sks_sketch* s, int64_t new_m, cudaStream_t stream) {
     SKS_TRY(gaussian_extend<T>(stream, A, p.lda, p.n, d, s->seed, (int)s->m, (int)(new_m - s->m), Y, s->ldy,
                                (T*)s->gbuf, s->gbuf_elems, (T*)s->split, s->split_elems, s->kind == SKS_RADEMACHER));
   } else {
-    SKS_TRY(sjlt_form<T, T>(stream, A, p.lda, p.n, d, (int)new_m, s->s, s->seed, Y, s->ldy, s->sj, s->sj_elems));
+    SKS_TRY(sjlt_form<T, T>(stream, A, p.lda, p.n, d, (int)new_m, s->s, s->seed, Y, s->ldy, s->sj, s->sj_elems,
+                            s->st));
   }
   s->m = new_m;
   return SKS_OK;

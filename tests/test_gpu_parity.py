@@ -133,9 +133,9 @@ def test_srht_multi_pass_transform(dt, tol):
                                    (4100, 130, 100), (3000, 100, 300), (20000, 1028, 32), (9000, 130, 64),
                                    (7000, 258, 17)])
 def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
-    # small and medium m: float32 partial rows in registers (8, 16, 32 rows of
-    # 4 columns), the column-block kernel (partial rows in shared memory: float64,
-    # float32 past 32 rows or with d not a multiple of 4); d = 2052
+    # small and medium m: float32 partial rows in registers (8, 16 rows of 4
+    # columns, then eight warp groups), the column-block kernel (partial rows in
+    # shared memory: float64, float32 with d not a multiple of 4); d = 2052
     # spans three column blocks of 1024 float32 columns, the last one ragged;
     # n = 20000 takes several 256-row hash batches per CTA; m = 300 is past
     # the shared-memory limit (the L2 scatter).
@@ -146,6 +146,25 @@ def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
     ref = OS.sketch("sjlt", A, m, seed=99, sjlt_s=4)
     scale = np.sqrt(np.sum(A * A, axis=0))[None, :]
     assert float(np.max(np.abs(got - ref) / scale)) < tol
+
+
+@pytest.mark.parametrize("n,d,m,s", [(20000, 1100, 33, 4), (9001, 516, 128, 4), (40000, 260, 200, 4),
+                                     (6000, 4096, 256, 4), (20011, 132, 511, 4), (3000, 1028, 512, 4),
+                                     (12345, 100, 700, 4), (5000, 64, 1024, 4), (9000, 200, 96, 2),
+                                     (9000, 200, 300, 3), (7000, 96, 64, 1)])
+def test_sjlt_warp_group_kernel(n, d, m, s):
+    # float32, 16 < m <= 256, s <= 4: the sketch rows live in the registers of
+    # warp groups (rows g RPG .. (g+1) RPG - 1 of 128 columns per CTA) fed by a
+    # table of the hashed rows sorted by group; m > 256 takes the L2 scatter.
+    # Ragged cases: n not a multiple of the 32-row stage, d not a multiple of
+    # the 128-column block, m below G RPG, s = 1, 2, 3.
+    rng = np.random.default_rng(n + d + m + 7 * s)
+    A = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+    sk = api().Sketch(dev(A, torch.float32), 0.1, dev(np.ones(d)), kind="sjlt", m=m, sjlt_s=s, seed=123)
+    got = host(sk.matrix())
+    ref = OS.sketch("sjlt", A, m, seed=123, sjlt_s=s)
+    scale = np.sqrt(np.sum(A * A, axis=0))[None, :]
+    assert float(np.max(np.abs(got - ref) / scale)) < 1e-5
 
 
 @pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])

@@ -616,7 +616,7 @@ sks_status sjlt_block_launch(cudaStream_t stream, const T* A, long long lda, int
   return SKS_OK;
 }
 
-// ---------------------------------------------------------------- SJLT by warp groups (float32, 16 < m <= 256)
+// ---------------------------------------------------------------- SJLT by warp groups (float32, 16 < m <= 128)
 // The s target rows of every data row are hashed once per pass into a table
 // (one record per 32 data rows: the (row, local sketch row, sign) entries
 // sorted by warp group, and the group offsets).  A CTA owns a block of 128
@@ -802,6 +802,171 @@ sks_status sjlt_grp_launch(cudaStream_t stream, const float* A, long long lda, i
   return SKS_OK;
 }
 
+// ---------------------------------------------------------------- SJLT by warp groups, rows in shared memory (128 < m <= 512)
+// Same table, ring and column-block schedule as sjlt_grp_kernel, but each of
+// the 16 consumer warps keeps its RPG = m / 16 sketch rows (of 32 VEC columns)
+// in a private shared-memory slab and applies an entry as a read-modify-write
+// of one slab row.  Two entries are taken per step (their rows may coincide:
+// then both go into one update), so two row updates are in flight per warp.
+constexpr int kSlG = 16;  // consumer warps
+
+template <int VEC>
+__global__ void __launch_bounds__((kSlG + 1) * 32, 1) sjlt_slab_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                       const uint16_t* __restrict__ tab,
+                                                                       int64_t nstages, int d, uint32_t m, int rpg,
+                                                                       int64_t ncb, float scale, float* __restrict__ Y,
+                                                                       long long ldy, DevStatus* st) {
+  using V = typename std::conditional<VEC == 4, float4, typename std::conditional<VEC == 2, float2, float>::type>::type;
+  constexpr int W = 32 * VEC;
+  constexpr int kTile = kSgRows * W;
+  extern __shared__ __align__(128) unsigned char sl_smem[];
+  float* tiles = reinterpret_cast<float*>(sl_smem);
+  uint16_t* recs = reinterpret_cast<uint16_t*>(sl_smem + (size_t)kSgStages * kTile * sizeof(float));
+  uint64_t* full = reinterpret_cast<uint64_t*>(sl_smem + (size_t)kSgStages * (kTile * sizeof(float) + 2 * kSgRecU16));
+  uint64_t* empty = full + kSgStages;
+  float* slab = reinterpret_cast<float*>(empty + kSgStages);  // kSlG * rpg rows of W floats
+  __shared__ int abort_flag;
+  __shared__ long long issued;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t cb = (int64_t)blockIdx.x % ncb, idx = (int64_t)blockIdx.x / ncb;
+  const int64_t k = (int64_t)gridDim.x / ncb + (cb < (int64_t)gridDim.x % ncb ? 1 : 0);
+  const int64_t s0 = nstages * idx / k, s1 = nstages * (idx + 1) / k;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSgStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kSlG);
+    }
+    abort_flag = 0;
+    issued = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == kSlG) {  // producer
+    if (lane == 0) {
+      long long it = 0;
+      for (int64_t sg = s0; sg < s1; ++sg, ++it) {
+        const int slot = (int)(it % kSgStages);
+        if (it >= kSgStages && !mbar_wait(&empty[slot], (uint32_t)((it / kSgStages - 1) & 1), st, 44)) break;
+        if (*(volatile int*)&abort_flag) break;
+        mbar_arrive_expect_tx(&full[slot], (uint32_t)(kTile * sizeof(float) + 2 * kSgRecU16));
+        tma_load_2d(tiles + (size_t)slot * kTile, &tmap, &full[slot], (int)(cb * W), (int)(sg * kSgRows));
+        bulk_load(recs + slot * kSgRecU16, tab + sg * kSgRecU16, 2 * kSgRecU16, &full[slot]);
+      }
+      issued = it;
+    }
+  } else {
+    float* my = slab + (size_t)warp * rpg * W + lane * VEC;  // this warp's rows, this lane's columns
+    for (int r = 0; r < rpg; ++r)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) my[r * W + e] = 0.f;
+    long long it = 0;
+    bool ok = true;
+    for (int64_t sg = s0; sg < s1; ++sg, ++it) {
+      const int slot = (int)(it % kSgStages);
+      if (!mbar_wait_warp(&full[slot], (uint32_t)((it / kSgStages) & 1), st, 45)) {
+        if (lane == 0) atomicExch(&abort_flag, 1);
+        ok = false;
+        break;
+      }
+      const uint16_t* rec = recs + slot * kSgRecU16;
+      const int e0 = rec[128 + warp], e1 = rec[129 + warp];
+      const float* tile = tiles + (size_t)slot * kTile + lane * VEC;
+      int e = e0;
+      for (; e + 1 < e1; e += 2) {
+        const uint32_t a = rec[e], b = rec[e + 1];
+        const uint32_t ra = (a >> 5) & 1023u, rb = (b >> 5) & 1023u;
+        const V va = *reinterpret_cast<const V*>(tile + (a & 31u) * W);
+        const V vb = *reinterpret_cast<const V*>(tile + (b & 31u) * W);
+        V sa = *reinterpret_cast<const V*>(my + ra * W);
+        V sb = *reinterpret_cast<const V*>(my + rb * W);
+        const float ga = (a & 0x8000u) ? -1.f : 1.f, gb = (b & 0x8000u) ? -1.f : 1.f;
+        const bool same = ra == rb;
+        float* pa = reinterpret_cast<float*>(&sa);
+        float* pb = reinterpret_cast<float*>(&sb);
+        const float* qa = reinterpret_cast<const float*>(&va);
+        const float* qb = reinterpret_cast<const float*>(&vb);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          pa[q] = fmaf(ga, qa[q], pa[q]);
+          pb[q] = fmaf(gb, qb[q], pb[q]);
+          if (same) pa[q] = fmaf(gb, qb[q], pa[q]);
+        }
+        *reinterpret_cast<V*>(my + ra * W) = sa;
+        if (!same) *reinterpret_cast<V*>(my + rb * W) = sb;
+      }
+      if (e < e1) {
+        const uint32_t a = rec[e];
+        const uint32_t ra = (a >> 5) & 1023u;
+        const V va = *reinterpret_cast<const V*>(tile + (a & 31u) * W);
+        V sa = *reinterpret_cast<const V*>(my + ra * W);
+        const float ga = (a & 0x8000u) ? -1.f : 1.f;
+        float* pa = reinterpret_cast<float*>(&sa);
+        const float* qa = reinterpret_cast<const float*>(&va);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) pa[q] = fmaf(ga, qa[q], pa[q]);
+        *reinterpret_cast<V*>(my + ra * W) = sa;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+    const int c = (int)cb * W + lane * VEC;
+    if (ok && s0 < s1 && c < d) {
+      for (int r = 0; r < rpg; ++r) {
+        const uint32_t row = (uint32_t)(warp * rpg + r);
+        if (row >= m) break;
+        float* y = Y + (long long)row * ldy + c;
+        if constexpr (VEC == 4)
+          atomicAdd(reinterpret_cast<float4*>(y), make_float4(my[r * W] * scale, my[r * W + 1] * scale,
+                                                              my[r * W + 2] * scale, my[r * W + 3] * scale));
+        else if constexpr (VEC == 2)
+          atomicAdd(reinterpret_cast<float2*>(y), make_float2(my[r * W] * scale, my[r * W + 1] * scale));
+        else
+          atomicAdd(y, my[r * W] * scale);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == kSlG * 32) {
+    for (long long t = issued > kSgStages ? issued - kSgStages : 0; t < issued; ++t)
+      mbar_wait(&full[t % kSgStages], (uint32_t)((t / kSgStages) & 1), st, 46);
+  }
+}
+
+template <int VEC>
+size_t sjlt_slab_smem(int rpg) {
+  return (size_t)kSgStages * ((size_t)kSgRows * 32 * VEC * sizeof(float) + 2 * kSgRecU16) + 2 * kSgStages * 8 +
+         (size_t)kSlG * rpg * 32 * VEC * sizeof(float);
+}
+
+template <int VEC>
+sks_status sjlt_slab_launch(cudaStream_t stream, const float* A, long long lda, int64_t n, int d, int m, int s_eff,
+                            uint64_t seed, float* Y, long long ldy, uint16_t* tab, DevStatus* st) {
+  constexpr int W = 32 * VEC;
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int64_t nstages = (n + kSgRows - 1) / kSgRows;
+  const int rpg = (m + kSlG - 1) / kSlG;
+  sjlt_table_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nstages + 7) / 8, (int64_t)sms * 16)), 256, 0,
+                      stream>>>(n, (uint32_t)m, s_eff, make_key(seed), rpg, kSlG, tab, nstages);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  CUtensorMap tmap;
+  SKS_TRY(make_tmap_2d(&tmap, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), (uint64_t)n, (uint64_t)d,
+                       (uint64_t)lda, (uint32_t)W, (uint32_t)kSgRows));
+  const size_t smem = sjlt_slab_smem<VEC>(rpg);
+  auto kern = sjlt_slab_kernel<VEC>;
+  SKS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (kSlG + 1) * 32, smem));
+  const int64_t ncb = (d + W - 1) / W;
+  int64_t grid = std::max<int64_t>(ncb, (int64_t)sms * std::max(1, per_sm));
+  grid = std::min<int64_t>(grid, ncb * nstages);
+  kern<<<(unsigned)grid, (kSlG + 1) * 32, smem, stream>>>(tmap, tab, nstages, d, (uint32_t)m, rpg, ncb,
+                                                          (float)(1.0 / std::sqrt((double)s_eff)), Y, ldy, st);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
+
 }  // namespace
 
 size_t sjlt_table_bytes(int64_t n) { return (size_t)((n + kSgRows - 1) / kSgRows) * 2 * kSgRecU16; }
@@ -935,7 +1100,8 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
       if (al16 && d % 4 == 0 && lda % 4 == 0 && ldy % 4 == 0) {
         if (m <= 8) return sjlt_reg_launch<8, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
         if (m <= 16) return sjlt_reg_launch<16, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
-        // 16 < m <= 256: sketch rows in the registers of warp groups (one pass over A from HBM)
+        // 16 < m <= 256: sketch rows in the registers or shared memory of warp groups (one pass over A
+        // from HBM)
         if (m <= 256 && s_eff <= kSgMaxS && sj_ws && sj_ws_elems * sizeof(uint32_t) >= sjlt_table_bytes(n) &&
             n < (1ll << 31)) {
           const float* Af = (const float*)A;
@@ -946,8 +1112,15 @@ sks_status sjlt_form(cudaStream_t stream, const TA* A, long long lda, int64_t n,
           if (m <= 32) return sjlt_grp_launch<4, 8>(stream, Af, lda, n, d, m, s_eff, seed, Yf, ldy, tab, st);
           if (m <= 64) return sjlt_grp_launch<8, 8>(stream, Af, lda, n, d, m, s_eff, seed, Yf, ldy, tab, st);
           if (m <= 128) return sjlt_grp_launch<16, 8>(stream, Af, lda, n, d, m, s_eff, seed, Yf, ldy, tab, st);
-          return sjlt_grp_launch<16, 16>(stream, Af, lda, n, d, m, s_eff, seed, Yf, ldy, tab, st);
+          // 128 < m <= 512: rows in per-warp shared-memory slabs (7.4 / 9.8 ms at m = 256 / 512; registers
+          // of 16 warps: 10.2 ms at m = 256; the scatter: 12.7 / 11.5 ms; slabs of 32 columns at m = 1024:
+          // 17.0 ms against the scatter's 10.9)
+          return sjlt_slab_launch<4>(stream, Af, lda, n, d, m, s_eff, seed, Yf, ldy, tab, st);
         }
+        if (m <= 512 && s_eff <= kSgMaxS && sj_ws && sj_ws_elems * sizeof(uint32_t) >= sjlt_table_bytes(n) &&
+            n < (1ll << 31))
+          return sjlt_slab_launch<2>(stream, (const float*)A, lda, n, d, m, s_eff, seed, (float*)Y, ldy,
+                                     reinterpret_cast<uint16_t*>(sj_ws), st);
         if (m <= 32) return sjlt_reg_launch<32, 4>(stream, (const float*)A, lda, n, d, m, s_eff, seed, Y, ldy);
       }
       if (fits(4)) return sjlt_block_launch<TY, 4>(stream, At, lda, n, d, m, s_eff, seed, Y, ldy, bytes(4));

@@ -153,9 +153,10 @@ def test_sjlt_small_sketch_column_blocks(dt, tol, n, d, m):
                                      (12345, 100, 700, 4), (5000, 64, 1024, 4), (9000, 200, 96, 2),
                                      (9000, 200, 300, 3), (7000, 96, 64, 1)])
 def test_sjlt_warp_group_kernel(n, d, m, s):
-    # float32, 16 < m <= 256, s <= 4: the sketch rows live in the registers of
-    # warp groups (rows g RPG .. (g+1) RPG - 1 of 128 columns per CTA) fed by a
-    # table of the hashed rows sorted by group; m > 256 takes the L2 scatter.
+    # float32, 16 < m <= 512, s <= 4: the sketch rows live in the registers
+    # (m <= 128) or per-warp shared-memory slabs (m <= 512) of warp groups
+    # (rows g RPG .. (g+1) RPG - 1 of 128 or 64 columns per CTA) fed by a table
+    # of the hashed rows sorted by group; m > 512 takes the L2 scatter.
     # Ragged cases: n not a multiple of the 32-row stage, d not a multiple of
     # the 128-column block, m below G RPG, s = 1, 2, 3.
     rng = np.random.default_rng(n + d + m + 7 * s)

@@ -20,7 +20,8 @@ using namespace apcore;
 
 // The stand-alone pass: one pass per launch; partial sums summed by apass_finalize.
 template <typename TA, typename TX, int G, int QMAX, int K, bool XG = false>
-__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 && QMAX <= 4) ? 2 : 1)
+__global__ void __launch_bounds__(kThreads,
+                                  (sizeof(TA) == 4 && QMAX <= 4 && (sizeof(TX) == 4 || (!XG && K == 1))) ? 2 : 1)
     apass_kernel(const __grid_constant__ CUtensorMap tmap, ApassArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   ApassCore<TA, TX, G, QMAX, K, XG> core;
@@ -140,9 +141,10 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   rows = std::min(rows, 256);
   rows = rows / ng * ng;
   const DeviceInfo& di = device_info();
-  // the float32 pass (HBM-bound, latency-limited at one CTA per SM) runs two
-  // CTAs per SM, each with half the shared memory
-  const int ctas_per_sm = (a_f32 && vec_f32 && !wide) ? 2 : 1;
+  // the float32 pass (HBM-bound, latency-limited at one CTA per SM) and the
+  // double-float pass with one right-hand side (bound by its float32 operation
+  // chains) run two CTAs per SM, each with half the shared memory
+  const int ctas_per_sm = (a_f32 && !wide && (vec_f32 || k == 1)) ? 2 : 1;
   const size_t budget = (di.smem_optin ? di.smem_optin : 232448) / ctas_per_sm - (ctas_per_sm > 1 ? 1024 : 0);
   const size_t fixed = ((size_t)2 * 8 * kRC * k * xsz + 127) / 128 * 128;
   const size_t stage_bytes = ((size_t)rows * row_bytes);

@@ -58,6 +58,17 @@ sks_status hess_apply_noalloc(const sks_problem* p, const double* x, double* y, 
   const int64_t kb = p->k == 8 ? 8 : 1;
   ApassPlan plan;
   SKS_TRY(apass_plan(std::max<int64_t>(p->n, 1), p->d, kb, f32, vec32, &plan));
+  {  // a plan of two CTAs per SM falls back to one per SM (each CTA keeps one set of partial sums)
+     // when its partials would not fit; what does not fit then is rejected below
+    const size_t esz = vec32 ? 4 : 8;
+    const size_t per_cta = plan.partial_elems / (size_t)plan.grid;  // elements
+    const int sms = device_info().sms > 0 ? device_info().sms : 152;
+    const size_t room = kNoallocScratchBytes - 4096 - (vec32 ? (size_t)2 * p->d * kb * sizeof(float) : 0);
+    if (plan.partial_elems * esz > room && plan.grid > sms) {
+      plan.grid = sms;
+      plan.partial_elems = (size_t)plan.grid * per_cta;
+    }
+  }
   // Layout inside the static scratch: status | partial sums | float32 copies of x and y.
   Carver c(nullptr, 0);
   c.take<DevStatus>(1);

@@ -362,7 +362,8 @@ size_t precond_ws_bytes(const sks_problem* p, int64_t m_max) {
   if (p->dtype == SKS_F32) c.take<double>((size_t)m_max * d);  // Y64
   c.take<double>(cholesky_ws_elems((int)d));
   c.take<double>(std::min<size_t>(4 * d * d, (size_t)1 << 24));
-  c.take<double>(2 * std::max<size_t>(d, (size_t)m_max));
+  c.take<double>(std::max<size_t>(2 * d, (size_t)m_max));  // t1 (also 2 d column factors during a build)
+  c.take<double>(std::max<size_t>(d, (size_t)m_max));      // t2
   if (p->dtype == SKS_F32) {
     const size_t e = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
     for (int i = 0; i < 4; ++i) c.take<__nv_bfloat16>(e + 64);
@@ -388,7 +389,7 @@ sks_status precond_init(sks_precond* P, const sks_problem* p, int64_t m_max, voi
   P->chol_ws = c.take<double>(cholesky_ws_elems((int)d));
   P->split_elems = std::min<size_t>(4 * d * d, (size_t)1 << 24);
   P->split = c.take<double>(P->split_elems);
-  P->t1 = c.take<double>(std::max<size_t>(d, (size_t)m_max));
+  P->t1 = c.take<double>(std::max<size_t>(2 * d, (size_t)m_max));
   P->t2 = c.take<double>(std::max<size_t>(d, (size_t)m_max));
   if (p->dtype == SKS_F32) {
     P->bf_elems = std::max(tc_gram_split_elems((int)m_max, (int)d), tc_gram_split_elems((int)d, (int)m_max));
@@ -450,9 +451,11 @@ sks_status precond_factor(sks_precond* P, const sks_sketch* s, double nu, const 
       // uses Y_eff = Z' Lambda^{1/2}, so the preconditioner is exactly the
       // inverse of c^2 Y_eff^T Y_eff + nu^2 Lambda.
       int Kp = 0;
-      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, false, lam, P->bf[0], P->bf[1], P->rmax, &Kp));
+      // colfac: 1/sqrt(lambda) and sqrt(lambda) in the two apply vectors (free during a build)
+      SKS_TRY(tc_split(stream, (const float*)s->Y, s->ldy, m, d, false, lam, P->bf[0], P->bf[1], P->rmax, &Kp,
+                       P->t1));
       SKS_TRY(tc_gram(stream, m, m, Kp, P->bf[0], P->bf[1], P->bf[0], P->bf[1], P->c2, 0.0, P->H, m, true, P->st));
-      SKS_TRY(tc_unsplit(stream, P->bf[0], P->bf[1], m, d, Kp, lam, P->Y64, d));
+      SKS_TRY(tc_unsplit(stream, P->bf[0], P->bf[1], m, d, Kp, P->t1 + d, P->Y64, d));
     } else {
       scale_cols_kernel<<<blocks_for((long long)m * d), 256, 0, stream>>>(m, d, Y64, ldy, lam, P->Ys, d);
       note_launch();

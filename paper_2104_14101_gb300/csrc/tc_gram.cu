@@ -308,40 +308,63 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // Operand element (orow, k) of X (transpose: X[k][orow], else X[orow][k]),
 // divided by sqrt(colscale[c]) in float64 and rounded once to float32.
+// isq: 1/sqrt(colscale) per column (float64, precomputed once), or NULL.
 __device__ __forceinline__ float operand_elem(const float* __restrict__ X, long long ldx, int rows, int cols,
-                                             int transpose, const double* __restrict__ colscale, int orow, int k) {
+                                             int transpose, const double* __restrict__ isq, int orow, int k) {
   const int r = transpose ? k : orow;
   const int c = transpose ? orow : k;
   if (r >= rows || c >= cols) return 0.f;
   float v = X[(long long)r * ldx + c];
-  if (colscale) v = (float)((double)v / sqrt(colscale[c]));
+  if (isq) v = (float)((double)v * isq[c]);
   return v;
 }
 
+// isq[c] = 1 / sqrt(colscale[c]), sq[c] = sqrt(colscale[c])
+__global__ void colfac_kernel(int cols, const double* __restrict__ colscale, double* __restrict__ isq,
+                              double* __restrict__ sq) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const double s = sqrt(colscale[c]);
+  sq[c] = s;
+  isq[c] = 1.0 / s;
+}
+
 // Maximum |element| of every operand row (as float bits; non-negative floats
-// order like their bit patterns).  Grid-stride over the input in its own
-// layout, so reads are coalesced for both orientations.
+// order like their bit patterns).  Operand rows along the input's rows
+// (transpose = 0): one warp per row, no atomics; along its columns: a
+// grid-stride walk in the input's layout (coalesced) with one atomic each.
 __global__ void rowmax_kernel(const float* __restrict__ X, long long ldx, int rows, int cols, int transpose,
-                              const double* __restrict__ colscale, unsigned* __restrict__ rmax) {
+                              const double* __restrict__ isq, unsigned* __restrict__ rmax) {
+  if (!transpose) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += nw) {
+      float mx = 0.f;
+      for (int c = lane; c < cols; c += 32) mx = fmaxf(mx, fabsf(operand_elem(X, ldx, rows, cols, 0, isq, (int)r, c)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) rmax[r] = __float_as_uint(mx);
+    }
+    return;
+  }
   const long long total = (long long)rows * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / cols), c = (int)(e % cols);
-    const int orow = transpose ? c : r, k = transpose ? r : c;
-    const float v = fabsf(operand_elem(X, ldx, rows, cols, transpose, colscale, orow, k));
-    atomicMax(&rmax[orow], __float_as_uint(v));
+    const float v = fabsf(operand_elem(X, ldx, rows, cols, 1, isq, c, r));
+    atomicMax(&rmax[c], __float_as_uint(v));
   }
 }
 
 // hi/lo slices against the row's maximum exponent (see the file comment).
 __global__ void split_scaled_kernel(const float* __restrict__ X, long long ldx, int rows, int cols, int transpose,
-                                    const double* __restrict__ colscale, const unsigned* __restrict__ rmax,
+                                    const double* __restrict__ isq, const unsigned* __restrict__ rmax,
                                     int out_rows, int Kp, __nv_bfloat16* __restrict__ Hh,
                                     __nv_bfloat16* __restrict__ Hl) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)out_rows * Kp) return;
   const int orow = (int)(e / Kp), k = (int)(e % Kp);
-  const float v = operand_elem(X, ldx, rows, cols, transpose, colscale, orow, k);
+  const float v = operand_elem(X, ldx, rows, cols, transpose, isq, orow, k);
   const float mx = __uint_as_float(rmax[orow]);
   float h = 0.f, l = 0.f;
   if (mx > 0.f) {
@@ -357,14 +380,14 @@ __global__ void split_scaled_kernel(const float* __restrict__ X, long long ldx, 
 // Y_eff[r][c] = (hi + lo)[r][c] * sqrt(scale[c])  (float64), the sketch that
 // the split operands represent exactly.
 __global__ void unsplit_kernel(const __nv_bfloat16* __restrict__ Hh, const __nv_bfloat16* __restrict__ Hl, int rows,
-                               int cols, int Kp, const double* __restrict__ colscale, double* __restrict__ Y,
+                               int cols, int Kp, const double* __restrict__ sq, double* __restrict__ Y,
                                long long ldy) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)rows * cols) return;
   const int r = (int)(e / cols), c = (int)(e % cols);
   const long long k = (long long)r * Kp + c;
   double v = (double)__bfloat162float(Hh[k]) + (double)__bfloat162float(Hl[k]);
-  if (colscale) v *= sqrt(colscale[c]);
+  if (sq) v *= sq[c];
   Y[(long long)r * ldy + c] = v;
 }
 
@@ -864,10 +887,10 @@ __global__ void split8_t_kernel(const float* __restrict__ A, long long lda, long
 }  // namespace
 
 sks_status tc_unsplit(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, int rows, int cols,
-                      int Kp, const double* colscale, double* Y, long long ldy) {
+                      int Kp, const double* sq, double* Y, long long ldy) {
   const long long total = (long long)rows * cols;
   if (total > 0) {
-    unsplit_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(Hh, Hl, rows, cols, Kp, colscale, Y, ldy);
+    unsplit_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(Hh, Hl, rows, cols, Kp, sq, Y, ldy);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
   }
@@ -880,19 +903,28 @@ size_t tc_gram_split_elems(int out_rows, int K) {
 }
 
 sks_status tc_split(cudaStream_t stream, const float* X, long long ldx, int rows, int cols, bool transpose,
-                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, unsigned* rmax, int* Kp_out) {
+                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, unsigned* rmax, int* Kp_out,
+                    double* colfac) {
   const int out_rows = transpose ? cols : rows;
   const int K = transpose ? rows : cols;
   const int Kp = (K + TBK - 1) / TBK * TBK;
   const long long total = (long long)out_rows * Kp;
+  if (colscale && !colfac) return fail(SKS_ERR_INVALID_ARG, "tc_split: column scaling needs colfac");
+  const double* isq = nullptr;
+  if (colscale && cols > 0) {
+    colfac_kernel<<<(cols + 255) / 256, 256, 0, stream>>>(cols, colscale, colfac, colfac + cols);
+    note_launch();
+    isq = colfac;
+  }
   if (total > 0) {
     SKS_CUDA_TRY(cudaMemsetAsync(rmax, 0, (size_t)out_rows * sizeof(unsigned), stream));
     const long long in_total = (long long)rows * cols;
-    const unsigned g1 = (unsigned)std::max<long long>(1, std::min<long long>((in_total + 255) / 256, 4096));
-    rowmax_kernel<<<g1, 256, 0, stream>>>(X, ldx, rows, cols, transpose ? 1 : 0, colscale, rmax);
+    const unsigned g1 = transpose ? (unsigned)std::max<long long>(1, std::min<long long>((in_total + 255) / 256, 4096))
+                                  : (unsigned)std::max<long long>(1, std::min<long long>((rows + 7) / 8, 4096));
+    rowmax_kernel<<<g1, 256, 0, stream>>>(X, ldx, rows, cols, transpose ? 1 : 0, isq, rmax);
     note_launch();
     split_scaled_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(
-        X, ldx, rows, cols, transpose ? 1 : 0, colscale, rmax, out_rows, Kp, Hh, Hl);
+        X, ldx, rows, cols, transpose ? 1 : 0, isq, rmax, out_rows, Kp, Hh, Hl);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
   }

@@ -13,16 +13,20 @@ size_t tc_gram_split_elems(int out_rows, int K);
 // X (rows x cols float32, leading dimension ldx) -> bfloat16 hi/lo slices of
 // shape out_rows x Kp (Kp = K rounded up to 64, zero padded), where the
 // operand is X (out_rows = rows, K = cols) or X^T (transpose: out_rows =
-// cols, K = rows); optional division of column c of X by sqrt(colscale[c]).
-// Each operand row is split against its own maximum exponent so that the
-// tensor-core products are exact (tc_gram.cu).  rmax: out_rows scratch words.
+// cols, K = rows); optional division of column c of X by sqrt(colscale[c])
+// (then colfac, 2 cols doubles, receives 1/sqrt(colscale) and sqrt(colscale)
+// for tc_unsplit).  Each operand row is split against its own maximum
+// exponent so that the tensor-core products are exact (tc_gram.cu).  rmax:
+// out_rows scratch words.
 sks_status tc_split(cudaStream_t stream, const float* X, long long ldx, int rows, int cols, bool transpose,
-                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, unsigned* rmax, int* Kp_out);
+                    const double* colscale, __nv_bfloat16* Hh, __nv_bfloat16* Hl, unsigned* rmax, int* Kp_out,
+                    double* colfac = nullptr);
 
-// Y (rows x cols float64) = (Hh + Hl) * diag(sqrt(colscale)): the matrix the
-// split operands represent exactly (colscale may be NULL).
+// Y (rows x cols float64) = (Hh + Hl) * diag(sq): the matrix the split
+// operands represent exactly (sq = the second half of tc_split's colfac, or
+// NULL for no scaling).
 sks_status tc_unsplit(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, int rows, int cols,
-                      int Kp, const double* colscale, double* Y, long long ldy);
+                      int Kp, const double* sq, double* Y, long long ldy);
 
 // C = alpha * (Ah + Al)(Bh + Bl)^T + beta * C (float64 C, M x N); operands
 // M x Kp and N x Kp bfloat16 row-major; lower: only C's lower triangle (M == N).

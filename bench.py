@@ -259,7 +259,10 @@ def sketch_phase_roofline(kind, st, n, d, esize, peak_gbs):
     gbs = st["sketch_passes"] * per_pass / (st["ms_sketch"] * 1e-3) / 1e9
     return {"bound": "hbm (read of A per pass); larger m: L2 read-modify-write", "achieved": gbs, "peak": peak_gbs,
             "unit": "GB/s", "frac": gbs / peak_gbs, "passes": int(st["sketch_passes"]), "ms": st["ms_sketch"],
-            "bytes_per_pass": per_pass}
+            "bytes_per_pass": per_pass,
+            # a phase of several kernels: its DRAM traffic is not one ncu counter (the per-kernel captures
+            # under profiles/ show each pass reading A once)
+            "traffic": None}
 
 
 def host64(A, rows=None):
@@ -667,8 +670,10 @@ def run_ours(args, wl, world, rank, local):
         if rs:
             ap_step_ms = ap_ms / max(1, len(stats))
             if rs["ms"] > ap_step_ms:
-                line["roofline"] = dict(rs, kernel="SJLT sketch phase (sjlt_reg_kernel for m <= 32, "
-                                                   "sjlt_scatter_kernel for m >= 64): CUDA events around each pass",
+                line["roofline"] = dict(rs, kernel="SJLT sketch phase (sjlt_reg_kernel for m <= 16, sjlt_grp_kernel "
+                                                   "for 16 < m <= 128 (sketch rows in registers), sjlt_slab_kernel for "
+                                                   "128 < m <= 512 (rows in shared memory), sjlt_scatter_kernel for "
+                                                   "m > 512 (L2 atomics)): CUDA events around each pass",
                                         share_of_step=rs["ms"] / ms)
                 line["roofline_apass"] = dict(roofline, share_of_step=ap_step_ms / ms)
             else:

@@ -14,7 +14,11 @@
 //                           waits on another); CTA 0 stores L_kk^{-1}, the
 //                           others form their rows of the panel
 //                           L_ik = H_ik L_kk^{-T} = H_ik (L_kk^{-1})^T;
-//   syrk_df32_planes_kernel the trailing update H_ij -= L_ik L_jk^T (lower tiles).
+//   trailing update       H_ij -= L_ik L_jk^T on the lower part: on the tensor
+//                           cores from order kTcSyrkMin up (tc_syrk_df32: each
+//                           row of the panel split into six bfloat16 integer
+//                           slices, the slice products summed exactly per level),
+//                           else syrk_df32_planes_kernel on the float32 pipe.
 // Then X from the diagonal-block inverses by recursive merging,
 //   inv([A 0; B C]) = [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}],
 // in float32 (Cholesky form: the apply X^T X is positive definite for any
@@ -28,12 +32,14 @@
 #include <algorithm>
 
 #include "dense.h"
+#include "tc_gram.h"
 
 namespace sks {
 
 namespace {
 
 constexpr int NB = 64;       // block size of the factorisation
+constexpr int kTcSyrkMin = 256;  // trailing matrices from this order up go to the tensor cores
 constexpr int kCT = 256;     // threads of the factor and update kernels
 
 struct F2 {
@@ -554,7 +560,8 @@ sks_status cholesky_inverse_df32(cudaStream_t stream, int n, const double* H, lo
   float* R = Dl + (size_t)nblk * NB * NB;             // X32, or the X planes
   float* Hh = ws32;
   float* Hl = ws32 + (size_t)n * n;
-  float* T = ws32 + (size_t)2 * n * n;                // merge scratch: 2 n^2 + 64 floats
+  float* T = ws32 + (size_t)2 * n * n;                // merge (and trailing-update) scratch: 2 n^2 + 64 floats
+  const size_t T_bytes = ((size_t)2 * n * n + 64) * sizeof(float);
   const int sms = device_info().sms > 0 ? device_info().sms : 152;
   diag_scale_kernel<<<1, 256, 0, stream>>>(n, H, ldh, sexp);
   note_launch();
@@ -576,11 +583,16 @@ sks_status cholesky_inverse_df32(cudaStream_t stream, int n, const double* H, lo
     if (rest > 0) {
       const long long pan = (long long)(k0 + nb) * ld + k0;
       const long long tr = (long long)(k0 + nb) * ld + k0 + nb;
-      const int tb = (rest + NB - 1) / NB;
-      syrk_df32_planes_kernel<<<(unsigned)(tb * (tb + 1) / 2), kCT, kSySmem, stream>>>(rest, nb, Hh + pan, Hl + pan,
-                                                                                      Hh + tr, Hl + tr, ld);
-      note_launch();
-      SKS_CUDA_TRY(cudaGetLastError());
+      if (nb == NB && rest >= kTcSyrkMin && T_bytes >= tc_syrk_ws_bytes(rest)) {
+        // full 64-column panels of a large trailing matrix: the tensor cores (exact slice products)
+        SKS_TRY(tc_syrk_df32(stream, rest, Hh + pan, Hl + pan, ld, Hh + tr, Hl + tr, ld, T, T_bytes, st));
+      } else {
+        const int tb = (rest + NB - 1) / NB;
+        syrk_df32_planes_kernel<<<(unsigned)(tb * (tb + 1) / 2), kCT, kSySmem, stream>>>(rest, nb, Hh + pan,
+                                                                                        Hl + pan, Hh + tr, Hl + tr, ld);
+        note_launch();
+        SKS_CUDA_TRY(cudaGetLastError());
+      }
     }
   }
   // X' = L'^{-1} of the scaled factor from the diagonal-block inverses by merging

@@ -114,6 +114,18 @@ SKS_DEV void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 16 consecutive float32 columns, without the wait (tmem_ld_wait()
+// before the registers are read): several loads in flight at once
+SKS_DEV void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+SKS_DEV void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // Double-float accumulation (Knuth's TwoSum): (s, e) += x.
 SKS_DEV void df_add(float& s, float& e, float x) {
   const float t = s + x;
@@ -884,7 +896,302 @@ __global__ void split8_t_kernel(const float* __restrict__ A, long long lda, long
   }
 }
 
+
+// ------------------------------------------------------------------ double-float trailing update
+// T -= P P^T on the lower part of the trailing matrix of the double-float
+// Cholesky (chol.cu), P = the current panel (rest x 64, float32 hi/lo planes).
+// Each row of P is split against its own exponent e_i (|P_i.| < 2^e_i) into
+// kSySlices bfloat16 slices of integers, P_iq = sum_s q_s 2^(e_i - 8 s) up to
+// 2^(e_i - 49), |q_1| <= 256 and |q_s| <= 128 after it.  The products of slices
+// s and t of rows i and j are integers times 2^(e_i + e_j - 8 (s + t)); all
+// pairs of one level l = s + t (2 .. kSySlices + 1; deeper levels are below
+// 2^-54 of the leading one) sum in one float32 TMEM accumulator, exactly
+// (< 2^23 for K = 64).  The epilogue scales each level by its power of two,
+// adds the levels smallest first with TwoSum and subtracts the double-float
+// result from T.
+constexpr int kSySlices = 6;
+constexpr int kSyLevels = kSySlices;               // levels 2 .. kSySlices + 1
+constexpr int kSyM = 128, kSyN = 64, kSyK = 64;
+constexpr int kSyATile = kSyM * kSyK * 2;           // 16 KB per slice
+constexpr int kSyBTile = kSyN * kSyK * 2;           // 8 KB per slice
+constexpr int kSyBytes = kSySlices * (kSyATile + kSyBTile);
+constexpr int kSyEpiWarps = 8;
+constexpr int kSyThreads = (2 + kSyEpiWarps) * 32;
+constexpr uint32_t kSyTmemCols = 512;               // kSyLevels accumulators of kSyN columns
+
+// One warp per row of P: the row exponent and the slices (rows past `rest`,
+// up to rest_pad, are zero).  SL: [kSySlices][rest_pad][64] bfloat16.
+__global__ void syrk_slice_kernel(int rest, int rest_pad, const float* __restrict__ Ph, const float* __restrict__ Pl,
+                                  long long ld, __nv_bfloat16* __restrict__ SL, int* __restrict__ ex) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rest_pad; r += nw) {
+    float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
+    if (r < rest) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        h[u] = Ph[(long long)r * ld + lane + 32 * u];
+        l[u] = Pl[(long long)r * ld + lane + 32 * u];
+      }
+    }
+    float mx = fmaxf(fabsf(h[0]), fabsf(h[1]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx >= 0x1p-100f && mx < 0x1p+100f) frexpf(mx, &e);  // mx < 2^e; tinier rows count as zero
+    else mx = 0.f;
+    if (lane == 0) ex[r] = mx > 0.f ? e : -1000;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float sc = mx > 0.f ? __int_as_float((127 + 8 - e) << 23) : 0.f;  // 2^(8 - e), exact
+      float H = h[u] * sc, L = l[u] * sc;
+#pragma unroll
+      for (int s = 0; s < kSySlices; ++s) {
+        const float q = rintf(H);
+        // remainder (H - q) + L as an unevaluated pair; H - q is exact
+        const float a = __fsub_rn(H, q);
+        const float t = __fadd_rn(a, L);
+        const float bb = __fsub_rn(t, a);
+        const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(L, bb));
+        SL[((size_t)s * rest_pad + r) * kSyK + lane + 32 * u] = __float2bfloat16_rn(q);  // an integer <= 256: exact
+        H = t * 256.f;
+        L = err * 256.f;
+      }
+    }
+  }
+}
+
+struct SyrkArgs {
+  int rest, rest_pad;
+  const int* ex;
+  float* Th;
+  float* Tl;
+  long long ldt;
+  DevStatus* st;
+};
+
+__global__ void __launch_bounds__(kSyThreads, 1) tc_syrk_kernel(const __grid_constant__ CUtensorMap mA,
+                                                                const __grid_constant__ CUtensorMap mB, SyrkArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sa = smem;                                 // kSySlices A tiles (128 rows)
+  unsigned char* sb = smem + (size_t)kSySlices * kSyATile;  // kSySlices B tiles (64 rows)
+  __shared__ uint64_t full, done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  // lower tiles (tm, tn), tn <= 2 tm + 1, from the linear block index b = tm (tm + 1) + tn
+  const int b = (int)blockIdx.x;
+  int tm = (int)((sqrtf(4.f * (float)b + 1.f) - 1.f) * 0.5f);
+  while ((tm + 1) * (tm + 2) <= b) ++tm;
+  while (tm * (tm + 1) > b) --tm;
+  const int tn = b - tm * (tm + 1);
+  const int row0 = tm * kSyM, col0 = tn * kSyN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(&full, 1);
+    mbar_init(&done, 1);
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(kSyTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&full, (uint32_t)kSyBytes);
+#pragma unroll
+      for (int s = 0; s < kSySlices; ++s) {
+        tma_load_2d(sa + (size_t)s * kSyATile, &mA, &full, 0, s * g.rest_pad + row0);
+        tma_load_2d(sb + (size_t)s * kSyBTile, &mB, &full, 0, s * g.rest_pad + col0);
+      }
+      if (!mbar_wait(&full, 0u, g.st, 47)) abort_flag = 1;  // every copy has landed before exit
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      if (mbar_wait(&full, 0u, g.st, 48) && !abort_flag) {
+        tc_fence_after();
+        constexpr uint32_t idesc = idesc_bf16_f32(kSyM, kSyN);
+#pragma unroll 1
+        for (int lv = 2; lv <= kSySlices + 1; ++lv) {
+          const uint32_t d_tmem = tmem + (uint32_t)((lv - 2) * kSyN);
+          bool first = true;
+          for (int s = 1; s <= lv - 1; ++s) {
+            const int t = lv - s;
+            if (s > kSySlices || t > kSySlices) continue;
+            const uint64_t ad = smem_desc_sw128(sa + (size_t)(s - 1) * kSyATile);
+            const uint64_t bd = smem_desc_sw128(sb + (size_t)(t - 1) * kSyBTile);
+#pragma unroll
+            for (int k = 0; k < kSyK / 16; ++k) {
+              umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, (first && k == 0) ? 0u : 1u);
+            }
+            first = false;
+          }
+        }
+        umma_commit(&done);
+        if (!mbar_wait(&done, 0u, g.st, 49)) abort_flag = 1;
+      } else {
+        abort_flag = 1;
+      }
+    }
+  } else {
+    const int ew = warp - 2;           // 0..7
+    const int quad = warp & 3;         // TMEM lane quadrant this warp may access
+    const int cblk = ew >> 2;          // columns [32 cblk, 32 cblk + 32)
+    const int row = quad * 32 + lane;  // tile row of this thread
+    // the tile's row and column exponents, fetched while the MMAs run
+    __shared__ int exr[kSyM], exc[kSyN];
+    {
+      const int t = threadIdx.x - 64;
+      if (t < kSyM) exr[t] = row0 + t < g.rest_pad ? g.ex[row0 + t] : -1000;
+      else if (t < kSyM + kSyN) exc[t - kSyM] = col0 + t - kSyM < g.rest_pad ? g.ex[col0 + t - kSyM] : -1000;
+    }
+    named_bar_sync(1, kSyEpiWarps * 32);
+    const bool ok = mbar_wait_warp(&done, 0u, g.st, 50);
+    tc_fence_after();
+    const int ei = exr[row];
+    // per thread (a TMEM lane = a tile row): the double-float update of 32 columns, staged in the
+    // operand buffers (free once the MMAs are done) so that the read-modify-write of T below runs
+    // along rows (coalesced)
+    float* uh = reinterpret_cast<float*>(smem);                 // [kSyM][kSyN + 1]
+    float* ul = uh + kSyM * (kSyN + 1);
+    const bool live = ok && !abort_flag;
+    if (live) {
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        const int c0 = cblk * 32 + half * 16;
+        uint32_t vr[kSyLevels][16];
+#pragma unroll
+        for (int lv = 0; lv < kSyLevels; ++lv)
+          tmem_ld16_nowait(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(lv * kSyN + c0), vr[lv]);
+        tmem_ld_wait();
+        float v[kSyLevels][16];
+#pragma unroll
+        for (int lv = 0; lv < kSyLevels; ++lv)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[lv][i] = __uint_as_float(vr[lv][i]);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int ej = exc[c0 + jj];
+          float sh = 0.f, sl = 0.f;
+          if (ei > -1000 && ej > -1000) {
+            // levels smallest first: term_l = acc_l 2^(e_i + e_j - 8 l), l = 2 .. kSySlices + 1
+#pragma unroll
+            for (int lv = kSyLevels - 1; lv >= 0; --lv) {
+              const int E = ei + ej - 8 * (lv + 2);
+              // exact: an integer below 2^24 times a power of two (terms below the float range vanish)
+              const float x = (E >= -126 && E <= 127) ? v[lv][jj] * __int_as_float((127 + E) << 23)
+                                                       : (E > 127 ? ldexpf(v[lv][jj], E) : 0.f);
+              const float t = __fadd_rn(sh, x);
+              const float bb = __fsub_rn(t, sh);
+              sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+              sh = t;
+            }
+          }
+          uh[row * (kSyN + 1) + c0 + jj] = sh;
+          ul[row * (kSyN + 1) + c0 + jj] = sl;
+        }
+      }
+    }
+    named_bar_sync(1, kSyEpiWarps * 32);
+    if (live) {
+      // T_ij -= (uh + ul)_ij for the tile's lower part: warp ew takes rows ew, ew + 8, ...; lane = column.
+      // All loads of T are issued before any store (independent addresses: one round trip per batch).
+      constexpr int kRows = kSyM / kSyEpiWarps;  // 16 rows per warp
+      constexpr int kCh = kSyN / 32;             // 2 column chunks
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        float th[kRows / 2][kCh], tl[kRows / 2][kCh];
+        bool in[kRows / 2][kCh];
+#pragma unroll
+        for (int q = 0; q < kRows / 2; ++q)
+#pragma unroll
+          for (int c = 0; c < kCh; ++c) {
+            const int r = ew + kSyEpiWarps * (half * (kRows / 2) + q);
+            const int ri = row0 + r, gj = col0 + c * 32 + lane;
+            in[q][c] = ri < g.rest && gj < g.rest && gj <= ri;
+            const long long gidx = (long long)ri * g.ldt + gj;
+            th[q][c] = in[q][c] ? g.Th[gidx] : 0.f;
+            tl[q][c] = in[q][c] ? g.Tl[gidx] : 0.f;
+          }
+#pragma unroll
+        for (int q = 0; q < kRows / 2; ++q)
+#pragma unroll
+          for (int c = 0; c < kCh; ++c) {
+            if (!in[q][c]) continue;
+            const int r = ew + kSyEpiWarps * (half * (kRows / 2) + q);
+            const int ri = row0 + r, gj = col0 + c * 32 + lane;
+            const float sh = uh[r * (kSyN + 1) + c * 32 + lane], sl = ul[r * (kSyN + 1) + c * 32 + lane];
+            const float s = __fsub_rn(th[q][c], sh);
+            const float bb = __fsub_rn(s, th[q][c]);
+            const float err = __fsub_rn(__fsub_rn(th[q][c], __fsub_rn(s, bb)), __fadd_rn(sh, bb));
+            const float lo = __fadd_rn(err, __fsub_rn(tl[q][c], sl));
+            const float nh = __fadd_rn(s, lo);
+            const long long gidx = (long long)ri * g.ldt + gj;
+            g.Th[gidx] = nh;
+            g.Tl[gidx] = __fsub_rn(lo, __fsub_rn(nh, s));
+          }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSyTmemCols) : "memory");
+  }
+}
+
 }  // namespace
+
+size_t tc_syrk_ws_bytes(int n) {
+  const size_t rp = (size_t)(n + kSyM - 1) / kSyM * kSyM;
+  return (size_t)kSySlices * rp * kSyK * sizeof(__nv_bfloat16) + rp * sizeof(int) + 256;
+}
+
+sks_status tc_syrk_df32(cudaStream_t stream, int rest, const float* Ph, const float* Pl, long long ld, float* Th,
+                        float* Tl, long long ldt, void* ws, size_t ws_bytes, DevStatus* st) {
+  if (rest <= 0) return SKS_OK;
+  if (ws_bytes < tc_syrk_ws_bytes(rest)) return fail(SKS_ERR_WORKSPACE, "tc_syrk: workspace too small");
+  const int rest_pad = (rest + kSyM - 1) / kSyM * kSyM;
+  unsigned char* base = (unsigned char*)(((uintptr_t)ws + 127) & ~(uintptr_t)127);
+  __nv_bfloat16* SL = (__nv_bfloat16*)base;
+  int* ex = (int*)(base + (size_t)kSySlices * rest_pad * kSyK * sizeof(__nv_bfloat16));
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  syrk_slice_kernel<<<(unsigned)std::min(sms * 8, (rest_pad + 7) / 8), 256, 0, stream>>>(rest, rest_pad, Ph, Pl, ld,
+                                                                                          SL, ex);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  CUtensorMap mA, mB;
+  SKS_TRY(make_tmap_2d_bf16_sw128(&mA, SL, (uint64_t)kSySlices * rest_pad, kSyK, kSyK, kSyM));
+  SKS_TRY(make_tmap_2d_bf16_sw128(&mB, SL, (uint64_t)kSySlices * rest_pad, kSyK, kSyK, kSyN));
+  SyrkArgs g;
+  g.rest = rest;
+  g.rest_pad = rest_pad;
+  g.ex = ex;
+  g.Th = Th;
+  g.Tl = Tl;
+  g.ldt = ldt;
+  g.st = st;
+  const int T = rest_pad / kSyM;
+  const size_t smem = (size_t)kSyBytes + 1024;
+  static bool attr_set = false;  // the size never changes; set once per process
+  if (!attr_set) {
+    SKS_CUDA_TRY(cudaFuncSetAttribute(tc_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  tc_syrk_kernel<<<(unsigned)(T * (T + 1)), kSyThreads, smem, stream>>>(mA, mB, g);
+  note_launch();
+  SKS_CUDA_TRY(cudaGetLastError());
+  return SKS_OK;
+}
 
 sks_status tc_unsplit(cudaStream_t stream, const __nv_bfloat16* Hh, const __nv_bfloat16* Hl, int rows, int cols,
                       int Kp, const double* sq, double* Y, long long ldy) {

@@ -34,6 +34,15 @@ sks_status tc_gram(cudaStream_t stream, int M, int N, int Kp, const __nv_bfloat1
                    const __nv_bfloat16* Bh, const __nv_bfloat16* Bl, double alpha, double beta, double* C,
                    long long ldc, bool lower, DevStatus* st);
 
+// ---- double-float trailing update of the mixed factorisation on the tensor cores
+// T -= P P^T (lower part, rest x rest, float32 hi/lo planes with leading
+// dimension ldt), P = rest x 64 hi/lo planes (leading dimension ld): P sliced
+// per row into six bfloat16 integer slices, the slice products summed exactly
+// per level in TMEM (tc_gram.cu).  ws: tc_syrk_ws_bytes(rest) bytes.
+size_t tc_syrk_ws_bytes(int n);
+sks_status tc_syrk_df32(cudaStream_t stream, int rest, const float* Ph, const float* Pl, long long ld, float* Th,
+                        float* Tl, long long ldt, void* ws, size_t ws_bytes, DevStatus* st);
+
 // ---- Gaussian sketch of a float32 A on the tensor cores (K4)
 // Padded K (data rows rounded up to 64) of the split A^T.
 int tc_gauss_kp(long long n);

@@ -174,25 +174,40 @@ __global__ void split_lower_kernel(int n, const double* __restrict__ H, long lon
 }
 
 // ---------------------------------------------------------------- diagonal block + panel
-// Thread t = 16 ty + tx owns the diagonal-block entries (ty + 16a, tx + 16b),
-// b <= a, in registers: A (the matrix being factored; column k becomes L's
-// column k at step k) and W (the inverse factor, built row by row:
-// W starts as I; at step k row k is final after scaling by 1/L_kk, and
-// W_ij -= L_ik X_kj for i > k, j <= k).  Column k of A and row k of W are
-// read by everyone from two shared buffers, written by their owners at the
-// end of step k - 1: one barrier per step.
+// The 64 x 64 diagonal block is factored by 16-column sub-blocks, all in
+// shared memory (hi/lo planes A and X):
+//   (1) the 16 x 16 diagonal sub-block: 16 right-looking steps, one barrier
+//       each; the columns are scaled by rd_k = 1/sqrt(pivot_k) afterwards, and
+//       its inverse W is built alongside (W = I; at step k,
+//       W_ij -= L_ik (W_kj rd_k) for i > k >= j; row k is scaled by rd_k);
+//   (2) the rows of the block below the sub-block: L = A X_cc^T;
+//   (3) the block's own trailing update A_ij -= sum_q L_iq L_jq.
+// Then the off-diagonal 16 x 16 blocks of X = L^{-1} in three rounds,
+// X_rc = -X_rr sum_{c <= q < r} L_rq X_qc.
+constexpr int kSub = 16;
+constexpr int kSubTri = kSub * (kSub + 1) / 2;  // 136 entries of a lower 16 x 16 block
+
+SKS_DEV void tri_index(int t, int& i, int& j) {  // t -> (i, j), j <= i, row-major lower triangle
+  i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  j = t - i * (i + 1) / 2;
+}
+
 template <int PR>
 __global__ void __launch_bounds__(kCT) chol_panel_df32_kernel(float* __restrict__ Hh, float* __restrict__ Hl,
                                                                long long ld, int n, int k0, int nb,
                                                                float* __restrict__ Dh, float* __restrict__ Dl,
                                                                DevStatus* st) {
   extern __shared__ float cp_smem[];
-  float (*Xh)[NB + 1] = (float (*)[NB + 1])cp_smem;  // the block's inverse factor, for the panel
+  float (*Ah)[NB + 1] = (float (*)[NB + 1])cp_smem;  // the block, becoming L
+  float (*Al)[NB + 1] = Ah + NB;
+  float (*Xh)[NB + 1] = Al + NB;                      // its inverse factor
   float (*Xl)[NB + 1] = Xh + NB;
   float (*Ph)[NB + 1] = Xl + NB;                      // PR panel rows
   float (*Pl)[NB + 1] = Ph + PR;
-  __shared__ float colh[2][NB], coll[2][NB], rowh[2][NB], rowl[2][NB];
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  __shared__ float rdh[NB], rdl[NB];
+  const int tid = threadIdx.x;
   const bool panel = blockIdx.x > 0;
   const int r0 = k0 + nb + ((int)blockIdx.x - 1) * PR;
   const int prow = panel ? min(PR, n - r0) : 0;
@@ -210,112 +225,176 @@ __global__ void __launch_bounds__(kCT) chol_panel_df32_kernel(float* __restrict_
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  float Ah[4][4], Al[4][4], Wh[4][4], Wl[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b <= a; ++b) {
-      const int i = ty + 16 * a, j = tx + 16 * b;
-      const bool in = j <= i && i < nb;
-      const long long g = (long long)(k0 + i) * ld + k0 + j;
-      Ah[a][b] = in ? Hh[g] : (i == j ? 1.f : 0.f);
-      Al[a][b] = in ? Hl[g] : 0.f;
-      Wh[a][b] = i == j ? 1.f : 0.f;
-      Wl[a][b] = 0.f;
-    }
-  if (tx == 0) {  // column 0 of A (entries (i, 0) sit at b = 0)
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const F2 v = f2_two_sum(Ah[a][0], Al[a][0]);
-      colh[0][ty + 16 * a] = v.h;
-      coll[0][ty + 16 * a] = v.l;
-    }
+  for (int e = tid; e < NB * NB; e += kCT) {  // identity padding past nb
+    const int i = e / NB, j = e % NB;
+    const bool in = j <= i && i < nb;
+    const long long g = (long long)(k0 + i) * ld + k0 + j;
+    Ah[i][j] = in ? Hh[g] : (i == j ? 1.f : 0.f);
+    Al[i][j] = in ? Hl[g] : 0.f;
+    Xh[i][j] = 0.f;
+    Xl[i][j] = 0.f;
   }
-  if (ty == 0) {  // row 0 of W is e_0
-    rowh[0][tx] = tx == 0 ? 1.f : 0.f;
-    rowl[0][tx] = 0.f;
-  }
-  __syncthreads();
-  for (int k = 0; k < nb; ++k) {
-    const int cur = k & 1, nxt = cur ^ 1;
-    F2 piv = {colh[cur][k], coll[cur][k]};
-    if (!(piv.h > 0.f) || !(piv.h < INFINITY)) {
-      if (tid == 0 && blockIdx.x == 0) raise_status(st, SKS_ERR_NOT_PD, 21, k0 + k);
-      piv = {1.f, 0.f};
-    }
-    const F2 r = f2_rsqrt(piv);
-    F2 li[4], lj[4], xk[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = ty + 16 * a;
-      li[a] = i > k ? f2_mul({colh[cur][i], coll[cur][i]}, r) : F2{0.f, 0.f};
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = tx + 16 * b;
-      lj[b] = j > k ? f2_mul({colh[cur][j], coll[cur][j]}, r) : F2{0.f, 0.f};
-      xk[b] = j <= k ? f2_mul({rowh[cur][j], rowl[cur][j]}, r) : F2{0.f, 0.f};
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = ty + 16 * a;
-      if (i > k) {
-#pragma unroll
-        for (int b = 0; b <= a; ++b) {
-          const int j = tx + 16 * b;
-          if (j <= i) {
-            if (j > k) f2_acc<true>(Ah[a][b], Al[a][b], li[a], lj[b]);  // trailing update of A
-            else f2_acc<true>(Wh[a][b], Wl[a][b], li[a], xk[b]);        // W_ij -= L_ik X_kj
-          }
+  // this thread's entries of a 16 x 16 lower triangle (two sets: Cholesky and inverse)
+  int ti0, tj0;
+  tri_index(tid < kSubTri ? tid : tid - kSubTri, ti0, tj0);
+  const bool tinv = tid >= kSubTri;  // threads 136..255 take inverse entries 0..119
+  int ti1 = 0, tj1 = 0;
+  if (tid < 2 * kSubTri - kCT) tri_index(kCT - kSubTri + tid, ti1, tj1);  // inverse entries 120..135
+  const bool has1 = tid < 2 * kSubTri - kCT;
+  for (int c = 0; c < NB / kSub; ++c) {
+    const int c0 = kSub * c;
+    if (tid < kSub) Xh[c0 + tid][c0 + tid] = 1.f;  // W = I
+    __syncthreads();
+    for (int k = 0; k < kSub; ++k) {
+      const int kk = c0 + k;
+      F2 piv = {Ah[kk][kk], Al[kk][kk]};
+      if (!(piv.h > 0.f) || !(piv.h < INFINITY)) {
+        if (tid == 0 && blockIdx.x == 0) raise_status(st, SKS_ERR_NOT_PD, 21, k0 + kk);
+        piv = {1.f, 0.f};
+      }
+      const F2 r = f2_rsqrt(piv);
+      if (tid == 0) {
+        rdh[kk] = r.h;
+        rdl[kk] = r.l;
+      }
+      if (!tinv) {  // Cholesky entry (i, j): A_ij -= (A_ik r)(A_jk r) for j > k
+        if (tj0 > k) {
+          const F2 li = f2_mul({Ah[c0 + ti0][kk], Al[c0 + ti0][kk]}, r);
+          const F2 lj = f2_mul({Ah[c0 + tj0][kk], Al[c0 + tj0][kk]}, r);
+          f2_acc<true>(Ah[c0 + ti0][c0 + tj0], Al[c0 + ti0][c0 + tj0], li, lj);
         }
+      } else if (ti0 > k && tj0 <= k) {  // inverse entry: W_ij -= (A_ik r)(W_kj r)
+        const F2 li = f2_mul({Ah[c0 + ti0][kk], Al[c0 + ti0][kk]}, r);
+        const F2 xk = f2_mul({Xh[kk][c0 + tj0], Xl[kk][c0 + tj0]}, r);
+        f2_acc<true>(Xh[c0 + ti0][c0 + tj0], Xl[c0 + ti0][c0 + tj0], li, xk);
+      }
+      if (has1 && ti1 > k && tj1 <= k) {
+        const F2 li = f2_mul({Ah[c0 + ti1][kk], Al[c0 + ti1][kk]}, r);
+        const F2 xk = f2_mul({Xh[kk][c0 + tj1], Xl[kk][c0 + tj1]}, r);
+        f2_acc<true>(Xh[c0 + ti1][c0 + tj1], Xl[c0 + ti1][c0 + tj1], li, xk);
+      }
+      __syncthreads();
+    }
+    // scale: L_ij = A_ij rd_j (j <= i), X_ij = W_ij rd_i
+    if (!tinv) {
+      const F2 v = f2_mul({Ah[c0 + ti0][c0 + tj0], Al[c0 + ti0][c0 + tj0]}, {rdh[c0 + tj0], rdl[c0 + tj0]});
+      Ah[c0 + ti0][c0 + tj0] = v.h;
+      Al[c0 + ti0][c0 + tj0] = v.l;
+    } else {
+      const F2 v = f2_mul({Xh[c0 + ti0][c0 + tj0], Xl[c0 + ti0][c0 + tj0]}, {rdh[c0 + ti0], rdl[c0 + ti0]});
+      Xh[c0 + ti0][c0 + tj0] = v.h;
+      Xl[c0 + ti0][c0 + tj0] = v.l;
+    }
+    if (has1) {
+      const F2 v = f2_mul({Xh[c0 + ti1][c0 + tj1], Xl[c0 + ti1][c0 + tj1]}, {rdh[c0 + ti1], rdl[c0 + ti1]});
+      Xh[c0 + ti1][c0 + tj1] = v.h;
+      Xl[c0 + ti1][c0 + tj1] = v.l;
+    }
+    __syncthreads();
+    const int below = NB - c0 - kSub;  // rows of the block under the sub-block
+    if (below == 0) break;
+    // (2) L_ij = sum_{q <= j} A_iq X_jq for the rows below (values kept until all are read)
+    F2 res[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int e = tid + u * kCT;
+      res[u] = {0.f, 0.f};
+      if (e < below * kSub) {
+        const int i = c0 + kSub + e / kSub, j = e % kSub;
+        float sh = 0.f, sl = 0.f;
+        for (int q = 0; q <= j; ++q)
+          f2_acc<false>(sh, sl, {Ah[i][c0 + q], Al[i][c0 + q]}, {Xh[c0 + j][c0 + q], Xl[c0 + j][c0 + q]});
+        res[u] = f2_two_sum(sh, sl);
       }
     }
-    // finish column k of L and row k of X; publish column k + 1 and row k + 1
-    const F2 dk = f2_mul(piv, r);  // L_kk = sqrt(pivot)
+    __syncthreads();
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b <= a; ++b) {
-        const int i = ty + 16 * a, j = tx + 16 * b;
-        if (j == k && i >= k) {
-          const F2 v = i == k ? dk : li[a];
-          Ah[a][b] = v.h;
-          Al[a][b] = v.l;
-        }
-        if (i == k && j <= k) {
-          Wh[a][b] = xk[b].h;
-          Wl[a][b] = xk[b].l;
-        }
-        if (j == k + 1 && i >= k + 1) {
-          const F2 v = f2_two_sum(Ah[a][b], Al[a][b]);
-          colh[nxt][i] = v.h;
-          coll[nxt][i] = v.l;
-        }
-        if (i == k + 1 && j <= k + 1) {
-          const F2 v = f2_two_sum(Wh[a][b], Wl[a][b]);
-          rowh[nxt][j] = v.h;
-          rowl[nxt][j] = v.l;
-        }
+    for (int u = 0; u < 3; ++u) {
+      const int e = tid + u * kCT;
+      if (e < below * kSub) {
+        const int i = c0 + kSub + e / kSub, j = e % kSub;
+        Ah[i][c0 + j] = res[u].h;
+        Al[i][c0 + j] = res[u].l;
       }
+    }
+    __syncthreads();
+    // (3) A_ij -= sum_{q in the sub-block} L_iq L_jq, c0 + 16 <= j <= i < 64
+    const int tcount = below * (below + 1) / 2;
+    for (int e = tid; e < tcount; e += kCT) {
+      int i, j;
+      tri_index(e, i, j);
+      i += c0 + kSub;
+      j += c0 + kSub;
+      float sh = Ah[i][j], sl = Al[i][j];
+#pragma unroll 4
+      for (int q = 0; q < kSub; ++q)
+        f2_acc<true>(sh, sl, {Ah[i][c0 + q], Al[i][c0 + q]}, {Ah[j][c0 + q], Al[j][c0 + q]});
+      const F2 v = f2_two_sum(sh, sl);
+      Ah[i][j] = v.h;
+      Al[i][j] = v.l;
+    }
     __syncthreads();
   }
-  // inverse factor into shared memory (zeros above the diagonal)
+  // off-diagonal 16 x 16 blocks of X, round s: (r, c) = (c + s, c)
+  for (int s = 1; s < NB / kSub; ++s) {
+    const int nblk16 = NB / kSub - s;
+    F2 res[3];
+    // T_rc = sum_{c16 <= q < r16} L_iq X_qj   (X_qj = 0 for q < j inside X_cc)
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = ty + 16 * a, j = tx + 16 * b;
-      F2 v = {0.f, 0.f};
-      if (b <= a) v = f2_two_sum(Wh[a][b], Wl[a][b]);
-      if (j > i) v = {0.f, 0.f};
-      Xh[i][j] = v.h;
-      Xl[i][j] = v.l;
+    for (int u = 0; u < 3; ++u) {
+      const int e = tid + u * kCT;
+      res[u] = {0.f, 0.f};
+      if (e < nblk16 * kSub * kSub) {
+        const int c = e / (kSub * kSub), rr = c + s;
+        const int i = rr * kSub + (e / kSub) % kSub, j = c * kSub + e % kSub;
+        float sh = 0.f, sl = 0.f;
+        for (int q = j; q < rr * kSub; ++q) f2_acc<false>(sh, sl, {Ah[i][q], Al[i][q]}, {Xh[q][j], Xl[q][j]});
+        res[u] = f2_two_sum(sh, sl);
+      }
     }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {  // T into the (still zero) X_rc block
+      const int e = tid + u * kCT;
+      if (e < nblk16 * kSub * kSub) {
+        const int c = e / (kSub * kSub), rr = c + s;
+        const int i = rr * kSub + (e / kSub) % kSub, j = c * kSub + e % kSub;
+        Xh[i][j] = res[u].h;
+        Xl[i][j] = res[u].l;
+      }
+    }
+    __syncthreads();
+    // X_rc = -X_rr T_rc   (X_rr lower)
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int e = tid + u * kCT;
+      res[u] = {0.f, 0.f};
+      if (e < nblk16 * kSub * kSub) {
+        const int c = e / (kSub * kSub), rr = c + s;
+        const int il = (e / kSub) % kSub;
+        const int i = rr * kSub + il, j = c * kSub + e % kSub;
+        float sh = 0.f, sl = 0.f;
+        for (int q = 0; q <= il; ++q)
+          f2_acc<true>(sh, sl, {Xh[i][rr * kSub + q], Xl[i][rr * kSub + q]}, {Xh[rr * kSub + q][j], Xl[rr * kSub + q][j]});
+        res[u] = f2_two_sum(sh, sl);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int e = tid + u * kCT;
+      if (e < nblk16 * kSub * kSub) {
+        const int c = e / (kSub * kSub), rr = c + s;
+        const int i = rr * kSub + (e / kSub) % kSub, j = c * kSub + e % kSub;
+        Xh[i][j] = res[u].h;
+        Xl[i][j] = res[u].l;
+      }
+    }
+    __syncthreads();
+  }
   // L_kk itself is not stored: only its inverse is used later (the panel
   // below and the merges read blocks strictly below the diagonal blocks), so
   // the other CTAs may still be reading the diagonal block.
   if (!panel) {
-    __syncthreads();
     for (int e = tid; e < NB * NB; e += kCT) {
       Dh[e] = Xh[e / NB][e % NB];
       Dl[e] = Xl[e / NB][e % NB];
@@ -325,6 +404,7 @@ __global__ void __launch_bounds__(kCT) chol_panel_df32_kernel(float* __restrict_
   cp_async_wait_all();
   __syncthreads();
   // panel rows: L_rj = sum_{q <= j} P_rq X_jq; rows ty + 16a, columns tx + 16b
+  const int ty = tid >> 4, tx = tid & 15;
   constexpr int RA = PR / 16;
   float sh[RA][4], sl[RA][4];
 #pragma unroll
@@ -428,18 +508,26 @@ __global__ void __launch_bounds__(kCT) syrk_df32_planes_kernel(int rest, int kk,
 }
 
 // ---------------------------------------------------------------- double-float GEMM (merges)
-// C = alpha * A B (row-major planes; alpha = +1 or -1).  a_lower: A is lower
-// triangular (terms k > i are zero and skipped); b_lower: B is lower
-// triangular (terms k < j skipped).  64 x 64 tiles, K in steps of 32.
+// C = alpha * A B (row-major planes; alpha = +1 or -1), batched over
+// blockIdx.z with element strides sA, sB, sC.  a_lower: A is lower triangular
+// (terms k > i are zero and skipped); b_lower: B is lower triangular (terms
+// k < j skipped).  64 x 64 tiles, K in steps of 32.
 constexpr int kGK = 32;
 __global__ void __launch_bounds__(kCT) gemm_df32_kernel(int M, int N, int K, const float* __restrict__ Ah_,
-                                                        const float* __restrict__ Al_, long long lda,
+                                                        const float* __restrict__ Al_, long long lda, long long sA,
                                                         const float* __restrict__ Bh_, const float* __restrict__ Bl_,
-                                                        long long ldb, float* __restrict__ Ch, float* __restrict__ Cl,
-                                                        long long ldc, float alpha, int a_lower, int b_lower) {
+                                                        long long ldb, long long sB, float* __restrict__ Ch,
+                                                        float* __restrict__ Cl, long long ldc, long long sC,
+                                                        float alpha, int a_lower, int b_lower) {
   __shared__ float Ash[NB][kGK + 1], Asl[NB][kGK + 1];  // A tile [row][k]
   __shared__ float Bsh[NB][kGK + 1], Bsl[NB][kGK + 1];  // B tile transposed [col][k]
   const int row0 = blockIdx.y * NB, col0 = blockIdx.x * NB;
+  Ah_ += blockIdx.z * sA;  // batch entry z
+  Al_ += blockIdx.z * sA;
+  Bh_ += blockIdx.z * sB;
+  Bl_ += blockIdx.z * sB;
+  Ch += blockIdx.z * sC;
+  Cl += blockIdx.z * sC;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   int kb = 0, ke = K;
   if (a_lower) ke = min(K, row0 + NB);
@@ -523,7 +611,7 @@ __global__ void planes_to_f64_kernel(int n, const float* __restrict__ Xh, const 
 template <int PR>
 static sks_status launch_panel(cudaStream_t stream, int grid, float* Hh, float* Hl, long long ld, int n, int k0, int nb,
                                float* Dh, float* Dl, DevStatus* st) {
-  constexpr size_t smem = (size_t)(2 * NB + 2 * PR) * (NB + 1) * sizeof(float);
+  constexpr size_t smem = (size_t)(4 * NB + 2 * PR) * (NB + 1) * sizeof(float);
   SKS_CUDA_TRY(cudaFuncSetAttribute(chol_panel_df32_kernel<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   chol_panel_df32_kernel<PR><<<grid, kCT, smem, stream>>>(Hh, Hl, ld, n, k0, nb, Dh, Dl, st);
@@ -532,12 +620,13 @@ static sks_status launch_panel(cudaStream_t stream, int grid, float* Hh, float* 
 }
 
 static sks_status gemm_df32(cudaStream_t stream, int M, int N, int K, const float* Ah, const float* Al, long long lda,
-                            const float* Bh, const float* Bl, long long ldb, float* Ch, float* Cl, long long ldc,
-                            float alpha, bool a_lower, bool b_lower) {
-  if (M <= 0 || N <= 0) return SKS_OK;
-  const dim3 grid((unsigned)((N + NB - 1) / NB), (unsigned)((M + NB - 1) / NB));
-  gemm_df32_kernel<<<grid, kCT, 0, stream>>>(M, N, K, Ah, Al, lda, Bh, Bl, ldb, Ch, Cl, ldc, alpha, a_lower ? 1 : 0,
-                                             b_lower ? 1 : 0);
+                            long long sA, const float* Bh, const float* Bl, long long ldb, long long sB, float* Ch,
+                            float* Cl, long long ldc, long long sC, float alpha, bool a_lower, bool b_lower,
+                            int batch) {
+  if (M <= 0 || N <= 0 || batch <= 0) return SKS_OK;
+  const dim3 grid((unsigned)((N + NB - 1) / NB), (unsigned)((M + NB - 1) / NB), (unsigned)batch);
+  gemm_df32_kernel<<<grid, kCT, 0, stream>>>(M, N, K, Ah, Al, lda, sA, Bh, Bl, ldb, sB, Ch, Cl, ldc, sC, alpha,
+                                             a_lower ? 1 : 0, b_lower ? 1 : 0);
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   return SKS_OK;
@@ -604,19 +693,27 @@ sks_status cholesky_inverse_df32(cudaStream_t stream, int n, const double* H, lo
     place_dinv_kernel<<<pg, 256, 0, stream>>>(n, nblk, Dh, nullptr, X32, nullptr, ld);
     note_launch();
     SKS_CUDA_TRY(cudaGetLastError());
-    float* tmp32 = T;
-    const size_t rest32 = (size_t)n * n;
+    // one batched pair of products per level for the full pairs (n2 = b), one for a ragged last pair
     for (int b = NB; b < n; b *= 2) {
-      for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
-        const int n1 = b, n2 = std::min(b, n - r0 - b);
+      const int full = n / (2 * b);
+      const int r0l = full * 2 * b;
+      const int n2l = std::max(0, std::min(b, n - r0l - b));
+      for (int part = 0; part < 2; ++part) {
+        const int cnt = part == 0 ? full : (n2l > 0 ? 1 : 0);
+        if (cnt == 0) continue;
+        const int r0 = part == 0 ? 0 : r0l, n1 = b, n2 = part == 0 ? b : n2l;
+        const long long sd = (long long)2 * b * (ld + 1);  // from one pair's diagonal corner to the next
+        float* tmp32 = T;
+        float* part32 = T + (size_t)cnt * n2 * n1;
+        const size_t rest32 = (size_t)2 * n * n + 64 - (size_t)cnt * n2 * n1;
         const float* Ainv = X32 + (long long)r0 * ld + r0;
         const float* Lb = Hh + (long long)(r0 + b) * ld + r0;
         const float* Cinv = X32 + (long long)(r0 + b) * ld + (r0 + b);
         float* out = X32 + (long long)(r0 + b) * ld + r0;
-        SKS_TRY(gemm<float>(stream, n2, n1, n1, Lb, ld, false, Ainv, ld, false, tmp32, n1, 1.0, 0.0, false, 1, 0, 0, 0,
-                            tmp32 + (size_t)n2 * n1, rest32, 2));
-        SKS_TRY(gemm<float>(stream, n2, n1, n2, Cinv, ld, false, tmp32, n1, false, out, ld, -1.0, 0.0, false, 1, 0, 0,
-                            0, tmp32 + (size_t)n2 * n1, rest32, 1));
+        SKS_TRY(gemm<float>(stream, n2, n1, n1, Lb, ld, false, Ainv, ld, false, tmp32, n1, 1.0, 0.0, false, cnt, sd,
+                            sd, (long long)n2 * n1, part32, rest32, 2));
+        SKS_TRY(gemm<float>(stream, n2, n1, n2, Cinv, ld, false, tmp32, n1, false, out, ld, -1.0, 0.0, false, cnt, sd,
+                            (long long)n2 * n1, sd, part32, rest32, 1));
       }
     }
     planes_to_f64_kernel<<<dim3(gx, (unsigned)n), 256, 0, stream>>>(n, X32, nullptr, ld, sexp, X, ldx);
@@ -631,15 +728,24 @@ sks_status cholesky_inverse_df32(cudaStream_t stream, int n, const double* H, lo
   note_launch();
   SKS_CUDA_TRY(cudaGetLastError());
   for (int b = NB; b < n; b *= 2) {
-    for (int r0 = 0; r0 + b < n; r0 += 2 * b) {
-      const int n1 = b, n2 = std::min(b, n - r0 - b);
+    const int full = n / (2 * b);
+    const int r0l = full * 2 * b;
+    const int n2l = std::max(0, std::min(b, n - r0l - b));
+    for (int part = 0; part < 2; ++part) {
+      const int cnt = part == 0 ? full : (n2l > 0 ? 1 : 0);
+      if (cnt == 0) continue;
+      const int r0 = part == 0 ? 0 : r0l, n1 = b, n2 = part == 0 ? b : n2l;
+      const long long sd = (long long)2 * b * (ld + 1);
       const long long oa = (long long)r0 * ld + r0, ob = (long long)(r0 + b) * ld + r0;
       const long long oc = (long long)(r0 + b) * ld + (r0 + b);
+      const long long st = (long long)n2 * n1;
       float* th = T;
-      float* tl = T + (size_t)n2 * n1;
+      float* tl = T + (size_t)cnt * st;
       // tmp = B A^{-1} (A^{-1} lower), then X_21 = -C^{-1} tmp (C^{-1} lower)
-      SKS_TRY(gemm_df32(stream, n2, n1, n1, Hh + ob, Hl + ob, ld, Xh + oa, Xl + oa, ld, th, tl, n1, 1.f, false, true));
-      SKS_TRY(gemm_df32(stream, n2, n1, n2, Xh + oc, Xl + oc, ld, th, tl, n1, Xh + ob, Xl + ob, ld, -1.f, true, false));
+      SKS_TRY(gemm_df32(stream, n2, n1, n1, Hh + ob, Hl + ob, ld, sd, Xh + oa, Xl + oa, ld, sd, th, tl, n1, st, 1.f,
+                        false, true, cnt));
+      SKS_TRY(gemm_df32(stream, n2, n1, n2, Xh + oc, Xl + oc, ld, sd, th, tl, n1, st, Xh + ob, Xl + ob, ld, sd, -1.f,
+                        true, false, cnt));
     }
   }
   planes_to_f64_kernel<<<dim3(gx, (unsigned)n), 256, 0, stream>>>(n, Xh, Xl, ld, sexp, X, ldx);

@@ -7,6 +7,7 @@
 // these kernels are bound by the float64 FMA pipe; a 64x64 register-tiled
 // CUDA-core GEMM already saturates it.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "dense.h"
@@ -292,11 +293,134 @@ __global__ void gemv_rows_kernel(int rows, int cols, const T* __restrict__ M, lo
 
 // ============================================================================ host
 
+// float32 C = alpha * A B (both row-major, not transposed), batched over
+// blockIdx.z: 128 x 128 tiles, K in steps of 8 through a double-buffered
+// shared-memory pair, each of 256 threads keeping 8 x 8 outputs in registers
+// (rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, likewise the columns), so that a
+// K step is four 16-byte shared loads per 64 FMAs.  a_lower / b_lower skip the
+// K range a triangular operand makes zero.  Needs lda, ldb, ldc and every
+// batch stride to be multiples of 4 floats and 16-byte aligned bases.
+constexpr int SG_M = 128, SG_N = 128, SG_K = 8, SG_T = 256;
+__global__ void __launch_bounds__(SG_T) sgemm128_kernel(int M, int N, int K, const float* __restrict__ A0,
+                                                        long long lda, long long sA, const float* __restrict__ B0,
+                                                        long long ldb, long long sB, float* __restrict__ C0,
+                                                        long long ldc, long long sC, float alpha, int a_lower,
+                                                        int b_lower) {
+  __shared__ __align__(16) float As[2][SG_K][SG_M];
+  __shared__ __align__(16) float Bs[2][SG_K][SG_N];
+  const float* A = A0 + blockIdx.z * sA;
+  const float* B = B0 + blockIdx.z * sB;
+  float* C = C0 + blockIdx.z * sC;
+  const int row0 = blockIdx.y * SG_M, col0 = blockIdx.x * SG_N;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  int kb = 0, ke = K;
+  if (a_lower) ke = min(K, row0 + SG_M);
+  if (b_lower) kb = (min(col0, K) / SG_K) * SG_K;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  // loader roles: A: row tid/2, k (tid%2)*4 .. +4; B: k tid/32, columns (tid%32)*4 .. +4
+  const int ar = tid >> 1, ak = (tid & 1) * 4;
+  const int bk = tid >> 5, bn = (tid & 31) * 4;
+  float4 ra, rb;
+  auto load = [&](int k0) {
+    const int gi = row0 + ar, gk = k0 + ak;
+    ra = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gi < M) {
+      if (gk + 3 < ke) ra = *reinterpret_cast<const float4*>(A + (long long)gi * lda + gk);
+      else {
+        float t[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t[q] = gk + q < ke ? A[(long long)gi * lda + gk + q] : 0.f;
+        ra = make_float4(t[0], t[1], t[2], t[3]);
+      }
+    }
+    const int gkb = k0 + bk, gj = col0 + bn;
+    rb = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gkb < ke) {
+      if (gj + 3 < N) rb = *reinterpret_cast<const float4*>(B + (long long)gkb * ldb + gj);
+      else {
+        float t[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t[q] = gj + q < N ? B[(long long)gkb * ldb + gj + q] : 0.f;
+        rb = make_float4(t[0], t[1], t[2], t[3]);
+      }
+    }
+  };
+  auto store = [&](int buf) {
+    As[buf][ak + 0][ar] = ra.x;
+    As[buf][ak + 1][ar] = ra.y;
+    As[buf][ak + 2][ar] = ra.z;
+    As[buf][ak + 3][ar] = ra.w;
+    *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = rb;
+  };
+  if (kb < ke) {
+    load(kb);
+    store(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = kb; k0 < ke; k0 += SG_K) {
+    const bool more = k0 + SG_K < ke;
+    if (more) load(k0 + SG_K);  // in flight while this step computes
+#pragma unroll
+    for (int k = 0; k < SG_K; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gi = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gi >= M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gj = col0 + h * 64 + tx * 4;
+      float* c = C + (long long)gi * ldc + gj;
+      const float4 v = make_float4(alpha * acc[i][h * 4], alpha * acc[i][h * 4 + 1], alpha * acc[i][h * 4 + 2],
+                                   alpha * acc[i][h * 4 + 3]);
+      if (gj + 3 < N) *reinterpret_cast<float4*>(c) = v;
+      else {
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (gj + q < N) c[q] = vv[q];
+      }
+    }
+  }
+}
+
 template <typename T>
 sks_status gemm(cudaStream_t stream, int M, int N, int K, const T* A, long long lda, bool ta, const T* B,
                 long long ldb, bool tb, T* C, long long ldc, double alpha, double beta, bool lower, int batch,
                 long long sA, long long sB, long long sC, T* split_ws, size_t split_ws_elems, int tri_ops) {
   if (M <= 0 || N <= 0 || batch <= 0) return SKS_OK;
+  if constexpr (std::is_same<T, float>::value) {
+    // the 128 x 128 register-blocked kernel: plain (not transposed) operands, C overwritten
+    const bool al = ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0 && ((uintptr_t)C & 15) == 0 &&
+                    lda % 4 == 0 && ldb % 4 == 0 && ldc % 4 == 0 && sA % 4 == 0 && sB % 4 == 0 && sC % 4 == 0;
+    if (!ta && !tb && !lower && beta == 0.0 && al && K > 0 && M >= 64 && N >= 64) {
+      const dim3 grid((unsigned)((N + SG_N - 1) / SG_N), (unsigned)((M + SG_M - 1) / SG_M), (unsigned)batch);
+      sgemm128_kernel<<<grid, SG_T, 0, stream>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, (float)alpha,
+                                                 (tri_ops & 1) ? 1 : 0, (tri_ops & 2) ? 1 : 0);
+      note_launch();
+      SKS_CUDA_TRY(cudaGetLastError());
+      return SKS_OK;
+    }
+  }
   GemmArgs<T> g;
   g.a_lower = (tri_ops & 1) ? 1 : 0;
   g.b_lower = (tri_ops & 2) ? 1 : 0;

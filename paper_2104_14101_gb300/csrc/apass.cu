@@ -20,8 +20,10 @@ using namespace apcore;
 
 // The stand-alone pass: one pass per launch; partial sums summed by apass_finalize.
 template <typename TA, typename TX, int G, int QMAX, int K, bool XG = false>
-__global__ void __launch_bounds__(kThreads,
-                                  (sizeof(TA) == 4 && QMAX <= 4 && (sizeof(TX) == 4 || (!XG && K == 1))) ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && QMAX <= 4 && !(K == 8 && QMAX > 1) &&
+                                             (sizeof(TX) == 4 || (!XG && K == 1)))
+                                                ? 2
+                                                : 1)
     apass_kernel(const __grid_constant__ CUtensorMap tmap, ApassArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   ApassCore<TA, TX, G, QMAX, K, XG> core;
@@ -128,6 +130,12 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
     else if (nvec <= 128 * qcap) group = 128;
   }
   int qmax = (k == 8) ? (a_f32 ? 1 : 2) : qcap;
+  // eight float32 right-hand sides: four warps per row, two column vectors each (half the
+  // cross-warp reductions per element of a whole-CTA row)
+  if (k == 8 && a_f32 && vec_f32 && nvec <= 128 * 2) {
+    group = 128;
+    qmax = 2;
+  }
   const bool wide = d > 4096;  // more column vectors per thread, one CTA per SM (float64 / double-float: x through L1)
   if (wide) qmax = a_f32 ? kWideQF32 : kWideQF64;
   const int q = (nvec + group - 1) / group;
@@ -144,7 +152,7 @@ sks_status apass_plan(int64_t n, int64_t d, int64_t k, bool a_f32, bool vec_f32,
   // the float32 pass (HBM-bound, latency-limited at one CTA per SM) and the
   // double-float pass with one right-hand side (bound by its float32 operation
   // chains) run two CTAs per SM, each with half the shared memory
-  const int ctas_per_sm = (a_f32 && !wide && (vec_f32 || k == 1)) ? 2 : 1;
+  const int ctas_per_sm = (a_f32 && !wide && (vec_f32 || k == 1) && !(k == 8 && qmax > 1)) ? 2 : 1;
   const size_t budget = (di.smem_optin ? di.smem_optin : 232448) / ctas_per_sm - (ctas_per_sm > 1 ? 1024 : 0);
   const size_t fixed = ((size_t)2 * 8 * kRC * k * xsz + 127) / 128 * 128;
   const size_t stage_bytes = ((size_t)rows * row_bytes);
@@ -204,6 +212,7 @@ sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n,
     return launch_t<double, double, 256, 8, 1>(SKS_APASS_ARGS);
   }
   if (vec_f32) {
+    if (k == 8 && pl.group == 128) return launch_t<float, float, 128, 2, 8>(SKS_APASS_ARGS);
     if (k == 8) return launch_t<float, float, 256, 1, 8>(SKS_APASS_ARGS);
     if (pl.group == 32) return launch_t<float, float, 32, 4, 1>(SKS_APASS_ARGS);
     if (pl.group == 128) return launch_t<float, float, 128, 4, 1>(SKS_APASS_ARGS);

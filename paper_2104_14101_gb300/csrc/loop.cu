@@ -244,7 +244,8 @@ SKS_DEV void reduce_phase(const LoopTask& T, int d, int nparts, const double* u,
 }
 
 template <typename TA, typename TX, int G, int QMAX, int K>
-__global__ void __launch_bounds__(kThreads, (sizeof(TA) == 4 && sizeof(TX) == 4 && QMAX <= 4) ? 2 : 1)
+__global__ void __launch_bounds__(kThreads,
+                                  (sizeof(TA) == 4 && sizeof(TX) == 4 && QMAX <= 4 && !(K == 8 && QMAX > 1)) ? 2 : 1)
     solve_loop_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                  ApassArgs ap, LoopTask T) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -581,6 +582,7 @@ sks_status dispatch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n, int
     SKS_LOOP(double, double, 256, 8, 1);
   }
   if (!vec_f32) return fail(SKS_ERR_UNSUPPORTED, "solver loop: float32 A needs the float32 pass");
+  if (K == 8 && pl.group == 128) SKS_LOOP(float, float, 128, 2, 8);
   if (K == 8) SKS_LOOP(float, float, 256, 1, 8);
   if (pl.group == 32) SKS_LOOP(float, float, 32, 4, 1);
   if (pl.group == 128) SKS_LOOP(float, float, 128, 4, 1);

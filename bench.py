@@ -89,12 +89,16 @@ WORKLOADS = {
               desc="dual formulation (eq. 2), adaptive PCG, SRHT, float64: n=1545 < d=10936, sigma_j=0.995^j, "
                    "nu=1e-2, Lambda=I, b ~ N(0,1), tol 1e-10 on the dual"),
     # C4: the differentiable solve -- forward mixed adaptive PCG on 8 right-hand sides, backward the
-    # adjoint solve with the same preconditioner and the fused dA pass
-    "C4": dict(config="C4", adjoint=True, method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-8,
+    # adjoint solve with the same preconditioner and the fused dA pass.  The configuration names no
+    # embedding: the SRHT (the paper's, Section 2.1); C4-gauss runs the tensor-core Gaussian sketch
+    "C4": dict(config="C4", adjoint=True, method="pcg", kind="srht", m_init=1, m_max=0, tol=1e-8,
                precision="mixed", cpu_rows=1 << 13,
                desc="differentiable solve: n=2^18, d=1024, float32 A, sigma_j=(1+j)^-1/2, 8 right-hand sides, "
-                    "nu=1e-2, Lambda=1+U; forward mixed adaptive PCG (Gaussian, tol 1e-8), backward adjoint solve "
+                    "nu=1e-2, Lambda=1+U; forward mixed adaptive PCG (SRHT, tol 1e-8), backward adjoint solve "
                     "+ dA, db, dnu, dLambda"),
+    "C4-gauss": dict(config="C4", adjoint=True, method="pcg", kind="gaussian", m_init=1, m_max=0, tol=1e-8,
+                     precision="mixed", cpu_rows=1 << 13,
+                     desc="differentiable solve as C4 with the tensor-core Gaussian sketch (bf16 G, split A)"),
     # the paper's synthetic experiments (Section 6, Figs. 1-3): nu swept over 1e-1 .. 1e-4 at n = 2^19,
     # sigma_j = 0.995^j; timed mixed solves, and delta_t / delta_0 and m_t traced in the plain form
     "P-sweep": dict(config="P", d=7000, sweep=True, method="pcg", kind="srht", m_init=1, m_max=1 << 15, tol=1e-8,

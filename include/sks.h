@@ -399,6 +399,10 @@ typedef struct {
   double apass_flops;        /* 4 n d per A-pass of every problem, summed            */
   float ms_gram;             /* the same for the sketched-Hessian (Gram) kernels     */
   double gram_flops;         /* 2 x 64 x 64 per sketch row of every Gram tile        */
+  float ms_factor;           /* the same window for the factorisation kernels        */
+  float ms_apply;            /* ... for the preconditioner apply                     */
+  float ms_rounds;           /* ... for whole rounds (first kernel to the last); the
+                                rest of ms_solve is the setup (H E A of every problem) */
 } sks_batch_info;
 
 sks_status sks_batch_workspace_size(const sks_problem* probs, int count, const sks_opts* o, size_t* bytes);

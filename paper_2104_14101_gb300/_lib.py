@@ -62,7 +62,8 @@ class BatchInfo(C.Structure):
     _fields_ = [("rounds", C.c_int64), ("kernels_per_round", C.c_int64), ("rows_per_unit", C.c_int64),
                 ("ms_setup", C.c_float), ("ms_autotune", C.c_float), ("ms_solve", C.c_float),
                 ("ms_apass", C.c_float), ("apass_flops", C.c_double), ("ms_gram", C.c_float),
-                ("gram_flops", C.c_double)]
+                ("gram_flops", C.c_double), ("ms_factor", C.c_float), ("ms_apply", C.c_float),
+                ("ms_rounds", C.c_float)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

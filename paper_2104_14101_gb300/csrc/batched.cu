@@ -42,6 +42,10 @@ enum : int { PH_INIT = 0, PH_GROW = 1, PH_ITER = 2, PH_DONE = 3, PH_FAIL = 4 };
 // d-vector slots of a problem
 enum : int { V_R = 0, V_RT, V_P, V_HV, V_XP, V_RP, V_RTP, V_U, V_W, V_DINV, kNumVec };
 
+// phase timers: A-pass, sketched-Hessian matrix (Gram), its factorisation,
+// preconditioner apply, the whole round (first kernel to the count kernel)
+enum : int { TK_APASS = 0, TK_GRAM, TK_FACTOR, TK_APPLY, TK_ROUND, kTimers };
+
 constexpr int kTile = 64;           // dense tiles and Cholesky panels
 constexpr int kTP = kTile + 2;      // padded shared-memory row
 constexpr int kMaxD = 1024;         // A-pass: 32 lanes x 32 columns
@@ -89,12 +93,12 @@ struct BCtl {
   const int* pre_ap;   // prefix of ceil(n / rows_per_unit)
   const int* pre_red;  // prefix of ceil(d / 256)
   int* active;         // problems not finished after the round
-  // A-pass accounting: [0] earliest CTA start and [1] latest CTA end of the
-  // round's A-pass kernel (%globaltimer ns), [2] summed durations over rounds;
+  // Phase timers, kTimers x 3: [0] earliest CTA start and [1] latest CTA end
+  // of the phase's kernels in this round (%globaltimer ns), [2] the windows
+  // summed over rounds (TK_* order; null in the autotuner's launches).
   // flops: 4 n d per A-pass unit row block, summed over rounds
-  unsigned long long* tap;
+  unsigned long long* tk;
   double* apass_flops;
-  unsigned long long* tgram;  // the same for the Gram kernel (first start, last end, sum)
   double* gram_flops;         // 2 x 64 x 64 per sketch row (or column) of every Gram unit
   // the graph's while loop: rounds run while some problem is unfinished and
   // fewer than max_rounds have run (the count kernel sets the condition)
@@ -102,6 +106,14 @@ struct BCtl {
   long long* rounds;
   long long max_rounds;
 };
+
+// phase timer window: the first CTA start and the last CTA end of a phase
+SKS_DEV void tk_start(const BCtl& c, int id) {
+  if (threadIdx.x == 0 && c.tk) atomicMin(&c.tk[3 * id], (unsigned long long)global_ns());
+}
+SKS_DEV void tk_stop(const BCtl& c, int id) {
+  if (threadIdx.x == 0 && c.tk) atomicMax(&c.tk[3 * id + 1], (unsigned long long)global_ns());
+}
 
 // largest p with pre[p] <= u  (pre[0] = 0 <= u < pre[P])
 SKS_DEV int find_problem(const int* __restrict__ pre, int P, int u) {
@@ -133,6 +145,7 @@ SKS_DEV int factor_size(const BState& s, const BDesc& q) { return s.form == 0 ? 
 // ------------------------------------------------------------------ round kernels
 
 __global__ void b_begin_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
+  if (blockIdx.x == 0) tk_start(c, TK_ROUND);
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.P) return;
   BState& s = S[p];
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
   __shared__ __align__(16) double As[16][kTP];
   __shared__ __align__(16) double Bs[16][kTP];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  if (threadIdx.x == 0 && c.tgram) atomicMin(&c.tgram[0], (unsigned long long)global_ns());
+  tk_start(c, TK_GRAM);
   double flops = 0.0;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int tu = u / kGramSplit, ks = u - tu * kGramSplit;
@@ -298,15 +311,14 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
         }
       }
   }
-  if (threadIdx.x == 0 && c.tgram) {
-    atomicMax(&c.tgram[1], (unsigned long long)global_ns());
-    if (flops > 0) atomicAdd(c.gram_flops, flops);
-  }
+  tk_stop(c, TK_GRAM);
+  if (threadIdx.x == 0 && c.tk && flops > 0) atomicAdd(c.gram_flops, flops);
 }
 
 // Sum of the slice partials (slice order fixed), scale and diagonal, into M.
 __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
                                                             int total) {
+  tk_start(c, TK_GRAM);
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = find_problem(c.pre_tri, c.P, u);
     const BState s = S[p];
@@ -337,11 +349,13 @@ __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc*
       q.M[(int64_t)gi * d + gj] = v;
     }
   }
+  tk_stop(c, TK_GRAM);
 }
 
 // Panel k, diagonal block: L_kk = chol(M_kk) in shared memory; writes L_kk
 // (lower), L_kk^T (strict upper) and 1 / diag(L_kk).
 __global__ void __launch_bounds__(256) b_potrf_kernel(BCtl c, const BDesc* __restrict__ D, BState* S, int k) {
+  tk_start(c, TK_FACTOR);
   __shared__ double L[kTile][kTile + 1];
   __shared__ int bad;
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
@@ -401,6 +415,7 @@ __global__ void __launch_bounds__(256) b_potrf_kernel(BCtl c, const BDesc* __res
     }
     __syncthreads();
   }
+  tk_stop(c, TK_FACTOR);
 }
 
 // Panel k, blocks below the diagonal: L_ik = M_ik L_kk^{-T} (one thread per
@@ -408,6 +423,7 @@ __global__ void __launch_bounds__(256) b_potrf_kernel(BCtl c, const BDesc* __res
 // upper part.
 __global__ void __launch_bounds__(64) b_trsm_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
                                                     int total) {
+  tk_start(c, TK_FACTOR);
   extern __shared__ double tr_smem[];
   double (*L)[kTile + 1] = (double (*)[kTile + 1])tr_smem;                    // [64][65]
   double (*X)[kTile + 1] = (double (*)[kTile + 1])(tr_smem + kTile * (kTile + 1));  // [64][65]
@@ -448,12 +464,14 @@ __global__ void __launch_bounds__(64) b_trsm_kernel(BCtl c, const BDesc* __restr
     }
     __syncthreads();
   }
+  tk_stop(c, TK_FACTOR);
 }
 
 // Panel k, trailing update of the lower tiles (ti >= tj > k):
 // M_ij -= L_ik L_jk^T.
 __global__ void __launch_bounds__(256) b_update_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
                                                        int total) {
+  tk_start(c, TK_FACTOR);
   __shared__ __align__(16) double As[16][kTP];
   __shared__ __align__(16) double Bs[16][kTP];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -498,6 +516,7 @@ __global__ void __launch_bounds__(256) b_update_kernel(BCtl c, const BDesc* __re
         if (gi < N && gj < N) q.M[(int64_t)gi * d + gj] -= acc[i][j];
       }
   }
+  tk_stop(c, TK_FACTOR);
 }
 
 // One A-pass unit: rows [r0, r1) of A against v (in shared memory); warp w
@@ -549,7 +568,7 @@ __global__ void __launch_bounds__(kApThreads, 1) b_apass_kernel(BCtl c, const BD
   extern __shared__ __align__(16) double ap_smem[];
   double* vs = ap_smem;            // [d]
   double* red = ap_smem + kMaxD;   // [8][d]
-  if (threadIdx.x == 0 && c.tap) atomicMin(&c.tap[0], (unsigned long long)global_ns());
+  tk_start(c, TK_APASS);
   double flops = 0.0;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = find_problem(c.pre_ap, c.P, u);
@@ -572,10 +591,8 @@ __global__ void __launch_bounds__(kApThreads, 1) b_apass_kernel(BCtl c, const BD
     else apass_unit<32>(q.A, q.lda, d, r0, r1, vs, red, out);
     flops += 4.0 * (double)(r1 - r0) * d;
   }
-  if (threadIdx.x == 0 && c.tap) {
-    atomicMax(&c.tap[1], (unsigned long long)global_ns());
-    if (flops > 0) atomicAdd(c.apass_flops, flops);
-  }
+  tk_stop(c, TK_APASS);
+  if (threadIdx.x == 0 && c.tk && flops > 0) atomicAdd(c.apass_flops, flops);
 }
 
 // Hv = sum of the unit partials + nu^2 Lambda v, in chunks of 256 columns.
@@ -682,6 +699,7 @@ SKS_DEV void tri_solve(const double* __restrict__ M, int ld, int N, const double
 //   form 1: H_S^{-1} z = u - (nu^2 Lambda)^{-1} Y_s^T K^{-1} Y_s u,  u = (nu^2 Lambda)^{-1} z,
 //           Y_s = Y / sqrt(m), K = I + Y_s (nu^2 Lambda)^{-1} Y_s^T = L L^T
 __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S) {
+  tk_start(c, TK_APPLY);
   __shared__ double y[kMaxD];
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     const BState s = S[p];
@@ -722,6 +740,7 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
     }
     __syncthreads();
   }
+  tk_stop(c, TK_APPLY);
 }
 
 // GROW: restart p = r~, delta~_t = delta~_I = r^T r~.
@@ -820,15 +839,14 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
     *c.active = a;
     const long long r = ++*c.rounds;
     cudaGraphSetConditional(c.cond, (a > 0 && r < c.max_rounds) ? 1u : 0u);
-    if (c.tap) {
-      if (c.tap[1] > c.tap[0]) c.tap[2] += c.tap[1] - c.tap[0];
-      c.tap[0] = ~0ull;
-      c.tap[1] = 0ull;
-    }
-    if (c.tgram) {
-      if (c.tgram[1] > c.tgram[0]) c.tgram[2] += c.tgram[1] - c.tgram[0];
-      c.tgram[0] = ~0ull;
-      c.tgram[1] = 0ull;
+    if (c.tk) {
+      c.tk[3 * TK_ROUND + 1] = global_ns();
+      for (int i = 0; i < kTimers; ++i) {
+        unsigned long long* t = c.tk + 3 * i;
+        if (t[1] > t[0]) t[2] += t[1] - t[0];
+        t[0] = ~0ull;
+        t[1] = 0ull;
+      }
     }
   }
 }
@@ -838,13 +856,12 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
 // Per-solve counters: A-pass and Gram timing windows, flop sums, rounds.
 __global__ void b_reset_kernel(BCtl c) {
   if (threadIdx.x != 0) return;
-  c.tap[0] = ~0ull;
-  c.tap[1] = 0ull;
-  c.tap[2] = 0ull;
+  for (int i = 0; i < kTimers; ++i) {
+    c.tk[3 * i] = ~0ull;
+    c.tk[3 * i + 1] = 0ull;
+    c.tk[3 * i + 2] = 0ull;
+  }
   *c.apass_flops = 0.0;
-  c.tgram[0] = ~0ull;
-  c.tgram[1] = 0ull;
-  c.tgram[2] = 0ull;
   *c.gram_flops = 0.0;
   *c.rounds = 0;
 }
@@ -872,9 +889,8 @@ struct Layout {
   BDesc* D = nullptr;
   BState* S = nullptr;
   int *pre_tri = nullptr, *pre_T = nullptr, *pre_ap = nullptr, *pre_red = nullptr, *active = nullptr;
-  unsigned long long* tap = nullptr;
+  unsigned long long* tk = nullptr;
   double* apass_flops = nullptr;
-  unsigned long long* tgram = nullptr;
   double* gram_flops = nullptr;
   long long* rounds = nullptr;
   DevStatus* st = nullptr;
@@ -921,9 +937,8 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
   L->pre_ap = c.take<int>(P + 1);
   L->pre_red = c.take<int>(P + 1);
   L->active = c.take<int>(1);
-  L->tap = c.take<unsigned long long>(3);
+  L->tk = c.take<unsigned long long>(3 * kTimers);
   L->apass_flops = c.take<double>(1);
-  L->tgram = c.take<unsigned long long>(3);
   L->gram_flops = c.take<double>(1);
   L->rounds = c.take<long long>(1);
   L->st = c.take<DevStatus>(1);
@@ -1136,9 +1151,8 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
   c.pre_ap = L.pre_ap;
   c.pre_red = L.pre_red;
   c.active = L.active;
-  c.tap = L.tap;
+  c.tk = L.tk;
   c.apass_flops = L.apass_flops;
-  c.tgram = L.tgram;
   c.gram_flops = L.gram_flops;
   c.rounds = L.rounds;
   int dmax = 0;
@@ -1176,8 +1190,7 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
       SKS_TRY(upload_prefix(L.pre_ap, pa, stream));
       BCtl ct = c;
       ct.rows_per_unit = rows;
-      ct.tap = nullptr;
-      ct.tgram = nullptr;
+      ct.tk = nullptr;
       const int g = std::max(1, std::min(pa[P], ap_grid_max));
       b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);  // warm
       SKS_CUDA_TRY(cudaEventRecord(e.a, stream));
@@ -1264,13 +1277,12 @@ sks_status batch_solve(sks_batch* B, double* const* xs, sks_stats* stats, sks_ba
 
   // ---- per-problem results (the one synchronisation of the solve)
   std::vector<BState> hs(P);
-  unsigned long long h_tap[3] = {0, 0, 0}, h_tgram[3] = {0, 0, 0};
+  unsigned long long h_tk[3 * kTimers] = {};
   double h_flops = 0.0, h_gflops = 0.0;
   long long rounds = 0;
   SKS_CUDA_TRY(cudaMemcpyAsync(hs.data(), L.S, P * sizeof(BState), cudaMemcpyDeviceToHost, stream));
-  SKS_CUDA_TRY(cudaMemcpyAsync(h_tap, L.tap, sizeof(h_tap), cudaMemcpyDeviceToHost, stream));
+  SKS_CUDA_TRY(cudaMemcpyAsync(h_tk, L.tk, sizeof(h_tk), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(&h_flops, L.apass_flops, sizeof(double), cudaMemcpyDeviceToHost, stream));
-  SKS_CUDA_TRY(cudaMemcpyAsync(h_tgram, L.tgram, sizeof(h_tgram), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(&h_gflops, L.gram_flops, sizeof(double), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaMemcpyAsync(&rounds, L.rounds, sizeof(long long), cudaMemcpyDeviceToHost, stream));
   SKS_CUDA_TRY(cudaStreamSynchronize(stream));
@@ -1309,10 +1321,13 @@ sks_status batch_solve(sks_batch* B, double* const* xs, sks_stats* stats, sks_ba
     info->ms_setup = B->ms_plan;
     info->ms_autotune = B->ms_tune;
     info->ms_solve = ms_solve;
-    info->ms_apass = (float)((double)h_tap[2] * 1e-6);
+    info->ms_apass = (float)((double)h_tk[3 * TK_APASS + 2] * 1e-6);
     info->apass_flops = h_flops;
-    info->ms_gram = (float)((double)h_tgram[2] * 1e-6);
+    info->ms_gram = (float)((double)h_tk[3 * TK_GRAM + 2] * 1e-6);
     info->gram_flops = h_gflops;
+    info->ms_factor = (float)((double)h_tk[3 * TK_FACTOR + 2] * 1e-6);
+    info->ms_apply = (float)((double)h_tk[3 * TK_APPLY + 2] * 1e-6);
+    info->ms_rounds = (float)((double)h_tk[3 * TK_ROUND + 2] * 1e-6);
   }
   if (result != SKS_OK) {
     const char* what = result == SKS_ERR_NO_CONVERGENCE ? "did not converge"

@@ -70,12 +70,17 @@ WORKLOADS = {
                        precision="mixed", desc="C3 recipe at n=2^17 (profiling size)"),
     "C3-srht-profile": dict(config="C3", n=1 << 17, method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=8192,
                             tol=1e-8, precision="mixed", desc="C3 recipe with the SRHT at n=2^17 (profiling size)"),
-    # C5: 256 uneven problems solved together (float64, SRHT, tol 1e-8) vs the same problems one at a time
+    # C5: 256 uneven problems solved together (SRHT, tol 1e-8) vs the same problems one at a time in the
+    # plain float64 form; the batch runs the mixed form on float32 A, the baseline the exact float64 upcast
     "C5": dict(config="C5", batched=True, count=256, method="pcg", kind="srht", m_init=1, m_max=0, tol=1e-8,
-               precision="plain", ref_problems=6,
+               precision="mixed", ref_problems=6,
                desc="256 independent problems, n log-uniform in [2^11, 2^16], d log-uniform in [32, 1024], "
                     "n >= 4d, sigma_j = 0.9^j or 1/(1+j), nu log-uniform in [1e-4, 1e-1], Lambda = I, SRHT, "
-                    "adaptive PCG to 1e-8, batched (one captured round replayed) vs one solve at a time"),
+                    "adaptive PCG to 1e-8; batched mixed form (float32 A, refinement; one captured graph) vs one "
+                    "plain float64 solve at a time on the float64 upcast"),
+    "C5-plain": dict(config="C5", batched=True, count=256, method="pcg", kind="srht", m_init=1, m_max=0, tol=1e-8,
+                     precision="plain", ref_problems=6,
+                     desc="C5 with the batch in the plain float64 form (float64 A) vs one solve at a time"),
     # the paper's experiment sizes: mixed form only (the float64 copy and its SRHT would add ~120 GB);
     # m capped at 2^15 (the sketch and its float64 copy are m_max x d)
     "P-d7000": dict(config="P", d=7000, method="pcg", kind="srht", sjlt_s=1, m_init=1, m_max=1 << 15, tol=1e-8,
@@ -359,7 +364,9 @@ def run_reference_batched(args, wl, world, rank):
     from oracle import solvers as O
     gdev = "cuda" if torch.cuda.is_available() else "cpu"
     specs, probs = synthetic.make_batch_torch(wl["count"], seed=0, device=gdev)
-    host = [(A.cpu().numpy(), b.cpu().numpy(), nu, lam.cpu().numpy()) for A, b, nu, lam in probs]
+    # the mixed batch solves A rounded to float32: the oracle takes the same (upcast) problems
+    cast = (lambda A: A.float().double()) if wl["precision"] == "mixed" else (lambda A: A)
+    host = [(cast(A).cpu().numpy(), b.cpu().numpy(), nu, lam.cpu().numpy()) for A, b, nu, lam in probs]
     del probs
     k = min(wl["ref_problems"], len(host))
     nd_all = sum(A.shape[0] * A.shape[1] for A, _, _, _ in host)
@@ -881,8 +888,15 @@ def run_batched(args, wl, world, rank, local):
     torch.cuda.set_device(dev)
     lib = _lib.load()
     specs, probs = synthetic.make_batch_torch(wl["count"], seed=0, device=dev)
+    mixed = wl["precision"] == "mixed"
+    if mixed:
+        # the mixed form's problem is A rounded to float32; its float64 upcast (exact) is the baseline's
+        run = [(A.float(), b, nu, lam) for A, b, nu, lam in probs]
+        probs = [(A32.double(), b, nu, lam) for A32, b, nu, lam in run]
+    else:
+        run = probs
     opts = dict(kind=wl["kind"], m_init=wl["m_init"], m_max=wl["m_max"], tol=wl["tol"], seed=0, max_iter=1000)
-    bs = sks.BatchSolver(probs, **opts)
+    bs = sks.BatchSolver(run, precision=wl["precision"], **opts)
     for _ in range(args.warmup):
         bs.solve()
     torch.cuda.synchronize()
@@ -909,34 +923,46 @@ def run_batched(args, wl, world, rank, local):
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     n_tot = sum(int(A.shape[0]) * int(A.shape[1]) for A, _, _, _ in probs)
 
-    # roofline of the batched A-pass (float64, ALU-bound): device-clock duration of its launches
+    # roofline of the batched A-pass: device-clock windows of its launches (first CTA start to last CTA end
+    # per round); apass_flops counts 4 n d per pass
     ap_ms = sum(i["ms_apass"] for i in infos)
     ap_flops = sum(i["apass_flops"] for i in infos)
-    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = ap_flops / (ap_ms * 1e-3) / 1e12 if ap_ms > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
-                "kernel": "b_apass_kernel (batched float64 A-pass)", "ms_apass_per_step": ap_ms / args.steps,
-                "flops_per_step": ap_flops / args.steps,
-                "peak_source": "float64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2 flop) at the sampled "
-                               "median SM clock"}
+    if mixed:
+        # float32 A: n d 4 bytes per pass = the flop count; bound by HBM
+        peaks, peak_src = load_peaks()
+        gbs = ap_flops / (ap_ms * 1e-3) / 1e9 if ap_ms > 0 else None
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": (gbs / peaks["hbm_gbs"]) if gbs else None, "traffic": None,
+                    "kernel": "b_apass_mixed_kernel (batched float32 A-pass: float32 inner passes, double-float "
+                              "refinement residuals)",
+                    "ms_apass_per_step": ap_ms / args.steps, "bytes_per_step": ap_flops / args.steps,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}
+    else:
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = ap_flops / (ap_ms * 1e-3) / 1e12 if ap_ms > 0 else None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+                    "kernel": "b_apass_kernel (batched float64 A-pass)", "ms_apass_per_step": ap_ms / args.steps,
+                    "flops_per_step": ap_flops / args.steps,
+                    "peak_source": "float64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2 flop) at the "
+                                   "sampled median SM clock"}
 
     # end to end through the public call: inputs from pinned host memory every step, solutions read back
-    host_in = [(A.cpu().pin_memory(), b.cpu().pin_memory(), lam.cpu().pin_memory()) for A, b, _, lam in probs]
-    h2d = sum(a.numel() * 8 + b.numel() * 8 + l.numel() * 8 for a, b, l in host_in)
-    d2h = sum(int(A.shape[1]) * 8 for A, _, _, _ in probs)
+    host_in = [(A.cpu().pin_memory(), b.cpu().pin_memory(), lam.cpu().pin_memory()) for A, b, _, lam in run]
+    h2d = sum(a.numel() * a.element_size() + b.numel() * 8 + l.numel() * 8 for a, b, l in host_in)
+    d2h = sum(int(A.shape[1]) * 8 for A, _, _, _ in run)
     kp = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     for _ in range(kp):
-        for (A, b, _, lam), (ah, bh, lh) in zip(probs, host_in):
+        for (A, b, _, lam), (ah, bh, lh) in zip(run, host_in):
             A.copy_(ah, non_blocking=True)
             b.copy_(bh, non_blocking=True)
             lam.copy_(lh, non_blocking=True)
-        xs_e, _, _ = sks.solve_batched(probs, **opts)
+        xs_e, _, _ = sks.solve_batched(run, precision=wl["precision"], **opts)
         _ = [x.cpu() for x in xs_e]
     e3.record(stream)
     torch.cuda.synchronize()
@@ -967,10 +993,11 @@ def run_batched(args, wl, world, rank, local):
     line = {
         "metric": BATCH_METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": "C5: " + wl["desc"], "problems": len(probs), "sum_nd": n_tot,
                    "max_d": max(int(A.shape[1]) for A, _, _, _ in probs),
-                   "l2": "inputs larger than L2 (A = %.2f GiB)" % (n_tot * 8 / 2 ** 30),
+                   "precision": wl["precision"],
+                   "l2": "inputs larger than L2 (A = %.2f GiB)" % (n_tot * (4 if mixed else 8) / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
         "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -978,10 +1005,14 @@ def run_batched(args, wl, world, rank, local):
         "clocks": clk,
         "batch_info": info,
         "batch_stats": {"iters_max": max(s["iters"] for s in stats), "final_m_max": max(s["final_m"] for s in stats),
+                        "outer_iters_max": max(s["outer_iters"] for s in stats),
                         "all_ok": all(s["status"] == 0 for s in stats)},
         "compare": {"one_at_a_time_ms": ms_single, "batched_ms": ms, "speedup_batched": ms_single / ms,
-                    "same_iterations": sum(1 for a, b in zip(stats, single_stats)
-                                           if (a["iters"], a["final_m"]) == (b["iters"], b["final_m"]))},
+                    # the plain batch runs Algorithm 2 step for step like the single solver; the mixed
+                    # form's inner solves take their own path
+                    "same_iterations": (None if mixed else
+                                        sum(1 for a, b in zip(stats, single_stats)
+                                            if (a["iters"], a["final_m"]) == (b["iters"], b["final_m"])))},
         "rel_err_H_vs_oracle": {"problems": len(errs), "max": max(errs), "median": float(np.median(errs)),
                                 "all_within_tol": bool(max(errs) <= wl["tol"])},
     }

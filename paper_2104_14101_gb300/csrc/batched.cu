@@ -1,5 +1,6 @@
 // batched.cu -- many independent problems (1) solved together by the adaptive
-// PCG of Algorithm 2 (float64, SRHT embedding of Section 2.1).
+// PCG of Algorithm 2 with the SRHT embedding of Section 2.1, in the plain
+// float64 form or in the mixed form (float32 A, see below).
 //
 // Every decision of Algorithm 2 (accept / reject, doubling of m, stop) is
 // taken on the device, per problem, so one ROUND -- a fixed sequence of
@@ -17,6 +18,17 @@
 //   ITER  : one PCG step with the improvement test of Algorithm 2; on
 //           rejection I = t                                        -> GROW
 //           on acceptance, stop when delta~ <= (tol/2)^2 b^T x   -> DONE
+// Mixed form (float32 A, iterative refinement around Algorithm 2): INIT
+// computes the refinement residual r = b - H x_o with a double-float pass
+// over the float32 A and starts an inner solve of H dx = r from dx = 0
+// (t = I = 0); the first restart of the inner solve (GROW when no sketch
+// exists yet, else RESTART: r~ = H_S^{-1} r with the current factor) stops
+// the whole solve when delta~ <= (tol/2)^2 b^T x_o; inner iterations run
+// their A-pass in float32 and end when delta~ <= inner_tol^2 delta~_0, then
+// x_o += dx -> INIT.  The sketch (float32 H E A_pad) and m carry over from
+// one inner solve to the next; the Gram sums exact float32 products in
+// double-float arithmetic on the float32 pipe; factor, apply and the vector
+// steps stay in float64.
 // A round runs, in order: m update, permutation rows, Gram / Woodbury
 // matrix, blocked Cholesky (three kernels per 64-column panel), the A-pass of
 // every INIT / ITER problem, its reduction, the first half of the step, the
@@ -38,9 +50,9 @@
 namespace sks {
 namespace {
 
-enum : int { PH_INIT = 0, PH_GROW = 1, PH_ITER = 2, PH_DONE = 3, PH_FAIL = 4 };
-// d-vector slots of a problem
-enum : int { V_R = 0, V_RT, V_P, V_HV, V_XP, V_RP, V_RTP, V_U, V_W, V_DINV, kNumVec };
+enum : int { PH_INIT = 0, PH_GROW = 1, PH_ITER = 2, PH_RESTART = 3, PH_DONE = 4, PH_FAIL = 5 };
+// d-vector slots of a problem (V_XI: the inner iterate dx of the mixed form)
+enum : int { V_R = 0, V_RT, V_P, V_HV, V_XP, V_RP, V_RTP, V_U, V_W, V_DINV, V_XI, kNumVec };
 
 // phase timers: A-pass, sketched-Hessian matrix (Gram), its factorisation,
 // preconditioner apply, the whole round (first kernel to the count kernel)
@@ -61,7 +73,10 @@ struct BDesc {
   const double* lam;
   double nu2;
   double* x;         // caller's x (x0 on entry)
-  const double* B;   // H E A_pad, n_pad x d, ld d
+  const double* B;   // H E A_pad, n_pad x d, ld d (plain form)
+  const float* Af;   // mixed form: the float32 A (A is NULL)
+  float* Bf;         // mixed form: float32 H E A_pad, n_pad x d, ld d (B is NULL)
+  float* ilam;       // mixed form: 1 / lambda rounded to float32 (Woodbury Gram)
   uint32_t* perm;    // sketch row r is B[perm[r]]
   double* M;         // d x d, ld d: lower = factor L, strict upper = L^T
   double* vec;       // kNumVec d-vectors
@@ -80,6 +95,11 @@ struct BState {
   int64_t k_begin;    // first sketch row this round's Gram adds
   double dt, dI, btx;
   int64_t rejections, a_passes, factorizations;
+  // mixed form: refinement steps done, 1 until the first restart of an inner
+  // solve, delta~ at that restart, iterations over all inner solves
+  int outer, fresh;
+  double d0;
+  int64_t t_all;
 };
 
 struct BCtl {
@@ -87,6 +107,9 @@ struct BCtl {
   int rows_per_unit;
   int64_t max_iter;
   double c, phi, tol2;
+  int mixed;           // 1: float32 A with refinement (the mixed form)
+  int64_t max_outer;   // mixed form: refinement steps
+  double inner2;       // mixed form: inner_tol^2
   Key key;
   const int* pre_tri;  // prefix over problems of T(T+1)/2, T = ceil(d / 64)
   const int* pre_T;    // prefix of T
@@ -207,6 +230,39 @@ SKS_DEV int gram_slices(const BState& s, int d) {
   return min(kGramSplit, max(1, (int)((k + per - 1) / per)));
 }
 
+// A Gram unit's 4 x 4 outputs: the raw slice sum to the partial tiles (nks > 1),
+// else G (Cholesky form, added to the rows summed before) and the matrix M.
+SKS_DEV void gram_epilogue(const BDesc& q, const BState& s, int nks, int ks, int l, int i0, int j0, int N,
+                           const double (&acc)[4][4], int tx, int ty) {
+  if (nks > 1) {
+    double* tile = q.gpart + ((size_t)ks * (size_t)q.ntri + l) * (kTile * kTile);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tile[(ty * 4 + i) * kTile + tx * 4 + j] = acc[i][j];
+    return;
+  }
+  const int d = q.d;
+  const double scale = s.form == 0 ? 1.0 / (double)s.m : 1.0 / ((double)s.m * q.nu2);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
+      if (gi < N && gj < N) {
+        double g = acc[i][j];
+        if (s.form == 0) {
+          double* gp = q.G + (int64_t)gi * d + gj;
+          if (s.k_begin > 0) g += *gp;
+          *gp = g;
+        }
+        double v = g * scale;
+        if (gi == gj) v += s.form == 0 ? q.nu2 * q.lam[gi] : 1.0;
+        q.M[(int64_t)gi * d + gj] = v;
+      }
+    }
+}
+
 // Sketched-Hessian matrix of every GROW problem, lower 64 x 64 tiles:
 //   form 0: M = (1/m) G + nu^2 Lambda, G = Y^T Y (Y = rows perm[0..m) of B)
 //           kept across doublings: G += Y_new^T Y_new for the rows added
@@ -284,32 +340,118 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
         __syncthreads();
       }
     }
-    if (nks > 1) {
-      double* tile = q.gpart + ((size_t)ks * (size_t)q.ntri + l) * (kTile * kTile);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) tile[(ty * 4 + i) * kTile + tx * 4 + j] = acc[i][j];
-      continue;
-    }
-    const double scale = s.form == 0 ? 1.0 / (double)m : 1.0 / ((double)m * q.nu2);
+    gram_epilogue(q, s, nks, ks, l, i0, j0, N, acc, tx, ty);
+  }
+  tk_stop(c, TK_GRAM);
+  if (threadIdx.x == 0 && c.tk && flops > 0) atomicAdd(c.gram_flops, flops);
+}
+
+// (hi, lo) += a b: the product exact (TwoProd), summed by Knuth's TwoSum into
+// the high part; the rounding errors go to the low part (double-float, ~2^-44
+// relative after thousands of terms).  The _rn intrinsics keep the compiler
+// from contracting the sums into multiply-adds.
+SKS_DEV void df_mac(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float z = __fsub_rn(s, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(p, z)), e));
+  hi = s;
+}
+
+constexpr int kTPf = kTile + 4;  // float shared-memory row (16-byte aligned quads)
+
+// The Gram units of b_gram_kernel for the mixed form: float32 sketch rows (and
+// 1/lambda in float32 for the Woodbury form), exact products summed in
+// double-float on the float32 pipe (a float64 Gram runs at 1/64 of its rate
+// on this part).
+__global__ void __launch_bounds__(256) b_gram_mixed_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
+                                                           int total) {
+  __shared__ __align__(16) float As[16][kTPf];
+  __shared__ __align__(16) float Bs[16][kTPf];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  tk_start(c, TK_GRAM);
+  double flops = 0.0;
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int tu = u / kGramSplit, ks = u - tu * kGramSplit;
+    const int p = find_problem(c.pre_tri, c.P, tu);
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    const int nks = gram_slices(s, q.d);
+    if (ks >= nks) continue;
+    const int l = tu - c.pre_tri[p];
+    int ti, tj;
+    tri_index(l, &ti, &tj);
+    const int N = factor_size(s, q);
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    if (i0 >= N) continue;
+    const int d = q.d;
+    const int m = (int)s.m;
+    float hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
-        if (gi < N && gj < N) {
-          double g = acc[i][j];
-          if (s.form == 0) {
-            double* gp = q.G + (int64_t)gi * d + gj;
-            if (s.k_begin > 0) g += *gp;
-            *gp = g;
+      for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+    int kb, ke;
+    if (s.form == 0) {
+      const int k_begin = (int)s.k_begin;
+      const int per = ((m - k_begin + nks - 1) / nks + 15) / 16 * 16;
+      kb = k_begin + ks * per;
+      ke = min(m, kb + per);
+    } else {
+      const int per = ((d + nks - 1) / nks + 15) / 16 * 16;
+      kb = ks * per;
+      ke = min(d, kb + per);
+    }
+    flops += 2.0 * kTile * kTile * (double)max(0, ke - kb);
+    for (int k0 = kb; k0 < ke; k0 += 16) {
+      if (s.form == 0) {
+        for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+          const int kk = e >> 6, ii = e & 63;
+          const int r = k0 + kk;
+          float a = 0.f, b = 0.f;
+          if (r < ke) {
+            const float* y = q.Bf + (int64_t)q.perm[r] * d;
+            if (i0 + ii < N) a = y[i0 + ii];
+            if (j0 + ii < N) b = y[j0 + ii];
           }
-          double v = g * scale;
-          if (gi == gj) v += s.form == 0 ? q.nu2 * q.lam[gi] : 1.0;
-          q.M[(int64_t)gi * d + gj] = v;
+          As[kk][ii] = a;
+          Bs[kk][ii] = b;
+        }
+      } else {
+        for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+          const int ii = e >> 4, kk = e & 15;
+          const int col = k0 + kk;
+          float a = 0.f, b = 0.f;
+          if (col < ke) {
+            if (i0 + ii < N) a = __fmul_rn(q.Bf[(int64_t)q.perm[i0 + ii] * d + col], q.ilam[col]);
+            if (j0 + ii < N) b = q.Bf[(int64_t)q.perm[j0 + ii] * d + col];
+          }
+          As[kk][ii] = a;
+          Bs[kk][ii] = b;
         }
       }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {
+        const float4 a4 = *(const float4*)&As[k][ty * 4];
+        const float4 b4 = *(const float4*)&Bs[k][tx * 4];
+        const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_mac(a[i], b[j], hi[i][j], lo[i][j]);
+      }
+      __syncthreads();
+    }
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = (double)hi[i][j] + (double)lo[i][j];
+    gram_epilogue(q, s, nks, ks, l, i0, j0, N, acc, tx, ty);
   }
   tk_stop(c, TK_GRAM);
   if (threadIdx.x == 0 && c.tk && flops > 0) atomicAdd(c.gram_flops, flops);
@@ -595,6 +737,185 @@ __global__ void __launch_bounds__(kApThreads, 1) b_apass_kernel(BCtl c, const BD
   if (threadIdx.x == 0 && c.tk && flops > 0) atomicAdd(c.apass_flops, flops);
 }
 
+// ---- mixed form A-pass (float32 A)
+SKS_DEV void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// (h, l) += (bh, bl), renormalised
+SKS_DEV void df_add2(float& h, float& l, float bh, float bl) {
+  float s, e;
+  df_two_sum(h, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// Inner iterations: rows [r0, r1) of the float32 A against p rounded to
+// float32 (vs), float32 sums; the unit's d partial sums leave as float64.
+template <int QC>
+SKS_DEV void apass_unit_f32(const float* __restrict__ A, long long lda, int d, int64_t r0, int64_t r1,
+                            const float* vs, float* red, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[QC];
+#pragma unroll
+  for (int j = 0; j < QC; ++j) acc[j] = 0.f;
+  for (int64_t r = r0 + warp; r < r1; r += kApWarps) {
+    const float* a = A + r * lda;
+    float av[QC];
+    float dot = 0.f;
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const int col = lane + 32 * j;
+      av[j] = col < d ? __ldg(a + col) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const int col = lane + 32 * j;
+      if (col < d) dot = fmaf(av[j], vs[col], dot);
+    }
+    dot = warp_sum(dot);
+#pragma unroll
+    for (int j = 0; j < QC; ++j) acc[j] = fmaf(dot, av[j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < QC; ++j) {
+    const int col = lane + 32 * j;
+    if (col < d) red[warp * d + col] = acc[j];
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < d; col += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kApWarps; ++w) t += red[w * d + col];
+    out[col] = (double)t;
+  }
+  __syncthreads();
+}
+
+// Refinement residual: rows [r0, r1) of the float32 A against x_o split into
+// two floats (xh + xl), every product exact (TwoProd) and every sum in
+// double-float; the unit's partial sums leave as float64 (hi + lo).
+template <int QC>
+SKS_DEV void apass_unit_df(const float* __restrict__ A, long long lda, int d, int64_t r0, int64_t r1,
+                           const float* xh, const float* xl, float* redh, float* redl, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float ah[QC], al[QC];
+#pragma unroll
+  for (int j = 0; j < QC; ++j) ah[j] = al[j] = 0.f;
+  for (int64_t r = r0 + warp; r < r1; r += kApWarps) {
+    const float* a = A + r * lda;
+    float av[QC];
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const int col = lane + 32 * j;
+      av[j] = col < d ? __ldg(a + col) : 0.f;
+    }
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const int col = lane + 32 * j;
+      if (col < d) {
+        const float p = __fmul_rn(av[j], xh[col]);
+        const float e = __fmaf_rn(av[j], xl[col], __fmaf_rn(av[j], xh[col], -p));
+        float t, u;
+        df_two_sum(sh, p, t, u);
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(u, e));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+      df_add2(sh, sl, oh, ol);
+    }
+    // acc_j += a_j (sh + sl)
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const float p = __fmul_rn(av[j], sh);
+      const float e = __fmaf_rn(av[j], sl, __fmaf_rn(av[j], sh, -p));
+      float t, u;
+      df_two_sum(ah[j], p, t, u);
+      ah[j] = t;
+      al[j] = __fadd_rn(al[j], __fadd_rn(u, e));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < QC; ++j) {
+    const int col = lane + 32 * j;
+    if (col < d) {
+      redh[warp * d + col] = ah[j];
+      redl[warp * d + col] = al[j];
+    }
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < d; col += blockDim.x) {
+    float h = redh[col], l = redl[col];
+#pragma unroll
+    for (int w = 1; w < kApWarps; ++w) df_add2(h, l, redh[w * d + col], redl[w * d + col]);
+    out[col] = (double)h + (double)l;
+  }
+  __syncthreads();
+}
+
+// Mixed-form A-pass: DF = true serves the INIT problems (v = x_o, double-
+// float), DF = false the ITER problems (v = p, float32).  tune = 1 (unit-
+// height timing only) runs every unit as ITER.
+template <bool DF>
+__global__ void __launch_bounds__(kApThreads) b_apass_mixed_kernel(BCtl c, const BDesc* __restrict__ D,
+                                                                   const BState* S, int total, int tune) {
+  extern __shared__ __align__(16) float apf_smem[];
+  float* vh = apf_smem;                     // [d]
+  float* vl = apf_smem + kMaxD;             // [d] (DF only)
+  float* redh = apf_smem + (DF ? 2 : 1) * kMaxD;   // [8][d]
+  float* redl = redh + kApWarps * kMaxD;    // [8][d] (DF only)
+  tk_start(c, TK_APASS);
+  double flops = 0.0;
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_ap, c.P, u);
+    const int phase = S[p].phase;
+    if (!tune && phase != (DF ? PH_INIT : PH_ITER)) continue;
+    const BDesc& q = D[p];
+    const int d = q.d;
+    if (DF) {
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double x = q.x[j];
+        const float h = (float)x;
+        vh[j] = h;
+        vl[j] = (float)(x - (double)h);
+      }
+    } else {
+      const double* v = q.vec + (size_t)V_P * d;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) vh[j] = (float)v[j];
+    }
+    __syncthreads();
+    const int t = u - c.pre_ap[p];
+    const int64_t r0 = (int64_t)t * c.rows_per_unit;
+    const int64_t r1 = min(q.n, r0 + c.rows_per_unit);
+    double* out = q.part + (size_t)t * d;
+    if (DF) {
+      if (d <= 32) apass_unit_df<1>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
+      else if (d <= 64) apass_unit_df<2>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
+      else if (d <= 128) apass_unit_df<4>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
+      else if (d <= 256) apass_unit_df<8>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
+      else if (d <= 512) apass_unit_df<16>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
+      else apass_unit_df<32>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
+    } else {
+      if (d <= 32) apass_unit_f32<1>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 64) apass_unit_f32<2>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 128) apass_unit_f32<4>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 256) apass_unit_f32<8>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 512) apass_unit_f32<16>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else apass_unit_f32<32>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+    }
+    flops += 4.0 * (double)(r1 - r0) * d;
+  }
+  tk_stop(c, TK_APASS);
+  if (threadIdx.x == 0 && c.tk && flops > 0) atomicAdd(c.apass_flops, flops);
+}
+constexpr size_t apass_mixed_smem(bool df) { return (size_t)(df ? 2 + 2 * kApWarps : 1 + kApWarps) * kMaxD * 4; }
+
 // Hv = sum of the unit partials + nu^2 Lambda v, in chunks of 256 columns.
 __global__ void __launch_bounds__(256) b_reduce_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
                                                        int total) {
@@ -633,15 +954,27 @@ __global__ void __launch_bounds__(256) b_step1_kernel(BCtl c, const BDesc* __res
     const double* Hv = q.vec + (size_t)V_HV * d;
     if (phase == PH_INIT) {
       for (int j = threadIdx.x; j < d; j += blockDim.x) r[j] = q.b[j] - Hv[j];
+      if (c.mixed) {
+        // a new inner solve of H dx = r from dx = 0; b^T x_o for the stop rule
+        double* xi = q.vec + (size_t)V_XI * d;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) xi[j] = 0.0;
+        const double btx = block_dot(d, q.b, q.x, scratch);
+        if (threadIdx.x == 0) {
+          S[p].btx = btx;
+          S[p].t = 0;
+          S[p].I = 0;
+        }
+      }
     } else {
       const double* pv = q.vec + (size_t)V_P * d;
+      const double* xc = c.mixed ? q.vec + (size_t)V_XI * d : q.x;
       const double pHp = block_dot(d, pv, Hv, scratch);
       const double alpha = S[p].dt / pHp;
       const bool bad = !(pHp > 0.0) || !isfinite(alpha);
       double* xp = q.vec + (size_t)V_XP * d;
       double* rp = q.vec + (size_t)V_RP * d;
       for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        xp[j] = q.x[j] + alpha * pv[j];
+        xp[j] = xc[j] + alpha * pv[j];
         rp[j] = r[j] - alpha * Hv[j];
       }
       if (bad && threadIdx.x == 0) {
@@ -703,11 +1036,12 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
   __shared__ double y[kMaxD];
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     const BState s = S[p];
-    if (s.phase != PH_GROW && s.phase != PH_ITER) continue;
+    if (s.phase != PH_GROW && s.phase != PH_ITER && s.phase != PH_RESTART) continue;
     const BDesc& q = D[p];
     const int d = q.d;
-    const double* z = q.vec + (size_t)(s.phase == PH_GROW ? V_R : V_RP) * d;
-    double* out = q.vec + (size_t)(s.phase == PH_GROW ? V_RT : V_RTP) * d;
+    const bool restart = s.phase != PH_ITER;
+    const double* z = q.vec + (size_t)(restart ? V_R : V_RP) * d;
+    double* out = q.vec + (size_t)(restart ? V_RT : V_RTP) * d;
     const double* dinv = q.vec + (size_t)V_DINV * d;
     if (s.form == 0) {
       for (int j = threadIdx.x; j < d; j += blockDim.x) y[j] = z[j];
@@ -723,9 +1057,13 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
       __syncthreads();
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int r = warp; r < m; r += nw) {
-        const double* row = q.B + (int64_t)q.perm[r] * d;
+        const int64_t off = (int64_t)q.perm[r] * d;
         double t = 0.0;
-        for (int j = lane; j < d; j += 32) t = fma(row[j], u[j], t);
+        if (q.Bf) {
+          for (int j = lane; j < d; j += 32) t = fma((double)q.Bf[off + j], u[j], t);
+        } else {
+          for (int j = lane; j < d; j += 32) t = fma(q.B[off + j], u[j], t);
+        }
         t = warp_sum(t);
         if (lane == 0) y[r] = t * ism;
       }
@@ -734,7 +1072,11 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
       tri_solve(q.M, d, m, dinv, y, true);
       for (int j = threadIdx.x; j < d; j += blockDim.x) {
         double t = 0.0;
-        for (int r = 0; r < m; ++r) t = fma(q.B[(int64_t)q.perm[r] * d + j], y[r], t);
+        if (q.Bf) {
+          for (int r = 0; r < m; ++r) t = fma((double)q.Bf[(int64_t)q.perm[r] * d + j], y[r], t);
+        } else {
+          for (int r = 0; r < m; ++r) t = fma(q.B[(int64_t)q.perm[r] * d + j], y[r], t);
+        }
         out[j] = u[j] - t * ism / (q.nu2 * q.lam[j]);
       }
     }
@@ -746,9 +1088,27 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
 // GROW: restart p = r~, delta~_t = delta~_I = r^T r~.
 // ITER: delta~+ = r+^T r~+, the improvement test of Algorithm 2, the update.
 // INIT: on to the first sketch.
+// Mixed form, end of an inner solve: x_o += dx, then the next refinement step
+// (or NO_CONVERGENCE after max_outer of them).
+SKS_DEV void finish_inner(const BCtl& c, const BDesc& q, BState* S, int p) {
+  const double* xi = q.vec + (size_t)V_XI * q.d;
+  for (int j = threadIdx.x; j < q.d; j += blockDim.x) q.x[j] += xi[j];
+  if (threadIdx.x == 0) {
+    BState& s = S[p];
+    s.outer += 1;
+    if (s.outer >= c.max_outer) {
+      s.status = SKS_ERR_NO_CONVERGENCE;
+      s.phase = PH_FAIL;
+    } else {
+      s.phase = PH_INIT;
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) b_step2_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
   __shared__ double scratch[32];
-  __shared__ int s_accept, s_phase;
+  __shared__ int s_accept, s_phase, s_inner_done;
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     // thread 0 changes the phase below: every thread reads it first
     __syncthreads();
@@ -756,30 +1116,45 @@ __global__ void __launch_bounds__(256) b_step2_kernel(BCtl c, const BDesc* __res
     __syncthreads();
     const int phase = s_phase;
     if (phase == PH_INIT) {
-      if (threadIdx.x == 0) S[p].phase = PH_GROW;
+      if (threadIdx.x == 0) {
+        // mixed form: a sketch exists after the first refinement step
+        S[p].phase = (c.mixed && S[p].m > 0) ? PH_RESTART : PH_GROW;
+        S[p].fresh = c.mixed;
+      }
       continue;
     }
-    if (phase != PH_GROW && phase != PH_ITER) continue;
+    if (phase != PH_GROW && phase != PH_ITER && phase != PH_RESTART) continue;
     const BDesc& q = D[p];
     const int d = q.d;
     double* r = q.vec + (size_t)V_R * d;
     double* rt = q.vec + (size_t)V_RT * d;
     double* pv = q.vec + (size_t)V_P * d;
-    if (phase == PH_GROW) {
+    if (phase != PH_ITER) {
       const double dt = block_dot(d, r, rt, scratch);
       for (int j = threadIdx.x; j < d; j += blockDim.x) pv[j] = rt[j];
       if (threadIdx.x == 0) {
         BState& s = S[p];
         s.dt = dt;
         s.dI = dt;
+        s_inner_done = 0;
         if (!isfinite(dt)) {
           s.status = SKS_ERR_NUMERIC;
           s.phase = PH_FAIL;
-        } else {
+        } else if (!c.mixed) {
           s.phase = dt <= 0.0 ? PH_DONE : PH_ITER;
+        } else if (s.fresh) {
+          // first restart of an inner solve: delta~ at x_o estimates its error
+          s.fresh = 0;
+          s.d0 = dt;
+          s.phase = (dt <= 0.0 || dt <= c.tol2 * s.btx) ? PH_DONE : PH_ITER;
+        } else if (dt <= 0.0) {
+          s_inner_done = 1;
+        } else {
+          s.phase = PH_ITER;
         }
       }
       __syncthreads();
+      if (s_inner_done) finish_inner(c, q, S, p);
       continue;
     }
     const double* rp = q.vec + (size_t)V_RP * d;
@@ -806,18 +1181,37 @@ __global__ void __launch_bounds__(256) b_step2_kernel(BCtl c, const BDesc* __res
     __syncthreads();
     if (!s_accept) continue;
     const double beta = dp / S[p].dt;
+    double* xd = c.mixed ? q.vec + (size_t)V_XI * d : q.x;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
       pv[j] = rtp[j] + beta * pv[j];
-      q.x[j] = xp[j];
+      xd[j] = xp[j];
       r[j] = rp[j];
       rt[j] = rtp[j];
     }
     __syncthreads();
+    if (c.mixed) {
+      // inner solve: relative decrement inner_tol^2 against its first restart
+      if (threadIdx.x == 0) {
+        BState& s = S[p];
+        s.dt = dp;
+        s.t += 1;
+        s.t_all += 1;
+        s_inner_done = (dp <= 0.0 || dp <= c.inner2 * s.d0) ? 1 : 0;
+        if (!s_inner_done && s.t_all >= c.max_iter) {
+          s.status = SKS_ERR_NO_CONVERGENCE;
+          s.phase = PH_FAIL;
+        }
+      }
+      __syncthreads();
+      if (s_inner_done) finish_inner(c, q, S, p);
+      continue;
+    }
     const double btx = block_dot(d, q.b, q.x, scratch);
     if (threadIdx.x == 0) {
       BState& s = S[p];
       s.dt = dp;
       s.t += 1;
+      s.t_all = s.t;
       s.btx = btx;
       if (dp <= 0.0 || dp <= c.tol2 * btx) {
         s.phase = PH_DONE;
@@ -874,6 +1268,14 @@ __global__ void b_check_kernel(const BDesc* __restrict__ D, int P, DevStatus* st
   }
 }
 
+// mixed form: 1 / lambda rounded to float32 (Woodbury Gram)
+__global__ void b_prep_mixed_kernel(const BDesc* __restrict__ D, int P) {
+  for (int p = blockIdx.x; p < P; p += gridDim.x) {
+    const BDesc& q = D[p];
+    for (int j = threadIdx.x; j < q.d; j += blockDim.x) q.ilam[j] = (float)(1.0 / q.lam[j]);
+  }
+}
+
 __global__ void b_init_kernel(BState* S, int P) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
@@ -914,12 +1316,17 @@ sks_status check_batch(const sks_problem* probs, int count, const sks_opts* o) {
   if (o->stop_rule != SKS_STOP_ESTIMATE)
     return fail(SKS_ERR_UNSUPPORTED, "the batch stops by the estimate rule only");
   if (o->kind != SKS_SRHT) return fail(SKS_ERR_UNSUPPORTED, "batch: only the SRHT embedding is implemented");
-  if (o->precision != SKS_PLAIN_F64) return fail(SKS_ERR_UNSUPPORTED, "batch: only the plain float64 form");
+  const bool mixed = o->precision == SKS_MIXED_REFINED;
+  if (mixed && (o->max_outer < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)))
+    return fail(SKS_ERR_INVALID_ARG, "mixed form needs max_outer >= 1 and inner_tol in (0, 1)");
   for (int i = 0; i < count; ++i) {
     const sks_problem& p = probs[i];
     const sks_status v = validate_problem(&p);
     if (v != SKS_OK) return fail(v, "batch problem " + std::to_string(i) + ": " + last_error_cstr());
-    if (p.dtype != SKS_F64) return fail(SKS_ERR_INVALID_ARG, "batch problem " + std::to_string(i) + ": needs float64 A");
+    if (!mixed && p.dtype != SKS_F64)
+      return fail(SKS_ERR_INVALID_ARG, "batch problem " + std::to_string(i) + ": the plain form needs float64 A");
+    if (mixed && p.dtype != SKS_F32)
+      return fail(SKS_ERR_INVALID_ARG, "batch problem " + std::to_string(i) + ": the mixed form needs float32 A");
     if (p.k != 1) return fail(SKS_ERR_UNSUPPORTED, "batch problem " + std::to_string(i) + ": one right-hand side");
     if (p.n < 1) return fail(SKS_ERR_UNSUPPORTED, "batch problem " + std::to_string(i) + ": n >= 1");
     if (p.d > kMaxD) return fail(SKS_ERR_UNSUPPORTED, "batch problem " + std::to_string(i) + ": d <= 1024");
@@ -946,7 +1353,9 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
   for (int i = 0; i < P; ++i) {
     const sks_problem& p = probs[i];
     BDesc& q = L->host[i];
-    q.A = (const double*)p.A;
+    const bool mixed = o->precision == SKS_MIXED_REFINED;
+    q.A = mixed ? nullptr : (const double*)p.A;
+    q.Af = mixed ? (const float*)p.A : nullptr;
     q.lda = p.lda;
     q.n = p.n;
     q.d = (int)p.d;
@@ -957,7 +1366,15 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
     q.m_max = m_max_of(p, o);
     q.m_init = o->m_init;
     const int64_t n_pad = (int64_t)1 << q.bits;
-    q.B = c.take<double>((size_t)n_pad * q.d);
+    if (mixed) {
+      q.B = nullptr;
+      q.Bf = c.take<float>((size_t)n_pad * q.d);
+      q.ilam = c.take<float>((size_t)q.d);
+    } else {
+      q.B = c.take<double>((size_t)n_pad * q.d);
+      q.Bf = nullptr;
+      q.ilam = nullptr;
+    }
     q.perm = c.take<uint32_t>((size_t)q.m_max);
     q.M = c.take<double>((size_t)q.d * q.d);
     q.vec = c.take<double>((size_t)kNumVec * q.d);
@@ -995,6 +1412,8 @@ struct Round {
   int P, kmax, tot_tri, tot_T, tot_ap, tot_red;
   int g_tile, g_gram, g_trsm, g_ap, g_prob;
   size_t ap_smem;
+  bool mixed;
+  int g_apd;          // mixed form: grid of the double-float (residual) A-pass
 };
 
 // Enqueues one round on `stream`; returns the number of kernels.
@@ -1005,7 +1424,8 @@ int enqueue_round(const Round& R, cudaStream_t stream) {
   ++n;
   b_perm_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
   ++n;
-  b_gram_kernel<<<R.g_gram, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri * kGramSplit);
+  if (R.mixed) b_gram_mixed_kernel<<<R.g_gram, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri * kGramSplit);
+  else b_gram_kernel<<<R.g_gram, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri * kGramSplit);
   b_gram_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri);
   n += 2;
   for (int k = 0; k < R.kmax; ++k) {
@@ -1017,7 +1437,14 @@ int enqueue_round(const Round& R, cudaStream_t stream) {
       n += 2;
     }
   }
-  b_apass_kernel<<<R.g_ap, kApThreads, R.ap_smem, stream>>>(R.ctl, R.D, R.S, R.tot_ap);
+  if (R.mixed) {
+    b_apass_mixed_kernel<true><<<R.g_apd, kApThreads, apass_mixed_smem(true), stream>>>(R.ctl, R.D, R.S, R.tot_ap, 0);
+    b_apass_mixed_kernel<false><<<R.g_ap, kApThreads, apass_mixed_smem(false), stream>>>(R.ctl, R.D, R.S, R.tot_ap,
+                                                                                        0);
+    ++n;
+  } else {
+    b_apass_kernel<<<R.g_ap, kApThreads, R.ap_smem, stream>>>(R.ctl, R.D, R.S, R.tot_ap);
+  }
   b_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_red);
   b_step1_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
   b_apply_kernel<<<R.g_prob, 512, 0, stream>>>(R.ctl, R.D, R.S);
@@ -1145,6 +1572,9 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
   c.phi = (1.0 - std::sqrt(1.0 - rho)) / (1.0 + std::sqrt(1.0 - rho));
   c.c = 4.0 * (1.0 + std::sqrt(rho)) / (1.0 - std::sqrt(rho));
   c.tol2 = (o->tol / 2.0) * (o->tol / 2.0);
+  c.mixed = o->precision == SKS_MIXED_REFINED ? 1 : 0;
+  c.max_outer = c.mixed ? o->max_outer : 1;
+  c.inner2 = c.mixed ? o->inner_tol * o->inner_tol : 0.0;
   c.key = make_key(o->seed);
   c.pre_tri = L.pre_tri;
   c.pre_T = L.pre_T;
@@ -1161,7 +1591,8 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
     dmax = std::max(dmax, q.d);
     mmax_all = std::max(mmax_all, q.m_max);
   }
-  c.max_rounds = 4 + 2 * (ilog2_ceil(mmax_all) + 2) + c.max_iter;
+  // every doubling and every refinement step (residual, restart) costs a round
+  c.max_rounds = 4 + 2 * (ilog2_ceil(mmax_all) + 2) + c.max_iter + 3 * c.max_outer;
   R.kmax = (dmax + kTile - 1) / kTile;
   R.tot_tri = pre_tri[P];
   R.tot_T = pre_T[P];
@@ -1170,12 +1601,25 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
   R.g_tile = std::max(1, std::min(R.tot_tri, 4 * sms));
   R.g_gram = std::max(1, std::min(R.tot_tri * kGramSplit, 4 * sms));
   R.g_trsm = std::max(1, std::min(R.tot_T, 8 * sms));
-  R.ap_smem = (size_t)(1 + kApWarps) * kMaxD * sizeof(double);
-  SKS_CUDA_TRY(cudaFuncSetAttribute(b_apass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R.ap_smem));
+  R.mixed = c.mixed != 0;
+  R.ap_smem = R.mixed ? apass_mixed_smem(false) : (size_t)(1 + kApWarps) * kMaxD * sizeof(double);
   SKS_CUDA_TRY(cudaFuncSetAttribute(b_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsmSmem));
-  int ap_occ = 1;
-  SKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ap_occ, b_apass_kernel, kApThreads, R.ap_smem));
+  int ap_occ = 1, apd_occ = 1;
+  if (R.mixed) {
+    SKS_CUDA_TRY(cudaFuncSetAttribute(b_apass_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)apass_mixed_smem(false)));
+    SKS_CUDA_TRY(cudaFuncSetAttribute(b_apass_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)apass_mixed_smem(true)));
+    SKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ap_occ, b_apass_mixed_kernel<false>, kApThreads,
+                                                               apass_mixed_smem(false)));
+    SKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&apd_occ, b_apass_mixed_kernel<true>, kApThreads,
+                                                               apass_mixed_smem(true)));
+  } else {
+    SKS_CUDA_TRY(cudaFuncSetAttribute(b_apass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R.ap_smem));
+    SKS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ap_occ, b_apass_kernel, kApThreads, R.ap_smem));
+  }
   const int ap_grid_max = sms * std::max(1, ap_occ);
+  const int apd_grid_max = sms * std::max(1, apd_occ);
 
   // ---- autotune the A-pass unit height on this batch (all problems in INIT)
   SKS_CUDA_TRY(cudaEventRecord(ev_tune.a, stream));
@@ -1192,9 +1636,12 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
       ct.rows_per_unit = rows;
       ct.tk = nullptr;
       const int g = std::max(1, std::min(pa[P], ap_grid_max));
-      b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);  // warm
-      SKS_CUDA_TRY(cudaEventRecord(e.a, stream));
-      for (int rep = 0; rep < 3; ++rep) b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);
+      // the mixed form times its float32 inner pass (every unit, v = 0)
+      for (int rep = 0; rep < 4; ++rep) {
+        if (rep == 1) SKS_CUDA_TRY(cudaEventRecord(e.a, stream));  // after one warm launch
+        if (R.mixed) b_apass_mixed_kernel<false><<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P], 1);
+        else b_apass_kernel<<<g, kApThreads, R.ap_smem, stream>>>(ct, L.D, L.S, pa[P]);
+      }
       SKS_CUDA_TRY(cudaEventRecord(e.b, stream));
       note_launch(4);
       SKS_CUDA_TRY(cudaGetLastError());
@@ -1211,6 +1658,7 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
   c.rows_per_unit = chosen;
   R.tot_ap = pre_ap[P];
   R.g_ap = std::max(1, std::min(R.tot_ap, ap_grid_max));
+  R.g_apd = std::max(1, std::min(R.tot_ap, apd_grid_max));
   B->chosen = chosen;
   SKS_CUDA_TRY(cudaEventRecord(ev_tune.b, stream));
 
@@ -1224,9 +1672,11 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
     b_reset_kernel<<<1, 32, 0, B->cs>>>(c);
     b_init_kernel<<<(P + 127) / 128, 128, 0, B->cs>>>(L.S, P);
     sks_status sr = SKS_OK;
+    if (R.mixed) b_prep_mixed_kernel<<<std::min(P, 4 * sms), 256, 0, B->cs>>>(L.D, P);
     for (int i = 0; i < P && sr == SKS_OK; ++i) {
       const BDesc& q = L.host[i];
-      sr = srht_form<double>(B->cs, q.A, q.lda, q.n, q.d, (double*)q.B, q.d, o->seed);
+      if (R.mixed) sr = srht_form<float>(B->cs, q.Af, q.lda, q.n, q.d, q.Bf, q.d, o->seed);
+      else sr = srht_form<double>(B->cs, q.A, q.lda, q.n, q.d, (double*)q.B, q.d, o->seed);
     }
     cudaGraph_t got = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(B->cs, &got);
@@ -1272,7 +1722,7 @@ sks_status batch_solve(sks_batch* B, double* const* xs, sks_stats* stats, sks_ba
   SKS_CUDA_TRY(cudaMemcpyAsync(L.D, L.host.data(), P * sizeof(BDesc), cudaMemcpyHostToDevice, stream));
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.a, stream));
   SKS_CUDA_TRY(cudaGraphLaunch(B->e, stream));
-  note_launch(2 + 3 * P);  // setup kernels (counted per round below)
+  note_launch(2 + 3 * P + (B->R.mixed ? 1 : 0));  // setup kernels (counted per round below)
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.b, stream));
 
   // ---- per-problem results (the one synchronisation of the solve)
@@ -1301,7 +1751,7 @@ sks_status batch_solve(sks_batch* B, double* const* xs, sks_stats* stats, sks_ba
     if (stats) {
       sks_stats& t = stats[i];
       std::memset(&t, 0, sizeof(t));
-      t.iters = s.t;
+      t.iters = s.t_all;
       t.rejections = s.rejections;
       t.final_m = s.m;
       t.a_passes = s.a_passes;
@@ -1309,7 +1759,8 @@ sks_status batch_solve(sks_batch* B, double* const* xs, sks_stats* stats, sks_ba
       t.factorizations = s.factorizations;
       t.final_delta_tilde = s.dt;
       t.est_rel_err = s.btx > 0 ? std::sqrt(std::max(0.0, s.dt / s.btx)) : 0.0;
-      t.outer_iters = 1;
+      // mixed form: refinement residuals computed (the last one met the stop rule)
+      t.outer_iters = B->R.mixed ? (int64_t)s.outer + (s.phase == PH_DONE ? 1 : 0) : 1;
       t.ms_total = ms_solve;
       t.status = (sks_status)s.status;
     }

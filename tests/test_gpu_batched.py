@@ -113,3 +113,71 @@ def test_batched_solver_is_reusable():
     for a, b in zip(xa, xb):
         assert torch.equal(a, b)
     assert [s["iters"] for s in sa] == [s["iters"] for s in sb]
+
+
+# ---- mixed form (float32 A, iterative refinement around Algorithm 2)
+
+def to_dev32(probs):
+    return [(dev(p.A.astype(np.float32)), dev(p.b), p.nu, dev(p.lam)) for p in probs]
+
+
+def up32(p):
+    """The problem the mixed form solves: A rounded to float32, upcast exactly."""
+    return p.A.astype(np.float32).astype(np.float64)
+
+
+def test_batched_mixed_matches_oracle():
+    probs = batch_problems(SHAPES, seed0=50)
+    tol = 1e-8
+    xs, stats, info = api().solve_batched(to_dev32(probs), precision="mixed", tol=tol, max_iter=2000)
+    assert info["rounds"] > 0
+    for p, x, st in zip(probs, xs, stats):
+        assert st["status"] == 0, st
+        A = up32(p)
+        ref = O.direct_solve(A, p.b, p.nu, p.lam)
+        err = O.rel_err_H(A, p.nu, p.lam, host(x), ref)
+        assert err <= tol, (p.A.shape, p.nu, err, st)
+        assert st["outer_iters"] >= 1 and st["final_m"] >= 1
+        # the estimate the stop rule used is the decrement at the returned x
+        assert st["est_rel_err"] <= tol
+
+
+def test_batched_mixed_edge_cases_and_reuse():
+    probs = batch_problems(SHAPES[1:4], seed0=60)
+    items = to_dev32(probs)
+    items[0] = (items[0][0], torch.zeros_like(items[0][1]), items[0][2], items[0][3])
+    solver = api().BatchSolver(items, precision="mixed", tol=1e-8)
+    xa, sa, _ = solver.solve()
+    xb, sb, _ = solver.solve()
+    assert np.all(host(xa[0]) == 0.0) and sa[0]["iters"] == 0 and sa[0]["status"] == 0
+    for a, b in zip(xa, xb):
+        assert torch.equal(a, b)
+    for i in (1, 2):
+        p = probs[i]
+        A = up32(p)
+        assert O.rel_err_H(A, p.nu, p.lam, host(xa[i]), O.direct_solve(A, p.b, p.nu, p.lam)) <= 1e-8
+    # a warm start near the solution: converged, and no more work than from 0
+    x0s = [torch.zeros(p.A.shape[1], dtype=torch.float64, device="cuda") for p in probs]
+    A2 = up32(probs[2])
+    ref2 = O.direct_solve(A2, probs[2].b, probs[2].nu, probs[2].lam)
+    x0s[2] = dev(ref2 * (1 + 1e-6))
+    xw, sw, _ = solver.solve(x0s=x0s)
+    assert sw[2]["status"] == 0 and sw[2]["iters"] <= sa[2]["iters"]
+    assert O.rel_err_H(A2, probs[2].nu, probs[2].lam, host(xw[2]), ref2) <= 1e-8
+
+
+def test_batched_mixed_reports_no_convergence_after_max_outer():
+    # one refinement step with a loose inner solve cannot reach 1e-10
+    probs = batch_problems([SHAPES[3], SHAPES[5]], seed0=70)
+    solver = api().BatchSolver(to_dev32(probs), precision="mixed", tol=1e-10, max_outer=1, inner_tol=0.5)
+    xs, stats, _ = solver.solve(check=False)
+    for st in stats:
+        assert st["status_name"] == "NO_CONVERGENCE" and st["outer_iters"] == 1
+
+
+def test_batched_precision_must_match_the_dtype_of_A():
+    probs = batch_problems(SHAPES[:2], seed0=80)
+    with pytest.raises(api()._lib.SksError, match="mixed form needs float32 A"):
+        api().BatchSolver(to_dev(probs), precision="mixed")
+    with pytest.raises(api()._lib.SksError, match="plain form needs float64 A"):
+        api().BatchSolver(to_dev32(probs), precision="plain")

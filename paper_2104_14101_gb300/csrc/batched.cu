@@ -41,9 +41,11 @@
 // is chosen by timing candidate heights on the actual batch (autotuning).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
+#include "df32.cuh"
 #include "internal.h"
 #include "sketch.h"
 
@@ -77,6 +79,7 @@ struct BDesc {
   const float* Af;   // mixed form: the float32 A (A is NULL)
   float* Bf;         // mixed form: float32 H E A_pad, n_pad x d, ld d (B is NULL)
   float* ilam;       // mixed form: 1 / lambda rounded to float32 (Woodbury Gram)
+  double* Li;        // mixed form: inverses of the factor's 64 x 64 diagonal blocks (block b at b * 4096)
   uint32_t* perm;    // sketch row r is B[perm[r]]
   double* M;         // d x d, ld d: lower = factor L, strict upper = L^T
   double* vec;       // kNumVec d-vectors
@@ -100,6 +103,8 @@ struct BState {
   int outer, fresh;
   double d0;
   int64_t t_all;
+  int sexp;   // mixed form: the factorisation works on 2^(-2 sexp) M
+  int xzero;  // x_0 = 0: the first residual is b, without a pass over A
 };
 
 struct BCtl {
@@ -126,6 +131,7 @@ struct BCtl {
   // the graph's while loop: rounds run while some problem is unfinished and
   // fewer than max_rounds have run (the count kernel sets the condition)
   cudaGraphConditionalHandle cond;
+  int use_cond;        // 0: rounds launched one by one (stepwise mode), no graph condition
   long long* rounds;
   long long max_rounds;
 };
@@ -150,7 +156,7 @@ SKS_DEV int find_problem(const int* __restrict__ pre, int P, int u) {
 }
 
 SKS_DEV void tri_index(int l, int* ti, int* tj) {
-  int i = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+  int i = (int)((sqrtf(8.0f * (float)l + 1.0f) - 1.0f) * 0.5f);
   while ((i + 1) * (i + 2) / 2 <= l) ++i;
   while (i * (i + 1) / 2 > l) --i;
   *ti = i;
@@ -186,6 +192,7 @@ __global__ void b_begin_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
 // perm[r] = pi(r) for the new sketch rows r in [m_old, m)
 __global__ void b_perm_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
@@ -279,6 +286,7 @@ __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __rest
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int tu = u / kGramSplit, ks = u - tu * kGramSplit;
     const int p = find_problem(c.pre_tri, c.P, tu);
+    if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
@@ -375,6 +383,7 @@ __global__ void __launch_bounds__(256) b_gram_mixed_kernel(BCtl c, const BDesc* 
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int tu = u / kGramSplit, ks = u - tu * kGramSplit;
     const int p = find_problem(c.pre_tri, c.P, tu);
+    if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
@@ -463,6 +472,7 @@ __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc*
   tk_start(c, TK_GRAM);
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = find_problem(c.pre_tri, c.P, u);
+    if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
@@ -501,6 +511,7 @@ __global__ void __launch_bounds__(256) b_potrf_kernel(BCtl c, const BDesc* __res
   __shared__ double L[kTile][kTile + 1];
   __shared__ int bad;
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
@@ -571,6 +582,7 @@ __global__ void __launch_bounds__(64) b_trsm_kernel(BCtl c, const BDesc* __restr
   double (*X)[kTile + 1] = (double (*)[kTile + 1])(tr_smem + kTile * (kTile + 1));  // [64][65]
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = find_problem(c.pre_T, c.P, u);
+    if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
@@ -619,6 +631,7 @@ __global__ void __launch_bounds__(256) b_update_kernel(BCtl c, const BDesc* __re
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = find_problem(c.pre_tri, c.P, u);
+    if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
     if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
@@ -656,6 +669,273 @@ __global__ void __launch_bounds__(256) b_update_kernel(BCtl c, const BDesc* __re
       for (int j = 0; j < 4; ++j) {
         const int gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
         if (gi < N && gj < N) q.M[(int64_t)gi * d + gj] -= acc[i][j];
+      }
+  }
+  tk_stop(c, TK_FACTOR);
+}
+
+// ---- mixed form: the factorisation in double-float arithmetic
+//
+// The batch's float64 factorisation is bound, along its chain of 64-column
+// panels, by the float64 pipe (two FMAs per clock per SM).  The mixed form
+// runs the same blocked Cholesky on the float32 pipe: every M value is split
+// into a float pair by integer operations after a power-of-two scaling
+// (M' = 2^(-2 sexp) M, largest diagonal entry in [1, 4), so no pair
+// underflows), and written back as float64 at its true scale.  The diagonal
+// block's kernel also inverts its factor, so the panel below is a product
+// (L_ik = M_ik L_kk^{-T}) and the apply multiplies by the block inverses
+// instead of running a substitution chain.
+
+// float64 x 2^sh -> float pair, and back (integer operations but one float64 add)
+SKS_DEV F2 to_f2(double v, int sh) { return split_f64(scale_pow2(v, sh)); }
+SKS_DEV double from_f2(F2 v, int sh) { return scale_pow2(f32_to_f64_bits(v.h) + f32_to_f64_bits(v.l), sh); }
+
+// Panel k, diagonal block, mixed form: L_kk = chol(M_kk) and X = L_kk^{-1},
+// both right-looking, in registers: thread (c, g) holds column c, rows
+// g + 4q (q < 16) of the block and of X.  Step j: the pivot's owner
+// publishes it; the four owners of column j scale it and publish it; every
+// thread updates its trailing entries with column j, the owners of row j of
+// X scale that row and publish it, and every thread updates its rows of X
+// below j.  Writes L_kk (lower), L_kk^T (strict upper) and X (Li block k).
+// At k = 0 the CTA first picks the problem's scaling exponent.
+__global__ void __launch_bounds__(256) b_potrf_df_kernel(BCtl c, const BDesc* __restrict__ D, BState* S, int k) {
+  __shared__ F2 colv[kTile], xrow[kTile];
+  __shared__ F2 s_piv, s_r;
+  __shared__ int s_bad, s_emax;
+  tk_start(c, TK_FACTOR);
+  const int tid = threadIdx.x, cc = tid & 63, g = tid >> 6;
+  for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    if (S[p].phase != PH_GROW) continue;
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    const int N = factor_size(s, q);
+    const int k0 = k * kTile;
+    if (k0 >= N) continue;
+    const int nb = min(kTile, N - k0);
+    const int d = q.d;
+    int te;
+    if (k == 0) {
+      if (tid == 0) s_emax = -1100;
+      __syncthreads();
+      int e = -1100;
+      for (int i = tid; i < N; i += blockDim.x) {
+        const long long b = __double_as_longlong(q.M[(int64_t)i * d + i]);
+        const int E = (int)((b >> 52) & 0x7ff);
+        if (b > 0 && E > 0 && E < 0x7ff) e = max(e, E - 1023);
+      }
+      atomicMax(&s_emax, e);
+      __syncthreads();
+      const int em = s_emax > -1000 ? s_emax : 0;
+      te = (em - (em & 1)) / 2;  // 2 te <= em < 2 te + 2
+      if (tid == 0) S[p].sexp = te;
+    } else {
+      te = s.sexp;
+    }
+    F2 v[16], xi[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = g + 4 * r;
+      v[r] = (i < nb && cc <= i) ? to_f2(q.M[(int64_t)(k0 + i) * d + k0 + cc], -2 * te) : F2{0.f, 0.f};
+      xi[r] = (i < nb && cc == i) ? F2{1.f, 0.f} : F2{0.f, 0.f};
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      const int jr = j >> 2, jg = j & 3;
+      if (cc == j && g == jg) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          if (r == jr) s_piv = v[r];
+      }
+      __syncthreads();
+      if (cc == j) {
+        const F2 pv = s_piv;
+        if (!(pv.h > 0.f) || !isfinite(pv.h)) {
+          if (g == jg) s_bad = j + 1;
+        } else {
+          const F2 r = f2_rsqrt(pv);  // 1 / L_jj
+#pragma unroll
+          for (int rr = 0; rr < 16; ++rr) {
+            const int i = g + 4 * rr;
+            if (i > j && i < nb) {
+              v[rr] = f2_mul(v[rr], r);
+              colv[i] = v[rr];
+            } else if (i == j) {
+              v[rr] = f2_mul(pv, r);  // L_jj = p / sqrt(p)
+              s_r = r;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (s_bad) break;
+      if (cc > j) {
+        const F2 lc = colv[cc];
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const int i = g + 4 * rr;
+          if (i >= cc && i < nb) f2_acc<true>(v[rr].h, v[rr].l, colv[i], lc);
+        }
+      }
+      if (g == jg && cc <= j) {
+        const F2 r = s_r;
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr)
+          if (rr == jr) {
+            xi[rr] = f2_mul(xi[rr], r);
+            xrow[cc] = xi[rr];
+          }
+      }
+      __syncthreads();
+      if (cc <= j) {
+        const F2 xj = xrow[cc];
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const int i = g + 4 * rr;
+          if (i > j && i < nb) f2_acc<true>(xi[rr].h, xi[rr].l, colv[i], xj);
+        }
+      }
+    }
+    if (s_bad) {
+      if (tid == 0) {
+        S[p].status = SKS_ERR_NOT_PD;
+        S[p].phase = PH_FAIL;
+      }
+      __syncthreads();
+      continue;
+    }
+    double* Lib = q.Li + (size_t)k * (kTile * kTile);
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      const int i = g + 4 * rr;
+      if (i < nb && cc <= i) {
+        const double val = from_f2(v[rr], te);
+        q.M[(int64_t)(k0 + i) * d + k0 + cc] = val;
+        if (cc < i) q.M[(int64_t)(k0 + cc) * d + k0 + i] = val;
+      }
+      Lib[i * kTile + cc] = (i < nb && cc <= i) ? from_f2(xi[rr], -te) : 0.0;
+    }
+    __syncthreads();
+  }
+  tk_stop(c, TK_FACTOR);
+}
+
+// acc[i][j] += sum over 16 steps of a[k][ty*4+i] b[k][tx*4+j] in double-float
+SKS_DEV void df_tile_chunk(const float (*Ah)[kTPf], const float (*Al)[kTPf], const float (*Bh)[kTPf],
+                           const float (*Bl)[kTPf], F2 (&acc)[4][4], int tx, int ty) {
+#pragma unroll 2
+  for (int k = 0; k < 16; ++k) {
+    const float4 ah = *(const float4*)&Ah[k][ty * 4], al = *(const float4*)&Al[k][ty * 4];
+    const float4 bh = *(const float4*)&Bh[k][tx * 4], bl = *(const float4*)&Bl[k][tx * 4];
+    const F2 a[4] = {{ah.x, al.x}, {ah.y, al.y}, {ah.z, al.z}, {ah.w, al.w}};
+    const F2 b[4] = {{bh.x, bl.x}, {bh.y, bl.y}, {bh.z, bl.z}, {bh.w, bl.w}};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) f2_acc<false>(acc[i][j].h, acc[i][j].l, a[i], b[j]);
+  }
+}
+
+// acc = A B^T for a 64 x 64 output tile: A rows ra (< na valid), B rows rb
+// (< nbv valid), K columns (both row-major, float64, scaled by 2^sha / 2^shb
+// on the way in).
+SKS_DEV void df_tile_abt(const double* __restrict__ A, int64_t lda, int na, int sha, const double* __restrict__ B,
+                         int64_t ldb, int nbv, int shb, int K, F2 (&acc)[4][4], float (*Ah)[kTPf],
+                         float (*Al)[kTPf], float (*Bh)[kTPf], float (*Bl)[kTPf]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = F2{0.f, 0.f};
+  for (int c0 = 0; c0 < K; c0 += 16) {
+    for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+      const int ii = e >> 4, kk = e & 15;
+      const int col = c0 + kk;
+      F2 a = {0.f, 0.f}, b = {0.f, 0.f};
+      if (col < K) {
+        if (ii < na) a = to_f2(A[(int64_t)ii * lda + col], sha);
+        if (ii < nbv) b = to_f2(B[(int64_t)ii * ldb + col], shb);
+      }
+      Ah[kk][ii] = a.h;
+      Al[kk][ii] = a.l;
+      Bh[kk][ii] = b.h;
+      Bl[kk][ii] = b.l;
+    }
+    __syncthreads();
+    df_tile_chunk(Ah, Al, Bh, Bl, acc, tx, ty);
+    __syncthreads();
+  }
+}
+
+// Panel k, blocks below the diagonal, mixed form: L_ik = M_ik L_kk^{-T}
+// (a product with the block inverse), to the lower part and transposed to
+// the upper part.
+__global__ void __launch_bounds__(256) b_trsm_df_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
+                                                        int total) {
+  __shared__ __align__(16) float Ah[16][kTPf], Al[16][kTPf], Bh[16][kTPf], Bl[16][kTPf];
+  tk_start(c, TK_FACTOR);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_T, c.P, u);
+    if (S[p].phase != PH_GROW) continue;
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    const int N = factor_size(s, q);
+    const int i = u - c.pre_T[p];
+    const int k0 = k * kTile, i0 = i * kTile;
+    if (i <= k || i0 >= N) continue;
+    const int nb = min(kTile, N - k0), rb = min(kTile, N - i0);
+    const int d = q.d, te = s.sexp;
+    F2 acc[4][4];
+    // M'_ik (2^-2te M) times X' (2^te X): 2^-te L_ik
+    df_tile_abt(q.M + (int64_t)i0 * d + k0, d, rb, -2 * te, q.Li + (size_t)k * (kTile * kTile), kTile, nb, te, nb,
+                acc, Ah, Al, Bh, Bl);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int r = ty * 4 + a, cl = tx * 4 + b;
+        if (r < rb && cl < nb) {
+          const double val = from_f2(acc[a][b], te);
+          q.M[(int64_t)(i0 + r) * d + k0 + cl] = val;
+          q.M[(int64_t)(k0 + cl) * d + i0 + r] = val;
+        }
+      }
+  }
+  tk_stop(c, TK_FACTOR);
+}
+
+// Panel k, trailing update of the lower tiles (ti >= tj > k), mixed form:
+// M_ij -= L_ik L_jk^T with the product in double-float.
+__global__ void __launch_bounds__(256) b_update_df_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
+                                                          int total) {
+  __shared__ __align__(16) float Ah[16][kTPf], Al[16][kTPf], Bh[16][kTPf], Bl[16][kTPf];
+  tk_start(c, TK_FACTOR);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = find_problem(c.pre_tri, c.P, u);
+    if (S[p].phase != PH_GROW) continue;
+    const BState s = S[p];
+    if (s.phase != PH_GROW) continue;
+    const BDesc& q = D[p];
+    int ti, tj;
+    tri_index(u - c.pre_tri[p], &ti, &tj);
+    const int N = factor_size(s, q);
+    const int k0 = k * kTile, i0 = ti * kTile, j0 = tj * kTile;
+    if (tj <= k || i0 >= N) continue;
+    const int nb = min(kTile, N - k0);
+    const int d = q.d, te = s.sexp;
+    F2 acc[4][4];
+    df_tile_abt(q.M + (int64_t)i0 * d + k0, d, min(kTile, N - i0), -te, q.M + (int64_t)j0 * d + k0, d,
+                min(kTile, N - j0), -te, nb, acc, Ah, Al, Bh, Bl);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int gi = i0 + ty * 4 + a, gj = j0 + tx * 4 + b;
+        if (gi < N && gj < N) q.M[(int64_t)gi * d + gj] -= from_f2(acc[a][b], 2 * te);
       }
   }
   tk_stop(c, TK_FACTOR);
@@ -716,6 +996,7 @@ __global__ void __launch_bounds__(kApThreads, 1) b_apass_kernel(BCtl c, const BD
     const int p = find_problem(c.pre_ap, c.P, u);
     const int phase = S[p].phase;
     if (phase != PH_INIT && phase != PH_ITER) continue;
+    if (phase == PH_INIT && S[p].xzero) continue;  // H x_0 = 0
     const BDesc& q = D[p];
     const int d = q.d;
     const double* v = phase == PH_INIT ? q.x : q.vec + (size_t)V_P * d;
@@ -876,6 +1157,7 @@ __global__ void __launch_bounds__(kApThreads) b_apass_mixed_kernel(BCtl c, const
     const int p = find_problem(c.pre_ap, c.P, u);
     const int phase = S[p].phase;
     if (!tune && phase != (DF ? PH_INIT : PH_ITER)) continue;
+    if (DF && !tune && S[p].xzero && S[p].outer == 0) continue;  // H x_0 = 0
     const BDesc& q = D[p];
     const int d = q.d;
     if (DF) {
@@ -927,6 +1209,10 @@ __global__ void __launch_bounds__(256) b_reduce_kernel(BCtl c, const BDesc* __re
     const int d = q.d;
     const int col = (u - c.pre_red[p]) * 256 + threadIdx.x;
     if (col >= d) continue;
+    if (phase == PH_INIT && S[p].xzero && S[p].outer == 0) {  // H x_0 = 0: no pass was made
+      q.vec[(size_t)V_HV * d + col] = 0.0;
+      continue;
+    }
     const int units = (int)((q.n + c.rows_per_unit - 1) / c.rows_per_unit);
     const double* v = phase == PH_INIT ? q.x : q.vec + (size_t)V_P * d;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -982,7 +1268,7 @@ __global__ void __launch_bounds__(256) b_step1_kernel(BCtl c, const BDesc* __res
         S[p].phase = PH_FAIL;
       }
     }
-    if (threadIdx.x == 0) S[p].a_passes += 1;
+    if (threadIdx.x == 0 && !(phase == PH_INIT && S[p].xzero && S[p].outer == 0)) S[p].a_passes += 1;
     __syncthreads();
   }
 }
@@ -1027,6 +1313,48 @@ SKS_DEV void tri_solve(const double* __restrict__ M, int ld, int N, const double
   }
 }
 
+// The same solves with the inverses of the diagonal blocks (Li, mixed form):
+// per block the off-diagonal part as above, then y_b = X_bb y_b (lower) or
+// X_bb^T y_b (upper) as a product -- no substitution chain.  tmp: 64 doubles
+// of shared memory.
+SKS_DEV void tri_solve_inv(const double* __restrict__ M, int ld, int N, const double* __restrict__ Li, double* y,
+                           bool upper, double* tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nblk = (N + kTile - 1) / kTile;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = upper ? nblk - 1 - bi : bi;
+    const int b0 = blk * kTile, nb = min(kTile, N - b0);
+    const int j0 = upper ? b0 + nb : 0, j1 = upper ? N : b0;
+    if (j1 > j0) {
+      for (int i = warp; i < nb; i += nw) {
+        const double* row = M + (int64_t)(b0 + i) * ld;
+        double s = 0.0;
+        for (int j = j0 + lane; j < j1; j += 32) s = fma(row[j], y[j], s);
+        s = warp_sum(s);
+        if (lane == 0) y[b0 + i] -= s;
+      }
+    }
+    __syncthreads();
+    const double* X = Li + (size_t)blk * (kTile * kTile);
+    if (!upper) {
+      for (int i = warp; i < nb; i += nw) {
+        double s = 0.0;
+        for (int l = lane; l <= i; l += 32) s = fma(X[i * kTile + l], y[b0 + l], s);
+        s = warp_sum(s);
+        if (lane == 0) tmp[i] = s;
+      }
+    } else if (threadIdx.x < nb) {
+      const int i = threadIdx.x;
+      double s = 0.0;
+      for (int l = i; l < nb; ++l) s = fma(X[l * kTile + i], y[b0 + l], s);
+      tmp[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) y[b0 + threadIdx.x] = tmp[threadIdx.x];
+    __syncthreads();
+  }
+}
+
 // GROW: r~ = H_S^{-1} r.   ITER: r~+ = H_S^{-1} r+.
 //   form 0: H_S = L L^T (two triangular solves)
 //   form 1: H_S^{-1} z = u - (nu^2 Lambda)^{-1} Y_s^T K^{-1} Y_s u,  u = (nu^2 Lambda)^{-1} z,
@@ -1034,6 +1362,7 @@ SKS_DEV void tri_solve(const double* __restrict__ M, int ld, int N, const double
 __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S) {
   tk_start(c, TK_APPLY);
   __shared__ double y[kMaxD];
+  __shared__ double tmp[kTile];
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     const BState s = S[p];
     if (s.phase != PH_GROW && s.phase != PH_ITER && s.phase != PH_RESTART) continue;
@@ -1046,8 +1375,13 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
     if (s.form == 0) {
       for (int j = threadIdx.x; j < d; j += blockDim.x) y[j] = z[j];
       __syncthreads();
-      tri_solve(q.M, d, d, dinv, y, false);
-      tri_solve(q.M, d, d, dinv, y, true);
+      if (q.Li) {
+        tri_solve_inv(q.M, d, d, q.Li, y, false, tmp);
+        tri_solve_inv(q.M, d, d, q.Li, y, true, tmp);
+      } else {
+        tri_solve(q.M, d, d, dinv, y, false);
+        tri_solve(q.M, d, d, dinv, y, true);
+      }
       for (int j = threadIdx.x; j < d; j += blockDim.x) out[j] = y[j];
     } else {
       const int m = (int)s.m;
@@ -1068,8 +1402,13 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
         if (lane == 0) y[r] = t * ism;
       }
       __syncthreads();
-      tri_solve(q.M, d, m, dinv, y, false);
-      tri_solve(q.M, d, m, dinv, y, true);
+      if (q.Li) {
+        tri_solve_inv(q.M, d, m, q.Li, y, false, tmp);
+        tri_solve_inv(q.M, d, m, q.Li, y, true, tmp);
+      } else {
+        tri_solve(q.M, d, m, dinv, y, false);
+        tri_solve(q.M, d, m, dinv, y, true);
+      }
       for (int j = threadIdx.x; j < d; j += blockDim.x) {
         double t = 0.0;
         if (q.Bf) {
@@ -1232,7 +1571,7 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
   if (threadIdx.x == 0) {
     *c.active = a;
     const long long r = ++*c.rounds;
-    cudaGraphSetConditional(c.cond, (a > 0 && r < c.max_rounds) ? 1u : 0u);
+    if (c.use_cond) cudaGraphSetConditional(c.cond, (a > 0 && r < c.max_rounds) ? 1u : 0u);
     if (c.tk) {
       c.tk[3 * TK_ROUND + 1] = global_ns();
       for (int i = 0; i < kTimers; ++i) {
@@ -1273,6 +1612,21 @@ __global__ void b_prep_mixed_kernel(const BDesc* __restrict__ D, int P) {
   for (int p = blockIdx.x; p < P; p += gridDim.x) {
     const BDesc& q = D[p];
     for (int j = threadIdx.x; j < q.d; j += blockDim.x) q.ilam[j] = (float)(1.0 / q.lam[j]);
+  }
+}
+
+// x_0 = 0 (the usual start): the first r = b - H x_0 needs no pass over A.
+__global__ void b_xzero_kernel(const BDesc* __restrict__ D, BState* S, int P) {
+  __shared__ int any;
+  for (int p = blockIdx.x; p < P; p += gridDim.x) {
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const BDesc& q = D[p];
+    for (int j = threadIdx.x; j < q.d; j += blockDim.x)
+      if (q.x[j] != 0.0) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) S[p].xzero = any ? 0 : 1;
+    __syncthreads();
   }
 }
 
@@ -1370,7 +1724,9 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
       q.B = nullptr;
       q.Bf = c.take<float>((size_t)n_pad * q.d);
       q.ilam = c.take<float>((size_t)q.d);
+      q.Li = c.take<double>((size_t)((q.d + kTile - 1) / kTile) * kTile * kTile);
     } else {
+      q.Li = nullptr;
       q.B = c.take<double>((size_t)n_pad * q.d);
       q.Bf = nullptr;
       q.ilam = nullptr;
@@ -1429,11 +1785,17 @@ int enqueue_round(const Round& R, cudaStream_t stream) {
   b_gram_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri);
   n += 2;
   for (int k = 0; k < R.kmax; ++k) {
-    b_potrf_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S, k);
+    if (R.mixed) b_potrf_df_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S, k);
+    else b_potrf_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S, k);
     ++n;
     if (k + 1 < R.kmax) {
-      b_trsm_kernel<<<R.g_trsm, 64, kTrsmSmem, stream>>>(R.ctl, R.D, R.S, k, R.tot_T);
-      b_update_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, k, R.tot_tri);
+      if (R.mixed) {
+        b_trsm_df_kernel<<<R.g_trsm, 256, 0, stream>>>(R.ctl, R.D, R.S, k, R.tot_T);
+        b_update_df_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, k, R.tot_tri);
+      } else {
+        b_trsm_kernel<<<R.g_trsm, 64, kTrsmSmem, stream>>>(R.ctl, R.D, R.S, k, R.tot_T);
+        b_update_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, k, R.tot_tri);
+      }
       n += 2;
     }
   }
@@ -1513,6 +1875,25 @@ sks_status batch_workspace_size(const sks_problem* probs, int count, const sks_o
   Layout L;
   SKS_TRY(batch_layout(probs, count, o, nullptr, 0, &L));
   *bytes = L.used;
+  return SKS_OK;
+}
+
+// The solve's setup: counters reset, every problem INIT, 1 / lambda (mixed
+// form) and H E A_pad of every problem.
+sks_status enqueue_setup(const sks_batch* B, const BCtl& c, cudaStream_t stream) {
+  const Layout& L = B->L;
+  const int P = B->P;
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  b_reset_kernel<<<1, 32, 0, stream>>>(c);
+  b_init_kernel<<<(P + 127) / 128, 128, 0, stream>>>(L.S, P);
+  b_xzero_kernel<<<std::min(P, 4 * sms), 256, 0, stream>>>(L.D, L.S, P);
+  if (B->R.mixed) b_prep_mixed_kernel<<<std::min(P, 4 * sms), 256, 0, stream>>>(L.D, P);
+  for (int i = 0; i < P; ++i) {
+    const BDesc& q = L.host[i];
+    const sks_status sr = B->R.mixed ? srht_form<float>(stream, q.Af, q.lda, q.n, q.d, q.Bf, q.d, B->opts.seed)
+                                     : srht_form<double>(stream, q.A, q.lda, q.n, q.d, (double*)q.B, q.d, B->opts.seed);
+    if (sr != SKS_OK) return sr;
+  }
   return SKS_OK;
 }
 
@@ -1669,15 +2050,7 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
   SKS_CUDA_TRY(cudaStreamBeginCaptureToGraph(B->cs, B->g_setup, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
   {
-    b_reset_kernel<<<1, 32, 0, B->cs>>>(c);
-    b_init_kernel<<<(P + 127) / 128, 128, 0, B->cs>>>(L.S, P);
-    sks_status sr = SKS_OK;
-    if (R.mixed) b_prep_mixed_kernel<<<std::min(P, 4 * sms), 256, 0, B->cs>>>(L.D, P);
-    for (int i = 0; i < P && sr == SKS_OK; ++i) {
-      const BDesc& q = L.host[i];
-      if (R.mixed) sr = srht_form<float>(B->cs, q.Af, q.lda, q.n, q.d, q.Bf, q.d, o->seed);
-      else sr = srht_form<double>(B->cs, q.A, q.lda, q.n, q.d, (double*)q.B, q.d, o->seed);
-    }
+    const sks_status sr = enqueue_setup(B, c, B->cs);
     cudaGraph_t got = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(B->cs, &got);
     SKS_TRY(sr);
@@ -1688,6 +2061,7 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
   SKS_CUDA_TRY(cudaGraphConditionalHandleCreate(&c.cond, B->g, 1u, cudaGraphCondAssignDefault));
   cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
   np.conditional.handle = c.cond;
+  c.use_cond = 1;
   np.conditional.type = cudaGraphCondTypeWhile;
   np.conditional.size = 1;
   SKS_CUDA_TRY(cudaGraphAddNode(&n_while, B->g, &n_setup, nullptr, 1, &np));
@@ -1721,8 +2095,26 @@ sks_status batch_solve(sks_batch* B, double* const* xs, sks_stats* stats, sks_ba
   SKS_TRY(ev_solve.init());
   SKS_CUDA_TRY(cudaMemcpyAsync(L.D, L.host.data(), P * sizeof(BDesc), cudaMemcpyHostToDevice, stream));
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.a, stream));
-  SKS_CUDA_TRY(cudaGraphLaunch(B->e, stream));
-  note_launch(2 + 3 * P + (B->R.mixed ? 1 : 0));  // setup kernels (counted per round below)
+  const char* sw = std::getenv("SKS_BATCH_STEPWISE");
+  if (sw && sw[0] == '1') {
+    // Profiling aid: the same setup and rounds launched one by one from the
+    // host (profilers do not see the kernels of a conditional graph node);
+    // the active count is read after every round.
+    Round Rs = B->R;
+    Rs.ctl.use_cond = 0;
+    SKS_TRY(enqueue_setup(B, Rs.ctl, stream));
+    for (long long r = 0; r < Rs.ctl.max_rounds; ++r) {
+      enqueue_round(Rs, stream);
+      SKS_CUDA_TRY(cudaGetLastError());
+      int act = 0;
+      SKS_CUDA_TRY(cudaMemcpyAsync(&act, L.active, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      SKS_CUDA_TRY(cudaStreamSynchronize(stream));
+      if (act == 0) break;
+    }
+  } else {
+    SKS_CUDA_TRY(cudaGraphLaunch(B->e, stream));
+  }
+  note_launch(3 + 3 * P + (B->R.mixed ? 1 : 0));  // setup kernels (counted per round below)
   SKS_CUDA_TRY(cudaEventRecord(ev_solve.b, stream));
 
   // ---- per-problem results (the one synchronisation of the solve)

@@ -54,7 +54,8 @@ namespace {
 
 enum : int { PH_INIT = 0, PH_GROW = 1, PH_ITER = 2, PH_RESTART = 3, PH_DONE = 4, PH_FAIL = 5 };
 // d-vector slots of a problem (V_XI: the inner iterate dx of the mixed form)
-enum : int { V_R = 0, V_RT, V_P, V_HV, V_XP, V_RP, V_RTP, V_U, V_W, V_DINV, V_XI, kNumVec };
+// V_ISC: 1 / (nu^2 lambda) (mixed form)
+enum : int { V_R = 0, V_RT, V_P, V_HV, V_XP, V_RP, V_RTP, V_U, V_W, V_DINV, V_XI, V_ISC, kNumVec };
 
 // phase timers: A-pass, sketched-Hessian matrix (Gram), its factorisation,
 // preconditioner apply, the whole round (first kernel to the count kernel)
@@ -79,7 +80,12 @@ struct BDesc {
   const float* Af;   // mixed form: the float32 A (A is NULL)
   float* Bf;         // mixed form: float32 H E A_pad, n_pad x d, ld d (B is NULL)
   float* ilam;       // mixed form: 1 / lambda rounded to float32 (Woodbury Gram)
-  double* Li;        // mixed form: inverses of the factor's 64 x 64 diagonal blocks (block b at b * 4096)
+  // mixed form: the factor L' = 2^(-sexp) L as float pairs (lower part, its
+  // transpose mirrored in the upper part; d x d, ld d) and the inverses of
+  // its 64 x 64 diagonal blocks (block b at b * 4096, row-major, zero above
+  // the diagonal)
+  float2* Lf;
+  float2* Lif;
   uint32_t* perm;    // sketch row r is B[perm[r]]
   double* M;         // d x d, ld d: lower = factor L, strict upper = L^T
   double* vec;       // kNumVec d-vectors
@@ -692,22 +698,27 @@ SKS_DEV double from_f2(F2 v, int sh) { return scale_pow2(f32_to_f64_bits(v.h) + 
 
 // Panel k, diagonal block, mixed form: L_kk = chol(M_kk) and X = L_kk^{-1},
 // both right-looking, in registers: thread (c, g) holds column c, rows
-// g + 4q (q < 16) of the block and of X.  Step j: the pivot's owner
+// g + 16q (q < 4) of the block and of X (1024 threads: enough warps to hide
+// the latency of the double-float chains between the step's barriers).  Step j: the pivot's owner
 // publishes it; the four owners of column j scale it and publish it; every
 // thread updates its trailing entries with column j, the owners of row j of
 // X scale that row and publish it, and every thread updates its rows of X
 // below j.  Writes L_kk (lower), L_kk^T (strict upper) and X (Li block k).
 // At k = 0 the CTA first picks the problem's scaling exponent.
-__global__ void __launch_bounds__(256) b_potrf_df_kernel(BCtl c, const BDesc* __restrict__ D, BState* S, int k) {
+constexpr int kPotThreads = 1024;                    // 16 threads per column of the block
+constexpr int kPotRows = kTile / (kPotThreads / kTile);  // rows per thread (4)
+
+__global__ void __launch_bounds__(kPotThreads) b_potrf_df_kernel(BCtl c, const BDesc* __restrict__ D, BState* S,
+                                                                 int k) {
   __shared__ F2 colv[kTile], xrow[kTile];
   __shared__ F2 s_piv, s_r;
   __shared__ int s_bad, s_emax;
+  constexpr int NGR = kPotThreads / kTile;  // row groups
   tk_start(c, TK_FACTOR);
   const int tid = threadIdx.x, cc = tid & 63, g = tid >> 6;
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
-    if (s.phase != PH_GROW) continue;
     const BDesc& q = D[p];
     const int N = factor_size(s, q);
     const int k0 = k * kTile;
@@ -732,20 +743,20 @@ __global__ void __launch_bounds__(256) b_potrf_df_kernel(BCtl c, const BDesc* __
     } else {
       te = s.sexp;
     }
-    F2 v[16], xi[16];
+    F2 v[kPotRows], xi[kPotRows];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int i = g + 4 * r;
+    for (int r = 0; r < kPotRows; ++r) {
+      const int i = g + NGR * r;
       v[r] = (i < nb && cc <= i) ? to_f2(q.M[(int64_t)(k0 + i) * d + k0 + cc], -2 * te) : F2{0.f, 0.f};
       xi[r] = (i < nb && cc == i) ? F2{1.f, 0.f} : F2{0.f, 0.f};
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-      const int jr = j >> 2, jg = j & 3;
+      const int jr = j / NGR, jg = j % NGR;
       if (cc == j && g == jg) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r)
+        for (int r = 0; r < kPotRows; ++r)
           if (r == jr) s_piv = v[r];
       }
       __syncthreads();
@@ -756,8 +767,8 @@ __global__ void __launch_bounds__(256) b_potrf_df_kernel(BCtl c, const BDesc* __
         } else {
           const F2 r = f2_rsqrt(pv);  // 1 / L_jj
 #pragma unroll
-          for (int rr = 0; rr < 16; ++rr) {
-            const int i = g + 4 * rr;
+          for (int rr = 0; rr < kPotRows; ++rr) {
+            const int i = g + NGR * rr;
             if (i > j && i < nb) {
               v[rr] = f2_mul(v[rr], r);
               colv[i] = v[rr];
@@ -773,15 +784,15 @@ __global__ void __launch_bounds__(256) b_potrf_df_kernel(BCtl c, const BDesc* __
       if (cc > j) {
         const F2 lc = colv[cc];
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr) {
-          const int i = g + 4 * rr;
+        for (int rr = 0; rr < kPotRows; ++rr) {
+          const int i = g + NGR * rr;
           if (i >= cc && i < nb) f2_acc<true>(v[rr].h, v[rr].l, colv[i], lc);
         }
       }
       if (g == jg && cc <= j) {
         const F2 r = s_r;
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr)
+        for (int rr = 0; rr < kPotRows; ++rr)
           if (rr == jr) {
             xi[rr] = f2_mul(xi[rr], r);
             xrow[cc] = xi[rr];
@@ -791,8 +802,8 @@ __global__ void __launch_bounds__(256) b_potrf_df_kernel(BCtl c, const BDesc* __
       if (cc <= j) {
         const F2 xj = xrow[cc];
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr) {
-          const int i = g + 4 * rr;
+        for (int rr = 0; rr < kPotRows; ++rr) {
+          const int i = g + NGR * rr;
           if (i > j && i < nb) f2_acc<true>(xi[rr].h, xi[rr].l, colv[i], xj);
         }
       }
@@ -805,16 +816,16 @@ __global__ void __launch_bounds__(256) b_potrf_df_kernel(BCtl c, const BDesc* __
       __syncthreads();
       continue;
     }
-    double* Lib = q.Li + (size_t)k * (kTile * kTile);
+    float2* Lib = q.Lif + (size_t)k * (kTile * kTile);
 #pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-      const int i = g + 4 * rr;
+    for (int rr = 0; rr < kPotRows; ++rr) {
+      const int i = g + NGR * rr;
       if (i < nb && cc <= i) {
-        const double val = from_f2(v[rr], te);
-        q.M[(int64_t)(k0 + i) * d + k0 + cc] = val;
-        if (cc < i) q.M[(int64_t)(k0 + cc) * d + k0 + i] = val;
+        const float2 val = make_float2(v[rr].h, v[rr].l);
+        q.Lf[(int64_t)(k0 + i) * d + k0 + cc] = val;
+        if (cc < i) q.Lf[(int64_t)(k0 + cc) * d + k0 + i] = val;
       }
-      Lib[i * kTile + cc] = (i < nb && cc <= i) ? from_f2(xi[rr], -te) : 0.0;
+      Lib[i * kTile + cc] = (i < nb && cc <= i) ? make_float2(xi[rr].h, xi[rr].l) : make_float2(0.f, 0.f);
     }
     __syncthreads();
   }
@@ -837,10 +848,18 @@ SKS_DEV void df_tile_chunk(const float (*Ah)[kTPf], const float (*Al)[kTPf], con
   }
 }
 
+// one operand element: float64 scaled by 2^sh and split, or a float pair as is
+SKS_DEV F2 ld_f2(const double* p, int64_t i, int sh) { return to_f2(p[i], sh); }
+SKS_DEV F2 ld_f2(const float2* p, int64_t i, int) {
+  const float2 v = p[i];
+  return F2{v.x, v.y};
+}
+
 // acc = A B^T for a 64 x 64 output tile: A rows ra (< na valid), B rows rb
-// (< nbv valid), K columns (both row-major, float64, scaled by 2^sha / 2^shb
-// on the way in).
-SKS_DEV void df_tile_abt(const double* __restrict__ A, int64_t lda, int na, int sha, const double* __restrict__ B,
+// (< nbv valid), K columns (both row-major; float64 operands scaled by
+// 2^sha / 2^shb on the way in, float-pair operands taken as they are).
+template <typename TA, typename TB>
+SKS_DEV void df_tile_abt(const TA* __restrict__ A, int64_t lda, int na, int sha, const TB* __restrict__ B,
                          int64_t ldb, int nbv, int shb, int K, F2 (&acc)[4][4], float (*Ah)[kTPf],
                          float (*Al)[kTPf], float (*Bh)[kTPf], float (*Bl)[kTPf]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -854,8 +873,8 @@ SKS_DEV void df_tile_abt(const double* __restrict__ A, int64_t lda, int na, int 
       const int col = c0 + kk;
       F2 a = {0.f, 0.f}, b = {0.f, 0.f};
       if (col < K) {
-        if (ii < na) a = to_f2(A[(int64_t)ii * lda + col], sha);
-        if (ii < nbv) b = to_f2(B[(int64_t)ii * ldb + col], shb);
+        if (ii < na) a = ld_f2(A, (int64_t)ii * lda + col, sha);
+        if (ii < nbv) b = ld_f2(B, (int64_t)ii * ldb + col, shb);
       }
       Ah[kk][ii] = a.h;
       Al[kk][ii] = a.l;
@@ -889,18 +908,18 @@ __global__ void __launch_bounds__(256) b_trsm_df_kernel(BCtl c, const BDesc* __r
     const int nb = min(kTile, N - k0), rb = min(kTile, N - i0);
     const int d = q.d, te = s.sexp;
     F2 acc[4][4];
-    // M'_ik (2^-2te M) times X' (2^te X): 2^-te L_ik
-    df_tile_abt(q.M + (int64_t)i0 * d + k0, d, rb, -2 * te, q.Li + (size_t)k * (kTile * kTile), kTile, nb, te, nb,
-                acc, Ah, Al, Bh, Bl);
+    // M'_ik (2^-2te M) times (L'_kk)^{-T}: L'_ik = 2^-te L_ik
+    df_tile_abt(q.M + (int64_t)i0 * d + k0, d, rb, -2 * te, q.Lif + (size_t)k * (kTile * kTile), kTile, nb, 0,
+                nb, acc, Ah, Al, Bh, Bl);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int r = ty * 4 + a, cl = tx * 4 + b;
         if (r < rb && cl < nb) {
-          const double val = from_f2(acc[a][b], te);
-          q.M[(int64_t)(i0 + r) * d + k0 + cl] = val;
-          q.M[(int64_t)(k0 + cl) * d + i0 + r] = val;
+          const float2 val = make_float2(acc[a][b].h, acc[a][b].l);
+          q.Lf[(int64_t)(i0 + r) * d + k0 + cl] = val;
+          q.Lf[(int64_t)(k0 + cl) * d + i0 + r] = val;
         }
       }
   }
@@ -928,8 +947,9 @@ __global__ void __launch_bounds__(256) b_update_df_kernel(BCtl c, const BDesc* _
     const int nb = min(kTile, N - k0);
     const int d = q.d, te = s.sexp;
     F2 acc[4][4];
-    df_tile_abt(q.M + (int64_t)i0 * d + k0, d, min(kTile, N - i0), -te, q.M + (int64_t)j0 * d + k0, d,
-                min(kTile, N - j0), -te, nb, acc, Ah, Al, Bh, Bl);
+    // L'_ik L'_jk^T = 2^-2te L_ik L_jk^T
+    df_tile_abt(q.Lf + (int64_t)i0 * d + k0, d, min(kTile, N - i0), 0, q.Lf + (int64_t)j0 * d + k0, d,
+                min(kTile, N - j0), 0, nb, acc, Ah, Al, Bh, Bl);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1035,30 +1055,47 @@ SKS_DEV void df_add2(float& h, float& l, float bh, float bl) {
 
 // Inner iterations: rows [r0, r1) of the float32 A against p rounded to
 // float32 (vs), float32 sums; the unit's d partial sums leave as float64.
-template <int QC>
+// A warp takes RR rows at a time (their loads in flight together, their dot
+// reductions interleaved): narrow rows need several to keep HBM busy.
+template <int QC, int RR>
 SKS_DEV void apass_unit_f32(const float* __restrict__ A, long long lda, int d, int64_t r0, int64_t r1,
                             const float* vs, float* red, double* __restrict__ out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float acc[QC];
+  float xv[QC];
 #pragma unroll
-  for (int j = 0; j < QC; ++j) acc[j] = 0.f;
-  for (int64_t r = r0 + warp; r < r1; r += kApWarps) {
-    const float* a = A + r * lda;
-    float av[QC];
-    float dot = 0.f;
+  for (int j = 0; j < QC; ++j) {
+    acc[j] = 0.f;
+    const int col = lane + 32 * j;
+    xv[j] = col < d ? vs[col] : 0.f;
+  }
+  for (int64_t r = r0 + warp; r < r1; r += (int64_t)kApWarps * RR) {
+    float av[RR][QC];
+    float dot[RR];
 #pragma unroll
-    for (int j = 0; j < QC; ++j) {
-      const int col = lane + 32 * j;
-      av[j] = col < d ? __ldg(a + col) : 0.f;
+    for (int k = 0; k < RR; ++k) {
+      const int64_t rk = r + (int64_t)k * kApWarps;
+      const float* a = A + rk * lda;
+#pragma unroll
+      for (int j = 0; j < QC; ++j) {
+        const int col = lane + 32 * j;
+        av[k][j] = (rk < r1 && col < d) ? __ldg(a + col) : 0.f;
+      }
     }
 #pragma unroll
-    for (int j = 0; j < QC; ++j) {
-      const int col = lane + 32 * j;
-      if (col < d) dot = fmaf(av[j], vs[col], dot);
-    }
-    dot = warp_sum(dot);
+    for (int k = 0; k < RR; ++k) {
+      dot[k] = 0.f;
 #pragma unroll
-    for (int j = 0; j < QC; ++j) acc[j] = fmaf(dot, av[j], acc[j]);
+      for (int j = 0; j < QC; ++j) dot[k] = fmaf(av[k][j], xv[j], dot[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < RR; ++k) dot[k] += __shfl_xor_sync(0xffffffffu, dot[k], o);
+#pragma unroll
+    for (int k = 0; k < RR; ++k)
+#pragma unroll
+      for (int j = 0; j < QC; ++j) acc[j] = fmaf(dot[k], av[k][j], acc[j]);
   }
 #pragma unroll
   for (int j = 0; j < QC; ++j) {
@@ -1184,12 +1221,12 @@ __global__ void __launch_bounds__(kApThreads) b_apass_mixed_kernel(BCtl c, const
       else if (d <= 512) apass_unit_df<16>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
       else apass_unit_df<32>(q.Af, q.lda, d, r0, r1, vh, vl, redh, redl, out);
     } else {
-      if (d <= 32) apass_unit_f32<1>(q.Af, q.lda, d, r0, r1, vh, redh, out);
-      else if (d <= 64) apass_unit_f32<2>(q.Af, q.lda, d, r0, r1, vh, redh, out);
-      else if (d <= 128) apass_unit_f32<4>(q.Af, q.lda, d, r0, r1, vh, redh, out);
-      else if (d <= 256) apass_unit_f32<8>(q.Af, q.lda, d, r0, r1, vh, redh, out);
-      else if (d <= 512) apass_unit_f32<16>(q.Af, q.lda, d, r0, r1, vh, redh, out);
-      else apass_unit_f32<32>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      if (d <= 32) apass_unit_f32<1, 8>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 64) apass_unit_f32<2, 8>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 128) apass_unit_f32<4, 4>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 256) apass_unit_f32<8, 2>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else if (d <= 512) apass_unit_f32<16, 2>(q.Af, q.lda, d, r0, r1, vh, redh, out);
+      else apass_unit_f32<32, 1>(q.Af, q.lda, d, r0, r1, vh, redh, out);
     }
     flops += 4.0 * (double)(r1 - r0) * d;
   }
@@ -1313,48 +1350,6 @@ SKS_DEV void tri_solve(const double* __restrict__ M, int ld, int N, const double
   }
 }
 
-// The same solves with the inverses of the diagonal blocks (Li, mixed form):
-// per block the off-diagonal part as above, then y_b = X_bb y_b (lower) or
-// X_bb^T y_b (upper) as a product -- no substitution chain.  tmp: 64 doubles
-// of shared memory.
-SKS_DEV void tri_solve_inv(const double* __restrict__ M, int ld, int N, const double* __restrict__ Li, double* y,
-                           bool upper, double* tmp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nblk = (N + kTile - 1) / kTile;
-  for (int bi = 0; bi < nblk; ++bi) {
-    const int blk = upper ? nblk - 1 - bi : bi;
-    const int b0 = blk * kTile, nb = min(kTile, N - b0);
-    const int j0 = upper ? b0 + nb : 0, j1 = upper ? N : b0;
-    if (j1 > j0) {
-      for (int i = warp; i < nb; i += nw) {
-        const double* row = M + (int64_t)(b0 + i) * ld;
-        double s = 0.0;
-        for (int j = j0 + lane; j < j1; j += 32) s = fma(row[j], y[j], s);
-        s = warp_sum(s);
-        if (lane == 0) y[b0 + i] -= s;
-      }
-    }
-    __syncthreads();
-    const double* X = Li + (size_t)blk * (kTile * kTile);
-    if (!upper) {
-      for (int i = warp; i < nb; i += nw) {
-        double s = 0.0;
-        for (int l = lane; l <= i; l += 32) s = fma(X[i * kTile + l], y[b0 + l], s);
-        s = warp_sum(s);
-        if (lane == 0) tmp[i] = s;
-      }
-    } else if (threadIdx.x < nb) {
-      const int i = threadIdx.x;
-      double s = 0.0;
-      for (int l = i; l < nb; ++l) s = fma(X[l * kTile + i], y[b0 + l], s);
-      tmp[i] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < nb) y[b0 + threadIdx.x] = tmp[threadIdx.x];
-    __syncthreads();
-  }
-}
-
 // GROW: r~ = H_S^{-1} r.   ITER: r~+ = H_S^{-1} r+.
 //   form 0: H_S = L L^T (two triangular solves)
 //   form 1: H_S^{-1} z = u - (nu^2 Lambda)^{-1} Y_s^T K^{-1} Y_s u,  u = (nu^2 Lambda)^{-1} z,
@@ -1362,7 +1357,6 @@ SKS_DEV void tri_solve_inv(const double* __restrict__ M, int ld, int N, const do
 __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S) {
   tk_start(c, TK_APPLY);
   __shared__ double y[kMaxD];
-  __shared__ double tmp[kTile];
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     const BState s = S[p];
     if (s.phase != PH_GROW && s.phase != PH_ITER && s.phase != PH_RESTART) continue;
@@ -1375,13 +1369,8 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
     if (s.form == 0) {
       for (int j = threadIdx.x; j < d; j += blockDim.x) y[j] = z[j];
       __syncthreads();
-      if (q.Li) {
-        tri_solve_inv(q.M, d, d, q.Li, y, false, tmp);
-        tri_solve_inv(q.M, d, d, q.Li, y, true, tmp);
-      } else {
-        tri_solve(q.M, d, d, dinv, y, false);
-        tri_solve(q.M, d, d, dinv, y, true);
-      }
+      tri_solve(q.M, d, d, dinv, y, false);
+      tri_solve(q.M, d, d, dinv, y, true);
       for (int j = threadIdx.x; j < d; j += blockDim.x) out[j] = y[j];
     } else {
       const int m = (int)s.m;
@@ -1402,13 +1391,8 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
         if (lane == 0) y[r] = t * ism;
       }
       __syncthreads();
-      if (q.Li) {
-        tri_solve_inv(q.M, d, m, q.Li, y, false, tmp);
-        tri_solve_inv(q.M, d, m, q.Li, y, true, tmp);
-      } else {
-        tri_solve(q.M, d, m, dinv, y, false);
-        tri_solve(q.M, d, m, dinv, y, true);
-      }
+      tri_solve(q.M, d, m, dinv, y, false);
+      tri_solve(q.M, d, m, dinv, y, true);
       for (int j = threadIdx.x; j < d; j += blockDim.x) {
         double t = 0.0;
         if (q.Bf) {
@@ -1417,6 +1401,157 @@ __global__ void __launch_bounds__(512) b_apply_kernel(BCtl c, const BDesc* __res
           for (int r = 0; r < m; ++r) t = fma(q.B[(int64_t)q.perm[r] * d + j], y[r], t);
         }
         out[j] = u[j] - t * ism / (q.nu2 * q.lam[j]);
+      }
+    }
+    __syncthreads();
+  }
+  tk_stop(c, TK_APPLY);
+}
+
+// ---- mixed form: the preconditioner apply in double-float
+SKS_DEV F2 f2_add(F2 a, F2 b) {
+  const F2 s = f2_two_sum(a.h, b.h);
+  return f2_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+SKS_DEV F2 warp_sum_f2(F2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = f2_add(v, F2{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+  return v;
+}
+// largest binary exponent of |v[0..n)| over the block (0 if every entry is 0)
+SKS_DEV int block_max_exp(const double* v, int n, int* s_e) {
+  if (threadIdx.x == 0) *s_e = -2000;
+  __syncthreads();
+  int e = -2000;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int E = (int)((__double_as_longlong(v[j]) >> 52) & 0x7ff);
+    if (E > 0 && E < 0x7ff) e = max(e, E - 1023);
+  }
+  atomicMax(s_e, e);
+  __syncthreads();
+  const int r = *s_e;
+  __syncthreads();
+  return r > -2000 ? r : 0;
+}
+
+// yd[0..N) <- (L L^T)^{-1} yd with the float-pair factor L' = 2^-te L of the
+// problem (Lf, Lif): the vector scaled by a power of two into range, blocked
+// forward and backward solves (off-diagonal part one warp per row, the
+// diagonal block as a product with its inverse), scaled back.
+SKS_DEV void df_chol_solve(const BDesc& q, int N, int te, double* yd, F2* yf, F2* tmpf, int* s_e) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int d = q.d;
+  const int ez = block_max_exp(yd, N, s_e);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) yf[j] = to_f2(yd[j], -ez);
+  __syncthreads();
+  const int nblk = (N + kTile - 1) / kTile;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool upper = pass == 1;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int blk = upper ? nblk - 1 - bi : bi;
+      const int b0 = blk * kTile, nb = min(kTile, N - b0);
+      const int j0 = upper ? b0 + nb : 0, j1 = upper ? N : b0;
+      if (j1 > j0) {
+        for (int i = warp; i < nb; i += nw) {
+          const float2* row = q.Lf + (int64_t)(b0 + i) * d;
+          F2 acc = {0.f, 0.f}, acc2 = {0.f, 0.f};
+          int j = j0 + lane;
+          for (; j + 96 < j1; j += 128) {  // four loads in flight per lane
+            const float2 a0 = row[j], a1 = row[j + 32], a2 = row[j + 64], a3 = row[j + 96];
+            f2_acc<false>(acc.h, acc.l, F2{a0.x, a0.y}, yf[j]);
+            f2_acc<false>(acc2.h, acc2.l, F2{a1.x, a1.y}, yf[j + 32]);
+            f2_acc<false>(acc.h, acc.l, F2{a2.x, a2.y}, yf[j + 64]);
+            f2_acc<false>(acc2.h, acc2.l, F2{a3.x, a3.y}, yf[j + 96]);
+          }
+          for (; j < j1; j += 32) {
+            const float2 a = row[j];
+            f2_acc<false>(acc.h, acc.l, F2{a.x, a.y}, yf[j]);
+          }
+          acc = warp_sum_f2(f2_add(acc, acc2));
+          if (lane == 0) yf[b0 + i] = f2_add(yf[b0 + i], F2{-acc.h, -acc.l});
+        }
+      }
+      __syncthreads();
+      const float2* X = q.Lif + (size_t)blk * (kTile * kTile);
+      for (int i = warp; i < nb; i += nw) {
+        F2 acc = {0.f, 0.f};
+        if (!upper) {
+          for (int l = lane; l <= i; l += 32) {
+            const float2 a = X[i * kTile + l];
+            f2_acc<false>(acc.h, acc.l, F2{a.x, a.y}, yf[b0 + l]);
+          }
+        } else {
+          for (int l = i + lane; l < nb; l += 32) {
+            const float2 a = X[l * kTile + i];
+            f2_acc<false>(acc.h, acc.l, F2{a.x, a.y}, yf[b0 + l]);
+          }
+        }
+        acc = warp_sum_f2(acc);
+        if (lane == 0) tmpf[i] = acc;
+      }
+      __syncthreads();
+      if (threadIdx.x < nb) yf[b0 + threadIdx.x] = tmpf[threadIdx.x];
+      __syncthreads();
+    }
+  }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) yd[j] = from_f2(yf[j], ez - 2 * te);
+  __syncthreads();
+}
+
+// GROW / RESTART: r~ = H_S^{-1} r.   ITER: r~+ = H_S^{-1} r+   (mixed form,
+// double-float on the float32 pipe; the same forms as b_apply_kernel).
+__global__ void __launch_bounds__(512) b_apply_mixed_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S) {
+  __shared__ double yd[kMaxD];
+  __shared__ F2 yf[kMaxD];
+  __shared__ F2 tmpf[kTile];
+  __shared__ int s_e;
+  tk_start(c, TK_APPLY);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
+    const int ph = S[p].phase;
+    if (ph != PH_GROW && ph != PH_ITER && ph != PH_RESTART) continue;
+    const BState s = S[p];
+    const BDesc& q = D[p];
+    const int d = q.d;
+    const bool restart = s.phase != PH_ITER;
+    const double* z = q.vec + (size_t)(restart ? V_R : V_RP) * d;
+    double* out = q.vec + (size_t)(restart ? V_RT : V_RTP) * d;
+    if (s.form == 0) {
+      for (int j = threadIdx.x; j < d; j += blockDim.x) yd[j] = z[j];
+      __syncthreads();
+      df_chol_solve(q, d, s.sexp, yd, yf, tmpf, &s_e);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) out[j] = yd[j];
+    } else {
+      // u = (nu^2 Lambda)^{-1} z;  t = Y_s u;  w = K^{-1} t;  out = u - (nu^2 Lambda)^{-1} Y_s^T w
+      const int m = (int)s.m;
+      const double ism = 1.0 / sqrt((double)m);
+      const double* isc = q.vec + (size_t)V_ISC * d;
+      double* u = q.vec + (size_t)V_U * d;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double v = z[j] * isc[j];
+        u[j] = v;
+        yd[j] = v;
+      }
+      __syncthreads();
+      const int eu = block_max_exp(yd, d, &s_e);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) yf[j] = to_f2(yd[j], -eu);
+      __syncthreads();
+      for (int r = warp; r < m; r += nw) {
+        const float* row = q.Bf + (int64_t)q.perm[r] * d;
+        F2 acc = {0.f, 0.f};
+        for (int j = lane; j < d; j += 32) f2_acc<false>(acc.h, acc.l, F2{row[j], 0.f}, yf[j]);
+        acc = warp_sum_f2(acc);
+        if (lane == 0) yd[r] = from_f2(acc, eu) * ism;
+      }
+      __syncthreads();
+      df_chol_solve(q, m, s.sexp, yd, yf, tmpf, &s_e);
+      const int ew = block_max_exp(yd, m, &s_e);
+      for (int r = threadIdx.x; r < m; r += blockDim.x) yf[r] = to_f2(yd[r], -ew);
+      __syncthreads();
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        F2 acc = {0.f, 0.f};
+        for (int r = 0; r < m; ++r) f2_acc<false>(acc.h, acc.l, F2{q.Bf[(int64_t)q.perm[r] * d + j], 0.f}, yf[r]);
+        out[j] = u[j] - from_f2(acc, ew) * ism * isc[j];
       }
     }
     __syncthreads();
@@ -1611,7 +1746,10 @@ __global__ void b_check_kernel(const BDesc* __restrict__ D, int P, DevStatus* st
 __global__ void b_prep_mixed_kernel(const BDesc* __restrict__ D, int P) {
   for (int p = blockIdx.x; p < P; p += gridDim.x) {
     const BDesc& q = D[p];
-    for (int j = threadIdx.x; j < q.d; j += blockDim.x) q.ilam[j] = (float)(1.0 / q.lam[j]);
+    for (int j = threadIdx.x; j < q.d; j += blockDim.x) {
+      q.ilam[j] = (float)(1.0 / q.lam[j]);
+      q.vec[(size_t)V_ISC * q.d + j] = 1.0 / (q.nu2 * q.lam[j]);
+    }
   }
 }
 
@@ -1724,9 +1862,11 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
       q.B = nullptr;
       q.Bf = c.take<float>((size_t)n_pad * q.d);
       q.ilam = c.take<float>((size_t)q.d);
-      q.Li = c.take<double>((size_t)((q.d + kTile - 1) / kTile) * kTile * kTile);
+      q.Lf = c.take<float2>((size_t)q.d * q.d);
+      q.Lif = c.take<float2>((size_t)((q.d + kTile - 1) / kTile) * kTile * kTile);
     } else {
-      q.Li = nullptr;
+      q.Lf = nullptr;
+      q.Lif = nullptr;
       q.B = c.take<double>((size_t)n_pad * q.d);
       q.Bf = nullptr;
       q.ilam = nullptr;
@@ -1785,7 +1925,7 @@ int enqueue_round(const Round& R, cudaStream_t stream) {
   b_gram_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_tri);
   n += 2;
   for (int k = 0; k < R.kmax; ++k) {
-    if (R.mixed) b_potrf_df_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S, k);
+    if (R.mixed) b_potrf_df_kernel<<<R.g_prob, kPotThreads, 0, stream>>>(R.ctl, R.D, R.S, k);
     else b_potrf_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S, k);
     ++n;
     if (k + 1 < R.kmax) {
@@ -1809,7 +1949,8 @@ int enqueue_round(const Round& R, cudaStream_t stream) {
   }
   b_reduce_kernel<<<R.g_tile, 256, 0, stream>>>(R.ctl, R.D, R.S, R.tot_red);
   b_step1_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
-  b_apply_kernel<<<R.g_prob, 512, 0, stream>>>(R.ctl, R.D, R.S);
+  if (R.mixed) b_apply_mixed_kernel<<<R.g_prob, 512, 0, stream>>>(R.ctl, R.D, R.S);
+  else b_apply_kernel<<<R.g_prob, 512, 0, stream>>>(R.ctl, R.D, R.S);
   b_step2_kernel<<<R.g_prob, 256, 0, stream>>>(R.ctl, R.D, R.S);
   b_count_kernel<<<1, 256, 0, stream>>>(R.ctl, R.S);
   n += 6;

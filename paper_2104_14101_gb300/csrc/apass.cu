@@ -219,7 +219,19 @@ sks_status apass_launch(const ApassPlan& pl, const CUtensorMap* tmap, int64_t n,
     return launch_t<float, float, 256, 4, 1>(SKS_APASS_ARGS);
   }
   // float32 A, float64 vectors: double-float arithmetic (~2^-44 relative)
-  if (k == 8) return launch_t<float, df32, 256, 1, 8>(SKS_APASS_ARGS);
+  if (k == 8) {
+    // two passes of four columns each: the eight double-float accumulators and
+    // vectors of one pass do not fit a thread's registers (spills); the second
+    // read of A costs less than the spills
+    const size_t h = (size_t)4 * d;
+    const double* xd = (const double*)x;
+    const double* ad = (const double*)addv;
+    double* yd = (double*)y;
+    SKS_TRY((launch_t<float, df32, 256, 1, 4>(pl, tmap, n, d, xd, yd, nu2, lambda, partials, st, stream, sgn, ad,
+                                               addc, ev_begin, nullptr)));
+    return launch_t<float, df32, 256, 1, 4>(pl, tmap, n, d, xd + h, yd + h, nu2, lambda, partials, st, stream, sgn,
+                                            ad ? ad + h : nullptr, addc, nullptr, ev_end);
+  }
   if (pl.group == 32) return launch_t<float, df32, 32, 4, 1>(SKS_APASS_ARGS);
   if (pl.group == 128) return launch_t<float, df32, 128, 4, 1>(SKS_APASS_ARGS);
   return launch_t<float, df32, 256, 4, 1>(SKS_APASS_ARGS);

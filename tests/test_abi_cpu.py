@@ -75,7 +75,8 @@ def test_opts_default_and_validation_without_gpu(lib_path):
 
 def test_batched_validation_without_gpu(lib_path):
     # The batched entry point rejects what it does not implement before any
-    # device work: no problems, float32 A, another embedding, d > 1024.
+    # device work: no problems, float32 A in the plain form (float64 A in the
+    # mixed form), another embedding, d > 1024.
     from paper_2104_14101_gb300 import _lib
     lib = _lib.load(lib_path)
     o = _lib.Opts()
@@ -101,6 +102,17 @@ def test_batched_validation_without_gpu(lib_path):
     o.kind = _lib.KINDS["srht"]
     arr[1].k = 2
     assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_UNSUPPORTED
+    arr[1].k = 1
+    # the mixed form: float32 A only; its layout holds the float32 H E A_pad,
+    # the factor as float pairs and the block inverses instead of float64 copies
+    o.precision = _lib.MIXED_REFINED
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_INVALID_ARG
+    assert b"mixed form needs float32 A" in lib.sks_last_error()
+    arr[0].dtype = arr[1].dtype = _lib.F32
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.OK
+    assert nb.value > 2 * (64 * 8 * 4 + 8 * 8 * 8 + 64 * 64 * 8)
+    o.max_outer = 0
+    assert lib.sks_batch_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(nb)) == _lib.ERR_INVALID_ARG
 
 
 def test_new_entry_points_validation_without_gpu(lib_path):

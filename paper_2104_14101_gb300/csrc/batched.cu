@@ -127,6 +127,10 @@ struct BCtl {
   const int* pre_ap;   // prefix of ceil(n / rows_per_unit)
   const int* pre_red;  // prefix of ceil(d / 256)
   int* active;         // problems not finished after the round
+  // 64-column panels of the largest matrix factored this round (0: no problem
+  // grows); set by b_begin_kernel, cleared by the count kernel.  Gram and
+  // factorisation launches beyond it return at once instead of walking units.
+  int* round_kmax;
   // Phase timers, kTimers x 3: [0] earliest CTA start and [1] latest CTA end
   // of the phase's kernels in this round (%globaltimer ns), [2] the windows
   // summed over rounds (TK_* order; null in the autotuner's launches).
@@ -193,10 +197,12 @@ __global__ void b_begin_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
   s.k_begin = s.form == 0 ? s.gram_rows : 0;
   if (s.form == 0) s.gram_rows = s.m;
   s.factorizations += 1;
+  atomicMax(c.round_kmax, ((s.form == 0 ? q.d : (int)s.m) + kTile - 1) / kTile);
 }
 
 // perm[r] = pi(r) for the new sketch rows r in [m_old, m)
 __global__ void b_perm_kernel(BCtl c, const BDesc* __restrict__ D, BState* S) {
+  if (*c.round_kmax == 0) return;  // no problem grows this round
   for (int p = blockIdx.x; p < c.P; p += gridDim.x) {
     if (S[p].phase != PH_GROW) continue;
     const BState s = S[p];
@@ -284,6 +290,7 @@ SKS_DEV void gram_epilogue(const BDesc& q, const BState& s, int nks, int ks, int
 // raw slice sum goes to the problem's partial tiles.
 __global__ void __launch_bounds__(256) b_gram_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
                                                      int total) {
+  if (*c.round_kmax == 0) return;  // no problem grows this round
   __shared__ __align__(16) double As[16][kTP];
   __shared__ __align__(16) double Bs[16][kTP];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -381,6 +388,7 @@ constexpr int kTPf = kTile + 4;  // float shared-memory row (16-byte aligned qua
 // on this part).
 __global__ void __launch_bounds__(256) b_gram_mixed_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
                                                            int total) {
+  if (*c.round_kmax == 0) return;  // no problem grows this round
   __shared__ __align__(16) float As[16][kTPf];
   __shared__ __align__(16) float Bs[16][kTPf];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -475,6 +483,7 @@ __global__ void __launch_bounds__(256) b_gram_mixed_kernel(BCtl c, const BDesc* 
 // Sum of the slice partials (slice order fixed), scale and diagonal, into M.
 __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S,
                                                             int total) {
+  if (*c.round_kmax == 0) return;  // no problem grows this round
   tk_start(c, TK_GRAM);
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = find_problem(c.pre_tri, c.P, u);
@@ -513,6 +522,7 @@ __global__ void __launch_bounds__(256) b_gram_reduce_kernel(BCtl c, const BDesc*
 // Panel k, diagonal block: L_kk = chol(M_kk) in shared memory; writes L_kk
 // (lower), L_kk^T (strict upper) and 1 / diag(L_kk).
 __global__ void __launch_bounds__(256) b_potrf_kernel(BCtl c, const BDesc* __restrict__ D, BState* S, int k) {
+  if (k >= *c.round_kmax) return;  // no matrix of this round has panel k
   tk_start(c, TK_FACTOR);
   __shared__ double L[kTile][kTile + 1];
   __shared__ int bad;
@@ -582,6 +592,7 @@ __global__ void __launch_bounds__(256) b_potrf_kernel(BCtl c, const BDesc* __res
 // upper part.
 __global__ void __launch_bounds__(64) b_trsm_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
                                                     int total) {
+  if (k >= *c.round_kmax) return;  // no matrix of this round has panel k
   tk_start(c, TK_FACTOR);
   extern __shared__ double tr_smem[];
   double (*L)[kTile + 1] = (double (*)[kTile + 1])tr_smem;                    // [64][65]
@@ -631,6 +642,7 @@ __global__ void __launch_bounds__(64) b_trsm_kernel(BCtl c, const BDesc* __restr
 // M_ij -= L_ik L_jk^T.
 __global__ void __launch_bounds__(256) b_update_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
                                                        int total) {
+  if (k >= *c.round_kmax) return;  // no matrix of this round has panel k
   tk_start(c, TK_FACTOR);
   __shared__ __align__(16) double As[16][kTP];
   __shared__ __align__(16) double Bs[16][kTP];
@@ -710,6 +722,7 @@ constexpr int kPotRows = kTile / (kPotThreads / kTile);  // rows per thread (4)
 
 __global__ void __launch_bounds__(kPotThreads) b_potrf_df_kernel(BCtl c, const BDesc* __restrict__ D, BState* S,
                                                                  int k) {
+  if (k >= *c.round_kmax) return;  // no matrix of this round has panel k
   __shared__ F2 colv[kTile], xrow[kTile];
   __shared__ F2 s_piv, s_r;
   __shared__ int s_bad, s_emax;
@@ -892,6 +905,7 @@ SKS_DEV void df_tile_abt(const TA* __restrict__ A, int64_t lda, int na, int sha,
 // the upper part.
 __global__ void __launch_bounds__(256) b_trsm_df_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
                                                         int total) {
+  if (k >= *c.round_kmax) return;  // no matrix of this round has panel k
   __shared__ __align__(16) float Ah[16][kTPf], Al[16][kTPf], Bh[16][kTPf], Bl[16][kTPf];
   tk_start(c, TK_FACTOR);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -930,6 +944,7 @@ __global__ void __launch_bounds__(256) b_trsm_df_kernel(BCtl c, const BDesc* __r
 // M_ij -= L_ik L_jk^T with the product in double-float.
 __global__ void __launch_bounds__(256) b_update_df_kernel(BCtl c, const BDesc* __restrict__ D, const BState* S, int k,
                                                           int total) {
+  if (k >= *c.round_kmax) return;  // no matrix of this round has panel k
   __shared__ __align__(16) float Ah[16][kTPf], Al[16][kTPf], Bh[16][kTPf], Bl[16][kTPf];
   tk_start(c, TK_FACTOR);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -1705,6 +1720,7 @@ __global__ void b_count_kernel(BCtl c, const BState* S) {
   a = block_sum(a, scratch);
   if (threadIdx.x == 0) {
     *c.active = a;
+    *c.round_kmax = 0;
     const long long r = ++*c.rounds;
     if (c.use_cond) cudaGraphSetConditional(c.cond, (a > 0 && r < c.max_rounds) ? 1u : 0u);
     if (c.tk) {
@@ -1731,6 +1747,7 @@ __global__ void b_reset_kernel(BCtl c) {
   }
   *c.apass_flops = 0.0;
   *c.gram_flops = 0.0;
+  *c.round_kmax = 0;
   *c.rounds = 0;
 }
 
@@ -1783,6 +1800,7 @@ struct Layout {
   BDesc* D = nullptr;
   BState* S = nullptr;
   int *pre_tri = nullptr, *pre_T = nullptr, *pre_ap = nullptr, *pre_red = nullptr, *active = nullptr;
+  int* round_kmax = nullptr;
   unsigned long long* tk = nullptr;
   double* apass_flops = nullptr;
   double* gram_flops = nullptr;
@@ -1836,6 +1854,7 @@ sks_status batch_layout(const sks_problem* probs, int P, const sks_opts* o, void
   L->pre_ap = c.take<int>(P + 1);
   L->pre_red = c.take<int>(P + 1);
   L->active = c.take<int>(1);
+  L->round_kmax = c.take<int>(1);
   L->tk = c.take<unsigned long long>(3 * kTimers);
   L->apass_flops = c.take<double>(1);
   L->gram_flops = c.take<double>(1);
@@ -2103,6 +2122,7 @@ sks_status batch_create(sks_batch** out, const sks_problem* probs, int P, const 
   c.pre_ap = L.pre_ap;
   c.pre_red = L.pre_red;
   c.active = L.active;
+  c.round_kmax = L.round_kmax;
   c.tk = L.tk;
   c.apass_flops = L.apass_flops;
   c.gram_flops = L.gram_flops;

@@ -364,14 +364,19 @@ sks_status sks_adjoint(const sks_problem* p, const sks_opts* o, const double* x,
 
 /* ---------------------------------------------------------------------------
  * Batched solve: `count` independent problems of eq. 1, each by the adaptive
- * PCG of Algorithm 2 with the same options (float64 plain form, SRHT
- * embedding, one right-hand side per problem, d <= 1024, n >= 1).  Every
- * decision of Algorithm 2 is taken on the device, per problem, so one round of
- * batched kernels advances every unfinished problem by one step or one
- * re-sketch; the rounds run inside one CUDA graph launch (a while loop on the
- * device, see the batch plans below) until all problems have stopped.  Each problem's iterates, m sequence and stop are
- * those of sks_adaptive_pcg_solve with the same options (up to the rounding
- * order of the sums); the same seed serves every problem.
+ * PCG of Algorithm 2 with the same options (SRHT embedding, one right-hand
+ * side per problem, d <= 1024, n >= 1, the estimate stop rule), in the plain
+ * form (o->precision SKS_PLAIN_F64, every A float64) or the mixed form
+ * (SKS_MIXED_REFINED, every A float32: float32 inner passes over A, refinement
+ * residuals b - H x and the preconditioner's Gram, factor and apply in
+ * double-float, max_outer refinement steps of relative accuracy inner_tol).
+ * Every decision of Algorithm 2 is taken on the device, per problem, so one
+ * round of batched kernels advances every unfinished problem by one step or
+ * one re-sketch; the rounds run inside one CUDA graph launch (a while loop on
+ * the device, see the batch plans below) until all problems have stopped.  In
+ * the plain form each problem's iterates, m sequence and stop are those of
+ * sks_adaptive_pcg_solve with the same options (up to the rounding order of
+ * the sums); the same seed serves every problem.
  * probs:  host array of `count` problem descriptions (device A, b, lambda).
  * x:      host array of `count` device pointers, d_i float64 each; in: x_0,
  *         out: the solution (the last accepted iterate for a problem that
@@ -428,7 +433,11 @@ sks_status sks_solve_batched(const sks_problem* probs, int count, const sks_opts
  * stay valid and unchanged (A, lambda) until sks_batch_destroy; b may change
  * between solves.  info->ms_setup is the planning time of the create call,
  * info->ms_solve the graph's device time.  Plans are not thread-safe: one
- * solve at a time per plan.
+ * solve at a time per plan.  With the environment variable
+ * SKS_BATCH_STEPWISE=1 sks_batch_solve launches the same setup and rounds one
+ * by one from the host instead (one synchronisation per round), for
+ * profilers that do not see the kernels inside a conditional graph node; the
+ * results are the same.
  * ------------------------------------------------------------------------- */
 typedef struct sks_batch sks_batch;
 sks_status sks_batch_create(sks_batch** out, const sks_problem* probs, int count, const sks_opts* o,

@@ -352,7 +352,9 @@ def fixed_solve(A, b, nu, lam, method="fixed-pcg", x0=None, check=True, **opts):
 
 class BatchSolver:
     """Many independent problems (each one (A, b, nu, lam)) solved together:
-    adaptive PCG per problem, every decision on the device.  The plan
+    adaptive PCG per problem, every decision on the device; precision="plain"
+    takes float64 A, precision="mixed" float32 A (float32 inner passes,
+    double-float refinement and preconditioner).  The plan
     (``sks_batch_create``: input checks, the A-pass unit height -- timed on
     this batch when rows_per_unit=0 -- and one instantiated CUDA graph whose
     while loop repeats the round until every problem has stopped) is made

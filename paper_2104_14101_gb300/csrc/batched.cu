@@ -428,34 +428,46 @@ __global__ void __launch_bounds__(256) b_gram_mixed_kernel(BCtl c, const BDesc* 
       ke = min(d, kb + per);
     }
     flops += 2.0 * kTile * kTile * (double)max(0, ke - kb);
-    for (int k0 = kb; k0 < ke; k0 += 16) {
-      if (s.form == 0) {
-        for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+    // the next chunk's elements are loaded into registers while the current
+    // one is multiplied (the gathered sketch rows' latency stays hidden)
+    constexpr int kPer = 16 * kTile / 256;  // elements per thread and operand
+    float pa[kPer], pb[kPer];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = threadIdx.x + 256 * t;
+        float a = 0.f, b = 0.f;
+        if (s.form == 0) {
           const int kk = e >> 6, ii = e & 63;
           const int r = k0 + kk;
-          float a = 0.f, b = 0.f;
           if (r < ke) {
             const float* y = q.Bf + (int64_t)q.perm[r] * d;
             if (i0 + ii < N) a = y[i0 + ii];
             if (j0 + ii < N) b = y[j0 + ii];
           }
-          As[kk][ii] = a;
-          Bs[kk][ii] = b;
-        }
-      } else {
-        for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+        } else {
           const int ii = e >> 4, kk = e & 15;
           const int col = k0 + kk;
-          float a = 0.f, b = 0.f;
           if (col < ke) {
             if (i0 + ii < N) a = __fmul_rn(q.Bf[(int64_t)q.perm[i0 + ii] * d + col], q.ilam[col]);
             if (j0 + ii < N) b = q.Bf[(int64_t)q.perm[j0 + ii] * d + col];
           }
-          As[kk][ii] = a;
-          Bs[kk][ii] = b;
         }
+        pa[t] = a;
+        pb[t] = b;
+      }
+    };
+    if (kb < ke) fetch(kb);
+    for (int k0 = kb; k0 < ke; k0 += 16) {
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = threadIdx.x + 256 * t;
+        const int kk = s.form == 0 ? e >> 6 : e & 15, ii = s.form == 0 ? e & 63 : e >> 4;
+        As[kk][ii] = pa[t];
+        Bs[kk][ii] = pb[t];
       }
       __syncthreads();
+      if (k0 + 16 < ke) fetch(k0 + 16);
 #pragma unroll 4
       for (int k = 0; k < 16; ++k) {
         const float4 a4 = *(const float4*)&As[k][ty * 4];

@@ -892,21 +892,35 @@ SKS_DEV void df_tile_abt(const TA* __restrict__ A, int64_t lda, int na, int sha,
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = F2{0.f, 0.f};
+  // the next 16 columns are loaded into registers (raw values, split when
+  // stored) while the current ones are multiplied; 256 threads, 4 elements
+  // of each operand per thread
+  constexpr int kPer = 16 * kTile / 256;
+  TA ra[kPer];
+  TB rb[kPer];
+  auto fetch = [&](int c0) {
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int e = threadIdx.x + 256 * t;
+      const int ii = e >> 4, col = c0 + (e & 15);
+      ra[t] = (col < K && ii < na) ? A[(int64_t)ii * lda + col] : TA{};
+      rb[t] = (col < K && ii < nbv) ? B[(int64_t)ii * ldb + col] : TB{};
+    }
+  };
+  if (K > 0) fetch(0);
   for (int c0 = 0; c0 < K; c0 += 16) {
-    for (int e = threadIdx.x; e < 16 * kTile; e += blockDim.x) {
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int e = threadIdx.x + 256 * t;
       const int ii = e >> 4, kk = e & 15;
-      const int col = c0 + kk;
-      F2 a = {0.f, 0.f}, b = {0.f, 0.f};
-      if (col < K) {
-        if (ii < na) a = ld_f2(A, (int64_t)ii * lda + col, sha);
-        if (ii < nbv) b = ld_f2(B, (int64_t)ii * ldb + col, shb);
-      }
+      const F2 a = ld_f2(ra + t, 0, sha), b = ld_f2(rb + t, 0, shb);
       Ah[kk][ii] = a.h;
       Al[kk][ii] = a.l;
       Bh[kk][ii] = b.h;
       Bl[kk][ii] = b.l;
     }
     __syncthreads();
+    if (c0 + 16 < K) fetch(c0 + 16);
     df_tile_chunk(Ah, Al, Bh, Bl, acc, tx, ty);
     __syncthreads();
   }
